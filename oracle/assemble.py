@@ -1,0 +1,166 @@
+"""Geometry and the assembled stiffness matrix (Section 3.1, Eq. laplaceproblemdiscrete).
+
+For the order-p level the element matrix is the Galerkin stiffness
+
+    A_e[i, j] = sum_q w_q |det J_q| (J_q^{-T} grad N_i(xi_q)) . (J_q^{-T} grad N_j(xi_q)),
+
+i.e. minus the paper's L^p_ij (the sign is flipped so that A is symmetric
+positive definite on the free nodes).  J_q is the Jacobian of the isoparametric
+order-P geometry map x(xi) = sum_i X_i N^P_i(xi) (the finest order P, also on
+the coarse levels: coarse operators are re-discretised with the finest
+geometry, the "direct assembly" option of Section 4.4).  In 3D the nodes of the
+order-P map are x, y affine over the base triangle and z = -h + sigma (h + eta)
+in sigma layers, which reproduces the sigma-transform of Section 3.1.
+
+The global matrix is A = sum_e Q_e^T A_e Q_e (COO with duplicates summed).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+from .mesh import Level
+from .refelem import RefPrism, RefTri, tri_basis
+
+
+class Problem:
+    """Mesh + p-levels (finest first) + the order-P geometry.
+
+    ``eta_nodal``: eta at the finest level's 2D nodes (canonical numbering); by
+    default the mesh's eta evaluated there."""
+
+    def __init__(self, mesh, levels, eta_nodal=None):
+        self.mesh = mesh
+        self.dim = mesh.dim
+        self.levels = [Level(mesh, p) for p in levels]
+        fin = self.levels[0]
+        self.P = levels[0]
+        if mesh.dim == 3:
+            if eta_nodal is None:
+                eta_nodal = np.zeros(fin.N2)
+                tn = RefTri(self.P).nodes
+                for b in range(mesh.tri.shape[0]):
+                    xy = fin.tri_node_xy(b, tn)
+                    eta_nodal[fin.map2[b]] = mesh.eta(xy[:, 0], xy[:, 1])
+            self.eta_nodal = np.asarray(eta_nodal, dtype=np.float64)
+        else:
+            self.eta_nodal = None
+        self._A = {}
+
+    # ----------------------------------------------------------- coordinates
+    def eta_at_level(self, li: int) -> np.ndarray:
+        """eta_P (the order-P surface interpolant) at level li's 2D nodes."""
+        lev, fin = self.levels[li], self.levels[0]
+        if li == 0:
+            return self.eta_nodal.copy()
+        B, _, _ = tri_basis(self.P, RefTri(lev.p).nodes)
+        out = np.zeros(lev.N2)
+        for b in range(self.mesh.tri.shape[0]):
+            out[lev.map2[b]] = B @ self.eta_nodal[fin.map2[b]]
+        return out
+
+    def coords(self, li: int) -> np.ndarray:
+        """Physical coordinates [N, dim] of level li's global nodes; in 3D
+        z = -h + sigma (h + eta_P) at the node."""
+        lev, mesh = self.levels[li], self.mesh
+        tn = RefTri(lev.p).nodes
+        xy2 = np.zeros((lev.N2, 2))
+        for b in range(mesh.tri.shape[0]):
+            xy2[lev.map2[b]] = lev.tri_node_xy(b, tn)
+        if self.dim == 2:
+            return xy2
+        eta2 = self.eta_at_level(li)
+        zn = RefPrism(lev.p).zn
+        nl, h = mesh.nlayers, mesh.depth
+        out = np.zeros((lev.N, 3))
+        for kz in range(nl * lev.p + 1):
+            l, k = divmod(kz, lev.p)
+            if l == nl:
+                l, k = nl - 1, lev.p
+            sigma = (l + (zn[k] + 1.0) / 2.0) / nl
+            sl = slice(kz * lev.N2, (kz + 1) * lev.N2)
+            out[sl, :2] = xy2
+            out[sl, 2] = -h + sigma * (h + eta2)
+        return out
+
+    # ----------------------------------------------------------- geometry
+    def element_nodes_P(self) -> np.ndarray:
+        """Coordinates of the order-P nodes of every element, [E, Np_P, dim]."""
+        mesh, P = self.mesh, self.P
+        fin = self.levels[0]
+        tn = RefTri(P).nodes
+        if self.dim == 2:
+            X = np.empty((mesh.tri.shape[0], tn.shape[0], 2))
+            for b in range(mesh.tri.shape[0]):
+                X[b] = fin.tri_node_xy(b, tn)
+            return X
+        ref = RefPrism(P)
+        nl, h = mesh.nlayers, mesh.depth
+        X = np.empty((mesh.nelem, ref.Np, 3))
+        for b in range(mesh.tri.shape[0]):
+            xy = fin.tri_node_xy(b, tn)
+            eta = self.eta_nodal[fin.map2[b]]
+            for l in range(nl):
+                e = b * nl + l
+                for k in range(P + 1):
+                    sigma = (l + (ref.zn[k] + 1.0) / 2.0) / nl
+                    sl = slice(k * ref.NT, (k + 1) * ref.NT)
+                    X[e, sl, :2] = xy
+                    X[e, sl, 2] = -h + sigma * (h + eta)
+        return X
+
+    def jacobians(self, li: int) -> np.ndarray:
+        """J[e, q, d, a] = d x_d / d xi_a of the order-P map at level li's quadrature points."""
+        lev = self.levels[li]
+        refP = RefTri(self.P) if self.dim == 2 else RefPrism(self.P)
+        _, gP = refP.basis_at(lev.ref.qpts)            # [dim, Nq, NpP]
+        X = self.element_nodes_P()
+        return np.einsum("eid,aqi->eqda", X, gP)
+
+    def geometric_factors(self, li: int) -> np.ndarray:
+        """G[e, q, a, b] = w_q |det J| (J^{-1} J^{-T})_{ab} at level li's quadrature points."""
+        J = self.jacobians(li)
+        det = np.linalg.det(J)
+        Jinv = np.linalg.inv(J)                          # [e, q, a, d]
+        w = self.levels[li].ref.qw
+        return (w[None, :, None, None] * np.abs(det)[:, :, None, None]
+                * np.einsum("eqad,eqbd->eqab", Jinv, Jinv))
+
+    # ----------------------------------------------------------- matrices
+    def element_matrices(self, li: int) -> np.ndarray:
+        """A_e [E, Np, Np] of level li from the definition (sum over quadrature points)."""
+        lev = self.levels[li]
+        G = self.geometric_factors(li)
+        g = lev.ref.grads                                  # [dim, Nq, Np]
+        dim, Nq, Np = g.shape
+        # H[e, a, q, j] = sum_b G[e, q, a, b] g[b, q, j]; A_e = sum_{a,q} g[a, q, i] H[e, a, q, j]
+        H = np.einsum("eqab,bqj->eaqj", G, g)
+        return np.matmul(g.reshape(dim * Nq, Np).T[None], H.reshape(-1, dim * Nq, Np))
+
+    def stiffness(self, li: int) -> sp.csr_matrix:
+        """Assembled global A (all nodes, no boundary conditions), CSR."""
+        if li in self._A:
+            return self._A[li]
+        lev = self.levels[li]
+        Ae = self.element_matrices(li)
+        E, Np = lev.emap.shape
+        rows = np.repeat(lev.emap, Np, axis=1).ravel()
+        cols = np.tile(lev.emap, (1, Np)).ravel()
+        A = sp.coo_matrix((Ae.ravel(), (rows, cols)), shape=(lev.N, lev.N)).tocsr()
+        A.sum_duplicates()
+        self._A[li] = A
+        return A
+
+    def free_matrix(self, li: int) -> sp.csr_matrix:
+        """A_FF: rows and columns of the free (non-Dirichlet) nodes."""
+        lev = self.levels[li]
+        A = self.stiffness(li)
+        return A[lev.free][:, lev.free].tocsr()
+
+    def masked_apply(self, li: int, x: np.ndarray) -> np.ndarray:
+        """The library's sem_apply convention: y_F = A_FF x_F, y_D = x_D."""
+        lev = self.levels[li]
+        A = self.stiffness(li)
+        xf = np.where(lev.dmask, 0.0, x)
+        y = A @ xf
+        return np.where(lev.dmask, x, y)
