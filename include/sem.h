@@ -1,0 +1,184 @@
+/*
+ * sem.h - C ABI of the GB300 p-multigrid spectral element Laplace solver.
+ *
+ * The library solves the Laplace problem for the velocity potential of the
+ * fully nonlinear potential-flow model (Section 2, Eq. laplaceproblem):
+ *     phi = phi~ on the free surface z = eta,  laplace(phi) = 0 in the fluid,
+ *     n . grad(phi) = 0 on the bottom and the walls,
+ * discretised by a Galerkin spectral element method with a continuous nodal
+ * basis of order P on straight triangles (2D vertical slices) or sigma-layer
+ * prisms with a curvilinear free surface (3D) (Section 3.1, Eq.
+ * laplaceproblemdiscrete), and solved by PCG (Algorithm 3), preconditioned
+ * defect correction (Algorithm 2) or flexible GMRES, each preconditioned by
+ * one geometric p-multigrid V-cycle (Algorithm 1) with Chebyshev-Jacobi
+ * smoothing, p-transfers P and R = P^T (Section 4.1, Eq. rest) and an FP64
+ * coarse solve at order 1.
+ *
+ * Conventions shared by every entry point
+ *  - The stiffness matrix is A = -L^p (L^p of Eq. laplaceproblemdiscrete), so
+ *    that A restricted to the free (non-Dirichlet) nodes is symmetric
+ *    positive definite.
+ *  - Vectors are FP64, one entry per global node of a level, in the library's
+ *    canonical numbering (first appearance over elements for triangle meshes;
+ *    id = kz * N2 + g2 for prism meshes, g2 the 2D id, kz the vertical index).
+ *  - "_dev" pointers are CUDA device pointers owned by the caller; "_host"
+ *    pointers are host memory owned by the caller.  The handle owns all other
+ *    device memory (geometry, maps, workspaces); no entry point allocates after
+ *    sem_setup.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls are
+ *    asynchronous with respect to the host except where stated.
+ *  - Errors are returned as sem_status; nothing exits, aborts or traps.  The
+ *    message of the last error of the calling thread is sem_last_error().
+ */
+#ifndef SEM_GB300_H
+#define SEM_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SEM_MAX_LEVELS 8
+
+typedef enum {
+    SEM_OK = 0,
+    SEM_NOT_CONVERGED = 1,  /* i_max reached; the last iterate and stats are written */
+    SEM_EINVAL = -1,        /* invalid argument (message in sem_last_error) */
+    SEM_ECUDA = -2,         /* CUDA runtime error */
+    SEM_ENOMEM = -3,        /* device or host allocation failed (sem_setup only) */
+    SEM_NAN = -4,           /* non-finite residual */
+    SEM_BREAKDOWN = -5,     /* p^T A p <= 0 in PCG, or a zero Krylov vector */
+    SEM_TIMEOUT = -6        /* a bounded device-side wait ran out */
+} sem_status;
+
+typedef enum { SEM_OUTER_PCG = 0, SEM_OUTER_FGMRES = 1, SEM_OUTER_PDC = 2 } sem_outer;
+typedef enum { SEM_PREC_FP64 = 0, SEM_PREC_MIXED_FP32 = 1 } sem_precision;
+
+/* Mesh description (host memory, read during sem_setup only).
+ * dim 2: ntri straight triangles in the (x, z) plane; vxy holds (x, z).
+ * dim 3: ntri base triangles in the (x, y) plane extruded into nlayers sigma
+ *        layers between the flat bottom z = -depth and the free surface
+ *        z = eta(x, y): the node at sigma in [0, 1] sits at
+ *        z = -depth + sigma * (depth + eta).  Prism e lies over base triangle
+ *        e / nlayers in layer e % nlayers (layer 0 at the bottom).
+ * Triangles are counter-clockwise; vertex ids index vxy.
+ * eta: free-surface elevation at the order-P 2D nodes of the base mesh in
+ *      canonical order (see sem_mesh_nodes2d), or NULL for a flat surface.
+ * face_bc: [nelem][nfaces] flags, 1 = Dirichlet (phi = phi~), 0 = homogeneous
+ *      Neumann or interior.  Triangle faces: f0=(v0,v1), f1=(v1,v2), f2=(v2,v0).
+ *      Prism faces: f0..f2 lateral quads over those edges, f3 bottom, f4 top. */
+typedef struct {
+    int dim;
+    int nvert;
+    const double* vxy;          /* [nvert][2] */
+    int ntri;
+    const int* tri;             /* [ntri][3] */
+    int nlayers;                /* dim 3 only (>= 1) */
+    double depth;               /* dim 3 only (> 0) */
+    const double* eta;          /* dim 3 only, [N2 at order P] or NULL */
+    const signed char* face_bc; /* [nelem][nfaces] */
+} sem_mesh;
+
+/* Solver options; fill with sem_default_options and adjust.
+ * level_p[0] = P > level_p[1] > ... > level_p[nlevels-1] = 1 (order per level).
+ * Smoother: k_cheb-step Chebyshev iteration on D^{-1}A over [cheb_lo*b, b],
+ * b = cheb_hi * lambda_hat, lambda_hat = power_its power iterations from
+ * x_i = sin(i+1) on free nodes; nu1 pre- and nu2 post-sweeps (Algorithm 1).
+ * Stop test ||r||_2 <= rtol*||f||_2 + atol on the FP64 free-node residual.
+ * The coarse order-1 system is solved by FP64 Jacobi-CG to coarse_rtol
+ * relative residual (at most coarse_imax iterations). */
+typedef struct {
+    int outer;                  /* sem_outer */
+    int precision;              /* sem_precision: FP64, or FP32 V-cycle inside an FP64 outer */
+    int nu1, nu2, k_cheb;
+    double cheb_lo, cheb_hi;
+    int power_its;
+    int nlevels;
+    int level_p[SEM_MAX_LEVELS];
+    double rtol, atol;
+    int imax;
+    int gmres_m;                /* FGMRES restart length */
+    double coarse_rtol;
+    int coarse_imax;
+    int profile;                /* 1: time every operator apply with CUDA events (sem_stats.apply_ms) */
+} sem_options;
+
+typedef struct {
+    int status;                 /* sem_status of the solve */
+    int iters;                  /* outer iterations (preconditioner applications after the first) */
+    double fnorm;               /* ||f||_2 of the lifted right-hand side */
+    double res0, res_final;     /* ||r||_2 at start and end (FP64 residual) */
+    double q_mean;              /* geometric mean residual contraction per iteration (Eq. convrate) */
+    long long fine_applies;     /* operator applies on the finest level (work units, Section 4.4) */
+    long long vcycles;
+    int coarse_iters_max;       /* largest coarse CG iteration count seen */
+    double ms;                  /* wall time of the call on the stream (CUDA events) */
+    double apply_ms;            /* summed time of finest-level apply kernels (profile = 1) */
+    long long apply_launches;   /* finest-level apply kernel launches (profile = 1) */
+    long long kernel_launches;  /* kernels of this library launched by the call */
+} sem_stats;
+
+typedef struct sem_handle sem_handle;
+
+/* Defaults for finest order P: PCG, FP64, nu1 = nu2 = 1, k_cheb = 3,
+ * cheb_lo = 0.1, cheb_hi = 1.1, power_its = 20, levels P -> ... -> 1 from the
+ * table {6:6,3,1; 5:5,3,1; 4:4,2,1; 3:3,2,1; 2:2,1; 1:1}, rtol 1e-8, atol 0,
+ * imax 200, gmres_m 30, coarse_rtol 1e-12, coarse_imax 5000. */
+void sem_default_options(sem_options* opts, int P);
+
+/* Canonical order-p 2D node coordinates of the triangle mesh in `mesh`
+ * (x, z for dim 2; x, y of the base mesh for dim 3).  Pass xy = NULL to get the
+ * count in *n2 only; otherwise xy must hold 2 * (*n2) doubles.  Host only,
+ * synchronous.  This is where the caller samples eta before sem_setup. */
+sem_status sem_mesh_nodes2d(const sem_mesh* mesh, int p, long long* n2, double* xy);
+
+/* Build every level (numbering, geometric factors, Jacobi diagonals, Chebyshev
+ * bounds, transfers, coarse workspace) and allocate all device memory on the
+ * current CUDA device.  Synchronous.  P in 1..6; opts NULL = defaults. */
+sem_status sem_setup(const sem_mesh* mesh, int P, const sem_options* opts, sem_handle** out);
+void sem_destroy(sem_handle* h);
+
+/* Sizes of a level: global nodes, Dirichlet nodes, elements, nodes per element. */
+sem_status sem_query(const sem_handle* h, int level, long long* ndof, long long* ndirichlet,
+                     long long* nelem, int* np);
+/* Host copies: Dirichlet node ids (ascending; the order of dirichlet_eta),
+ * node coordinates [N][dim], the element map [E][Np] (global ids), the
+ * lambda_hat estimate of every level (coarsest entry 0). */
+sem_status sem_dirichlet_nodes(const sem_handle* h, int level, long long* idx_host);
+sem_status sem_node_coords(const sem_handle* h, int level, double* xyz_host);
+sem_status sem_element_map(const sem_handle* h, int level, int* map_host);
+sem_status sem_lambda_max(const sem_handle* h, double* lam_host);
+/* The assembled diagonal of A at a level (all nodes), host copy. */
+sem_status sem_diagonal(const sem_handle* h, int level, double* diag_host);
+
+/* Matrix-free operator (Eq. laplaceproblemdiscrete, a2 of the hot path):
+ * y_F = A_FF x_F on the free nodes and y_D = x_D on the Dirichlet nodes of
+ * `level` (0 = finest).  x_dev, y_dev: N doubles, distinct buffers. */
+sem_status sem_apply(sem_handle* h, int level, const double* x_dev, double* y_dev, void* stream);
+
+/* One V-cycle (Algorithm 1, zero initial guess on every level): z = M^{-1} r on
+ * the finest level.  Dirichlet entries of r are ignored; those of z are 0. */
+sem_status pmg_vcycle(sem_handle* h, const double* r_dev, double* z_dev, void* stream);
+
+/* Solve for phi on the finest level.  dirichlet_eta_dev: phi~ at the Dirichlet
+ * nodes (order of sem_dirichlet_nodes); rhs_dev: optional load vector added to
+ * the free rows (NULL = 0, the Laplace problem); tol: rtol (atol from options;
+ * tol <= 0 uses the options' rtol).  phi_dev receives phi on all nodes
+ * (phi = phi~ on Dirichlet nodes).  Synchronises the stream once per outer
+ * iteration to read the residual norm.  Returns SEM_NOT_CONVERGED with the last
+ * iterate when imax is reached.  stats may be NULL. */
+sem_status laplace_solve(sem_handle* h, const double* rhs_dev, const double* dirichlet_eta_dev,
+                         double tol, double* phi_dev, sem_stats* stats, void* stream);
+
+/* As laplace_solve, with host buffers: copies dirichlet_eta (and rhs) to the
+ * device, solves, copies phi back; the copies are inside the timed call.
+ * Synchronous. */
+sem_status laplace_solve_host(sem_handle* h, const double* rhs_host, const double* dirichlet_eta_host,
+                              double tol, double* phi_host, sem_stats* stats, void* stream);
+
+/* Thread-local message of the last error ("" if none). */
+const char* sem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SEM_GB300_H */

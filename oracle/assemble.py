@@ -84,42 +84,42 @@ class Problem:
         return out
 
     # ----------------------------------------------------------- geometry
-    def element_nodes_P(self) -> np.ndarray:
-        """Coordinates of the order-P nodes of every element, [E, Np_P, dim]."""
+    def element_nodes_P(self, elements=None) -> np.ndarray:
+        """Coordinates of the order-P nodes of the given elements (default all), [E, Np_P, dim]."""
         mesh, P = self.mesh, self.P
         fin = self.levels[0]
         tn = RefTri(P).nodes
+        elems = np.arange(mesh.nelem) if elements is None else np.asarray(elements)
         if self.dim == 2:
-            X = np.empty((mesh.tri.shape[0], tn.shape[0], 2))
-            for b in range(mesh.tri.shape[0]):
-                X[b] = fin.tri_node_xy(b, tn)
+            X = np.empty((elems.size, tn.shape[0], 2))
+            for i, b in enumerate(elems):
+                X[i] = fin.tri_node_xy(b, tn)
             return X
         ref = RefPrism(P)
         nl, h = mesh.nlayers, mesh.depth
-        X = np.empty((mesh.nelem, ref.Np, 3))
-        for b in range(mesh.tri.shape[0]):
+        X = np.empty((elems.size, ref.Np, 3))
+        for i, e in enumerate(elems):
+            b, l = divmod(int(e), nl)
             xy = fin.tri_node_xy(b, tn)
             eta = self.eta_nodal[fin.map2[b]]
-            for l in range(nl):
-                e = b * nl + l
-                for k in range(P + 1):
-                    sigma = (l + (ref.zn[k] + 1.0) / 2.0) / nl
-                    sl = slice(k * ref.NT, (k + 1) * ref.NT)
-                    X[e, sl, :2] = xy
-                    X[e, sl, 2] = -h + sigma * (h + eta)
+            for k in range(P + 1):
+                sigma = (l + (ref.zn[k] + 1.0) / 2.0) / nl
+                sl = slice(k * ref.NT, (k + 1) * ref.NT)
+                X[i, sl, :2] = xy
+                X[i, sl, 2] = -h + sigma * (h + eta)
         return X
 
-    def jacobians(self, li: int) -> np.ndarray:
+    def jacobians(self, li: int, elements=None) -> np.ndarray:
         """J[e, q, d, a] = d x_d / d xi_a of the order-P map at level li's quadrature points."""
         lev = self.levels[li]
         refP = RefTri(self.P) if self.dim == 2 else RefPrism(self.P)
         _, gP = refP.basis_at(lev.ref.qpts)            # [dim, Nq, NpP]
-        X = self.element_nodes_P()
+        X = self.element_nodes_P(elements)
         return np.einsum("eid,aqi->eqda", X, gP)
 
-    def geometric_factors(self, li: int) -> np.ndarray:
+    def geometric_factors(self, li: int, elements=None) -> np.ndarray:
         """G[e, q, a, b] = w_q |det J| (J^{-1} J^{-T})_{ab} at level li's quadrature points."""
-        J = self.jacobians(li)
+        J = self.jacobians(li, elements)
         det = np.linalg.det(J)
         Jinv = np.linalg.inv(J)                          # [e, q, a, d]
         w = self.levels[li].ref.qw
@@ -127,10 +127,10 @@ class Problem:
                 * np.einsum("eqad,eqbd->eqab", Jinv, Jinv))
 
     # ----------------------------------------------------------- matrices
-    def element_matrices(self, li: int) -> np.ndarray:
+    def element_matrices(self, li: int, elements=None) -> np.ndarray:
         """A_e [E, Np, Np] of level li from the definition (sum over quadrature points)."""
         lev = self.levels[li]
-        G = self.geometric_factors(li)
+        G = self.geometric_factors(li, elements)
         g = lev.ref.grads                                  # [dim, Nq, Np]
         dim, Nq, Np = g.shape
         # H[e, a, q, j] = sum_b G[e, q, a, b] g[b, q, j]; A_e = sum_{a,q} g[a, q, i] H[e, a, q, j]
@@ -164,3 +164,21 @@ class Problem:
         xf = np.where(lev.dmask, 0.0, x)
         y = A @ xf
         return np.where(lev.dmask, x, y)
+
+    def apply_rows(self, li: int, x: np.ndarray, rows: np.ndarray, masked: bool = True) -> np.ndarray:
+        """Rows of the masked apply (y_F = A_FF x_F, y_D = x_D), or of the plain
+        product A x (masked=False), computed one by one from the element matrices
+        of the elements containing each row's node."""
+        lev = self.levels[li]
+        rows = np.asarray(rows)
+        hit = np.isin(lev.emap, rows)
+        elems = np.flatnonzero(hit.any(axis=1))
+        Ae = self.element_matrices(li, elems)
+        xf = np.where(lev.dmask, 0.0, x) if masked else x
+        out = {int(r): 0.0 for r in rows}
+        for k, e in enumerate(elems):
+            ye = Ae[k] @ xf[lev.emap[e]]
+            for l, g in enumerate(lev.emap[e]):
+                if int(g) in out:
+                    out[int(g)] += ye[l]
+        return np.array([x[r] if (masked and lev.dmask[r]) else out[int(r)] for r in rows])

@@ -88,10 +88,9 @@ class Level:
             self.N = N2 * (nl * p + 1)
         dmask = np.zeros(self.N, dtype=bool)
         fb = mesh.face_bc
-        for e in range(self.emap.shape[0]):
-            for f in range(fb.shape[1]):
-                if fb[e, f]:
-                    dmask[self.emap[e, self.ref.face_nodes(f)]] = True
+        faces = [np.asarray(self.ref.face_nodes(f)) for f in range(fb.shape[1])]
+        for e, f in zip(*np.nonzero(fb)):
+            dmask[self.emap[e, faces[f]]] = True
         self.dmask = dmask
         self.free = np.flatnonzero(~dmask)
         self.dirichlet = np.flatnonzero(dmask)

@@ -1,0 +1,69 @@
+"""Timed run of the oracle's p-multigrid PCG (Algorithm 3) on a bounded sample.
+
+Used only by bench.py's CPU baseline and reference arm, as a separate process
+(so that thread limits apply before NumPy loads).  The oracle runs as it
+stands: assembled CSR matrices, SciPy sparse products, sparse LU coarse solve.
+
+    python -m oracle.timing --n 8 --P 6 --nlayers 4 --solves 4 [--warmup 0]
+
+prints one JSON line: free DOF, solves, seconds, DOF/s, iterations.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=8)
+    ap.add_argument("--nlayers", type=int, default=4)
+    ap.add_argument("--P", type=int, default=6)
+    ap.add_argument("--solves", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=0)
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--per-solve", action="store_true", help="print one line per timed solve")
+    a = ap.parse_args(argv)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import numpy as np
+
+    import workloads as W
+    from oracle import solvers as S
+    from oracle.assemble import Problem
+
+    levels = {6: [6, 3, 1], 5: [5, 3, 1], 4: [4, 2, 1], 3: [3, 2, 1], 2: [2, 1], 1: [1]}[a.P]
+    mesh = W.config_box3d(a.n, a.nlayers)
+    t0 = time.perf_counter()
+    prob = Problem(mesh, levels)
+    lev = prob.levels[0]
+    C = prob.coords(0)
+    phiD = W.potential3d(*C[lev.dirichlet].T)
+    ops = S.MGOperators(prob, lo=0.1, hi=1.1)
+    setup_s = time.perf_counter() - t0
+    for _ in range(a.warmup):
+        S.pcg(ops, S.lift(prob, phiD), rtol=a.rtol)
+    times, iters = [], []
+    for _ in range(a.solves):
+        t = time.perf_counter()
+        f = S.lift(prob, phiD)
+        res = S.pcg(ops, f, rtol=a.rtol)
+        u = res.u
+        u[lev.dirichlet] = phiD
+        times.append(time.perf_counter() - t)
+        iters.append(res.iters)
+        if a.per_solve:
+            print(json.dumps({"solve_s": times[-1], "iters": res.iters}), flush=True)
+    dof = int(lev.free.size)
+    tot = float(np.sum(times))
+    print(json.dumps({"dof_free": dof, "solves": a.solves, "seconds": tot, "dof_per_s": dof * a.solves / tot,
+                      "solves_per_s": a.solves / tot, "iters": iters, "setup_s": setup_s,
+                      "mesh": f"{a.n}x{a.n}x{a.nlayers} P={a.P}"}))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,307 @@
+"""Python binding of the GB300 p-multigrid spectral element Laplace solver.
+
+Argument marshalling only: every function forwards to the C ABI of
+``libsem_gb300.so`` (declared in ``include/sem.h``) with the same name.  Device
+buffers are passed as CUDA tensors (or raw device pointers), streams as
+``torch.cuda.Stream`` (or raw ``cudaStream_t`` integers).  Importing this
+module fails loudly when the CUDA library has not been built: there is no CPU
+fallback of any kind.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, Structure, byref, c_byte, c_char_p, c_double, c_int, c_longlong, c_void_p
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsem_gb300.so")
+SEM_MAX_LEVELS = 8
+
+SEM_OK, SEM_NOT_CONVERGED = 0, 1
+SEM_EINVAL, SEM_ECUDA, SEM_ENOMEM, SEM_NAN, SEM_BREAKDOWN, SEM_TIMEOUT = -1, -2, -3, -4, -5, -6
+OUTER = {"pcg": 0, "fgmres": 1, "pdc": 2}
+PRECISION = {"fp64": 0, "mixed_fp32": 1}
+
+EXPORTS = ("sem_default_options", "sem_mesh_nodes2d", "sem_setup", "sem_destroy", "sem_query",
+           "sem_dirichlet_nodes", "sem_node_coords", "sem_element_map", "sem_lambda_max", "sem_diagonal",
+           "sem_apply", "pmg_vcycle", "laplace_solve", "laplace_solve_host", "sem_last_error")
+
+
+class SemMesh(Structure):
+    _fields_ = [("dim", c_int), ("nvert", c_int), ("vxy", POINTER(c_double)), ("ntri", c_int),
+                ("tri", POINTER(c_int)), ("nlayers", c_int), ("depth", c_double),
+                ("eta", POINTER(c_double)), ("face_bc", POINTER(c_byte))]
+
+
+class SemOptions(Structure):
+    _fields_ = [("outer", c_int), ("precision", c_int), ("nu1", c_int), ("nu2", c_int), ("k_cheb", c_int),
+                ("cheb_lo", c_double), ("cheb_hi", c_double), ("power_its", c_int), ("nlevels", c_int),
+                ("level_p", c_int * SEM_MAX_LEVELS), ("rtol", c_double), ("atol", c_double), ("imax", c_int),
+                ("gmres_m", c_int), ("coarse_rtol", c_double), ("coarse_imax", c_int), ("profile", c_int)]
+
+
+class SemStats(Structure):
+    _fields_ = [("status", c_int), ("iters", c_int), ("fnorm", c_double), ("res0", c_double),
+                ("res_final", c_double), ("q_mean", c_double), ("fine_applies", c_longlong),
+                ("vcycles", c_longlong), ("coarse_iters_max", c_int), ("ms", c_double),
+                ("apply_ms", c_double), ("apply_launches", c_longlong), ("kernel_launches", c_longlong)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class SemError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run paper_2009_00705_gb300.build.build() "
+                          "(the solver has no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    L.sem_default_options.argtypes = [POINTER(SemOptions), c_int]
+    L.sem_default_options.restype = None
+    L.sem_mesh_nodes2d.argtypes = [POINTER(SemMesh), c_int, POINTER(c_longlong), POINTER(c_double)]
+    L.sem_setup.argtypes = [POINTER(SemMesh), c_int, POINTER(SemOptions), POINTER(c_void_p)]
+    L.sem_destroy.argtypes = [c_void_p]
+    L.sem_destroy.restype = None
+    L.sem_query.argtypes = [c_void_p, c_int, POINTER(c_longlong), POINTER(c_longlong), POINTER(c_longlong),
+                            POINTER(c_int)]
+    L.sem_dirichlet_nodes.argtypes = [c_void_p, c_int, POINTER(c_longlong)]
+    L.sem_node_coords.argtypes = [c_void_p, c_int, POINTER(c_double)]
+    L.sem_element_map.argtypes = [c_void_p, c_int, POINTER(c_int)]
+    L.sem_lambda_max.argtypes = [c_void_p, POINTER(c_double)]
+    L.sem_diagonal.argtypes = [c_void_p, c_int, POINTER(c_double)]
+    L.sem_apply.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_void_p]
+    L.pmg_vcycle.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
+    L.laplace_solve.argtypes = [c_void_p, c_void_p, c_void_p, c_double, c_void_p, POINTER(SemStats), c_void_p]
+    L.laplace_solve_host.argtypes = [c_void_p, c_void_p, c_void_p, c_double, c_void_p, POINTER(SemStats),
+                                     c_void_p]
+    L.sem_last_error.restype = c_char_p
+    for name in ("sem_mesh_nodes2d", "sem_setup", "sem_query", "sem_dirichlet_nodes", "sem_node_coords",
+                 "sem_element_map", "sem_lambda_max", "sem_diagonal", "sem_apply", "pmg_vcycle",
+                 "laplace_solve", "laplace_solve_host"):
+        getattr(L, name).restype = c_int
+    _lib = L
+    return L
+
+
+def _check(status: int, allow=(SEM_OK,)) -> int:
+    if status not in allow:
+        raise SemError(status, lib().sem_last_error().decode())
+    return status
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _dptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(POINTER(ctype))
+
+
+class _MeshArgs:
+    """Keeps the numpy arrays of a SemMesh alive while the library reads them."""
+
+    def __init__(self, mesh, eta_nodal=None):
+        self.vxy = np.ascontiguousarray(mesh.vxy, dtype=np.float64)
+        self.tri = np.ascontiguousarray(mesh.tri, dtype=np.int32)
+        self.fb = np.ascontiguousarray(mesh.face_bc, dtype=np.int8)
+        self.eta = None if eta_nodal is None else np.ascontiguousarray(eta_nodal, dtype=np.float64)
+        self.s = SemMesh(int(mesh.dim), int(self.vxy.shape[0]), _dptr(self.vxy, c_double), int(self.tri.shape[0]),
+                         _dptr(self.tri, c_int), int(getattr(mesh, "nlayers", 0) or 0),
+                         float(getattr(mesh, "depth", 1.0)),
+                         _dptr(self.eta, c_double) if self.eta is not None else None, _dptr(self.fb, c_byte))
+
+
+# ---------------------------------------------------------------- C ABI, same names
+def sem_default_options(P: int, **overrides) -> SemOptions:
+    o = SemOptions()
+    lib().sem_default_options(byref(o), int(P))
+    for k, v in overrides.items():
+        if k == "levels":
+            o.nlevels = len(v)
+            for i, p in enumerate(v):
+                o.level_p[i] = int(p)
+        elif k == "outer":
+            o.outer = OUTER[v] if isinstance(v, str) else int(v)
+        elif k == "precision":
+            o.precision = PRECISION[v] if isinstance(v, str) else int(v)
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def sem_mesh_nodes2d(mesh, p: int) -> np.ndarray:
+    m = _MeshArgs(mesh)
+    n = c_longlong(0)
+    _check(lib().sem_mesh_nodes2d(byref(m.s), int(p), byref(n), None))
+    xy = np.zeros((n.value, 2))
+    _check(lib().sem_mesh_nodes2d(byref(m.s), int(p), byref(n), _dptr(xy, c_double)))
+    return xy
+
+
+def sem_setup(mesh, P: int, opts: SemOptions | None = None, eta_nodal=None) -> int:
+    m = _MeshArgs(mesh, eta_nodal)
+    h = c_void_p()
+    _check(lib().sem_setup(byref(m.s), int(P), byref(opts) if opts is not None else None, byref(h)))
+    return h.value
+
+
+def sem_destroy(h: int) -> None:
+    lib().sem_destroy(h)
+
+
+def sem_query(h: int, level: int = 0) -> dict:
+    N, nd, ne, npe = c_longlong(), c_longlong(), c_longlong(), c_int()
+    _check(lib().sem_query(h, level, byref(N), byref(nd), byref(ne), byref(npe)))
+    return {"ndof": N.value, "ndirichlet": nd.value, "nelem": ne.value, "np": npe.value}
+
+
+def sem_dirichlet_nodes(h: int, level: int = 0) -> np.ndarray:
+    q = sem_query(h, level)
+    out = np.zeros(q["ndirichlet"], dtype=np.int64)
+    _check(lib().sem_dirichlet_nodes(h, level, _dptr(out, c_longlong)))
+    return out
+
+
+def sem_node_coords(h: int, level: int = 0, dim: int = 3) -> np.ndarray:
+    q = sem_query(h, level)
+    out = np.zeros((q["ndof"], dim))
+    _check(lib().sem_node_coords(h, level, _dptr(out, c_double)))
+    return out
+
+
+def sem_element_map(h: int, level: int = 0) -> np.ndarray:
+    q = sem_query(h, level)
+    out = np.zeros((q["nelem"], q["np"]), dtype=np.int32)
+    _check(lib().sem_element_map(h, level, _dptr(out, c_int)))
+    return out
+
+
+def sem_lambda_max(h: int, nlevels: int) -> np.ndarray:
+    out = np.zeros(nlevels)
+    _check(lib().sem_lambda_max(h, _dptr(out, c_double)))
+    return out
+
+
+def sem_diagonal(h: int, level: int = 0) -> np.ndarray:
+    q = sem_query(h, level)
+    out = np.zeros(q["ndof"])
+    _check(lib().sem_diagonal(h, level, _dptr(out, c_double)))
+    return out
+
+
+def sem_apply(h: int, level: int, x, y, stream=None) -> None:
+    _check(lib().sem_apply(h, level, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def pmg_vcycle(h: int, r, z, stream=None) -> None:
+    _check(lib().pmg_vcycle(h, _ptr(r), _ptr(z), _stream(stream)))
+
+
+def laplace_solve(h: int, rhs, dirichlet_eta, tol: float, phi, stream=None, allow_not_converged=False) -> dict:
+    st = SemStats()
+    allow = (SEM_OK, SEM_NOT_CONVERGED) if allow_not_converged else (SEM_OK,)
+    _check(lib().laplace_solve(h, _ptr(rhs), _ptr(dirichlet_eta), float(tol), _ptr(phi), byref(st),
+                               _stream(stream)), allow)
+    return st.as_dict()
+
+
+def laplace_solve_host(h: int, rhs, dirichlet_eta: np.ndarray, tol: float, phi: np.ndarray, stream=None) -> dict:
+    """Host-buffer variant: dirichlet_eta / rhs / phi are host arrays (pinned memory recommended)."""
+    st = SemStats()
+
+    def hp(a):
+        if a is None:
+            return None
+        return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+    _check(lib().laplace_solve_host(h, hp(rhs), hp(dirichlet_eta), float(tol), hp(phi), byref(st),
+                                    _stream(stream)))
+    return st.as_dict()
+
+
+def sem_last_error() -> str:
+    return lib().sem_last_error().decode()
+
+
+# ---------------------------------------------------------------- convenience wrapper
+class Solver:
+    """Owns one sem_handle.  ``mesh`` is any object with dim, vxy, tri, nlayers,
+    depth and face_bc (e.g. workloads.Mesh); ``eta_nodal`` is eta at the order-P
+    2D nodes (see sem_mesh_nodes2d), or None for a flat surface."""
+
+    def __init__(self, mesh, P: int, eta_nodal=None, **opts):
+        self.P = P
+        self.dim = int(mesh.dim)
+        self.opts = sem_default_options(P, **opts)
+        self.nlevels = self.opts.nlevels
+        self.h = sem_setup(mesh, P, self.opts, eta_nodal)
+
+    def close(self):
+        if self.h:
+            sem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def query(self, level=0):
+        return sem_query(self.h, level)
+
+    def dirichlet_nodes(self, level=0):
+        return sem_dirichlet_nodes(self.h, level)
+
+    def coords(self, level=0):
+        return sem_node_coords(self.h, level, self.dim)
+
+    def element_map(self, level=0):
+        return sem_element_map(self.h, level)
+
+    def lambdas(self):
+        return sem_lambda_max(self.h, self.nlevels)
+
+    def diagonal(self, level=0):
+        return sem_diagonal(self.h, level)
+
+    def apply(self, level, x, y, stream=None):
+        sem_apply(self.h, level, x, y, stream)
+
+    def vcycle(self, r, z, stream=None):
+        pmg_vcycle(self.h, r, z, stream)
+
+    def solve(self, dirichlet_eta, phi, tol=0.0, rhs=None, stream=None, allow_not_converged=False):
+        return laplace_solve(self.h, rhs, dirichlet_eta, tol, phi, stream, allow_not_converged)
+
+    def solve_host(self, dirichlet_eta, phi, tol=0.0, rhs=None, stream=None):
+        return laplace_solve_host(self.h, rhs, dirichlet_eta, tol, phi, stream)

@@ -1,0 +1,861 @@
+// CUDA kernels of the p-multigrid SEM Laplace solver (sm_103a).
+//
+//  * matrix-free stiffness apply (Eq. laplaceproblemdiscrete), sum-factorised in
+//    the vertical direction of the prisms: gather -> reference derivatives at
+//    the quadrature points -> geometric factors -> transposed contraction ->
+//    direct-stiffness summation into the global vector;
+//  * geometric factors G = w |det J| J^{-1} J^{-T} of the sigma-layer prism map
+//    (Section 3.1, Eq. jacobian / K) and of straight triangles;
+//  * the assembled diagonal (Jacobi smoother), p-restriction R = P^T and
+//    prolongation P (Section 4.1, Eq. rest), Chebyshev smoothing updates and
+//    the FP64 reductions of the Krylov iterations (Algorithms 2, 3).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "sem_internal.hpp"
+
+namespace sem {
+
+namespace {
+
+constexpr int kVecThreads = 256;
+constexpr int kRedThreads = 256;
+constexpr int kSMs = 152;
+
+inline int vec_grid(long long n) {
+    long long g = (n + kVecThreads - 1) / kVecThreads;
+    if (g > kSMs * 16) g = kSMs * 16;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+template <int P, bool PRISM>
+struct Dims {
+    static constexpr int NT = (P + 1) * (P + 2) / 2;
+    static constexpr int NZ = PRISM ? P + 1 : 1;
+    static constexpr int QT = (P + 1) * (P + 1);
+    static constexpr int QZ = PRISM ? P + 1 : 1;
+    static constexpr int Np = NT * NZ;
+    static constexpr int Nq = QT * QZ;
+    static constexpr int NC = PRISM ? 6 : 3;
+    static constexpr int NREF = 6 * QT * NT + 2 * QZ * NZ;
+    static constexpr int NWORK = Np + 2 * NT * QZ + 3 * Nq;
+};
+
+__device__ __forceinline__ int decode(int m) { return m >= 0 ? m : -m - 1; }
+
+// ------------------------------------------------------------------ apply
+// One CTA processes elements e = blockIdx.x, blockIdx.x + gridDim.x, ...
+// Shared memory: the level's reference matrices, then per-element work arrays.
+template <int P, bool PRISM, typename T, bool LIFT>
+__global__ void __launch_bounds__(128) k_apply(int E, const int* __restrict__ map, const T* __restrict__ G,
+                                               const T* __restrict__ refm, const T* __restrict__ x,
+                                               T* __restrict__ y, const int* __restrict__ skip) {
+    using D = Dims<P, PRISM>;
+    if (skip != nullptr && *skip) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    const T* sBt = sm;                       // [QT][NT]
+    const T* sDr = sBt + D::QT * D::NT;
+    const T* sDs = sDr + D::QT * D::NT;
+    const T* sBtT = sDs + D::QT * D::NT;     // [NT][QT]
+    const T* sDrT = sBtT + D::QT * D::NT;
+    const T* sDsT = sDrT + D::QT * D::NT;
+    const T* sBz = sDsT + D::QT * D::NT;     // [QZ][NZ]
+    const T* sDz = sBz + D::QZ * D::NZ;
+    T* xe = sm + D::NREF;                    // [Np]
+    T* U = xe + D::Np;                       // [NT][QZ]  (z-interpolated values; later X_r)
+    T* W = U + D::NT * D::QZ;                // [NT][QZ]  (z-derivatives; later X_t)
+    T* vr = W + D::NT * D::QZ;               // [Nq]
+    T* vs = vr + D::Nq;
+    T* vt = vs + D::Nq;
+    for (int i = threadIdx.x; i < D::NREF; i += blockDim.x) sm[i] = refm[i];
+    __syncthreads();
+    for (int e = blockIdx.x; e < E; e += gridDim.x) {
+        const int* me = map + (size_t)e * D::Np;
+        for (int i = threadIdx.x; i < D::Np; i += blockDim.x) {
+            const int m = me[i];
+            xe[i] = (m >= 0) ? x[m] : (LIFT ? x[-m - 1] : T(0));
+        }
+        __syncthreads();
+        if (PRISM) {
+            // vertical stage: values and t-derivatives at the vertical Gauss points
+            for (int i = threadIdx.x; i < D::NT * D::QZ; i += blockDim.x) {
+                const int n = i / D::QZ, qz = i - n * D::QZ;
+                T u = 0, w = 0;
+#pragma unroll
+                for (int k = 0; k < D::NZ; ++k) {
+                    const T xv = xe[k * D::NT + n];
+                    u += sBz[qz * D::NZ + k] * xv;
+                    w += sDz[qz * D::NZ + k] * xv;
+                }
+                U[i] = u;
+                W[i] = w;
+            }
+        } else {
+            for (int i = threadIdx.x; i < D::NT; i += blockDim.x) U[i] = xe[i];
+        }
+        __syncthreads();
+        // triangle stage and geometric factors at every quadrature point
+        const T* Ge = G + (size_t)e * D::NC * D::Nq;
+        for (int q = threadIdx.x; q < D::Nq; q += blockDim.x) {
+            const int qz = q / D::QT, qt = q - qz * D::QT;
+            T ur = 0, us = 0, ut = 0;
+#pragma unroll 4
+            for (int n = 0; n < D::NT; ++n) {
+                const T uv = U[n * D::QZ + qz];
+                ur += sDrT[n * D::QT + qt] * uv;
+                us += sDsT[n * D::QT + qt] * uv;
+                if (PRISM) ut += sBtT[n * D::QT + qt] * W[n * D::QZ + qz];
+            }
+            if (PRISM) {
+                const T g0 = Ge[q], g1 = Ge[D::Nq + q], g2 = Ge[2 * D::Nq + q];
+                const T g3 = Ge[3 * D::Nq + q], g4 = Ge[4 * D::Nq + q], g5 = Ge[5 * D::Nq + q];
+                vr[q] = g0 * ur + g1 * us + g2 * ut;
+                vs[q] = g1 * ur + g3 * us + g4 * ut;
+                vt[q] = g2 * ur + g4 * us + g5 * ut;
+            } else {
+                const T g0 = Ge[q], g1 = Ge[D::Nq + q], g2 = Ge[2 * D::Nq + q];
+                vr[q] = g0 * ur + g1 * us;
+                vs[q] = g1 * ur + g2 * us;
+            }
+        }
+        __syncthreads();
+        // transposed triangle stage
+        for (int i = threadIdx.x; i < D::NT * D::QZ; i += blockDim.x) {
+            const int qz = i / D::NT, n = i - qz * D::NT;
+            T a = 0, b = 0;
+#pragma unroll 4
+            for (int qt = 0; qt < D::QT; ++qt) {
+                const int q = qz * D::QT + qt;
+                a += sDr[qt * D::NT + n] * vr[q] + sDs[qt * D::NT + n] * vs[q];
+                if (PRISM) b += sBt[qt * D::NT + n] * vt[q];
+            }
+            U[n * D::QZ + qz] = a;
+            W[n * D::QZ + qz] = b;
+        }
+        __syncthreads();
+        // transposed vertical stage and direct-stiffness summation (free rows only)
+        for (int i = threadIdx.x; i < D::Np; i += blockDim.x) {
+            T s;
+            if (PRISM) {
+                const int k = i / D::NT, n = i - k * D::NT;
+                s = 0;
+#pragma unroll
+                for (int qz = 0; qz < D::QZ; ++qz)
+                    s += sBz[qz * D::NZ + k] * U[n * D::QZ + qz] + sDz[qz * D::NZ + k] * W[n * D::QZ + qz];
+            } else {
+                s = U[i];
+            }
+            const int m = me[i];
+            if (m >= 0) atomicAdd(&y[m], s);
+        }
+        __syncthreads();
+    }
+}
+
+template <int P, bool PRISM, typename T, bool LIFT>
+cudaError_t apply_impl(const Level& L, const T* refm, const T* G, const T* x, T* y, const int* skip,
+                       cudaStream_t s) {
+    using D = Dims<P, PRISM>;
+    const size_t smem = sizeof(T) * (D::NREF + D::NWORK);
+    static bool configured = false;   // per template instance; attribute is per-function
+    if (!configured) {
+        cudaError_t err = cudaFuncSetAttribute(k_apply<P, PRISM, T, LIFT>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        configured = true;
+    }
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply<P, PRISM, T, LIFT>, 128, smem);
+    if (per_sm < 1) per_sm = 1;
+    int grid = kSMs * per_sm;
+    if (grid > L.E) grid = L.E;
+    if (grid < 1) return cudaSuccess;
+    k_apply<P, PRISM, T, LIFT><<<grid, 128, smem, s>>>(L.E, L.map, G, refm, x, y, skip);
+    return cudaGetLastError();
+}
+
+template <typename T, bool LIFT>
+cudaError_t apply_dispatch(const Level& L, const T* refm, const T* G, const T* x, T* y, const int* skip,
+                           cudaStream_t s) {
+    const bool prism = (L.dim == 3);
+#define SEM_CASE(PP)                                                                     \
+    case PP:                                                                             \
+        return prism ? apply_impl<PP, true, T, LIFT>(L, refm, G, x, y, skip, s)          \
+                     : apply_impl<PP, false, T, LIFT>(L, refm, G, x, y, skip, s);
+    switch (L.p) {
+        SEM_CASE(1)
+        SEM_CASE(2)
+        SEM_CASE(3)
+        SEM_CASE(4)
+        SEM_CASE(5)
+        SEM_CASE(6)
+        default:
+            return cudaErrorInvalidValue;
+    }
+#undef SEM_CASE
+}
+
+// ------------------------------------------------------------------ geometry
+// Sigma-layer prism: x, y affine over the base triangle, z = -h + sigma (h + eta_P(r, s)),
+// sigma = (l + (t + 1)/2) / nlayers.  J = [[M, 0], [z_r z_s, z_t]] (block lower triangular),
+// so J^{-1} has rows grad r = (M^{-1})_0, grad s = (M^{-1})_1 and
+// grad t = (-(z_r, z_s) M^{-1} / z_t, 1 / z_t).
+__global__ void k_geom_prism(int E, int nlayers, int QT, int QZ, int NTP, double depth,
+                             const double* __restrict__ vtri, const double* __restrict__ etaP,
+                             const double* __restrict__ BP, const double* __restrict__ DrP,
+                             const double* __restrict__ DsP, const double* __restrict__ qinfo,
+                             double* __restrict__ G, float* __restrict__ G32) {
+    const int Nq = QT * QZ;
+    const long long total = (long long)E * Nq;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int e = (int)(t / Nq), q = (int)(t - (long long)e * Nq);
+        const int qz = q / QT, qt = q - qz * QT;
+        const int b = e / nlayers, l = e - b * nlayers;
+        const double* v = vtri + 6 * (size_t)b;
+        const double m00 = 0.5 * (v[2] - v[0]), m01 = 0.5 * (v[4] - v[0]);
+        const double m10 = 0.5 * (v[3] - v[1]), m11 = 0.5 * (v[5] - v[1]);
+        const double* et = etaP + (size_t)b * NTP;
+        double eta = 0, er = 0, es = 0;
+        for (int n = 0; n < NTP; ++n) {
+            eta += BP[qt * NTP + n] * et[n];
+            er += DrP[qt * NTP + n] * et[n];
+            es += DsP[qt * NTP + n] * et[n];
+        }
+        const double tw = qinfo[qt], zq = qinfo[QT + qz], zw = qinfo[QT + QZ + qz];
+        const double sigma = (l + 0.5 * (zq + 1.0)) / nlayers;
+        const double zr = sigma * er, zs = sigma * es, zt = (depth + eta) / (2.0 * nlayers);
+        const double a2 = m00 * m11 - m01 * m10;
+        const double i00 = m11 / a2, i01 = -m01 / a2, i10 = -m10 / a2, i11 = m00 / a2;
+        const double gr[3] = {i00, i01, 0.0};
+        const double gs[3] = {i10, i11, 0.0};
+        const double gt[3] = {-(zr * i00 + zs * i10) / zt, -(zr * i01 + zs * i11) / zt, 1.0 / zt};
+        const double wdet = tw * zw * fabs(zt * a2);
+        const double c[6] = {
+            wdet * (gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]),
+            wdet * (gr[0] * gs[0] + gr[1] * gs[1] + gr[2] * gs[2]),
+            wdet * (gr[0] * gt[0] + gr[1] * gt[1] + gr[2] * gt[2]),
+            wdet * (gs[0] * gs[0] + gs[1] * gs[1] + gs[2] * gs[2]),
+            wdet * (gs[0] * gt[0] + gs[1] * gt[1] + gs[2] * gt[2]),
+            wdet * (gt[0] * gt[0] + gt[1] * gt[1] + gt[2] * gt[2])};
+        double* Ge = G + (size_t)e * 6 * Nq;
+        float* Ge32 = G32 + (size_t)e * 6 * Nq;
+        for (int k = 0; k < 6; ++k) {
+            Ge[k * Nq + q] = c[k];
+            Ge32[k * Nq + q] = (float)c[k];
+        }
+    }
+}
+
+// Straight triangle in the (x, z) plane: constant Jacobian M, G = w |det M| M^{-1} M^{-T}.
+__global__ void k_geom_tri(int E, int QT, const double* __restrict__ vtri, const double* __restrict__ qinfo,
+                           double* __restrict__ G, float* __restrict__ G32) {
+    const long long total = (long long)E * QT;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int e = (int)(t / QT), q = (int)(t - (long long)e * QT);
+        const double* v = vtri + 6 * (size_t)e;
+        const double m00 = 0.5 * (v[2] - v[0]), m01 = 0.5 * (v[4] - v[0]);
+        const double m10 = 0.5 * (v[3] - v[1]), m11 = 0.5 * (v[5] - v[1]);
+        const double a2 = m00 * m11 - m01 * m10;
+        const double i00 = m11 / a2, i01 = -m01 / a2, i10 = -m10 / a2, i11 = m00 / a2;
+        const double w = qinfo[q] * fabs(a2);
+        const double c[3] = {w * (i00 * i00 + i01 * i01), w * (i00 * i10 + i01 * i11), w * (i10 * i10 + i11 * i11)};
+        double* Ge = G + (size_t)e * 3 * QT;
+        float* Ge32 = G32 + (size_t)e * 3 * QT;
+        for (int k = 0; k < 3; ++k) {
+            Ge[k * QT + q] = c[k];
+            Ge32[k * QT + q] = (float)c[k];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ diagonal
+// diag(A)_i = sum over elements of sum_q grad N_l^T G_q grad N_l, sum-factorised
+// over the vertical direction for prisms.
+__global__ void k_diag(int E, int dim, int NT, int NZ, int QT, int QZ, const int* __restrict__ map,
+                       const double* __restrict__ G, const double* __restrict__ refm, double* __restrict__ diag) {
+    extern __shared__ double sdiag[];       // [6][NT][QZ]
+    const int Nq = QT * QZ, Np = NT * NZ;
+    const int nc = (dim == 3) ? 6 : 3;
+    const double* Bt = refm;
+    const double* Dr = Bt + QT * NT;
+    const double* Ds = Dr + QT * NT;
+    const double* Bz = refm + 6 * QT * NT;
+    const double* Dz = Bz + QZ * NZ;
+    for (int e = blockIdx.x; e < E; e += gridDim.x) {
+        const double* Ge = G + (size_t)e * nc * Nq;
+        for (int i = threadIdx.x; i < NT * QZ; i += blockDim.x) {
+            const int n = i / QZ, qz = i - n * QZ;
+            double s[6] = {0, 0, 0, 0, 0, 0};
+            for (int qt = 0; qt < QT; ++qt) {
+                const int q = qz * QT + qt;
+                const double dr = Dr[qt * NT + n], ds = Ds[qt * NT + n], bt = Bt[qt * NT + n];
+                if (dim == 3) {
+                    s[0] += dr * dr * Ge[q];
+                    s[1] += dr * ds * Ge[Nq + q];
+                    s[2] += dr * bt * Ge[2 * Nq + q];
+                    s[3] += ds * ds * Ge[3 * Nq + q];
+                    s[4] += ds * bt * Ge[4 * Nq + q];
+                    s[5] += bt * bt * Ge[5 * Nq + q];
+                } else {
+                    s[0] += dr * dr * Ge[q];
+                    s[1] += dr * ds * Ge[Nq + q];
+                    s[3] += ds * ds * Ge[2 * Nq + q];
+                }
+            }
+            for (int c = 0; c < 6; ++c) sdiag[c * NT * QZ + i] = s[c];
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < Np; i += blockDim.x) {
+            const int k = i / NT, n = i - k * NT;
+            double v = 0;
+            for (int qz = 0; qz < QZ; ++qz) {
+                const int j = n * QZ + qz;
+                const double bz = Bz[qz * NZ + k], dz = Dz[qz * NZ + k];
+                v += bz * bz * (sdiag[j] + 2.0 * sdiag[NT * QZ + j] + sdiag[3 * NT * QZ + j]) +
+                     2.0 * bz * dz * (sdiag[2 * NT * QZ + j] + sdiag[4 * NT * QZ + j]) +
+                     dz * dz * sdiag[5 * NT * QZ + j];
+            }
+            atomicAdd(&diag[decode(map[(size_t)e * Np + i])], v);
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ transfers
+// Restriction (R = P^T): fine residual r = f - y weighted by 1/multiplicity,
+// element-wise I^T, summed into the coarse right-hand side (free coarse rows).
+template <typename T>
+__global__ void k_restrict(int E, int Npf, int Npc, const int* __restrict__ mapf, const int* __restrict__ mapc,
+                           const T* __restrict__ wmult, const T* __restrict__ I, const T* __restrict__ f,
+                           const T* __restrict__ y, T* __restrict__ fc) {
+    extern __shared__ __align__(16) unsigned char smr[];
+    T* re = reinterpret_cast<T*>(smr);
+    for (int e = blockIdx.x; e < E; e += gridDim.x) {
+        for (int l = threadIdx.x; l < Npf; l += blockDim.x) {
+            const int m = mapf[(size_t)e * Npf + l];
+            re[l] = (m >= 0) ? wmult[m] * (f[m] - y[m]) : T(0);
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; c < Npc; c += blockDim.x) {
+            const int m = mapc[(size_t)e * Npc + c];
+            if (m < 0) continue;
+            T s = 0;
+            for (int l = 0; l < Npf; ++l) s += I[l * Npc + c] * re[l];
+            atomicAdd(&fc[m], s);
+        }
+        __syncthreads();
+    }
+}
+
+// Prolongation and correction: uf += P uc, each fine node written by its owner element.
+template <typename T>
+__global__ void k_prolong(int E, int Npf, int Npc, const int* __restrict__ mapf, const int* __restrict__ mapc,
+                          const unsigned char* __restrict__ owner, const T* __restrict__ I,
+                          const T* __restrict__ uc, T* __restrict__ uf) {
+    extern __shared__ __align__(16) unsigned char smp[];
+    T* ce = reinterpret_cast<T*>(smp);
+    for (int e = blockIdx.x; e < E; e += gridDim.x) {
+        for (int c = threadIdx.x; c < Npc; c += blockDim.x) {
+            const int m = mapc[(size_t)e * Npc + c];
+            ce[c] = (m >= 0) ? uc[m] : T(0);
+        }
+        __syncthreads();
+        for (int l = threadIdx.x; l < Npf; l += blockDim.x) {
+            if (!owner[(size_t)e * Npf + l]) continue;
+            T s = 0;
+            for (int c = 0; c < Npc; ++c) s += I[l * Npc + c] * ce[c];
+            uf[mapf[(size_t)e * Npf + l]] += s;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic block sum (fixed tree) of one value per thread; result in thread 0.
+__device__ double block_sum(double v) {
+    __shared__ double ws[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) ws[wid] = v;
+    __syncthreads();
+    v = (threadIdx.x < (blockDim.x >> 5)) ? ws[threadIdx.x] : 0.0;
+    if (wid == 0) v = warp_sum(v);
+    return v;
+}
+
+// Writes this block's NS partial sums; returns true in the block that finishes
+// last, after which part[] holds every block's partials (read them in order).
+template <int NS>
+__device__ bool partials_done(const double* s, double* part, unsigned* counter) {
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < NS; ++k) part[(size_t)k * gridDim.x + blockIdx.x] = s[k];
+        __threadfence();
+        const unsigned t = atomicAdd(counter, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+template <int NS>
+__device__ void final_sums(const double* part, double* out) {
+    for (int k = 0; k < NS; ++k) {
+        double v = 0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+            v += ((volatile const double*)part)[(size_t)k * gridDim.x + b];
+        v = block_sum(v);
+        if (threadIdx.x == 0) out[k] = v;
+        __syncthreads();
+    }
+}
+
+__global__ void k_dot(long long n, const double* __restrict__ a, const double* __restrict__ b,
+                      double* part, unsigned* counter, double* out) {
+    double s = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        s += a[i] * b[i];
+    double v[1] = {block_sum(s)};
+    if (partials_done<1>(v, part, counter)) {
+        double r[1];
+        final_sums<1>(part, r);
+        if (threadIdx.x == 0) { out[0] = r[0]; *counter = 0; }
+    }
+}
+
+__global__ void k_residual(long long n, const double* __restrict__ f, const double* __restrict__ y,
+                           double* __restrict__ r, double* part, unsigned* counter, double* out) {
+    double s = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double v = f[i] - y[i];
+        r[i] = v;
+        s += v * v;
+    }
+    double v[1] = {block_sum(s)};
+    if (partials_done<1>(v, part, counter)) {
+        double rr[1];
+        final_sums<1>(part, rr);
+        if (threadIdx.x == 0) { out[0] = rr[0]; *counter = 0; }
+    }
+}
+
+// PCG (Algorithm 3): alpha = delta / (p^T q); u += alpha p; r -= alpha q; rr = r^T r.
+__global__ void k_pcg_update(long long n, const double* num, const double* den, const double* __restrict__ p,
+                             const double* __restrict__ q, double* __restrict__ u, double* __restrict__ r,
+                             double* part, unsigned* counter, double* out) {
+    const double alpha = (*num) / (*den);
+    double s = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        u[i] += alpha * p[i];
+        const double v = r[i] - alpha * q[i];
+        r[i] = v;
+        s += v * v;
+    }
+    double v[1] = {block_sum(s)};
+    if (partials_done<1>(v, part, counter)) {
+        double rr[1];
+        final_sums<1>(part, rr);
+        if (threadIdx.x == 0) { out[0] = rr[0]; *counter = 0; }
+    }
+}
+
+__global__ void k_pcg_dir(long long n, const double* num, const double* den, const double* __restrict__ z,
+                          double* __restrict__ p) {
+    const double beta = (*num) / (*den);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = z[i] + beta * p[i];
+}
+
+// ------------------------------------------------------------------ coarse CG (FP64)
+// Jacobi-preconditioned CG with every scalar on the device; all kernels are
+// predicated on flags[F_CG_DONE] so that the host may launch several iterations
+// ahead of the convergence test.
+__global__ void k_cg_init(long long n, const double* __restrict__ b, const double* __restrict__ dinv,
+                          double* __restrict__ x, double* __restrict__ r, double* __restrict__ z,
+                          double* __restrict__ p, double* part, unsigned* counter, double* scal, int* flags,
+                          double rtol2) {
+    double s[2] = {0, 0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double bi = b[i];
+        const double zi = dinv[i] * bi;
+        x[i] = 0;
+        r[i] = bi;
+        z[i] = zi;
+        p[i] = zi;
+        s[0] += bi * zi;
+        s[1] += bi * bi;
+    }
+    double v[2] = {block_sum(s[0]), block_sum(s[1])};
+    if (partials_done<2>(v, part, counter)) {
+        double t[2];
+        final_sums<2>(part, t);
+        if (threadIdx.x == 0) {
+            scal[S_CG_RHO] = t[0];
+            scal[S_CG_RR] = t[1];
+            scal[S_CG_TOL2] = rtol2 * t[1];
+            flags[F_CG_DONE] = (t[1] <= rtol2 * t[1]) || (t[1] == 0.0);
+            flags[F_CG_ITERS] = 0;
+            *counter = 0;
+        }
+    }
+}
+
+__global__ void k_cg_pq(long long n, const double* __restrict__ p, const double* __restrict__ q, double* part,
+                        unsigned* counter, double* scal, const int* flags) {
+    if (flags[F_CG_DONE]) return;
+    double s = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        s += p[i] * q[i];
+    double v[1] = {block_sum(s)};
+    if (partials_done<1>(v, part, counter)) {
+        double t[1];
+        final_sums<1>(part, t);
+        if (threadIdx.x == 0) { scal[S_CG_PQ] = t[0]; *counter = 0; }
+    }
+}
+
+__global__ void k_cg_update(long long n, const double* __restrict__ dinv, double* __restrict__ x,
+                            double* __restrict__ r, double* __restrict__ z, const double* __restrict__ p,
+                            const double* __restrict__ q, double* part, unsigned* counter, double* scal, int* flags) {
+    if (flags[F_CG_DONE]) return;
+    const double alpha = scal[S_CG_RHO] / scal[S_CG_PQ];
+    double s[2] = {0, 0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        x[i] += alpha * p[i];
+        const double ri = r[i] - alpha * q[i];
+        r[i] = ri;
+        const double zi = dinv[i] * ri;
+        z[i] = zi;
+        s[0] += ri * zi;
+        s[1] += ri * ri;
+    }
+    double v[2] = {block_sum(s[0]), block_sum(s[1])};
+    if (partials_done<2>(v, part, counter)) {
+        double t[2];
+        final_sums<2>(part, t);
+        if (threadIdx.x == 0) {
+            scal[S_CG_BETA] = t[0] / scal[S_CG_RHO];
+            scal[S_CG_RHO] = t[0];
+            scal[S_CG_RR] = t[1];
+            flags[F_CG_ITERS] += 1;
+            if (t[1] <= scal[S_CG_TOL2] || !(t[1] == t[1])) flags[F_CG_DONE] = 1;
+            *counter = 0;
+        }
+    }
+}
+
+__global__ void k_cg_dir(long long n, const double* __restrict__ z, double* __restrict__ p, const double* scal,
+                         const int* flags) {
+    if (flags[F_CG_DONE]) return;
+    const double beta = scal[S_CG_BETA];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = z[i] + beta * p[i];
+}
+
+// ------------------------------------------------------------------ FGMRES helpers
+constexpr int kMaxMulti = 65;
+
+__global__ void k_multidot(long long n, int k, const double* __restrict__ V, const double* __restrict__ w,
+                           double* part, unsigned* counter, double* out) {
+    __shared__ bool last;
+    for (int j = 0; j < k; ++j) {
+        double s = 0;
+        const double* vj = V + (size_t)j * n;
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+            s += vj[i] * w[i];
+        s = block_sum(s);
+        if (threadIdx.x == 0) part[(size_t)j * gridDim.x + blockIdx.x] = s;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int j = 0; j < k; ++j) {
+        double v = 0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+            v += ((volatile const double*)part)[(size_t)j * gridDim.x + b];
+        v = block_sum(v);
+        if (threadIdx.x == 0) out[j] = v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *counter = 0;
+}
+
+__global__ void k_multiaxpy(long long n, int k, const double* __restrict__ V, const double* __restrict__ c,
+                            double sign, double* __restrict__ w) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double s = 0;
+        for (int j = 0; j < k; ++j) s += c[j] * V[(size_t)j * n + i];
+        w[i] += sign * s;
+    }
+}
+
+__global__ void k_scale(long long n, const double* __restrict__ w, const double* nrm2, double* __restrict__ v) {
+    const double inv = 1.0 / sqrt(*nrm2);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        v[i] = w[i] * inv;
+}
+
+// ------------------------------------------------------------------ element-wise vector kernels
+template <typename T>
+__global__ void k_cheb_first(long long n, T c, const T* __restrict__ dinv, const T* __restrict__ f,
+                             T* __restrict__ u, T* __restrict__ d) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const T v = c * dinv[i] * f[i];
+        d[i] = v;
+        u[i] = v;
+    }
+}
+
+template <typename T>
+__global__ void k_cheb_restart(long long n, T c, const T* __restrict__ dinv, const T* __restrict__ f,
+                               const T* __restrict__ y, T* __restrict__ u, T* __restrict__ d) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const T v = c * dinv[i] * (f[i] - y[i]);
+        d[i] = v;
+        u[i] += v;
+    }
+}
+
+template <typename T>
+__global__ void k_cheb_step(long long n, T c1, T c2, const T* __restrict__ dinv, const T* __restrict__ f,
+                            const T* __restrict__ y, T* __restrict__ u, T* __restrict__ d) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const T v = c1 * d[i] + c2 * dinv[i] * (f[i] - y[i]);
+        d[i] = v;
+        u[i] += v;
+    }
+}
+
+__global__ void k_axpy(long long n, double a, const double* __restrict__ x, double* __restrict__ y) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] += a * x[i];
+}
+
+__global__ void k_copy_idx(long long nd, const long long* __restrict__ idx, const double* __restrict__ src,
+                           double* __restrict__ dst) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nd; i += (long long)gridDim.x * blockDim.x)
+        dst[idx[i]] = src[idx[i]];
+}
+
+__global__ void k_scatter_idx(long long nd, const long long* __restrict__ idx, const double* __restrict__ vals,
+                              double* __restrict__ dst) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nd; i += (long long)gridDim.x * blockDim.x)
+        dst[idx[i]] = vals[i];
+}
+
+__global__ void k_zero_idx(long long nd, const long long* __restrict__ idx, double* __restrict__ v) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nd; i += (long long)gridDim.x * blockDim.x)
+        v[idx[i]] = 0.0;
+}
+
+__global__ void k_to_f32(long long n, const double* __restrict__ a, float* __restrict__ b) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+__global__ void k_to_f64(long long n, const float* __restrict__ a, double* __restrict__ b) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        b[i] = (double)a[i];
+}
+
+}  // namespace
+
+// ====================================================================== launchers
+int reduce_blocks() { return 2 * kSMs; }
+
+cudaError_t launch_apply64(const Level& L, const double* x, double* y, bool lift, const int* skip, cudaStream_t s) {
+    return lift ? apply_dispatch<double, true>(L, L.ref64.m, L.G, x, y, skip, s)
+                : apply_dispatch<double, false>(L, L.ref64.m, L.G, x, y, skip, s);
+}
+
+cudaError_t launch_apply32(const Level& L, const float* x, float* y, cudaStream_t s) {
+    return apply_dispatch<float, false>(L, L.ref32.m, L.G32, x, y, nullptr, s);
+}
+
+cudaError_t launch_geometry(Level& L, const double* vtri, const double* etaP, const double* BP, const double* DrP,
+                            const double* DsP, int NTP, int nlayers, double depth, cudaStream_t s) {
+    // quadrature info: [tw (QT) | zq (QZ) | zw (QZ)]
+    std::vector<double> qi(L.ref.tw);
+    qi.insert(qi.end(), L.ref.zq.begin(), L.ref.zq.end());
+    qi.insert(qi.end(), L.ref.zw.begin(), L.ref.zw.end());
+    double* dq = nullptr;
+    cudaError_t err = cudaMalloc(&dq, qi.size() * sizeof(double));
+    if (err != cudaSuccess) return err;
+    err = cudaMemcpyAsync(dq, qi.data(), qi.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (err == cudaSuccess) {
+        const long long total = (long long)L.E * L.Nq;
+        const int grid = (int)std::min<long long>((total + 255) / 256, kSMs * 32);
+        if (L.dim == 3)
+            k_geom_prism<<<grid, 256, 0, s>>>(L.E, nlayers, L.QT, L.QZ, NTP, depth, vtri, etaP, BP, DrP, DsP, dq, L.G,
+                                              L.G32);
+        else
+            k_geom_tri<<<grid, 256, 0, s>>>(L.E, L.QT, vtri, dq, L.G, L.G32);
+        err = cudaGetLastError();
+    }
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    cudaFree(dq);
+    return err != cudaSuccess ? err : e2;
+}
+
+cudaError_t launch_diag(const Level& L, double* diag, cudaStream_t s) {
+    const size_t smem = sizeof(double) * 6 * L.NT * L.QZ;
+    const int grid = std::min(L.E, kSMs * 8);
+    k_diag<<<grid, 128, smem, s>>>(L.E, L.dim, L.NT, L.NZ, L.QT, L.QZ, L.map, L.G, L.ref64.m, diag);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t restrict_t(const Level& F, const Level& C, const T* wm, const T* I, const T* f, const T* y, T* fc,
+                              cudaStream_t s) {
+    const int grid = std::min(F.E, kSMs * 8);
+    k_restrict<T><<<grid, 64, sizeof(T) * F.Np, s>>>(F.E, F.Np, C.Np, F.map, C.map, wm, I, f, y, fc);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t prolong_t(const Level& F, const Level& C, const T* I, const T* uc, T* uf, cudaStream_t s) {
+    const int grid = std::min(F.E, kSMs * 8);
+    k_prolong<T><<<grid, 128, sizeof(T) * C.Np, s>>>(F.E, F.Np, C.Np, F.map, C.map, F.owner, I, uc, uf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restrict64(const Level& F, const Level& C, const double* f, const double* y, double* fc,
+                              cudaStream_t s) {
+    return restrict_t<double>(F, C, F.wmult, F.I64, f, y, fc, s);
+}
+cudaError_t launch_restrict32(const Level& F, const Level& C, const float* f, const float* y, float* fc,
+                              cudaStream_t s) {
+    return restrict_t<float>(F, C, F.wmult32, F.I32, f, y, fc, s);
+}
+cudaError_t launch_prolong64(const Level& F, const Level& C, const double* uc, double* uf, cudaStream_t s) {
+    return prolong_t<double>(F, C, F.I64, uc, uf, s);
+}
+cudaError_t launch_prolong32(const Level& F, const Level& C, const float* uc, float* uf, cudaStream_t s) {
+    return prolong_t<float>(F, C, F.I32, uc, uf, s);
+}
+
+template <typename T>
+cudaError_t cheb_first(long long n, T c, const T* dinv, const T* f, T* u, T* d, cudaStream_t s) {
+    k_cheb_first<T><<<vec_grid(n), kVecThreads, 0, s>>>(n, c, dinv, f, u, d);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t cheb_restart(long long n, T c, const T* dinv, const T* f, const T* y, T* u, T* d, cudaStream_t s) {
+    k_cheb_restart<T><<<vec_grid(n), kVecThreads, 0, s>>>(n, c, dinv, f, y, u, d);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t cheb_step(long long n, T c1, T c2, const T* dinv, const T* f, const T* y, T* u, T* d, cudaStream_t s) {
+    k_cheb_step<T><<<vec_grid(n), kVecThreads, 0, s>>>(n, c1, c2, dinv, f, y, u, d);
+    return cudaGetLastError();
+}
+template cudaError_t cheb_first<double>(long long, double, const double*, const double*, double*, double*, cudaStream_t);
+template cudaError_t cheb_first<float>(long long, float, const float*, const float*, float*, float*, cudaStream_t);
+template cudaError_t cheb_restart<double>(long long, double, const double*, const double*, const double*, double*,
+                                          double*, cudaStream_t);
+template cudaError_t cheb_restart<float>(long long, float, const float*, const float*, const float*, float*, float*,
+                                         cudaStream_t);
+template cudaError_t cheb_step<double>(long long, double, double, const double*, const double*, const double*,
+                                       double*, double*, cudaStream_t);
+template cudaError_t cheb_step<float>(long long, float, float, const float*, const float*, const float*, float*,
+                                      float*, cudaStream_t);
+
+cudaError_t dot64(long long n, const double* a, const double* b, Scratch& sc, double* out, cudaStream_t s) {
+    k_dot<<<reduce_blocks(), kRedThreads, 0, s>>>(n, a, b, sc.part, sc.counter, out);
+    return cudaGetLastError();
+}
+cudaError_t residual64(long long n, const double* f, const double* y, double* r, Scratch& sc, double* rr,
+                       cudaStream_t s) {
+    k_residual<<<reduce_blocks(), kRedThreads, 0, s>>>(n, f, y, r, sc.part, sc.counter, rr);
+    return cudaGetLastError();
+}
+cudaError_t pcg_update(long long n, const double* num, const double* den, const double* p, const double* q, double* u,
+                       double* r, Scratch& sc, double* rr, cudaStream_t s) {
+    k_pcg_update<<<reduce_blocks(), kRedThreads, 0, s>>>(n, num, den, p, q, u, r, sc.part, sc.counter, rr);
+    return cudaGetLastError();
+}
+cudaError_t pcg_direction(long long n, const double* num, const double* den, const double* z, double* p,
+                          cudaStream_t s) {
+    k_pcg_dir<<<vec_grid(n), kVecThreads, 0, s>>>(n, num, den, z, p);
+    return cudaGetLastError();
+}
+cudaError_t axpy64(long long n, double a, const double* x, double* y, cudaStream_t s) {
+    k_axpy<<<vec_grid(n), kVecThreads, 0, s>>>(n, a, x, y);
+    return cudaGetLastError();
+}
+cudaError_t copy_dirichlet(long long nd, const long long* idx, const double* src, double* dst, cudaStream_t s) {
+    if (nd <= 0) return cudaSuccess;
+    k_copy_idx<<<vec_grid(nd), kVecThreads, 0, s>>>(nd, idx, src, dst);
+    return cudaGetLastError();
+}
+cudaError_t scatter_dirichlet(long long nd, const long long* idx, const double* vals, double* dst, cudaStream_t s) {
+    if (nd <= 0) return cudaSuccess;
+    k_scatter_idx<<<vec_grid(nd), kVecThreads, 0, s>>>(nd, idx, vals, dst);
+    return cudaGetLastError();
+}
+cudaError_t zero_dirichlet(long long nd, const long long* idx, double* v, cudaStream_t s) {
+    if (nd <= 0) return cudaSuccess;
+    k_zero_idx<<<vec_grid(nd), kVecThreads, 0, s>>>(nd, idx, v);
+    return cudaGetLastError();
+}
+cudaError_t to_f32(long long n, const double* a, float* b, cudaStream_t s) {
+    k_to_f32<<<vec_grid(n), kVecThreads, 0, s>>>(n, a, b);
+    return cudaGetLastError();
+}
+cudaError_t to_f64(long long n, const float* a, double* b, cudaStream_t s) {
+    k_to_f64<<<vec_grid(n), kVecThreads, 0, s>>>(n, a, b);
+    return cudaGetLastError();
+}
+cudaError_t multidot64(long long n, int k, const double* V, const double* w, Scratch& sc, double* out, cudaStream_t s) {
+    if (k > kMaxMulti) return cudaErrorInvalidValue;
+    k_multidot<<<reduce_blocks(), kRedThreads, 0, s>>>(n, k, V, w, sc.part, sc.counter, out);
+    return cudaGetLastError();
+}
+cudaError_t multiaxpy64(long long n, int k, const double* V, const double* c, double sign, double* w, cudaStream_t s) {
+    k_multiaxpy<<<vec_grid(n), kVecThreads, 0, s>>>(n, k, V, c, sign, w);
+    return cudaGetLastError();
+}
+cudaError_t scale64(long long n, const double* w, const double* nrm2, double* v, cudaStream_t s) {
+    k_scale<<<vec_grid(n), kVecThreads, 0, s>>>(n, w, nrm2, v);
+    return cudaGetLastError();
+}
+cudaError_t cg_init(long long n, const double* b, const double* dinv, double* x, double* r, double* z, double* p,
+                    Scratch& sc, double rtol2, cudaStream_t s) {
+    k_cg_init<<<reduce_blocks(), kRedThreads, 0, s>>>(n, b, dinv, x, r, z, p, sc.part, sc.counter, sc.scal, sc.flags,
+                                                       rtol2);
+    return cudaGetLastError();
+}
+cudaError_t cg_pq(long long n, const double* p, const double* q, Scratch& sc, cudaStream_t s) {
+    k_cg_pq<<<reduce_blocks(), kRedThreads, 0, s>>>(n, p, q, sc.part, sc.counter, sc.scal, sc.flags);
+    return cudaGetLastError();
+}
+cudaError_t cg_update(long long n, const double* dinv, double* x, double* r, double* z, const double* p,
+                      const double* q, Scratch& sc, cudaStream_t s) {
+    k_cg_update<<<reduce_blocks(), kRedThreads, 0, s>>>(n, dinv, x, r, z, p, q, sc.part, sc.counter, sc.scal,
+                                                         sc.flags);
+    return cudaGetLastError();
+}
+cudaError_t cg_direction(long long n, const double* z, double* p, Scratch& sc, cudaStream_t s) {
+    k_cg_dir<<<vec_grid(n), kVecThreads, 0, s>>>(n, z, p, sc.scal, sc.flags);
+    return cudaGetLastError();
+}
+
+}  // namespace sem

@@ -1,0 +1,159 @@
+// Internal state of a sem_handle and the kernel launchers shared by the
+// translation units of the library.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sem.h"
+#include "refelem.hpp"
+
+namespace sem {
+
+void set_error(const std::string& msg);
+
+// Device copies of one level's reference matrices (Section 3.1):
+// [Bt | DrT | DsT | Drt | Dst | Bz | Dz] where Bt/Drt/Dst are [QT][NT] and
+// BtT/DrT/DsT the transposes [NT][QT].
+template <typename T>
+struct RefDev {
+    T* m = nullptr;      // device block
+    size_t count = 0;
+};
+
+struct Level {
+    int dim = 3, p = 1;
+    int NT = 0, NZ = 1, QT = 0, QZ = 1, Np = 0, Nq = 0, ncomp = 6;
+    int E = 0;           // elements
+    long long N = 0;     // global nodes
+    long long N2 = 0;    // 2D nodes (per vertical level in 3D)
+    RefLevel ref;
+    std::vector<int> hmap;                 // [E][Np]: g >= 0 free, -(g+1) Dirichlet
+    std::vector<long long> hdir;           // Dirichlet node ids, ascending
+    std::vector<double> hdiag;             // assembled diagonal (all nodes)
+    double lam = 0.0;                      // lambda_hat of D^{-1}A
+    // device
+    int* map = nullptr;
+    double* G = nullptr;                   // [E][ncomp][Nq]
+    float* G32 = nullptr;
+    double* dinv = nullptr;                // 1/diag on free nodes, 0 on Dirichlet
+    float* dinv32 = nullptr;
+    long long* dir = nullptr;              // Dirichlet node ids
+    RefDev<double> ref64;
+    RefDev<float> ref32;
+    // transfer to the next coarser level (valid for all but the coarsest)
+    double* I64 = nullptr;                 // [Np][Np_c]
+    float* I32 = nullptr;
+    unsigned char* owner = nullptr;        // [E][Np]: this element writes the prolonged value
+    double* wmult = nullptr;               // 1 / (elements sharing the node)
+    float* wmult32 = nullptr;
+    // workspaces (length N)
+    double *u = nullptr, *f = nullptr, *y = nullptr, *d = nullptr;
+    float *u32 = nullptr, *f32 = nullptr, *y32 = nullptr, *d32 = nullptr;
+};
+
+struct Scratch {
+    double* part = nullptr;        // block partial sums
+    unsigned* counter = nullptr;   // last-block counters
+    double* scal = nullptr;        // device scalars
+    int* flags = nullptr;          // device flags / counters
+    double* hpinned = nullptr;     // pinned host mirror of scal (D2H of scalars)
+    int* hflags = nullptr;
+};
+
+}  // namespace sem
+
+struct sem_handle {
+    int dim = 3, P = 1, nlayers = 0;
+    double depth = 1.0;
+    sem_options opts{};
+    std::vector<sem::Level> lv;
+    sem::Scratch sc;
+    // outer-iteration vectors on the finest level (FP64)
+    double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *x = nullptr, *fr = nullptr;
+    // FGMRES basis
+    double* V = nullptr;           // [(m+1)][N]
+    double* Zb = nullptr;          // [m][N]
+    // coarse CG (FP64) on the coarsest level
+    double *cx = nullptr, *cr = nullptr, *cz = nullptr, *cp = nullptr, *cq = nullptr, *cb = nullptr;
+    // staging buffers of laplace_solve_host
+    double *st_eta = nullptr, *st_rhs = nullptr, *st_phi = nullptr;
+    // host geometry copies for coordinate queries
+    std::vector<double> vxy;
+    std::vector<int> tri;
+    std::vector<double> eta2;      // eta at order-P 2D nodes
+    std::vector<std::vector<int>> map2;   // per level: [ntri][NT] 2D ids
+    // profiling events
+    std::vector<cudaEvent_t> ev;
+    int ev_used = 0;
+    double apply_ms = 0.0;
+    long long apply_launches = 0;
+    long long fine_applies = 0;
+    long long launches = 0;        // kernels launched since the counter was reset
+    long long vcycles = 0;
+    int coarse_iters_max = 0;
+    int device = 0;
+};
+
+namespace sem {
+
+// ---------------------------------------------------------------- kernels.cu
+int reduce_blocks();
+cudaError_t launch_apply64(const Level& L, const double* x, double* y, bool lift, const int* skip,
+                           cudaStream_t s);
+cudaError_t launch_apply32(const Level& L, const float* x, float* y, cudaStream_t s);
+cudaError_t launch_geometry(Level& L, const double* vtri, const double* etaP, const double* BP,
+                            const double* DrP, const double* DsP, int NTP, int nlayers, double depth,
+                            cudaStream_t s);
+cudaError_t launch_diag(const Level& L, double* diag, cudaStream_t s);
+cudaError_t launch_restrict64(const Level& F, const Level& C, const double* f, const double* y,
+                              double* fc, cudaStream_t s);
+cudaError_t launch_restrict32(const Level& F, const Level& C, const float* f, const float* y,
+                              float* fc, cudaStream_t s);
+cudaError_t launch_prolong64(const Level& F, const Level& C, const double* uc, double* uf, cudaStream_t s);
+cudaError_t launch_prolong32(const Level& F, const Level& C, const float* uc, float* uf, cudaStream_t s);
+
+// vector kernels (n = vector length)
+template <typename T>
+cudaError_t cheb_first(long long n, T c, const T* dinv, const T* f, T* u, T* d, cudaStream_t s);
+template <typename T>
+cudaError_t cheb_restart(long long n, T c, const T* dinv, const T* f, const T* y, T* u, T* d, cudaStream_t s);
+template <typename T>
+cudaError_t cheb_step(long long n, T c1, T c2, const T* dinv, const T* f, const T* y, T* u, T* d,
+                      cudaStream_t s);
+cudaError_t dot64(long long n, const double* a, const double* b, Scratch& sc, double* out, cudaStream_t s);
+cudaError_t residual64(long long n, const double* f, const double* y, double* r, Scratch& sc, double* rr,
+                       cudaStream_t s);
+cudaError_t pcg_update(long long n, const double* num, const double* den, const double* p, const double* q,
+                       double* u, double* r, Scratch& sc, double* rr, cudaStream_t s);
+cudaError_t pcg_direction(long long n, const double* num, const double* den, const double* z, double* p,
+                          cudaStream_t s);
+cudaError_t axpy64(long long n, double a, const double* x, double* y, cudaStream_t s);
+cudaError_t copy_dirichlet(long long nd, const long long* idx, const double* src, double* dst, cudaStream_t s);
+cudaError_t scatter_dirichlet(long long nd, const long long* idx, const double* vals, double* dst, cudaStream_t s);
+cudaError_t zero_dirichlet(long long nd, const long long* idx, double* v, cudaStream_t s);
+cudaError_t to_f32(long long n, const double* a, float* b, cudaStream_t s);
+cudaError_t to_f64(long long n, const float* a, double* b, cudaStream_t s);
+cudaError_t multidot64(long long n, int k, const double* V, const double* w, Scratch& sc, double* out,
+                       cudaStream_t s);
+cudaError_t multiaxpy64(long long n, int k, const double* V, const double* c, double sign, double* w,
+                        cudaStream_t s);
+cudaError_t scale64(long long n, const double* w, const double* nrm2, double* v, cudaStream_t s);
+// coarse CG: device-resident scalars, predicated on a done flag
+cudaError_t cg_init(long long n, const double* b, const double* dinv, double* x, double* r, double* z,
+                    double* p, Scratch& sc, double rtol2, cudaStream_t s);
+cudaError_t cg_pq(long long n, const double* p, const double* q, Scratch& sc, cudaStream_t s);
+cudaError_t cg_update(long long n, const double* dinv, double* x, double* r, double* z, const double* p,
+                      const double* q, Scratch& sc, cudaStream_t s);
+cudaError_t cg_direction(long long n, const double* z, double* p, Scratch& sc, cudaStream_t s);
+
+// scalar slots in Scratch::scal
+enum {
+    S_RR = 0, S_PQ = 1, S_DELTA0 = 2, S_DELTA1 = 3, S_FF = 4, S_TMP = 5,
+    S_CG_RHO = 8, S_CG_PQ = 9, S_CG_RR = 10, S_CG_TOL2 = 11, S_CG_RHONEW = 12, S_CG_BETA = 13,
+    S_MULTI = 16                    // FGMRES dots start here (up to 64 + 1)
+};
+enum { F_CG_DONE = 0, F_CG_ITERS = 1 };
+
+}  // namespace sem

@@ -1,0 +1,329 @@
+// Host-side setup of a sem_handle: canonical numbering, Dirichlet sets,
+// transfer bookkeeping, device allocation, geometric factors, Jacobi
+// diagonals and the Chebyshev eigenvalue estimates (setup step of the hot path;
+// the paper pre-computes its operators once at t = 0, Section 4.4).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "sem_internal.hpp"
+
+namespace sem {
+
+namespace {
+thread_local std::string g_err;
+}
+
+void set_error(const std::string& msg) { g_err = msg; }
+const char* last_error() { return g_err.c_str(); }
+
+// First-appearance numbering of order-p triangle nodes: vertices by vertex id,
+// edge nodes by (edge, position from the lower vertex id), interior nodes new.
+void tri_numbering(int nvert, int ntri, const int* tri, int p, std::vector<int>& map2, long long& N2) {
+    const int NT = (p + 1) * (p + 2) / 2;
+    map2.assign((size_t)ntri * NT, -1);
+    std::vector<long long> vid(nvert, -1);
+    std::unordered_map<uint64_t, std::vector<long long>> edges;
+    edges.reserve((size_t)ntri * 2);
+    long long next = 0;
+    for (int e = 0; e < ntri; ++e) {
+        const int v[3] = {tri[3 * e], tri[3 * e + 1], tri[3 * e + 2]};
+        int n = 0;
+        for (int j = 0; j <= p; ++j)
+            for (int i = 0; i + j <= p; ++i, ++n) {
+                long long* slot = nullptr;
+                long long interior = -1;
+                int vtx = -1;
+                if (i == 0 && j == 0) vtx = v[0];
+                else if (i == p && j == 0) vtx = v[1];
+                else if (i == 0 && j == p) vtx = v[2];
+                if (vtx >= 0) {
+                    slot = &vid[vtx];
+                } else {
+                    int va = -1, vb = -1, pos = 0;
+                    if (j == 0) { va = v[0]; vb = v[1]; pos = i; }
+                    else if (i + j == p) { va = v[1]; vb = v[2]; pos = j; }
+                    else if (i == 0) { va = v[2]; vb = v[0]; pos = p - j; }
+                    if (va >= 0) {
+                        if (va > vb) { std::swap(va, vb); pos = p - pos; }
+                        const uint64_t key = ((uint64_t)(uint32_t)va << 32) | (uint32_t)vb;
+                        auto& ids = edges[key];
+                        if (ids.empty()) ids.assign(p - 1, -1);
+                        slot = &ids[pos - 1];
+                    } else {
+                        slot = &interior;
+                    }
+                }
+                if (*slot < 0) *slot = next++;
+                map2[(size_t)e * NT + n] = (int)*slot;
+            }
+    }
+    N2 = next;
+}
+
+// 2D coordinates of the order-p nodes (first appearance wins).
+void tri_coords(int ntri, const int* tri, const double* vxy, int p, const std::vector<int>& map2, long long N2,
+                std::vector<double>& xy) {
+    const int NT = (p + 1) * (p + 2) / 2;
+    const std::vector<double> tn = tri_nodes(p);
+    xy.assign(2 * N2, 0.0);
+    std::vector<char> seen(N2, 0);
+    for (int e = 0; e < ntri; ++e) {
+        const double* a = vxy + 2 * tri[3 * e];
+        const double* b = vxy + 2 * tri[3 * e + 1];
+        const double* c = vxy + 2 * tri[3 * e + 2];
+        for (int n = 0; n < NT; ++n) {
+            const int g = map2[(size_t)e * NT + n];
+            if (seen[g]) continue;
+            seen[g] = 1;
+            const double r = tn[2 * n], s = tn[2 * n + 1];
+            xy[2 * g] = -0.5 * (r + s) * a[0] + 0.5 * (1 + r) * b[0] + 0.5 * (1 + s) * c[0];
+            xy[2 * g + 1] = -0.5 * (r + s) * a[1] + 0.5 * (1 + r) * b[1] + 0.5 * (1 + s) * c[1];
+        }
+    }
+}
+
+namespace {
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+template <typename T>
+cudaError_t upload(T** p, const std::vector<T>& h) {
+    cudaError_t e = dalloc(p, h.size());
+    if (e != cudaSuccess) return e;
+    if (!h.empty()) e = cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+std::vector<double> ref_block(const RefLevel& r) {
+    // [Bt | Drt | Dst | BtT | DrT | DsT | Bz | Dz]
+    std::vector<double> out;
+    out.insert(out.end(), r.Bt.begin(), r.Bt.end());
+    out.insert(out.end(), r.Drt.begin(), r.Drt.end());
+    out.insert(out.end(), r.Dst.begin(), r.Dst.end());
+    for (const std::vector<double>* M : {&r.Bt, &r.Drt, &r.Dst})
+        for (int n = 0; n < r.NT; ++n)
+            for (int q = 0; q < r.QT; ++q) out.push_back((*M)[(size_t)q * r.NT + n]);
+    out.insert(out.end(), r.Bz.begin(), r.Bz.end());
+    out.insert(out.end(), r.Dz.begin(), r.Dz.end());
+    return out;
+}
+
+std::vector<float> to_float(const std::vector<double>& v) {
+    std::vector<float> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = (float)v[i];
+    return o;
+}
+
+}  // namespace
+
+#define CK(expr)                                                                          \
+    do {                                                                                  \
+        cudaError_t _e = (expr);                                                          \
+        if (_e != cudaSuccess) {                                                          \
+            set_error(std::string("CUDA error in setup: ") + cudaGetErrorString(_e) +   \
+                      " (" #expr ")");                                                    \
+            return _e == cudaErrorMemoryAllocation ? SEM_ENOMEM : SEM_ECUDA;             \
+        }                                                                                 \
+    } while (0)
+
+sem_status build_level(sem_handle* h, const sem_mesh* m, int li, int p) {
+    Level& L = h->lv[li];
+    L.dim = m->dim;
+    L.p = p;
+    L.ref.build(m->dim, p);
+    L.NT = L.ref.NT; L.NZ = L.ref.NZ; L.QT = L.ref.QT; L.QZ = L.ref.QZ;
+    L.Np = L.ref.Np; L.Nq = L.ref.Nq;
+    L.ncomp = (m->dim == 3) ? 6 : 3;
+    std::vector<int>& map2 = h->map2[li];
+    long long N2 = 0;
+    tri_numbering(m->nvert, m->ntri, m->tri, p, map2, N2);
+    L.N2 = N2;
+    const int nl = (m->dim == 3) ? m->nlayers : 1;
+    L.E = m->ntri * nl;
+    L.N = (m->dim == 3) ? N2 * (long long)(nl * p + 1) : N2;
+    if (L.N >= (1LL << 31) - 1 || (long long)L.E * L.Np >= (1LL << 40)) {
+        set_error("mesh too large for 32-bit node ids");
+        return SEM_EINVAL;
+    }
+    std::vector<long long> gmap((size_t)L.E * L.Np);
+    if (m->dim == 3) {
+        for (int b = 0; b < m->ntri; ++b)
+            for (int l = 0; l < nl; ++l) {
+                const size_t e = (size_t)b * nl + l;
+                for (int k = 0; k <= p; ++k)
+                    for (int n = 0; n < L.NT; ++n)
+                        gmap[e * L.Np + k * L.NT + n] = (long long)(l * p + k) * N2 + map2[(size_t)b * L.NT + n];
+            }
+    } else {
+        for (size_t i = 0; i < gmap.size(); ++i) gmap[i] = map2[i];
+    }
+    const int nf = (m->dim == 3) ? 5 : 3;
+    std::vector<char> dmask(L.N, 0);
+    for (int e = 0; e < L.E; ++e)
+        for (int f = 0; f < nf; ++f)
+            if (m->face_bc[(size_t)e * nf + f])
+                for (int l : L.ref.face_nodes[f]) dmask[gmap[(size_t)e * L.Np + l]] = 1;
+    L.hdir.clear();
+    for (long long i = 0; i < L.N; ++i)
+        if (dmask[i]) L.hdir.push_back(i);
+    if (L.hdir.empty()) {
+        set_error("no Dirichlet face: the pure-Neumann Laplace problem is singular");
+        return SEM_EINVAL;
+    }
+    L.hmap.resize(gmap.size());
+    std::vector<int> mult(L.N, 0);
+    std::vector<char> seen(L.N, 0);
+    std::vector<unsigned char> owner(gmap.size(), 0);
+    for (size_t i = 0; i < gmap.size(); ++i) {
+        const long long g = gmap[i];
+        L.hmap[i] = dmask[g] ? (int)(-g - 1) : (int)g;
+        mult[g] += 1;
+        if (!seen[g]) {
+            seen[g] = 1;
+            owner[i] = dmask[g] ? 0 : 1;
+        }
+    }
+    std::vector<double> wm(L.N);
+    for (long long i = 0; i < L.N; ++i) wm[i] = mult[i] > 0 ? 1.0 / mult[i] : 0.0;
+    CK(upload(&L.map, L.hmap));
+    CK(upload(&L.owner, owner));
+    CK(upload(&L.wmult, wm));
+    CK(upload(&L.wmult32, to_float(wm)));
+    CK(upload(&L.dir, L.hdir));
+    const std::vector<double> rb = ref_block(L.ref);
+    CK(upload(&L.ref64.m, rb));
+    CK(upload(&L.ref32.m, to_float(rb)));
+    L.ref64.count = L.ref32.count = rb.size();
+    CK(dalloc(&L.G, (size_t)L.E * L.ncomp * L.Nq));
+    CK(dalloc(&L.G32, (size_t)L.E * L.ncomp * L.Nq));
+    CK(dalloc(&L.dinv, L.N));
+    CK(dalloc(&L.dinv32, L.N));
+    CK(dalloc(&L.u, L.N));
+    CK(dalloc(&L.f, L.N));
+    CK(dalloc(&L.y, L.N));
+    CK(dalloc(&L.d, L.N));
+    CK(dalloc(&L.u32, L.N));
+    CK(dalloc(&L.f32, L.N));
+    CK(dalloc(&L.y32, L.N));
+    CK(dalloc(&L.d32, L.N));
+    return SEM_OK;
+}
+
+sem_status build_geometry(sem_handle* h, const sem_mesh* m) {
+    const int P = h->P;
+    const Level& L0 = h->lv[0];
+    std::vector<double> vtri((size_t)m->ntri * 6);
+    for (int b = 0; b < m->ntri; ++b)
+        for (int k = 0; k < 3; ++k) {
+            vtri[6 * b + 2 * k] = m->vxy[2 * m->tri[3 * b + k]];
+            vtri[6 * b + 2 * k + 1] = m->vxy[2 * m->tri[3 * b + k] + 1];
+        }
+    double* dvtri = nullptr;
+    CK(upload(&dvtri, vtri));
+    const int NTP = L0.NT;
+    h->eta2.assign(L0.N2, 0.0);
+    if (m->dim == 3 && m->eta) std::memcpy(h->eta2.data(), m->eta, sizeof(double) * L0.N2);
+    std::vector<double> etaP((size_t)m->ntri * NTP);
+    for (int b = 0; b < m->ntri; ++b)
+        for (int n = 0; n < NTP; ++n) etaP[(size_t)b * NTP + n] = h->eta2[h->map2[0][(size_t)b * NTP + n]];
+    double* detaP = nullptr;
+    CK(upload(&detaP, etaP));
+    for (size_t li = 0; li < h->lv.size(); ++li) {
+        Level& L = h->lv[li];
+        std::vector<double> B, Dr, Ds;
+        tri_lagrange(P, L.ref.tq.data(), L.QT, B, Dr, Ds);   // order-P map at level-p points
+        double *dB = nullptr, *dDr = nullptr, *dDs = nullptr;
+        CK(upload(&dB, B));
+        CK(upload(&dDr, Dr));
+        CK(upload(&dDs, Ds));
+        cudaError_t e = launch_geometry(L, dvtri, detaP, dB, dDr, dDs, NTP, h->nlayers, h->depth, 0);
+        cudaFree(dB);
+        cudaFree(dDr);
+        cudaFree(dDs);
+        CK(e);
+    }
+    cudaFree(dvtri);
+    cudaFree(detaP);
+    return SEM_OK;
+}
+
+sem_status build_diagonals(sem_handle* h) {
+    for (Level& L : h->lv) {
+        double* dg = nullptr;
+        CK(dalloc(&dg, L.N));
+        CK(cudaMemset(dg, 0, sizeof(double) * L.N));
+        CK(launch_diag(L, dg, 0));
+        CK(cudaDeviceSynchronize());
+        L.hdiag.resize(L.N);
+        CK(cudaMemcpy(L.hdiag.data(), dg, sizeof(double) * L.N, cudaMemcpyDeviceToHost));
+        cudaFree(dg);
+        std::vector<double> dinv(L.N);
+        std::vector<char> dm(L.N, 0);
+        for (long long i : L.hdir) dm[i] = 1;
+        for (long long i = 0; i < L.N; ++i) {
+            if (!dm[i] && !(L.hdiag[i] > 0.0)) {
+                set_error("non-positive diagonal entry: degenerate element");
+                return SEM_EINVAL;
+            }
+            dinv[i] = dm[i] ? 0.0 : 1.0 / L.hdiag[i];
+        }
+        CK(cudaMemcpy(L.dinv, dinv.data(), sizeof(double) * L.N, cudaMemcpyHostToDevice));
+        const std::vector<float> d32 = to_float(dinv);
+        CK(cudaMemcpy(L.dinv32, d32.data(), sizeof(float) * L.N, cudaMemcpyHostToDevice));
+    }
+    return SEM_OK;
+}
+
+sem_status build_transfers(sem_handle* h) {
+    for (size_t li = 0; li + 1 < h->lv.size(); ++li) {
+        Level& F = h->lv[li];
+        const Level& C = h->lv[li + 1];
+        const std::vector<double> I = interp_matrix(F.dim, F.p, C.p);
+        CK(upload(&F.I64, I));
+        CK(upload(&F.I32, to_float(I)));
+    }
+    return SEM_OK;
+}
+
+sem_status build_workspace(sem_handle* h) {
+    const long long N = h->lv[0].N;
+    const Level& Lc = h->lv.back();
+    Scratch& sc = h->sc;
+    CK(dalloc(&sc.part, (size_t)reduce_blocks() * 66));
+    CK(dalloc(&sc.counter, 4));
+    CK(cudaMemset(sc.counter, 0, 4 * sizeof(unsigned)));
+    CK(dalloc(&sc.scal, 128));
+    CK(cudaMemset(sc.scal, 0, 128 * sizeof(double)));
+    CK(dalloc(&sc.flags, 8));
+    CK(cudaMemset(sc.flags, 0, 8 * sizeof(int)));
+    CK(cudaMallocHost((void**)&sc.hpinned, 128 * sizeof(double)));
+    CK(cudaMallocHost((void**)&sc.hflags, 8 * sizeof(int)));
+    for (double** v : {&h->r, &h->z, &h->p, &h->q, &h->x, &h->fr}) CK(dalloc(v, N));
+    if (h->opts.outer == SEM_OUTER_FGMRES) {
+        CK(dalloc(&h->V, (size_t)(h->opts.gmres_m + 1) * N));
+        CK(dalloc(&h->Zb, (size_t)h->opts.gmres_m * N));
+    }
+    for (double** v : {&h->cx, &h->cr, &h->cz, &h->cp, &h->cq, &h->cb}) CK(dalloc(v, Lc.N));
+    CK(dalloc(&h->st_eta, h->lv[0].hdir.size()));
+    CK(dalloc(&h->st_rhs, N));
+    CK(dalloc(&h->st_phi, N));
+    if (h->opts.profile) {
+        h->ev.resize(512);
+        for (auto& e : h->ev) CK(cudaEventCreate(&e));
+    }
+    return SEM_OK;
+}
+
+}  // namespace sem

@@ -1,0 +1,767 @@
+// Solver driver and C ABI: Chebyshev-Jacobi smoothing, the p-multigrid V-cycle
+// (Algorithm 1), the FP64 coarse solve, PCG (Algorithm 3), preconditioned
+// defect correction (Algorithm 2) and flexible GMRES, plus the entry points
+// declared in include/sem.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sem_internal.hpp"
+
+namespace sem {
+const char* last_error();
+void tri_numbering(int nvert, int ntri, const int* tri, int p, std::vector<int>& map2, long long& N2);
+void tri_coords(int ntri, const int* tri, const double* vxy, int p, const std::vector<int>& map2, long long N2,
+                std::vector<double>& xy);
+sem_status build_level(sem_handle* h, const sem_mesh* m, int li, int p);
+sem_status build_geometry(sem_handle* h, const sem_mesh* m);
+sem_status build_diagonals(sem_handle* h);
+sem_status build_transfers(sem_handle* h);
+sem_status build_workspace(sem_handle* h);
+}  // namespace sem
+
+using namespace sem;
+
+#define CKS(expr)                                                                        \
+    do {                                                                                 \
+        cudaError_t _e = (expr);                                                         \
+        if (_e != cudaSuccess) {                                                         \
+            set_error(std::string("CUDA error: ") + cudaGetErrorString(_e) + " (" #expr ")"); \
+            return SEM_ECUDA;                                                            \
+        }                                                                                \
+    } while (0)
+
+// K(): one kernel launch of this library (counted in sem_stats.kernel_launches).
+#define K(expr)              \
+    do {                     \
+        CKS(expr);           \
+        h->launches += 1;    \
+    } while (0)
+
+#define CKST(expr)                      \
+    do {                                \
+        sem_status _s = (expr);         \
+        if (_s != SEM_OK) return _s;    \
+    } while (0)
+
+namespace {
+
+// Chebyshev coefficients of one sweep (three-term recurrence on [a, b]).
+struct Cheb {
+    double c0;               // first step: d = c0 D^{-1} r
+    double c1[16], c2[16];   // step j >= 1: d = c1 d + c2 D^{-1} r
+};
+
+Cheb cheb_coeffs(double lam, const sem_options& o) {
+    Cheb c{};
+    const double b = o.cheb_hi * lam, a = o.cheb_lo * b;
+    const double theta = 0.5 * (b + a), delta = 0.5 * (b - a), sigma = theta / delta;
+    c.c0 = 1.0 / theta;
+    double rho = 1.0 / sigma;
+    for (int j = 1; j < o.k_cheb && j < 16; ++j) {
+        const double rn = 1.0 / (2.0 * sigma - rho);
+        c.c1[j] = rn * rho;
+        c.c2[j] = 2.0 * rn / delta;
+        rho = rn;
+    }
+    return c;
+}
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Finest-level apply with optional event timing (profile = 1).
+sem_status apply_level64(sem_handle* h, int li, const double* x, double* y, bool lift, cudaStream_t s) {
+    const Level& L = h->lv[li];
+    CKS(cudaMemsetAsync(y, 0, sizeof(double) * L.N, s));
+    const bool timed = (li == 0) && h->opts.profile && (h->ev_used + 2 <= (int)h->ev.size());
+    if (timed) CKS(cudaEventRecord(h->ev[h->ev_used], s));
+    K(launch_apply64(L, x, y, lift, nullptr, s));
+    if (timed) {
+        CKS(cudaEventRecord(h->ev[h->ev_used + 1], s));
+        h->ev_used += 2;
+        h->apply_launches += 1;
+    }
+    if (li == 0) h->fine_applies += 1;
+    return SEM_OK;
+}
+
+sem_status apply_level32(sem_handle* h, int li, const float* x, float* y, cudaStream_t s) {
+    const Level& L = h->lv[li];
+    CKS(cudaMemsetAsync(y, 0, sizeof(float) * L.N, s));
+    K(launch_apply32(L, x, y, s));
+    if (li == 0) h->fine_applies += 1;
+    return SEM_OK;
+}
+
+// Sum the elapsed times of recorded apply events (the stream has been synchronised).
+void flush_events(sem_handle* h) {
+    for (int i = 0; i + 1 < h->ev_used; i += 2) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]) == cudaSuccess) h->apply_ms += ms;
+    }
+    h->ev_used = 0;
+}
+
+// FP64 Jacobi-CG on the coarsest level: x = A_c^{-1} b to coarse_rtol.
+sem_status coarse_solve(sem_handle* h, const double* b, double* x, cudaStream_t s) {
+    const Level& C = h->lv.back();
+    Scratch& sc = h->sc;
+    const double rt = h->opts.coarse_rtol;
+    K(cg_init(C.N, b, C.dinv, x, h->cr, h->cz, h->cp, sc, rt * rt, s));
+    int it = 0;
+    const int chunk = 8;
+    while (it < h->opts.coarse_imax) {
+        for (int k = 0; k < chunk; ++k) {
+            CKS(cudaMemsetAsync(h->cq, 0, sizeof(double) * C.N, s));
+            K(launch_apply64(C, h->cp, h->cq, false, sc.flags + F_CG_DONE, s));
+            K(cg_pq(C.N, h->cp, h->cq, sc, s));
+            K(cg_update(C.N, C.dinv, x, h->cr, h->cz, h->cp, h->cq, sc, s));
+            K(cg_direction(C.N, h->cz, h->cp, sc, s));
+        }
+        it += chunk;
+        CKS(cudaMemcpyAsync(sc.hflags, sc.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CKS(cudaStreamSynchronize(s));
+        if (sc.hflags[F_CG_DONE]) break;
+    }
+    const int used = sc.hflags[F_CG_ITERS];
+    h->coarse_iters_max = std::max(h->coarse_iters_max, used);
+    if (!sc.hflags[F_CG_DONE]) {
+        set_error("coarse CG did not reach coarse_rtol within coarse_imax iterations");
+        return SEM_NOT_CONVERGED;
+    }
+    return SEM_OK;
+}
+
+// One Chebyshev-Jacobi sweep of level li (u = 0 on entry when zero_init).
+template <typename T>
+sem_status smooth(sem_handle* h, int li, const T* f, T* u, bool zero_init, cudaStream_t s);
+
+template <>
+sem_status smooth<double>(sem_handle* h, int li, const double* f, double* u, bool zero_init, cudaStream_t s) {
+    const Level& L = h->lv[li];
+    const Cheb c = cheb_coeffs(L.lam, h->opts);
+    if (zero_init) {
+        K(cheb_first<double>(L.N, c.c0, L.dinv, f, u, L.d, s));
+    } else {
+        CKST(apply_level64(h, li, u, L.y, false, s));
+        K(cheb_restart<double>(L.N, c.c0, L.dinv, f, L.y, u, L.d, s));
+    }
+    for (int j = 1; j < h->opts.k_cheb; ++j) {
+        CKST(apply_level64(h, li, u, L.y, false, s));
+        K(cheb_step<double>(L.N, c.c1[j], c.c2[j], L.dinv, f, L.y, u, L.d, s));
+    }
+    return SEM_OK;
+}
+
+template <>
+sem_status smooth<float>(sem_handle* h, int li, const float* f, float* u, bool zero_init, cudaStream_t s) {
+    const Level& L = h->lv[li];
+    const Cheb c = cheb_coeffs(L.lam, h->opts);
+    if (zero_init) {
+        K(cheb_first<float>(L.N, (float)c.c0, L.dinv32, f, u, L.d32, s));
+    } else {
+        CKST(apply_level32(h, li, u, L.y32, s));
+        K(cheb_restart<float>(L.N, (float)c.c0, L.dinv32, f, L.y32, u, L.d32, s));
+    }
+    for (int j = 1; j < h->opts.k_cheb; ++j) {
+        CKST(apply_level32(h, li, u, L.y32, s));
+        K(cheb_step<float>(L.N, (float)c.c1[j], (float)c.c2[j], L.dinv32, f, L.y32, u, L.d32, s));
+    }
+    return SEM_OK;
+}
+
+// Algorithm 1 with zero initial guess on every level, FP64 throughout.
+sem_status vcycle64(sem_handle* h, const double* f0, double* u0, cudaStream_t s) {
+    const int nl = (int)h->lv.size();
+    h->vcycles += 1;
+    if (nl == 1) return coarse_solve(h, f0, u0, s);
+    for (int li = 0; li + 1 < nl; ++li) {
+        Level& L = h->lv[li];
+        Level& C = h->lv[li + 1];
+        const double* f = (li == 0) ? f0 : L.f;
+        double* u = (li == 0) ? u0 : L.u;
+        for (int m = 0; m < h->opts.nu1; ++m) CKST(smooth<double>(h, li, f, u, m == 0, s));
+        if (h->opts.nu1 == 0) CKS(cudaMemsetAsync(u, 0, sizeof(double) * L.N, s));
+        CKST(apply_level64(h, li, u, L.y, false, s));
+        CKS(cudaMemsetAsync(C.f, 0, sizeof(double) * C.N, s));
+        K(launch_restrict64(L, C, f, L.y, C.f, s));
+    }
+    const sem_status cs = coarse_solve(h, h->lv[nl - 1].f, h->lv[nl - 1].u, s);
+    if (cs != SEM_OK) return cs;
+    for (int li = nl - 2; li >= 0; --li) {
+        Level& L = h->lv[li];
+        const Level& C = h->lv[li + 1];
+        const double* f = (li == 0) ? f0 : L.f;
+        double* u = (li == 0) ? u0 : L.u;
+        K(launch_prolong64(L, C, C.u, u, s));
+        for (int m = 0; m < h->opts.nu2; ++m) CKST(smooth<double>(h, li, f, u, false, s));
+    }
+    return SEM_OK;
+}
+
+// Algorithm 1 in FP32 on every level but the coarsest, which is solved in FP64.
+sem_status vcycle32(sem_handle* h, const float* f0, float* u0, cudaStream_t s) {
+    const int nl = (int)h->lv.size();
+    h->vcycles += 1;
+    Level& Cc = h->lv[nl - 1];
+    if (nl == 1) {
+        K(to_f64(Cc.N, f0, h->cb, s));
+        CKST(coarse_solve(h, h->cb, Cc.u, s));
+        K(to_f32(Cc.N, Cc.u, u0, s));
+        return SEM_OK;
+    }
+    for (int li = 0; li + 1 < nl; ++li) {
+        Level& L = h->lv[li];
+        Level& C = h->lv[li + 1];
+        const float* f = (li == 0) ? f0 : L.f32;
+        float* u = (li == 0) ? u0 : L.u32;
+        for (int m = 0; m < h->opts.nu1; ++m) CKST(smooth<float>(h, li, f, u, m == 0, s));
+        if (h->opts.nu1 == 0) CKS(cudaMemsetAsync(u, 0, sizeof(float) * L.N, s));
+        CKST(apply_level32(h, li, u, L.y32, s));
+        CKS(cudaMemsetAsync(C.f32, 0, sizeof(float) * C.N, s));
+        K(launch_restrict32(L, C, f, L.y32, C.f32, s));
+    }
+    K(to_f64(Cc.N, Cc.f32, h->cb, s));
+    const sem_status cs = coarse_solve(h, h->cb, Cc.u, s);
+    if (cs != SEM_OK) return cs;
+    K(to_f32(Cc.N, Cc.u, Cc.u32, s));
+    for (int li = nl - 2; li >= 0; --li) {
+        Level& L = h->lv[li];
+        const Level& C = h->lv[li + 1];
+        const float* f = (li == 0) ? f0 : L.f32;
+        float* u = (li == 0) ? u0 : L.u32;
+        K(launch_prolong32(L, C, C.u32, u, s));
+        for (int m = 0; m < h->opts.nu2; ++m) CKST(smooth<float>(h, li, f, u, false, s));
+    }
+    return SEM_OK;
+}
+
+// z = M^{-1} r on the finest level in the configured precision (r has zero Dirichlet entries).
+sem_status precondition(sem_handle* h, const double* r, double* z, cudaStream_t s) {
+    if (h->opts.precision == SEM_PREC_MIXED_FP32) {
+        Level& L = h->lv[0];
+        K(to_f32(L.N, r, L.f32, s));
+        CKST(vcycle32(h, L.f32, L.u32, s));
+        K(to_f64(L.N, L.u32, z, s));
+        return SEM_OK;
+    }
+    return vcycle64(h, r, z, s);
+}
+
+sem_status read_scalars(sem_handle* h, int first, int count, cudaStream_t s) {
+    CKS(cudaMemcpyAsync(h->sc.hpinned + first, h->sc.scal + first, count * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CKS(cudaStreamSynchronize(s));
+    if (h->opts.profile) flush_events(h);
+    return SEM_OK;
+}
+
+// Power iteration for lambda_hat of D^{-1} A on level li.
+sem_status estimate_lambda(sem_handle* h, int li) {
+    Level& L = h->lv[li];
+    std::vector<double> x0(L.N, 0.0);
+    std::vector<char> dm(L.N, 0);
+    for (long long i : L.hdir) dm[i] = 1;
+    double nrm = 0;
+    for (long long i = 0; i < L.N; ++i)
+        if (!dm[i]) { x0[i] = std::sin((double)i + 1.0); nrm += x0[i] * x0[i]; }
+    nrm = std::sqrt(nrm);
+    for (long long i = 0; i < L.N; ++i) x0[i] /= nrm;
+    CKS(cudaMemcpy(L.u, x0.data(), sizeof(double) * L.N, cudaMemcpyHostToDevice));
+    cudaStream_t s = 0;
+    for (int it = 0; it < h->opts.power_its; ++it) {
+        CKS(cudaMemsetAsync(L.y, 0, sizeof(double) * L.N, s));
+        K(launch_apply64(L, L.u, L.y, false, nullptr, s));
+        K(cheb_first<double>(L.N, 1.0, L.dinv, L.y, L.d, L.f, s));   // d = D^{-1} A x (f: scratch copy)
+        K(dot64(L.N, L.d, L.d, h->sc, h->sc.scal + S_TMP, s));
+        K(scale64(L.N, L.d, h->sc.scal + S_TMP, L.u, s));             // x = d / ||d||
+    }
+    CKST(read_scalars(h, S_TMP, 1, s));
+    L.lam = std::sqrt(h->sc.hpinned[S_TMP]);
+    return SEM_OK;
+}
+
+void free_level(Level& L) {
+    void* ptrs[] = {L.map, L.G, L.G32, L.dinv, L.dinv32, L.dir, L.ref64.m, L.ref32.m, L.I64, L.I32,
+                    L.owner, L.wmult, L.wmult32, L.u, L.f, L.y, L.d, L.u32, L.f32, L.y32, L.d32};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+sem_status check_mesh(const sem_mesh* m, int P) {
+    if (!m || (m->dim != 2 && m->dim != 3)) { set_error("mesh->dim must be 2 or 3"); return SEM_EINVAL; }
+    if (P < 1 || P > 6) { set_error("P must be in 1..6"); return SEM_EINVAL; }
+    if (m->nvert < 3 || m->ntri < 1 || !m->vxy || !m->tri || !m->face_bc) {
+        set_error("mesh arrays missing or empty");
+        return SEM_EINVAL;
+    }
+    for (long long i = 0; i < 3LL * m->ntri; ++i)
+        if (m->tri[i] < 0 || m->tri[i] >= m->nvert) { set_error("triangle vertex id out of range"); return SEM_EINVAL; }
+    for (int b = 0; b < m->ntri; ++b) {
+        const double* a = m->vxy + 2 * m->tri[3 * b];
+        const double* c1 = m->vxy + 2 * m->tri[3 * b + 1];
+        const double* c2 = m->vxy + 2 * m->tri[3 * b + 2];
+        const double area2 = (c1[0] - a[0]) * (c2[1] - a[1]) - (c2[0] - a[0]) * (c1[1] - a[1]);
+        if (!(area2 > 0.0)) { set_error("triangle not counter-clockwise or degenerate"); return SEM_EINVAL; }
+    }
+    if (m->dim == 3 && (m->nlayers < 1 || !(m->depth > 0.0))) {
+        set_error("dim 3 needs nlayers >= 1 and depth > 0");
+        return SEM_EINVAL;
+    }
+    return SEM_OK;
+}
+
+sem_status check_options(const sem_options& o, int P) {
+    if (o.nlevels < 1 || o.nlevels > SEM_MAX_LEVELS || o.level_p[0] != P || o.level_p[o.nlevels - 1] != 1) {
+        set_error("levels must run from P down to 1");
+        return SEM_EINVAL;
+    }
+    for (int i = 1; i < o.nlevels; ++i)
+        if (o.level_p[i] >= o.level_p[i - 1]) { set_error("level orders must decrease"); return SEM_EINVAL; }
+    if (o.k_cheb < 1 || o.k_cheb > 15 || o.nu1 < 0 || o.nu2 < 0 || o.power_its < 1) {
+        set_error("smoother parameters out of range");
+        return SEM_EINVAL;
+    }
+    if (!(o.cheb_hi > 0) || !(o.cheb_lo > 0) || !(o.cheb_lo < 1)) { set_error("Chebyshev bounds"); return SEM_EINVAL; }
+    if (o.outer < 0 || o.outer > 2 || o.precision < 0 || o.precision > 1) { set_error("outer/precision"); return SEM_EINVAL; }
+    if (o.outer == SEM_OUTER_FGMRES && (o.gmres_m < 1 || o.gmres_m > 64)) { set_error("gmres_m in 1..64"); return SEM_EINVAL; }
+    if (o.imax < 0 || o.coarse_imax < 1 || !(o.coarse_rtol > 0)) { set_error("iteration limits"); return SEM_EINVAL; }
+    return SEM_OK;
+}
+
+sem_status fail_nan(double v) {
+    if (!std::isfinite(v)) { set_error("non-finite residual"); return SEM_NAN; }
+    return SEM_OK;
+}
+
+// ---------------------------------------------------------------- outer iterations
+// Each works on the free-node system in place: f = h->fr, u = phi (zero Dirichlet entries).
+sem_status outer_pcg(sem_handle* h, double* u, double tol, sem_stats* st, cudaStream_t s) {
+    const long long N = h->lv[0].N;
+    Scratch& sc = h->sc;
+    CKS(cudaMemcpyAsync(h->r, h->fr, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    double rn = st->fnorm;
+    st->res0 = rn;
+    int i = 0;
+    sem_status ret = SEM_OK;
+    if (rn > tol) {
+        CKST(precondition(h, h->r, h->z, s));
+        CKS(cudaMemcpyAsync(h->p, h->z, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+        int cur = S_DELTA0, nxt = S_DELTA1;
+        K(dot64(N, h->z, h->r, sc, sc.scal + cur, s));
+        while (true) {
+            if (i >= h->opts.imax) { ret = SEM_NOT_CONVERGED; break; }
+            CKST(apply_level64(h, 0, h->p, h->q, false, s));
+            K(dot64(N, h->p, h->q, sc, sc.scal + S_PQ, s));
+            K(pcg_update(N, sc.scal + cur, sc.scal + S_PQ, h->p, h->q, u, h->r, sc, sc.scal + S_RR, s));
+            ++i;
+            CKST(read_scalars(h, 0, 4, s));
+            const double pq = sc.hpinned[S_PQ];
+            rn = std::sqrt(sc.hpinned[S_RR]);
+            CKST(fail_nan(rn));
+            if (!(pq > 0.0)) { set_error("PCG breakdown: p^T A p <= 0"); ret = SEM_BREAKDOWN; break; }
+            if (rn <= tol) break;
+            CKST(precondition(h, h->r, h->z, s));
+            K(dot64(N, h->z, h->r, sc, sc.scal + nxt, s));
+            K(pcg_direction(N, sc.scal + nxt, sc.scal + cur, h->z, h->p, s));
+            std::swap(cur, nxt);
+        }
+    }
+    st->iters = i;
+    st->res_final = rn;
+    return ret;
+}
+
+sem_status outer_pdc(sem_handle* h, double* u, double tol, sem_stats* st, cudaStream_t s) {
+    const long long N = h->lv[0].N;
+    Scratch& sc = h->sc;
+    CKS(cudaMemcpyAsync(h->r, h->fr, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    double rn = st->fnorm;
+    st->res0 = rn;
+    int i = 0;
+    sem_status ret = SEM_OK;
+    while (rn > tol) {
+        if (i >= h->opts.imax) { ret = SEM_NOT_CONVERGED; break; }
+        CKST(precondition(h, h->r, h->z, s));
+        K(axpy64(N, 1.0, h->z, u, s));
+        CKST(apply_level64(h, 0, u, h->q, false, s));
+        K(residual64(N, h->fr, h->q, h->r, sc, sc.scal + S_RR, s));
+        ++i;
+        CKST(read_scalars(h, S_RR, 1, s));
+        rn = std::sqrt(sc.hpinned[S_RR]);
+        CKST(fail_nan(rn));
+    }
+    st->iters = i;
+    st->res_final = rn;
+    return ret;
+}
+
+sem_status outer_fgmres(sem_handle* h, double* u, double tol, sem_stats* st, cudaStream_t s) {
+    const long long N = h->lv[0].N;
+    const int m = h->opts.gmres_m;
+    Scratch& sc = h->sc;
+    double* hm = sc.scal + S_MULTI;
+    CKS(cudaMemcpyAsync(h->r, h->fr, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    double beta = st->fnorm;
+    st->res0 = beta;
+    int it = 0;
+    sem_status ret = SEM_OK;
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+    double* dy = nullptr;
+    while (beta > tol) {
+        if (it >= h->opts.imax) { ret = SEM_NOT_CONVERGED; break; }
+        // v0 = r / beta
+        h->sc.hpinned[S_TMP] = beta * beta;
+        CKS(cudaMemcpyAsync(sc.scal + S_TMP, h->sc.hpinned + S_TMP, sizeof(double), cudaMemcpyHostToDevice, s));
+        K(scale64(N, h->r, sc.scal + S_TMP, h->V, s));
+        std::fill(H.begin(), H.end(), 0.0);
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int j = 0;
+        double resid = beta;
+        while (j < m && it < h->opts.imax) {
+            double* vj = h->V + (size_t)j * N;
+            double* zj = h->Zb + (size_t)j * N;
+            double* w = h->V + (size_t)(j + 1) * N;
+            CKST(precondition(h, vj, zj, s));
+            CKST(apply_level64(h, 0, zj, w, false, s));
+            // classical Gram-Schmidt, twice
+            K(multidot64(N, j + 1, h->V, w, sc, hm, s));
+            K(multiaxpy64(N, j + 1, h->V, hm, -1.0, w, s));
+            CKST(read_scalars(h, S_MULTI, j + 1, s));
+            std::vector<double> h1(sc.hpinned + S_MULTI, sc.hpinned + S_MULTI + j + 1);
+            K(multidot64(N, j + 1, h->V, w, sc, hm, s));
+            K(multiaxpy64(N, j + 1, h->V, hm, -1.0, w, s));
+            K(dot64(N, w, w, sc, sc.scal + S_TMP, s));
+            CKST(read_scalars(h, S_MULTI, j + 1, s));
+            CKST(read_scalars(h, S_TMP, 1, s));
+            for (int i2 = 0; i2 <= j; ++i2) H[(size_t)i2 * m + j] = h1[i2] + sc.hpinned[S_MULTI + i2];
+            const double hn = std::sqrt(sc.hpinned[S_TMP]);
+            CKST(fail_nan(hn));
+            H[(size_t)(j + 1) * m + j] = hn;
+            if (hn > 0) K(scale64(N, w, sc.scal + S_TMP, w, s));
+            for (int i2 = 0; i2 < j; ++i2) {
+                const double t = cs[i2] * H[(size_t)i2 * m + j] + sn[i2] * H[(size_t)(i2 + 1) * m + j];
+                H[(size_t)(i2 + 1) * m + j] = -sn[i2] * H[(size_t)i2 * m + j] + cs[i2] * H[(size_t)(i2 + 1) * m + j];
+                H[(size_t)i2 * m + j] = t;
+            }
+            const double den = std::hypot(H[(size_t)j * m + j], H[(size_t)(j + 1) * m + j]);
+            cs[j] = H[(size_t)j * m + j] / den;
+            sn[j] = H[(size_t)(j + 1) * m + j] / den;
+            H[(size_t)j * m + j] = den;
+            H[(size_t)(j + 1) * m + j] = 0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            ++j;
+            ++it;
+            resid = std::fabs(g[j]);
+            if (resid <= tol || hn == 0.0) break;
+        }
+        for (int i2 = j - 1; i2 >= 0; --i2) {
+            double v = g[i2];
+            for (int k = i2 + 1; k < j; ++k) v -= H[(size_t)i2 * m + k] * y[k];
+            y[i2] = v / H[(size_t)i2 * m + i2];
+        }
+        if (!dy) CKS(cudaMalloc(&dy, sizeof(double) * m));
+        CKS(cudaMemcpyAsync(dy, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, s));
+        K(multiaxpy64(N, j, h->Zb, dy, 1.0, u, s));
+        CKST(apply_level64(h, 0, u, h->q, false, s));
+        K(residual64(N, h->fr, h->q, h->r, sc, sc.scal + S_RR, s));
+        CKST(read_scalars(h, S_RR, 1, s));
+        beta = std::sqrt(sc.hpinned[S_RR]);
+        CKST(fail_nan(beta));
+    }
+    if (dy) cudaFree(dy);
+    st->iters = it;
+    st->res_final = beta;
+    return ret;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* sem_last_error(void) { return sem::last_error(); }
+
+void sem_default_options(sem_options* o, int P) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->outer = SEM_OUTER_PCG;
+    o->precision = SEM_PREC_FP64;
+    o->nu1 = 1;
+    o->nu2 = 1;
+    o->k_cheb = 3;
+    o->cheb_lo = 0.1;
+    o->cheb_hi = 1.1;
+    o->power_its = 20;
+    static const int table[7][3] = {{1, 0, 0}, {1, 0, 0}, {2, 1, 0}, {3, 2, 1}, {4, 2, 1}, {5, 3, 1}, {6, 3, 1}};
+    if (P < 1 || P > 6) P = 1;
+    int n = 0;
+    for (int k = 0; k < 3; ++k)
+        if (table[P][k] > 0) o->level_p[n++] = table[P][k];
+    o->nlevels = n;
+    o->rtol = 1e-8;
+    o->atol = 0.0;
+    o->imax = 200;
+    o->gmres_m = 30;
+    o->coarse_rtol = 1e-12;
+    o->coarse_imax = 5000;
+    o->profile = 0;
+}
+
+sem_status sem_mesh_nodes2d(const sem_mesh* m, int p, long long* n2, double* xy) {
+    if (!m || !n2 || p < 1 || p > 6 || !m->tri || !m->vxy || m->ntri < 1) {
+        set_error("sem_mesh_nodes2d: bad arguments");
+        return SEM_EINVAL;
+    }
+    for (long long i = 0; i < 3LL * m->ntri; ++i)
+        if (m->tri[i] < 0 || m->tri[i] >= m->nvert) { set_error("triangle vertex id out of range"); return SEM_EINVAL; }
+    std::vector<int> map2;
+    long long N2 = 0;
+    tri_numbering(m->nvert, m->ntri, m->tri, p, map2, N2);
+    *n2 = N2;
+    if (xy) {
+        std::vector<double> c;
+        tri_coords(m->ntri, m->tri, m->vxy, p, map2, N2, c);
+        std::memcpy(xy, c.data(), sizeof(double) * c.size());
+    }
+    return SEM_OK;
+}
+
+sem_status sem_setup(const sem_mesh* m, int P, const sem_options* opts, sem_handle** out) {
+    if (!out) { set_error("out is NULL"); return SEM_EINVAL; }
+    *out = nullptr;
+    CKST(check_mesh(m, P));
+    sem_options o;
+    if (opts) o = *opts; else sem_default_options(&o, P);
+    CKST(check_options(o, P));
+    sem_handle* h = new (std::nothrow) sem_handle();
+    if (!h) { set_error("host allocation failed"); return SEM_ENOMEM; }
+    h->dim = m->dim;
+    h->P = P;
+    h->opts = o;
+    h->nlayers = (m->dim == 3) ? m->nlayers : 1;
+    h->depth = (m->dim == 3) ? m->depth : 0.0;
+    cudaGetDevice(&h->device);
+    h->vxy.assign(m->vxy, m->vxy + 2 * (size_t)m->nvert);
+    h->tri.assign(m->tri, m->tri + 3 * (size_t)m->ntri);
+    h->lv.resize(o.nlevels);
+    h->map2.resize(o.nlevels);
+    sem_status st = SEM_OK;
+    for (int li = 0; li < o.nlevels && st == SEM_OK; ++li) st = build_level(h, m, li, o.level_p[li]);
+    if (st == SEM_OK) st = build_geometry(h, m);
+    if (st == SEM_OK) st = build_diagonals(h);
+    if (st == SEM_OK) st = build_transfers(h);
+    if (st == SEM_OK) st = build_workspace(h);
+    for (int li = 0; li + 1 < o.nlevels && st == SEM_OK; ++li) st = estimate_lambda(h, li);
+    if (st == SEM_OK) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) { set_error(std::string("setup: ") + cudaGetErrorString(e)); st = SEM_ECUDA; }
+    }
+    if (st != SEM_OK) {
+        sem_destroy(h);
+        return st;
+    }
+    h->fine_applies = 0;
+    *out = h;
+    return SEM_OK;
+}
+
+void sem_destroy(sem_handle* h) {
+    if (!h) return;
+    for (Level& L : h->lv) free_level(L);
+    void* ptrs[] = {h->sc.part, h->sc.counter, h->sc.scal, h->sc.flags, h->r, h->z, h->p, h->q, h->x, h->fr,
+                    h->V, h->Zb, h->cx, h->cr, h->cz, h->cp, h->cq, h->cb, h->st_eta, h->st_rhs, h->st_phi};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (h->sc.hpinned) cudaFreeHost(h->sc.hpinned);
+    if (h->sc.hflags) cudaFreeHost(h->sc.hflags);
+    for (auto& e : h->ev) cudaEventDestroy(e);
+    delete h;
+}
+
+static sem_status check_level(const sem_handle* h, int level) {
+    if (!h) { set_error("handle is NULL"); return SEM_EINVAL; }
+    if (level < 0 || level >= (int)h->lv.size()) { set_error("level out of range"); return SEM_EINVAL; }
+    return SEM_OK;
+}
+
+sem_status sem_query(const sem_handle* h, int level, long long* ndof, long long* ndir, long long* nelem, int* np) {
+    CKST(check_level(h, level));
+    const Level& L = h->lv[level];
+    if (ndof) *ndof = L.N;
+    if (ndir) *ndir = (long long)L.hdir.size();
+    if (nelem) *nelem = L.E;
+    if (np) *np = L.Np;
+    return SEM_OK;
+}
+
+sem_status sem_dirichlet_nodes(const sem_handle* h, int level, long long* idx) {
+    CKST(check_level(h, level));
+    if (!idx) { set_error("idx is NULL"); return SEM_EINVAL; }
+    std::memcpy(idx, h->lv[level].hdir.data(), sizeof(long long) * h->lv[level].hdir.size());
+    return SEM_OK;
+}
+
+sem_status sem_element_map(const sem_handle* h, int level, int* map) {
+    CKST(check_level(h, level));
+    if (!map) { set_error("map is NULL"); return SEM_EINVAL; }
+    const Level& L = h->lv[level];
+    for (size_t i = 0; i < L.hmap.size(); ++i) map[i] = L.hmap[i] >= 0 ? L.hmap[i] : -L.hmap[i] - 1;
+    return SEM_OK;
+}
+
+sem_status sem_lambda_max(const sem_handle* h, double* lam) {
+    if (!h || !lam) { set_error("bad arguments"); return SEM_EINVAL; }
+    for (size_t i = 0; i < h->lv.size(); ++i) lam[i] = h->lv[i].lam;
+    return SEM_OK;
+}
+
+sem_status sem_diagonal(const sem_handle* h, int level, double* diag) {
+    CKST(check_level(h, level));
+    if (!diag) { set_error("diag is NULL"); return SEM_EINVAL; }
+    std::memcpy(diag, h->lv[level].hdiag.data(), sizeof(double) * h->lv[level].hdiag.size());
+    return SEM_OK;
+}
+
+sem_status sem_node_coords(const sem_handle* h, int level, double* xyz) {
+    CKST(check_level(h, level));
+    if (!xyz) { set_error("xyz is NULL"); return SEM_EINVAL; }
+    const Level& L = h->lv[level];
+    std::vector<double> xy;
+    tri_coords((int)(h->tri.size() / 3), h->tri.data(), h->vxy.data(), L.p, h->map2[level], L.N2, xy);
+    if (h->dim == 2) {
+        std::memcpy(xyz, xy.data(), sizeof(double) * xy.size());
+        return SEM_OK;
+    }
+    // eta_P at this level's 2D nodes: the order-P surface interpolated per base triangle
+    const Level& L0 = h->lv[0];
+    std::vector<double> eta(L.N2, 0.0);
+    std::vector<double> B, Dr, Ds;
+    tri_lagrange(h->P, L.ref.tnodes.data(), L.NT, B, Dr, Ds);
+    const int ntri = (int)(h->tri.size() / 3);
+    for (int b = 0; b < ntri; ++b)
+        for (int n = 0; n < L.NT; ++n) {
+            double v = 0;
+            for (int k = 0; k < L0.NT; ++k) v += B[(size_t)n * L0.NT + k] * h->eta2[h->map2[0][(size_t)b * L0.NT + k]];
+            eta[h->map2[level][(size_t)b * L.NT + n]] = v;
+        }
+    const int nl = h->nlayers, p = L.p;
+    for (int kz = 0; kz <= nl * p; ++kz) {
+        int l = kz / p, k = kz - l * p;
+        if (l == nl) { l = nl - 1; k = p; }
+        const double sigma = (l + 0.5 * (L.ref.znodes[k] + 1.0)) / nl;
+        for (long long g = 0; g < L.N2; ++g) {
+            const long long id = (long long)kz * L.N2 + g;
+            xyz[3 * id] = xy[2 * g];
+            xyz[3 * id + 1] = xy[2 * g + 1];
+            xyz[3 * id + 2] = -h->depth + sigma * (h->depth + eta[g]);
+        }
+    }
+    return SEM_OK;
+}
+
+sem_status sem_apply(sem_handle* h, int level, const double* x, double* y, void* stream) {
+    CKST(check_level(h, level));
+    if (!x || !y || x == y) { set_error("sem_apply: x and y must be distinct device buffers"); return SEM_EINVAL; }
+    cudaStream_t s = as_stream(stream);
+    const Level& L = h->lv[level];
+    CKST(apply_level64(h, level, x, y, false, s));
+    K(copy_dirichlet((long long)L.hdir.size(), L.dir, x, y, s));
+    return SEM_OK;
+}
+
+sem_status pmg_vcycle(sem_handle* h, const double* r, double* z, void* stream) {
+    if (!h || !r || !z || r == z) { set_error("pmg_vcycle: bad arguments"); return SEM_EINVAL; }
+    cudaStream_t s = as_stream(stream);
+    const Level& L = h->lv[0];
+    CKS(cudaMemcpyAsync(h->r, r, sizeof(double) * L.N, cudaMemcpyDeviceToDevice, s));
+    K(zero_dirichlet((long long)L.hdir.size(), L.dir, h->r, s));
+    return precondition(h, h->r, z, s);
+}
+
+sem_status laplace_solve(sem_handle* h, const double* rhs, const double* eta, double tol, double* phi,
+                         sem_stats* stats, void* stream) {
+    if (!h || !eta || !phi) { set_error("laplace_solve: bad arguments"); return SEM_EINVAL; }
+    cudaStream_t s = as_stream(stream);
+    const Level& L = h->lv[0];
+    const long long N = L.N, nd = (long long)L.hdir.size();
+    sem_stats st{};
+    h->fine_applies = 0;
+    h->vcycles = 0;
+    h->coarse_iters_max = 0;
+    h->apply_ms = 0;
+    h->apply_launches = 0;
+    h->launches = 0;
+    h->ev_used = 0;
+    cudaEvent_t e0, e1;
+    CKS(cudaEventCreate(&e0));
+    CKS(cudaEventCreate(&e1));
+    CKS(cudaEventRecord(e0, s));
+    // lifting: f = rhs_F - A_FD phi~
+    CKS(cudaMemsetAsync(h->x, 0, sizeof(double) * N, s));
+    K(scatter_dirichlet(nd, L.dir, eta, h->x, s));
+    CKST(apply_level64(h, 0, h->x, h->q, true, s));
+    h->fine_applies -= 1;   // lifting is not an iteration apply
+    if (rhs) {
+        CKS(cudaMemcpyAsync(h->fr, rhs, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+        K(axpy64(N, -1.0, h->q, h->fr, s));
+        K(zero_dirichlet(nd, L.dir, h->fr, s));
+    } else {
+        CKS(cudaMemsetAsync(h->fr, 0, sizeof(double) * N, s));
+        K(axpy64(N, -1.0, h->q, h->fr, s));
+    }
+    K(dot64(N, h->fr, h->fr, h->sc, h->sc.scal + S_FF, s));
+    CKST(read_scalars(h, S_FF, 1, s));
+    st.fnorm = std::sqrt(h->sc.hpinned[S_FF]);
+    CKST(fail_nan(st.fnorm));
+    const double rtol = (tol > 0) ? tol : h->opts.rtol;
+    const double thr = rtol * st.fnorm + h->opts.atol;
+    CKS(cudaMemsetAsync(phi, 0, sizeof(double) * N, s));
+    sem_status ret;
+    switch (h->opts.outer) {
+        case SEM_OUTER_PDC: ret = outer_pdc(h, phi, thr, &st, s); break;
+        case SEM_OUTER_FGMRES: ret = outer_fgmres(h, phi, thr, &st, s); break;
+        default: ret = outer_pcg(h, phi, thr, &st, s); break;
+    }
+    K(scatter_dirichlet(nd, L.dir, eta, phi, s));
+    CKS(cudaEventRecord(e1, s));
+    CKS(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (h->opts.profile) flush_events(h);
+    st.ms = ms;
+    st.status = ret;
+    st.fine_applies = h->fine_applies;
+    st.vcycles = h->vcycles;
+    st.coarse_iters_max = h->coarse_iters_max;
+    st.apply_ms = h->apply_ms;
+    st.apply_launches = h->apply_launches;
+    st.kernel_launches = h->launches;
+    st.q_mean = (st.iters > 0 && st.res0 > 0) ? std::pow(st.res_final / st.res0, 1.0 / st.iters) : 0.0;
+    if (stats) *stats = st;
+    return ret;
+}
+
+sem_status laplace_solve_host(sem_handle* h, const double* rhs_host, const double* eta_host, double tol,
+                              double* phi_host, sem_stats* stats, void* stream) {
+    if (!h || !eta_host || !phi_host) { set_error("laplace_solve_host: bad arguments"); return SEM_EINVAL; }
+    cudaStream_t s = as_stream(stream);
+    const Level& L = h->lv[0];
+    const long long N = L.N, nd = (long long)L.hdir.size();
+    CKS(cudaMemcpyAsync(h->st_eta, eta_host, sizeof(double) * nd, cudaMemcpyHostToDevice, s));
+    if (rhs_host) CKS(cudaMemcpyAsync(h->st_rhs, rhs_host, sizeof(double) * N, cudaMemcpyHostToDevice, s));
+    const sem_status ret = laplace_solve(h, rhs_host ? h->st_rhs : nullptr, h->st_eta, tol, h->st_phi, stats, stream);
+    CKS(cudaMemcpyAsync(phi_host, h->st_phi, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+    CKS(cudaStreamSynchronize(s));
+    return ret;
+}
+
+}  // extern "C"

@@ -1,0 +1,73 @@
+"""CPU checks of the C-ABI library: it loads, exports every entry point that
+include/sem.h declares, and its host-only numbering of order-p triangle nodes
+(sem_mesh_nodes2d) agrees with the oracle's canonical numbering.  No call here
+touches a GPU."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def sem():
+    import paper_2009_00705_gb300 as pkg
+    from paper_2009_00705_gb300 import build as B
+    B.build()
+    pkg.lib()
+    return pkg
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "sem.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:sem_status|void|const char\*)\s+(\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("sem_setup", "sem_apply", "pmg_vcycle", "laplace_solve", "sem_destroy", "sem_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(sem):
+    L = sem.lib()
+    for name in declared_functions():
+        assert hasattr(L, name), name
+    assert set(declared_functions()) == set(sem.EXPORTS)
+
+
+def test_default_options(sem):
+    o = sem.sem_default_options(6)
+    assert [o.level_p[i] for i in range(o.nlevels)] == [6, 3, 1]
+    o = sem.sem_default_options(4)
+    assert [o.level_p[i] for i in range(o.nlevels)] == [4, 2, 1]
+    assert o.k_cheb == 3 and o.nu1 == 1 and o.nu2 == 1 and o.rtol == 1e-8
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6])
+def test_host_numbering_matches_oracle(sem, p):
+    from oracle.mesh import Level
+    from oracle.refelem import RefTri
+    for mesh in (W.config_slice2d(), W.box3d(5, 3, 2)):
+        lev = Level(mesh, p)
+        xy = sem.sem_mesh_nodes2d(mesh, p)
+        assert xy.shape == (lev.N2, 2)
+        tn = RefTri(p).nodes
+        for b in range(mesh.tri.shape[0]):
+            np.testing.assert_allclose(xy[lev.map2[b]], lev.tri_node_xy(b, tn), atol=1e-13)
+
+
+def test_bad_mesh_is_rejected_without_gpu(sem):
+    m = W.config_slice2d()
+    m.tri = m.tri.copy()
+    m.tri[0, 0] = 10**6
+    with pytest.raises(sem.SemError) as e:
+        sem.sem_mesh_nodes2d(m, 3)
+    assert e.value.status == sem.SEM_EINVAL
+    assert "out of range" in sem.sem_last_error()
