@@ -167,6 +167,9 @@ def main():
     ap.add_argument("--sample-n", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--inner-imax", type=int, default=40)
+    ap.add_argument("--inner-rtol", type=float, default=1e-4)
+    ap.add_argument("--coarse-rtol", type=float, default=1e-12)
     a = ap.parse_args()
     if a.warmup < 3:
         a.warmup = 3
@@ -275,16 +278,20 @@ def main():
 
     mixed = None
     if not a.no_mixed:
-        ms_solver = sem.Solver(mesh, P, eta_nodal=eta, levels=levels_for(P), precision="mixed_fp32")
+        ms_solver = sem.Solver(mesh, P, eta_nodal=eta, levels=levels_for(P), precision="mixed_fp32", outer="pdc",
+                               inner_imax=a.inner_imax, inner_rtol=a.inner_rtol, coarse_rtol=a.coarse_rtol)
         phi_m = torch.empty(N, dtype=torch.float64, device="cuda")
         ms_m, st_m = timed(ms_solver, a.steps, a.warmup, phi_m)
         ms_m = max_over_ranks(ms_m)
         err = float(np.abs(phi_m.cpu().numpy() - phi64).max() / np.abs(phi64).max())
         mixed = {"value": dof * a.steps * world / (ms_m / 1000.0), "unit": UNIT,
-                 "ms_per_step": ms_m / a.steps, "iters": st_m[-1]["iters"],
+                 "ms_per_step": ms_m / a.steps, "outer_iters": st_m[-1]["iters"],
+                 "inner_iters": st_m[-1]["inner_iters"], "res_final_rel": st_m[-1]["res_final"] / st_m[-1]["fnorm"],
                  "speedup_vs_fp64": (dof * a.steps * world / (ms_m / 1000.0)) / value,
-                 "max_rel_diff_vs_fp64_solution": err, "outer": "PCG (FP64 residual)",
-                 "inner": "FP32 V-cycle, FP64 coarse CG"}
+                 "max_rel_diff_vs_fp64_solution": err,
+                 "outer": "FP64 defect correction (Algorithm 2) with FP64 residual",
+                 "inner": f"FP32 PCG to {a.inner_rtol:g} (<= {a.inner_imax} its) preconditioned by the FP32 V-cycle; "
+                          f"FP64 coarse CG to {a.coarse_rtol:g}"}
         ms_solver.close()
 
     if rank == 0:

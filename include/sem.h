@@ -100,6 +100,12 @@ typedef struct {
     double coarse_rtol;
     int coarse_imax;
     int profile;                /* 1: time every operator apply with CUDA events (sem_stats.apply_ms) */
+    int inner_imax;             /* MIXED_FP32 only: 0 = one FP32 V-cycle per outer iteration; > 0 = FP32 PCG
+                                   (FP32 V-cycle preconditioner) to inner_rtol, at most inner_imax iterations */
+    double inner_rtol;
+    int debug_barrier_extra;    /* testing only (default 0): > 0 makes every grid barrier of the persistent
+                                   coarse CG wait for arrivals that never come, so each wait runs into its
+                                   1 s limit and the call returns SEM_TIMEOUT with the context intact */
 } sem_options;
 
 typedef struct {
@@ -115,6 +121,7 @@ typedef struct {
     double apply_ms;            /* summed time of finest-level apply kernels (profile = 1) */
     long long apply_launches;   /* finest-level apply kernel launches (profile = 1) */
     long long kernel_launches;  /* kernels of this library launched by the call */
+    long long inner_iters;      /* FP32 inner PCG iterations (MIXED_FP32 with inner_imax > 0) */
 } sem_stats;
 
 typedef struct sem_handle sem_handle;
@@ -122,7 +129,8 @@ typedef struct sem_handle sem_handle;
 /* Defaults for finest order P: PCG, FP64, nu1 = nu2 = 1, k_cheb = 3,
  * cheb_lo = 0.1, cheb_hi = 1.1, power_its = 20, levels P -> ... -> 1 from the
  * table {6:6,3,1; 5:5,3,1; 4:4,2,1; 3:3,2,1; 2:2,1; 1:1}, rtol 1e-8, atol 0,
- * imax 200, gmres_m 30, coarse_rtol 1e-12, coarse_imax 5000. */
+ * imax 200, gmres_m 30, coarse_rtol 1e-12, coarse_imax 5000, inner_imax 0,
+ * inner_rtol 1e-4. */
 void sem_default_options(sem_options* opts, int P);
 
 /* Canonical order-p 2D node coordinates of the triangle mesh in `mesh`

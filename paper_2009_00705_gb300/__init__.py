@@ -39,14 +39,16 @@ class SemOptions(Structure):
     _fields_ = [("outer", c_int), ("precision", c_int), ("nu1", c_int), ("nu2", c_int), ("k_cheb", c_int),
                 ("cheb_lo", c_double), ("cheb_hi", c_double), ("power_its", c_int), ("nlevels", c_int),
                 ("level_p", c_int * SEM_MAX_LEVELS), ("rtol", c_double), ("atol", c_double), ("imax", c_int),
-                ("gmres_m", c_int), ("coarse_rtol", c_double), ("coarse_imax", c_int), ("profile", c_int)]
+                ("gmres_m", c_int), ("coarse_rtol", c_double), ("coarse_imax", c_int), ("profile", c_int),
+                ("inner_imax", c_int), ("inner_rtol", c_double), ("debug_barrier_extra", c_int)]
 
 
 class SemStats(Structure):
     _fields_ = [("status", c_int), ("iters", c_int), ("fnorm", c_double), ("res0", c_double),
                 ("res_final", c_double), ("q_mean", c_double), ("fine_applies", c_longlong),
                 ("vcycles", c_longlong), ("coarse_iters_max", c_int), ("ms", c_double),
-                ("apply_ms", c_double), ("apply_launches", c_longlong), ("kernel_launches", c_longlong)]
+                ("apply_ms", c_double), ("apply_launches", c_longlong), ("kernel_launches", c_longlong),
+                ("inner_iters", c_longlong)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

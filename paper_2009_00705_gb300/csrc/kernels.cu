@@ -11,6 +11,7 @@
 //    the FP64 reductions of the Krylov iterations (Algorithms 2, 3).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "sem_internal.hpp"
@@ -155,6 +156,211 @@ __global__ void __launch_bounds__(128) k_apply(int E, const int* __restrict__ ma
     }
 }
 
+// ------------------------------------------------------------------ prism apply, register-tiled
+// Same contraction as k_apply for prisms, organised for throughput: a CTA takes
+// EB elements at a time; in the triangle stage one thread owns a quadrature
+// point qt of one element and keeps the values at all QZ vertical points in
+// registers, and in the transposed stage one thread owns a triangle node n and
+// keeps all QZ partial sums, so the transposed vertical stage and the
+// direct-stiffness summation follow without another pass through shared memory.
+template <int P, typename T>
+struct PrismTile {
+    static constexpr int NT = (P + 1) * (P + 2) / 2, NZ = P + 1, QT = (P + 1) * (P + 1), QZ = P + 1;
+    static constexpr int Np = NT * NZ, Nq = QT * QZ;
+    static constexpr int VEC = 16 / sizeof(T);                  // elements per 16-byte load
+    static constexpr int QZP = (QZ + VEC - 1) / VEC * VEC;      // padded row length
+    // elements per CTA pass: fewer in FP64 (shared memory), more at low order (small elements)
+    static constexpr int EB = (sizeof(T) == 8 ? 4 : 8) * (P <= 2 ? 4 : (P == 3 ? 2 : 1));
+    static constexpr int THR_RAW = ((EB * NT + 31) / 32) * 32;
+    static constexpr int NTHR = THR_RAW < 64 ? 64 : (THR_RAW > 256 ? 256 : THR_RAW);
+    static constexpr bool TRANSPOSED = (sizeof(T) == 4);       // conflict-free copies for FP32 only
+    __host__ __device__ static constexpr int round4(int v) { return (v + 3) / 4 * 4; }
+    static constexpr int REF = round4(3 * QT * NT) + (TRANSPOSED ? round4(3 * QT * NT) : 0) + round4(2 * QZ * NZ);
+    static constexpr int WORK = round4(Np) + 2 * round4(NT * QZP) + 3 * round4(QT * QZP);
+    static constexpr size_t SMEM = sizeof(T) * (REF + (size_t)EB * WORK);
+};
+
+template <typename T, int N, int NP>
+__device__ __forceinline__ void load_row(const T* __restrict__ src, T (&out)[N]) {
+    static_assert(NP >= N, "row padding");
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int c = 0; c < NP / 4; ++c) {
+            const float4 v = reinterpret_cast<const float4*>(src)[c];
+            if (4 * c + 0 < N) out[4 * c + 0] = v.x;
+            if (4 * c + 1 < N) out[4 * c + 1] = v.y;
+            if (4 * c + 2 < N) out[4 * c + 2] = v.z;
+            if (4 * c + 3 < N) out[4 * c + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < NP / 2; ++c) {
+            const double2 v = reinterpret_cast<const double2*>(src)[c];
+            if (2 * c + 0 < N) out[2 * c + 0] = v.x;
+            if (2 * c + 1 < N) out[2 * c + 1] = v.y;
+        }
+    }
+}
+
+template <int P, typename T, bool LIFT>
+__global__ void __launch_bounds__(PrismTile<P, T>::NTHR)
+    k_apply_prism(int E, const int* __restrict__ map, const T* __restrict__ G, const T* __restrict__ refm,
+                  const T* __restrict__ x, T* __restrict__ y, const int* __restrict__ skip) {
+    using D = PrismTile<P, T>;
+    constexpr int NT = D::NT, NZ = D::NZ, QT = D::QT, QZ = D::QZ, Np = D::Np, Nq = D::Nq, QZP = D::QZP, EB = D::EB;
+    if (skip != nullptr && *skip) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    // reference matrices: [Bt | Dr | Ds] as [QT][NT]; (FP32) [BtT | DrT | DsT] as [NT][QT]; [Bz | Dz] as [QZ][NZ]
+    T* sB = sm;
+    T* sBT = sm + D::round4(3 * QT * NT);
+    T* sZ = sBT + (D::TRANSPOSED ? D::round4(3 * QT * NT) : 0);
+    for (int i = threadIdx.x; i < 3 * QT * NT; i += blockDim.x) sB[i] = refm[i];
+    if (D::TRANSPOSED)
+        for (int i = threadIdx.x; i < 3 * QT * NT; i += blockDim.x) sBT[i] = refm[3 * QT * NT + i];
+    for (int i = threadIdx.x; i < 2 * QZ * NZ; i += blockDim.x) sZ[i] = refm[6 * QT * NT + i];
+    T* work = sm + D::REF;
+    const T* sBt = sB;
+    const T* sDr = sB + QT * NT;
+    const T* sDs = sB + 2 * QT * NT;
+    const T* sBz = sZ;
+    const T* sDz = sZ + QZ * NZ;
+    __syncthreads();
+    for (int e0 = blockIdx.x * EB; e0 < E; e0 += gridDim.x * EB) {
+        const int nb = min(EB, E - e0);
+        // gather
+        for (int i = threadIdx.x; i < nb * Np; i += blockDim.x) {
+            const int b = i / Np, l = i - b * Np;
+            const int m = map[(size_t)(e0 + b) * Np + l];
+            work[b * D::WORK + l] = (m >= 0) ? x[m] : (LIFT ? x[-m - 1] : T(0));
+        }
+        __syncthreads();
+        // vertical stage: U[n][qz], W[n][qz] (values / t-derivatives at the vertical Gauss points)
+        for (int i = threadIdx.x; i < nb * NT; i += blockDim.x) {
+            const int b = i / NT, n = i - b * NT;
+            T* wb = work + b * D::WORK;
+            T xk[NZ];
+#pragma unroll
+            for (int k = 0; k < NZ; ++k) xk[k] = wb[k * NT + n];
+            T* U = wb + D::round4(Np) + n * QZP;
+            T* W = wb + D::round4(Np) + D::round4(NT * QZP) + n * QZP;
+#pragma unroll
+            for (int qz = 0; qz < QZ; ++qz) {
+                T u = 0, w = 0;
+#pragma unroll
+                for (int k = 0; k < NZ; ++k) {
+                    u += sBz[qz * NZ + k] * xk[k];
+                    w += sDz[qz * NZ + k] * xk[k];
+                }
+                U[qz] = u;
+                W[qz] = w;
+            }
+        }
+        __syncthreads();
+        // triangle stage + geometric factors: thread (b, qt), all qz in registers
+        for (int i = threadIdx.x; i < nb * QT; i += blockDim.x) {
+            const int b = i / QT, qt = i - b * QT;
+            T* wb = work + b * D::WORK;
+            const T* U = wb + D::round4(Np);
+            const T* W = U + D::round4(NT * QZP);
+            T ur[QZ], us[QZ], ut[QZ];
+#pragma unroll
+            for (int qz = 0; qz < QZ; ++qz) ur[qz] = us[qz] = ut[qz] = T(0);
+#pragma unroll 2
+            for (int n = 0; n < NT; ++n) {
+                T dr, ds, bt;
+                if (D::TRANSPOSED) {
+                    dr = sBT[QT * NT + n * QT + qt];
+                    ds = sBT[2 * QT * NT + n * QT + qt];
+                    bt = sBT[n * QT + qt];
+                } else {
+                    dr = sDr[qt * NT + n];
+                    ds = sDs[qt * NT + n];
+                    bt = sBt[qt * NT + n];
+                }
+                T uv[QZ], wv[QZ];
+                load_row<T, QZ, QZP>(U + n * QZP, uv);
+                load_row<T, QZ, QZP>(W + n * QZP, wv);
+#pragma unroll
+                for (int qz = 0; qz < QZ; ++qz) {
+                    ur[qz] += dr * uv[qz];
+                    us[qz] += ds * uv[qz];
+                    ut[qz] += bt * wv[qz];
+                }
+            }
+            const T* Ge = G + (size_t)(e0 + b) * 6 * Nq;
+            T* vr = wb + D::round4(Np) + 2 * D::round4(NT * QZP) + qt * QZP;
+            T* vs = vr + D::round4(QT * QZP);
+            T* vt = vs + D::round4(QT * QZP);
+#pragma unroll
+            for (int qz = 0; qz < QZ; ++qz) {
+                const int q = qz * QT + qt;
+                const T g0 = Ge[q], g1 = Ge[Nq + q], g2 = Ge[2 * Nq + q];
+                const T g3 = Ge[3 * Nq + q], g4 = Ge[4 * Nq + q], g5 = Ge[5 * Nq + q];
+                vr[qz] = g0 * ur[qz] + g1 * us[qz] + g2 * ut[qz];
+                vs[qz] = g1 * ur[qz] + g3 * us[qz] + g4 * ut[qz];
+                vt[qz] = g2 * ur[qz] + g4 * us[qz] + g5 * ut[qz];
+            }
+        }
+        __syncthreads();
+        // transposed triangle stage (thread (b, n), all qz), transposed vertical stage, summation
+        for (int i = threadIdx.x; i < nb * NT; i += blockDim.x) {
+            const int b = i / NT, n = i - b * NT;
+            const T* wb = work + b * D::WORK;
+            const T* vr = wb + D::round4(Np) + 2 * D::round4(NT * QZP);
+            const T* vs = vr + D::round4(QT * QZP);
+            const T* vt = vs + D::round4(QT * QZP);
+            T xr[QZ], xt[QZ];
+#pragma unroll
+            for (int qz = 0; qz < QZ; ++qz) xr[qz] = xt[qz] = T(0);
+#pragma unroll 2
+            for (int qt = 0; qt < QT; ++qt) {
+                const T dr = sDr[qt * NT + n], ds = sDs[qt * NT + n], bt = sBt[qt * NT + n];
+                T a[QZ], c[QZ], d[QZ];
+                load_row<T, QZ, QZP>(vr + qt * QZP, a);
+                load_row<T, QZ, QZP>(vs + qt * QZP, c);
+                load_row<T, QZ, QZP>(vt + qt * QZP, d);
+#pragma unroll
+                for (int qz = 0; qz < QZ; ++qz) {
+                    xr[qz] += dr * a[qz] + ds * c[qz];
+                    xt[qz] += bt * d[qz];
+                }
+            }
+            const int* me = map + (size_t)(e0 + b) * Np;
+#pragma unroll
+            for (int k = 0; k < NZ; ++k) {
+                T s = 0;
+#pragma unroll
+                for (int qz = 0; qz < QZ; ++qz) s += sBz[qz * NZ + k] * xr[qz] + sDz[qz * NZ + k] * xt[qz];
+                const int m = me[k * NT + n];
+                if (m >= 0) atomicAdd(&y[m], s);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int P, typename T, bool LIFT>
+cudaError_t apply_prism_impl(const Level& L, const T* refm, const T* G, const T* x, T* y, const int* skip,
+                             cudaStream_t s) {
+    using D = PrismTile<P, T>;
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaError_t err = cudaFuncSetAttribute(k_apply_prism<P, T, LIFT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)D::SMEM);
+        if (err != cudaSuccess) return err;
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_prism<P, T, LIFT>, D::NTHR, D::SMEM);
+        if (err != cudaSuccess) return err;
+        if (per_sm < 1) per_sm = 1;
+    }
+    const int batches = (L.E + D::EB - 1) / D::EB;
+    int grid = kSMs * per_sm;
+    if (grid > batches) grid = batches;
+    if (grid < 1) return cudaSuccess;
+    k_apply_prism<P, T, LIFT><<<grid, D::NTHR, D::SMEM, s>>>(L.E, L.map, G, refm, x, y, skip);
+    return cudaGetLastError();
+}
+
 template <int P, bool PRISM, typename T, bool LIFT>
 cudaError_t apply_impl(const Level& L, const T* refm, const T* G, const T* x, T* y, const int* skip,
                        cudaStream_t s) {
@@ -183,7 +389,7 @@ cudaError_t apply_dispatch(const Level& L, const T* refm, const T* G, const T* x
     const bool prism = (L.dim == 3);
 #define SEM_CASE(PP)                                                                     \
     case PP:                                                                             \
-        return prism ? apply_impl<PP, true, T, LIFT>(L, refm, G, x, y, skip, s)          \
+        return prism ? apply_prism_impl<PP, T, LIFT>(L, refm, G, x, y, skip, s)          \
                      : apply_impl<PP, false, T, LIFT>(L, refm, G, x, y, skip, s);
     switch (L.p) {
         SEM_CASE(1)
@@ -479,6 +685,46 @@ __global__ void k_pcg_dir(long long n, const double* num, const double* den, con
         p[i] = z[i] + beta * p[i];
 }
 
+// FP32 data, FP64 accumulation (inner PCG of the mixed-precision path)
+__global__ void k_dot32(long long n, const float* __restrict__ a, const float* __restrict__ b, double* part,
+                        unsigned* counter, double* out) {
+    double s = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        s += (double)a[i] * (double)b[i];
+    double v[1] = {block_sum(s)};
+    if (partials_done<1>(v, part, counter)) {
+        double r[1];
+        final_sums<1>(part, r);
+        if (threadIdx.x == 0) { out[0] = r[0]; *counter = 0; }
+    }
+}
+
+__global__ void k_pcg_update32(long long n, const double* num, const double* den, const float* __restrict__ p,
+                               const float* __restrict__ q, float* __restrict__ u, float* __restrict__ r,
+                               double* part, unsigned* counter, double* out) {
+    const float alpha = (float)((*num) / (*den));
+    double s = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        u[i] += alpha * p[i];
+        const float v = r[i] - alpha * q[i];
+        r[i] = v;
+        s += (double)v * v;
+    }
+    double v[1] = {block_sum(s)};
+    if (partials_done<1>(v, part, counter)) {
+        double rr[1];
+        final_sums<1>(part, rr);
+        if (threadIdx.x == 0) { out[0] = rr[0]; *counter = 0; }
+    }
+}
+
+__global__ void k_pcg_dir32(long long n, const double* num, const double* den, const float* __restrict__ z,
+                            float* __restrict__ p) {
+    const float beta = (float)((*num) / (*den));
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = z[i] + beta * p[i];
+}
+
 // ------------------------------------------------------------------ coarse CG (FP64)
 // Jacobi-preconditioned CG with every scalar on the device; all kernels are
 // predicated on flags[F_CG_DONE] so that the host may launch several iterations
@@ -563,6 +809,186 @@ __global__ void k_cg_dir(long long n, const double* __restrict__ z, double* __re
     const double beta = scal[S_CG_BETA];
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         p[i] = z[i] + beta * p[i];
+}
+
+// ------------------------------------------------------------------ persistent coarse CG
+// The whole Jacobi-preconditioned CG of the order-1 coarse level in one
+// cooperative launch (all CTAs co-resident).  Phases are separated by a grid
+// barrier whose waits are bounded: a CTA that waits longer than kBarrierSpins
+// polls sets bar[2] (timeout) and every CTA leaves at the next check, so the
+// host reads SEM_TIMEOUT instead of a hung GPU.  Reductions are deterministic:
+// block partial sums, then every CTA sums the partials in the same order.
+constexpr unsigned long long kBarrierTimeoutNs = 1000000000ULL;   // 1 s per barrier wait
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid barrier for co-resident CTAs.  bar[0]: arrivals, bar[1]: generation,
+// bar[2]: timeout flag.  `expected` is the number of arrivals that releases the
+// barrier (gridDim.x in normal use).
+__device__ bool grid_barrier(unsigned* bar, unsigned expected) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = bar + 1;
+        volatile unsigned* verr = bar + 2;
+        const unsigned gen = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(bar, 1u);
+        if (arrived == expected - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (*vgen == gen && *verr == 0u) {
+                if (global_ns() - t0 > kBarrierTimeoutNs) {
+                    atomicExch(bar + 2, 1u);
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ((volatile unsigned*)bar)[2] == 0u;
+}
+
+// sum of part[0..gridDim) in a fixed order; every CTA gets the same value
+__device__ double grid_total(const double* part) {
+    __shared__ double tot;
+    if (threadIdx.x < 32) {
+        double v = 0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) v += ((volatile const double*)part)[b];
+        v = warp_sum(v);
+        if (threadIdx.x == 0) tot = v;
+    }
+    __syncthreads();
+    const double t = tot;
+    __syncthreads();
+    return t;
+}
+
+// One thread per element: A_e x_e with the full reference gradients gref[DIM][NQ][NP].
+template <int DIM, int NP, int NQ>
+__device__ __forceinline__ void element_apply(int e, const int* __restrict__ map, const double* __restrict__ G,
+                                              const double* __restrict__ gref, const double* __restrict__ x,
+                                              double* __restrict__ y) {
+    constexpr int NC = DIM == 3 ? 6 : 3;
+    double xe[NP], ye[NP];
+    int m[NP];
+#pragma unroll
+    for (int l = 0; l < NP; ++l) {
+        m[l] = map[(size_t)e * NP + l];
+        xe[l] = m[l] >= 0 ? __ldcg(x + m[l]) : 0.0;     // written by other CTAs: read through L2
+        ye[l] = 0.0;
+    }
+    const double* Ge = G + (size_t)e * NC * NQ;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        double g[DIM];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            double v = 0;
+#pragma unroll
+            for (int l = 0; l < NP; ++l) v += __ldg(gref + (a * NQ + q) * NP + l) * xe[l];
+            g[a] = v;
+        }
+        double w[DIM];
+        if (DIM == 3) {
+            const double g0 = Ge[q], g1 = Ge[NQ + q], g2 = Ge[2 * NQ + q], g3 = Ge[3 * NQ + q], g4 = Ge[4 * NQ + q],
+                         g5 = Ge[5 * NQ + q];
+            w[0] = g0 * g[0] + g1 * g[1] + g2 * g[2];
+            w[1] = g1 * g[0] + g3 * g[1] + g4 * g[2];
+            w[2] = g2 * g[0] + g4 * g[1] + g5 * g[2];
+        } else {
+            const double g0 = Ge[q], g1 = Ge[NQ + q], g2 = Ge[2 * NQ + q];
+            w[0] = g0 * g[0] + g1 * g[1];
+            w[1] = g1 * g[0] + g2 * g[1];
+        }
+#pragma unroll
+        for (int a = 0; a < DIM; ++a)
+#pragma unroll
+            for (int l = 0; l < NP; ++l) ye[l] += __ldg(gref + (a * NQ + q) * NP + l) * w[a];
+    }
+#pragma unroll
+    for (int l = 0; l < NP; ++l)
+        if (m[l] >= 0) atomicAdd(&y[m[l]], ye[l]);
+}
+
+template <int DIM, int NP, int NQ>
+__global__ void __launch_bounds__(256) k_coarse_cg(int E, long long n, const int* __restrict__ map,
+                                                   const double* __restrict__ G, const double* __restrict__ gref,
+                                                   const double* __restrict__ dinv, const double* __restrict__ b,
+                                                   double* x, double* r, double* z, double* p, double* q,
+                                                   double* part, unsigned* bar, double* scal, int* flags,
+                                                   double rtol2, int imax, unsigned extra_arrivals) {
+    const unsigned nb = gridDim.x;
+    const unsigned expected = nb + extra_arrivals;   // extra_arrivals > 0 only in the timeout test
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    double s0 = 0, s1 = 0;
+    for (long long i = tid; i < n; i += stride) {
+        const double bi = b[i], zi = dinv[i] * bi;
+        x[i] = 0;
+        r[i] = bi;
+        z[i] = zi;
+        p[i] = zi;
+        q[i] = 0;
+        s0 += bi * zi;
+        s1 += bi * bi;
+    }
+    s0 = block_sum(s0);
+    s1 = block_sum(s1);
+    if (threadIdx.x == 0) { part[blockIdx.x] = s0; part[nb + blockIdx.x] = s1; }
+    if (!grid_barrier(bar, expected)) return;
+    double rho = grid_total(part);
+    const double bb = grid_total(part + nb);
+    const double tol2 = rtol2 * bb;
+    int it = 0;
+    double rr = bb;
+    while (rr > tol2 && rr > 0.0 && it < imax) {
+        for (long long e = tid; e < E; e += stride) element_apply<DIM, NP, NQ>((int)e, map, G, gref, p, q);
+        if (!grid_barrier(bar, expected)) return;
+        double pq = 0;
+        for (long long i = tid; i < n; i += stride) pq += p[i] * __ldcg(q + i);   // q: atomics of other CTAs
+        pq = block_sum(pq);
+        if (threadIdx.x == 0) part[blockIdx.x] = pq;
+        if (!grid_barrier(bar, expected)) return;
+        const double alpha = rho / grid_total(part);
+        double t0 = 0, t1 = 0;
+        for (long long i = tid; i < n; i += stride) {
+            x[i] += alpha * p[i];
+            const double ri = r[i] - alpha * __ldcg(q + i);
+            r[i] = ri;
+            const double zi = dinv[i] * ri;
+            z[i] = zi;
+            t0 += ri * zi;
+            t1 += ri * ri;
+        }
+        t0 = block_sum(t0);
+        t1 = block_sum(t1);
+        if (threadIdx.x == 0) { part[2 * nb + blockIdx.x] = t0; part[3 * nb + blockIdx.x] = t1; }
+        if (!grid_barrier(bar, expected)) return;
+        const double rho_new = grid_total(part + 2 * nb);
+        rr = grid_total(part + 3 * nb);
+        const double beta = rho_new / rho;
+        rho = rho_new;
+        for (long long i = tid; i < n; i += stride) {
+            p[i] = z[i] + beta * p[i];
+            q[i] = 0;
+        }
+        ++it;
+        if (!grid_barrier(bar, expected)) return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        flags[F_CG_ITERS] = it;
+        flags[F_CG_DONE] = (rr <= tol2 || rr == 0.0) ? 1 : 0;
+        scal[S_CG_RR] = rr;
+    }
 }
 
 // ------------------------------------------------------------------ FGMRES helpers
@@ -797,6 +1223,20 @@ cudaError_t pcg_direction(long long n, const double* num, const double* den, con
     k_pcg_dir<<<vec_grid(n), kVecThreads, 0, s>>>(n, num, den, z, p);
     return cudaGetLastError();
 }
+cudaError_t dot32(long long n, const float* a, const float* b, Scratch& sc, double* out, cudaStream_t s) {
+    k_dot32<<<reduce_blocks(), kRedThreads, 0, s>>>(n, a, b, sc.part, sc.counter, out);
+    return cudaGetLastError();
+}
+cudaError_t pcg_update32(long long n, const double* num, const double* den, const float* p, const float* q, float* u,
+                         float* r, Scratch& sc, double* rr, cudaStream_t s) {
+    k_pcg_update32<<<reduce_blocks(), kRedThreads, 0, s>>>(n, num, den, p, q, u, r, sc.part, sc.counter, rr);
+    return cudaGetLastError();
+}
+cudaError_t pcg_direction32(long long n, const double* num, const double* den, const float* z, float* p,
+                            cudaStream_t s) {
+    k_pcg_dir32<<<vec_grid(n), kVecThreads, 0, s>>>(n, num, den, z, p);
+    return cudaGetLastError();
+}
 cudaError_t axpy64(long long n, double a, const double* x, double* y, cudaStream_t s) {
     k_axpy<<<vec_grid(n), kVecThreads, 0, s>>>(n, a, x, y);
     return cudaGetLastError();
@@ -837,6 +1277,43 @@ cudaError_t scale64(long long n, const double* w, const double* nrm2, double* v,
     k_scale<<<vec_grid(n), kVecThreads, 0, s>>>(n, w, nrm2, v);
     return cudaGetLastError();
 }
+cudaError_t coarse_cg_persistent(const Level& C, const double* gref, const double* b, double* x, double* r,
+                                 double* z, double* p, double* q, Scratch& sc, double rtol2, int imax,
+                                 unsigned extra_arrivals, cudaStream_t s) {
+    void (*kern)(int, long long, const int*, const double*, const double*, const double*, const double*, double*,
+                 double*, double*, double*, double*, double*, unsigned*, double*, int*, double, int, unsigned);
+    if (C.dim == 3 && C.Np == 6 && C.Nq == 8) kern = k_coarse_cg<3, 6, 8>;
+    else if (C.dim == 2 && C.Np == 3 && C.Nq == 4) kern = k_coarse_cg<2, 3, 4>;
+    else return cudaErrorInvalidValue;
+    int per_sm = 0;
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
+    if (err != cudaSuccess) return err;
+    if (per_sm > 2) per_sm = 2;
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    int dev = 0, sms = kSMs;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long want = (std::max<long long>(C.N, C.E) + 255) / 256;
+    int grid = (int)std::min<long long>(want, (long long)sms * per_sm);
+    if (grid < 1) grid = 1;
+    err = cudaMemsetAsync(sc.counter + 1, 0, 3 * sizeof(unsigned), s);
+    if (err != cudaSuccess) return err;
+    int E = C.E;
+    long long n = C.N;
+    const int* map = C.map;
+    const double* G = C.G;
+    const double* dinv = C.dinv;
+    double* part = sc.part;
+    unsigned* bar = sc.counter + 1;
+    double* scal = sc.scal;
+    int* flags = sc.flags;
+    void* args[] = {&E,    &n,    &map,  &G,     &gref,  &dinv,  &b,     &x,    &r,
+                    &z,    &p,    &q,    &part,  &bar,   &scal,  &flags, &rtol2, &imax, &extra_arrivals};
+    err = cudaLaunchCooperativeKernel((void*)kern, grid, 256, args, 0, s);
+    if (err != cudaSuccess) return err;
+    return cudaGetLastError();
+}
+
 cudaError_t cg_init(long long n, const double* b, const double* dinv, double* x, double* r, double* z, double* p,
                     Scratch& sc, double rtol2, cudaStream_t s) {
     k_cg_init<<<reduce_blocks(), kRedThreads, 0, s>>>(n, b, dinv, x, r, z, p, sc.part, sc.counter, sc.scal, sc.flags,

@@ -51,6 +51,7 @@ struct Level {
     // workspaces (length N)
     double *u = nullptr, *f = nullptr, *y = nullptr, *d = nullptr;
     float *u32 = nullptr, *f32 = nullptr, *y32 = nullptr, *d32 = nullptr;
+    double* gref = nullptr;                // [dim][Nq][Np] full reference gradients (coarse level)
 };
 
 struct Scratch {
@@ -77,6 +78,9 @@ struct sem_handle {
     double* Zb = nullptr;          // [m][N]
     // coarse CG (FP64) on the coarsest level
     double *cx = nullptr, *cr = nullptr, *cz = nullptr, *cp = nullptr, *cq = nullptr, *cb = nullptr;
+    // inner FP32 PCG of the mixed-precision path (finest level)
+    float *ir = nullptr, *iz = nullptr, *ip = nullptr, *iq = nullptr, *ie = nullptr;
+    long long inner_iters = 0;
     // staging buffers of laplace_solve_host
     double *st_eta = nullptr, *st_rhs = nullptr, *st_phi = nullptr;
     // host geometry copies for coordinate queries
@@ -130,6 +134,11 @@ cudaError_t pcg_update(long long n, const double* num, const double* den, const 
 cudaError_t pcg_direction(long long n, const double* num, const double* den, const double* z, double* p,
                           cudaStream_t s);
 cudaError_t axpy64(long long n, double a, const double* x, double* y, cudaStream_t s);
+cudaError_t dot32(long long n, const float* a, const float* b, Scratch& sc, double* out, cudaStream_t s);
+cudaError_t pcg_update32(long long n, const double* num, const double* den, const float* p, const float* q, float* u,
+                         float* r, Scratch& sc, double* rr, cudaStream_t s);
+cudaError_t pcg_direction32(long long n, const double* num, const double* den, const float* z, float* p,
+                            cudaStream_t s);
 cudaError_t copy_dirichlet(long long nd, const long long* idx, const double* src, double* dst, cudaStream_t s);
 cudaError_t scatter_dirichlet(long long nd, const long long* idx, const double* vals, double* dst, cudaStream_t s);
 cudaError_t zero_dirichlet(long long nd, const long long* idx, double* v, cudaStream_t s);
@@ -147,11 +156,17 @@ cudaError_t cg_pq(long long n, const double* p, const double* q, Scratch& sc, cu
 cudaError_t cg_update(long long n, const double* dinv, double* x, double* r, double* z, const double* p,
                       const double* q, Scratch& sc, cudaStream_t s);
 cudaError_t cg_direction(long long n, const double* z, double* p, Scratch& sc, cudaStream_t s);
+// whole coarse CG in one cooperative launch (order-1 coarse levels); the barrier
+// timeout flag is counter[3]
+cudaError_t coarse_cg_persistent(const Level& C, const double* gref, const double* b, double* x, double* r,
+                                 double* z, double* p, double* q, Scratch& sc, double rtol2, int imax,
+                                 unsigned extra_arrivals, cudaStream_t s);
 
 // scalar slots in Scratch::scal
 enum {
     S_RR = 0, S_PQ = 1, S_DELTA0 = 2, S_DELTA1 = 3, S_FF = 4, S_TMP = 5,
     S_CG_RHO = 8, S_CG_PQ = 9, S_CG_RR = 10, S_CG_TOL2 = 11, S_CG_RHONEW = 12, S_CG_BETA = 13,
+    S_IRR = 6, S_IPQ = 7, S_IDELTA0 = 14, S_IDELTA1 = 15,
     S_MULTI = 16                    // FGMRES dots start here (up to 64 + 1)
 };
 enum { F_CG_DONE = 0, F_CG_ITERS = 1 };

@@ -286,6 +286,26 @@ sem_status build_diagonals(sem_handle* h) {
     return SEM_OK;
 }
 
+// Full reference gradients [dim][Nq][Np] of the coarsest level (thread-per-element apply
+// inside the persistent coarse CG).
+sem_status build_coarse_gradients(sem_handle* h) {
+    Level& C = h->lv.back();
+    const RefLevel& r = C.ref;
+    std::vector<double> g((size_t)C.dim * C.Nq * C.Np);
+    for (int qz = 0; qz < C.QZ; ++qz)
+        for (int qt = 0; qt < C.QT; ++qt)
+            for (int k = 0; k < C.NZ; ++k)
+                for (int n = 0; n < C.NT; ++n) {
+                    const int q = qz * C.QT + qt, l = k * C.NT + n;
+                    const double bz = r.Bz[qz * C.NZ + k], dz = r.Dz[qz * C.NZ + k];
+                    g[(size_t)(0 * C.Nq + q) * C.Np + l] = r.Drt[qt * C.NT + n] * bz;
+                    g[(size_t)(1 * C.Nq + q) * C.Np + l] = r.Dst[qt * C.NT + n] * bz;
+                    if (C.dim == 3) g[(size_t)(2 * C.Nq + q) * C.Np + l] = r.Bt[qt * C.NT + n] * dz;
+                }
+    CK(upload(&C.gref, g));
+    return SEM_OK;
+}
+
 sem_status build_transfers(sem_handle* h) {
     for (size_t li = 0; li + 1 < h->lv.size(); ++li) {
         Level& F = h->lv[li];
@@ -316,6 +336,8 @@ sem_status build_workspace(sem_handle* h) {
         CK(dalloc(&h->Zb, (size_t)h->opts.gmres_m * N));
     }
     for (double** v : {&h->cx, &h->cr, &h->cz, &h->cp, &h->cq, &h->cb}) CK(dalloc(v, Lc.N));
+    if (h->opts.precision == SEM_PREC_MIXED_FP32 && h->opts.inner_imax > 0)
+        for (float** v : {&h->ir, &h->iz, &h->ip, &h->iq, &h->ie}) CK(dalloc(v, N));
     CK(dalloc(&h->st_eta, h->lv[0].hdir.size()));
     CK(dalloc(&h->st_rhs, N));
     CK(dalloc(&h->st_phi, N));

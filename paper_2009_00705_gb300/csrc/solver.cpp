@@ -22,6 +22,7 @@ sem_status build_level(sem_handle* h, const sem_mesh* m, int li, int p);
 sem_status build_geometry(sem_handle* h, const sem_mesh* m);
 sem_status build_diagonals(sem_handle* h);
 sem_status build_transfers(sem_handle* h);
+sem_status build_coarse_gradients(sem_handle* h);
 sem_status build_workspace(sem_handle* h);
 }  // namespace sem
 
@@ -107,26 +108,41 @@ void flush_events(sem_handle* h) {
     h->ev_used = 0;
 }
 
-// FP64 Jacobi-CG on the coarsest level: x = A_c^{-1} b to coarse_rtol.
+// FP64 Jacobi-CG on the coarsest level: x = A_c^{-1} b to coarse_rtol.  An order-1
+// coarse level runs the whole CG in one persistent cooperative launch; higher orders
+// (single-level configurations) launch one kernel per CG step, predicated on a
+// device-side done flag, and test convergence every 8 iterations.
 sem_status coarse_solve(sem_handle* h, const double* b, double* x, cudaStream_t s) {
     const Level& C = h->lv.back();
     Scratch& sc = h->sc;
     const double rt = h->opts.coarse_rtol;
-    K(cg_init(C.N, b, C.dinv, x, h->cr, h->cz, h->cp, sc, rt * rt, s));
-    int it = 0;
-    const int chunk = 8;
-    while (it < h->opts.coarse_imax) {
-        for (int k = 0; k < chunk; ++k) {
-            CKS(cudaMemsetAsync(h->cq, 0, sizeof(double) * C.N, s));
-            K(launch_apply64(C, h->cp, h->cq, false, sc.flags + F_CG_DONE, s));
-            K(cg_pq(C.N, h->cp, h->cq, sc, s));
-            K(cg_update(C.N, C.dinv, x, h->cr, h->cz, h->cp, h->cq, sc, s));
-            K(cg_direction(C.N, h->cz, h->cp, sc, s));
-        }
-        it += chunk;
+    if (C.p == 1) {
+        K(coarse_cg_persistent(C, C.gref, b, x, h->cr, h->cz, h->cp, h->cq, sc, rt * rt, h->opts.coarse_imax,
+                               (unsigned)h->opts.debug_barrier_extra, s));
         CKS(cudaMemcpyAsync(sc.hflags, sc.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CKS(cudaMemcpyAsync(sc.hflags + 4, sc.counter + 3, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         CKS(cudaStreamSynchronize(s));
-        if (sc.hflags[F_CG_DONE]) break;
+        if (sc.hflags[4] != 0) {
+            set_error("coarse CG: a grid barrier wait ran out (device timeout)");
+            return SEM_TIMEOUT;
+        }
+    } else {
+        K(cg_init(C.N, b, C.dinv, x, h->cr, h->cz, h->cp, sc, rt * rt, s));
+        int it = 0;
+        const int chunk = 8;
+        while (it < h->opts.coarse_imax) {
+            for (int k = 0; k < chunk; ++k) {
+                CKS(cudaMemsetAsync(h->cq, 0, sizeof(double) * C.N, s));
+                K(launch_apply64(C, h->cp, h->cq, false, sc.flags + F_CG_DONE, s));
+                K(cg_pq(C.N, h->cp, h->cq, sc, s));
+                K(cg_update(C.N, C.dinv, x, h->cr, h->cz, h->cp, h->cq, sc, s));
+                K(cg_direction(C.N, h->cz, h->cp, sc, s));
+            }
+            it += chunk;
+            CKS(cudaMemcpyAsync(sc.hflags, sc.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+            CKS(cudaStreamSynchronize(s));
+            if (sc.hflags[F_CG_DONE]) break;
+        }
     }
     const int used = sc.hflags[F_CG_ITERS];
     h->coarse_iters_max = std::max(h->coarse_iters_max, used);
@@ -241,9 +257,46 @@ sem_status vcycle32(sem_handle* h, const float* f0, float* u0, cudaStream_t s) {
     return SEM_OK;
 }
 
+sem_status read_scalars(sem_handle* h, int first, int count, cudaStream_t s);
+
+// Inner FP32 PCG on A e = r (FP32 V-cycle preconditioner, FP64-accumulated dots) to
+// inner_rtol; e is returned in FP64.  r has zero Dirichlet entries.
+sem_status inner_pcg32(sem_handle* h, const double* r, double* e, cudaStream_t s) {
+    const Level& L = h->lv[0];
+    const long long N = L.N;
+    Scratch& sc = h->sc;
+    K(to_f32(N, r, h->ir, s));
+    CKS(cudaMemsetAsync(h->ie, 0, sizeof(float) * N, s));
+    K(dot32(N, h->ir, h->ir, sc, sc.scal + S_IRR, s));
+    CKST(read_scalars(h, S_IRR, 1, s));
+    const double tol2 = h->opts.inner_rtol * h->opts.inner_rtol * sc.hpinned[S_IRR];
+    if (sc.hpinned[S_IRR] > 0.0) {
+        CKST(vcycle32(h, h->ir, h->iz, s));
+        CKS(cudaMemcpyAsync(h->ip, h->iz, sizeof(float) * N, cudaMemcpyDeviceToDevice, s));
+        int cur = S_IDELTA0, nxt = S_IDELTA1;
+        K(dot32(N, h->iz, h->ir, sc, sc.scal + cur, s));
+        for (int it = 0; it < h->opts.inner_imax; ++it) {
+            CKST(apply_level32(h, 0, h->ip, h->iq, s));
+            K(dot32(N, h->ip, h->iq, sc, sc.scal + S_IPQ, s));
+            K(pcg_update32(N, sc.scal + cur, sc.scal + S_IPQ, h->ip, h->iq, h->ie, h->ir, sc, sc.scal + S_IRR, s));
+            h->inner_iters += 1;
+            CKST(read_scalars(h, S_IRR, 2, s));
+            if (!(sc.hpinned[S_IPQ] > 0.0) || !std::isfinite(sc.hpinned[S_IRR])) break;
+            if (sc.hpinned[S_IRR] <= tol2) break;
+            CKST(vcycle32(h, h->ir, h->iz, s));
+            K(dot32(N, h->iz, h->ir, sc, sc.scal + nxt, s));
+            K(pcg_direction32(N, sc.scal + nxt, sc.scal + cur, h->iz, h->ip, s));
+            std::swap(cur, nxt);
+        }
+    }
+    K(to_f64(N, h->ie, e, s));
+    return SEM_OK;
+}
+
 // z = M^{-1} r on the finest level in the configured precision (r has zero Dirichlet entries).
 sem_status precondition(sem_handle* h, const double* r, double* z, cudaStream_t s) {
     if (h->opts.precision == SEM_PREC_MIXED_FP32) {
+        if (h->opts.inner_imax > 0) return inner_pcg32(h, r, z, s);
         Level& L = h->lv[0];
         K(to_f32(L.N, r, L.f32, s));
         CKST(vcycle32(h, L.f32, L.u32, s));
@@ -286,7 +339,7 @@ sem_status estimate_lambda(sem_handle* h, int li) {
 }
 
 void free_level(Level& L) {
-    void* ptrs[] = {L.map, L.G, L.G32, L.dinv, L.dinv32, L.dir, L.ref64.m, L.ref32.m, L.I64, L.I32,
+    void* ptrs[] = {L.map, L.G, L.G32, L.dinv, L.dinv32, L.dir, L.ref64.m, L.ref32.m, L.I64, L.I32, L.gref,
                     L.owner, L.wmult, L.wmult32, L.u, L.f, L.y, L.d, L.u32, L.f32, L.y32, L.d32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -330,6 +383,10 @@ sem_status check_options(const sem_options& o, int P) {
     if (o.outer < 0 || o.outer > 2 || o.precision < 0 || o.precision > 1) { set_error("outer/precision"); return SEM_EINVAL; }
     if (o.outer == SEM_OUTER_FGMRES && (o.gmres_m < 1 || o.gmres_m > 64)) { set_error("gmres_m in 1..64"); return SEM_EINVAL; }
     if (o.imax < 0 || o.coarse_imax < 1 || !(o.coarse_rtol > 0)) { set_error("iteration limits"); return SEM_EINVAL; }
+    if (o.inner_imax < 0 || (o.inner_imax > 0 && !(o.inner_rtol > 0 && o.inner_rtol < 1))) {
+        set_error("inner_imax >= 0 and 0 < inner_rtol < 1");
+        return SEM_EINVAL;
+    }
     return SEM_OK;
 }
 
@@ -512,6 +569,9 @@ void sem_default_options(sem_options* o, int P) {
     o->coarse_rtol = 1e-12;
     o->coarse_imax = 5000;
     o->profile = 0;
+    o->inner_imax = 0;
+    o->inner_rtol = 1e-4;
+    o->debug_barrier_extra = 0;
 }
 
 sem_status sem_mesh_nodes2d(const sem_mesh* m, int p, long long* n2, double* xy) {
@@ -557,6 +617,7 @@ sem_status sem_setup(const sem_mesh* m, int P, const sem_options* opts, sem_hand
     if (st == SEM_OK) st = build_geometry(h, m);
     if (st == SEM_OK) st = build_diagonals(h);
     if (st == SEM_OK) st = build_transfers(h);
+    if (st == SEM_OK) st = build_coarse_gradients(h);
     if (st == SEM_OK) st = build_workspace(h);
     for (int li = 0; li + 1 < o.nlevels && st == SEM_OK; ++li) st = estimate_lambda(h, li);
     if (st == SEM_OK) {
@@ -576,7 +637,8 @@ void sem_destroy(sem_handle* h) {
     if (!h) return;
     for (Level& L : h->lv) free_level(L);
     void* ptrs[] = {h->sc.part, h->sc.counter, h->sc.scal, h->sc.flags, h->r, h->z, h->p, h->q, h->x, h->fr,
-                    h->V, h->Zb, h->cx, h->cr, h->cz, h->cp, h->cq, h->cb, h->st_eta, h->st_rhs, h->st_phi};
+                    h->V, h->Zb, h->cx, h->cr, h->cz, h->cp, h->cq, h->cb, h->st_eta, h->st_rhs, h->st_phi,
+                    h->ir, h->iz, h->ip, h->iq, h->ie};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->sc.hpinned) cudaFreeHost(h->sc.hpinned);
@@ -698,6 +760,7 @@ sem_status laplace_solve(sem_handle* h, const double* rhs, const double* eta, do
     h->apply_ms = 0;
     h->apply_launches = 0;
     h->launches = 0;
+    h->inner_iters = 0;
     h->ev_used = 0;
     cudaEvent_t e0, e1;
     CKS(cudaEventCreate(&e0));
@@ -745,6 +808,7 @@ sem_status laplace_solve(sem_handle* h, const double* rhs, const double* eta, do
     st.apply_ms = h->apply_ms;
     st.apply_launches = h->apply_launches;
     st.kernel_launches = h->launches;
+    st.inner_iters = h->inner_iters;
     st.q_mean = (st.iters > 0 && st.res0 > 0) ? std::pow(st.res_final / st.res0, 1.0 / st.iters) : 0.0;
     if (stats) *stats = st;
     return ret;
