@@ -46,7 +46,7 @@ TRAFFIC_SRC_SHA = None
 def workload_name(n, nl, P):
     return (f"3D sigma-prism box 2pi x 2pi x 1: {n}x{n} quads -> {2 * n * n} triangles x {nl} layers = "
             f"{2 * n * n * nl} prisms, P={P}, eta=0.1 sin(x)cos(y); PCG + p-multigrid V-cycle "
-            f"(Chebyshev-Jacobi k=3, nu=1+1, FP64 coarse CG at order 1) to rtol 1e-8")
+            f"(Chebyshev-Jacobi k=4 on [0.05b, b], nu=1+1, FP64 coarse CG at order 1 to 1e-3) to rtol 1e-8")
 
 
 def levels_for(P):
@@ -130,8 +130,8 @@ def cpu_baseline_obj(P, nl, sample_n=8, solves=4):
     o = oracle_run(sample_n, nl, P, solves)
     return {"value": o["dof_per_s"], "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{solves} oracle PCG-pMG solves to rtol 1e-8 on the {sample_n}x{sample_n}x{nl} P={P} "
-                      f"box ({o['dof_free']} free DOF, same eta/levels/smoother; assembled CSR + SciPy, "
-                      f"single thread), {o['seconds']:.1f} s; iterations {o['iters']}",
+                      f"box ({o['dof_free']} free DOF, same eta/levels/smoother, exact coarse solve; assembled "
+                      f"CSR + SciPy, single thread), {o['seconds']:.1f} s; iterations {o['iters']}",
             "solves_per_s_sample": o["solves_per_s"]}
 
 
@@ -169,7 +169,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--inner-imax", type=int, default=40)
     ap.add_argument("--inner-rtol", type=float, default=1e-4)
-    ap.add_argument("--coarse-rtol", type=float, default=1e-12)
+    ap.add_argument("--coarse-rtol", type=float, default=1e-3)
     a = ap.parse_args()
     if a.warmup < 3:
         a.warmup = 3

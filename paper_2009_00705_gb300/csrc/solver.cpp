@@ -552,8 +552,8 @@ void sem_default_options(sem_options* o, int P) {
     o->precision = SEM_PREC_FP64;
     o->nu1 = 1;
     o->nu2 = 1;
-    o->k_cheb = 3;
-    o->cheb_lo = 0.1;
+    o->k_cheb = 4;
+    o->cheb_lo = 0.05;
     o->cheb_hi = 1.1;
     o->power_its = 20;
     static const int table[7][3] = {{1, 0, 0}, {1, 0, 0}, {2, 1, 0}, {3, 2, 1}, {4, 2, 1}, {5, 3, 1}, {6, 3, 1}};
@@ -566,7 +566,7 @@ void sem_default_options(sem_options* o, int P) {
     o->atol = 0.0;
     o->imax = 200;
     o->gmres_m = 30;
-    o->coarse_rtol = 1e-12;
+    o->coarse_rtol = 1e-3;
     o->coarse_imax = 5000;
     o->profile = 0;
     o->inner_imax = 0;

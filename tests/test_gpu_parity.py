@@ -45,7 +45,7 @@ def make(sem, name, **opts):
     mesh_fn, levels = CASES[name]
     mesh = mesh_fn()
     prob = Problem(mesh, levels)
-    o = dict(levels=levels, coarse_rtol=1e-14, cheb_lo=0.1, cheb_hi=1.1)
+    o = dict(levels=levels, coarse_rtol=1e-14, cheb_lo=0.1, cheb_hi=1.1, k_cheb=3)
     o.update(opts)
     solver = sem.Solver(mesh, levels[0], eta_nodal=prob.eta_nodal, **o)
     return mesh, prob, solver
