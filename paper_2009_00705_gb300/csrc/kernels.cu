@@ -533,51 +533,96 @@ __global__ void k_diag(int E, int dim, int NT, int NZ, int QT, int QZ, const int
 }
 
 // ------------------------------------------------------------------ transfers
+// The element prolongation is a tensor product, I = Bt (x) Bz with Bt [NTf][NTc]
+// the coarse triangle basis at the fine triangle nodes and Bz [NZf][NZc] the
+// coarse 1D basis at the fine GLL nodes (Bz = [1] for triangles), so both
+// transfers are applied in two sum-factorised stages.  A CTA handles kTrEB
+// elements per pass.
+constexpr int kTrEB = 8;
+
 // Restriction (R = P^T): fine residual r = f - y weighted by 1/multiplicity,
-// element-wise I^T, summed into the coarse right-hand side (free coarse rows).
+// T[kf][nc] = sum_nf Bt[nf][nc] r[kf][nf], coarse[kc][nc] = sum_kf Bz[kf][kc] T[kf][nc],
+// summed into the coarse right-hand side (free coarse rows).
 template <typename T>
-__global__ void k_restrict(int E, int Npf, int Npc, const int* __restrict__ mapf, const int* __restrict__ mapc,
-                           const T* __restrict__ wmult, const T* __restrict__ I, const T* __restrict__ f,
-                           const T* __restrict__ y, T* __restrict__ fc) {
+__global__ void k_restrict(int E, int NTf, int NZf, int NTc, int NZc, const int* __restrict__ mapf,
+                           const int* __restrict__ mapc, const T* __restrict__ wmult, const T* __restrict__ Bt,
+                           const T* __restrict__ Bz, const T* __restrict__ f, const T* __restrict__ y,
+                           T* __restrict__ fc) {
     extern __shared__ __align__(16) unsigned char smr[];
-    T* re = reinterpret_cast<T*>(smr);
-    for (int e = blockIdx.x; e < E; e += gridDim.x) {
-        for (int l = threadIdx.x; l < Npf; l += blockDim.x) {
-            const int m = mapf[(size_t)e * Npf + l];
-            re[l] = (m >= 0) ? wmult[m] * (f[m] - y[m]) : T(0);
+    const int Npf = NTf * NZf, Npc = NTc * NZc;
+    T* sBt = reinterpret_cast<T*>(smr);
+    T* sBz = sBt + NTf * NTc;
+    T* re = sBz + NZf * NZc;                    // [EB][Npf]
+    T* tt = re + kTrEB * Npf;                   // [EB][NZf][NTc]
+    for (int i = threadIdx.x; i < NTf * NTc; i += blockDim.x) sBt[i] = Bt[i];
+    for (int i = threadIdx.x; i < NZf * NZc; i += blockDim.x) sBz[i] = Bz[i];
+    for (int e0 = blockIdx.x * kTrEB; e0 < E; e0 += gridDim.x * kTrEB) {
+        const int nb = min(kTrEB, E - e0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nb * Npf; i += blockDim.x) {
+            const int b = i / Npf, l = i - b * Npf;
+            const int m = mapf[(size_t)(e0 + b) * Npf + l];
+            re[b * Npf + l] = (m >= 0) ? wmult[m] * (f[m] - y[m]) : T(0);
         }
         __syncthreads();
-        for (int c = threadIdx.x; c < Npc; c += blockDim.x) {
-            const int m = mapc[(size_t)e * Npc + c];
+        for (int i = threadIdx.x; i < nb * NZf * NTc; i += blockDim.x) {
+            const int b = i / (NZf * NTc), rem = i - b * NZf * NTc, kf = rem / NTc, nc = rem - kf * NTc;
+            const T* rr = re + b * Npf + kf * NTf;
+            T v = 0;
+            for (int nf = 0; nf < NTf; ++nf) v += sBt[nf * NTc + nc] * rr[nf];
+            tt[b * NZf * NTc + kf * NTc + nc] = v;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < nb * Npc; i += blockDim.x) {
+            const int b = i / Npc, c = i - b * Npc, kc = c / NTc, nc = c - kc * NTc;
+            const int m = mapc[(size_t)(e0 + b) * Npc + c];
             if (m < 0) continue;
-            T s = 0;
-            for (int l = 0; l < Npf; ++l) s += I[l * Npc + c] * re[l];
-            atomicAdd(&fc[m], s);
+            T v = 0;
+            for (int kf = 0; kf < NZf; ++kf) v += sBz[kf * NZc + kc] * tt[b * NZf * NTc + kf * NTc + nc];
+            atomicAdd(&fc[m], v);
         }
-        __syncthreads();
     }
 }
 
 // Prolongation and correction: uf += P uc, each fine node written by its owner element.
+// T[kc][nf] = sum_nc Bt[nf][nc] uc[kc][nc], fine[kf][nf] = sum_kc Bz[kf][kc] T[kc][nf].
 template <typename T>
-__global__ void k_prolong(int E, int Npf, int Npc, const int* __restrict__ mapf, const int* __restrict__ mapc,
-                          const unsigned char* __restrict__ owner, const T* __restrict__ I,
-                          const T* __restrict__ uc, T* __restrict__ uf) {
+__global__ void k_prolong(int E, int NTf, int NZf, int NTc, int NZc, const int* __restrict__ mapf,
+                          const int* __restrict__ mapc, const unsigned char* __restrict__ owner,
+                          const T* __restrict__ Bt, const T* __restrict__ Bz, const T* __restrict__ uc,
+                          T* __restrict__ uf) {
     extern __shared__ __align__(16) unsigned char smp[];
-    T* ce = reinterpret_cast<T*>(smp);
-    for (int e = blockIdx.x; e < E; e += gridDim.x) {
-        for (int c = threadIdx.x; c < Npc; c += blockDim.x) {
-            const int m = mapc[(size_t)e * Npc + c];
-            ce[c] = (m >= 0) ? uc[m] : T(0);
+    const int Npf = NTf * NZf, Npc = NTc * NZc;
+    T* sBt = reinterpret_cast<T*>(smp);
+    T* sBz = sBt + NTf * NTc;
+    T* ce = sBz + NZf * NZc;                    // [EB][Npc]
+    T* tt = ce + kTrEB * Npc;                   // [EB][NZc][NTf]
+    for (int i = threadIdx.x; i < NTf * NTc; i += blockDim.x) sBt[i] = Bt[i];
+    for (int i = threadIdx.x; i < NZf * NZc; i += blockDim.x) sBz[i] = Bz[i];
+    for (int e0 = blockIdx.x * kTrEB; e0 < E; e0 += gridDim.x * kTrEB) {
+        const int nb = min(kTrEB, E - e0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nb * Npc; i += blockDim.x) {
+            const int b = i / Npc, c = i - b * Npc;
+            const int m = mapc[(size_t)(e0 + b) * Npc + c];
+            ce[b * Npc + c] = (m >= 0) ? uc[m] : T(0);
         }
         __syncthreads();
-        for (int l = threadIdx.x; l < Npf; l += blockDim.x) {
-            if (!owner[(size_t)e * Npf + l]) continue;
-            T s = 0;
-            for (int c = 0; c < Npc; ++c) s += I[l * Npc + c] * ce[c];
-            uf[mapf[(size_t)e * Npf + l]] += s;
+        for (int i = threadIdx.x; i < nb * NZc * NTf; i += blockDim.x) {
+            const int b = i / (NZc * NTf), rem = i - b * NZc * NTf, kc = rem / NTf, nf = rem - kc * NTf;
+            const T* cc = ce + b * Npc + kc * NTc;
+            T v = 0;
+            for (int nc = 0; nc < NTc; ++nc) v += sBt[nf * NTc + nc] * cc[nc];
+            tt[b * NZc * NTf + kc * NTf + nf] = v;
         }
         __syncthreads();
+        for (int i = threadIdx.x; i < nb * Npf; i += blockDim.x) {
+            const int b = i / Npf, l = i - b * Npf, kf = l / NTf, nf = l - kf * NTf;
+            if (!owner[(size_t)(e0 + b) * Npf + l]) continue;
+            T v = 0;
+            for (int kc = 0; kc < NZc; ++kc) v += sBz[kf * NZc + kc] * tt[b * NZc * NTf + kc * NTf + nf];
+            uf[mapf[(size_t)(e0 + b) * Npf + l]] += v;
+        }
     }
 }
 
@@ -872,56 +917,49 @@ __device__ double grid_total(const double* part) {
     return t;
 }
 
-// One thread per element: A_e x_e with the full reference gradients gref[DIM][NQ][NP].
-template <int DIM, int NP, int NQ>
-__device__ __forceinline__ void element_apply(int e, const int* __restrict__ map, const double* __restrict__ G,
-                                              const double* __restrict__ gref, const double* __restrict__ x,
-                                              double* __restrict__ y) {
-    constexpr int NC = DIM == 3 ? 6 : 3;
-    double xe[NP], ye[NP];
-    int m[NP];
-#pragma unroll
-    for (int l = 0; l < NP; ++l) {
-        m[l] = map[(size_t)e * NP + l];
-        xe[l] = m[l] >= 0 ? __ldcg(x + m[l]) : 0.0;     // written by other CTAs: read through L2
-        ye[l] = 0.0;
-    }
-    const double* Ge = G + (size_t)e * NC * NQ;
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        double g[DIM];
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) {
+// Element matrices of the coarsest level summed into its CSR matrix (free rows and
+// columns only): A_e[i][j] = sum_q sum_ab gref[a][q][i] G_ab(q) gref[b][q][j];
+// slot[e][i][j] is the CSR position of (map_i, map_j) or -1.  One thread per (e, i).
+__global__ void k_coarse_assemble(int E, int dim, int Np, int Nq, const double* __restrict__ G,
+                                  const double* __restrict__ gref, const int* __restrict__ slot,
+                                  double* __restrict__ vals) {
+    const int nc = dim == 3 ? 6 : 3;
+    const long long total = (long long)E * Np;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int e = (int)(t / Np), i = (int)(t - (long long)e * Np);
+        const double* Ge = G + (size_t)e * nc * Nq;
+        for (int j = 0; j < Np; ++j) {
+            const int sl = slot[((size_t)e * Np + i) * Np + j];
+            if (sl < 0) continue;
             double v = 0;
-#pragma unroll
-            for (int l = 0; l < NP; ++l) v += __ldg(gref + (a * NQ + q) * NP + l) * xe[l];
-            g[a] = v;
+            for (int q = 0; q < Nq; ++q) {
+                double gi[3], gj[3];
+                for (int a = 0; a < dim; ++a) {
+                    gi[a] = gref[(a * Nq + q) * Np + i];
+                    gj[a] = gref[(a * Nq + q) * Np + j];
+                }
+                double g[3][3];
+                if (dim == 3) {
+                    g[0][0] = Ge[q]; g[0][1] = g[1][0] = Ge[Nq + q]; g[0][2] = g[2][0] = Ge[2 * Nq + q];
+                    g[1][1] = Ge[3 * Nq + q]; g[1][2] = g[2][1] = Ge[4 * Nq + q]; g[2][2] = Ge[5 * Nq + q];
+                } else {
+                    g[0][0] = Ge[q]; g[0][1] = g[1][0] = Ge[Nq + q]; g[1][1] = Ge[2 * Nq + q];
+                }
+                for (int a = 0; a < dim; ++a)
+                    for (int c = 0; c < dim; ++c) v += gi[a] * g[a][c] * gj[c];
+            }
+            atomicAdd(&vals[sl], v);
         }
-        double w[DIM];
-        if (DIM == 3) {
-            const double g0 = Ge[q], g1 = Ge[NQ + q], g2 = Ge[2 * NQ + q], g3 = Ge[3 * NQ + q], g4 = Ge[4 * NQ + q],
-                         g5 = Ge[5 * NQ + q];
-            w[0] = g0 * g[0] + g1 * g[1] + g2 * g[2];
-            w[1] = g1 * g[0] + g3 * g[1] + g4 * g[2];
-            w[2] = g2 * g[0] + g4 * g[1] + g5 * g[2];
-        } else {
-            const double g0 = Ge[q], g1 = Ge[NQ + q], g2 = Ge[2 * NQ + q];
-            w[0] = g0 * g[0] + g1 * g[1];
-            w[1] = g1 * g[0] + g2 * g[1];
-        }
-#pragma unroll
-        for (int a = 0; a < DIM; ++a)
-#pragma unroll
-            for (int l = 0; l < NP; ++l) ye[l] += __ldg(gref + (a * NQ + q) * NP + l) * w[a];
     }
-#pragma unroll
-    for (int l = 0; l < NP; ++l)
-        if (m[l] >= 0) atomicAdd(&y[m[l]], ye[l]);
 }
 
-template <int DIM, int NP, int NQ>
-__global__ void __launch_bounds__(256) k_coarse_cg(int E, long long n, const int* __restrict__ map,
-                                                   const double* __restrict__ G, const double* __restrict__ gref,
+// Whole CG on the assembled coarse matrix; three grid barriers per iteration
+// (after the SpMV with p^T q, after the update with r^T z and r^T r, after the
+// new direction).  Values written by other CTAs (p in the SpMV) are read
+// through L2 (__ldcg).
+__global__ void __launch_bounds__(512) k_coarse_cg(long long n, const int* __restrict__ rowptr,
+                                                   const int* __restrict__ col, const double* __restrict__ vals,
                                                    const double* __restrict__ dinv, const double* __restrict__ b,
                                                    double* x, double* r, double* z, double* p, double* q,
                                                    double* part, unsigned* bar, double* scal, int* flags,
@@ -937,7 +975,6 @@ __global__ void __launch_bounds__(256) k_coarse_cg(int E, long long n, const int
         r[i] = bi;
         z[i] = zi;
         p[i] = zi;
-        q[i] = 0;
         s0 += bi * zi;
         s1 += bi * bi;
     }
@@ -951,18 +988,34 @@ __global__ void __launch_bounds__(256) k_coarse_cg(int E, long long n, const int
     int it = 0;
     double rr = bb;
     while (rr > tol2 && rr > 0.0 && it < imax) {
-        for (long long e = tid; e < E; e += stride) element_apply<DIM, NP, NQ>((int)e, map, G, gref, p, q);
-        if (!grid_barrier(bar, expected)) return;
         double pq = 0;
-        for (long long i = tid; i < n; i += stride) pq += p[i] * __ldcg(q + i);   // q: atomics of other CTAs
+        for (long long i = tid; i < n; i += stride) {
+            double v = 0;
+            const int k0 = rowptr[i], k1 = rowptr[i + 1];
+            for (int k = k0; k < k1; k += 8) {          // 8 independent gathers in flight
+                int c[8];
+                double a[8], pv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    c[u] = (k + u < k1) ? col[k + u] : -1;
+                    a[u] = (k + u < k1) ? vals[k + u] : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) pv[u] = c[u] >= 0 ? __ldcg(p + c[u]) : 0.0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v += a[u] * pv[u];
+            }
+            q[i] = v;
+            pq += p[i] * v;
+        }
         pq = block_sum(pq);
-        if (threadIdx.x == 0) part[blockIdx.x] = pq;
+        if (threadIdx.x == 0) part[2 * nb + blockIdx.x] = pq;
         if (!grid_barrier(bar, expected)) return;
-        const double alpha = rho / grid_total(part);
+        const double alpha = rho / grid_total(part + 2 * nb);
         double t0 = 0, t1 = 0;
         for (long long i = tid; i < n; i += stride) {
             x[i] += alpha * p[i];
-            const double ri = r[i] - alpha * __ldcg(q + i);
+            const double ri = r[i] - alpha * q[i];
             r[i] = ri;
             const double zi = dinv[i] * ri;
             z[i] = zi;
@@ -971,17 +1024,15 @@ __global__ void __launch_bounds__(256) k_coarse_cg(int E, long long n, const int
         }
         t0 = block_sum(t0);
         t1 = block_sum(t1);
-        if (threadIdx.x == 0) { part[2 * nb + blockIdx.x] = t0; part[3 * nb + blockIdx.x] = t1; }
+        if (threadIdx.x == 0) { part[blockIdx.x] = t0; part[nb + blockIdx.x] = t1; }
         if (!grid_barrier(bar, expected)) return;
-        const double rho_new = grid_total(part + 2 * nb);
-        rr = grid_total(part + 3 * nb);
+        const double rho_new = grid_total(part);
+        rr = grid_total(part + nb);
         const double beta = rho_new / rho;
         rho = rho_new;
-        for (long long i = tid; i < n; i += stride) {
-            p[i] = z[i] + beta * p[i];
-            q[i] = 0;
-        }
         ++it;
+        if (rr <= tol2) break;
+        for (long long i = tid; i < n; i += stride) p[i] = z[i] + beta * p[i];
         if (!grid_barrier(bar, expected)) return;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1149,33 +1200,36 @@ cudaError_t launch_diag(const Level& L, double* diag, cudaStream_t s) {
 }
 
 template <typename T>
-static cudaError_t restrict_t(const Level& F, const Level& C, const T* wm, const T* I, const T* f, const T* y, T* fc,
-                              cudaStream_t s) {
-    const int grid = std::min(F.E, kSMs * 8);
-    k_restrict<T><<<grid, 64, sizeof(T) * F.Np, s>>>(F.E, F.Np, C.Np, F.map, C.map, wm, I, f, y, fc);
+static cudaError_t restrict_t(const Level& F, const Level& C, const T* wm, const T* Bt, const T* Bz, const T* f,
+                              const T* y, T* fc, cudaStream_t s) {
+    const int grid = std::min((F.E + kTrEB - 1) / kTrEB, kSMs * 8);
+    const size_t smem = sizeof(T) * (F.NT * C.NT + F.NZ * C.NZ + kTrEB * (F.Np + F.NZ * C.NT));
+    k_restrict<T><<<grid, 256, smem, s>>>(F.E, F.NT, F.NZ, C.NT, C.NZ, F.map, C.map, wm, Bt, Bz, f, y, fc);
     return cudaGetLastError();
 }
 
 template <typename T>
-static cudaError_t prolong_t(const Level& F, const Level& C, const T* I, const T* uc, T* uf, cudaStream_t s) {
-    const int grid = std::min(F.E, kSMs * 8);
-    k_prolong<T><<<grid, 128, sizeof(T) * C.Np, s>>>(F.E, F.Np, C.Np, F.map, C.map, F.owner, I, uc, uf);
+static cudaError_t prolong_t(const Level& F, const Level& C, const T* Bt, const T* Bz, const T* uc, T* uf,
+                             cudaStream_t s) {
+    const int grid = std::min((F.E + kTrEB - 1) / kTrEB, kSMs * 8);
+    const size_t smem = sizeof(T) * (F.NT * C.NT + F.NZ * C.NZ + kTrEB * (C.Np + C.NZ * F.NT));
+    k_prolong<T><<<grid, 256, smem, s>>>(F.E, F.NT, F.NZ, C.NT, C.NZ, F.map, C.map, F.owner, Bt, Bz, uc, uf);
     return cudaGetLastError();
 }
 
 cudaError_t launch_restrict64(const Level& F, const Level& C, const double* f, const double* y, double* fc,
                               cudaStream_t s) {
-    return restrict_t<double>(F, C, F.wmult, F.I64, f, y, fc, s);
+    return restrict_t<double>(F, C, F.wmult, F.It64, F.Iz64, f, y, fc, s);
 }
 cudaError_t launch_restrict32(const Level& F, const Level& C, const float* f, const float* y, float* fc,
                               cudaStream_t s) {
-    return restrict_t<float>(F, C, F.wmult32, F.I32, f, y, fc, s);
+    return restrict_t<float>(F, C, F.wmult32, F.It32, F.Iz32, f, y, fc, s);
 }
 cudaError_t launch_prolong64(const Level& F, const Level& C, const double* uc, double* uf, cudaStream_t s) {
-    return prolong_t<double>(F, C, F.I64, uc, uf, s);
+    return prolong_t<double>(F, C, F.It64, F.Iz64, uc, uf, s);
 }
 cudaError_t launch_prolong32(const Level& F, const Level& C, const float* uc, float* uf, cudaStream_t s) {
-    return prolong_t<float>(F, C, F.I32, uc, uf, s);
+    return prolong_t<float>(F, C, F.It32, F.Iz32, uc, uf, s);
 }
 
 template <typename T>
@@ -1277,39 +1331,37 @@ cudaError_t scale64(long long n, const double* w, const double* nrm2, double* v,
     k_scale<<<vec_grid(n), kVecThreads, 0, s>>>(n, w, nrm2, v);
     return cudaGetLastError();
 }
-cudaError_t coarse_cg_persistent(const Level& C, const double* gref, const double* b, double* x, double* r,
-                                 double* z, double* p, double* q, Scratch& sc, double rtol2, int imax,
-                                 unsigned extra_arrivals, cudaStream_t s) {
-    void (*kern)(int, long long, const int*, const double*, const double*, const double*, const double*, double*,
-                 double*, double*, double*, double*, double*, unsigned*, double*, int*, double, int, unsigned);
-    if (C.dim == 3 && C.Np == 6 && C.Nq == 8) kern = k_coarse_cg<3, 6, 8>;
-    else if (C.dim == 2 && C.Np == 3 && C.Nq == 4) kern = k_coarse_cg<2, 3, 4>;
-    else return cudaErrorInvalidValue;
+cudaError_t coarse_assemble(const Level& C, const double* gref, const int* slot, double* vals, cudaStream_t s) {
+    const long long total = (long long)C.E * C.Np;
+    const int grid = (int)std::min<long long>((total + 255) / 256, kSMs * 16);
+    k_coarse_assemble<<<grid, 256, 0, s>>>(C.E, C.dim, C.Np, C.Nq, C.G, gref, slot, vals);
+    return cudaGetLastError();
+}
+
+cudaError_t coarse_cg_persistent(const Level& C, const int* rowptr, const int* col, const double* vals,
+                                 const double* b, double* x, double* r, double* z, double* p, double* q, Scratch& sc,
+                                 double rtol2, int imax, unsigned extra_arrivals, cudaStream_t s) {
     int per_sm = 0;
-    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_cg, 512, 0);
     if (err != cudaSuccess) return err;
-    if (per_sm > 2) per_sm = 2;
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
     int dev = 0, sms = kSMs;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    long long want = (std::max<long long>(C.N, C.E) + 255) / 256;
-    int grid = (int)std::min<long long>(want, (long long)sms * per_sm);
+    // one CTA per SM at most: fewer participants make the grid barrier cheaper
+    int grid = (int)std::min<long long>((C.N + 511) / 512, (long long)sms);
     if (grid < 1) grid = 1;
     err = cudaMemsetAsync(sc.counter + 1, 0, 3 * sizeof(unsigned), s);
     if (err != cudaSuccess) return err;
-    int E = C.E;
     long long n = C.N;
-    const int* map = C.map;
-    const double* G = C.G;
     const double* dinv = C.dinv;
     double* part = sc.part;
     unsigned* bar = sc.counter + 1;
     double* scal = sc.scal;
     int* flags = sc.flags;
-    void* args[] = {&E,    &n,    &map,  &G,     &gref,  &dinv,  &b,     &x,    &r,
-                    &z,    &p,    &q,    &part,  &bar,   &scal,  &flags, &rtol2, &imax, &extra_arrivals};
-    err = cudaLaunchCooperativeKernel((void*)kern, grid, 256, args, 0, s);
+    void* args[] = {&n,    &rowptr, &col,  &vals,  &dinv,  &b,     &x,    &r,   &z,
+                    &p,    &q,      &part, &bar,   &scal,  &flags, &rtol2, &imax, &extra_arrivals};
+    err = cudaLaunchCooperativeKernel((void*)k_coarse_cg, grid, 512, args, 0, s);
     if (err != cudaSuccess) return err;
     return cudaGetLastError();
 }

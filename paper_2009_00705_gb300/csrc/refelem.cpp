@@ -305,24 +305,18 @@ void RefLevel::build(int dim_, int p_) {
     face_nodes.push_back(top);
 }
 
-std::vector<double> interp_matrix(int dim, int pf, int pc) {
+void interp_factors(int dim, int pf, int pc, std::vector<double>& Bt, std::vector<double>& Bz) {
     const std::vector<double> fn = tri_nodes(pf);
-    const int NTf = (pf + 1) * (pf + 2) / 2, NTc = (pc + 1) * (pc + 2) / 2;
-    std::vector<double> B, Dr, Ds;
-    tri_lagrange(pc, fn.data(), NTf, B, Dr, Ds);
-    if (dim == 2) return B;
+    const int NTf = (pf + 1) * (pf + 2) / 2;
+    std::vector<double> Dr, Ds;
+    tri_lagrange(pc, fn.data(), NTf, Bt, Dr, Ds);
+    if (dim == 2) {
+        Bz.assign(1, 1.0);
+        return;
+    }
     const std::vector<double> zf = gll(pf), zc = gll(pc);
-    std::vector<double> Bz, Dz;
+    std::vector<double> Dz;
     lagrange1d(zc, zf.data(), pf + 1, Bz, Dz);
-    const int Npf = NTf * (pf + 1), Npc = NTc * (pc + 1);
-    std::vector<double> I((size_t)Npf * Npc);
-    for (int kf = 0; kf <= pf; ++kf)
-        for (int nf = 0; nf < NTf; ++nf)
-            for (int kc = 0; kc <= pc; ++kc)
-                for (int nc = 0; nc < NTc; ++nc)
-                    I[(size_t)(kf * NTf + nf) * Npc + kc * NTc + nc] =
-                        B[(size_t)nf * NTc + nc] * Bz[(size_t)kf * (pc + 1) + kc];
-    return I;
 }
 
 }  // namespace sem

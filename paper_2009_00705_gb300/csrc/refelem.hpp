@@ -39,7 +39,9 @@ struct RefLevel {
     void build(int dim, int p);
 };
 
-// Element prolongation: order-pc basis at the order-pf nodes, [Np_f][Np_c].
-std::vector<double> interp_matrix(int dim, int pf, int pc);
+// Element prolongation (order-pc basis at the order-pf nodes) in tensor factors:
+// triangle part Bt [NT_f][NT_c] and vertical part Bz [NZ_f][NZ_c] ([1] for
+// triangles); I[(kf,nf)][(kc,nc)] = Bt[nf][nc] * Bz[kf][kc].
+void interp_factors(int dim, int pf, int pc, std::vector<double>& Bt, std::vector<double>& Bz);
 
 }  // namespace sem

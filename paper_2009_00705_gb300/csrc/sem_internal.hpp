@@ -43,8 +43,10 @@ struct Level {
     RefDev<double> ref64;
     RefDev<float> ref32;
     // transfer to the next coarser level (valid for all but the coarsest)
-    double* I64 = nullptr;                 // [Np][Np_c]
-    float* I32 = nullptr;
+    double* It64 = nullptr;                // [NT][NT_c]: coarse triangle basis at the fine triangle nodes
+    double* Iz64 = nullptr;                // [NZ][NZ_c]: coarse 1D basis at the fine GLL nodes ([1] in 2D)
+    float* It32 = nullptr;
+    float* Iz32 = nullptr;
     unsigned char* owner = nullptr;        // [E][Np]: this element writes the prolonged value
     double* wmult = nullptr;               // 1 / (elements sharing the node)
     float* wmult32 = nullptr;
@@ -52,6 +54,10 @@ struct Level {
     double *u = nullptr, *f = nullptr, *y = nullptr, *d = nullptr;
     float *u32 = nullptr, *f32 = nullptr, *y32 = nullptr, *d32 = nullptr;
     double* gref = nullptr;                // [dim][Nq][Np] full reference gradients (coarse level)
+    int* csr_rowptr = nullptr;             // coarse level: assembled matrix, free rows/cols
+    int* csr_col = nullptr;
+    double* csr_val = nullptr;
+    long long csr_nnz = 0;
 };
 
 struct Scratch {
@@ -156,11 +162,12 @@ cudaError_t cg_pq(long long n, const double* p, const double* q, Scratch& sc, cu
 cudaError_t cg_update(long long n, const double* dinv, double* x, double* r, double* z, const double* p,
                       const double* q, Scratch& sc, cudaStream_t s);
 cudaError_t cg_direction(long long n, const double* z, double* p, Scratch& sc, cudaStream_t s);
-// whole coarse CG in one cooperative launch (order-1 coarse levels); the barrier
-// timeout flag is counter[3]
-cudaError_t coarse_cg_persistent(const Level& C, const double* gref, const double* b, double* x, double* r,
-                                 double* z, double* p, double* q, Scratch& sc, double rtol2, int imax,
-                                 unsigned extra_arrivals, cudaStream_t s);
+// coarse level: assembled CSR matrix (free rows/cols) and the whole CG in one
+// cooperative launch; the barrier timeout flag is counter[3]
+cudaError_t coarse_assemble(const Level& C, const double* gref, const int* slot, double* vals, cudaStream_t s);
+cudaError_t coarse_cg_persistent(const Level& C, const int* rowptr, const int* col, const double* vals,
+                                 const double* b, double* x, double* r, double* z, double* p, double* q, Scratch& sc,
+                                 double rtol2, int imax, unsigned extra_arrivals, cudaStream_t s);
 
 // scalar slots in Scratch::scal
 enum {

@@ -303,6 +303,47 @@ sem_status build_coarse_gradients(sem_handle* h) {
                     if (C.dim == 3) g[(size_t)(2 * C.Nq + q) * C.Np + l] = r.Bt[qt * C.NT + n] * dz;
                 }
     CK(upload(&C.gref, g));
+    // CSR pattern of the free-free coarse matrix and the slot of every element entry
+    if ((long long)C.E * C.Np * C.Np > (1LL << 28)) return SEM_OK;   // large coarse elements: matrix-free CG
+    std::vector<std::vector<int>> cols(C.N);
+    for (int e = 0; e < C.E; ++e)
+        for (int i = 0; i < C.Np; ++i) {
+            const int gi = C.hmap[(size_t)e * C.Np + i];
+            if (gi < 0) continue;
+            for (int j = 0; j < C.Np; ++j) {
+                const int gj = C.hmap[(size_t)e * C.Np + j];
+                if (gj >= 0) cols[gi].push_back(gj);
+            }
+        }
+    std::vector<int> rowptr(C.N + 1, 0), col;
+    for (long long i = 0; i < C.N; ++i) {
+        std::sort(cols[i].begin(), cols[i].end());
+        cols[i].erase(std::unique(cols[i].begin(), cols[i].end()), cols[i].end());
+        rowptr[i + 1] = rowptr[i] + (int)cols[i].size();
+        col.insert(col.end(), cols[i].begin(), cols[i].end());
+    }
+    std::vector<int> slot((size_t)C.E * C.Np * C.Np, -1);
+    for (int e = 0; e < C.E; ++e)
+        for (int i = 0; i < C.Np; ++i) {
+            const int gi = C.hmap[(size_t)e * C.Np + i];
+            if (gi < 0) continue;
+            for (int j = 0; j < C.Np; ++j) {
+                const int gj = C.hmap[(size_t)e * C.Np + j];
+                if (gj < 0) continue;
+                const auto it = std::lower_bound(cols[gi].begin(), cols[gi].end(), gj);
+                slot[((size_t)e * C.Np + i) * C.Np + j] = rowptr[gi] + (int)(it - cols[gi].begin());
+            }
+        }
+    C.csr_nnz = (long long)col.size();
+    int* dslot = nullptr;
+    CK(upload(&C.csr_rowptr, rowptr));
+    CK(upload(&C.csr_col, col));
+    CK(upload(&dslot, slot));
+    CK(dalloc(&C.csr_val, col.size()));
+    CK(cudaMemset(C.csr_val, 0, sizeof(double) * col.size()));
+    CK(coarse_assemble(C, C.gref, dslot, C.csr_val, 0));
+    CK(cudaDeviceSynchronize());
+    cudaFree(dslot);
     return SEM_OK;
 }
 
@@ -310,9 +351,12 @@ sem_status build_transfers(sem_handle* h) {
     for (size_t li = 0; li + 1 < h->lv.size(); ++li) {
         Level& F = h->lv[li];
         const Level& C = h->lv[li + 1];
-        const std::vector<double> I = interp_matrix(F.dim, F.p, C.p);
-        CK(upload(&F.I64, I));
-        CK(upload(&F.I32, to_float(I)));
+        std::vector<double> Bt, Bz;
+        interp_factors(F.dim, F.p, C.p, Bt, Bz);
+        CK(upload(&F.It64, Bt));
+        CK(upload(&F.Iz64, Bz));
+        CK(upload(&F.It32, to_float(Bt)));
+        CK(upload(&F.Iz32, to_float(Bz)));
     }
     return SEM_OK;
 }

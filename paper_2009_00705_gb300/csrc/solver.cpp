@@ -108,17 +108,18 @@ void flush_events(sem_handle* h) {
     h->ev_used = 0;
 }
 
-// FP64 Jacobi-CG on the coarsest level: x = A_c^{-1} b to coarse_rtol.  An order-1
-// coarse level runs the whole CG in one persistent cooperative launch; higher orders
-// (single-level configurations) launch one kernel per CG step, predicated on a
-// device-side done flag, and test convergence every 8 iterations.
+// FP64 Jacobi-CG on the coarsest level: x = A_c^{-1} b to coarse_rtol.  The coarse
+// matrix is assembled in CSR at setup and the whole CG runs in one persistent
+// cooperative launch; coarse levels too large to assemble (high-order single-level
+// configurations) launch one kernel per CG step, predicated on a device-side done
+// flag, and test convergence every 8 iterations.
 sem_status coarse_solve(sem_handle* h, const double* b, double* x, cudaStream_t s) {
     const Level& C = h->lv.back();
     Scratch& sc = h->sc;
     const double rt = h->opts.coarse_rtol;
-    if (C.p == 1) {
-        K(coarse_cg_persistent(C, C.gref, b, x, h->cr, h->cz, h->cp, h->cq, sc, rt * rt, h->opts.coarse_imax,
-                               (unsigned)h->opts.debug_barrier_extra, s));
+    if (C.csr_val != nullptr) {
+        K(coarse_cg_persistent(C, C.csr_rowptr, C.csr_col, C.csr_val, b, x, h->cr, h->cz, h->cp, h->cq, sc, rt * rt,
+                               h->opts.coarse_imax, (unsigned)h->opts.debug_barrier_extra, s));
         CKS(cudaMemcpyAsync(sc.hflags, sc.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
         CKS(cudaMemcpyAsync(sc.hflags + 4, sc.counter + 3, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         CKS(cudaStreamSynchronize(s));
@@ -339,7 +340,8 @@ sem_status estimate_lambda(sem_handle* h, int li) {
 }
 
 void free_level(Level& L) {
-    void* ptrs[] = {L.map, L.G, L.G32, L.dinv, L.dinv32, L.dir, L.ref64.m, L.ref32.m, L.I64, L.I32, L.gref,
+    void* ptrs[] = {L.map, L.G, L.G32, L.dinv, L.dinv32, L.dir, L.ref64.m, L.ref32.m, L.It64, L.Iz64, L.It32, L.Iz32, L.gref,
+                    L.csr_rowptr, L.csr_col, L.csr_val,
                     L.owner, L.wmult, L.wmult32, L.u, L.f, L.y, L.d, L.u32, L.f32, L.y32, L.d32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
