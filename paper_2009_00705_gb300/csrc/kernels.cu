@@ -169,8 +169,9 @@ struct PrismTile {
     static constexpr int Np = NT * NZ, Nq = QT * QZ;
     static constexpr int VEC = 16 / sizeof(T);                  // elements per 16-byte load
     static constexpr int QZP = (QZ + VEC - 1) / VEC * VEC;      // padded row length
-    // elements per CTA pass: fewer in FP64 (shared memory), more at low order (small elements)
-    static constexpr int EB = (sizeof(T) == 8 ? 4 : 8) * (P <= 2 ? 4 : (P == 3 ? 2 : 1));
+    // elements per CTA pass: 8 at P = 6 fills whole warps in both heavy stages
+    // (8 * 49 quadrature columns, 8 * 28 triangle nodes); more at low order
+    static constexpr int EB = 8 * (P <= 2 ? 4 : (P == 3 ? 2 : 1));
     static constexpr int THR_RAW = ((EB * NT + 31) / 32) * 32;
     static constexpr int NTHR = THR_RAW < 64 ? 64 : (THR_RAW > 256 ? 256 : THR_RAW);
     static constexpr bool TRANSPOSED = (sizeof(T) == 4);       // conflict-free copies for FP32 only
@@ -228,6 +229,19 @@ __global__ void __launch_bounds__(PrismTile<P, T>::NTHR)
     __syncthreads();
     for (int e0 = blockIdx.x * EB; e0 < E; e0 += gridDim.x * EB) {
         const int nb = min(EB, E - e0);
+        {   // pull the next pass's geometric factors and map into L2 while this pass computes
+            const int en = e0 + gridDim.x * EB;
+            if (en < E) {
+                const int nn = min(EB, E - en);
+                const char* g0 = reinterpret_cast<const char*>(G + (size_t)en * 6 * Nq);
+                const size_t gbytes = (size_t)nn * 6 * Nq * sizeof(T);
+                for (size_t off = (size_t)threadIdx.x * 128; off < gbytes; off += (size_t)blockDim.x * 128)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(g0 + off));
+                const char* m0 = reinterpret_cast<const char*>(map + (size_t)en * Np);
+                for (size_t off = (size_t)threadIdx.x * 128; off < (size_t)nn * Np * 4; off += (size_t)blockDim.x * 128)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(m0 + off));
+            }
+        }
         // gather
         for (int i = threadIdx.x; i < nb * Np; i += blockDim.x) {
             const int b = i / Np, l = i - b * Np;
@@ -988,25 +1002,39 @@ __global__ void __launch_bounds__(512) k_coarse_cg(long long n, const int* __res
     int it = 0;
     double rr = bb;
     while (rr > tol2 && rr > 0.0 && it < imax) {
+        // SpMV q = A p with 4 lanes per row; lane 0 of the group owns q[row] and p^T q.
+        // The loop runs over warp-uniform groups of 8 rows (all 32 lanes reach the
+        // shuffles); lanes past the last row contribute zero.
         double pq = 0;
-        for (long long i = tid; i < n; i += stride) {
+        const int l4 = threadIdx.x & 3;
+        const long long rstride = stride >> 2;                  // multiple of 8 (blockDim % 32 == 0)
+        for (long long rb = (tid >> 2) & ~7LL; rb < n; rb += rstride) {
+            const long long row = rb + ((tid >> 2) & 7);
+            const bool active = row < n;
             double v = 0;
-            const int k0 = rowptr[i], k1 = rowptr[i + 1];
-            for (int k = k0; k < k1; k += 8) {          // 8 independent gathers in flight
-                int c[8];
-                double a[8], pv[8];
+            if (active) {
+                const int k0 = rowptr[row], k1 = rowptr[row + 1];
+                for (int k = k0 + l4; k < k1; k += 32) {    // up to 8 independent gathers per lane
+                    int c[8];
+                    double a[8], pv[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    c[u] = (k + u < k1) ? col[k + u] : -1;
-                    a[u] = (k + u < k1) ? vals[k + u] : 0.0;
+                    for (int u = 0; u < 8; ++u) {
+                        const int kk = k + 4 * u;
+                        c[u] = (kk < k1) ? col[kk] : -1;
+                        a[u] = (kk < k1) ? vals[kk] : 0.0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) pv[u] = c[u] >= 0 ? __ldcg(p + c[u]) : 0.0;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) v += a[u] * pv[u];
                 }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) pv[u] = c[u] >= 0 ? __ldcg(p + c[u]) : 0.0;
-#pragma unroll
-                for (int u = 0; u < 8; ++u) v += a[u] * pv[u];
             }
-            q[i] = v;
-            pq += p[i] * v;
+            v += __shfl_down_sync(0xffffffffu, v, 2, 4);
+            v += __shfl_down_sync(0xffffffffu, v, 1, 4);
+            if (active && l4 == 0) {
+                q[row] = v;
+                pq += __ldcg(p + row) * v;
+            }
         }
         pq = block_sum(pq);
         if (threadIdx.x == 0) part[2 * nb + blockIdx.x] = pq;
@@ -1015,7 +1043,7 @@ __global__ void __launch_bounds__(512) k_coarse_cg(long long n, const int* __res
         double t0 = 0, t1 = 0;
         for (long long i = tid; i < n; i += stride) {
             x[i] += alpha * p[i];
-            const double ri = r[i] - alpha * q[i];
+            const double ri = r[i] - alpha * __ldcg(q + i);   // q[i] was written by another lane group
             r[i] = ri;
             const double zi = dinv[i] * ri;
             z[i] = zi;
@@ -1348,8 +1376,9 @@ cudaError_t coarse_cg_persistent(const Level& C, const int* rowptr, const int* c
     int dev = 0, sms = kSMs;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // one CTA per SM at most: fewer participants make the grid barrier cheaper
-    int grid = (int)std::min<long long>((C.N + 511) / 512, (long long)sms);
+    // one CTA per SM at most (fewer participants make the grid barrier cheaper);
+    // the SpMV uses 4 lanes per row, so 128 rows per CTA
+    int grid = (int)std::min<long long>((C.N + 127) / 128, (long long)sms);
     if (grid < 1) grid = 1;
     err = cudaMemsetAsync(sc.counter + 1, 0, 3 * sizeof(unsigned), s);
     if (err != cudaSuccess) return err;
