@@ -688,6 +688,15 @@ __device__ void final_sums(const double* part, double* out) {
     }
 }
 
+// num / den computed once per block (FP64 division is a multi-instruction sequence on
+// the FP64 pipe) and broadcast through shared memory.
+__device__ __forceinline__ double block_ratio(const double* num, const double* den) {
+    __shared__ double ratio;
+    if (threadIdx.x == 0) ratio = (*num) / (*den);
+    __syncthreads();
+    return ratio;
+}
+
 __global__ void k_dot(long long n, const double* __restrict__ a, const double* __restrict__ b,
                       double* part, unsigned* counter, double* out) {
     double s = 0;
@@ -721,7 +730,7 @@ __global__ void k_residual(long long n, const double* __restrict__ f, const doub
 __global__ void k_pcg_update(long long n, const double* num, const double* den, const double* __restrict__ p,
                              const double* __restrict__ q, double* __restrict__ u, double* __restrict__ r,
                              double* part, unsigned* counter, double* out) {
-    const double alpha = (*num) / (*den);
+    const double alpha = block_ratio(num, den);
     double s = 0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         u[i] += alpha * p[i];
@@ -739,7 +748,7 @@ __global__ void k_pcg_update(long long n, const double* num, const double* den, 
 
 __global__ void k_pcg_dir(long long n, const double* num, const double* den, const double* __restrict__ z,
                           double* __restrict__ p) {
-    const double beta = (*num) / (*den);
+    const double beta = block_ratio(num, den);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         p[i] = z[i] + beta * p[i];
 }
@@ -761,7 +770,7 @@ __global__ void k_dot32(long long n, const float* __restrict__ a, const float* _
 __global__ void k_pcg_update32(long long n, const double* num, const double* den, const float* __restrict__ p,
                                const float* __restrict__ q, float* __restrict__ u, float* __restrict__ r,
                                double* part, unsigned* counter, double* out) {
-    const float alpha = (float)((*num) / (*den));
+    const float alpha = (float)block_ratio(num, den);
     double s = 0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         u[i] += alpha * p[i];
@@ -779,7 +788,7 @@ __global__ void k_pcg_update32(long long n, const double* num, const double* den
 
 __global__ void k_pcg_dir32(long long n, const double* num, const double* den, const float* __restrict__ z,
                             float* __restrict__ p) {
-    const float beta = (float)((*num) / (*den));
+    const float beta = (float)block_ratio(num, den);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         p[i] = z[i] + beta * p[i];
 }
@@ -836,7 +845,7 @@ __global__ void k_cg_update(long long n, const double* __restrict__ dinv, double
                             double* __restrict__ r, double* __restrict__ z, const double* __restrict__ p,
                             const double* __restrict__ q, double* part, unsigned* counter, double* scal, int* flags) {
     if (flags[F_CG_DONE]) return;
-    const double alpha = scal[S_CG_RHO] / scal[S_CG_PQ];
+    const double alpha = block_ratio(scal + S_CG_RHO, scal + S_CG_PQ);
     double s[2] = {0, 0};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         x[i] += alpha * p[i];
@@ -1039,7 +1048,13 @@ __global__ void __launch_bounds__(512) k_coarse_cg(long long n, const int* __res
         pq = block_sum(pq);
         if (threadIdx.x == 0) part[2 * nb + blockIdx.x] = pq;
         if (!grid_barrier(bar, expected)) return;
-        const double alpha = rho / grid_total(part + 2 * nb);
+        __shared__ double s_alpha, s_beta;
+        {
+            const double pq_all = grid_total(part + 2 * nb);
+            if (threadIdx.x == 0) s_alpha = rho / pq_all;
+            __syncthreads();
+        }
+        const double alpha = s_alpha;
         double t0 = 0, t1 = 0;
         for (long long i = tid; i < n; i += stride) {
             x[i] += alpha * p[i];
@@ -1056,7 +1071,9 @@ __global__ void __launch_bounds__(512) k_coarse_cg(long long n, const int* __res
         if (!grid_barrier(bar, expected)) return;
         const double rho_new = grid_total(part);
         rr = grid_total(part + nb);
-        const double beta = rho_new / rho;
+        if (threadIdx.x == 0) s_beta = rho_new / rho;
+        __syncthreads();
+        const double beta = s_beta;
         rho = rho_new;
         ++it;
         if (rr <= tol2) break;
@@ -1113,7 +1130,10 @@ __global__ void k_multiaxpy(long long n, int k, const double* __restrict__ V, co
 }
 
 __global__ void k_scale(long long n, const double* __restrict__ w, const double* nrm2, double* __restrict__ v) {
-    const double inv = 1.0 / sqrt(*nrm2);
+    __shared__ double sinv;
+    if (threadIdx.x == 0) sinv = 1.0 / sqrt(*nrm2);
+    __syncthreads();
+    const double inv = sinv;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         v[i] = w[i] * inv;
 }

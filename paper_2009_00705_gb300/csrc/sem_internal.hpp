@@ -82,6 +82,7 @@ struct sem_handle {
     // FGMRES basis
     double* V = nullptr;           // [(m+1)][N]
     double* Zb = nullptr;          // [m][N]
+    double* gm_y = nullptr;        // [m] least-squares coefficients
     // coarse CG (FP64) on the coarsest level
     double *cx = nullptr, *cr = nullptr, *cz = nullptr, *cp = nullptr, *cq = nullptr, *cb = nullptr;
     // inner FP32 PCG of the mixed-precision path (finest level)

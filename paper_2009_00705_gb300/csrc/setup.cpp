@@ -378,6 +378,7 @@ sem_status build_workspace(sem_handle* h) {
     if (h->opts.outer == SEM_OUTER_FGMRES) {
         CK(dalloc(&h->V, (size_t)(h->opts.gmres_m + 1) * N));
         CK(dalloc(&h->Zb, (size_t)h->opts.gmres_m * N));
+        CK(dalloc(&h->gm_y, (size_t)h->opts.gmres_m));
     }
     for (double** v : {&h->cx, &h->cr, &h->cz, &h->cp, &h->cq, &h->cb}) CK(dalloc(v, Lc.N));
     if (h->opts.precision == SEM_PREC_MIXED_FP32 && h->opts.inner_imax > 0)

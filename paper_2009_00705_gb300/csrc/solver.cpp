@@ -470,7 +470,7 @@ sem_status outer_fgmres(sem_handle* h, double* u, double tol, sem_stats* st, cud
     int it = 0;
     sem_status ret = SEM_OK;
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
-    double* dy = nullptr;
+    double* dy = h->gm_y;
     while (beta > tol) {
         if (it >= h->opts.imax) { ret = SEM_NOT_CONVERGED; break; }
         // v0 = r / beta
@@ -525,7 +525,6 @@ sem_status outer_fgmres(sem_handle* h, double* u, double tol, sem_stats* st, cud
             for (int k = i2 + 1; k < j; ++k) v -= H[(size_t)i2 * m + k] * y[k];
             y[i2] = v / H[(size_t)i2 * m + i2];
         }
-        if (!dy) CKS(cudaMalloc(&dy, sizeof(double) * m));
         CKS(cudaMemcpyAsync(dy, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, s));
         K(multiaxpy64(N, j, h->Zb, dy, 1.0, u, s));
         CKST(apply_level64(h, 0, u, h->q, false, s));
@@ -534,7 +533,6 @@ sem_status outer_fgmres(sem_handle* h, double* u, double tol, sem_stats* st, cud
         beta = std::sqrt(sc.hpinned[S_RR]);
         CKST(fail_nan(beta));
     }
-    if (dy) cudaFree(dy);
     st->iters = it;
     st->res_final = beta;
     return ret;
@@ -640,7 +638,7 @@ void sem_destroy(sem_handle* h) {
     for (Level& L : h->lv) free_level(L);
     void* ptrs[] = {h->sc.part, h->sc.counter, h->sc.scal, h->sc.flags, h->r, h->z, h->p, h->q, h->x, h->fr,
                     h->V, h->Zb, h->cx, h->cr, h->cz, h->cp, h->cq, h->cb, h->st_eta, h->st_rhs, h->st_phi,
-                    h->ir, h->iz, h->ip, h->iq, h->ie};
+                    h->ir, h->iz, h->ip, h->iq, h->ie, h->gm_y};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->sc.hpinned) cudaFreeHost(h->sc.hpinned);
