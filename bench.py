@@ -37,10 +37,12 @@ UNIT = "DOF/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_NOMINAL_TFLOPS = 1.25          # GB300 FP64 (profiling recipe's nominal table)
 FALLBACK_HBM_GBS = 6800.0
-# ncu DRAM traffic of the FP64 apply (per launch, bytes) and the kernel source it
-# was taken from; reported as null once kernels.cu has changed since the capture.
-TRAFFIC = {}
-TRAFFIC_SRC_SHA = None
+# ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the FP64 prism
+# apply, per launch, scaled from the 48x48x4-prism capture (18,432 elements;
+# profiles/apply_fp64_p6_box48.md) to the 32,768-element benchmark mesh by element
+# count; reported as null once the kernel's source differs from the captured one.
+TRAFFIC = {("apply_fp64", 6): (351.068672e6 + 14.987776e6) * 32768 / 18432}
+TRAFFIC_SRC_SHA = "78f7f4ef51218cb6"
 
 
 def workload_name(n, nl, P):
@@ -65,10 +67,11 @@ def apply_bytes(P, E, N, word=8):
 
 
 def kernels_sha():
-    h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_2009_00705_gb300", "csrc", "kernels.cu"), "rb") as f:
-        h.update(f.read())
-    return h.hexdigest()[:16]
+    """Hash of the prism-apply kernel's source section in kernels.cu."""
+    src = open(os.path.join(ROOT, "paper_2009_00705_gb300", "csrc", "kernels.cu")).read()
+    a = src.index("// ------------------------------------------------------------------ prism apply, register-tiled")
+    b = src.index("template <int P, bool PRISM, typename T, bool LIFT>\ncudaError_t apply_impl(")
+    return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
 
 
 class Clocks:
@@ -155,6 +158,26 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def run_ncu_case(a):
+    import torch
+    import paper_2009_00705_gb300 as sem
+    import workloads as W
+    from paper_2009_00705_gb300 import build as B
+    B.build()
+    P = a.P
+    mesh = W.config_box3d(a.ncu_case, a.nlayers)
+    xy = sem.sem_mesh_nodes2d(mesh, P)
+    s = sem.Solver(mesh, P, eta_nodal=mesh.eta(xy[:, 0], xy[:, 1]), levels=levels_for(P), precision="mixed_fp32",
+                   outer="pdc", inner_imax=2, inner_rtol=1e-4, imax=1)
+    C = s.coords(0)
+    phiD = torch.tensor(W.potential3d(*C[s.dirichlet_nodes(0)].T), device="cuda")
+    phi = torch.empty(s.query(0)["ndof"], dtype=torch.float64, device="cuda")
+    st = s.solve(phiD, phi, tol=1e-8, allow_not_converged=True)
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_case": a.ncu_case, "elements": s.query(0)["nelem"], "stats": st}))
+    s.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -170,11 +193,16 @@ def main():
     ap.add_argument("--inner-imax", type=int, default=40)
     ap.add_argument("--inner-rtol", type=float, default=1e-4)
     ap.add_argument("--coarse-rtol", type=float, default=1e-3)
+    ap.add_argument("--ncu-case", type=int, default=0, metavar="N",
+                    help="profiler driver: one short mixed-precision solve on an N x N x 4 P=6 box "
+                         "(FP64 and FP32 applies, transfers and the coarse CG all launch); prints stats only")
     a = ap.parse_args()
     if a.warmup < 3:
         a.warmup = 3
     if a.impl == "reference":
         return run_reference(a)
+    if a.ncu_case:
+        return run_ncu_case(a)
 
     # CPU baseline first: a separate process, before any GPU work in this one
     rank = int(os.environ.get("RANK", "0"))
