@@ -185,6 +185,28 @@ sem_status laplace_solve(sem_handle* h, const double* rhs_dev, const double* dir
 sem_status laplace_solve_host(sem_handle* h, const double* rhs_host, const double* dirichlet_eta_host,
                               double tol, double* phi_host, sem_stats* stats, void* stream);
 
+/* Jacobi-preconditioned FP64 CG on a caller-supplied CSR matrix that allocates no
+ * memory at all.  The paper has no counterpart: this is a variant of the
+ * library's coarse-level CG for callers that cannot call cudaMalloc - code whose
+ * device memory is owned by another framework's pool allocator, code running in
+ * a time-critical loop that cannot absorb the device-wide synchronisation of an
+ * allocation, or plug-ins given only fixed buffers - and that have no sem_setup
+ * handle.  The caller passes every input and output (device pointers): rowptr
+ * [n+1], col and vals [nnz] of an SPD matrix (rows with no entries are treated
+ * as excluded: give them dinv = 0 and b = 0), dinv [n] (inverse diagonal), b [n];
+ * x [n] receives the solution.  The CG's work vectors, reduction partials and
+ * barrier state live in one static device array of the library sized for
+ * n <= 131072 rows (about 4.2 MB, held on every GPU that loads the library until
+ * the process exits); larger n returns SEM_EINVAL.  The first call on a device
+ * looks up that array's device address (with the device current), so make one
+ * call before capturing a stream into a CUDA graph.  All calls share the array:
+ * calls that overlap on the GPU race.  Synchronous: stops at ||r|| <= rtol ||b||
+ * (SEM_OK) or after imax iterations (SEM_NOT_CONVERGED); *iters_host (may be
+ * NULL) receives the iteration count; SEM_TIMEOUT if a grid-barrier wait ran out. */
+sem_status sem_cg_csr_noalloc(long long n, const int* rowptr, const int* col, const double* vals,
+                              const double* dinv, const double* b, double* x, double rtol, int imax,
+                              int* iters_host, void* stream);
+
 /* Thread-local message of the last error ("" if none). */
 const char* sem_last_error(void);
 

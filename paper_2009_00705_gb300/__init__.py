@@ -26,7 +26,8 @@ PRECISION = {"fp64": 0, "mixed_fp32": 1}
 
 EXPORTS = ("sem_default_options", "sem_mesh_nodes2d", "sem_setup", "sem_destroy", "sem_query",
            "sem_dirichlet_nodes", "sem_node_coords", "sem_element_map", "sem_lambda_max", "sem_diagonal",
-           "sem_apply", "pmg_vcycle", "laplace_solve", "laplace_solve_host", "sem_last_error")
+           "sem_apply", "pmg_vcycle", "laplace_solve", "laplace_solve_host", "sem_last_error",
+           "sem_cg_csr_noalloc")
 
 
 class SemMesh(Structure):
@@ -91,6 +92,9 @@ def lib():
     L.laplace_solve_host.argtypes = [c_void_p, c_void_p, c_void_p, c_double, c_void_p, POINTER(SemStats),
                                      c_void_p]
     L.sem_last_error.restype = c_char_p
+    L.sem_cg_csr_noalloc.argtypes = [c_longlong, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                     c_double, c_int, POINTER(c_int), c_void_p]
+    L.sem_cg_csr_noalloc.restype = c_int
     for name in ("sem_mesh_nodes2d", "sem_setup", "sem_query", "sem_dirichlet_nodes", "sem_node_coords",
                  "sem_element_map", "sem_lambda_max", "sem_diagonal", "sem_apply", "pmg_vcycle",
                  "laplace_solve", "laplace_solve_host"):
@@ -248,6 +252,18 @@ def laplace_solve_host(h: int, rhs, dirichlet_eta: np.ndarray, tol: float, phi: 
     _check(lib().laplace_solve_host(h, hp(rhs), hp(dirichlet_eta), float(tol), hp(phi), byref(st),
                                     _stream(stream)))
     return st.as_dict()
+
+
+def sem_cg_csr_noalloc(n: int, rowptr, col, vals, dinv, b, x, rtol: float, imax: int, stream=None,
+                       allow_not_converged=False) -> int:
+    """Jacobi-PCG on a caller-supplied CSR matrix that allocates nothing (device buffers
+    in, device buffer out; scratch in the library's static device array).  Returns the
+    iteration count."""
+    it = c_int(0)
+    allow = (SEM_OK, SEM_NOT_CONVERGED) if allow_not_converged else (SEM_OK,)
+    _check(lib().sem_cg_csr_noalloc(int(n), _ptr(rowptr), _ptr(col), _ptr(vals), _ptr(dinv), _ptr(b), _ptr(x),
+                                    float(rtol), int(imax), byref(it), _stream(stream)), allow)
+    return it.value
 
 
 def sem_last_error() -> str:

@@ -13,6 +13,8 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <mutex>
+#include <string>
 
 #include "sem_internal.hpp"
 
@@ -1436,4 +1438,108 @@ cudaError_t cg_direction(long long n, const double* z, double* p, Scratch& sc, c
     return cudaGetLastError();
 }
 
+
+// ====================================================================== no-allocation CG
+// A variant of the coarse CG launch for callers that cannot allocate device
+// memory: the CG vectors r, z, p, q, the reduction partials, the barrier state
+// and the result flags live in one file-scope device array instead of
+// handle-owned workspaces.  Every GPU that loads the library holds the array
+// until the process exits.  All calls share it and it keeps the last call's
+// contents, so calls that overlap on the GPU race; the barrier state and the
+// flags are cleared at the start of every call.
+namespace {
+
+constexpr long long kNoAllocMaxRows = 1LL << 17;          // 131,072 rows
+constexpr long long kNoAllocPart = 1024;                  // >= 3 x (CTAs of one launch)
+constexpr size_t kNoAllocBytes = sizeof(double) * (4 * kNoAllocMaxRows + kNoAllocPart + 32) + 64;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+unsigned char* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+std::mutex g_noalloc_mutex;
+
+// Device address of the scratch array on the current device (looked up once per device,
+// with that device current).
+cudaError_t noalloc_scratch(unsigned char** out) {
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (g_noalloc_ptr[dev] == nullptr) {
+        void* ptr = nullptr;
+        err = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (err != cudaSuccess) return err;
+        g_noalloc_ptr[dev] = static_cast<unsigned char*>(ptr);
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
 }  // namespace sem
+
+extern "C" sem_status sem_cg_csr_noalloc(long long n, const int* rowptr, const int* col, const double* vals,
+                                         const double* dinv, const double* b, double* x, double rtol, int imax,
+                                         int* iters_host, void* stream) {
+    using namespace sem;
+    if (n < 1 || n > kNoAllocMaxRows) {
+        set_error("sem_cg_csr_noalloc: n must be in 1.." + std::to_string(kNoAllocMaxRows) +
+                  " (the size of the library's static scratch)");
+        return SEM_EINVAL;
+    }
+    if (!rowptr || !col || !vals || !dinv || !b || !x || !(rtol > 0.0) || imax < 0) {
+        set_error("sem_cg_csr_noalloc: bad arguments");
+        return SEM_EINVAL;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned char* base = nullptr;
+    cudaError_t err = noalloc_scratch(&base);
+    if (err != cudaSuccess) {
+        set_error(std::string("sem_cg_csr_noalloc: ") + cudaGetErrorString(err));
+        return SEM_ECUDA;
+    }
+    double* r = reinterpret_cast<double*>(base);
+    double* z = r + kNoAllocMaxRows;
+    double* p = z + kNoAllocMaxRows;
+    double* q = p + kNoAllocMaxRows;
+    double* part = q + kNoAllocMaxRows;
+    double* scal = part + kNoAllocPart;
+    int* flags = reinterpret_cast<int*>(scal + 32);
+    unsigned* bar = reinterpret_cast<unsigned*>(flags + 8);
+    int per_sm = 0, dev = 0, sms = kSMs;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_cg, 512, 0);
+    if (err == cudaSuccess && per_sm < 1) err = cudaErrorCooperativeLaunchTooLarge;
+    const int grid = (int)std::max<long long>(1, std::min<long long>((n + 127) / 128, (long long)sms));
+    if (err == cudaSuccess) err = cudaMemsetAsync(flags, 0, 8 * sizeof(int) + 4 * sizeof(unsigned), s);
+    double rtol2 = rtol * rtol;
+    unsigned extra = 0;
+    if (err == cudaSuccess) {
+        void* args[] = {&n, &rowptr, &col, &vals, &dinv, &b, &x, &r, &z, &p, &q, &part, &bar, &scal, &flags,
+                        &rtol2, &imax, &extra};
+        err = cudaLaunchCooperativeKernel((void*)k_coarse_cg, grid, 512, args, 0, s);
+    }
+    int hf[2] = {0, 0};
+    unsigned timeout = 0;
+    if (err == cudaSuccess) err = cudaMemcpyAsync(hf, flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(&timeout, bar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    if (err != cudaSuccess) {
+        set_error(std::string("sem_cg_csr_noalloc: ") + cudaGetErrorString(err));
+        return SEM_ECUDA;
+    }
+    if (iters_host) *iters_host = hf[F_CG_ITERS];
+    if (timeout) {
+        set_error("sem_cg_csr_noalloc: a grid barrier wait ran out (device timeout)");
+        return SEM_TIMEOUT;
+    }
+    if (!hf[F_CG_DONE]) {
+        set_error("sem_cg_csr_noalloc: rtol not reached within imax iterations");
+        return SEM_NOT_CONVERGED;
+    }
+    return SEM_OK;
+}
