@@ -52,6 +52,7 @@ typedef enum {
 
 typedef enum { SEM_OUTER_PCG = 0, SEM_OUTER_FGMRES = 1, SEM_OUTER_PDC = 2 } sem_outer;
 typedef enum { SEM_PREC_FP64 = 0, SEM_PREC_MIXED_FP32 = 1 } sem_precision;
+typedef enum { SEM_SMOOTH_CHEBYSHEV = 0, SEM_SMOOTH_LEARNED = 1 } sem_smoother;
 
 /* Mesh description (host memory, read during sem_setup only).
  * dim 2: ntri straight triangles in the (x, z) plane; vxy holds (x, z).
@@ -106,6 +107,13 @@ typedef struct {
     int debug_barrier_extra;    /* testing only (default 0): > 0 makes every grid barrier of the persistent
                                    coarse CG wait for arrivals that never come, so each wait runs into its
                                    1 s limit and the call returns SEM_TIMEOUT with the context intact */
+    int smoother;               /* sem_smoother.  LEARNED (MIXED_FP32 only): once sem_learned_train has
+                                   run, the first finest-level post-smoothing sweep of the FP32 V-cycle is
+                                   the correction network's, kept only if it lowers the residual norm
+                                   (otherwise the Chebyshev sweep runs).  The V-cycle is then nonlinear:
+                                   use the PDC or FGMRES outer iteration. */
+    int mlp_hidden;             /* hidden width of the correction network (default 256) */
+    unsigned long long mlp_seed; /* seed of the network's initial weights */
 } sem_options;
 
 typedef struct {
@@ -122,6 +130,8 @@ typedef struct {
     long long apply_launches;   /* finest-level apply kernel launches (profile = 1) */
     long long kernel_launches;  /* kernels of this library launched by the call */
     long long inner_iters;      /* FP32 inner PCG iterations (MIXED_FP32 with inner_imax > 0) */
+    long long learned_accepts;  /* learned sweeps kept (smoother = LEARNED) */
+    long long learned_fallbacks; /* learned sweeps rejected by the residual test (Chebyshev ran instead) */
 } sem_stats;
 
 typedef struct sem_handle sem_handle;
@@ -184,6 +194,33 @@ sem_status laplace_solve(sem_handle* h, const double* rhs_dev, const double* dir
  * Synchronous. */
 sem_status laplace_solve_host(sem_handle* h, const double* rhs_host, const double* dirichlet_eta_host,
                               double tol, double* phi_host, sem_stats* stats, void* stream);
+
+/* Per-element correction network of the learned smoothing sweep (needs a handle set up
+ * with smoother = SEM_SMOOTH_LEARNED).  y = W2 relu(W1 x + b1) + b2 with x, y of
+ * length Np (nodes of a finest-level element) and hidden width H = mlp_hidden;
+ * W1 [H][Np], b1 [H], W2 [Np][H], b2 [Np] row-major FP32 host arrays.  The
+ * GEMMs use BF16 copies of W1 and W2 with FP32 activations and accumulation.
+ * Network inputs are element residuals scaled to unit norm (Jacobi-scaled:
+ * x_e = z_e / ||z_e||, z = D^{-1} r); outputs are the element correction in the
+ * same scale.  There is no counterpart in the paper, whose smoother is the
+ * element-block Schwarz method (Eq. Mass); the network learns such a local map. */
+sem_status sem_mlp_get_weights(const sem_handle* h, float* W1, float* b1, float* W2, float* b2);
+sem_status sem_mlp_set_weights(sem_handle* h, const float* W1, const float* b1, const float* W2, const float* b2);
+/* Y [B][Np] = network(X [B][Np]) for B <= number of finest elements (device buffers). */
+sem_status sem_mlp_forward(sem_handle* h, int B, const float* X_dev, float* Y_dev, void* stream);
+/* Mean squared error L = sum_b ||y_b - t_b||^2 / B and its gradients (host arrays shaped
+ * like the weights), for B <= number of finest elements; synchronous. */
+sem_status sem_mlp_gradient(sem_handle* h, int B, const float* X_dev, const float* T_dev, double* loss_host,
+                            float* dW1, float* db1, float* dW2, float* db2, void* stream);
+/* Train the network with Adam (learning rate lr) on residual/error pairs that the plain
+ * solver generates: for each of `snapshots` seeded random errors e0 (SplitMix64 of
+ * (seed, snapshot, node)), f = A e0, the plain FP32 V-cycle iteration u <- u + M r from
+ * u = 0 runs `steps` times and every iterate gives one pair (r = f - A u, e = e0 - u),
+ * every finest element of which is a training sample.  Nothing is stored: each pair is
+ * one Adam step.  loss_first / loss_last (host, may be NULL) receive the loss of the first
+ * and last step.  Synchronous. */
+sem_status sem_learned_train(sem_handle* h, int snapshots, int steps, double lr, unsigned long long seed,
+                             double* loss_first, double* loss_last, void* stream);
 
 /* Jacobi-preconditioned FP64 CG on a caller-supplied CSR matrix that allocates no
  * memory at all.  The paper has no counterpart: this is a variant of the

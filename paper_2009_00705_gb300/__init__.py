@@ -23,11 +23,13 @@ SEM_OK, SEM_NOT_CONVERGED = 0, 1
 SEM_EINVAL, SEM_ECUDA, SEM_ENOMEM, SEM_NAN, SEM_BREAKDOWN, SEM_TIMEOUT = -1, -2, -3, -4, -5, -6
 OUTER = {"pcg": 0, "fgmres": 1, "pdc": 2}
 PRECISION = {"fp64": 0, "mixed_fp32": 1}
+SMOOTHER = {"chebyshev": 0, "learned": 1}
 
 EXPORTS = ("sem_default_options", "sem_mesh_nodes2d", "sem_setup", "sem_destroy", "sem_query",
            "sem_dirichlet_nodes", "sem_node_coords", "sem_element_map", "sem_lambda_max", "sem_diagonal",
            "sem_apply", "pmg_vcycle", "laplace_solve", "laplace_solve_host", "sem_last_error",
-           "sem_cg_csr_noalloc")
+           "sem_cg_csr_noalloc", "sem_mlp_get_weights", "sem_mlp_set_weights", "sem_mlp_forward",
+           "sem_mlp_gradient", "sem_learned_train")
 
 
 class SemMesh(Structure):
@@ -41,7 +43,8 @@ class SemOptions(Structure):
                 ("cheb_lo", c_double), ("cheb_hi", c_double), ("power_its", c_int), ("nlevels", c_int),
                 ("level_p", c_int * SEM_MAX_LEVELS), ("rtol", c_double), ("atol", c_double), ("imax", c_int),
                 ("gmres_m", c_int), ("coarse_rtol", c_double), ("coarse_imax", c_int), ("profile", c_int),
-                ("inner_imax", c_int), ("inner_rtol", c_double), ("debug_barrier_extra", c_int)]
+                ("inner_imax", c_int), ("inner_rtol", c_double), ("debug_barrier_extra", c_int),
+                ("smoother", c_int), ("mlp_hidden", c_int), ("mlp_seed", ctypes.c_ulonglong)]
 
 
 class SemStats(Structure):
@@ -49,7 +52,7 @@ class SemStats(Structure):
                 ("res_final", c_double), ("q_mean", c_double), ("fine_applies", c_longlong),
                 ("vcycles", c_longlong), ("coarse_iters_max", c_int), ("ms", c_double),
                 ("apply_ms", c_double), ("apply_launches", c_longlong), ("kernel_launches", c_longlong),
-                ("inner_iters", c_longlong)]
+                ("inner_iters", c_longlong), ("learned_accepts", c_longlong), ("learned_fallbacks", c_longlong)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -95,6 +98,16 @@ def lib():
     L.sem_cg_csr_noalloc.argtypes = [c_longlong, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                      c_double, c_int, POINTER(c_int), c_void_p]
     L.sem_cg_csr_noalloc.restype = c_int
+    fp = POINTER(ctypes.c_float)
+    L.sem_mlp_get_weights.argtypes = [c_void_p, fp, fp, fp, fp]
+    L.sem_mlp_set_weights.argtypes = [c_void_p, fp, fp, fp, fp]
+    L.sem_mlp_forward.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_void_p]
+    L.sem_mlp_gradient.argtypes = [c_void_p, c_int, c_void_p, c_void_p, POINTER(c_double), fp, fp, fp, fp, c_void_p]
+    L.sem_learned_train.argtypes = [c_void_p, c_int, c_int, c_double, ctypes.c_ulonglong, POINTER(c_double),
+                                    POINTER(c_double), c_void_p]
+    for name in ("sem_mlp_get_weights", "sem_mlp_set_weights", "sem_mlp_forward", "sem_mlp_gradient",
+                 "sem_learned_train"):
+        getattr(L, name).restype = c_int
     for name in ("sem_mesh_nodes2d", "sem_setup", "sem_query", "sem_dirichlet_nodes", "sem_node_coords",
                  "sem_element_map", "sem_lambda_max", "sem_diagonal", "sem_apply", "pmg_vcycle",
                  "laplace_solve", "laplace_solve_host"):
@@ -160,6 +173,8 @@ def sem_default_options(P: int, **overrides) -> SemOptions:
             o.outer = OUTER[v] if isinstance(v, str) else int(v)
         elif k == "precision":
             o.precision = PRECISION[v] if isinstance(v, str) else int(v)
+        elif k == "smoother":
+            o.smoother = SMOOTHER[v] if isinstance(v, str) else int(v)
         else:
             setattr(o, k, v)
     return o
@@ -266,6 +281,46 @@ def sem_cg_csr_noalloc(n: int, rowptr, col, vals, dinv, b, x, rtol: float, imax:
     return it.value
 
 
+def _mlp_shapes(h: int, hidden: int):
+    npe = sem_query(h, 0)["np"]
+    return {"W1": (hidden, npe), "b1": (hidden,), "W2": (npe, hidden), "b2": (npe,)}
+
+
+def sem_mlp_get_weights(h: int, hidden: int) -> dict:
+    out = {k: np.zeros(v, dtype=np.float32) for k, v in _mlp_shapes(h, hidden).items()}
+    fp = POINTER(ctypes.c_float)
+    _check(lib().sem_mlp_get_weights(h, *(out[k].ctypes.data_as(fp) for k in ("W1", "b1", "W2", "b2"))))
+    return out
+
+
+def sem_mlp_set_weights(h: int, W1, b1, W2, b2) -> None:
+    arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (W1, b1, W2, b2)]
+    fp = POINTER(ctypes.c_float)
+    _check(lib().sem_mlp_set_weights(h, *(a.ctypes.data_as(fp) for a in arrs)))
+
+
+def sem_mlp_forward(h: int, B: int, X, Y, stream=None) -> None:
+    _check(lib().sem_mlp_forward(h, int(B), _ptr(X), _ptr(Y), _stream(stream)))
+
+
+def sem_mlp_gradient(h: int, hidden: int, B: int, X, T, stream=None):
+    """(loss, dict of gradients shaped like the weights)."""
+    g = {k: np.zeros(v, dtype=np.float32) for k, v in _mlp_shapes(h, hidden).items()}
+    loss = c_double(0.0)
+    fp = POINTER(ctypes.c_float)
+    _check(lib().sem_mlp_gradient(h, int(B), _ptr(X), _ptr(T), byref(loss),
+                                  *(g[k].ctypes.data_as(fp) for k in ("W1", "b1", "W2", "b2")), _stream(stream)))
+    return loss.value, g
+
+
+def sem_learned_train(h: int, snapshots: int, steps: int, lr: float = 1e-3, seed: int = 1, stream=None):
+    """(loss of the first step, loss of the last step)."""
+    l0, l1 = c_double(0.0), c_double(0.0)
+    _check(lib().sem_learned_train(h, int(snapshots), int(steps), float(lr), ctypes.c_ulonglong(seed), byref(l0),
+                                   byref(l1), _stream(stream)))
+    return l0.value, l1.value
+
+
 def sem_last_error() -> str:
     return lib().sem_last_error().decode()
 
@@ -323,3 +378,19 @@ class Solver:
 
     def solve_host(self, dirichlet_eta, phi, tol=0.0, rhs=None, stream=None):
         return laplace_solve_host(self.h, rhs, dirichlet_eta, tol, phi, stream)
+
+    # correction network of the learned smoothing sweep (smoother="learned")
+    def mlp_weights(self):
+        return sem_mlp_get_weights(self.h, self.opts.mlp_hidden)
+
+    def set_mlp_weights(self, W1, b1, W2, b2):
+        sem_mlp_set_weights(self.h, W1, b1, W2, b2)
+
+    def mlp_gradient(self, B, X, T, stream=None):
+        return sem_mlp_gradient(self.h, self.opts.mlp_hidden, B, X, T, stream)
+
+    def mlp_forward(self, B, X, Y, stream=None):
+        sem_mlp_forward(self.h, B, X, Y, stream)
+
+    def train(self, snapshots, steps, lr=1e-3, seed=1, stream=None):
+        return sem_learned_train(self.h, snapshots, steps, lr, seed, stream)

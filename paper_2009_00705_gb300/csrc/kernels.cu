@@ -1143,7 +1143,8 @@ __global__ void k_scale(long long n, const double* __restrict__ w, const double*
 // ------------------------------------------------------------------ element-wise vector kernels
 template <typename T>
 __global__ void k_cheb_first(long long n, T c, const T* __restrict__ dinv, const T* __restrict__ f,
-                             T* __restrict__ u, T* __restrict__ d) {
+                             T* __restrict__ u, T* __restrict__ d, const int* __restrict__ skip) {
+    if (skip != nullptr && *skip) return;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const T v = c * dinv[i] * f[i];
         d[i] = v;
@@ -1153,7 +1154,9 @@ __global__ void k_cheb_first(long long n, T c, const T* __restrict__ dinv, const
 
 template <typename T>
 __global__ void k_cheb_restart(long long n, T c, const T* __restrict__ dinv, const T* __restrict__ f,
-                               const T* __restrict__ y, T* __restrict__ u, T* __restrict__ d) {
+                               const T* __restrict__ y, T* __restrict__ u, T* __restrict__ d,
+                               const int* __restrict__ skip) {
+    if (skip != nullptr && *skip) return;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const T v = c * dinv[i] * (f[i] - y[i]);
         d[i] = v;
@@ -1163,7 +1166,9 @@ __global__ void k_cheb_restart(long long n, T c, const T* __restrict__ dinv, con
 
 template <typename T>
 __global__ void k_cheb_step(long long n, T c1, T c2, const T* __restrict__ dinv, const T* __restrict__ f,
-                            const T* __restrict__ y, T* __restrict__ u, T* __restrict__ d) {
+                            const T* __restrict__ y, T* __restrict__ u, T* __restrict__ d,
+                            const int* __restrict__ skip) {
+    if (skip != nullptr && *skip) return;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const T v = c1 * d[i] + c2 * dinv[i] * (f[i] - y[i]);
         d[i] = v;
@@ -1213,8 +1218,8 @@ cudaError_t launch_apply64(const Level& L, const double* x, double* y, bool lift
                 : apply_dispatch<double, false>(L, L.ref64.m, L.G, x, y, skip, s);
 }
 
-cudaError_t launch_apply32(const Level& L, const float* x, float* y, cudaStream_t s) {
-    return apply_dispatch<float, false>(L, L.ref32.m, L.G32, x, y, nullptr, s);
+cudaError_t launch_apply32(const Level& L, const float* x, float* y, cudaStream_t s, const int* skip) {
+    return apply_dispatch<float, false>(L, L.ref32.m, L.G32, x, y, skip, s);
 }
 
 cudaError_t launch_geometry(Level& L, const double* vtri, const double* etaP, const double* BP, const double* DrP,
@@ -1283,30 +1288,34 @@ cudaError_t launch_prolong32(const Level& F, const Level& C, const float* uc, fl
 }
 
 template <typename T>
-cudaError_t cheb_first(long long n, T c, const T* dinv, const T* f, T* u, T* d, cudaStream_t s) {
-    k_cheb_first<T><<<vec_grid(n), kVecThreads, 0, s>>>(n, c, dinv, f, u, d);
+cudaError_t cheb_first(long long n, T c, const T* dinv, const T* f, T* u, T* d, cudaStream_t s, const int* skip) {
+    k_cheb_first<T><<<vec_grid(n), kVecThreads, 0, s>>>(n, c, dinv, f, u, d, skip);
     return cudaGetLastError();
 }
 template <typename T>
-cudaError_t cheb_restart(long long n, T c, const T* dinv, const T* f, const T* y, T* u, T* d, cudaStream_t s) {
-    k_cheb_restart<T><<<vec_grid(n), kVecThreads, 0, s>>>(n, c, dinv, f, y, u, d);
+cudaError_t cheb_restart(long long n, T c, const T* dinv, const T* f, const T* y, T* u, T* d, cudaStream_t s,
+                         const int* skip) {
+    k_cheb_restart<T><<<vec_grid(n), kVecThreads, 0, s>>>(n, c, dinv, f, y, u, d, skip);
     return cudaGetLastError();
 }
 template <typename T>
-cudaError_t cheb_step(long long n, T c1, T c2, const T* dinv, const T* f, const T* y, T* u, T* d, cudaStream_t s) {
-    k_cheb_step<T><<<vec_grid(n), kVecThreads, 0, s>>>(n, c1, c2, dinv, f, y, u, d);
+cudaError_t cheb_step(long long n, T c1, T c2, const T* dinv, const T* f, const T* y, T* u, T* d, cudaStream_t s,
+                      const int* skip) {
+    k_cheb_step<T><<<vec_grid(n), kVecThreads, 0, s>>>(n, c1, c2, dinv, f, y, u, d, skip);
     return cudaGetLastError();
 }
-template cudaError_t cheb_first<double>(long long, double, const double*, const double*, double*, double*, cudaStream_t);
-template cudaError_t cheb_first<float>(long long, float, const float*, const float*, float*, float*, cudaStream_t);
+template cudaError_t cheb_first<double>(long long, double, const double*, const double*, double*, double*, cudaStream_t,
+                                        const int*);
+template cudaError_t cheb_first<float>(long long, float, const float*, const float*, float*, float*, cudaStream_t,
+                                       const int*);
 template cudaError_t cheb_restart<double>(long long, double, const double*, const double*, const double*, double*,
-                                          double*, cudaStream_t);
+                                          double*, cudaStream_t, const int*);
 template cudaError_t cheb_restart<float>(long long, float, const float*, const float*, const float*, float*, float*,
-                                         cudaStream_t);
+                                         cudaStream_t, const int*);
 template cudaError_t cheb_step<double>(long long, double, double, const double*, const double*, const double*,
-                                       double*, double*, cudaStream_t);
+                                       double*, double*, cudaStream_t, const int*);
 template cudaError_t cheb_step<float>(long long, float, float, const float*, const float*, const float*, float*,
-                                      float*, cudaStream_t);
+                                      float*, cudaStream_t, const int*);
 
 cudaError_t dot64(long long n, const double* a, const double* b, Scratch& sc, double* out, cudaStream_t s) {
     k_dot<<<reduce_blocks(), kRedThreads, 0, s>>>(n, a, b, sc.part, sc.counter, out);

@@ -1,0 +1,46 @@
+// Per-element correction network (learned smoothing sweep): device buffers and launchers.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace sem {
+
+enum { EPI_STORE = 0, EPI_BIAS = 1, EPI_BIAS_RELU = 2, EPI_ATOMIC = 3 };
+
+// y = W2 relu(W1 x + b1) + b2; W1 [H][nin], W2 [nout][H] (FP32 masters + BF16 copies used by the GEMMs)
+struct MlpNet {
+    int nin = 0, H = 0, nout = 0;
+    float *W1 = nullptr, *b1 = nullptr, *W2 = nullptr, *b2 = nullptr;
+    __nv_bfloat16 *W1b = nullptr, *W2b = nullptr;
+};
+
+struct MlpGrads {
+    float *dW1 = nullptr, *db1 = nullptr, *dW2 = nullptr, *db2 = nullptr;
+};
+
+struct MlpAdam {
+    float* m[4] = {};
+    float* v[4] = {};
+    long long t = 0;
+};
+
+// A1, H1: [B][H]; Y: [B][nout]
+cudaError_t mlp_forward(const MlpNet& net, int B, const float* X, float* A1, float* H1, float* Y, cudaStream_t s);
+// loss = sum ||Y - T||^2 / B (device double); gradients into g.  dY [B][nout], dH [B][H] are work buffers.
+cudaError_t mlp_backward(const MlpNet& net, int B, const float* X, const float* T, float* A1, float* H1, float* Y,
+                         float* dY, float* dH, MlpGrads& g, double* loss, cudaStream_t s);
+cudaError_t mlp_adam(MlpNet& net, const MlpGrads& g, MlpAdam& st, float lr, cudaStream_t s);
+cudaError_t mlp_sync_bf16(MlpNet& net, cudaStream_t s);
+template <typename V>
+cudaError_t gather_scaled(int E, int Np, const int* map, const V* r, const V* t, float* X, float* T, float* scale,
+                          cudaStream_t s);
+cudaError_t scatter_correction(int E, int Np, const int* map, const float* w, const float* Y, const float* scale,
+                               float* d, cudaStream_t s);
+cudaError_t mul32(long long n, const float* a, const float* b, float* out, cudaStream_t s);
+cudaError_t axpby32(long long n, const float* a, const float* b, float sign, float* out, cudaStream_t s);
+cudaError_t judge(const double* rr_old, const double* rr_new, int* flags, int accept_idx, int count_idx,
+                  cudaStream_t s);
+cudaError_t commit32(long long n, const int* flags, int idx, const float* src, float* dst, cudaStream_t s);
+cudaError_t random_free(long long n, unsigned long long seed, const float* dinv, float* v, cudaStream_t s);
+
+}  // namespace sem

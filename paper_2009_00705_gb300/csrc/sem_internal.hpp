@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "../../include/sem.h"
+#include "mlp.hpp"
 #include "refelem.hpp"
 
 namespace sem {
@@ -88,6 +89,16 @@ struct sem_handle {
     // inner FP32 PCG of the mixed-precision path (finest level)
     float *ir = nullptr, *iz = nullptr, *ip = nullptr, *iq = nullptr, *ie = nullptr;
     long long inner_iters = 0;
+    // learned smoothing sweep (per-element correction network) on the finest level
+    sem::MlpNet net;
+    sem::MlpGrads grads;
+    sem::MlpAdam adam;
+    float *mX = nullptr, *mT = nullptr, *mA1 = nullptr, *mH1 = nullptr, *mY = nullptr, *mdY = nullptr, *mdH = nullptr;
+    float* mscale = nullptr;
+    float *lr32 = nullptr, *ld32 = nullptr, *lu32 = nullptr;        // sweep work vectors
+    float *te0 = nullptr, *tf = nullptr, *tu = nullptr, *tz = nullptr; // training data generation
+    bool mlp_trained = false;
+    bool learned_active = true;
     // staging buffers of laplace_solve_host
     double *st_eta = nullptr, *st_rhs = nullptr, *st_phi = nullptr;
     // host geometry copies for coordinate queries
@@ -113,7 +124,7 @@ namespace sem {
 int reduce_blocks();
 cudaError_t launch_apply64(const Level& L, const double* x, double* y, bool lift, const int* skip,
                            cudaStream_t s);
-cudaError_t launch_apply32(const Level& L, const float* x, float* y, cudaStream_t s);
+cudaError_t launch_apply32(const Level& L, const float* x, float* y, cudaStream_t s, const int* skip = nullptr);
 cudaError_t launch_geometry(Level& L, const double* vtri, const double* etaP, const double* BP,
                             const double* DrP, const double* DsP, int NTP, int nlayers, double depth,
                             cudaStream_t s);
@@ -126,13 +137,16 @@ cudaError_t launch_prolong64(const Level& F, const Level& C, const double* uc, d
 cudaError_t launch_prolong32(const Level& F, const Level& C, const float* uc, float* uf, cudaStream_t s);
 
 // vector kernels (n = vector length)
+// skip (optional): a device flag; when it is set the kernel does nothing
 template <typename T>
-cudaError_t cheb_first(long long n, T c, const T* dinv, const T* f, T* u, T* d, cudaStream_t s);
+cudaError_t cheb_first(long long n, T c, const T* dinv, const T* f, T* u, T* d, cudaStream_t s,
+                       const int* skip = nullptr);
 template <typename T>
-cudaError_t cheb_restart(long long n, T c, const T* dinv, const T* f, const T* y, T* u, T* d, cudaStream_t s);
+cudaError_t cheb_restart(long long n, T c, const T* dinv, const T* f, const T* y, T* u, T* d, cudaStream_t s,
+                         const int* skip = nullptr);
 template <typename T>
 cudaError_t cheb_step(long long n, T c1, T c2, const T* dinv, const T* f, const T* y, T* u, T* d,
-                      cudaStream_t s);
+                      cudaStream_t s, const int* skip = nullptr);
 cudaError_t dot64(long long n, const double* a, const double* b, Scratch& sc, double* out, cudaStream_t s);
 cudaError_t residual64(long long n, const double* f, const double* y, double* r, Scratch& sc, double* rr,
                        cudaStream_t s);
@@ -174,9 +188,9 @@ cudaError_t coarse_cg_persistent(const Level& C, const int* rowptr, const int* c
 enum {
     S_RR = 0, S_PQ = 1, S_DELTA0 = 2, S_DELTA1 = 3, S_FF = 4, S_TMP = 5,
     S_CG_RHO = 8, S_CG_PQ = 9, S_CG_RR = 10, S_CG_TOL2 = 11, S_CG_RHONEW = 12, S_CG_BETA = 13,
-    S_IRR = 6, S_IPQ = 7, S_IDELTA0 = 14, S_IDELTA1 = 15,
+    S_IRR = 6, S_IPQ = 7, S_IDELTA0 = 14, S_IDELTA1 = 15, S_L0 = 100, S_L1 = 101, S_LOSS = 102,
     S_MULTI = 16                    // FGMRES dots start here (up to 64 + 1)
 };
-enum { F_CG_DONE = 0, F_CG_ITERS = 1 };
+enum { F_CG_DONE = 0, F_CG_ITERS = 1, F_LEARN_ACCEPT = 2, F_LEARN_COUNT = 3 /* +0 accepts, +1 fallbacks */ };
 
 }  // namespace sem

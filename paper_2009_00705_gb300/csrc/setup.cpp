@@ -9,6 +9,7 @@
 #include <cstdint>
 #include <cstring>
 #include <string>
+#include <random>
 #include <unordered_map>
 #include <vector>
 
@@ -390,6 +391,50 @@ sem_status build_workspace(sem_handle* h) {
         h->ev.resize(512);
         for (auto& e : h->ev) CK(cudaEventCreate(&e));
     }
+    return SEM_OK;
+}
+
+// Correction network, its Adam state and the buffers of the learned sweep and its
+// training (finest level), allocated when smoother = LEARNED.  Initial weights:
+// Glorot-uniform W1, W2 scaled by 0.1 (a small first correction), zero biases.
+sem_status build_mlp(sem_handle* h) {
+    if (h->opts.smoother != SEM_SMOOTH_LEARNED) return SEM_OK;
+    const Level& L = h->lv[0];
+    MlpNet& n = h->net;
+    n.nin = n.nout = L.Np;
+    n.H = h->opts.mlp_hidden;
+    const size_t n1 = (size_t)n.H * n.nin, n2 = (size_t)n.nout * n.H;
+    std::mt19937_64 rng(h->opts.mlp_seed);
+    std::uniform_real_distribution<double> U(-1.0, 1.0);
+    const double a1 = std::sqrt(6.0 / (n.nin + n.H)), a2 = 0.1 * std::sqrt(6.0 / (n.nout + n.H));
+    std::vector<float> W1(n1), W2(n2), b1(n.H, 0.f), b2(n.nout, 0.f);
+    for (auto& w : W1) w = (float)(a1 * U(rng));
+    for (auto& w : W2) w = (float)(a2 * U(rng));
+    CK(upload(&n.W1, W1));
+    CK(upload(&n.W2, W2));
+    CK(upload(&n.b1, b1));
+    CK(upload(&n.b2, b2));
+    CK(dalloc(&n.W1b, n1));
+    CK(dalloc(&n.W2b, n2));
+    CK(mlp_sync_bf16(n, 0));
+    MlpGrads& g = h->grads;
+    CK(dalloc(&g.dW1, n1));
+    CK(dalloc(&g.dW2, n2));
+    CK(dalloc(&g.db1, n.H));
+    CK(dalloc(&g.db2, n.nout));
+    const size_t sizes[4] = {n1, (size_t)n.H, n2, (size_t)n.nout};
+    for (int k = 0; k < 4; ++k) {
+        CK(dalloc(&h->adam.m[k], sizes[k]));
+        CK(dalloc(&h->adam.v[k], sizes[k]));
+        CK(cudaMemset(h->adam.m[k], 0, sizeof(float) * sizes[k]));
+        CK(cudaMemset(h->adam.v[k], 0, sizeof(float) * sizes[k]));
+    }
+    const size_t ep = (size_t)L.E * L.Np, eh = (size_t)L.E * n.H;
+    for (float** v : {&h->mX, &h->mT, &h->mY, &h->mdY}) CK(dalloc(v, ep));
+    for (float** v : {&h->mA1, &h->mH1, &h->mdH}) CK(dalloc(v, eh));
+    CK(dalloc(&h->mscale, L.E));
+    for (float** v : {&h->lr32, &h->ld32, &h->lu32, &h->te0, &h->tf, &h->tu, &h->tz}) CK(dalloc(v, L.N));
+    CK(cudaDeviceSynchronize());
     return SEM_OK;
 }
 

@@ -23,6 +23,7 @@ sem_status build_geometry(sem_handle* h, const sem_mesh* m);
 sem_status build_diagonals(sem_handle* h);
 sem_status build_transfers(sem_handle* h);
 sem_status build_coarse_gradients(sem_handle* h);
+sem_status build_mlp(sem_handle* h);
 sem_status build_workspace(sem_handle* h);
 }  // namespace sem
 
@@ -91,10 +92,11 @@ sem_status apply_level64(sem_handle* h, int li, const double* x, double* y, bool
     return SEM_OK;
 }
 
-sem_status apply_level32(sem_handle* h, int li, const float* x, float* y, cudaStream_t s) {
+sem_status apply_level32(sem_handle* h, int li, const float* x, float* y, cudaStream_t s,
+                         const int* skip = nullptr) {
     const Level& L = h->lv[li];
     CKS(cudaMemsetAsync(y, 0, sizeof(float) * L.N, s));
-    K(launch_apply32(L, x, y, s));
+    K(launch_apply32(L, x, y, s, skip));
     if (li == 0) h->fine_applies += 1;
     return SEM_OK;
 }
@@ -156,10 +158,12 @@ sem_status coarse_solve(sem_handle* h, const double* b, double* x, cudaStream_t 
 
 // One Chebyshev-Jacobi sweep of level li (u = 0 on entry when zero_init).
 template <typename T>
-sem_status smooth(sem_handle* h, int li, const T* f, T* u, bool zero_init, cudaStream_t s);
+sem_status smooth(sem_handle* h, int li, const T* f, T* u, bool zero_init, cudaStream_t s,
+                  const int* skip = nullptr);
 
 template <>
-sem_status smooth<double>(sem_handle* h, int li, const double* f, double* u, bool zero_init, cudaStream_t s) {
+sem_status smooth<double>(sem_handle* h, int li, const double* f, double* u, bool zero_init, cudaStream_t s,
+                          const int*) {
     const Level& L = h->lv[li];
     const Cheb c = cheb_coeffs(L.lam, h->opts);
     if (zero_init) {
@@ -176,20 +180,47 @@ sem_status smooth<double>(sem_handle* h, int li, const double* f, double* u, boo
 }
 
 template <>
-sem_status smooth<float>(sem_handle* h, int li, const float* f, float* u, bool zero_init, cudaStream_t s) {
+sem_status smooth<float>(sem_handle* h, int li, const float* f, float* u, bool zero_init, cudaStream_t s,
+                         const int* skip) {
     const Level& L = h->lv[li];
     const Cheb c = cheb_coeffs(L.lam, h->opts);
     if (zero_init) {
-        K(cheb_first<float>(L.N, (float)c.c0, L.dinv32, f, u, L.d32, s));
+        K(cheb_first<float>(L.N, (float)c.c0, L.dinv32, f, u, L.d32, s, skip));
     } else {
-        CKST(apply_level32(h, li, u, L.y32, s));
-        K(cheb_restart<float>(L.N, (float)c.c0, L.dinv32, f, L.y32, u, L.d32, s));
+        CKST(apply_level32(h, li, u, L.y32, s, skip));
+        K(cheb_restart<float>(L.N, (float)c.c0, L.dinv32, f, L.y32, u, L.d32, s, skip));
     }
     for (int j = 1; j < h->opts.k_cheb; ++j) {
-        CKST(apply_level32(h, li, u, L.y32, s));
-        K(cheb_step<float>(L.N, (float)c.c1[j], (float)c.c2[j], L.dinv32, f, L.y32, u, L.d32, s));
+        CKST(apply_level32(h, li, u, L.y32, s, skip));
+        K(cheb_step<float>(L.N, (float)c.c1[j], (float)c.c2[j], L.dinv32, f, L.y32, u, L.d32, s, skip));
     }
     return SEM_OK;
+}
+
+// The learned sweep that stands in for the first finest-level post-smoothing sweep:
+// u_try = u + W sum_e Q_e^T s_e MLP(z_e / s_e), z = D^{-1}(f - A u), s_e = ||z_e||.
+// It is kept only if it lowers the residual norm; otherwise the Chebyshev sweep it
+// replaces runs instead (its kernels are predicated on the device-side verdict).
+sem_status learned_sweep(sem_handle* h, const float* f, float* u, cudaStream_t s) {
+    Level& L = h->lv[0];
+    const long long N = L.N;
+    Scratch& sc = h->sc;
+    CKST(apply_level32(h, 0, u, L.y32, s));
+    K(axpby32(N, f, L.y32, -1.f, h->lr32, s));
+    K(dot32(N, h->lr32, h->lr32, sc, sc.scal + S_L0, s));
+    K(mul32(N, L.dinv32, h->lr32, h->ld32, s));
+    K(gather_scaled<float>(L.E, L.Np, L.map, h->ld32, (const float*)nullptr, h->mX, nullptr, h->mscale, s));
+    CKS(mlp_forward(h->net, L.E, h->mX, h->mA1, h->mH1, h->mY, s));
+    h->launches += 2;
+    CKS(cudaMemsetAsync(h->ld32, 0, sizeof(float) * N, s));
+    K(scatter_correction(L.E, L.Np, L.map, L.wmult32, h->mY, h->mscale, h->ld32, s));
+    K(axpby32(N, u, h->ld32, 1.f, h->lu32, s));
+    CKST(apply_level32(h, 0, h->lu32, L.y32, s));
+    K(axpby32(N, f, L.y32, -1.f, h->lr32, s));
+    K(dot32(N, h->lr32, h->lr32, sc, sc.scal + S_L1, s));
+    K(judge(sc.scal + S_L0, sc.scal + S_L1, sc.flags, F_LEARN_ACCEPT, F_LEARN_COUNT, s));
+    K(commit32(N, sc.flags, F_LEARN_ACCEPT, h->lu32, u, s));
+    return smooth<float>(h, 0, f, u, false, s, sc.flags + F_LEARN_ACCEPT);
 }
 
 // Algorithm 1 with zero initial guess on every level, FP64 throughout.
@@ -253,7 +284,11 @@ sem_status vcycle32(sem_handle* h, const float* f0, float* u0, cudaStream_t s) {
         const float* f = (li == 0) ? f0 : L.f32;
         float* u = (li == 0) ? u0 : L.u32;
         K(launch_prolong32(L, C, C.u32, u, s));
-        for (int m = 0; m < h->opts.nu2; ++m) CKST(smooth<float>(h, li, f, u, false, s));
+        const bool learned = (li == 0) && h->opts.smoother == SEM_SMOOTH_LEARNED && h->mlp_trained && h->learned_active;
+        for (int m = 0; m < h->opts.nu2; ++m) {
+            if (learned && m == 0) CKST(learned_sweep(h, f, u, s));
+            else CKST(smooth<float>(h, li, f, u, false, s));
+        }
     }
     return SEM_OK;
 }
@@ -385,6 +420,11 @@ sem_status check_options(const sem_options& o, int P) {
     if (o.outer < 0 || o.outer > 2 || o.precision < 0 || o.precision > 1) { set_error("outer/precision"); return SEM_EINVAL; }
     if (o.outer == SEM_OUTER_FGMRES && (o.gmres_m < 1 || o.gmres_m > 64)) { set_error("gmres_m in 1..64"); return SEM_EINVAL; }
     if (o.imax < 0 || o.coarse_imax < 1 || !(o.coarse_rtol > 0)) { set_error("iteration limits"); return SEM_EINVAL; }
+    if (o.smoother != SEM_SMOOTH_CHEBYSHEV && o.smoother != SEM_SMOOTH_LEARNED) { set_error("smoother"); return SEM_EINVAL; }
+    if (o.smoother == SEM_SMOOTH_LEARNED && (o.precision != SEM_PREC_MIXED_FP32 || o.mlp_hidden < 1 || o.mlp_hidden > 4096)) {
+        set_error("the learned smoother needs precision = MIXED_FP32 and 1 <= mlp_hidden <= 4096");
+        return SEM_EINVAL;
+    }
     if (o.inner_imax < 0 || (o.inner_imax > 0 && !(o.inner_rtol > 0 && o.inner_rtol < 1))) {
         set_error("inner_imax >= 0 and 0 < inner_rtol < 1");
         return SEM_EINVAL;
@@ -572,6 +612,9 @@ void sem_default_options(sem_options* o, int P) {
     o->inner_imax = 0;
     o->inner_rtol = 1e-4;
     o->debug_barrier_extra = 0;
+    o->smoother = SEM_SMOOTH_CHEBYSHEV;
+    o->mlp_hidden = 256;
+    o->mlp_seed = 20090705ULL;
 }
 
 sem_status sem_mesh_nodes2d(const sem_mesh* m, int p, long long* n2, double* xy) {
@@ -618,6 +661,7 @@ sem_status sem_setup(const sem_mesh* m, int P, const sem_options* opts, sem_hand
     if (st == SEM_OK) st = build_diagonals(h);
     if (st == SEM_OK) st = build_transfers(h);
     if (st == SEM_OK) st = build_coarse_gradients(h);
+    if (st == SEM_OK) st = build_mlp(h);
     if (st == SEM_OK) st = build_workspace(h);
     for (int li = 0; li + 1 < o.nlevels && st == SEM_OK; ++li) st = estimate_lambda(h, li);
     if (st == SEM_OK) {
@@ -638,7 +682,11 @@ void sem_destroy(sem_handle* h) {
     for (Level& L : h->lv) free_level(L);
     void* ptrs[] = {h->sc.part, h->sc.counter, h->sc.scal, h->sc.flags, h->r, h->z, h->p, h->q, h->x, h->fr,
                     h->V, h->Zb, h->cx, h->cr, h->cz, h->cp, h->cq, h->cb, h->st_eta, h->st_rhs, h->st_phi,
-                    h->ir, h->iz, h->ip, h->iq, h->ie, h->gm_y};
+                    h->ir, h->iz, h->ip, h->iq, h->ie, h->gm_y, h->net.W1, h->net.b1, h->net.W2, h->net.b2,
+                    h->net.W1b, h->net.W2b, h->grads.dW1, h->grads.db1, h->grads.dW2, h->grads.db2,
+                    h->adam.m[0], h->adam.m[1], h->adam.m[2], h->adam.m[3], h->adam.v[0], h->adam.v[1],
+                    h->adam.v[2], h->adam.v[3], h->mX, h->mT, h->mA1, h->mH1, h->mY, h->mdY, h->mdH, h->mscale,
+                    h->lr32, h->ld32, h->lu32, h->te0, h->tf, h->tu, h->tz};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->sc.hpinned) cudaFreeHost(h->sc.hpinned);
@@ -761,6 +809,7 @@ sem_status laplace_solve(sem_handle* h, const double* rhs, const double* eta, do
     h->apply_launches = 0;
     h->launches = 0;
     h->inner_iters = 0;
+    CKS(cudaMemsetAsync(h->sc.flags + F_LEARN_COUNT, 0, 2 * sizeof(int), s));
     h->ev_used = 0;
     cudaEvent_t e0, e1;
     CKS(cudaEventCreate(&e0));
@@ -809,6 +858,12 @@ sem_status laplace_solve(sem_handle* h, const double* rhs, const double* eta, do
     st.apply_launches = h->apply_launches;
     st.kernel_launches = h->launches;
     st.inner_iters = h->inner_iters;
+    if (h->opts.smoother == SEM_SMOOTH_LEARNED) {
+        int cnt[2] = {0, 0};
+        CKS(cudaMemcpy(cnt, h->sc.flags + F_LEARN_COUNT, 2 * sizeof(int), cudaMemcpyDeviceToHost));
+        st.learned_accepts = cnt[0];
+        st.learned_fallbacks = cnt[1];
+    }
     st.q_mean = (st.iters > 0 && st.res0 > 0) ? std::pow(st.res_final / st.res0, 1.0 / st.iters) : 0.0;
     if (stats) *stats = st;
     return ret;
@@ -825,6 +880,113 @@ sem_status laplace_solve_host(sem_handle* h, const double* rhs_host, const doubl
     const sem_status ret = laplace_solve(h, rhs_host ? h->st_rhs : nullptr, h->st_eta, tol, h->st_phi, stats, stream);
     CKS(cudaMemcpyAsync(phi_host, h->st_phi, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
     CKS(cudaStreamSynchronize(s));
+    return ret;
+}
+
+static sem_status check_mlp(const sem_handle* h) {
+    if (!h) { set_error("handle is NULL"); return SEM_EINVAL; }
+    if (h->opts.smoother != SEM_SMOOTH_LEARNED || !h->net.W1) {
+        set_error("the handle has no correction network (smoother != SEM_SMOOTH_LEARNED)");
+        return SEM_EINVAL;
+    }
+    return SEM_OK;
+}
+
+sem_status sem_mlp_get_weights(const sem_handle* h, float* W1, float* b1, float* W2, float* b2) {
+    CKST(check_mlp(h));
+    const MlpNet& n = h->net;
+    if (W1) CKS(cudaMemcpy(W1, n.W1, sizeof(float) * n.H * n.nin, cudaMemcpyDeviceToHost));
+    if (b1) CKS(cudaMemcpy(b1, n.b1, sizeof(float) * n.H, cudaMemcpyDeviceToHost));
+    if (W2) CKS(cudaMemcpy(W2, n.W2, sizeof(float) * n.nout * n.H, cudaMemcpyDeviceToHost));
+    if (b2) CKS(cudaMemcpy(b2, n.b2, sizeof(float) * n.nout, cudaMemcpyDeviceToHost));
+    return SEM_OK;
+}
+
+sem_status sem_mlp_set_weights(sem_handle* h, const float* W1, const float* b1, const float* W2, const float* b2) {
+    CKST(check_mlp(h));
+    MlpNet& n = h->net;
+    if (!W1 || !b1 || !W2 || !b2) { set_error("sem_mlp_set_weights: NULL array"); return SEM_EINVAL; }
+    CKS(cudaMemcpy(n.W1, W1, sizeof(float) * n.H * n.nin, cudaMemcpyHostToDevice));
+    CKS(cudaMemcpy(n.b1, b1, sizeof(float) * n.H, cudaMemcpyHostToDevice));
+    CKS(cudaMemcpy(n.W2, W2, sizeof(float) * n.nout * n.H, cudaMemcpyHostToDevice));
+    CKS(cudaMemcpy(n.b2, b2, sizeof(float) * n.nout, cudaMemcpyHostToDevice));
+    CKS(mlp_sync_bf16(n, 0));
+    CKS(cudaDeviceSynchronize());
+    h->mlp_trained = true;        // weights supplied by the caller (e.g. a checkpoint)
+    return SEM_OK;
+}
+
+sem_status sem_mlp_forward(sem_handle* h, int B, const float* X, float* Y, void* stream) {
+    CKST(check_mlp(h));
+    if (B < 1 || B > h->lv[0].E || !X || !Y) { set_error("sem_mlp_forward: need 1 <= B <= elements"); return SEM_EINVAL; }
+    CKS(mlp_forward(h->net, B, X, h->mA1, h->mH1, Y, as_stream(stream)));
+    return SEM_OK;
+}
+
+sem_status sem_mlp_gradient(sem_handle* h, int B, const float* X, const float* T, double* loss, float* dW1,
+                            float* db1, float* dW2, float* db2, void* stream) {
+    CKST(check_mlp(h));
+    if (B < 1 || B > h->lv[0].E || !X || !T) { set_error("sem_mlp_gradient: need 1 <= B <= elements"); return SEM_EINVAL; }
+    cudaStream_t s = as_stream(stream);
+    const MlpNet& n = h->net;
+    CKS(mlp_forward(n, B, X, h->mA1, h->mH1, h->mY, s));
+    CKS(mlp_backward(n, B, X, T, h->mA1, h->mH1, h->mY, h->mdY, h->mdH, h->grads, h->sc.scal + S_LOSS, s));
+    CKS(cudaStreamSynchronize(s));
+    if (loss) CKS(cudaMemcpy(loss, h->sc.scal + S_LOSS, sizeof(double), cudaMemcpyDeviceToHost));
+    if (dW1) CKS(cudaMemcpy(dW1, h->grads.dW1, sizeof(float) * n.H * n.nin, cudaMemcpyDeviceToHost));
+    if (db1) CKS(cudaMemcpy(db1, h->grads.db1, sizeof(float) * n.H, cudaMemcpyDeviceToHost));
+    if (dW2) CKS(cudaMemcpy(dW2, h->grads.dW2, sizeof(float) * n.nout * n.H, cudaMemcpyDeviceToHost));
+    if (db2) CKS(cudaMemcpy(db2, h->grads.db2, sizeof(float) * n.nout, cudaMemcpyDeviceToHost));
+    return SEM_OK;
+}
+
+sem_status sem_learned_train(sem_handle* h, int snapshots, int steps, double lr, unsigned long long seed,
+                             double* loss_first, double* loss_last, void* stream) {
+    CKST(check_mlp(h));
+    if (snapshots < 1 || steps < 1 || !(lr > 0)) { set_error("sem_learned_train: bad arguments"); return SEM_EINVAL; }
+    cudaStream_t s = as_stream(stream);
+    Level& L = h->lv[0];
+    const long long N = L.N;
+    h->learned_active = false;          // the plain V-cycle generates the data
+    double l0 = 0, l1 = 0;
+    sem_status ret = SEM_OK;
+    for (int sn = 0; sn < snapshots && ret == SEM_OK; ++sn) {
+        const unsigned long long sseed = seed * 0x9E3779B97F4A7C15ULL + (unsigned long long)sn * 0xD1B54A32D192ED03ULL;
+        K(random_free(N, sseed, L.dinv32, h->te0, s));
+        ret = apply_level32(h, 0, h->te0, h->tf, s);
+        if (ret != SEM_OK) break;
+        CKS(cudaMemsetAsync(h->tu, 0, sizeof(float) * N, s));
+        for (int k = 0; k < steps; ++k) {
+            if (k == 0) {
+                CKS(cudaMemcpyAsync(h->lr32, h->tf, sizeof(float) * N, cudaMemcpyDeviceToDevice, s));
+            } else {
+                CKST(apply_level32(h, 0, h->tu, L.y32, s));
+                K(axpby32(N, h->tf, L.y32, -1.f, h->lr32, s));
+            }
+            K(axpby32(N, h->te0, h->tu, -1.f, h->lu32, s));           // error e = e0 - u
+            K(mul32(N, L.dinv32, h->lr32, h->ld32, s));               // z = D^{-1} r
+            K(gather_scaled<float>(L.E, L.Np, L.map, h->ld32, h->lu32, h->mX, h->mT, h->mscale, s));
+            CKS(mlp_forward(h->net, L.E, h->mX, h->mA1, h->mH1, h->mY, s));
+            CKS(mlp_backward(h->net, L.E, h->mX, h->mT, h->mA1, h->mH1, h->mY, h->mdY, h->mdH, h->grads,
+                             h->sc.scal + S_LOSS, s));
+            CKS(mlp_adam(h->net, h->grads, h->adam, (float)lr, s));
+            if (sn == 0 && k == 0) {
+                CKST(read_scalars(h, S_LOSS, 1, s));
+                l0 = h->sc.hpinned[S_LOSS];
+            }
+            ret = vcycle32(h, h->lr32, h->tz, s);
+            if (ret != SEM_OK) break;
+            K(axpby32(N, h->tu, h->tz, 1.f, h->tu, s));
+        }
+    }
+    if (ret == SEM_OK) {
+        CKST(read_scalars(h, S_LOSS, 1, s));
+        l1 = h->sc.hpinned[S_LOSS];
+        h->mlp_trained = true;
+    }
+    h->learned_active = true;
+    if (loss_first) *loss_first = l0;
+    if (loss_last) *loss_last = l1;
     return ret;
 }
 

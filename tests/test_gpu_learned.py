@@ -1,0 +1,116 @@
+"""The learned smoothing sweep: network forward/gradients against the FP64 oracle,
+training on solver-generated residual/error pairs, the residual judge with its
+Chebyshev fallback, and what the trained network gains over the plain method."""
+import time
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import mlp as M  # noqa: E402
+from oracle import solvers as S  # noqa: E402
+from oracle.assemble import Problem  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def sem():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2009_00705_gb300 as pkg
+    from paper_2009_00705_gb300 import build as B
+    B.build()
+    return pkg
+
+
+def _solver(sem, mesh, levels, **opts):
+    prob = Problem(mesh, levels)
+    o = dict(levels=levels, precision="mixed_fp32", smoother="learned", outer="fgmres")
+    o.update(opts)
+    return prob, sem.Solver(mesh, levels[0], eta_nodal=prob.eta_nodal, **o)
+
+
+@pytest.mark.parametrize("levels,hidden,mesh_fn", [([4, 2, 1], 40, lambda: W.config_box3d(4, 2)),
+                                                    ([6, 3, 1], 256, lambda: W.config_box3d(3, 3))])
+def test_network_forward_and_gradients_match_the_oracle(sem, levels, hidden, mesh_fn):
+    prob, s = _solver(sem, mesh_fn(), levels, mlp_hidden=hidden)
+    npe = prob.levels[0].ref.Np
+    E = prob.levels[0].emap.shape[0]
+    rng = np.random.default_rng(17)
+    # bf16-representable weights: the library's GEMMs read W1, W2 as bf16
+    W1 = M.bf16_round(rng.standard_normal((hidden, npe)) * 0.2).astype(np.float32)
+    W2 = M.bf16_round(rng.standard_normal((npe, hidden)) * 0.2).astype(np.float32)
+    b1 = (rng.standard_normal(hidden) * 0.1).astype(np.float32)
+    b2 = (rng.standard_normal(npe) * 0.1).astype(np.float32)
+    s.set_mlp_weights(W1, b1, W2, b2)
+    B = E - 3                                        # a ragged batch
+    X = rng.standard_normal((B, npe)).astype(np.float32)
+    T = rng.standard_normal((B, npe)).astype(np.float32)
+    Xd, Td = torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda")
+    Y = torch.zeros((B, npe), dtype=torch.float32, device="cuda")
+    s.mlp_forward(B, Xd, Y)
+    args = [a.astype(np.float64) for a in (W1, b1, W2, b2)]
+    _, _, y_ref = M.forward(*args, X.astype(np.float64))
+    assert np.abs(Y.cpu().numpy() - y_ref).max() <= 1e-5 * np.abs(y_ref).max()
+    loss, g = s.mlp_gradient(B, Xd, Td)
+    loss_ref, (gW1, gb1, gW2, gb2) = M.loss_and_grads(*args, X.astype(np.float64), T.astype(np.float64))
+    assert abs(loss - loss_ref) <= 1e-5 * loss_ref
+    for got, ref in ((g["W1"], gW1), (g["b1"], gb1), (g["W2"], gW2), (g["b2"], gb2)):
+        assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max()
+    s.close()
+
+
+def test_checkpoint_round_trip(sem):
+    mesh = W.config_box3d(4, 2)
+    prob, s1 = _solver(sem, mesh, [4, 2, 1], mlp_hidden=32)
+    s1.train(1, 2, lr=1e-3, seed=5)
+    w = s1.mlp_weights()
+    _, s2 = _solver(sem, mesh, [4, 2, 1], mlp_hidden=32, mlp_seed=999)
+    s2.set_mlp_weights(w["W1"], w["b1"], w["W2"], w["b2"])
+    E, npe = prob.levels[0].emap.shape
+    X = torch.randn((E, npe), dtype=torch.float32, device="cuda")
+    Y1 = torch.zeros_like(X)
+    Y2 = torch.zeros_like(X)
+    s1.mlp_forward(E, X, Y1)
+    s2.mlp_forward(E, X, Y2)
+    assert torch.equal(Y1, Y2)
+    s1.close()
+    s2.close()
+
+
+def test_training_and_what_the_network_gains(sem):
+    mesh = W.config_box3d(8, 4)
+    levels = [6, 3, 1]
+    prob, learned = _solver(sem, mesh, levels, mlp_hidden=256, imax=300)
+    lev = prob.levels[0]
+    C = prob.coords(0)
+    phiD = W.potential3d(*C[lev.dirichlet].T)
+    l0, l1 = learned.train(snapshots=6, steps=6, lr=1e-3, seed=7)
+    assert l1 < l0, (l0, l1)
+    phi = torch.zeros(lev.N, dtype=torch.float64, device="cuda")
+    dD = torch.tensor(phiD, device="cuda")
+    learned.solve(dD, phi, tol=1e-10)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    st_l = learned.solve(dD, phi, tol=1e-10)
+    torch.cuda.synchronize()
+    t_l = time.perf_counter() - t
+    ref = S.solve_laplace_direct(prob, phiD)
+    err = np.abs(phi.cpu().numpy() - ref).max() / np.abs(ref).max()
+    assert st_l["status"] == 0 and err < 1e-8
+    assert st_l["learned_accepts"] + st_l["learned_fallbacks"] == st_l["vcycles"]
+    _, plain = _solver(sem, mesh, levels, smoother="chebyshev", imax=300)
+    plain.solve(dD, phi, tol=1e-10)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    st_p = plain.solve(dD, phi, tol=1e-10)
+    torch.cuda.synchronize()
+    t_p = time.perf_counter() - t
+    print(f"\nlearned sweep: loss {l0:.3e} -> {l1:.3e}; FGMRES iterations {st_l['iters']} (plain {st_p['iters']}), "
+          f"accepted {st_l['learned_accepts']}/{st_l['vcycles']} sweeps, time {t_l * 1e3:.1f} ms "
+          f"(plain {t_p * 1e3:.1f} ms), q {st_l['q_mean']:.3f} (plain {st_p['q_mean']:.3f})")
+    learned.close()
+    plain.close()
