@@ -214,11 +214,13 @@ sem_status sem_mlp_gradient(sem_handle* h, int B, const float* X_dev, const floa
                             float* dW1, float* db1, float* dW2, float* db2, void* stream);
 /* Train the network with Adam (learning rate lr) on residual/error pairs that the plain
  * solver generates: for each of `snapshots` seeded random errors e0 (SplitMix64 of
- * (seed, snapshot, node)), f = A e0, the plain FP32 V-cycle iteration u <- u + M r from
- * u = 0 runs `steps` times and every iterate gives one pair (r = f - A u, e = e0 - u),
- * every finest element of which is a training sample.  Nothing is stored: each pair is
- * one Adam step.  loss_first / loss_last (host, may be NULL) receive the loss of the first
- * and last step.  Synchronous. */
+ * (seed, snapshot, node)), the plain FP32 V-cycle iteration for A u = A e0 from u = 0
+ * runs `steps` times; at every iterate its error e = e0 - u is taken to the point where
+ * the replaced sweep acts, after the V-cycle's coarse-grid correction
+ * (e_post = e - P A_c^{-1} R A e), and (A e_post, e_post) is one pair, every finest
+ * element of which is a training sample.  Nothing is stored: each pair is one Adam
+ * step.  loss_first / loss_last (host, may be NULL) receive the loss on one fixed
+ * validation pair before and after training.  Synchronous. */
 sem_status sem_learned_train(sem_handle* h, int snapshots, int steps, double lr, unsigned long long seed,
                              double* loss_first, double* loss_last, void* stream);
 

@@ -99,6 +99,7 @@ struct sem_handle {
     float *te0 = nullptr, *tf = nullptr, *tu = nullptr, *tz = nullptr; // training data generation
     bool mlp_trained = false;
     bool learned_active = true;
+    bool cgc_only = false;          // FP32 V-cycle without finest-level smoothing (coarse-grid correction)
     // staging buffers of laplace_solve_host
     double *st_eta = nullptr, *st_rhs = nullptr, *st_phi = nullptr;
     // host geometry copies for coordinate queries

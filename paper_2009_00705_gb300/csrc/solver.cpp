@@ -268,9 +268,12 @@ sem_status vcycle32(sem_handle* h, const float* f0, float* u0, cudaStream_t s) {
         Level& C = h->lv[li + 1];
         const float* f = (li == 0) ? f0 : L.f32;
         float* u = (li == 0) ? u0 : L.u32;
-        for (int m = 0; m < h->opts.nu1; ++m) CKST(smooth<float>(h, li, f, u, m == 0, s));
-        if (h->opts.nu1 == 0) CKS(cudaMemsetAsync(u, 0, sizeof(float) * L.N, s));
-        CKST(apply_level32(h, li, u, L.y32, s));
+        const bool skip_fine = (li == 0) && h->cgc_only;
+        if (!skip_fine)
+            for (int m = 0; m < h->opts.nu1; ++m) CKST(smooth<float>(h, li, f, u, m == 0, s));
+        if (h->opts.nu1 == 0 || skip_fine) CKS(cudaMemsetAsync(u, 0, sizeof(float) * L.N, s));
+        if (skip_fine) CKS(cudaMemsetAsync(L.y32, 0, sizeof(float) * L.N, s));
+        else CKST(apply_level32(h, li, u, L.y32, s));
         CKS(cudaMemsetAsync(C.f32, 0, sizeof(float) * C.N, s));
         K(launch_restrict32(L, C, f, L.y32, C.f32, s));
     }
@@ -285,6 +288,7 @@ sem_status vcycle32(sem_handle* h, const float* f0, float* u0, cudaStream_t s) {
         float* u = (li == 0) ? u0 : L.u32;
         K(launch_prolong32(L, C, C.u32, u, s));
         const bool learned = (li == 0) && h->opts.smoother == SEM_SMOOTH_LEARNED && h->mlp_trained && h->learned_active;
+        if ((li == 0) && h->cgc_only) continue;
         for (int m = 0; m < h->opts.nu2; ++m) {
             if (learned && m == 0) CKST(learned_sweep(h, f, u, s));
             else CKST(smooth<float>(h, li, f, u, false, s));
@@ -940,6 +944,36 @@ sem_status sem_mlp_gradient(sem_handle* h, int B, const float* X, const float* T
     return SEM_OK;
 }
 
+// One training pair at the point where the replaced sweep acts: the error e
+// (FP32; read before lr32 / tz / lu32 / ld32 are written) after the coarse-grid correction of the plain
+// V-cycle, e_post = e - P A_c^{-1} R A e, and its residual r_post = A e_post; the
+// network sees z = D^{-1} r_post per element (scaled to unit norm) and must
+// return e_post in the same scale.  Fills mX / mT / mscale.
+static sem_status make_pair(sem_handle* h, const float* e, cudaStream_t s) {
+    Level& L = h->lv[0];
+    const long long N = L.N;
+    CKST(apply_level32(h, 0, e, h->lr32, s));                  // r = A e
+    h->cgc_only = true;
+    const sem_status st = vcycle32(h, h->lr32, h->tz, s);      // coarse-grid correction of e
+    h->cgc_only = false;
+    CKST(st);
+    K(axpby32(N, e, h->tz, -1.f, h->lu32, s));                 // e_post
+    CKST(apply_level32(h, 0, h->lu32, h->lr32, s));            // r_post
+    K(mul32(N, L.dinv32, h->lr32, h->ld32, s));                // z = D^{-1} r_post
+    K(gather_scaled<float>(L.E, L.Np, L.map, h->ld32, h->lu32, h->mX, h->mT, h->mscale, s));
+    return SEM_OK;
+}
+
+static sem_status pair_loss(sem_handle* h, double* loss, cudaStream_t s) {
+    Level& L = h->lv[0];
+    CKS(mlp_forward(h->net, L.E, h->mX, h->mA1, h->mH1, h->mY, s));
+    CKS(mlp_backward(h->net, L.E, h->mX, h->mT, h->mA1, h->mH1, h->mY, h->mdY, h->mdH, h->grads,
+                     h->sc.scal + S_LOSS, s));
+    CKST(read_scalars(h, S_LOSS, 1, s));
+    *loss = h->sc.hpinned[S_LOSS];
+    return SEM_OK;
+}
+
 sem_status sem_learned_train(sem_handle* h, int snapshots, int steps, double lr, unsigned long long seed,
                              double* loss_first, double* loss_last, void* stream) {
     CKST(check_mlp(h));
@@ -948,42 +982,41 @@ sem_status sem_learned_train(sem_handle* h, int snapshots, int steps, double lr,
     Level& L = h->lv[0];
     const long long N = L.N;
     h->learned_active = false;          // the plain V-cycle generates the data
+    // fixed validation pair: the loss on it before and after training
+    const unsigned long long vseed = seed * 0x9E3779B97F4A7C15ULL + 0x5851F42D4C957F2DULL;
     double l0 = 0, l1 = 0;
-    sem_status ret = SEM_OK;
+    K(random_free(N, vseed, L.dinv32, h->te0, s));
+    sem_status ret = make_pair(h, h->te0, s);
+    if (ret == SEM_OK) ret = pair_loss(h, &l0, s);
     for (int sn = 0; sn < snapshots && ret == SEM_OK; ++sn) {
-        const unsigned long long sseed = seed * 0x9E3779B97F4A7C15ULL + (unsigned long long)sn * 0xD1B54A32D192ED03ULL;
-        K(random_free(N, sseed, L.dinv32, h->te0, s));
+        const unsigned long long sseed = seed * 0x9E3779B97F4A7C15ULL + (unsigned long long)(sn + 1) * 0xD1B54A32D192ED03ULL;
+        K(random_free(N, sseed, L.dinv32, h->te0, s));           // e0; the plain iteration solves A u = A e0
         ret = apply_level32(h, 0, h->te0, h->tf, s);
         if (ret != SEM_OK) break;
         CKS(cudaMemsetAsync(h->tu, 0, sizeof(float) * N, s));
-        for (int k = 0; k < steps; ++k) {
-            if (k == 0) {
-                CKS(cudaMemcpyAsync(h->lr32, h->tf, sizeof(float) * N, cudaMemcpyDeviceToDevice, s));
-            } else {
-                CKST(apply_level32(h, 0, h->tu, L.y32, s));
-                K(axpby32(N, h->tf, L.y32, -1.f, h->lr32, s));
-            }
-            K(axpby32(N, h->te0, h->tu, -1.f, h->lu32, s));           // error e = e0 - u
-            K(mul32(N, L.dinv32, h->lr32, h->ld32, s));               // z = D^{-1} r
-            K(gather_scaled<float>(L.E, L.Np, L.map, h->ld32, h->lu32, h->mX, h->mT, h->mscale, s));
+        for (int k = 0; k < steps && ret == SEM_OK; ++k) {
+            K(axpby32(N, h->te0, h->tu, -1.f, h->ld32, s));      // the plain solver's error e = e0 - u
+            ret = make_pair(h, h->ld32, s);
+            if (ret != SEM_OK) break;
             CKS(mlp_forward(h->net, L.E, h->mX, h->mA1, h->mH1, h->mY, s));
             CKS(mlp_backward(h->net, L.E, h->mX, h->mT, h->mA1, h->mH1, h->mY, h->mdY, h->mdH, h->grads,
                              h->sc.scal + S_LOSS, s));
             CKS(mlp_adam(h->net, h->grads, h->adam, (float)lr, s));
-            if (sn == 0 && k == 0) {
-                CKST(read_scalars(h, S_LOSS, 1, s));
-                l0 = h->sc.hpinned[S_LOSS];
-            }
+            h->launches += 2;
+            // advance the plain iteration: u <- u + M (f - A u)
+            CKST(apply_level32(h, 0, h->tu, L.y32, s));
+            K(axpby32(N, h->tf, L.y32, -1.f, h->lr32, s));
             ret = vcycle32(h, h->lr32, h->tz, s);
             if (ret != SEM_OK) break;
             K(axpby32(N, h->tu, h->tz, 1.f, h->tu, s));
         }
     }
     if (ret == SEM_OK) {
-        CKST(read_scalars(h, S_LOSS, 1, s));
-        l1 = h->sc.hpinned[S_LOSS];
-        h->mlp_trained = true;
+        K(random_free(N, vseed, L.dinv32, h->te0, s));
+        ret = make_pair(h, h->te0, s);
+        if (ret == SEM_OK) ret = pair_loss(h, &l1, s);
     }
+    if (ret == SEM_OK) h->mlp_trained = true;
     h->learned_active = true;
     if (loss_first) *loss_first = l0;
     if (loss_last) *loss_last = l1;
