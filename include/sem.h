@@ -219,8 +219,9 @@ sem_status sem_mlp_gradient(sem_handle* h, int B, const float* X_dev, const floa
  * the replaced sweep acts, after the V-cycle's coarse-grid correction
  * (e_post = e - P A_c^{-1} R A e), and (A e_post, e_post) is one pair, every finest
  * element of which is a training sample.  Nothing is stored: each pair is one Adam
- * step.  loss_first / loss_last (host, may be NULL) receive the loss on one fixed
- * validation pair before and after training.  Synchronous. */
+ * step.  loss_first / loss_last (host, may be NULL) receive the loss on one held-out
+ * pair (a separately seeded error after 3 plain V-cycles) before and after training.
+ * Synchronous. */
 sem_status sem_learned_train(sem_handle* h, int snapshots, int steps, double lr, unsigned long long seed,
                              double* loss_first, double* loss_last, void* stream);
 

@@ -982,11 +982,24 @@ sem_status sem_learned_train(sem_handle* h, int snapshots, int steps, double lr,
     Level& L = h->lv[0];
     const long long N = L.N;
     h->learned_active = false;          // the plain V-cycle generates the data
-    // fixed validation pair: the loss on it before and after training
+    // fixed validation pair (a held-out error of the plain iteration, after 3 V-cycles):
+    // the loss on it before and after training
     const unsigned long long vseed = seed * 0x9E3779B97F4A7C15ULL + 0x5851F42D4C957F2DULL;
     double l0 = 0, l1 = 0;
-    K(random_free(N, vseed, L.dinv32, h->te0, s));
-    sem_status ret = make_pair(h, h->te0, s);
+    auto validation_pair = [&]() -> sem_status {
+        K(random_free(N, vseed, L.dinv32, h->te0, s));
+        CKST(apply_level32(h, 0, h->te0, h->tf, s));
+        CKS(cudaMemsetAsync(h->tu, 0, sizeof(float) * N, s));
+        for (int k = 0; k < 3; ++k) {
+            CKST(apply_level32(h, 0, h->tu, L.y32, s));
+            K(axpby32(N, h->tf, L.y32, -1.f, h->lr32, s));
+            CKST(vcycle32(h, h->lr32, h->tz, s));
+            K(axpby32(N, h->tu, h->tz, 1.f, h->tu, s));
+        }
+        K(axpby32(N, h->te0, h->tu, -1.f, h->ld32, s));
+        return make_pair(h, h->ld32, s);
+    };
+    sem_status ret = validation_pair();
     if (ret == SEM_OK) ret = pair_loss(h, &l0, s);
     for (int sn = 0; sn < snapshots && ret == SEM_OK; ++sn) {
         const unsigned long long sseed = seed * 0x9E3779B97F4A7C15ULL + (unsigned long long)(sn + 1) * 0xD1B54A32D192ED03ULL;
@@ -1011,11 +1024,8 @@ sem_status sem_learned_train(sem_handle* h, int snapshots, int steps, double lr,
             K(axpby32(N, h->tu, h->tz, 1.f, h->tu, s));
         }
     }
-    if (ret == SEM_OK) {
-        K(random_free(N, vseed, L.dinv32, h->te0, s));
-        ret = make_pair(h, h->te0, s);
-        if (ret == SEM_OK) ret = pair_loss(h, &l1, s);
-    }
+    if (ret == SEM_OK) ret = validation_pair();
+    if (ret == SEM_OK) ret = pair_loss(h, &l1, s);
     if (ret == SEM_OK) h->mlp_trained = true;
     h->learned_active = true;
     if (loss_first) *loss_first = l0;

@@ -28,7 +28,7 @@ def sem():
 
 def _solver(sem, mesh, levels, **opts):
     prob = Problem(mesh, levels)
-    o = dict(levels=levels, precision="mixed_fp32", smoother="learned", outer="fgmres")
+    o = dict(levels=levels, precision="mixed_fp32", smoother="learned", outer="pdc")
     o.update(opts)
     return prob, sem.Solver(mesh, levels[0], eta_nodal=prob.eta_nodal, **o)
 
@@ -88,8 +88,8 @@ def test_training_and_what_the_network_gains(sem):
     lev = prob.levels[0]
     C = prob.coords(0)
     phiD = W.potential3d(*C[lev.dirichlet].T)
-    l0, l1 = learned.train(snapshots=6, steps=6, lr=1e-3, seed=7)
-    assert l1 < l0, (l0, l1)
+    l0, l1 = learned.train(snapshots=60, steps=6, lr=1e-3, seed=7)
+    assert l1 < 0.5 * l0, (l0, l1)
     phi = torch.zeros(lev.N, dtype=torch.float64, device="cuda")
     dD = torch.tensor(phiD, device="cuda")
     learned.solve(dD, phi, tol=1e-10)
@@ -109,7 +109,7 @@ def test_training_and_what_the_network_gains(sem):
     st_p = plain.solve(dD, phi, tol=1e-10)
     torch.cuda.synchronize()
     t_p = time.perf_counter() - t
-    print(f"\nlearned sweep: loss {l0:.3e} -> {l1:.3e}; FGMRES iterations {st_l['iters']} (plain {st_p['iters']}), "
+    print(f"\nlearned sweep: loss {l0:.3e} -> {l1:.3e}; PDC iterations {st_l['iters']} (plain {st_p['iters']}), "
           f"accepted {st_l['learned_accepts']}/{st_l['vcycles']} sweeps, time {t_l * 1e3:.1f} ms "
           f"(plain {t_p * 1e3:.1f} ms), q {st_l['q_mean']:.3f} (plain {st_p['q_mean']:.3f})")
     learned.close()
