@@ -190,6 +190,9 @@ def main():
     ap.add_argument("--sample-n", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--train-snapshots", type=int, default=60)
+    ap.add_argument("--train-steps", type=int, default=6)
     ap.add_argument("--inner-imax", type=int, default=40)
     ap.add_argument("--inner-rtol", type=float, default=1e-4)
     ap.add_argument("--coarse-rtol", type=float, default=1e-3)
@@ -322,6 +325,38 @@ def main():
                           f"FP64 coarse CG to {a.coarse_rtol:g}"}
         ms_solver.close()
 
+    learned = None
+    if not a.no_learned:
+        ls = sem.Solver(mesh, P, eta_nodal=eta, levels=levels_for(P), precision="mixed_fp32", outer="pdc",
+                        smoother="learned", coarse_rtol=a.coarse_rtol, imax=400)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        l0, l1 = ls.train(a.train_snapshots, a.train_steps, lr=1e-3, seed=7)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        phi_l = torch.empty(N, dtype=torch.float64, device="cuda")
+        ms_l, st_l = timed(ls, a.steps, a.warmup, phi_l)
+        ms_l = max_over_ranks(ms_l)
+        # the same outer/inner structure without the network, for the gain
+        ps = sem.Solver(mesh, P, eta_nodal=eta, levels=levels_for(P), precision="mixed_fp32", outer="pdc",
+                        coarse_rtol=a.coarse_rtol, imax=400)
+        ms_p, st_p = timed(ps, a.steps, a.warmup, phi_l)
+        ms_p = max_over_ranks(ms_p)
+        err = float(np.abs(phi_l.cpu().numpy() - phi64).max() / np.abs(phi64).max())
+        learned = {"value": dof * a.steps * world / (ms_l / 1000.0), "unit": UNIT, "ms_per_step": ms_l / a.steps,
+                   "outer_iters": st_l[-1]["iters"], "learned_accepts": st_l[-1]["learned_accepts"],
+                   "learned_fallbacks": st_l[-1]["learned_fallbacks"],
+                   "speedup_vs_fp64": (ms / a.steps) / (ms_l / a.steps),
+                   "same_cycle_without_network": {"ms_per_step": ms_p / a.steps, "outer_iters": st_p[-1]["iters"]},
+                   "max_rel_diff_vs_fp64_solution": err,
+                   "training": {"snapshots": a.train_snapshots, "steps_per_snapshot": a.train_steps,
+                                "seconds": t_train, "heldout_loss_before": l0, "heldout_loss_after": l1},
+                   "form": "FP64 defect correction (Algorithm 2) around the FP32 V-cycle whose first finest-level "
+                           "post-smoothing sweep is the trained 2-layer MLP (hidden 256, BF16 weights), kept when "
+                           "it lowers the residual, else the Chebyshev sweep"}
+        ls.close()
+        ps.close()
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
@@ -333,7 +368,7 @@ def main():
                            "l2": "no flush: every solve streams the 0.6 GB FP64 geometric factors (> 129 MB L2)",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "mixed_fp32": mixed}
+                "clocks": clk, "mixed_fp32": mixed, "learned": learned}
         print(json.dumps(line), flush=True)
     solver.close()
     if world > 1:
