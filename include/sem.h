@@ -114,6 +114,7 @@ typedef struct {
                                    use the PDC or FGMRES outer iteration. */
     int mlp_hidden;             /* hidden width of the correction network (default 256) */
     unsigned long long mlp_seed; /* seed of the network's initial weights */
+    int batch;                  /* 1: prepare the handle for laplace_solve_batch (own stream and iterate) */
 } sem_options;
 
 typedef struct {
@@ -246,6 +247,18 @@ sem_status sem_learned_train(sem_handle* h, int snapshots, int steps, double lr,
 sem_status sem_cg_csr_noalloc(long long n, const int* rowptr, const int* col, const double* vals,
                               const double* dinv, const double* b, double* x, double rtol, int imax,
                               int* iters_host, void* stream);
+
+/* Solve n independent problems (tanks), each set up by its own sem_setup with
+ * batch = 1 and inner_imax = 0, in lockstep (Section 4.1-4.4 per tank, Algorithm 2
+ * outer iteration: u <- u + M^{-1} r with the handle's V-cycle in its precision, FP64
+ * residual).  Every tank runs on its own stream; its iteration (V-cycle, update, FP64
+ * residual and norm) is captured once into a CUDA graph and replayed, so one lockstep
+ * iteration costs one graph launch per active tank and one host synchronisation for
+ * all of them.  dirichlet_eta[t] / phi[t]: device arrays of tank t as in
+ * laplace_solve; stats: n entries or NULL.  Starts after prior work on `stream` and
+ * makes `stream` wait for the result.  Returns the worst tank status. */
+sem_status laplace_solve_batch(sem_handle* const* hs, int n, const double* const* dirichlet_eta_dev, double tol,
+                               double* const* phi_dev, sem_stats* stats, void* stream);
 
 /* Thread-local message of the last error ("" if none). */
 const char* sem_last_error(void);

@@ -29,7 +29,7 @@ EXPORTS = ("sem_default_options", "sem_mesh_nodes2d", "sem_setup", "sem_destroy"
            "sem_dirichlet_nodes", "sem_node_coords", "sem_element_map", "sem_lambda_max", "sem_diagonal",
            "sem_apply", "pmg_vcycle", "laplace_solve", "laplace_solve_host", "sem_last_error",
            "sem_cg_csr_noalloc", "sem_mlp_get_weights", "sem_mlp_set_weights", "sem_mlp_forward",
-           "sem_mlp_gradient", "sem_learned_train")
+           "sem_mlp_gradient", "sem_learned_train", "laplace_solve_batch")
 
 
 class SemMesh(Structure):
@@ -105,8 +105,10 @@ def lib():
     L.sem_mlp_gradient.argtypes = [c_void_p, c_int, c_void_p, c_void_p, POINTER(c_double), fp, fp, fp, fp, c_void_p]
     L.sem_learned_train.argtypes = [c_void_p, c_int, c_int, c_double, ctypes.c_ulonglong, POINTER(c_double),
                                     POINTER(c_double), c_void_p]
+    L.laplace_solve_batch.argtypes = [POINTER(c_void_p), c_int, POINTER(c_void_p), c_double, POINTER(c_void_p),
+                                      POINTER(SemStats), c_void_p]
     for name in ("sem_mlp_get_weights", "sem_mlp_set_weights", "sem_mlp_forward", "sem_mlp_gradient",
-                 "sem_learned_train"):
+                 "sem_learned_train", "laplace_solve_batch"):
         getattr(L, name).restype = c_int
     for name in ("sem_mesh_nodes2d", "sem_setup", "sem_query", "sem_dirichlet_nodes", "sem_node_coords",
                  "sem_element_map", "sem_lambda_max", "sem_diagonal", "sem_apply", "pmg_vcycle",
@@ -319,6 +321,19 @@ def sem_learned_train(h: int, snapshots: int, steps: int, lr: float = 1e-3, seed
     _check(lib().sem_learned_train(h, int(snapshots), int(steps), float(lr), ctypes.c_ulonglong(seed), byref(l0),
                                    byref(l1), _stream(stream)))
     return l0.value, l1.value
+
+
+def laplace_solve_batch(handles, etas, tol: float, phis, stream=None, allow_not_converged=False):
+    """Lockstep batched solve of several tanks (handles set up with batch=1, inner_imax=0);
+    returns the list of per-tank stats."""
+    n = len(handles)
+    hs = (c_void_p * n)(*[int(h) for h in handles])
+    es = (c_void_p * n)(*[_ptr(e) for e in etas])
+    ps = (c_void_p * n)(*[_ptr(p) for p in phis])
+    st = (SemStats * n)()
+    allow = (SEM_OK, SEM_NOT_CONVERGED) if allow_not_converged else (SEM_OK,)
+    _check(lib().laplace_solve_batch(hs, n, es, float(tol), ps, st, _stream(stream)), allow)
+    return [st[i].as_dict() for i in range(n)]
 
 
 def sem_last_error() -> str:

@@ -100,6 +100,13 @@ struct sem_handle {
     bool mlp_trained = false;
     bool learned_active = true;
     bool cgc_only = false;          // FP32 V-cycle without finest-level smoothing (coarse-grid correction)
+    // batched lockstep solves (laplace_solve_batch): own stream, iterate, captured iteration graph
+    bool capturing = false;         // launches are being captured: no host synchronisation
+    cudaStream_t bstream = nullptr;
+    double* bu = nullptr;
+    cudaGraphExec_t bgraph = nullptr;
+    bool bgraph_failed = false;
+    long long bgraph_launches = 0, bgraph_applies = 0, bgraph_vcycles = 0;
     // staging buffers of laplace_solve_host
     double *st_eta = nullptr, *st_rhs = nullptr, *st_phi = nullptr;
     // host geometry copies for coordinate queries

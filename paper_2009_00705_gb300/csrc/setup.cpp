@@ -384,6 +384,10 @@ sem_status build_workspace(sem_handle* h) {
     for (double** v : {&h->cx, &h->cr, &h->cz, &h->cp, &h->cq, &h->cb}) CK(dalloc(v, Lc.N));
     if (h->opts.precision == SEM_PREC_MIXED_FP32 && h->opts.inner_imax > 0)
         for (float** v : {&h->ir, &h->iz, &h->ip, &h->iq, &h->ie}) CK(dalloc(v, N));
+    if (h->opts.batch) {
+        CK(dalloc(&h->bu, N));
+        CK(cudaStreamCreateWithFlags(&h->bstream, cudaStreamNonBlocking));
+    }
     CK(dalloc(&h->st_eta, h->lv[0].hdir.size()));
     CK(dalloc(&h->st_rhs, N));
     CK(dalloc(&h->st_phi, N));

@@ -80,7 +80,7 @@ cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 sem_status apply_level64(sem_handle* h, int li, const double* x, double* y, bool lift, cudaStream_t s) {
     const Level& L = h->lv[li];
     CKS(cudaMemsetAsync(y, 0, sizeof(double) * L.N, s));
-    const bool timed = (li == 0) && h->opts.profile && (h->ev_used + 2 <= (int)h->ev.size());
+    const bool timed = (li == 0) && h->opts.profile && !h->capturing && (h->ev_used + 2 <= (int)h->ev.size());
     if (timed) CKS(cudaEventRecord(h->ev[h->ev_used], s));
     K(launch_apply64(L, x, y, lift, nullptr, s));
     if (timed) {
@@ -122,6 +122,7 @@ sem_status coarse_solve(sem_handle* h, const double* b, double* x, cudaStream_t 
     if (C.csr_val != nullptr) {
         K(coarse_cg_persistent(C, C.csr_rowptr, C.csr_col, C.csr_val, b, x, h->cr, h->cz, h->cp, h->cq, sc, rt * rt,
                                h->opts.coarse_imax, (unsigned)h->opts.debug_barrier_extra, s));
+        if (h->capturing) return SEM_OK;     // checked after the batched solve (timeout flag)
         CKS(cudaMemcpyAsync(sc.hflags, sc.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
         CKS(cudaMemcpyAsync(sc.hflags + 4, sc.counter + 3, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         CKS(cudaStreamSynchronize(s));
@@ -619,6 +620,7 @@ void sem_default_options(sem_options* o, int P) {
     o->smoother = SEM_SMOOTH_CHEBYSHEV;
     o->mlp_hidden = 256;
     o->mlp_seed = 20090705ULL;
+    o->batch = 0;
 }
 
 sem_status sem_mesh_nodes2d(const sem_mesh* m, int p, long long* n2, double* xy) {
@@ -690,12 +692,14 @@ void sem_destroy(sem_handle* h) {
                     h->net.W1b, h->net.W2b, h->grads.dW1, h->grads.db1, h->grads.dW2, h->grads.db2,
                     h->adam.m[0], h->adam.m[1], h->adam.m[2], h->adam.m[3], h->adam.v[0], h->adam.v[1],
                     h->adam.v[2], h->adam.v[3], h->mX, h->mT, h->mA1, h->mH1, h->mY, h->mdY, h->mdH, h->mscale,
-                    h->lr32, h->ld32, h->lu32, h->te0, h->tf, h->tu, h->tz};
+                    h->lr32, h->ld32, h->lu32, h->te0, h->tf, h->tu, h->tz, h->bu};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->sc.hpinned) cudaFreeHost(h->sc.hpinned);
     if (h->sc.hflags) cudaFreeHost(h->sc.hflags);
     for (auto& e : h->ev) cudaEventDestroy(e);
+    if (h->bgraph) cudaGraphExecDestroy(h->bgraph);
+    if (h->bstream) cudaStreamDestroy(h->bstream);
     delete h;
 }
 
@@ -1031,6 +1035,164 @@ sem_status sem_learned_train(sem_handle* h, int snapshots, int steps, double lr,
     if (loss_first) *loss_first = l0;
     if (loss_last) *loss_last = l1;
     return ret;
+}
+
+// One lockstep iteration of a batched tank (no host synchronisation, capturable):
+// z = M^{-1} r; u += z; r = f - A u; ||r||^2 -> pinned host mirror.
+static sem_status batch_iteration(sem_handle* h, cudaStream_t s) {
+    const long long N = h->lv[0].N;
+    CKST(precondition(h, h->r, h->z, s));
+    K(axpy64(N, 1.0, h->z, h->bu, s));
+    CKST(apply_level64(h, 0, h->bu, h->q, false, s));
+    K(residual64(N, h->fr, h->q, h->r, h->sc, h->sc.scal + S_RR, s));
+    CKS(cudaMemcpyAsync(h->sc.hpinned + S_RR, h->sc.scal + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s));
+    return SEM_OK;
+}
+
+// Capture batch_iteration into the handle's graph (once); on any capture failure the
+// tank keeps running its iterations as direct launches.
+static void batch_capture(sem_handle* h) {
+    if (h->bgraph || h->bgraph_failed) return;
+    cudaStream_t s = h->bstream;
+    const long long l0 = h->launches, a0 = h->fine_applies, v0 = h->vcycles;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        h->bgraph_failed = true;
+        return;
+    }
+    h->capturing = true;
+    const sem_status st = batch_iteration(h, s);
+    h->capturing = false;
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(s, &g);
+    if (st != SEM_OK || ee != cudaSuccess || g == nullptr ||
+        cudaGraphInstantiate(&h->bgraph, g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        h->bgraph = nullptr;
+        h->bgraph_failed = true;
+    }
+    if (g) cudaGraphDestroy(g);
+    h->bgraph_launches = h->launches - l0;
+    h->bgraph_applies = h->fine_applies - a0;
+    h->bgraph_vcycles = h->vcycles - v0;
+    h->launches = l0;
+    h->fine_applies = a0;
+    h->vcycles = v0;
+}
+
+sem_status laplace_solve_batch(sem_handle* const* hs, int n, const double* const* eta, double tol, double* const* phi,
+                               sem_stats* stats, void* stream) {
+    if (!hs || n < 1 || !eta || !phi) { set_error("laplace_solve_batch: bad arguments"); return SEM_EINVAL; }
+    for (int t = 0; t < n; ++t) {
+        if (!hs[t] || !eta[t] || !phi[t]) { set_error("laplace_solve_batch: NULL tank entry"); return SEM_EINVAL; }
+        if (!hs[t]->opts.batch || hs[t]->opts.inner_imax != 0) {
+            set_error("laplace_solve_batch: every handle needs batch = 1 and inner_imax = 0");
+            return SEM_EINVAL;
+        }
+    }
+    cudaStream_t cs = as_stream(stream);
+    cudaEvent_t start, done;
+    CKS(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    CKS(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+    CKS(cudaEventRecord(start, cs));
+    std::vector<double> thr(n), fnorm(n);
+    std::vector<int> active(n, 1), iters(n, 0);
+    std::vector<sem_status> status(n, SEM_OK);
+    std::vector<double> rn(n);
+    // lifting of every tank on its own stream, then one synchronisation for all
+    for (int t = 0; t < n; ++t) {
+        sem_handle* h = hs[t];
+        cudaStream_t s = h->bstream;
+        const Level& L = h->lv[0];
+        const long long N = L.N, nd = (long long)L.hdir.size();
+        h->fine_applies = h->vcycles = h->launches = 0;
+        h->coarse_iters_max = 0;
+        CKS(cudaStreamWaitEvent(s, start, 0));
+        CKS(cudaMemsetAsync(h->sc.flags + F_LEARN_COUNT, 0, 2 * sizeof(int), s));
+        CKS(cudaMemsetAsync(h->x, 0, sizeof(double) * N, s));
+        K(scatter_dirichlet(nd, L.dir, eta[t], h->x, s));
+        CKST(apply_level64(h, 0, h->x, h->q, true, s));
+        h->fine_applies -= 1;
+        CKS(cudaMemsetAsync(h->fr, 0, sizeof(double) * N, s));
+        K(axpy64(N, -1.0, h->q, h->fr, s));
+        K(dot64(N, h->fr, h->fr, h->sc, h->sc.scal + S_FF, s));
+        CKS(cudaMemcpyAsync(h->sc.hpinned + S_FF, h->sc.scal + S_FF, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CKS(cudaMemcpyAsync(h->r, h->fr, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+        CKS(cudaMemsetAsync(h->bu, 0, sizeof(double) * N, s));
+    }
+    for (int t = 0; t < n; ++t) {
+        sem_handle* h = hs[t];
+        CKS(cudaStreamSynchronize(h->bstream));
+        fnorm[t] = std::sqrt(h->sc.hpinned[S_FF]);
+        rn[t] = fnorm[t];
+        const double rtol = (tol > 0) ? tol : h->opts.rtol;
+        thr[t] = rtol * fnorm[t] + h->opts.atol;
+        if (!std::isfinite(fnorm[t])) { status[t] = SEM_NAN; active[t] = 0; }
+        else if (fnorm[t] <= thr[t]) active[t] = 0;
+    }
+    // lockstep iterations
+    for (bool any = true; any;) {
+        any = false;
+        for (int t = 0; t < n; ++t) {
+            if (!active[t]) continue;
+            sem_handle* h = hs[t];
+            if (iters[t] >= h->opts.imax) { active[t] = 0; status[t] = SEM_NOT_CONVERGED; continue; }
+            batch_capture(h);
+            if (h->bgraph) {
+                CKS(cudaGraphLaunch(h->bgraph, h->bstream));
+                h->launches += h->bgraph_launches;
+                h->fine_applies += h->bgraph_applies;
+                h->vcycles += h->bgraph_vcycles;
+            } else {
+                CKST(batch_iteration(h, h->bstream));
+            }
+            any = true;
+        }
+        for (int t = 0; t < n; ++t) {
+            if (!active[t]) continue;
+            sem_handle* h = hs[t];
+            CKS(cudaStreamSynchronize(h->bstream));
+            iters[t] += 1;
+            rn[t] = std::sqrt(h->sc.hpinned[S_RR]);
+            if (!std::isfinite(rn[t])) { status[t] = SEM_NAN; active[t] = 0; }
+            else if (rn[t] <= thr[t]) active[t] = 0;
+        }
+    }
+    // results and join
+    sem_status worst = SEM_OK;
+    for (int t = 0; t < n; ++t) {
+        sem_handle* h = hs[t];
+        cudaStream_t s = h->bstream;
+        const Level& L = h->lv[0];
+        CKS(cudaMemcpyAsync(phi[t], h->bu, sizeof(double) * L.N, cudaMemcpyDeviceToDevice, s));
+        K(scatter_dirichlet((long long)L.hdir.size(), L.dir, eta[t], phi[t], s));
+        unsigned timeout = 0;
+        CKS(cudaMemcpyAsync(&timeout, h->sc.counter + 3, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        CKS(cudaStreamSynchronize(s));
+        if (timeout && status[t] == SEM_OK) status[t] = SEM_TIMEOUT;
+        CKS(cudaEventRecord(done, s));
+        CKS(cudaStreamWaitEvent(cs, done, 0));
+        if (stats) {
+            sem_stats st{};
+            st.status = status[t];
+            st.iters = iters[t];
+            st.fnorm = fnorm[t];
+            st.res0 = fnorm[t];
+            st.res_final = rn[t];
+            st.q_mean = (iters[t] > 0 && fnorm[t] > 0) ? std::pow(rn[t] / fnorm[t], 1.0 / iters[t]) : 0.0;
+            st.fine_applies = h->fine_applies;
+            st.vcycles = h->vcycles;
+            st.kernel_launches = h->launches;
+            stats[t] = st;
+        }
+        if (status[t] != SEM_OK && (worst == SEM_OK || status[t] < 0)) worst = status[t];
+    }
+    cudaEventDestroy(start);
+    cudaEventDestroy(done);
+    if (worst == SEM_TIMEOUT) set_error("laplace_solve_batch: a coarse-CG barrier wait ran out");
+    else if (worst == SEM_NAN) set_error("laplace_solve_batch: non-finite residual");
+    else if (worst == SEM_NOT_CONVERGED) set_error("laplace_solve_batch: a tank reached imax");
+    return worst;
 }
 
 }  // extern "C"

@@ -1,0 +1,67 @@
+"""Batched lockstep solves of several uneven tanks (random element counts and
+orders P in {3,...,6}) against the individual solves and the oracle."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import solvers as S  # noqa: E402
+from oracle.assemble import Problem  # noqa: E402
+
+LEVELS = {6: [6, 3, 1], 5: [5, 3, 1], 4: [4, 2, 1], 3: [3, 2, 1]}
+
+
+@pytest.fixture(scope="module")
+def sem():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2009_00705_gb300 as pkg
+    from paper_2009_00705_gb300 import build as B
+    B.build()
+    return pkg
+
+
+@pytest.mark.parametrize("precision", ["mixed_fp32", "fp64"])
+def test_batched_tanks_match_individual_solves_and_oracle(sem, precision):
+    tanks = []
+    for i in range(6):
+        mesh, P, modes = W.random_tank(i, count_range=(64, 700))
+        prob = Problem(mesh, LEVELS[P])
+        solver = sem.Solver(mesh, P, eta_nodal=prob.eta_nodal, levels=LEVELS[P], precision=precision, batch=1,
+                            outer="pdc", imax=400)
+        C = solver.coords(0)
+        dn = solver.dirichlet_nodes(0)
+        phiD = W.tank_potential(*C[dn].T, modes)
+        tanks.append((mesh, P, prob, solver, torch.tensor(phiD, device="cuda"), phiD))
+    phis = [torch.zeros(t[3].query(0)["ndof"], dtype=torch.float64, device="cuda") for t in tanks]
+    stats = sem.laplace_solve_batch([t[3].h for t in tanks], [t[4] for t in tanks], 1e-10, phis)
+    torch.cuda.synchronize()
+    # a second batched call reuses the captured iteration graphs
+    stats2 = sem.laplace_solve_batch([t[3].h for t in tanks], [t[4] for t in tanks], 1e-10, phis)
+    torch.cuda.synchronize()
+    for (mesh, P, prob, solver, dD, phiD), phi, st, st2 in zip(tanks, phis, stats, stats2):
+        assert st["status"] == 0 and st["res_final"] <= 1e-10 * st["fnorm"]
+        assert st2["iters"] == st["iters"]
+        single = torch.zeros_like(phi)
+        st1 = solver.solve(dD, single, tol=1e-10)
+        assert abs(st1["iters"] - st["iters"]) <= 1
+        got = phi.cpu().numpy()
+        assert np.abs(got - single.cpu().numpy()).max() <= 1e-8 * np.abs(got).max()
+        ref = S.solve_laplace_direct(prob, phiD)
+        assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max()
+    for t in tanks:
+        t[3].close()
+
+
+def test_batch_rejects_handles_not_prepared_for_it(sem):
+    mesh, P, modes = W.random_tank(0, count_range=(64, 100))
+    xy = sem.sem_mesh_nodes2d(mesh, P)
+    s = sem.Solver(mesh, P, eta_nodal=mesh.eta(xy[:, 0], xy[:, 1]), precision="mixed_fp32")
+    x = torch.zeros(s.query(0)["ndof"], dtype=torch.float64, device="cuda")
+    with pytest.raises(sem.SemError) as e:
+        sem.laplace_solve_batch([s.h], [x], 1e-8, [x])
+    assert e.value.status == sem.SEM_EINVAL
+    s.close()

@@ -153,18 +153,27 @@ def potential3d(x, y, z, h: float = 1.0):
     return cosh_mode3d(x, y, z, 1.0, 1.0, h) + 0.5 * cosh_mode3d(x, y, z, 2.0, 1.0, h)
 
 
+def tank_potential(x, y, z, modes, h: float = 1.0):
+    """Sum of cosh modes a * cosh_mode3d(kx, ky) (modes = [(a, kx, ky)]): harmonic,
+    zero normal derivative on the bottom and the walls of [0, 2pi]^2."""
+    out = np.zeros(np.broadcast(np.asarray(x), np.asarray(y), np.asarray(z)).shape)
+    for (a, kx, ky) in modes:
+        out = out + a * cosh_mode3d(x, y, z, kx, ky, h)
+    return out
+
+
 def random_vector(n: int, seed: int = SEED, dtype=np.float64) -> np.ndarray:
     """Seeded standard-normal vector (parity inputs for apply / V-cycle)."""
     rng = np.random.default_rng(seed)
     return rng.standard_normal(n).astype(dtype)
 
 
-def random_tank(i: int):
+def random_tank(i: int, count_range=(500, 20000)):
     """Seeded batched-tank description: element count uniform in [500, 20000] prisms
     (4 layers), P uniform in {3,4,5,6}, eta a sum of 8 random cosine modes with
     sum |a| <= 0.1, Dirichlet data from 3 random cosh modes.  Returns (mesh, P, modes)."""
     rng = np.random.default_rng(SEED + i)
-    count = int(rng.integers(500, 20001))
+    count = int(rng.integers(count_range[0], count_range[1] + 1))
     P = int(rng.integers(3, 7))
     n = max(2, int(round(math.sqrt(count / 8.0))))
     amps = rng.uniform(0.0, 1.0, 8)
