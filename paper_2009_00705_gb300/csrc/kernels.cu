@@ -1089,6 +1089,83 @@ __global__ void __launch_bounds__(512) k_coarse_cg(long long n, const int* __res
     }
 }
 
+// Whole coarse CG in one CTA (no grid barrier, so any number of these may run
+// concurrently and inside captured graphs): used for batched tanks and small
+// coarse problems.  Global-memory writes of the CTA's threads are ordered by
+// __syncthreads.
+__device__ double block_allsum(double v) {
+    __shared__ double bc;
+    v = block_sum(v);
+    if (threadIdx.x == 0) bc = v;
+    __syncthreads();
+    v = bc;
+    __syncthreads();
+    return v;
+}
+
+__global__ void __launch_bounds__(1024) k_coarse_cg_block(long long n, const int* __restrict__ rowptr,
+                                                          const int* __restrict__ col,
+                                                          const double* __restrict__ vals,
+                                                          const double* __restrict__ dinv,
+                                                          const double* __restrict__ b, double* x, double* r,
+                                                          double* z, double* p, double* q, double* scal, int* flags,
+                                                          double rtol2, int imax) {
+    double s0 = 0, s1 = 0;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+        const double bi = b[i], zi = dinv[i] * bi;
+        x[i] = 0;
+        r[i] = bi;
+        z[i] = zi;
+        p[i] = zi;
+        s0 += bi * zi;
+        s1 += bi * bi;
+    }
+    double rho = block_allsum(s0);
+    const double bb = block_allsum(s1);
+    const double tol2 = rtol2 * bb;
+    double rr = bb;
+    int it = 0;
+    __shared__ double s_ratio;
+    while (rr > tol2 && rr > 0.0 && it < imax) {
+        double pq = 0;
+        for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+            double v = 0;
+            for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) v += vals[k] * p[col[k]];
+            q[i] = v;
+            pq += p[i] * v;
+        }
+        pq = block_allsum(pq);
+        if (threadIdx.x == 0) s_ratio = rho / pq;
+        __syncthreads();
+        const double alpha = s_ratio;
+        double t0 = 0, t1 = 0;
+        for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+            x[i] += alpha * p[i];
+            const double ri = r[i] - alpha * q[i];
+            r[i] = ri;
+            const double zi = dinv[i] * ri;
+            z[i] = zi;
+            t0 += ri * zi;
+            t1 += ri * ri;
+        }
+        const double rho_new = block_allsum(t0);
+        rr = block_allsum(t1);
+        ++it;
+        if (rr <= tol2) break;
+        if (threadIdx.x == 0) s_ratio = rho_new / rho;
+        __syncthreads();
+        const double beta = s_ratio;
+        rho = rho_new;
+        for (long long i = threadIdx.x; i < n; i += blockDim.x) p[i] = z[i] + beta * p[i];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        flags[F_CG_ITERS] = it;
+        flags[F_CG_DONE] = (rr <= tol2 || rr == 0.0) ? 1 : 0;
+        scal[S_CG_RR] = rr;
+    }
+}
+
 // ------------------------------------------------------------------ FGMRES helpers
 constexpr int kMaxMulti = 65;
 
@@ -1423,6 +1500,14 @@ cudaError_t coarse_cg_persistent(const Level& C, const int* rowptr, const int* c
                     &p,    &q,      &part, &bar,   &scal,  &flags, &rtol2, &imax, &extra_arrivals};
     err = cudaLaunchCooperativeKernel((void*)k_coarse_cg, grid, 512, args, 0, s);
     if (err != cudaSuccess) return err;
+    return cudaGetLastError();
+}
+
+cudaError_t coarse_cg_single(const Level& C, const int* rowptr, const int* col, const double* vals, const double* b,
+                             double* x, double* r, double* z, double* p, double* q, Scratch& sc, double rtol2, int imax,
+                             cudaStream_t s) {
+    k_coarse_cg_block<<<1, 1024, 0, s>>>(C.N, rowptr, col, vals, C.dinv, b, x, r, z, p, q, sc.scal, sc.flags, rtol2,
+                                         imax);
     return cudaGetLastError();
 }
 

@@ -188,6 +188,10 @@ cudaError_t cg_direction(long long n, const double* z, double* p, Scratch& sc, c
 // coarse level: assembled CSR matrix (free rows/cols) and the whole CG in one
 // cooperative launch; the barrier timeout flag is counter[3]
 cudaError_t coarse_assemble(const Level& C, const double* gref, const int* slot, double* vals, cudaStream_t s);
+// the same CG in a single CTA (no inter-CTA waits): batched tanks and small coarse levels
+cudaError_t coarse_cg_single(const Level& C, const int* rowptr, const int* col, const double* vals, const double* b,
+                             double* x, double* r, double* z, double* p, double* q, Scratch& sc, double rtol2, int imax,
+                             cudaStream_t s);
 cudaError_t coarse_cg_persistent(const Level& C, const int* rowptr, const int* col, const double* vals,
                                  const double* b, double* x, double* r, double* z, double* p, double* q, Scratch& sc,
                                  double rtol2, int imax, unsigned extra_arrivals, cudaStream_t s);

@@ -120,11 +120,19 @@ sem_status coarse_solve(sem_handle* h, const double* b, double* x, cudaStream_t 
     Scratch& sc = h->sc;
     const double rt = h->opts.coarse_rtol;
     if (C.csr_val != nullptr) {
-        K(coarse_cg_persistent(C, C.csr_rowptr, C.csr_col, C.csr_val, b, x, h->cr, h->cz, h->cp, h->cq, sc, rt * rt,
-                               h->opts.coarse_imax, (unsigned)h->opts.debug_barrier_extra, s));
-        if (h->capturing) return SEM_OK;     // checked after the batched solve (timeout flag)
+        // one CTA for batched tanks (tanks run concurrently; no inter-CTA waits), the
+        // cooperative multi-CTA kernel otherwise
+        const bool single = h->opts.batch != 0;
+        if (single)
+            K(coarse_cg_single(C, C.csr_rowptr, C.csr_col, C.csr_val, b, x, h->cr, h->cz, h->cp, h->cq, sc, rt * rt,
+                               h->opts.coarse_imax, s));
+        else
+            K(coarse_cg_persistent(C, C.csr_rowptr, C.csr_col, C.csr_val, b, x, h->cr, h->cz, h->cp, h->cq, sc,
+                                   rt * rt, h->opts.coarse_imax, (unsigned)h->opts.debug_barrier_extra, s));
+        if (h->capturing) return SEM_OK;     // checked after the batched solve
         CKS(cudaMemcpyAsync(sc.hflags, sc.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
-        CKS(cudaMemcpyAsync(sc.hflags + 4, sc.counter + 3, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        sc.hflags[4] = 0;
+        if (!single) CKS(cudaMemcpyAsync(sc.hflags + 4, sc.counter + 3, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         CKS(cudaStreamSynchronize(s));
         if (sc.hflags[4] != 0) {
             set_error("coarse CG: a grid barrier wait ran out (device timeout)");
@@ -685,6 +693,9 @@ sem_status sem_setup(const sem_mesh* m, int P, const sem_options* opts, sem_hand
 
 void sem_destroy(sem_handle* h) {
     if (!h) return;
+    // no kernel or copy of this handle may still be in flight when its memory goes away
+    if (h->bstream) cudaStreamSynchronize(h->bstream);
+    cudaDeviceSynchronize();
     for (Level& L : h->lv) free_level(L);
     void* ptrs[] = {h->sc.part, h->sc.counter, h->sc.scal, h->sc.flags, h->r, h->z, h->p, h->q, h->x, h->fr,
                     h->V, h->Zb, h->cx, h->cr, h->cz, h->cp, h->cq, h->cb, h->st_eta, h->st_rhs, h->st_phi,
@@ -1080,9 +1091,8 @@ static void batch_capture(sem_handle* h) {
     h->vcycles = v0;
 }
 
-sem_status laplace_solve_batch(sem_handle* const* hs, int n, const double* const* eta, double tol, double* const* phi,
-                               sem_stats* stats, void* stream) {
-    if (!hs || n < 1 || !eta || !phi) { set_error("laplace_solve_batch: bad arguments"); return SEM_EINVAL; }
+static sem_status batch_impl(sem_handle* const* hs, int n, const double* const* eta, double tol, double* const* phi,
+                             sem_stats* stats, void* stream) {
     for (int t = 0; t < n; ++t) {
         if (!hs[t] || !eta[t] || !phi[t]) { set_error("laplace_solve_batch: NULL tank entry"); return SEM_EINVAL; }
         if (!hs[t]->opts.batch || hs[t]->opts.inner_imax != 0) {
@@ -1193,6 +1203,25 @@ sem_status laplace_solve_batch(sem_handle* const* hs, int n, const double* const
     else if (worst == SEM_NAN) set_error("laplace_solve_batch: non-finite residual");
     else if (worst == SEM_NOT_CONVERGED) set_error("laplace_solve_batch: a tank reached imax");
     return worst;
+}
+
+sem_status laplace_solve_batch(sem_handle* const* hs, int n, const double* const* eta, double tol, double* const* phi,
+                               sem_stats* stats, void* stream) {
+    if (!hs || n < 1 || !eta || !phi) { set_error("laplace_solve_batch: bad arguments"); return SEM_EINVAL; }
+    for (int t = 0; t < n; ++t) {
+        if (!hs[t] || !eta[t] || !phi[t]) { set_error("laplace_solve_batch: NULL tank entry"); return SEM_EINVAL; }
+        if (!hs[t]->opts.batch || hs[t]->opts.inner_imax != 0 || !hs[t]->bstream) {
+            set_error("laplace_solve_batch: every handle needs batch = 1 and inner_imax = 0");
+            return SEM_EINVAL;
+        }
+    }
+    const sem_status st = batch_impl(hs, n, eta, tol, phi, stats, stream);
+    if (st != SEM_OK && st != SEM_NOT_CONVERGED && st != SEM_NAN && st != SEM_TIMEOUT) {
+        // an error left the loop early: wait for every tank's work before returning
+        for (int t = 0; t < n; ++t) cudaStreamSynchronize(hs[t]->bstream);
+        cudaStreamSynchronize(as_stream(stream));
+    }
+    return st;
 }
 
 }  // extern "C"
