@@ -44,7 +44,7 @@ class SemOptions(Structure):
                 ("level_p", c_int * SEM_MAX_LEVELS), ("rtol", c_double), ("atol", c_double), ("imax", c_int),
                 ("gmres_m", c_int), ("coarse_rtol", c_double), ("coarse_imax", c_int), ("profile", c_int),
                 ("inner_imax", c_int), ("inner_rtol", c_double), ("debug_barrier_extra", c_int),
-                ("smoother", c_int), ("mlp_hidden", c_int), ("mlp_seed", ctypes.c_ulonglong)]
+                ("smoother", c_int), ("mlp_hidden", c_int), ("mlp_seed", ctypes.c_ulonglong), ("batch", c_int)]
 
 
 class SemStats(Structure):
@@ -177,8 +177,10 @@ def sem_default_options(P: int, **overrides) -> SemOptions:
             o.precision = PRECISION[v] if isinstance(v, str) else int(v)
         elif k == "smoother":
             o.smoother = SMOOTHER[v] if isinstance(v, str) else int(v)
-        else:
+        elif k in dict(SemOptions._fields_):
             setattr(o, k, v)
+        else:
+            raise TypeError(f"unknown solver option {k!r}")
     return o
 
 

@@ -71,3 +71,32 @@ def test_bad_mesh_is_rejected_without_gpu(sem):
         sem.sem_mesh_nodes2d(m, 3)
     assert e.value.status == sem.SEM_EINVAL
     assert "out of range" in sem.sem_last_error()
+
+
+def _c_struct_fields(name):
+    src = open(os.path.join(ROOT, "include", "sem.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", src).group(1)
+    fields = []
+    kw = {"const", "unsigned", "signed", "long", "short", "int", "double", "float", "char", "*"}
+    for decl in body.split(";"):
+        decl = re.sub(r"\[[^\]]*\]", "", decl).replace("*", " * ")
+        toks = decl.split()
+        if not toks:
+            continue
+        i = next(k for k, t in enumerate(toks) if t not in kw)
+        fields += [n.strip() for n in " ".join(toks[i:]).split(",")]
+    return fields
+
+
+@pytest.mark.parametrize("cname,pyname", [("sem_options", "SemOptions"), ("sem_stats", "SemStats"),
+                                           ("sem_mesh", "SemMesh")])
+def test_ctypes_structs_mirror_the_header(sem, cname, pyname):
+    # a field missing on the Python side would let the library write past the
+    # ctypes buffer; names and order must match exactly
+    assert [f for f, _ in getattr(sem, pyname)._fields_] == _c_struct_fields(cname)
+
+
+def test_unknown_option_is_an_error(sem):
+    with pytest.raises(TypeError):
+        sem.sem_default_options(4, no_such_option=1)
