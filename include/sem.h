@@ -115,6 +115,9 @@ typedef struct {
     int mlp_hidden;             /* hidden width of the correction network (default 256) */
     unsigned long long mlp_seed; /* seed of the network's initial weights */
     int batch;                  /* 1: prepare the handle for laplace_solve_batch (own stream and iterate) */
+    int autotune;               /* 1 (default): time the prism apply's tile shapes (elements per CTA pass)
+                                   on every level at setup and keep the faster (cached per order,
+                                   precision and element-count bucket for the process) */
 } sem_options;
 
 typedef struct {
@@ -133,6 +136,7 @@ typedef struct {
     long long inner_iters;      /* FP32 inner PCG iterations (MIXED_FP32 with inner_imax > 0) */
     long long learned_accepts;  /* learned sweeps kept (smoother = LEARNED) */
     long long learned_fallbacks; /* learned sweeps rejected by the residual test (Chebyshev ran instead) */
+    long long graph_iterations; /* laplace_solve_batch: iterations replayed from the captured CUDA graph */
 } sem_stats;
 
 typedef struct sem_handle sem_handle;
@@ -168,6 +172,8 @@ sem_status sem_dirichlet_nodes(const sem_handle* h, int level, long long* idx_ho
 sem_status sem_node_coords(const sem_handle* h, int level, double* xyz_host);
 sem_status sem_element_map(const sem_handle* h, int level, int* map_host);
 sem_status sem_lambda_max(const sem_handle* h, double* lam_host);
+/* Elements per CTA pass of the prism apply chosen for a level (FP64 and FP32 kernels). */
+sem_status sem_tile_shapes(const sem_handle* h, int level, int* elems_fp64, int* elems_fp32);
 /* The assembled diagonal of A at a level (all nodes), host copy. */
 sem_status sem_diagonal(const sem_handle* h, int level, double* diag_host);
 

@@ -29,7 +29,7 @@ EXPORTS = ("sem_default_options", "sem_mesh_nodes2d", "sem_setup", "sem_destroy"
            "sem_dirichlet_nodes", "sem_node_coords", "sem_element_map", "sem_lambda_max", "sem_diagonal",
            "sem_apply", "pmg_vcycle", "laplace_solve", "laplace_solve_host", "sem_last_error",
            "sem_cg_csr_noalloc", "sem_mlp_get_weights", "sem_mlp_set_weights", "sem_mlp_forward",
-           "sem_mlp_gradient", "sem_learned_train", "laplace_solve_batch")
+           "sem_mlp_gradient", "sem_learned_train", "laplace_solve_batch", "sem_tile_shapes")
 
 
 class SemMesh(Structure):
@@ -44,7 +44,8 @@ class SemOptions(Structure):
                 ("level_p", c_int * SEM_MAX_LEVELS), ("rtol", c_double), ("atol", c_double), ("imax", c_int),
                 ("gmres_m", c_int), ("coarse_rtol", c_double), ("coarse_imax", c_int), ("profile", c_int),
                 ("inner_imax", c_int), ("inner_rtol", c_double), ("debug_barrier_extra", c_int),
-                ("smoother", c_int), ("mlp_hidden", c_int), ("mlp_seed", ctypes.c_ulonglong), ("batch", c_int)]
+                ("smoother", c_int), ("mlp_hidden", c_int), ("mlp_seed", ctypes.c_ulonglong), ("batch", c_int),
+                ("autotune", c_int)]
 
 
 class SemStats(Structure):
@@ -52,7 +53,8 @@ class SemStats(Structure):
                 ("res_final", c_double), ("q_mean", c_double), ("fine_applies", c_longlong),
                 ("vcycles", c_longlong), ("coarse_iters_max", c_int), ("ms", c_double),
                 ("apply_ms", c_double), ("apply_launches", c_longlong), ("kernel_launches", c_longlong),
-                ("inner_iters", c_longlong), ("learned_accepts", c_longlong), ("learned_fallbacks", c_longlong)]
+                ("inner_iters", c_longlong), ("learned_accepts", c_longlong), ("learned_fallbacks", c_longlong),
+                ("graph_iterations", c_longlong)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -89,6 +91,8 @@ def lib():
     L.sem_element_map.argtypes = [c_void_p, c_int, POINTER(c_int)]
     L.sem_lambda_max.argtypes = [c_void_p, POINTER(c_double)]
     L.sem_diagonal.argtypes = [c_void_p, c_int, POINTER(c_double)]
+    L.sem_tile_shapes.argtypes = [c_void_p, c_int, POINTER(c_int), POINTER(c_int)]
+    L.sem_tile_shapes.restype = c_int
     L.sem_apply.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_void_p]
     L.pmg_vcycle.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
     L.laplace_solve.argtypes = [c_void_p, c_void_p, c_void_p, c_double, c_void_p, POINTER(SemStats), c_void_p]
@@ -244,6 +248,13 @@ def sem_diagonal(h: int, level: int = 0) -> np.ndarray:
     return out
 
 
+def sem_tile_shapes(h: int, level: int = 0):
+    """(elements per CTA pass of the FP64 prism apply, of the FP32 one) at a level."""
+    a, b = c_int(0), c_int(0)
+    _check(lib().sem_tile_shapes(h, level, byref(a), byref(b)))
+    return a.value, b.value
+
+
 def sem_apply(h: int, level: int, x, y, stream=None) -> None:
     _check(lib().sem_apply(h, level, _ptr(x), _ptr(y), _stream(stream)))
 
@@ -383,6 +394,9 @@ class Solver:
 
     def diagonal(self, level=0):
         return sem_diagonal(self.h, level)
+
+    def tile_shapes(self, level=0):
+        return sem_tile_shapes(self.h, level)
 
     def apply(self, level, x, y, stream=None):
         sem_apply(self.h, level, x, y, stream)

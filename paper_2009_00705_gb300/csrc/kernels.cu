@@ -158,225 +158,6 @@ __global__ void __launch_bounds__(128) k_apply(int E, const int* __restrict__ ma
     }
 }
 
-// ------------------------------------------------------------------ prism apply, register-tiled
-// Same contraction as k_apply for prisms, organised for throughput: a CTA takes
-// EB elements at a time; in the triangle stage one thread owns a quadrature
-// point qt of one element and keeps the values at all QZ vertical points in
-// registers, and in the transposed stage one thread owns a triangle node n and
-// keeps all QZ partial sums, so the transposed vertical stage and the
-// direct-stiffness summation follow without another pass through shared memory.
-template <int P, typename T>
-struct PrismTile {
-    static constexpr int NT = (P + 1) * (P + 2) / 2, NZ = P + 1, QT = (P + 1) * (P + 1), QZ = P + 1;
-    static constexpr int Np = NT * NZ, Nq = QT * QZ;
-    static constexpr int VEC = 16 / sizeof(T);                  // elements per 16-byte load
-    static constexpr int QZP = (QZ + VEC - 1) / VEC * VEC;      // padded row length
-    // elements per CTA pass: 8 at P = 6 fills whole warps in both heavy stages
-    // (8 * 49 quadrature columns, 8 * 28 triangle nodes); more at low order
-    static constexpr int EB = 8 * (P <= 2 ? 4 : (P == 3 ? 2 : 1));
-    static constexpr int THR_RAW = ((EB * NT + 31) / 32) * 32;
-    static constexpr int NTHR = THR_RAW < 64 ? 64 : (THR_RAW > 256 ? 256 : THR_RAW);
-    static constexpr bool TRANSPOSED = (sizeof(T) == 4);       // conflict-free copies for FP32 only
-    __host__ __device__ static constexpr int round4(int v) { return (v + 3) / 4 * 4; }
-    static constexpr int REF = round4(3 * QT * NT) + (TRANSPOSED ? round4(3 * QT * NT) : 0) + round4(2 * QZ * NZ);
-    static constexpr int WORK = round4(Np) + 2 * round4(NT * QZP) + 3 * round4(QT * QZP);
-    static constexpr size_t SMEM = sizeof(T) * (REF + (size_t)EB * WORK);
-};
-
-template <typename T, int N, int NP>
-__device__ __forceinline__ void load_row(const T* __restrict__ src, T (&out)[N]) {
-    static_assert(NP >= N, "row padding");
-    if constexpr (sizeof(T) == 4) {
-#pragma unroll
-        for (int c = 0; c < NP / 4; ++c) {
-            const float4 v = reinterpret_cast<const float4*>(src)[c];
-            if (4 * c + 0 < N) out[4 * c + 0] = v.x;
-            if (4 * c + 1 < N) out[4 * c + 1] = v.y;
-            if (4 * c + 2 < N) out[4 * c + 2] = v.z;
-            if (4 * c + 3 < N) out[4 * c + 3] = v.w;
-        }
-    } else {
-#pragma unroll
-        for (int c = 0; c < NP / 2; ++c) {
-            const double2 v = reinterpret_cast<const double2*>(src)[c];
-            if (2 * c + 0 < N) out[2 * c + 0] = v.x;
-            if (2 * c + 1 < N) out[2 * c + 1] = v.y;
-        }
-    }
-}
-
-template <int P, typename T, bool LIFT>
-__global__ void __launch_bounds__(PrismTile<P, T>::NTHR)
-    k_apply_prism(int E, const int* __restrict__ map, const T* __restrict__ G, const T* __restrict__ refm,
-                  const T* __restrict__ x, T* __restrict__ y, const int* __restrict__ skip) {
-    using D = PrismTile<P, T>;
-    constexpr int NT = D::NT, NZ = D::NZ, QT = D::QT, QZ = D::QZ, Np = D::Np, Nq = D::Nq, QZP = D::QZP, EB = D::EB;
-    if (skip != nullptr && *skip) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sm = reinterpret_cast<T*>(smem_raw);
-    // reference matrices: [Bt | Dr | Ds] as [QT][NT]; (FP32) [BtT | DrT | DsT] as [NT][QT]; [Bz | Dz] as [QZ][NZ]
-    T* sB = sm;
-    T* sBT = sm + D::round4(3 * QT * NT);
-    T* sZ = sBT + (D::TRANSPOSED ? D::round4(3 * QT * NT) : 0);
-    for (int i = threadIdx.x; i < 3 * QT * NT; i += blockDim.x) sB[i] = refm[i];
-    if (D::TRANSPOSED)
-        for (int i = threadIdx.x; i < 3 * QT * NT; i += blockDim.x) sBT[i] = refm[3 * QT * NT + i];
-    for (int i = threadIdx.x; i < 2 * QZ * NZ; i += blockDim.x) sZ[i] = refm[6 * QT * NT + i];
-    T* work = sm + D::REF;
-    const T* sBt = sB;
-    const T* sDr = sB + QT * NT;
-    const T* sDs = sB + 2 * QT * NT;
-    const T* sBz = sZ;
-    const T* sDz = sZ + QZ * NZ;
-    __syncthreads();
-    for (int e0 = blockIdx.x * EB; e0 < E; e0 += gridDim.x * EB) {
-        const int nb = min(EB, E - e0);
-        {   // pull the next pass's geometric factors and map into L2 while this pass computes
-            const int en = e0 + gridDim.x * EB;
-            if (en < E) {
-                const int nn = min(EB, E - en);
-                const char* g0 = reinterpret_cast<const char*>(G + (size_t)en * 6 * Nq);
-                const size_t gbytes = (size_t)nn * 6 * Nq * sizeof(T);
-                for (size_t off = (size_t)threadIdx.x * 128; off < gbytes; off += (size_t)blockDim.x * 128)
-                    asm volatile("prefetch.global.L2 [%0];" ::"l"(g0 + off));
-                const char* m0 = reinterpret_cast<const char*>(map + (size_t)en * Np);
-                for (size_t off = (size_t)threadIdx.x * 128; off < (size_t)nn * Np * 4; off += (size_t)blockDim.x * 128)
-                    asm volatile("prefetch.global.L2 [%0];" ::"l"(m0 + off));
-            }
-        }
-        // gather
-        for (int i = threadIdx.x; i < nb * Np; i += blockDim.x) {
-            const int b = i / Np, l = i - b * Np;
-            const int m = map[(size_t)(e0 + b) * Np + l];
-            work[b * D::WORK + l] = (m >= 0) ? x[m] : (LIFT ? x[-m - 1] : T(0));
-        }
-        __syncthreads();
-        // vertical stage: U[n][qz], W[n][qz] (values / t-derivatives at the vertical Gauss points)
-        for (int i = threadIdx.x; i < nb * NT; i += blockDim.x) {
-            const int b = i / NT, n = i - b * NT;
-            T* wb = work + b * D::WORK;
-            T xk[NZ];
-#pragma unroll
-            for (int k = 0; k < NZ; ++k) xk[k] = wb[k * NT + n];
-            T* U = wb + D::round4(Np) + n * QZP;
-            T* W = wb + D::round4(Np) + D::round4(NT * QZP) + n * QZP;
-#pragma unroll
-            for (int qz = 0; qz < QZ; ++qz) {
-                T u = 0, w = 0;
-#pragma unroll
-                for (int k = 0; k < NZ; ++k) {
-                    u += sBz[qz * NZ + k] * xk[k];
-                    w += sDz[qz * NZ + k] * xk[k];
-                }
-                U[qz] = u;
-                W[qz] = w;
-            }
-        }
-        __syncthreads();
-        // triangle stage + geometric factors: thread (b, qt), all qz in registers
-        for (int i = threadIdx.x; i < nb * QT; i += blockDim.x) {
-            const int b = i / QT, qt = i - b * QT;
-            T* wb = work + b * D::WORK;
-            const T* U = wb + D::round4(Np);
-            const T* W = U + D::round4(NT * QZP);
-            T ur[QZ], us[QZ], ut[QZ];
-#pragma unroll
-            for (int qz = 0; qz < QZ; ++qz) ur[qz] = us[qz] = ut[qz] = T(0);
-#pragma unroll 2
-            for (int n = 0; n < NT; ++n) {
-                T dr, ds, bt;
-                if (D::TRANSPOSED) {
-                    dr = sBT[QT * NT + n * QT + qt];
-                    ds = sBT[2 * QT * NT + n * QT + qt];
-                    bt = sBT[n * QT + qt];
-                } else {
-                    dr = sDr[qt * NT + n];
-                    ds = sDs[qt * NT + n];
-                    bt = sBt[qt * NT + n];
-                }
-                T uv[QZ], wv[QZ];
-                load_row<T, QZ, QZP>(U + n * QZP, uv);
-                load_row<T, QZ, QZP>(W + n * QZP, wv);
-#pragma unroll
-                for (int qz = 0; qz < QZ; ++qz) {
-                    ur[qz] += dr * uv[qz];
-                    us[qz] += ds * uv[qz];
-                    ut[qz] += bt * wv[qz];
-                }
-            }
-            const T* Ge = G + (size_t)(e0 + b) * 6 * Nq;
-            T* vr = wb + D::round4(Np) + 2 * D::round4(NT * QZP) + qt * QZP;
-            T* vs = vr + D::round4(QT * QZP);
-            T* vt = vs + D::round4(QT * QZP);
-#pragma unroll
-            for (int qz = 0; qz < QZ; ++qz) {
-                const int q = qz * QT + qt;
-                const T g0 = Ge[q], g1 = Ge[Nq + q], g2 = Ge[2 * Nq + q];
-                const T g3 = Ge[3 * Nq + q], g4 = Ge[4 * Nq + q], g5 = Ge[5 * Nq + q];
-                vr[qz] = g0 * ur[qz] + g1 * us[qz] + g2 * ut[qz];
-                vs[qz] = g1 * ur[qz] + g3 * us[qz] + g4 * ut[qz];
-                vt[qz] = g2 * ur[qz] + g4 * us[qz] + g5 * ut[qz];
-            }
-        }
-        __syncthreads();
-        // transposed triangle stage (thread (b, n), all qz), transposed vertical stage, summation
-        for (int i = threadIdx.x; i < nb * NT; i += blockDim.x) {
-            const int b = i / NT, n = i - b * NT;
-            const T* wb = work + b * D::WORK;
-            const T* vr = wb + D::round4(Np) + 2 * D::round4(NT * QZP);
-            const T* vs = vr + D::round4(QT * QZP);
-            const T* vt = vs + D::round4(QT * QZP);
-            T xr[QZ], xt[QZ];
-#pragma unroll
-            for (int qz = 0; qz < QZ; ++qz) xr[qz] = xt[qz] = T(0);
-#pragma unroll 2
-            for (int qt = 0; qt < QT; ++qt) {
-                const T dr = sDr[qt * NT + n], ds = sDs[qt * NT + n], bt = sBt[qt * NT + n];
-                T a[QZ], c[QZ], d[QZ];
-                load_row<T, QZ, QZP>(vr + qt * QZP, a);
-                load_row<T, QZ, QZP>(vs + qt * QZP, c);
-                load_row<T, QZ, QZP>(vt + qt * QZP, d);
-#pragma unroll
-                for (int qz = 0; qz < QZ; ++qz) {
-                    xr[qz] += dr * a[qz] + ds * c[qz];
-                    xt[qz] += bt * d[qz];
-                }
-            }
-            const int* me = map + (size_t)(e0 + b) * Np;
-#pragma unroll
-            for (int k = 0; k < NZ; ++k) {
-                T s = 0;
-#pragma unroll
-                for (int qz = 0; qz < QZ; ++qz) s += sBz[qz * NZ + k] * xr[qz] + sDz[qz * NZ + k] * xt[qz];
-                const int m = me[k * NT + n];
-                if (m >= 0) atomicAdd(&y[m], s);
-            }
-        }
-        __syncthreads();
-    }
-}
-
-template <int P, typename T, bool LIFT>
-cudaError_t apply_prism_impl(const Level& L, const T* refm, const T* G, const T* x, T* y, const int* skip,
-                             cudaStream_t s) {
-    using D = PrismTile<P, T>;
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        cudaError_t err = cudaFuncSetAttribute(k_apply_prism<P, T, LIFT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)D::SMEM);
-        if (err != cudaSuccess) return err;
-        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_prism<P, T, LIFT>, D::NTHR, D::SMEM);
-        if (err != cudaSuccess) return err;
-        if (per_sm < 1) per_sm = 1;
-    }
-    const int batches = (L.E + D::EB - 1) / D::EB;
-    int grid = kSMs * per_sm;
-    if (grid > batches) grid = batches;
-    if (grid < 1) return cudaSuccess;
-    k_apply_prism<P, T, LIFT><<<grid, D::NTHR, D::SMEM, s>>>(L.E, L.map, G, refm, x, y, skip);
-    return cudaGetLastError();
-}
-
 template <int P, bool PRISM, typename T, bool LIFT>
 cudaError_t apply_impl(const Level& L, const T* refm, const T* G, const T* x, T* y, const int* skip,
                        cudaStream_t s) {
@@ -399,14 +180,13 @@ cudaError_t apply_impl(const Level& L, const T* refm, const T* G, const T* x, T*
     return cudaGetLastError();
 }
 
+// triangles (2D vertical slices); prisms are in apply_prism.cu
 template <typename T, bool LIFT>
 cudaError_t apply_dispatch(const Level& L, const T* refm, const T* G, const T* x, T* y, const int* skip,
                            cudaStream_t s) {
-    const bool prism = (L.dim == 3);
 #define SEM_CASE(PP)                                                                     \
     case PP:                                                                             \
-        return prism ? apply_prism_impl<PP, T, LIFT>(L, refm, G, x, y, skip, s)          \
-                     : apply_impl<PP, false, T, LIFT>(L, refm, G, x, y, skip, s);
+        return apply_impl<PP, false, T, LIFT>(L, refm, G, x, y, skip, s);
     switch (L.p) {
         SEM_CASE(1)
         SEM_CASE(2)
@@ -1291,11 +1071,13 @@ __global__ void k_to_f64(long long n, const float* __restrict__ a, double* __res
 int reduce_blocks() { return 2 * kSMs; }
 
 cudaError_t launch_apply64(const Level& L, const double* x, double* y, bool lift, const int* skip, cudaStream_t s) {
+    if (L.dim == 3) return launch_apply_prism64(L, x, y, lift, skip, L.tile64, s);
     return lift ? apply_dispatch<double, true>(L, L.ref64.m, L.G, x, y, skip, s)
                 : apply_dispatch<double, false>(L, L.ref64.m, L.G, x, y, skip, s);
 }
 
 cudaError_t launch_apply32(const Level& L, const float* x, float* y, cudaStream_t s, const int* skip) {
+    if (L.dim == 3) return launch_apply_prism32(L, x, y, skip, L.tile32, s);
     return apply_dispatch<float, false>(L, L.ref32.m, L.G32, x, y, skip, s);
 }
 

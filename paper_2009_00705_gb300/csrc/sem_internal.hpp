@@ -55,6 +55,7 @@ struct Level {
     double *u = nullptr, *f = nullptr, *y = nullptr, *d = nullptr;
     float *u32 = nullptr, *f32 = nullptr, *y32 = nullptr, *d32 = nullptr;
     double* gref = nullptr;                // [dim][Nq][Np] full reference gradients (coarse level)
+    int tile64 = 0, tile32 = 0;            // prism apply tile-shape variant (autotuned)
     int* csr_rowptr = nullptr;             // coarse level: assembled matrix, free rows/cols
     int* csr_col = nullptr;
     double* csr_val = nullptr;
@@ -107,6 +108,7 @@ struct sem_handle {
     cudaGraphExec_t bgraph = nullptr;
     bool bgraph_failed = false;
     long long bgraph_launches = 0, bgraph_applies = 0, bgraph_vcycles = 0;
+    long long graph_iters = 0;
     // staging buffers of laplace_solve_host
     double *st_eta = nullptr, *st_rhs = nullptr, *st_phi = nullptr;
     // host geometry copies for coordinate queries
@@ -133,6 +135,12 @@ int reduce_blocks();
 cudaError_t launch_apply64(const Level& L, const double* x, double* y, bool lift, const int* skip,
                            cudaStream_t s);
 cudaError_t launch_apply32(const Level& L, const float* x, float* y, cudaStream_t s, const int* skip = nullptr);
+// apply_prism.cu: prism apply with tile-shape variant 0 or 1 (elements per CTA pass)
+cudaError_t launch_apply_prism64(const Level& L, const double* x, double* y, bool lift, const int* skip, int variant,
+                                 cudaStream_t s);
+cudaError_t launch_apply_prism32(const Level& L, const float* x, float* y, const int* skip, int variant,
+                                 cudaStream_t s);
+int prism_tile_elements(int P, int variant);
 cudaError_t launch_geometry(Level& L, const double* vtri, const double* etaP, const double* BP,
                             const double* DrP, const double* DsP, int NTP, int nlayers, double depth,
                             cudaStream_t s);

@@ -5,6 +5,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -387,6 +390,56 @@ sem_status estimate_lambda(sem_handle* h, int li) {
     return SEM_OK;
 }
 
+// Tile-shape autotuner of the prism apply: times both compiled variants (elements per
+// CTA pass) on this level's own mesh and keeps the faster; the choice is cached per
+// (order, precision, element-count bucket) for the rest of the process, so the tanks
+// of a batch are tuned once per kind.
+std::map<std::tuple<int, int, int>, int> g_tile_cache;
+std::mutex g_tile_mutex;
+
+cudaError_t tune_prism(Level& L, bool fp32) {
+    int bucket = 0;
+    while ((1 << (bucket + 1)) <= L.E) ++bucket;
+    const auto key = std::make_tuple(L.p, fp32 ? 4 : 8, bucket);
+    {
+        std::lock_guard<std::mutex> lock(g_tile_mutex);
+        auto it = g_tile_cache.find(key);
+        if (it != g_tile_cache.end()) {
+            (fp32 ? L.tile32 : L.tile64) = it->second;
+            return cudaSuccess;
+        }
+    }
+    cudaEvent_t e0, e1;
+    cudaError_t err = cudaEventCreate(&e0);
+    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    float best = 1e30f;
+    int choice = 0;
+    for (int v = 0; v < 2 && err == cudaSuccess; ++v) {
+        for (int rep = 0; rep < 4 && err == cudaSuccess; ++rep) {
+            if (rep == 1) err = cudaEventRecord(e0, 0);
+            if (fp32) {
+                cudaMemsetAsync(L.y32, 0, sizeof(float) * L.N, 0);
+                err = launch_apply_prism32(L, L.u32, L.y32, nullptr, v, 0);
+            } else {
+                cudaMemsetAsync(L.y, 0, sizeof(double) * L.N, 0);
+                err = launch_apply_prism64(L, L.u, L.y, false, nullptr, v, 0);
+            }
+        }
+        if (err == cudaSuccess) err = cudaEventRecord(e1, 0);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        if (err == cudaSuccess && ms < best) { best = ms; choice = v; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) return err;
+    (fp32 ? L.tile32 : L.tile64) = choice;
+    std::lock_guard<std::mutex> lock(g_tile_mutex);
+    g_tile_cache[key] = choice;
+    return cudaSuccess;
+}
+
 void free_level(Level& L) {
     void* ptrs[] = {L.map, L.G, L.G32, L.dinv, L.dinv32, L.dir, L.ref64.m, L.ref32.m, L.It64, L.Iz64, L.It32, L.Iz32, L.gref,
                     L.csr_rowptr, L.csr_col, L.csr_val,
@@ -629,6 +682,7 @@ void sem_default_options(sem_options* o, int P) {
     o->mlp_hidden = 256;
     o->mlp_seed = 20090705ULL;
     o->batch = 0;
+    o->autotune = 1;
 }
 
 sem_status sem_mesh_nodes2d(const sem_mesh* m, int p, long long* n2, double* xy) {
@@ -678,6 +732,16 @@ sem_status sem_setup(const sem_mesh* m, int P, const sem_options* opts, sem_hand
     if (st == SEM_OK) st = build_mlp(h);
     if (st == SEM_OK) st = build_workspace(h);
     for (int li = 0; li + 1 < o.nlevels && st == SEM_OK; ++li) st = estimate_lambda(h, li);
+    if (st == SEM_OK && o.autotune && m->dim == 3) {
+        // u / u32 hold finite data after the eigenvalue estimate; tune on them
+        for (Level& L : h->lv) {
+            if (st != SEM_OK) break;
+            cudaError_t e = to_f32(L.N, L.u, L.u32, 0);
+            if (e == cudaSuccess) e = tune_prism(L, false);
+            if (e == cudaSuccess) e = tune_prism(L, true);
+            if (e != cudaSuccess) { set_error(std::string("autotune: ") + cudaGetErrorString(e)); st = SEM_ECUDA; }
+        }
+    }
     if (st == SEM_OK) {
         cudaError_t e = cudaDeviceSynchronize();
         if (e != cudaSuccess) { set_error(std::string("setup: ") + cudaGetErrorString(e)); st = SEM_ECUDA; }
@@ -748,6 +812,14 @@ sem_status sem_element_map(const sem_handle* h, int level, int* map) {
 sem_status sem_lambda_max(const sem_handle* h, double* lam) {
     if (!h || !lam) { set_error("bad arguments"); return SEM_EINVAL; }
     for (size_t i = 0; i < h->lv.size(); ++i) lam[i] = h->lv[i].lam;
+    return SEM_OK;
+}
+
+sem_status sem_tile_shapes(const sem_handle* h, int level, int* elems_fp64, int* elems_fp32) {
+    CKST(check_level(h, level));
+    const Level& L = h->lv[level];
+    if (elems_fp64) *elems_fp64 = L.dim == 3 ? prism_tile_elements(L.p, L.tile64) : 1;
+    if (elems_fp32) *elems_fp32 = L.dim == 3 ? prism_tile_elements(L.p, L.tile32) : 1;
     return SEM_OK;
 }
 
@@ -1116,6 +1188,7 @@ static sem_status batch_impl(sem_handle* const* hs, int n, const double* const* 
         const Level& L = h->lv[0];
         const long long N = L.N, nd = (long long)L.hdir.size();
         h->fine_applies = h->vcycles = h->launches = 0;
+        h->graph_iters = 0;
         h->coarse_iters_max = 0;
         CKS(cudaStreamWaitEvent(s, start, 0));
         CKS(cudaMemsetAsync(h->sc.flags + F_LEARN_COUNT, 0, 2 * sizeof(int), s));
@@ -1150,6 +1223,7 @@ static sem_status batch_impl(sem_handle* const* hs, int n, const double* const* 
             batch_capture(h);
             if (h->bgraph) {
                 CKS(cudaGraphLaunch(h->bgraph, h->bstream));
+                h->graph_iters += 1;
                 h->launches += h->bgraph_launches;
                 h->fine_applies += h->bgraph_applies;
                 h->vcycles += h->bgraph_vcycles;
@@ -1193,6 +1267,7 @@ static sem_status batch_impl(sem_handle* const* hs, int n, const double* const* 
             st.fine_applies = h->fine_applies;
             st.vcycles = h->vcycles;
             st.kernel_launches = h->launches;
+            st.graph_iterations = h->graph_iters;
             stats[t] = st;
         }
         if (status[t] != SEM_OK && (worst == SEM_OK || status[t] < 0)) worst = status[t];

@@ -51,8 +51,12 @@ def _check_batch(sem, tanks):
     stats2 = sem.laplace_solve_batch([t[3].h for t in tanks], [t[4] for t in tanks], 1e-10, phis)
     torch.cuda.synchronize()
     for (mesh, P, prob, solver, dD, phiD), phi, st, st2 in zip(tanks, phis, stats, stats2):
+        e64, e32 = solver.tile_shapes(0)
+        assert e64 in (4, 8, 16, 32) and e32 in (4, 8, 16, 32)
         assert st["status"] == 0 and st["res_final"] <= 1e-10 * st["fnorm"]
         assert abs(st2["iters"] - st["iters"]) <= 1
+        # every iteration of the second call replays the graph captured in the first
+        assert st2["graph_iterations"] == st2["iters"], (st["graph_iterations"], st2)
         single = torch.zeros_like(phi)
         st1 = solver.solve(dD, single, tol=1e-10)
         assert abs(st1["iters"] - st["iters"]) <= 1
