@@ -40,7 +40,7 @@ FALLBACK_HBM_GBS = 6800.0
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the FP64 prism
 # apply, per launch, scaled from the 48x48x4-prism capture (18,432 elements;
 # profiles/apply_fp64_p6_box48.md) to the 32,768-element benchmark mesh by element
-# count; reported as null once the kernel's source differs from the captured one.
+# count; reported as null once apply_prism.cu differs from the captured source.
 TRAFFIC = {("apply_fp64", 6): (351.068672e6 + 14.987776e6) * 32768 / 18432}
 TRAFFIC_SRC_SHA = "78f7f4ef51218cb6"
 
@@ -67,11 +67,9 @@ def apply_bytes(P, E, N, word=8):
 
 
 def kernels_sha():
-    """Hash of the prism-apply kernel's source section in kernels.cu."""
-    src = open(os.path.join(ROOT, "paper_2009_00705_gb300", "csrc", "kernels.cu")).read()
-    a = src.index("// ------------------------------------------------------------------ prism apply, register-tiled")
-    b = src.index("template <int P, bool PRISM, typename T, bool LIFT>\ncudaError_t apply_impl(")
-    return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
+    """Hash of the prism-apply kernel's source (apply_prism.cu)."""
+    with open(os.path.join(ROOT, "paper_2009_00705_gb300", "csrc", "apply_prism.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
 class Clocks:
