@@ -82,8 +82,9 @@ typedef struct {
 /* Solver options; fill with sem_default_options and adjust.
  * level_p[0] = P > level_p[1] > ... > level_p[nlevels-1] = 1 (order per level).
  * Smoother: k_cheb-step Chebyshev iteration on D^{-1}A over [cheb_lo*b, b],
- * b = cheb_hi * lambda_hat, lambda_hat = power_its power iterations from
- * x_i = sin(i+1) on free nodes; nu1 pre- and nu2 post-sweeps (Algorithm 1).
+ * b = cheb_hi * lambda_hat, lambda_hat = the largest Ritz value of lanczos_steps
+ * Lanczos steps on D^{-1}A started from x_i = sin(i+1) on free nodes (a lower
+ * bound of lambda_max); nu1 pre- and nu2 post-sweeps (Algorithm 1).
  * Stop test ||r||_2 <= rtol*||f||_2 + atol on the FP64 free-node residual.
  * The coarse order-1 system is solved by FP64 Jacobi-CG to coarse_rtol
  * relative residual (at most coarse_imax iterations). */
@@ -92,7 +93,7 @@ typedef struct {
     int precision;              /* sem_precision: FP64, or FP32 V-cycle inside an FP64 outer */
     int nu1, nu2, k_cheb;
     double cheb_lo, cheb_hi;
-    int power_its;
+    int lanczos_steps;
     int nlevels;
     int level_p[SEM_MAX_LEVELS];
     double rtol, atol;
@@ -142,7 +143,7 @@ typedef struct {
 typedef struct sem_handle sem_handle;
 
 /* Defaults for finest order P: PCG, FP64, nu1 = nu2 = 1, k_cheb = 4,
- * cheb_lo = 0.05, cheb_hi = 1.1, power_its = 20, levels P -> ... -> 1 from the
+ * cheb_lo = 0.05, cheb_hi = 1.1, lanczos_steps = 30, levels P -> ... -> 1 from the
  * table {6:6,3,1; 5:5,3,1; 4:4,2,1; 3:3,2,1; 2:2,1; 1:1}, rtol 1e-8, atol 0,
  * imax 200, gmres_m 30, coarse_rtol 1e-3, coarse_imax 5000, inner_imax 0,
  * inner_rtol 1e-4.  The smoother and coarse-tolerance defaults minimise the

@@ -15,8 +15,11 @@ Readings of the paper used here (the CUDA library follows the same ones):
 * Stop test ||r||_2 <= rtol ||f||_2 + atol on the unpreconditioned free residual.
 * Smoother (not in the paper, which uses additive Schwarz): Chebyshev
   iteration of degree k on D^{-1} A (D = diagonal of A) for the interval
-  [lo*b, b], b = hi * lambda_hat, lambda_hat from 20 power iterations on
-  D^{-1} A started at x_i = sin(i + 1) on the free nodes.
+  [lo*b, b], b = hi * lambda_hat.  lambda_hat is the largest Ritz value of
+  30 Lanczos steps on D^{-1/2} A D^{-1/2} (free nodes) started from D^{-1/2} x0,
+  x0_i = sin(i + 1): a lower bound of lambda_max that converges far faster than
+  the power iteration (which stayed 16-22 % below lambda_max after 20 steps on
+  some sigma-prism meshes, enough for the smoother to amplify the top modes).
 """
 from __future__ import annotations
 
@@ -73,7 +76,7 @@ class MGOperators:
     """Matrices of every level for the free-node system (Dirichlet rows/cols zeroed)."""
 
     def __init__(self, prob: Problem, nu1=1, nu2=1, k_cheb=3, lo=0.25, hi=1.1,
-                 power_its=20, lambdas=None):
+                 lanczos_steps=30, lambdas=None):
         self.prob = prob
         self.L = len(prob.levels)
         self.nu1, self.nu2, self.k = nu1, nu2, k_cheb
@@ -91,7 +94,7 @@ class MGOperators:
         self.P = [prolongation(prob, li) for li in range(self.L - 1)]
         self.lam = []
         for li in range(self.L - 1):
-            lam = power_lambda(self.A[li], self.Dinv[li], prob.levels[li].dmask, power_its) \
+            lam = lanczos_lambda(self.A[li], self.Dinv[li], prob.levels[li].dmask, lanczos_steps) \
                 if lambdas is None else lambdas[li]
             self.lam.append(lam)
         c = prob.levels[-1]
@@ -160,18 +163,36 @@ def prolongation(prob: Problem, li: int) -> sp.csr_matrix:
     return P
 
 
-def power_lambda(A, Dinv, dmask, its=20) -> float:
-    """Largest eigenvalue estimate of D^{-1} A: x0_i = sin(i+1) on free nodes,
-    x <- y/||y|| with y = D^{-1} A x; returns the last ||y||."""
+def lanczos_lambda(A, Dinv, dmask, steps=30) -> float:
+    """Largest eigenvalue estimate of D^{-1} A: the largest eigenvalue of the
+    tridiagonal matrix T_k of k = ``steps`` Lanczos steps (no reorthogonalisation)
+    on the symmetric B = D^{-1/2} A_FF D^{-1/2}, started from v0 = D^{-1/2} x0 / ||.||
+    with x0_i = sin(i + 1) on the free nodes (Lanczos, e.g. Saad, Iterative
+    Methods for Sparse Linear Systems, Sec. 6.6).  Stops early when the Krylov
+    space is exhausted (beta_j = 0), where T_j is exact."""
+    free = ~np.asarray(dmask, dtype=bool)
     n = A.shape[0]
-    x = np.where(dmask, 0.0, np.sin(np.arange(n) + 1.0))
-    x = x / np.linalg.norm(x)
-    lam = 0.0
-    for _ in range(its):
-        y = Dinv * (A @ x)
-        lam = np.linalg.norm(y)
-        x = y / lam
-    return float(lam)
+    x0 = np.sin(np.arange(n) + 1.0)[free]
+    s = np.sqrt(Dinv[free])                     # D^{-1/2}
+    Aff = A[free][:, free]
+    v = s * x0
+    v = v / np.linalg.norm(v)
+    v_prev = np.zeros_like(v)
+    alphas, betas = [], []
+    beta = 0.0
+    for _ in range(steps):
+        w = s * (Aff @ (s * v)) - beta * v_prev
+        a = float(w @ v)
+        w = w - a * v
+        alphas.append(a)
+        beta = float(np.linalg.norm(w))
+        if beta <= 1e-14 * abs(a):
+            break
+        betas.append(beta)
+        v_prev, v = v, w / beta
+    k = len(alphas)
+    T = np.diag(alphas) + np.diag(betas[:k - 1], 1) + np.diag(betas[:k - 1], -1)
+    return float(np.linalg.eigvalsh(T).max())
 
 
 def chebyshev(apply, Dinv, f, x, k, a, b):

@@ -40,7 +40,7 @@ class SemMesh(Structure):
 
 class SemOptions(Structure):
     _fields_ = [("outer", c_int), ("precision", c_int), ("nu1", c_int), ("nu2", c_int), ("k_cheb", c_int),
-                ("cheb_lo", c_double), ("cheb_hi", c_double), ("power_its", c_int), ("nlevels", c_int),
+                ("cheb_lo", c_double), ("cheb_hi", c_double), ("lanczos_steps", c_int), ("nlevels", c_int),
                 ("level_p", c_int * SEM_MAX_LEVELS), ("rtol", c_double), ("atol", c_double), ("imax", c_int),
                 ("gmres_m", c_int), ("coarse_rtol", c_double), ("coarse_imax", c_int), ("profile", c_int),
                 ("inner_imax", c_int), ("inner_rtol", c_double), ("debug_barrier_extra", c_int),

@@ -134,12 +134,17 @@ sem_status coarse_solve(sem_handle* h, const double* b, double* x, cudaStream_t 
                                    rt * rt, h->opts.coarse_imax, (unsigned)h->opts.debug_barrier_extra, s));
         if (h->capturing) return SEM_OK;     // checked after the batched solve
         CKS(cudaMemcpyAsync(sc.hflags, sc.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CKS(cudaMemcpyAsync(sc.hpinned + S_CG_RR, sc.scal + S_CG_RR, sizeof(double), cudaMemcpyDeviceToHost, s));
         sc.hflags[4] = 0;
         if (!single) CKS(cudaMemcpyAsync(sc.hflags + 4, sc.counter + 3, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         CKS(cudaStreamSynchronize(s));
         if (sc.hflags[4] != 0) {
             set_error("coarse CG: a grid barrier wait ran out (device timeout)");
             return SEM_TIMEOUT;
+        }
+        if (!std::isfinite(sc.hpinned[S_CG_RR])) {
+            set_error("coarse CG: non-finite residual (non-finite right-hand side)");
+            return SEM_NAN;
         }
     } else {
         K(cg_init(C.N, b, C.dinv, x, h->cr, h->cz, h->cp, sc, rt * rt, s));
@@ -365,28 +370,79 @@ sem_status read_scalars(sem_handle* h, int first, int count, cudaStream_t s) {
     return SEM_OK;
 }
 
-// Power iteration for lambda_hat of D^{-1} A on level li.
+// Largest eigenvalue of the symmetric tridiagonal matrix with diagonal a[0..k) and
+// off-diagonal b[0..k-1), by bisection on the Sturm count (the number of
+// eigenvalues below x equals the number of negative pivots of T - x I).
+static double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& b) {
+    const int k = (int)a.size();
+    double lo = a[0], hi = a[0];
+    for (int j = 0; j < k; ++j) {
+        const double r = (j > 0 ? std::fabs(b[j - 1]) : 0.0) + (j + 1 < k ? std::fabs(b[j]) : 0.0);
+        lo = std::min(lo, a[j] - r);
+        hi = std::max(hi, a[j] + r);
+    }
+    auto below = [&](double x) {
+        int cnt = 0;
+        double d = 1.0;
+        for (int j = 0; j < k; ++j) {
+            const double bb = j > 0 ? b[j - 1] * b[j - 1] : 0.0;
+            d = (a[j] - x) - (j > 0 ? bb / d : 0.0);
+            if (d == 0.0) d = -1e-300;
+            if (d < 0.0) ++cnt;
+        }
+        return cnt;
+    };
+    for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(std::fabs(lo), std::fabs(hi)); ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (below(mid) < k) lo = mid;     // some eigenvalue lies at or above mid
+        else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// lambda_hat of D^{-1} A on level li: the largest Ritz value of lanczos_steps Lanczos
+// steps, taken from Jacobi-preconditioned CG on A x = x0 (x0_i = sin(i + 1) on the
+// free nodes) through the CG-Lanczos relation T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1},
+// T_j,j+1 = sqrt(beta_j)/alpha_j (e.g. Saad, Iterative Methods for Sparse Linear
+// Systems, Sec. 6.7.3).  The estimate is a lower bound of lambda_max; power
+// iteration converges too slowly on some sigma-prism meshes for the Chebyshev
+// interval to cover the top of the spectrum.
 sem_status estimate_lambda(sem_handle* h, int li) {
     Level& L = h->lv[li];
     std::vector<double> x0(L.N, 0.0);
     std::vector<char> dm(L.N, 0);
     for (long long i : L.hdir) dm[i] = 1;
-    double nrm = 0;
     for (long long i = 0; i < L.N; ++i)
-        if (!dm[i]) { x0[i] = std::sin((double)i + 1.0); nrm += x0[i] * x0[i]; }
-    nrm = std::sqrt(nrm);
-    for (long long i = 0; i < L.N; ++i) x0[i] /= nrm;
-    CKS(cudaMemcpy(L.u, x0.data(), sizeof(double) * L.N, cudaMemcpyHostToDevice));
+        if (!dm[i]) x0[i] = std::sin((double)i + 1.0);
+    CKS(cudaMemcpy(L.f, x0.data(), sizeof(double) * L.N, cudaMemcpyHostToDevice));
     cudaStream_t s = 0;
-    for (int it = 0; it < h->opts.power_its; ++it) {
-        CKS(cudaMemsetAsync(L.y, 0, sizeof(double) * L.N, s));
-        K(launch_apply64(L, L.u, L.y, false, nullptr, s));
-        K(cheb_first<double>(L.N, 1.0, L.dinv, L.y, L.d, L.f, s));   // d = D^{-1} A x (f: scratch copy)
-        K(dot64(L.N, L.d, L.d, h->sc, h->sc.scal + S_TMP, s));
-        K(scale64(L.N, L.d, h->sc.scal + S_TMP, L.u, s));             // x = d / ||d||
+    Scratch& sc = h->sc;
+    K(cg_init(L.N, L.f, L.dinv, L.u, h->r, h->z, h->p, sc, 0.0, s));
+    std::vector<double> alpha, beta;
+    for (int it = 0; it < h->opts.lanczos_steps; ++it) {
+        CKS(cudaMemsetAsync(h->q, 0, sizeof(double) * L.N, s));
+        K(launch_apply64(L, h->p, h->q, false, nullptr, s));
+        K(cg_pq(L.N, h->p, h->q, sc, s));
+        double rp[2];                                          // rho_j, p_j^T A p_j
+        CKS(cudaMemcpy(rp, sc.scal + S_CG_RHO, 2 * sizeof(double), cudaMemcpyDeviceToHost));
+        if (!(rp[0] > 0.0) || !(rp[1] > 0.0) || !std::isfinite(rp[0] / rp[1])) break;
+        alpha.push_back(rp[0] / rp[1]);
+        K(cg_update(L.N, L.dinv, L.u, h->r, h->z, h->p, h->q, sc, s));
+        double bt = 0.0;
+        CKS(cudaMemcpy(&bt, sc.scal + S_CG_BETA, sizeof(double), cudaMemcpyDeviceToHost));
+        if (!(bt > 0.0) || !std::isfinite(bt)) break;          // Krylov space exhausted: T is exact
+        beta.push_back(bt);
+        K(cg_direction(L.N, h->z, h->p, sc, s));
     }
-    CKST(read_scalars(h, S_TMP, 1, s));
-    L.lam = std::sqrt(h->sc.hpinned[S_TMP]);
+    if (alpha.empty()) { set_error("eigenvalue estimate: no Lanczos step (zero or indefinite level)"); return SEM_BREAKDOWN; }
+    const int k = (int)alpha.size();
+    std::vector<double> a(k), b(k > 1 ? k - 1 : 0);
+    for (int j = 0; j < k; ++j) {
+        a[j] = 1.0 / alpha[j] + (j > 0 ? beta[j - 1] / alpha[j - 1] : 0.0);
+        if (j + 1 < k) b[j] = std::sqrt(beta[j]) / alpha[j];
+    }
+    L.lam = tridiag_max_eig(a, b);
+    if (!std::isfinite(L.lam) || !(L.lam > 0.0)) { set_error("eigenvalue estimate not finite"); return SEM_NAN; }
     return SEM_OK;
 }
 
@@ -478,7 +534,7 @@ sem_status check_options(const sem_options& o, int P) {
     }
     for (int i = 1; i < o.nlevels; ++i)
         if (o.level_p[i] >= o.level_p[i - 1]) { set_error("level orders must decrease"); return SEM_EINVAL; }
-    if (o.k_cheb < 1 || o.k_cheb > 15 || o.nu1 < 0 || o.nu2 < 0 || o.power_its < 1) {
+    if (o.k_cheb < 1 || o.k_cheb > 15 || o.nu1 < 0 || o.nu2 < 0 || o.lanczos_steps < 1) {
         set_error("smoother parameters out of range");
         return SEM_EINVAL;
     }
@@ -661,7 +717,7 @@ void sem_default_options(sem_options* o, int P) {
     o->k_cheb = 4;
     o->cheb_lo = 0.05;
     o->cheb_hi = 1.1;
-    o->power_its = 20;
+    o->lanczos_steps = 30;
     static const int table[7][3] = {{1, 0, 0}, {1, 0, 0}, {2, 1, 0}, {3, 2, 1}, {4, 2, 1}, {5, 3, 1}, {6, 3, 1}};
     if (P < 1 || P > 6) P = 1;
     int n = 0;
@@ -733,10 +789,11 @@ sem_status sem_setup(const sem_mesh* m, int P, const sem_options* opts, sem_hand
     if (st == SEM_OK) st = build_workspace(h);
     for (int li = 0; li + 1 < o.nlevels && st == SEM_OK; ++li) st = estimate_lambda(h, li);
     if (st == SEM_OK && o.autotune && m->dim == 3) {
-        // u / u32 hold finite data after the eigenvalue estimate; tune on them
+        // u holds the Lanczos iterate on the smoothed levels; zero it on the coarsest
         for (Level& L : h->lv) {
             if (st != SEM_OK) break;
-            cudaError_t e = to_f32(L.N, L.u, L.u32, 0);
+            cudaError_t e = (&L == &h->lv.back()) ? cudaMemset(L.u, 0, sizeof(double) * L.N) : cudaSuccess;
+            if (e == cudaSuccess) e = to_f32(L.N, L.u, L.u32, 0);
             if (e == cudaSuccess) e = tune_prism(L, false);
             if (e == cudaSuccess) e = tune_prism(L, true);
             if (e != cudaSuccess) { set_error(std::string("autotune: ") + cudaGetErrorString(e)); st = SEM_ECUDA; }

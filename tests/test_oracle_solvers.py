@@ -1,10 +1,12 @@
 """Pins of the oracle's solvers: Chebyshev smoothing against its closed-form error
-polynomial, the power-iteration estimate against an eigen-solver, the V-cycle
+polynomial, the Lanczos eigenvalue estimate against a closed form and eigen-solvers, the V-cycle
 (Algorithm 1) against dense two-level algebra and its symmetry, and the outer
 iterations (Algorithms 2, 3 and FGMRES) against the direct solve."""
 import numpy as np
 import pytest
 import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 from numpy.polynomial import chebyshev as C
 
 import workloads as W
@@ -33,7 +35,17 @@ def test_chebyshev_error_is_scaled_chebyshev_polynomial(k):
     assert np.allclose(x - xs, _cheb_poly(lam, k, a, b) * (x0 - xs), atol=1e-12)
 
 
-def test_power_iteration_tends_to_largest_eigenvalue():
+def test_lanczos_estimate_matches_closed_form_of_1d_laplacian():
+    # A = tridiag(-1, 2, -1) of n interior nodes: D^{-1} A = A / 2 has eigenvalues
+    # 1 - cos(j pi / (n + 1)), so lambda_max = 1 + cos(pi / (n + 1)).
+    for n in (7, 40):
+        A = sp.diags([-np.ones(n - 1), 2 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1]).tocsr()
+        dinv = np.full(n, 0.5)
+        lam = S.lanczos_lambda(A, dinv, np.zeros(n, dtype=bool), steps=n)
+        assert abs(lam - (1 + np.cos(np.pi / (n + 1)))) < 1e-12
+
+
+def test_lanczos_estimate_is_a_converging_lower_bound():
     prob = Problem(W.slice2d(4, 2), [3, 1])
     ops = S.MGOperators(prob)
     lev = prob.levels[0]
@@ -41,10 +53,27 @@ def test_power_iteration_tends_to_largest_eigenvalue():
     dd = 1.0 / ops.Dinv[0][lev.free]
     Ds = np.diag(1 / np.sqrt(dd))
     lmax = np.linalg.eigvalsh(Ds @ A @ Ds).max()
-    lam_long = S.power_lambda(ops.A[0], ops.Dinv[0], lev.dmask, 3000)
-    assert abs(lam_long - lmax) < 1e-6 * lmax
-    lam20 = S.power_lambda(ops.A[0], ops.Dinv[0], lev.dmask, 20)
-    assert 0.8 * lmax < lam20 <= lmax * (1 + 1e-12)
+    # Ritz values interlace: the largest grows with the step count towards lambda_max
+    est = [S.lanczos_lambda(ops.A[0], ops.Dinv[0], lev.dmask, k) for k in (3, 6, 12, 24)]
+    assert all(b >= a - 1e-12 for a, b in zip(est, est[1:]))
+    assert est[-1] <= lmax * (1 + 1e-12) and est[-1] >= 0.99 * lmax
+    assert ops.lam[0] <= lmax * (1 + 1e-12) and ops.lam[0] >= 0.99 * lmax
+    full = S.lanczos_lambda(ops.A[0], ops.Dinv[0], lev.dmask, len(lev.free))
+    assert abs(full - lmax) < 1e-9 * lmax
+
+
+@pytest.mark.parametrize("n,P", [(6, 6), (10, 3)])
+def test_lanczos_estimate_on_sigma_prism_tanks(n, P):
+    # wavy-surface prism tanks: 30 steps come within 2 % of lambda_max (ARPACK)
+    mesh = W.box3d(n, n, 4, eta_modes=W.random_tank(1019)[0].eta_modes)
+    prob = Problem(mesh, [P, 1])
+    ops = S.MGOperators(prob)
+    lev = prob.levels[0]
+    A = prob.free_matrix(0)
+    d = A.diagonal()
+    B = sp.diags(1 / np.sqrt(d)) @ A @ sp.diags(1 / np.sqrt(d))
+    lmax = spla.eigsh(B, k=1, which="LA", tol=1e-10, return_eigenvectors=False)[0]
+    assert 0.98 * lmax <= ops.lam[0] <= lmax * (1 + 1e-10)
 
 
 def test_two_level_vcycle_equals_dense_algebra():
