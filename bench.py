@@ -48,7 +48,7 @@ TRAFFIC_SRC_SHA = "78f7f4ef51218cb6"
 def workload_name(n, nl, P):
     return (f"3D sigma-prism box 2pi x 2pi x 1: {n}x{n} quads -> {2 * n * n} triangles x {nl} layers = "
             f"{2 * n * n * nl} prisms, P={P}, eta=0.1 sin(x)cos(y); PCG + p-multigrid V-cycle "
-            f"(Chebyshev-Jacobi k=4 on [0.05b, b], nu=1+1, FP64 coarse CG at order 1 to 1e-3) to rtol 1e-8")
+            f"(Chebyshev-Jacobi k=5 on [0.01b, b], b = 1.05 lambda_hat (30 Lanczos steps), nu=1+1, FP64 coarse CG at order 1 to 1e-3) to rtol 1e-8")
 
 
 def levels_for(P):

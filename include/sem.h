@@ -142,8 +142,8 @@ typedef struct {
 
 typedef struct sem_handle sem_handle;
 
-/* Defaults for finest order P: PCG, FP64, nu1 = nu2 = 1, k_cheb = 4,
- * cheb_lo = 0.05, cheb_hi = 1.1, lanczos_steps = 30, levels P -> ... -> 1 from the
+/* Defaults for finest order P: PCG, FP64, nu1 = nu2 = 1, k_cheb = 5,
+ * cheb_lo = 0.01, cheb_hi = 1.05, lanczos_steps = 30, levels P -> ... -> 1 from the
  * table {6:6,3,1; 5:5,3,1; 4:4,2,1; 3:3,2,1; 2:2,1; 1:1}, rtol 1e-8, atol 0,
  * imax 200, gmres_m 30, coarse_rtol 1e-3, coarse_imax 5000, inner_imax 0,
  * inner_rtol 1e-4.  The smoother and coarse-tolerance defaults minimise the

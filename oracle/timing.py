@@ -43,7 +43,7 @@ def main(argv=None):
     lev = prob.levels[0]
     C = prob.coords(0)
     phiD = W.potential3d(*C[lev.dirichlet].T)
-    ops = S.MGOperators(prob, k_cheb=4, lo=0.05, hi=1.1)
+    ops = S.MGOperators(prob, k_cheb=5, lo=0.01, hi=1.05)
     setup_s = time.perf_counter() - t0
     for _ in range(a.warmup):
         S.pcg(ops, S.lift(prob, phiD), rtol=a.rtol)

@@ -714,9 +714,9 @@ void sem_default_options(sem_options* o, int P) {
     o->precision = SEM_PREC_FP64;
     o->nu1 = 1;
     o->nu2 = 1;
-    o->k_cheb = 4;
-    o->cheb_lo = 0.05;
-    o->cheb_hi = 1.1;
+    o->k_cheb = 5;
+    o->cheb_lo = 0.01;
+    o->cheb_hi = 1.05;
     o->lanczos_steps = 30;
     static const int table[7][3] = {{1, 0, 0}, {1, 0, 0}, {2, 1, 0}, {3, 2, 1}, {4, 2, 1}, {5, 3, 1}, {6, 3, 1}};
     if (P < 1 || P > 6) P = 1;

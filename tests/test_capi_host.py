@@ -47,7 +47,7 @@ def test_default_options(sem):
     assert [o.level_p[i] for i in range(o.nlevels)] == [6, 3, 1]
     o = sem.sem_default_options(4)
     assert [o.level_p[i] for i in range(o.nlevels)] == [4, 2, 1]
-    assert o.k_cheb == 4 and o.nu1 == 1 and o.nu2 == 1 and o.rtol == 1e-8 and o.cheb_lo == 0.05
+    assert o.k_cheb == 5 and o.nu1 == 1 and o.nu2 == 1 and o.rtol == 1e-8 and o.cheb_lo == 0.01
 
 
 @pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6])

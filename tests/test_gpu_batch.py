@@ -77,3 +77,34 @@ def test_batch_rejects_handles_not_prepared_for_it(sem):
         assert e.value.status == sem.SEM_EINVAL, sem.sem_last_error()
     finally:
         s.close()
+
+
+def test_full_size_tanks_whose_spectrum_defeats_power_iteration(sem):
+    """Two tanks of the 32-tank benchmark draw (3528 prisms at P = 6 and 6728 at
+    P = 3) whose lambda_max the 20-step power iteration underestimated by 16-22 %,
+    which made the Chebyshev sweep amplify the top modes: with the Lanczos estimate
+    both converge, batched and alone, and lambda_hat matches the oracle's."""
+    from oracle.solvers import MGOperators
+    tanks = []
+    try:
+        for i in (1019, 1031):
+            mesh, P, modes = W.random_tank(i)
+            xy = sem.sem_mesh_nodes2d(mesh, P)
+            s = sem.Solver(mesh, P, eta_nodal=mesh.eta(xy[:, 0], xy[:, 1]), levels=LEVELS[P],
+                           precision="mixed_fp32", outer="pdc", batch=1, imax=100)
+            C = s.coords(0)
+            dD = torch.tensor(W.tank_potential(*C[s.dirichlet_nodes(0)].T, modes), device="cuda")
+            tanks.append((mesh, P, s, dD))
+        phis = [torch.zeros(t[2].query(0)["ndof"], dtype=torch.float64, device="cuda") for t in tanks]
+        stats = sem.laplace_solve_batch([t[2].h for t in tanks], [t[3] for t in tanks], 1e-8, phis)
+        for (mesh, P, s, dD), phi, st in zip(tanks, phis, stats):
+            assert st["status"] == 0 and st["iters"] <= 40 and st["res_final"] <= 1e-8 * st["fnorm"], st
+            alone = torch.zeros_like(phi)
+            st1 = s.solve(dD, alone, tol=1e-8)
+            assert abs(st1["iters"] - st["iters"]) <= 1
+        mesh, P, s, _ = tanks[1]
+        ops = MGOperators(Problem(mesh, LEVELS[P][:2]))
+        assert abs(s.lambdas()[0] - ops.lam[0]) <= 1e-10 * ops.lam[0]
+    finally:
+        for t in tanks:
+            t[2].close()
