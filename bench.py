@@ -307,23 +307,49 @@ def main():
            "d2h_bytes_per_step": int(N * 8)}
     phi64 = phi.cpu().numpy()
 
-    mixed = None
+    def apply_view(ms_total, launches, word):
+        """Live event time of the finest-level single-precision applies against the HBM roofline."""
+        if not launches:
+            return None
+        avg_s = ms_total / launches / 1000.0
+        byts = apply_bytes(P, E, N, word=word)
+        return {"avg_launch_ms": avg_s * 1e3, "launches": launches, "algorithmic_bytes": byts,
+                "achieved_gbs": byts / avg_s / 1e9, "peak_gbs": hbm_peak,
+                "frac_of_hbm": byts / avg_s / 1e9 / hbm_peak,
+                "achieved_tflops": apply_flops_per_elem(P) * E / avg_s / 1e12}
+
+    mixed = mixed_tc = None
     if not a.no_mixed:
-        ms_solver = sem.Solver(mesh, P, eta_nodal=eta, levels=levels_for(P), precision="mixed_fp32", outer="pdc",
-                               inner_imax=a.inner_imax, inner_rtol=a.inner_rtol, coarse_rtol=a.coarse_rtol)
-        phi_m = torch.empty(N, dtype=torch.float64, device="cuda")
-        ms_m, st_m = timed(ms_solver, a.steps, a.warmup, phi_m)
-        ms_m = max_over_ranks(ms_m)
-        err = float(np.abs(phi_m.cpu().numpy() - phi64).max() / np.abs(phi64).max())
-        mixed = {"value": dof * a.steps * world / (ms_m / 1000.0), "unit": UNIT,
-                 "ms_per_step": ms_m / a.steps, "outer_iters": st_m[-1]["iters"],
-                 "inner_iters": st_m[-1]["inner_iters"], "res_final_rel": st_m[-1]["res_final"] / st_m[-1]["fnorm"],
-                 "speedup_vs_fp64": (dof * a.steps * world / (ms_m / 1000.0)) / value,
-                 "max_rel_diff_vs_fp64_solution": err,
-                 "outer": "FP64 defect correction (Algorithm 2) with FP64 residual",
-                 "inner": f"FP32 PCG to {a.inner_rtol:g} (<= {a.inner_imax} its) preconditioned by the FP32 V-cycle; "
-                          f"FP64 coarse CG to {a.coarse_rtol:g}"}
-        ms_solver.close()
+        for prec in ("mixed_fp32", "mixed_tf32"):
+            ms_solver = sem.Solver(mesh, P, eta_nodal=eta, levels=levels_for(P), precision=prec, outer="pdc",
+                                   inner_imax=a.inner_imax, inner_rtol=a.inner_rtol, coarse_rtol=a.coarse_rtol,
+                                   profile=1)
+            phi_m = torch.empty(N, dtype=torch.float64, device="cuda")
+            ms_m, st_m = timed(ms_solver, a.steps, a.warmup, phi_m)
+            ms_m = max_over_ranks(ms_m)
+            err = float(np.abs(phi_m.cpu().numpy() - phi64).max() / np.abs(phi64).max())
+            smooth = ("TF32 tensor-core apply (mma.sync m16n8k8, FP32 accumulation) in the Chebyshev sweeps of "
+                      "the P and intermediate levels, FP32 apply elsewhere" if prec == "mixed_tf32"
+                      else "FP32 SIMT apply throughout")
+            obj = {"value": dof * a.steps * world / (ms_m / 1000.0), "unit": UNIT,
+                   "ms_per_step": ms_m / a.steps, "outer_iters": st_m[-1]["iters"],
+                   "inner_iters": st_m[-1]["inner_iters"], "res_final_rel": st_m[-1]["res_final"] / st_m[-1]["fnorm"],
+                   "speedup_vs_fp64": (dof * a.steps * world / (ms_m / 1000.0)) / value,
+                   "max_rel_diff_vs_fp64_solution": err,
+                   "outer": "FP64 defect correction (Algorithm 2) with FP64 residual",
+                   "inner": f"FP32 PCG to {a.inner_rtol:g} (<= {a.inner_imax} its) preconditioned by the "
+                            f"single-precision V-cycle; FP64 coarse CG to {a.coarse_rtol:g}",
+                   "smoothing_operator": smooth,
+                   "apply_fp32": apply_view(sum(x["apply32_ms"] for x in st_m),
+                                            sum(x["apply32_launches"] for x in st_m), 4),
+                   "apply_fp64": apply_view(sum(x["apply_ms"] for x in st_m), sum(x["apply_launches"] for x in st_m), 8)}
+            if prec == "mixed_tf32":
+                obj["apply_tf32_tensor_cores"] = apply_view(sum(x["apply_tc_ms"] for x in st_m),
+                                                            sum(x["apply_tc_launches"] for x in st_m), 4)
+                mixed_tc = obj
+            else:
+                mixed = obj
+            ms_solver.close()
 
     learned = None
     if not a.no_learned:
@@ -380,6 +406,20 @@ def main():
         bstats = sem.laplace_solve_batch(hs, etas, 1e-8, outs)
         torch.cuda.synchronize()
         t_batch = time.perf_counter() - t0
+        # the host-stepped lockstep form on the same tanks (a first handle with batch_mode = 1)
+        mesh0, P0, _ = W.random_tank(1000)
+        xy0 = sem.sem_mesh_nodes2d(mesh0, P0)
+        lock0 = sem.Solver(mesh0, P0, eta_nodal=mesh0.eta(xy0[:, 0], xy0[:, 1]), levels=levels_for(P0),
+                           precision="mixed_fp32", outer="pdc", batch=1, coarse_rtol=a.coarse_rtol, imax=400,
+                           batch_mode=1)
+        hs_lock = [lock0.h] + hs[1:]
+        sem.laplace_solve_batch(hs_lock, etas, 1e-8, outs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sem.laplace_solve_batch(hs_lock, etas, 1e-8, outs)
+        torch.cuda.synchronize()
+        t_lock = time.perf_counter() - t0
+        lock0.close()
         for t in tanks:
             t[0].solve(t[1], t[2], tol=1e-8)
         torch.cuda.synchronize()
@@ -393,13 +433,15 @@ def main():
                    "orders": {str(p): sum(1 for t in tanks if t[4] == p) for p in (3, 4, 5, 6)},
                    "value": dof_b / t_batch, "unit": UNIT, "solves_per_s": len(tanks) / t_batch,
                    "ms_per_batch": t_batch * 1e3, "one_by_one_ms": t_seq * 1e3, "speedup_vs_one_by_one": t_seq / t_batch,
+                   "host_stepped_lockstep_ms": t_lock * 1e3,
                    "graph_iterations": sum(st_["graph_iterations"] for st_ in bstats),
                    "iterations": sum(st_["iters"] for st_ in bstats),
                    "tile_shapes_fp32_fine": sorted({t[0].tile_shapes(0)[1] for t in tanks}),
                    "setup_s": t_setup,
-                   "form": "lockstep FP64 defect correction per tank (FP32 V-cycle, single-CTA FP64 coarse CG), "
-                           "each tank's iteration a captured CUDA graph replayed on its own stream; one host "
-                           "synchronisation per lockstep iteration"}
+                   "form": "FP64 defect correction per tank (FP32 V-cycle, single-CTA FP64 coarse CG); the whole "
+                           "batch one instantiated CUDA graph: per tank a branch with the lifting and a WHILE "
+                           "conditional node around one iteration whose last kernel tests convergence on the "
+                           "device; one graph launch and one host synchronisation per batch"}
         for t in tanks:
             t[0].close()
 
@@ -414,7 +456,7 @@ def main():
                            "l2": "no flush: every solve streams the 0.6 GB FP64 geometric factors (> 129 MB L2)",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "mixed_fp32": mixed, "learned": learned, "batched": batched}
+                "clocks": clk, "mixed_fp32": mixed, "mixed_tf32": mixed_tc, "learned": learned, "batched": batched}
         print(json.dumps(line), flush=True)
     solver.close()
     if world > 1:

@@ -51,7 +51,10 @@ typedef enum {
 } sem_status;
 
 typedef enum { SEM_OUTER_PCG = 0, SEM_OUTER_FGMRES = 1, SEM_OUTER_PDC = 2 } sem_outer;
-typedef enum { SEM_PREC_FP64 = 0, SEM_PREC_MIXED_FP32 = 1 } sem_precision;
+/* MIXED_FP32: FP32 V-cycle (and optional FP32 inner PCG) inside an FP64 outer iteration with
+ * FP64 residual and FP64 coarse solve.  MIXED_TF32: the same, with the Chebyshev sweeps of
+ * prism levels of order 2..6 on the tensor cores (TF32 operands, FP32 accumulation). */
+typedef enum { SEM_PREC_FP64 = 0, SEM_PREC_MIXED_FP32 = 1, SEM_PREC_MIXED_TF32 = 2 } sem_precision;
 typedef enum { SEM_SMOOTH_CHEBYSHEV = 0, SEM_SMOOTH_LEARNED = 1 } sem_smoother;
 
 /* Mesh description (host memory, read during sem_setup only).
@@ -119,6 +122,9 @@ typedef struct {
     int autotune;               /* 1 (default): time the prism apply's tile shapes (elements per CTA pass)
                                    on every level at setup and keep the faster (cached per order,
                                    precision and element-count bucket for the process) */
+    int batch_mode;             /* laplace_solve_batch with this handle first in the list: 0 (default)
+                                   the whole batch as one CUDA graph launch with the convergence test
+                                   on the device, 1 host-stepped lockstep */
 } sem_options;
 
 typedef struct {
@@ -131,13 +137,17 @@ typedef struct {
     long long vcycles;
     int coarse_iters_max;       /* largest coarse CG iteration count seen */
     double ms;                  /* wall time of the call on the stream (CUDA events) */
-    double apply_ms;            /* summed time of finest-level apply kernels (profile = 1) */
-    long long apply_launches;   /* finest-level apply kernel launches (profile = 1) */
+    double apply_ms;            /* summed time of finest-level FP64 apply kernels (profile = 1) */
+    long long apply_launches;   /* finest-level FP64 apply kernel launches (profile = 1) */
     long long kernel_launches;  /* kernels of this library launched by the call */
     long long inner_iters;      /* FP32 inner PCG iterations (MIXED_FP32 with inner_imax > 0) */
     long long learned_accepts;  /* learned sweeps kept (smoother = LEARNED) */
     long long learned_fallbacks; /* learned sweeps rejected by the residual test (Chebyshev ran instead) */
     long long graph_iterations; /* laplace_solve_batch: iterations replayed from the captured CUDA graph */
+    double apply32_ms;          /* profile = 1: summed event time of the finest-level FP32 applies */
+    long long apply32_launches;
+    double apply_tc_ms;         /* profile = 1: same for the TF32 tensor-core applies (MIXED_TF32) */
+    long long apply_tc_launches;
 } sem_stats;
 
 typedef struct sem_handle sem_handle;
@@ -182,6 +192,15 @@ sem_status sem_diagonal(const sem_handle* h, int level, double* diag_host);
  * y_F = A_FF x_F on the free nodes and y_D = x_D on the Dirichlet nodes of
  * `level` (0 = finest).  x_dev, y_dev: N doubles, distinct buffers. */
 sem_status sem_apply(sem_handle* h, int level, const double* x_dev, double* y_dev, void* stream);
+
+/* The same operator in single precision, as the mixed V-cycle applies it: the FP32
+ * kernel (tensor_cores = 0) or the TF32 tensor-core kernel of the MIXED_TF32
+ * Chebyshev sweeps (tensor_cores = 1; prism levels of order 2..6, else SEM_EINVAL;
+ * operands rounded to TF32, FP32 accumulation).  x_dev, y_dev: N floats, distinct;
+ * y_D = x_D.  The tensor-core form synchronises the stream and returns SEM_TIMEOUT
+ * if a geometric-factor copy inside the kernel did not complete within 1 s. */
+sem_status sem_apply32(sem_handle* h, int level, const float* x_dev, float* y_dev, int tensor_cores,
+                       void* stream);
 
 /* One V-cycle (Algorithm 1, zero initial guess on every level): z = M^{-1} r on
  * the finest level.  Dirichlet entries of r are ignored; those of z are 0. */
@@ -256,14 +275,18 @@ sem_status sem_cg_csr_noalloc(long long n, const int* rowptr, const int* col, co
                               int* iters_host, void* stream);
 
 /* Solve n independent problems (tanks), each set up by its own sem_setup with
- * batch = 1 and inner_imax = 0, in lockstep (Section 4.1-4.4 per tank, Algorithm 2
- * outer iteration: u <- u + M^{-1} r with the handle's V-cycle in its precision, FP64
- * residual).  Every tank runs on its own stream; its iteration (V-cycle, update, FP64
- * residual and norm) is captured once into a CUDA graph and replayed, so one lockstep
- * iteration costs one graph launch per active tank and one host synchronisation for
- * all of them.  dirichlet_eta[t] / phi[t]: device arrays of tank t as in
- * laplace_solve; stats: n entries or NULL.  Starts after prior work on `stream` and
- * makes `stream` wait for the result.  Returns the worst tank status. */
+ * batch = 1 and inner_imax = 0 (Section 4.1-4.4 per tank, Algorithm 2 outer iteration:
+ * u <- u + M^{-1} r with the handle's V-cycle in its precision, FP64 residual).
+ * batch_mode 0 of hs[0] (default): the whole batch is one instantiated CUDA graph, one
+ * branch per tank, each a WHILE conditional node around one iteration whose last kernel
+ * tests ||r|| <= rtol ||f|| + atol and the iteration limit on the device; one graph
+ * launch and one host synchronisation per call.  The graph is built on the first call
+ * and reused while the list of handles and the tolerances are the same (it is owned by
+ * hs[0]).  If it cannot be built, or with batch_mode 1: host-stepped lockstep, every
+ * tank's iteration captured into its own graph, one graph launch per active tank and
+ * one host synchronisation per iteration.  dirichlet_eta[t] / phi[t]: device arrays of
+ * tank t as in laplace_solve; a handle may appear once.  stats: n entries or NULL.
+ * Ordered after prior work on `stream`; synchronous.  Returns the worst tank status. */
 sem_status laplace_solve_batch(sem_handle* const* hs, int n, const double* const* dirichlet_eta_dev, double tol,
                                double* const* phi_dev, sem_stats* stats, void* stream);
 

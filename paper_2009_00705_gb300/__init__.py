@@ -22,12 +22,12 @@ SEM_MAX_LEVELS = 8
 SEM_OK, SEM_NOT_CONVERGED = 0, 1
 SEM_EINVAL, SEM_ECUDA, SEM_ENOMEM, SEM_NAN, SEM_BREAKDOWN, SEM_TIMEOUT = -1, -2, -3, -4, -5, -6
 OUTER = {"pcg": 0, "fgmres": 1, "pdc": 2}
-PRECISION = {"fp64": 0, "mixed_fp32": 1}
+PRECISION = {"fp64": 0, "mixed_fp32": 1, "mixed_tf32": 2}
 SMOOTHER = {"chebyshev": 0, "learned": 1}
 
 EXPORTS = ("sem_default_options", "sem_mesh_nodes2d", "sem_setup", "sem_destroy", "sem_query",
            "sem_dirichlet_nodes", "sem_node_coords", "sem_element_map", "sem_lambda_max", "sem_diagonal",
-           "sem_apply", "pmg_vcycle", "laplace_solve", "laplace_solve_host", "sem_last_error",
+           "sem_apply", "sem_apply32", "pmg_vcycle", "laplace_solve", "laplace_solve_host", "sem_last_error",
            "sem_cg_csr_noalloc", "sem_mlp_get_weights", "sem_mlp_set_weights", "sem_mlp_forward",
            "sem_mlp_gradient", "sem_learned_train", "laplace_solve_batch", "sem_tile_shapes")
 
@@ -45,7 +45,7 @@ class SemOptions(Structure):
                 ("gmres_m", c_int), ("coarse_rtol", c_double), ("coarse_imax", c_int), ("profile", c_int),
                 ("inner_imax", c_int), ("inner_rtol", c_double), ("debug_barrier_extra", c_int),
                 ("smoother", c_int), ("mlp_hidden", c_int), ("mlp_seed", ctypes.c_ulonglong), ("batch", c_int),
-                ("autotune", c_int)]
+                ("autotune", c_int), ("batch_mode", c_int)]
 
 
 class SemStats(Structure):
@@ -54,7 +54,8 @@ class SemStats(Structure):
                 ("vcycles", c_longlong), ("coarse_iters_max", c_int), ("ms", c_double),
                 ("apply_ms", c_double), ("apply_launches", c_longlong), ("kernel_launches", c_longlong),
                 ("inner_iters", c_longlong), ("learned_accepts", c_longlong), ("learned_fallbacks", c_longlong),
-                ("graph_iterations", c_longlong)]
+                ("graph_iterations", c_longlong), ("apply32_ms", c_double), ("apply32_launches", c_longlong),
+                ("apply_tc_ms", c_double), ("apply_tc_launches", c_longlong)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -94,6 +95,7 @@ def lib():
     L.sem_tile_shapes.argtypes = [c_void_p, c_int, POINTER(c_int), POINTER(c_int)]
     L.sem_tile_shapes.restype = c_int
     L.sem_apply.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_void_p]
+    L.sem_apply32.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_int, c_void_p]
     L.pmg_vcycle.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
     L.laplace_solve.argtypes = [c_void_p, c_void_p, c_void_p, c_double, c_void_p, POINTER(SemStats), c_void_p]
     L.laplace_solve_host.argtypes = [c_void_p, c_void_p, c_void_p, c_double, c_void_p, POINTER(SemStats),
@@ -115,7 +117,7 @@ def lib():
                  "sem_learned_train", "laplace_solve_batch"):
         getattr(L, name).restype = c_int
     for name in ("sem_mesh_nodes2d", "sem_setup", "sem_query", "sem_dirichlet_nodes", "sem_node_coords",
-                 "sem_element_map", "sem_lambda_max", "sem_diagonal", "sem_apply", "pmg_vcycle",
+                 "sem_element_map", "sem_lambda_max", "sem_diagonal", "sem_apply", "sem_apply32", "pmg_vcycle",
                  "laplace_solve", "laplace_solve_host"):
         getattr(L, name).restype = c_int
     _lib = L
@@ -259,6 +261,11 @@ def sem_apply(h: int, level: int, x, y, stream=None) -> None:
     _check(lib().sem_apply(h, level, _ptr(x), _ptr(y), _stream(stream)))
 
 
+def sem_apply32(h: int, level: int, x, y, tensor_cores: bool = False, stream=None) -> None:
+    """FP32 operator apply (x, y float32 device buffers); tensor_cores selects the TF32 MMA kernel."""
+    _check(lib().sem_apply32(h, level, _ptr(x), _ptr(y), int(bool(tensor_cores)), _stream(stream)))
+
+
 def pmg_vcycle(h: int, r, z, stream=None) -> None:
     _check(lib().pmg_vcycle(h, _ptr(r), _ptr(z), _stream(stream)))
 
@@ -400,6 +407,9 @@ class Solver:
 
     def apply(self, level, x, y, stream=None):
         sem_apply(self.h, level, x, y, stream)
+
+    def apply32(self, level, x, y, tensor_cores=False, stream=None):
+        sem_apply32(self.h, level, x, y, tensor_cores, stream)
 
     def vcycle(self, r, z, stream=None):
         pmg_vcycle(self.h, r, z, stream)

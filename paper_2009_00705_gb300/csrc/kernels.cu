@@ -1038,8 +1038,9 @@ __global__ void k_axpy(long long n, double a, const double* __restrict__ x, doub
         y[i] += a * x[i];
 }
 
-__global__ void k_copy_idx(long long nd, const long long* __restrict__ idx, const double* __restrict__ src,
-                           double* __restrict__ dst) {
+template <typename T>
+__global__ void k_copy_idx(long long nd, const long long* __restrict__ idx, const T* __restrict__ src,
+                           T* __restrict__ dst) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nd; i += (long long)gridDim.x * blockDim.x)
         dst[idx[i]] = src[idx[i]];
 }
@@ -1180,6 +1181,37 @@ cudaError_t dot64(long long n, const double* a, const double* b, Scratch& sc, do
     k_dot<<<reduce_blocks(), kRedThreads, 0, s>>>(n, a, b, sc.part, sc.counter, out);
     return cudaGetLastError();
 }
+__global__ void k_batch_loop(double* scal, int* flags, double rtol, double atol, int imax,
+                             cudaGraphConditionalHandle cond, int init) {
+    const double ff = scal[S_FF];
+    const double thr = rtol * sqrt(ff) + atol;
+    int it = flags[F_BATCH_ITERS];
+    double rr = ff;
+    if (init) {
+        it = 0;
+    } else {
+        rr = scal[S_RR];
+        it += 1;
+    }
+    flags[F_BATCH_ITERS] = it;
+    const bool finite = isfinite(rr);
+    const bool met = finite && rr <= thr * thr;
+    const bool more = finite && !met && it < imax;
+    flags[F_BATCH_STATUS] = !finite ? -4 : (met ? 0 : 1);
+    cudaGraphSetConditional(cond, more ? 1u : 0u);
+}
+
+cudaError_t batch_loop_init(double* scal, int* flags, double rtol, double atol, int imax,
+                            cudaGraphConditionalHandle cond, cudaStream_t s) {
+    k_batch_loop<<<1, 1, 0, s>>>(scal, flags, rtol, atol, imax, cond, 1);
+    return cudaGetLastError();
+}
+cudaError_t batch_loop_check(double* scal, int* flags, double rtol, double atol, int imax,
+                             cudaGraphConditionalHandle cond, cudaStream_t s) {
+    k_batch_loop<<<1, 1, 0, s>>>(scal, flags, rtol, atol, imax, cond, 0);
+    return cudaGetLastError();
+}
+
 cudaError_t residual64(long long n, const double* f, const double* y, double* r, Scratch& sc, double* rr,
                        cudaStream_t s) {
     k_residual<<<reduce_blocks(), kRedThreads, 0, s>>>(n, f, y, r, sc.part, sc.counter, rr);
@@ -1215,7 +1247,12 @@ cudaError_t axpy64(long long n, double a, const double* x, double* y, cudaStream
 }
 cudaError_t copy_dirichlet(long long nd, const long long* idx, const double* src, double* dst, cudaStream_t s) {
     if (nd <= 0) return cudaSuccess;
-    k_copy_idx<<<vec_grid(nd), kVecThreads, 0, s>>>(nd, idx, src, dst);
+    k_copy_idx<double><<<vec_grid(nd), kVecThreads, 0, s>>>(nd, idx, src, dst);
+    return cudaGetLastError();
+}
+cudaError_t copy_dirichlet32(long long nd, const long long* idx, const float* src, float* dst, cudaStream_t s) {
+    if (nd <= 0) return cudaSuccess;
+    k_copy_idx<float><<<vec_grid(nd), kVecThreads, 0, s>>>(nd, idx, src, dst);
     return cudaGetLastError();
 }
 cudaError_t scatter_dirichlet(long long nd, const long long* idx, const double* vals, double* dst, cudaStream_t s) {

@@ -62,6 +62,18 @@ struct Level {
     long long csr_nnz = 0;
 };
 
+// The whole batched solve of a list of tanks as one instantiated CUDA graph: per tank a
+// branch with the lifting, a loop-control kernel and a WHILE conditional node whose body
+// is one defect-correction iteration (the device decides when the tank has converged).
+// Owned by the first handle of the list; valid while the list (by handle uid) and rtol
+// are unchanged.
+struct BatchPlan {
+    std::vector<unsigned long long> uids;
+    std::vector<double> rtol;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<long long> pro_launches, body_launches, body_applies, body_vcycles;
+};
+
 struct Scratch {
     double* part = nullptr;        // block partial sums
     unsigned* counter = nullptr;   // last-block counters
@@ -107,6 +119,9 @@ struct sem_handle {
     double* bu = nullptr;
     cudaGraphExec_t bgraph = nullptr;
     bool bgraph_failed = false;
+    unsigned long long uid = 0;     // unique per sem_setup in this process
+    sem::BatchPlan* bplan = nullptr;   // graph-resident batched solve (this handle first in the list)
+    bool bplan_failed = false;
     long long bgraph_launches = 0, bgraph_applies = 0, bgraph_vcycles = 0;
     long long graph_iters = 0;
     // staging buffers of laplace_solve_host
@@ -118,9 +133,12 @@ struct sem_handle {
     std::vector<std::vector<int>> map2;   // per level: [ntri][NT] 2D ids
     // profiling events
     std::vector<cudaEvent_t> ev;
+    std::vector<int> ev_kind;      // per event pair: 0 FP64, 1 FP32, 2 TF32 tensor-core apply
     int ev_used = 0;
-    double apply_ms = 0.0;
+    double apply_ms = 0.0;         // FP64 finest-level applies
     long long apply_launches = 0;
+    double apply32_ms = 0.0, apply_tc_ms = 0.0;
+    long long apply32_launches = 0, apply_tc_launches = 0;
     long long fine_applies = 0;
     long long launches = 0;        // kernels launched since the counter was reset
     long long vcycles = 0;
@@ -141,6 +159,11 @@ cudaError_t launch_apply_prism64(const Level& L, const double* x, double* y, boo
 cudaError_t launch_apply_prism32(const Level& L, const float* x, float* y, const int* skip, int variant,
                                  cudaStream_t s);
 int prism_tile_elements(int P, int variant);
+// apply_prism_tc.cu: TF32 tensor-core prism apply (FP32 in/out) for the mixed V-cycle's
+// Chebyshev sweeps, orders 2..6; *err is set when its bounded copy wait runs out
+cudaError_t launch_apply_prism_tc(const Level& L, const float* x, float* y, const int* skip, int* err,
+                                  cudaStream_t s);
+bool prism_tc_supported(int p);
 cudaError_t launch_geometry(Level& L, const double* vtri, const double* etaP, const double* BP,
                             const double* DrP, const double* DsP, int NTP, int nlayers, double depth,
                             cudaStream_t s);
@@ -171,12 +194,22 @@ cudaError_t pcg_update(long long n, const double* num, const double* den, const 
 cudaError_t pcg_direction(long long n, const double* num, const double* den, const double* z, double* p,
                           cudaStream_t s);
 cudaError_t axpy64(long long n, double a, const double* x, double* y, cudaStream_t s);
+// Device-side loop control of the graph-resident batched solve: `init` (before the
+// loop) and `check` (end of every iteration) set the WHILE node's condition from
+// ||r||^2 = scal[S_RR] (or ||f||^2 = scal[S_FF] at init) against (rtol ||f|| + atol)^2
+// and count iterations in flags[F_BATCH_ITERS]; flags[F_BATCH_STATUS] ends as 0 (met),
+// 1 (imax reached) or -4 (non-finite).
+cudaError_t batch_loop_init(double* scal, int* flags, double rtol, double atol, int imax,
+                            cudaGraphConditionalHandle cond, cudaStream_t s);
+cudaError_t batch_loop_check(double* scal, int* flags, double rtol, double atol, int imax,
+                             cudaGraphConditionalHandle cond, cudaStream_t s);
 cudaError_t dot32(long long n, const float* a, const float* b, Scratch& sc, double* out, cudaStream_t s);
 cudaError_t pcg_update32(long long n, const double* num, const double* den, const float* p, const float* q, float* u,
                          float* r, Scratch& sc, double* rr, cudaStream_t s);
 cudaError_t pcg_direction32(long long n, const double* num, const double* den, const float* z, float* p,
                             cudaStream_t s);
 cudaError_t copy_dirichlet(long long nd, const long long* idx, const double* src, double* dst, cudaStream_t s);
+cudaError_t copy_dirichlet32(long long nd, const long long* idx, const float* src, float* dst, cudaStream_t s);
 cudaError_t scatter_dirichlet(long long nd, const long long* idx, const double* vals, double* dst, cudaStream_t s);
 cudaError_t zero_dirichlet(long long nd, const long long* idx, double* v, cudaStream_t s);
 cudaError_t to_f32(long long n, const double* a, float* b, cudaStream_t s);
@@ -211,6 +244,7 @@ enum {
     S_IRR = 6, S_IPQ = 7, S_IDELTA0 = 14, S_IDELTA1 = 15, S_L0 = 100, S_L1 = 101, S_LOSS = 102,
     S_MULTI = 16                    // FGMRES dots start here (up to 64 + 1)
 };
-enum { F_CG_DONE = 0, F_CG_ITERS = 1, F_LEARN_ACCEPT = 2, F_LEARN_COUNT = 3 /* +0 accepts, +1 fallbacks */ };
+enum { F_CG_DONE = 0, F_CG_ITERS = 1, F_LEARN_ACCEPT = 2, F_LEARN_COUNT = 3 /* +0 accepts, +1 fallbacks */,
+       F_TC_ERR = 5, F_BATCH_ITERS = 6, F_BATCH_STATUS = 7 };
 
 }  // namespace sem

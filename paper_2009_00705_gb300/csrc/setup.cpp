@@ -208,7 +208,7 @@ sem_status build_level(sem_handle* h, const sem_mesh* m, int li, int p) {
     CK(upload(&L.ref32.m, to_float(rb)));
     L.ref64.count = L.ref32.count = rb.size();
     CK(dalloc(&L.G, (size_t)L.E * L.ncomp * L.Nq));
-    CK(dalloc(&L.G32, (size_t)L.E * L.ncomp * L.Nq));
+    CK(dalloc(&L.G32, (size_t)L.E * L.ncomp * L.Nq + 16));   // +64 B: the tensor-core apply's bulk copies round up to 16 B
     CK(dalloc(&L.dinv, L.N));
     CK(dalloc(&L.dinv32, L.N));
     CK(dalloc(&L.u, L.N));
@@ -382,7 +382,7 @@ sem_status build_workspace(sem_handle* h) {
         CK(dalloc(&h->gm_y, (size_t)h->opts.gmres_m));
     }
     for (double** v : {&h->cx, &h->cr, &h->cz, &h->cp, &h->cq, &h->cb}) CK(dalloc(v, Lc.N));
-    if (h->opts.precision == SEM_PREC_MIXED_FP32 && h->opts.inner_imax > 0)
+    if (h->opts.precision != SEM_PREC_FP64 && h->opts.inner_imax > 0)
         for (float** v : {&h->ir, &h->iz, &h->ip, &h->iq, &h->ie}) CK(dalloc(v, N));
     if (h->opts.batch) {
         CK(dalloc(&h->bu, N));
@@ -393,6 +393,7 @@ sem_status build_workspace(sem_handle* h) {
     CK(dalloc(&h->st_phi, N));
     if (h->opts.profile) {
         h->ev.resize(512);
+        h->ev_kind.assign(256, 0);
         for (auto& e : h->ev) CK(cudaEventCreate(&e));
     }
     return SEM_OK;

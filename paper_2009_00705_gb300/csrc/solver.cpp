@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -79,18 +80,29 @@ Cheb cheb_coeffs(double lam, const sem_options& o) {
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Event timing of finest-level applies (profile = 1, outside graph capture): the pair of
+// events brackets the apply kernel alone, on the stream it is launched on.
+static bool timed_begin(sem_handle* h, int li, cudaStream_t s) {
+    const bool timed = (li == 0) && h->opts.profile && !h->capturing && (h->ev_used + 2 <= (int)h->ev.size());
+    if (timed) cudaEventRecord(h->ev[h->ev_used], s);
+    return timed;
+}
+static void timed_end(sem_handle* h, int kind, cudaStream_t s) {
+    cudaEventRecord(h->ev[h->ev_used + 1], s);
+    h->ev_kind[h->ev_used / 2] = kind;
+    h->ev_used += 2;
+    if (kind == 0) h->apply_launches += 1;
+    else if (kind == 1) h->apply32_launches += 1;
+    else h->apply_tc_launches += 1;
+}
+
 // Finest-level apply with optional event timing (profile = 1).
 sem_status apply_level64(sem_handle* h, int li, const double* x, double* y, bool lift, cudaStream_t s) {
     const Level& L = h->lv[li];
     CKS(cudaMemsetAsync(y, 0, sizeof(double) * L.N, s));
-    const bool timed = (li == 0) && h->opts.profile && !h->capturing && (h->ev_used + 2 <= (int)h->ev.size());
-    if (timed) CKS(cudaEventRecord(h->ev[h->ev_used], s));
+    const bool timed = timed_begin(h, li, s);
     K(launch_apply64(L, x, y, lift, nullptr, s));
-    if (timed) {
-        CKS(cudaEventRecord(h->ev[h->ev_used + 1], s));
-        h->ev_used += 2;
-        h->apply_launches += 1;
-    }
+    if (timed) timed_end(h, 0, s);
     if (li == 0) h->fine_applies += 1;
     return SEM_OK;
 }
@@ -99,7 +111,9 @@ sem_status apply_level32(sem_handle* h, int li, const float* x, float* y, cudaSt
                          const int* skip = nullptr) {
     const Level& L = h->lv[li];
     CKS(cudaMemsetAsync(y, 0, sizeof(float) * L.N, s));
+    const bool timed = timed_begin(h, li, s);
     K(launch_apply32(L, x, y, s, skip));
+    if (timed) timed_end(h, 1, s);
     if (li == 0) h->fine_applies += 1;
     return SEM_OK;
 }
@@ -108,7 +122,9 @@ sem_status apply_level32(sem_handle* h, int li, const float* x, float* y, cudaSt
 void flush_events(sem_handle* h) {
     for (int i = 0; i + 1 < h->ev_used; i += 2) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]) == cudaSuccess) h->apply_ms += ms;
+        if (cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]) != cudaSuccess) continue;
+        const int kind = h->ev_kind[i / 2];
+        (kind == 0 ? h->apply_ms : kind == 1 ? h->apply32_ms : h->apply_tc_ms) += ms;
     }
     h->ev_used = 0;
 }
@@ -196,6 +212,20 @@ sem_status smooth<double>(sem_handle* h, int li, const double* f, double* u, boo
     return SEM_OK;
 }
 
+// The operator of an FP32 Chebyshev sweep: the TF32 tensor-core prism apply in MIXED_TF32
+// (orders 2..6), the FP32 apply otherwise.
+static sem_status apply_smooth32(sem_handle* h, int li, const float* x, float* y, cudaStream_t s, const int* skip) {
+    const Level& L = h->lv[li];
+    if (h->opts.precision != SEM_PREC_MIXED_TF32 || L.dim != 3 || !prism_tc_supported(L.p))
+        return apply_level32(h, li, x, y, s, skip);
+    CKS(cudaMemsetAsync(y, 0, sizeof(float) * L.N, s));
+    const bool timed = timed_begin(h, li, s);
+    K(launch_apply_prism_tc(L, x, y, skip, h->sc.flags + F_TC_ERR, s));
+    if (timed) timed_end(h, 2, s);
+    if (li == 0) h->fine_applies += 1;
+    return SEM_OK;
+}
+
 template <>
 sem_status smooth<float>(sem_handle* h, int li, const float* f, float* u, bool zero_init, cudaStream_t s,
                          const int* skip) {
@@ -204,11 +234,11 @@ sem_status smooth<float>(sem_handle* h, int li, const float* f, float* u, bool z
     if (zero_init) {
         K(cheb_first<float>(L.N, (float)c.c0, L.dinv32, f, u, L.d32, s, skip));
     } else {
-        CKST(apply_level32(h, li, u, L.y32, s, skip));
+        CKST(apply_smooth32(h, li, u, L.y32, s, skip));
         K(cheb_restart<float>(L.N, (float)c.c0, L.dinv32, f, L.y32, u, L.d32, s, skip));
     }
     for (int j = 1; j < h->opts.k_cheb; ++j) {
-        CKST(apply_level32(h, li, u, L.y32, s, skip));
+        CKST(apply_smooth32(h, li, u, L.y32, s, skip));
         K(cheb_step<float>(L.N, (float)c.c1[j], (float)c.c2[j], L.dinv32, f, L.y32, u, L.d32, s, skip));
     }
     return SEM_OK;
@@ -352,7 +382,7 @@ sem_status inner_pcg32(sem_handle* h, const double* r, double* e, cudaStream_t s
 
 // z = M^{-1} r on the finest level in the configured precision (r has zero Dirichlet entries).
 sem_status precondition(sem_handle* h, const double* r, double* z, cudaStream_t s) {
-    if (h->opts.precision == SEM_PREC_MIXED_FP32) {
+    if (h->opts.precision != SEM_PREC_FP64) {
         if (h->opts.inner_imax > 0) return inner_pcg32(h, r, z, s);
         Level& L = h->lv[0];
         K(to_f32(L.N, r, L.f32, s));
@@ -539,17 +569,33 @@ sem_status check_options(const sem_options& o, int P) {
         return SEM_EINVAL;
     }
     if (!(o.cheb_hi > 0) || !(o.cheb_lo > 0) || !(o.cheb_lo < 1)) { set_error("Chebyshev bounds"); return SEM_EINVAL; }
-    if (o.outer < 0 || o.outer > 2 || o.precision < 0 || o.precision > 1) { set_error("outer/precision"); return SEM_EINVAL; }
+    if (o.outer < 0 || o.outer > 2 || o.precision < 0 || o.precision > 2) { set_error("outer/precision"); return SEM_EINVAL; }
     if (o.outer == SEM_OUTER_FGMRES && (o.gmres_m < 1 || o.gmres_m > 64)) { set_error("gmres_m in 1..64"); return SEM_EINVAL; }
     if (o.imax < 0 || o.coarse_imax < 1 || !(o.coarse_rtol > 0)) { set_error("iteration limits"); return SEM_EINVAL; }
+    if (o.batch_mode < 0 || o.batch_mode > 1) { set_error("batch_mode 0 or 1"); return SEM_EINVAL; }
     if (o.smoother != SEM_SMOOTH_CHEBYSHEV && o.smoother != SEM_SMOOTH_LEARNED) { set_error("smoother"); return SEM_EINVAL; }
-    if (o.smoother == SEM_SMOOTH_LEARNED && (o.precision != SEM_PREC_MIXED_FP32 || o.mlp_hidden < 1 || o.mlp_hidden > 4096)) {
-        set_error("the learned smoother needs precision = MIXED_FP32 and 1 <= mlp_hidden <= 4096");
+    if (o.smoother == SEM_SMOOTH_LEARNED && (o.precision == SEM_PREC_FP64 || o.mlp_hidden < 1 || o.mlp_hidden > 4096)) {
+        set_error("the learned smoother needs a mixed precision and 1 <= mlp_hidden <= 4096");
         return SEM_EINVAL;
     }
     if (o.inner_imax < 0 || (o.inner_imax > 0 && !(o.inner_rtol > 0 && o.inner_rtol < 1))) {
         set_error("inner_imax >= 0 and 0 < inner_rtol < 1");
         return SEM_EINVAL;
+    }
+    return SEM_OK;
+}
+
+// A timed-out geometric-factor copy inside the tensor-core apply (flag set on the device):
+// turns *ret into SEM_TIMEOUT and clears the flag.  Synchronous; reads the flag of
+// MIXED_TF32 handles, or of any handle when `always`.
+sem_status check_tc_flag(sem_handle* h, sem_status* ret, bool always = false) {
+    if (!always && h->opts.precision != SEM_PREC_MIXED_TF32) return SEM_OK;
+    int terr = 0;
+    CKS(cudaMemcpy(&terr, h->sc.flags + F_TC_ERR, sizeof(int), cudaMemcpyDeviceToHost));
+    if (terr) {
+        CKS(cudaMemset(h->sc.flags + F_TC_ERR, 0, sizeof(int)));
+        set_error("tensor-core apply: a geometric-factor copy did not complete within its wait bound");
+        *ret = SEM_TIMEOUT;
     }
     return SEM_OK;
 }
@@ -739,6 +785,7 @@ void sem_default_options(sem_options* o, int P) {
     o->mlp_seed = 20090705ULL;
     o->batch = 0;
     o->autotune = 1;
+    o->batch_mode = 0;
 }
 
 sem_status sem_mesh_nodes2d(const sem_mesh* m, int p, long long* n2, double* xy) {
@@ -808,6 +855,8 @@ sem_status sem_setup(const sem_mesh* m, int P, const sem_options* opts, sem_hand
         return st;
     }
     h->fine_applies = 0;
+    static std::atomic<unsigned long long> next_uid{1};
+    h->uid = next_uid.fetch_add(1);
     *out = h;
     return SEM_OK;
 }
@@ -831,6 +880,10 @@ void sem_destroy(sem_handle* h) {
     if (h->sc.hflags) cudaFreeHost(h->sc.hflags);
     for (auto& e : h->ev) cudaEventDestroy(e);
     if (h->bgraph) cudaGraphExecDestroy(h->bgraph);
+    if (h->bplan) {
+        if (h->bplan->exec) cudaGraphExecDestroy(h->bplan->exec);
+        delete h->bplan;
+    }
     if (h->bstream) cudaStreamDestroy(h->bstream);
     delete h;
 }
@@ -934,6 +987,29 @@ sem_status sem_apply(sem_handle* h, int level, const double* x, double* y, void*
     return SEM_OK;
 }
 
+sem_status sem_apply32(sem_handle* h, int level, const float* x, float* y, int tensor_cores, void* stream) {
+    CKST(check_level(h, level));
+    if (!x || !y || x == y) { set_error("sem_apply32: x and y must be distinct device buffers"); return SEM_EINVAL; }
+    cudaStream_t s = as_stream(stream);
+    const Level& L = h->lv[level];
+    if (tensor_cores) {
+        if (L.dim != 3 || !prism_tc_supported(L.p)) {
+            set_error("sem_apply32: the tensor-core apply needs a prism level of order 2..6");
+            return SEM_EINVAL;
+        }
+        CKS(cudaMemsetAsync(y, 0, sizeof(float) * L.N, s));
+        K(launch_apply_prism_tc(L, x, y, nullptr, h->sc.flags + F_TC_ERR, s));
+        CKS(cudaStreamSynchronize(s));
+        sem_status ret = SEM_OK;
+        CKST(check_tc_flag(h, &ret, true));
+        if (ret != SEM_OK) return ret;
+    } else {
+        CKST(apply_level32(h, level, x, y, s));
+    }
+    K(copy_dirichlet32((long long)L.hdir.size(), L.dir, x, y, s));
+    return SEM_OK;
+}
+
 sem_status pmg_vcycle(sem_handle* h, const double* r, double* z, void* stream) {
     if (!h || !r || !z || r == z) { set_error("pmg_vcycle: bad arguments"); return SEM_EINVAL; }
     cudaStream_t s = as_stream(stream);
@@ -953,8 +1029,8 @@ sem_status laplace_solve(sem_handle* h, const double* rhs, const double* eta, do
     h->fine_applies = 0;
     h->vcycles = 0;
     h->coarse_iters_max = 0;
-    h->apply_ms = 0;
-    h->apply_launches = 0;
+    h->apply_ms = h->apply32_ms = h->apply_tc_ms = 0;
+    h->apply_launches = h->apply32_launches = h->apply_tc_launches = 0;
     h->launches = 0;
     h->inner_iters = 0;
     CKS(cudaMemsetAsync(h->sc.flags + F_LEARN_COUNT, 0, 2 * sizeof(int), s));
@@ -998,12 +1074,17 @@ sem_status laplace_solve(sem_handle* h, const double* rhs, const double* eta, do
     cudaEventDestroy(e1);
     if (h->opts.profile) flush_events(h);
     st.ms = ms;
+    CKST(check_tc_flag(h, &ret));
     st.status = ret;
     st.fine_applies = h->fine_applies;
     st.vcycles = h->vcycles;
     st.coarse_iters_max = h->coarse_iters_max;
     st.apply_ms = h->apply_ms;
     st.apply_launches = h->apply_launches;
+    st.apply32_ms = h->apply32_ms;
+    st.apply32_launches = h->apply32_launches;
+    st.apply_tc_ms = h->apply_tc_ms;
+    st.apply_tc_launches = h->apply_tc_launches;
     st.kernel_launches = h->launches;
     st.inner_iters = h->inner_iters;
     if (h->opts.smoother == SEM_SMOOTH_LEARNED) {
@@ -1177,15 +1258,17 @@ sem_status sem_learned_train(sem_handle* h, int snapshots, int steps, double lr,
     return ret;
 }
 
-// One lockstep iteration of a batched tank (no host synchronisation, capturable):
-// z = M^{-1} r; u += z; r = f - A u; ||r||^2 -> pinned host mirror.
-static sem_status batch_iteration(sem_handle* h, cudaStream_t s) {
+// One defect-correction iteration of a batched tank (no host synchronisation,
+// capturable): z = M^{-1} r; u += z; r = f - A u; ||r||^2 -> scal[S_RR] (and its pinned
+// host mirror when host_copy).
+static sem_status batch_iteration(sem_handle* h, cudaStream_t s, bool host_copy = true) {
     const long long N = h->lv[0].N;
     CKST(precondition(h, h->r, h->z, s));
     K(axpy64(N, 1.0, h->z, h->bu, s));
     CKST(apply_level64(h, 0, h->bu, h->q, false, s));
     K(residual64(N, h->fr, h->q, h->r, h->sc, h->sc.scal + S_RR, s));
-    CKS(cudaMemcpyAsync(h->sc.hpinned + S_RR, h->sc.scal + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (host_copy)
+        CKS(cudaMemcpyAsync(h->sc.hpinned + S_RR, h->sc.scal + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s));
     return SEM_OK;
 }
 
@@ -1220,6 +1303,189 @@ static void batch_capture(sem_handle* h) {
     h->vcycles = v0;
 }
 
+// Lifting of a batched tank from its staged Dirichlet data (h->st_eta): f = -A_FD phi~,
+// ||f||^2 -> scal[S_FF], r = f, u = 0.  Capturable.
+static sem_status batch_lift(sem_handle* h, cudaStream_t s) {
+    const Level& L = h->lv[0];
+    const long long N = L.N, nd = (long long)L.hdir.size();
+    CKS(cudaMemsetAsync(h->x, 0, sizeof(double) * N, s));
+    K(scatter_dirichlet(nd, L.dir, h->st_eta, h->x, s));
+    CKST(apply_level64(h, 0, h->x, h->q, true, s));
+    CKS(cudaMemsetAsync(h->fr, 0, sizeof(double) * N, s));
+    K(axpy64(N, -1.0, h->q, h->fr, s));
+    K(dot64(N, h->fr, h->fr, h->sc, h->sc.scal + S_FF, s));
+    CKS(cudaMemcpyAsync(h->r, h->fr, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    CKS(cudaMemsetAsync(h->bu, 0, sizeof(double) * N, s));
+    return SEM_OK;
+}
+
+// End every capture still open on the listed streams (after a failed graph build).
+static void end_captures(const std::vector<cudaStream_t>& streams) {
+    for (cudaStream_t s : streams) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(s, &g);
+            if (g) cudaGraphDestroy(g);
+        }
+    }
+    cudaGetLastError();
+}
+
+// Build the graph-resident batched solve (see BatchPlan).  The capture starts on a private
+// origin stream (the caller's may be the legacy default stream, which cannot capture);
+// every tank's branch runs on its own stream and the WHILE bodies are captured on a
+// second private stream.  Returns nullptr when any step fails (all captures ended,
+// errors cleared).
+static BatchPlan* build_batch_plan(sem_handle* const* hs, int n, const std::vector<double>& rtol) {
+    BatchPlan* plan = new (std::nothrow) BatchPlan();
+    if (!plan) return nullptr;
+    plan->rtol = rtol;
+    plan->pro_launches.assign(n, 0);
+    plan->body_launches.assign(n, 0);
+    plan->body_applies.assign(n, 0);
+    plan->body_vcycles.assign(n, 0);
+    cudaStream_t cs = nullptr, body = nullptr;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join(n, nullptr);
+    std::vector<cudaStream_t> streams;
+    bool ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&body, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int t = 0; t < n && ok; ++t) ok = cudaEventCreateWithFlags(&join[t], cudaEventDisableTiming) == cudaSuccess;
+    if (cs) streams.push_back(cs);
+    if (body) streams.push_back(body);
+    for (int t = 0; t < n; ++t) {
+        streams.push_back(hs[t]->bstream);
+        plan->uids.push_back(hs[t]->uid);
+    }
+    ok = ok && cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    ok = ok && cudaEventRecord(fork, cs) == cudaSuccess;
+    for (int t = 0; t < n && ok; ++t) {
+        sem_handle* h = hs[t];
+        cudaStream_t s = h->bstream;
+        const long long l0 = h->launches, a0 = h->fine_applies, v0 = h->vcycles;
+        h->capturing = true;
+        ok = cudaStreamWaitEvent(s, fork, 0) == cudaSuccess && batch_lift(h, s) == SEM_OK;
+        cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+        cudaGraph_t g = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        cudaGraphConditionalHandle cond{};
+        ok = ok && cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, &deps, nullptr, &ndeps) == cudaSuccess &&
+             cst == cudaStreamCaptureStatusActive;
+        ok = ok && cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault) == cudaSuccess;
+        ok = ok && batch_loop_init(h->sc.scal, h->sc.flags, rtol[t], h->opts.atol, h->opts.imax, cond, s) == cudaSuccess;
+        if (ok) h->launches += 1;
+        plan->pro_launches[t] = h->launches - l0;
+        ok = ok && cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, &deps, nullptr, &ndeps) == cudaSuccess;
+        cudaGraphNodeParams p{};
+        p.type = cudaGraphNodeTypeConditional;
+        p.conditional.handle = cond;
+        p.conditional.type = cudaGraphCondTypeWhile;
+        p.conditional.size = 1;
+        cudaGraphNode_t node = nullptr;
+        ok = ok && cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &p) == cudaSuccess;
+        ok = ok && cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies) ==
+                       cudaSuccess;
+        if (ok) {
+            const long long l1 = h->launches, a1 = h->fine_applies, v1 = h->vcycles;
+            ok = cudaStreamBeginCaptureToGraph(body, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                ok = batch_iteration(h, body, false) == SEM_OK &&
+                     batch_loop_check(h->sc.scal, h->sc.flags, rtol[t], h->opts.atol, h->opts.imax, cond, body) ==
+                         cudaSuccess;
+                h->launches += 1;
+                cudaGraph_t bg = nullptr;
+                ok = (cudaStreamEndCapture(body, &bg) == cudaSuccess) && ok;
+            }
+            plan->body_launches[t] = h->launches - l1;
+            plan->body_applies[t] = h->fine_applies - a1;
+            plan->body_vcycles[t] = h->vcycles - v1;
+        }
+        h->capturing = false;
+        h->launches = l0;
+        h->fine_applies = a0;
+        h->vcycles = v0;
+        ok = ok && cudaEventRecord(join[t], s) == cudaSuccess && cudaStreamWaitEvent(cs, join[t], 0) == cudaSuccess;
+    }
+    cudaGraph_t top = nullptr;
+    const cudaError_t ee = cs ? cudaStreamEndCapture(cs, &top) : cudaErrorInvalidValue;
+    ok = ok && ee == cudaSuccess && top != nullptr;
+    ok = ok && cudaGraphInstantiate(&plan->exec, top, 0) == cudaSuccess;
+    if (top) cudaGraphDestroy(top);
+    end_captures(streams);
+    if (body) cudaStreamDestroy(body);
+    if (cs) cudaStreamDestroy(cs);
+    if (fork) cudaEventDestroy(fork);
+    for (cudaEvent_t e : join)
+        if (e) cudaEventDestroy(e);
+    if (!ok) {
+        if (plan->exec) cudaGraphExecDestroy(plan->exec);
+        delete plan;
+        cudaGetLastError();
+        return nullptr;
+    }
+    return plan;
+}
+
+// One launch of a graph-resident batched solve: stage every tank's Dirichlet data, launch
+// the graph, write phi, then read each tank's iteration count and status from the device.
+static sem_status batch_run_plan(BatchPlan* plan, sem_handle* const* hs, int n, const double* const* eta,
+                                 double* const* phi, sem_stats* stats, cudaStream_t cs) {
+    for (int t = 0; t < n; ++t) {
+        sem_handle* h = hs[t];
+        const long long nd = (long long)h->lv[0].hdir.size();
+        if (nd > 0) CKS(cudaMemcpyAsync(h->st_eta, eta[t], sizeof(double) * nd, cudaMemcpyDeviceToDevice, cs));
+    }
+    CKS(cudaGraphLaunch(plan->exec, cs));
+    for (int t = 0; t < n; ++t) {
+        sem_handle* h = hs[t];
+        const Level& L = h->lv[0];
+        CKS(cudaMemcpyAsync(phi[t], h->bu, sizeof(double) * L.N, cudaMemcpyDeviceToDevice, cs));
+        K(scatter_dirichlet((long long)L.hdir.size(), L.dir, eta[t], phi[t], cs));
+    }
+    CKS(cudaStreamSynchronize(cs));
+    sem_status worst = SEM_OK;
+    for (int t = 0; t < n; ++t) {
+        sem_handle* h = hs[t];
+        int fl[2] = {0, 0};
+        double sc2[2] = {0, 0};
+        CKS(cudaMemcpy(fl, h->sc.flags + F_BATCH_ITERS, 2 * sizeof(int), cudaMemcpyDeviceToHost));
+        CKS(cudaMemcpy(&sc2[0], h->sc.scal + S_RR, sizeof(double), cudaMemcpyDeviceToHost));
+        CKS(cudaMemcpy(&sc2[1], h->sc.scal + S_FF, sizeof(double), cudaMemcpyDeviceToHost));
+        const int iters = fl[0];
+        sem_status st_t = fl[1] == 0 ? SEM_OK : (fl[1] == 1 ? SEM_NOT_CONVERGED : SEM_NAN);
+        CKST(check_tc_flag(h, &st_t));
+        const double fnorm = std::sqrt(sc2[1]);
+        const double rn = iters > 0 ? std::sqrt(sc2[0]) : fnorm;
+        h->graph_iters = iters;
+        h->fine_applies = iters * plan->body_applies[t];
+        h->vcycles = iters * plan->body_vcycles[t];
+        h->launches = plan->pro_launches[t] + iters * plan->body_launches[t];
+        if (stats) {
+            sem_stats st{};
+            st.status = st_t;
+            st.iters = iters;
+            st.fnorm = fnorm;
+            st.res0 = fnorm;
+            st.res_final = rn;
+            st.q_mean = (iters > 0 && fnorm > 0) ? std::pow(rn / fnorm, 1.0 / iters) : 0.0;
+            st.fine_applies = h->fine_applies;
+            st.vcycles = h->vcycles;
+            st.kernel_launches = h->launches;
+            st.graph_iterations = iters;
+            stats[t] = st;
+        }
+        if (st_t != SEM_OK && (worst == SEM_OK || st_t < 0)) worst = st_t;
+    }
+    if (worst == SEM_NAN) set_error("laplace_solve_batch: non-finite residual");
+    else if (worst == SEM_NOT_CONVERGED) set_error("laplace_solve_batch: a tank reached imax");
+    else if (worst == SEM_TIMEOUT) set_error("laplace_solve_batch: a tensor-core copy wait ran out");
+    return worst;
+}
+
 static sem_status batch_impl(sem_handle* const* hs, int n, const double* const* eta, double tol, double* const* phi,
                              sem_stats* stats, void* stream) {
     for (int t = 0; t < n; ++t) {
@@ -1230,6 +1496,25 @@ static sem_status batch_impl(sem_handle* const* hs, int n, const double* const* 
         }
     }
     cudaStream_t cs = as_stream(stream);
+    // graph-resident form first: the whole batch as one graph launch, loops decided on the device
+    sem_handle* h0 = hs[0];
+    if (!h0->bplan_failed && (h0->opts.batch_mode == 0)) {
+        std::vector<double> rtolv(n);
+        for (int t = 0; t < n; ++t) rtolv[t] = (tol > 0) ? tol : hs[t]->opts.rtol;
+        bool valid = h0->bplan != nullptr && (int)h0->bplan->uids.size() == n && h0->bplan->rtol == rtolv;
+        for (int t = 0; t < n && valid; ++t) valid = h0->bplan->uids[t] == hs[t]->uid;
+        if (!valid) {
+            if (h0->bplan) {
+                if (h0->bplan->exec) cudaGraphExecDestroy(h0->bplan->exec);
+                delete h0->bplan;
+                h0->bplan = nullptr;
+            }
+            CKS(cudaStreamSynchronize(cs));
+            h0->bplan = build_batch_plan(hs, n, rtolv);
+            if (!h0->bplan) h0->bplan_failed = true;
+        }
+        if (h0->bplan) return batch_run_plan(h0->bplan, hs, n, eta, phi, stats, cs);
+    }
     cudaEvent_t start, done;
     CKS(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
     CKS(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
@@ -1311,6 +1596,7 @@ static sem_status batch_impl(sem_handle* const* hs, int n, const double* const* 
         CKS(cudaMemcpyAsync(&timeout, h->sc.counter + 3, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         CKS(cudaStreamSynchronize(s));
         if (timeout && status[t] == SEM_OK) status[t] = SEM_TIMEOUT;
+        CKST(check_tc_flag(h, &status[t]));
         CKS(cudaEventRecord(done, s));
         CKS(cudaStreamWaitEvent(cs, done, 0));
         if (stats) {
@@ -1346,6 +1632,8 @@ sem_status laplace_solve_batch(sem_handle* const* hs, int n, const double* const
             set_error("laplace_solve_batch: every handle needs batch = 1 and inner_imax = 0");
             return SEM_EINVAL;
         }
+        for (int u = 0; u < t; ++u)
+            if (hs[u] == hs[t]) { set_error("laplace_solve_batch: a handle appears twice"); return SEM_EINVAL; }
     }
     const sem_status st = batch_impl(hs, n, eta, tol, phi, stats, stream);
     if (st != SEM_OK && st != SEM_NOT_CONVERGED && st != SEM_NAN && st != SEM_TIMEOUT) {

@@ -24,14 +24,15 @@ def sem():
     return pkg
 
 
-@pytest.mark.parametrize("precision", ["mixed_fp32", "fp64"])
-def test_batched_tanks_match_individual_solves_and_oracle(sem, precision):
+@pytest.mark.parametrize("precision,mode", [("mixed_fp32", 0), ("mixed_fp32", 1), ("fp64", 0), ("mixed_tf32", 0)])
+def test_batched_tanks_match_individual_solves_and_oracle(sem, precision, mode):
+    # mode 0: the whole batch as one graph launch with device-side loops; 1: host-stepped lockstep
     tanks = []
     for i in range(6):
         mesh, P, modes = W.random_tank(i, count_range=(64, 700))
         prob = Problem(mesh, LEVELS[P])
         solver = sem.Solver(mesh, P, eta_nodal=prob.eta_nodal, levels=LEVELS[P], precision=precision, batch=1,
-                            outer="pdc", imax=400)
+                            outer="pdc", imax=400, batch_mode=mode)
         C = solver.coords(0)
         dn = solver.dirichlet_nodes(0)
         phiD = W.tank_potential(*C[dn].T, modes)
@@ -55,7 +56,8 @@ def _check_batch(sem, tanks):
         assert e64 in (4, 8, 16, 32) and e32 in (4, 8, 16, 32)
         assert st["status"] == 0 and st["res_final"] <= 1e-10 * st["fnorm"]
         assert abs(st2["iters"] - st["iters"]) <= 1
-        # every iteration of the second call replays the graph captured in the first
+        # every iteration of the second call runs inside a graph (the batch graph, or the
+        # tank's iteration graph in lockstep mode)
         assert st2["graph_iterations"] == st2["iters"], (st["graph_iterations"], st2)
         single = torch.zeros_like(phi)
         st1 = solver.solve(dD, single, tol=1e-10)
@@ -77,6 +79,14 @@ def test_batch_rejects_handles_not_prepared_for_it(sem):
         assert e.value.status == sem.SEM_EINVAL, sem.sem_last_error()
     finally:
         s.close()
+    b = sem.Solver(mesh, P, eta_nodal=mesh.eta(xy[:, 0], xy[:, 1]), precision="mixed_fp32", outer="pdc", batch=1)
+    try:
+        x = torch.zeros(b.query(0)["ndof"], dtype=torch.float64, device="cuda")
+        with pytest.raises(sem.SemError) as e:
+            sem.laplace_solve_batch([b.h, b.h], [x, x], 1e-8, [x, x])
+        assert e.value.status == sem.SEM_EINVAL and "twice" in sem.sem_last_error()
+    finally:
+        b.close()
 
 
 def test_full_size_tanks_whose_spectrum_defeats_power_iteration(sem):

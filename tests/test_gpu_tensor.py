@@ -1,0 +1,140 @@
+"""The TF32 tensor-core prism apply (Chebyshev sweeps of the MIXED_TF32 V-cycle).
+
+Tolerance: operands are rounded to TF32 (unit roundoff 2^-11 = 4.9e-4) and the
+products accumulate in FP32, so an entry of y = A x carries an error of order
+1e-3 of the terms it sums; for random x the entries are of the size of their
+terms, and the bound is 5e-3 of max|y| entrywise and 2e-3 of ||y||_2 overall.
+The solves that use the kernel still reach an FP64 residual of 1e-11, so their
+error against the oracle's direct solution is the tolerance's (1e-8)."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import solvers as S  # noqa: E402
+from oracle.assemble import Problem  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def sem():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2009_00705_gb300 as pkg
+    from paper_2009_00705_gb300 import build as B
+    B.build()
+    pkg.lib()
+    return pkg
+
+
+SMALL = {
+    "p6": (lambda: W.config_box3d(3, 3), [6, 3, 1]),
+    "p5_ragged": (lambda: W.box3d(5, 3, 3, eta_modes=W.eta_sinx_cosy(0.08)), [5, 3, 1]),
+    "p4": (lambda: W.config_box3d(4, 2), [4, 2, 1]),
+    "p3": (lambda: W.box3d(4, 3, 2, eta_modes=W.eta_sinx_cosy(0.1)), [3, 2, 1]),
+}
+
+
+def _solver(sem, mesh, prob, levels, **o):
+    return sem.Solver(mesh, levels[0], eta_nodal=prob.eta_nodal, levels=levels, coarse_rtol=1e-14, **o)
+
+
+def _check_apply(y_tc, y_ref):
+    scale = np.abs(y_ref).max()
+    assert np.abs(y_tc - y_ref).max() <= 5e-3 * scale, np.abs(y_tc - y_ref).max() / scale
+    assert np.linalg.norm(y_tc - y_ref) <= 2e-3 * np.linalg.norm(y_ref)
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_tensor_core_apply_matches_oracle_on_every_level(sem, name):
+    mesh_fn, levels = SMALL[name]
+    mesh = mesh_fn()
+    prob = Problem(mesh, levels)
+    s = _solver(sem, mesh, prob, levels)
+    try:
+        for li, p in enumerate(levels):
+            if p < 2:
+                continue
+            N = prob.levels[li].N
+            x = W.random_vector(N, seed=100 + li).astype(np.float32)
+            xd = torch.tensor(x, device="cuda")
+            y_tc = torch.zeros(N, dtype=torch.float32, device="cuda")
+            y_32 = torch.zeros(N, dtype=torch.float32, device="cuda")
+            s.apply32(li, xd, y_tc, tensor_cores=True)
+            s.apply32(li, xd, y_32, tensor_cores=False)
+            torch.cuda.synchronize()
+            ref = prob.masked_apply(li, x.astype(np.float64))
+            y32 = y_32.cpu().numpy().astype(np.float64)
+            assert np.abs(y32 - ref).max() <= 1e-5 * np.abs(ref).max()
+            _check_apply(y_tc.cpu().numpy().astype(np.float64), ref)
+    finally:
+        s.close()
+
+
+def test_tensor_core_apply_many_passes_per_cta(sem):
+    # 19 x 19 x 3 prisms at P = 6: 2166 elements = 271 passes of 8 over at most 152
+    # CTAs, the last pass ragged (6 elements); rows sampled against the oracle
+    mesh = W.box3d(19, 19, 3, eta_modes=W.eta_sinx_cosy(0.1))
+    levels = [6, 3, 1]
+    xy = sem.sem_mesh_nodes2d(mesh, 6)
+    s = sem.Solver(mesh, 6, eta_nodal=mesh.eta(xy[:, 0], xy[:, 1]), levels=levels)
+    try:
+        q = s.query(0)
+        N = q["ndof"]
+        x = W.random_vector(N, seed=7).astype(np.float32)
+        xd = torch.tensor(x, device="cuda")
+        y_tc = torch.zeros(N, dtype=torch.float32, device="cuda")
+        y_32 = torch.zeros(N, dtype=torch.float32, device="cuda")
+        s.apply32(0, xd, y_tc, tensor_cores=True)
+        s.apply32(0, xd, y_32, tensor_cores=False)
+        torch.cuda.synchronize()
+        _check_apply(y_tc.cpu().numpy().astype(np.float64), y_32.cpu().numpy().astype(np.float64))
+        prob = Problem(mesh, [6, 1])
+        rows = np.random.default_rng(3).choice(N, 200, replace=False)
+        ref = prob.apply_rows(0, x.astype(np.float64), rows)
+        got = y_tc.cpu().numpy().astype(np.float64)[rows]
+        assert np.abs(got - ref).max() <= 5e-3 * np.abs(ref).max()
+    finally:
+        s.close()
+
+
+def test_tensor_core_apply_rejects_triangles_and_order_one(sem):
+    mesh = W.config_slice2d()
+    s = sem.Solver(mesh, 4, levels=[4, 2, 1])
+    try:
+        x = torch.zeros(s.query(0)["ndof"], dtype=torch.float32, device="cuda")
+        y = torch.zeros_like(x)
+        with pytest.raises(sem.SemError) as e:
+            s.apply32(0, x, y, tensor_cores=True)
+        assert e.value.status == sem.SEM_EINVAL
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("name", ["p6", "p5_ragged"])
+def test_mixed_tf32_solve_matches_oracle(sem, name):
+    mesh_fn, levels = SMALL[name]
+    mesh = mesh_fn()
+    prob = Problem(mesh, levels)
+    lev = prob.levels[0]
+    C = prob.coords(0)
+    phiD = W.potential3d(*C[lev.dirichlet].T)
+    phi_ref = S.solve_laplace_direct(prob, phiD)
+    its = {}
+    for prec in ("mixed_fp32", "mixed_tf32"):
+        s = _solver(sem, mesh, prob, levels, outer="pdc", precision=prec, inner_imax=50, inner_rtol=1e-4,
+                    imax=100)
+        try:
+            phi = torch.zeros(lev.N, dtype=torch.float64, device="cuda")
+            st = s.solve(torch.tensor(phiD, device="cuda"), phi, tol=1e-11)
+            torch.cuda.synchronize()
+            assert st["status"] == 0 and st["res_final"] <= 1e-11 * st["fnorm"]
+            got = phi.cpu().numpy()
+            assert np.abs(got - phi_ref).max() <= 1e-8 * np.abs(phi_ref).max()
+            its[prec] = (st["iters"], st["inner_iters"])
+        finally:
+            s.close()
+    # the smoothing operator's rounding leaves the convergence essentially unchanged
+    assert its["mixed_tf32"][1] <= its["mixed_fp32"][1] + 3, its
