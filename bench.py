@@ -61,9 +61,13 @@ def apply_flops_per_elem(P):
     return 2 * fma
 
 
-def apply_bytes(P, E, N, word=8):
+def apply_bytes(P, E, N, word=8, gword=None):
+    """Algorithmic bytes of one apply: x in and y out (word each), the 6 geometric factors
+    per quadrature point (gword each; the tensor-core apply streams BF16 factors) and the
+    int32 element map."""
     NT, NZ, QT, QZ = (P + 1) * (P + 2) // 2, P + 1, (P + 1) ** 2, P + 1
-    return 2 * N * word + E * 6 * QT * QZ * word + E * NT * NZ * 4
+    gword = word if gword is None else gword
+    return 2 * N * word + E * 6 * QT * QZ * gword + E * NT * NZ * 4
 
 
 def kernels_sha():
@@ -165,7 +169,7 @@ def run_ncu_case(a):
     P = a.P
     mesh = W.config_box3d(a.ncu_case, a.nlayers)
     xy = sem.sem_mesh_nodes2d(mesh, P)
-    s = sem.Solver(mesh, P, eta_nodal=mesh.eta(xy[:, 0], xy[:, 1]), levels=levels_for(P), precision="mixed_fp32",
+    s = sem.Solver(mesh, P, eta_nodal=mesh.eta(xy[:, 0], xy[:, 1]), levels=levels_for(P), precision="mixed_tf32",
                    outer="pdc", inner_imax=2, inner_rtol=1e-4, imax=1)
     C = s.coords(0)
     phiD = torch.tensor(W.potential3d(*C[s.dirichlet_nodes(0)].T), device="cuda")
@@ -197,8 +201,8 @@ def main():
     ap.add_argument("--inner-rtol", type=float, default=1e-4)
     ap.add_argument("--coarse-rtol", type=float, default=1e-3)
     ap.add_argument("--ncu-case", type=int, default=0, metavar="N",
-                    help="profiler driver: one short mixed-precision solve on an N x N x 4 P=6 box "
-                         "(FP64 and FP32 applies, transfers and the coarse CG all launch); prints stats only")
+                    help="profiler driver: one short MIXED_TF32 solve on an N x N x 4 P=6 box (FP64, FP32 and "
+                         "tensor-core applies, transfers and the coarse CG all launch); prints stats only")
     a = ap.parse_args()
     if a.warmup < 3:
         a.warmup = 3
@@ -307,12 +311,12 @@ def main():
            "d2h_bytes_per_step": int(N * 8)}
     phi64 = phi.cpu().numpy()
 
-    def apply_view(ms_total, launches, word):
-        """Live event time of the finest-level single-precision applies against the HBM roofline."""
+    def apply_view(ms_total, launches, word, gword=None):
+        """Live event time of the finest-level applies against the HBM roofline."""
         if not launches:
             return None
         avg_s = ms_total / launches / 1000.0
-        byts = apply_bytes(P, E, N, word=word)
+        byts = apply_bytes(P, E, N, word=word, gword=gword)
         return {"avg_launch_ms": avg_s * 1e3, "launches": launches, "algorithmic_bytes": byts,
                 "achieved_gbs": byts / avg_s / 1e9, "peak_gbs": hbm_peak,
                 "frac_of_hbm": byts / avg_s / 1e9 / hbm_peak,
@@ -345,7 +349,7 @@ def main():
                    "apply_fp64": apply_view(sum(x["apply_ms"] for x in st_m), sum(x["apply_launches"] for x in st_m), 8)}
             if prec == "mixed_tf32":
                 obj["apply_tf32_tensor_cores"] = apply_view(sum(x["apply_tc_ms"] for x in st_m),
-                                                            sum(x["apply_tc_launches"] for x in st_m), 4)
+                                                            sum(x["apply_tc_launches"] for x in st_m), 4, gword=2)
                 mixed_tc = obj
             else:
                 mixed = obj

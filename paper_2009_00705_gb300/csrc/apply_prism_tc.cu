@@ -1,20 +1,21 @@
 // Tensor-core prism apply for the smoothing sweeps of the mixed-precision V-cycle
-// (Eq. laplaceproblemdiscrete, same contraction as apply_prism.cu): the two triangle
-// contractions per element run as TF32 warp MMAs (m16n8k8) with FP32 accumulation.
+// (Eq. laplaceproblemdiscrete, same contraction as apply_prism.cu).  Both triangle
+// contractions run as TF32 warp MMAs (m16n8k8) with FP32 accumulation, with the
+// element data as the A operand -- 16 rows = two elements x 8 vertical points -- and
+// the reference matrices as the B operand:
 //
-//   forward   [Ur; Us] = [Dr; Ds] U,  Ut = Bt W      rows qt, columns qz (one 8-wide tile)
-//   backward  Xr = Dr^T Vr + Ds^T Vs,  Xt = Bt^T Vt  rows n,  columns qz
+//   forward   [Ur Us Ut](e,qz; qt) = U(e,qz; n) [Dr Ds](n; qt),  W(e,qz; n) Bt(n; qt)
+//   backward  Xr(e,qz; n) = Vr(e,qz; qt) Dr(qt; n) + Vs Ds,  Xt = Vt Bt
 //
-// The reference matrices are the A operands (constant, TF32-rounded once into shared
-// memory with a padded row stride so ldmatrix is conflict-free); an element's nodal
-// data is the B operand with its vertical points as the 8 MMA columns, so every
-// element is one n-tile and a warp reuses each A fragment across several elements.
-// The geometric factors of a whole CTA pass (one contiguous range of G) arrive in
-// shared memory by one bulk asynchronous copy signalled on an mbarrier, issued as
-// soon as the previous pass has consumed its factors; the vertical stages and the
-// direct-stiffness summation stay on the SIMT pipes.  Operand rounding to TF32 makes
-// the result differ from the FP32 apply by a few 1e-4 relative: the kernel serves the
-// Chebyshev sweeps only, where the operator need not be exact.
+// The geometric factors come from a BF16 copy of G (half the bytes of the FP32
+// factors), staged per CTA pass into shared memory by bulk asynchronous copies on an
+// mbarrier; the pass's element map arrives the same way into a double buffer.  The
+// vertical stages, the gather and the direct-stiffness summation stay on the SIMT
+// pipes.  Shared memory stays below half an SM so that two CTAs share each SM and one
+// computes while the other waits.  Rounding the operands to TF32 and the factors to
+// BF16 makes the result differ from the FP32 apply by a few 1e-3 relative: the kernel
+// serves the Chebyshev sweeps only, where the operator need not be exact.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -28,38 +29,45 @@ namespace {
 constexpr int kTcSMs = 152;
 constexpr int kTcWarps = 8;
 constexpr int kTcThreads = 32 * kTcWarps;
-constexpr unsigned long long kTcWaitNs = 1000000000ULL;   // 1 s bound on the copy wait
+constexpr unsigned long long kTcWaitNs = 1000000000ULL;   // 1 s bound on a copy wait
+
+// elements per CTA pass by order: even, and every pass's map and factor block starts
+// on a 16-byte boundary (checked below)
+__host__ __device__ constexpr int tc_pass_elems(int P) {
+    return P == 6 ? 4 : (P == 5 ? 8 : (P == 4 ? 12 : 16));
+}
 
 template <int P>
 struct TcTile {
     static constexpr int NT = (P + 1) * (P + 2) / 2, NZ = P + 1, QT = (P + 1) * (P + 1), QZ = P + 1;
     static constexpr int Np = NT * NZ, Nq = QT * QZ;
-    static_assert(QZ <= 8, "an element's vertical points fill one 8-wide MMA column tile");
-    static constexpr int MTF = (QT + 15) / 16;     // forward m-tiles (rows qt)
-    static constexpr int KSF = (NT + 7) / 8;       // forward k-steps (columns n)
-    static constexpr int MTB = (NT + 15) / 16;     // backward m-tiles (rows n)
-    static constexpr int KSB = (QT + 7) / 8;       // backward k-steps (columns qt)
-    static_assert(MTF * 16 >= KSB * 8, "forward rows cover the backward K extent");
-    static constexpr int LDF = KSF * 8 + 4;        // row stride of the forward A matrices (floats)
-    static constexpr int LDB = KSB * 8 + 4;        // row stride of the backward A matrices
-    static constexpr int GE = 4;                   // elements per forward warp task
-    static constexpr int GB = 2;                   // elements per backward warp task
-    static constexpr int EB = GE * ((kTcWarps + MTF - 1) / MTF);   // elements per CTA pass (even)
-    static_assert(EB % 2 == 0 && EB % GB == 0, "pass size");
+    static_assert(QZ <= 8, "an element's vertical points fill 8 rows of the MMA");
+    static constexpr int NTF = (QT + 7) / 8;       // forward n-tiles (qt)
+    static constexpr int KSF = (NT + 7) / 8;       // forward k-steps (n)
+    static constexpr int NTB = KSF;                // backward n-tiles (n)
+    static constexpr int KSB = NTF;                // backward k-steps (qt)
+    // B-operand row strides (floats): stride/4 odd keeps the 8 rows of a fragment on
+    // distinct bank quads
+    static constexpr int LDF = KSF * 8 + 4;
+    static constexpr int LDB = KSB * 8 + 4;
+    static constexpr int EB = tc_pass_elems(P);
+    static constexpr int NPAIR = EB / 2;
+    static_assert(EB % 2 == 0, "elements pair up into MMA rows");
+    static_assert((EB * Np * 4) % 16 == 0, "map blocks of a pass start on 16-byte boundaries");
+    static_assert((EB * 6 * Nq * 2) % 16 == 0, "factor blocks of a pass start on 16-byte boundaries");
     __host__ __device__ static constexpr int r4(int v) { return (v + 3) / 4 * 4; }
-    // shared-memory regions, in floats (every offset a multiple of 4 floats = 16 bytes)
-    static constexpr int GSZ = r4(EB * 6 * Nq);
-    static constexpr int AF = 3 * MTF * 16 * LDF;
-    static constexpr int AB = 3 * MTB * 16 * LDB;
+    // shared-memory regions in 4-byte words, each a multiple of 4 words (16 bytes)
+    static constexpr int GSZ = r4((EB * 6 * Nq + 1) / 2);     // BF16 factors of a pass
+    static constexpr int BF = 3 * NTF * 8 * LDF;              // Dr, Ds, Bt as [qt][n]
+    static constexpr int BB = 3 * NTB * 8 * LDB;              // Dr, Ds, Bt as [n][qt]
     static constexpr int ZZ = r4(2 * QZ * NZ);
-    static constexpr int MAP = r4(EB * Np);
-    static constexpr int XS = r4(Np);              // gathered nodal values [NZ][NT]
-    static constexpr int US = KSF * 8 * 8;         // U or W: [KSF*8][8]
-    static constexpr int VS = KSB * 8 * 8;         // Vr, Vs or Vt: [KSB*8][8]
-    static constexpr int RS = MTB * 16 * 8;        // Xr or Xt: [MTB*16][8]
-    static constexpr int WORK = XS + 2 * US + 3 * VS + 2 * RS;
-    static constexpr int TOTAL = GSZ + AF + AB + ZZ + MAP + EB * WORK;
-    static constexpr size_t SMEM = sizeof(float) * (size_t)TOTAL;
+    static constexpr int MAP = r4(EB * Np);                    // one map buffer (ints)
+    static constexpr int UW = KSF * 8 * 8;                     // U or W [n][8]; later Xr or Xt
+    static constexpr int VS = KSB * 8 * 8;                     // Vr, Vs or Vt [qt][8]
+    static constexpr int WORK = 2 * UW + 3 * VS;
+    static constexpr int TOTAL = GSZ + BF + BB + ZZ + 2 * MAP + EB * WORK;
+    static constexpr size_t SMEM = 4 * (size_t)TOTAL;
+    static_assert(SMEM + 1024 + 128 <= 233472 / 2, "two CTAs per SM");
 };
 
 __device__ __forceinline__ uint32_t to_tf32(float f) {
@@ -70,12 +78,6 @@ __device__ __forceinline__ uint32_t to_tf32(float f) {
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t (&a)[4]) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3])
-                 : "r"(addr));
 }
 
 __device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
@@ -107,93 +109,102 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     }
 }
 
-// One thread: bulk-copy the geometric factors of elements [e, e + nb) into sG.  The
-// byte count is rounded up to 16 (the G allocation carries 64 bytes of padding) and
-// split into 16 KB pieces on the same mbarrier.
-template <int P>
-__device__ void issue_g(const float* G, int e, int nb, float* sG, uint32_t bar) {
-    using D = TcTile<P>;
-    const char* src = reinterpret_cast<const char*>(G + (size_t)e * 6 * D::Nq);
-    const uint32_t bytes = ((uint32_t)nb * 6u * D::Nq * 4u + 15u) & ~15u;
+// One thread: bulk-copy `bytes` (rounded up to 16; the source allocations carry 64
+// bytes of padding) from global `src` to shared `dst`, in pieces of at most 16 KB,
+// completing on mbarrier `bar`.
+__device__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint32_t bar) {
+    bytes = (bytes + 15u) & ~15u;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-    const uint32_t dst = smem_u32(sG);
+    const uint32_t d = smem_u32(dst);
+    const char* s = reinterpret_cast<const char*>(src);
     for (uint32_t off = 0; off < bytes; off += 16384u) {
         const uint32_t n = (bytes - off < 16384u) ? (bytes - off) : 16384u;
         asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst + off),
-            "l"(src + off), "r"(n), "r"(bar)
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d + off),
+            "l"(s + off), "r"(n), "r"(bar)
             : "memory");
     }
 }
 
 template <int P>
-__global__ void __launch_bounds__(kTcThreads, 1)
-    k_apply_prism_tc(int E, const int* __restrict__ map, const float* __restrict__ G, const float* __restrict__ refm,
-                     const float* __restrict__ x, float* __restrict__ y, const int* __restrict__ skip, int* err) {
+__global__ void __launch_bounds__(kTcThreads, 2)
+    k_apply_prism_tc(int E, const int* __restrict__ map, const __nv_bfloat16* __restrict__ G16,
+                     const float* __restrict__ refm, const float* __restrict__ x, float* __restrict__ y,
+                     const int* __restrict__ skip, int* err) {
     using D = TcTile<P>;
     constexpr int NT = D::NT, NZ = D::NZ, QT = D::QT, QZ = D::QZ, Np = D::Np, Nq = D::Nq, EB = D::EB;
     if (skip != nullptr && *skip) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ __align__(8) unsigned long long mbar[2];   // [0] geometric factors, [1] element map
     __shared__ int s_fail;
     float* sm = reinterpret_cast<float*>(smem_raw);
-    float* sG = sm;
-    float* sAF = sG + D::GSZ;                 // [3][MTF*16][LDF]: Dr, Ds, Bt (TF32 bits)
-    float* sAB = sAF + D::AF;                 // [3][MTB*16][LDB]: Dr^T, Ds^T, Bt^T
-    float* sZ = sAB + D::AB;                  // [Bz | Dz] as [QZ][NZ]
-    int* sMap = reinterpret_cast<int*>(sZ + D::ZZ);
-    float* work = sZ + D::ZZ + D::MAP;
+    __nv_bfloat16* sG = reinterpret_cast<__nv_bfloat16*>(sm);
+    float* sBF = sm + D::GSZ;                  // [3][NTF*8][LDF]: Dr, Ds, Bt as (qt, n), TF32 bits
+    float* sBB = sBF + D::BF;                  // [3][NTB*8][LDB]: Dr, Ds, Bt as (n, qt)
+    float* sZ = sBB + D::BB;                   // [Bz | Dz] as [QZ][NZ]
+    int* sMap0 = reinterpret_cast<int*>(sZ + D::ZZ);    // two map buffers of D::MAP ints
+    float* work = sZ + D::ZZ + 2 * D::MAP;    // per element: U, W (later Xr, Xt), Vr, Vs, Vt
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = lane >> 2, t = lane & 3;
 
     // every pad entry must be finite (and zero where it meets a non-zero operand)
     for (int i = tid; i < D::TOTAL; i += kTcThreads) sm[i] = 0.f;
     __syncthreads();
-    const float* rBt = refm;
-    const float* rDr = refm + QT * NT;
-    const float* rDs = refm + 2 * QT * NT;
     for (int i = tid; i < QT * NT; i += kTcThreads) {
         const int qt = i / NT, n = i - qt * NT;
-        sAF[(0 * D::MTF * 16 + qt) * D::LDF + n] = __uint_as_float(to_tf32(rDr[i]));
-        sAF[(1 * D::MTF * 16 + qt) * D::LDF + n] = __uint_as_float(to_tf32(rDs[i]));
-        sAF[(2 * D::MTF * 16 + qt) * D::LDF + n] = __uint_as_float(to_tf32(rBt[i]));
-        sAB[(0 * D::MTB * 16 + n) * D::LDB + qt] = __uint_as_float(to_tf32(rDr[i]));
-        sAB[(1 * D::MTB * 16 + n) * D::LDB + qt] = __uint_as_float(to_tf32(rDs[i]));
-        sAB[(2 * D::MTB * 16 + n) * D::LDB + qt] = __uint_as_float(to_tf32(rBt[i]));
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            // reference blocks in refm: Bt, Dr, Ds as [QT][NT]; here Dr, Ds, Bt
+            const float v = refm[((m + 1) % 3) * QT * NT + i];
+            sBF[(m * D::NTF * 8 + qt) * D::LDF + n] = __uint_as_float(to_tf32(v));
+            sBB[(m * D::NTB * 8 + n) * D::LDB + qt] = __uint_as_float(to_tf32(v));
+        }
     }
     for (int i = tid; i < 2 * QZ * NZ; i += kTcThreads) sZ[i] = refm[6 * QT * NT + i];
     const float* sBz = sZ;
     const float* sDz = sZ + QZ * NZ;
-    const uint32_t bar = smem_u32(&mbar);
+    const uint32_t barg = smem_u32(&mbar[0]), barm = smem_u32(&mbar[1]);
     if (tid == 0) {
         s_fail = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barg) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barm) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    uint32_t parity = 0;
-    if (tid == 0 && blockIdx.x * EB < E) issue_g<P>(G, blockIdx.x * EB, min(EB, E - blockIdx.x * EB), sG, bar);
+    uint32_t pg = 0, pm = 0;
+    int buf = 0;
+    if (tid == 0 && blockIdx.x * EB < E) {
+        const int e = blockIdx.x * EB, nb0 = min(EB, E - e);
+        bulk_copy(sMap0, map + (size_t)e * Np, (uint32_t)nb0 * Np * 4u, barm);
+        bulk_copy(sG, G16 + (size_t)e * 6 * Nq, (uint32_t)nb0 * 6u * Nq * 2u, barg);
+    }
 
     for (int e0 = blockIdx.x * EB; e0 < E; e0 += gridDim.x * EB) {
         const int nb = min(EB, E - e0);
-        // gather: element-local nodal values and the map of the pass
-        for (int i = tid; i < nb * Np; i += kTcThreads) {
-            const int b = i / Np, l = i - b * Np;
-            const int m = map[(size_t)(e0 + b) * Np + l];
-            sMap[b * Np + l] = m;
-            work[b * D::WORK + l] = (m >= 0) ? x[m] : 0.f;
-        }
+        const int* sMap = sMap0 + buf * D::MAP;
+        if (!mbar_wait(barm, pm)) s_fail = 1;
         __syncthreads();
-        // vertical stage: U[n][qz] = sum_k Bz[qz][k] X[k][n], W likewise with Dz (TF32-rounded)
+        if (s_fail) break;          // uniform: every thread read s_fail after the barrier
+        pm ^= 1u;
+        // the next pass's map into the other buffer (its last reader, the previous pass's
+        // summation, finished before the barrier that closed that pass)
+        if (tid == 0) {
+            const int en = e0 + gridDim.x * EB;
+            if (en < E)
+                bulk_copy(sMap0 + (buf ^ 1) * D::MAP, map + (size_t)en * Np, (uint32_t)min(EB, E - en) * Np * 4u, barm);
+        }
+        // gather and vertical stage: U(n, qz) = sum_k Bz[qz][k] x(k, n), W likewise with Dz
         for (int i = tid; i < nb * NT; i += kTcThreads) {
             const int b = i / NT, n = i - b * NT;
-            float* wb = work + b * D::WORK;
             float xk[NZ];
 #pragma unroll
-            for (int k = 0; k < NZ; ++k) xk[k] = wb[k * NT + n];
-            float* U = wb + D::XS + n * 8;
-            float* W = wb + D::XS + D::US + n * 8;
+            for (int k = 0; k < NZ; ++k) {
+                const int m = sMap[b * Np + k * NT + n];
+                xk[k] = (m >= 0) ? x[m] : 0.f;
+            }
+            float* U = work + b * D::WORK + n * 8;
+            float* W = U + D::UW;
 #pragma unroll
             for (int qz = 0; qz < QZ; ++qz) {
                 float u = 0.f, w = 0.f;
@@ -207,127 +218,100 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
         }
         // this pass's geometric factors
-        if (!mbar_wait(bar, parity)) s_fail = 1;
+        if (!mbar_wait(barg, pg)) s_fail = 1;
         __syncthreads();
-        if (s_fail) break;          // uniform: every thread read s_fail after the barrier
-        parity ^= 1u;
-        // forward contractions and the geometric factors: warp task = (m-tile, GE elements)
-        for (int task = warp; task < D::MTF * (EB / D::GE); task += kTcWarps) {
-            const int mt = task % D::MTF, grp = task / D::MTF;
-            float c[3][D::GE][4];
-#pragma unroll
-            for (int m = 0; m < 3; ++m)
-#pragma unroll
-                for (int j = 0; j < D::GE; ++j)
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) c[m][j][r] = 0.f;
-            const int arow = mt * 16 + (lane & 7) + ((lane >> 3) & 1) * 8;
-            const int acol = (lane >> 4) * 4;
+        if (s_fail) break;
+        pg ^= 1u;
+        // forward contractions and the geometric factors: warp task = (element pair, qt tile)
+        for (int task = warp; task < D::NPAIR * D::NTF; task += kTcWarps) {
+            const int pr = task / D::NTF, j = task - pr * D::NTF;
+            const float* U0 = work + (2 * pr) * D::WORK;
+            const float* U1 = U0 + D::WORK;
+            const float* W0 = U0 + D::UW;
+            const float* W1 = U1 + D::UW;
+            float cr[4] = {0.f, 0.f, 0.f, 0.f}, cs[4] = {0.f, 0.f, 0.f, 0.f}, ct[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int ks = 0; ks < D::KSF; ++ks) {
-                uint32_t ar[4], as[4], at[4];
-                ldsm_x4(smem_u32(sAF + (0 * D::MTF * 16 + arow) * D::LDF + ks * 8 + acol), ar);
-                ldsm_x4(smem_u32(sAF + (1 * D::MTF * 16 + arow) * D::LDF + ks * 8 + acol), as);
-                ldsm_x4(smem_u32(sAF + (2 * D::MTF * 16 + arow) * D::LDF + ks * 8 + acol), at);
-#pragma unroll
-                for (int j = 0; j < D::GE; ++j) {
-                    const float* wb = work + (grp * D::GE + j) * D::WORK;
-                    const float* U = wb + D::XS;
-                    const float* W = wb + D::XS + D::US;
-                    const uint32_t u0 = __float_as_uint(U[(ks * 8 + t) * 8 + g]);
-                    const uint32_t u1 = __float_as_uint(U[(ks * 8 + t + 4) * 8 + g]);
-                    const uint32_t w0 = __float_as_uint(W[(ks * 8 + t) * 8 + g]);
-                    const uint32_t w1 = __float_as_uint(W[(ks * 8 + t + 4) * 8 + g]);
-                    mma_tf32(c[0][j], ar, u0, u1);
-                    mma_tf32(c[1][j], as, u0, u1);
-                    mma_tf32(c[2][j], at, w0, w1);
-                }
+                const int o0 = (ks * 8 + t) * 8 + g, o1 = o0 + 32;
+                const uint32_t au[4] = {__float_as_uint(U0[o0]), __float_as_uint(U1[o0]), __float_as_uint(U0[o1]),
+                                        __float_as_uint(U1[o1])};
+                const uint32_t aw[4] = {__float_as_uint(W0[o0]), __float_as_uint(W1[o0]), __float_as_uint(W0[o1]),
+                                        __float_as_uint(W1[o1])};
+                const int row = (j * 8 + g) * D::LDF + ks * 8 + t;
+                const float* B0 = sBF + row;
+                const float* B1 = B0 + D::NTF * 8 * D::LDF;
+                const float* B2 = B1 + D::NTF * 8 * D::LDF;
+                mma_tf32(cr, au, __float_as_uint(B0[0]), __float_as_uint(B0[4]));
+                mma_tf32(cs, au, __float_as_uint(B1[0]), __float_as_uint(B1[4]));
+                mma_tf32(ct, aw, __float_as_uint(B2[0]), __float_as_uint(B2[4]));
             }
 #pragma unroll
-            for (int j = 0; j < D::GE; ++j) {
-                const int b = grp * D::GE + j;
+            for (int r = 0; r < 4; ++r) {
+                const int b = 2 * pr + (r >> 1);
                 if (b >= nb) continue;
-                float* wb = work + b * D::WORK;
-                float* Vr = wb + D::XS + 2 * D::US;
-                float* Vs = Vr + D::VS;
-                float* Vt = Vs + D::VS;
-                const float* Gb = sG + (size_t)b * 6 * Nq;
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const int qt = mt * 16 + g + ((r >> 1) << 3);
-                    const int qz = 2 * t + (r & 1);
-                    float vr = 0.f, vs = 0.f, vt = 0.f;
-                    if (qt < QT && qz < QZ) {
-                        const int q = qz * QT + qt;
-                        const float g0 = Gb[q], g1 = Gb[Nq + q], g2 = Gb[2 * Nq + q];
-                        const float g3 = Gb[3 * Nq + q], g4 = Gb[4 * Nq + q], g5 = Gb[5 * Nq + q];
-                        const float ur = c[0][j][r], us = c[1][j][r], ut = c[2][j][r];
-                        vr = g0 * ur + g1 * us + g2 * ut;
-                        vs = g1 * ur + g3 * us + g4 * ut;
-                        vt = g2 * ur + g4 * us + g5 * ut;
-                    }
-                    if (qt < D::KSB * 8) {
-                        Vr[qt * 8 + qz] = __uint_as_float(to_tf32(vr));
-                        Vs[qt * 8 + qz] = __uint_as_float(to_tf32(vs));
-                        Vt[qt * 8 + qz] = __uint_as_float(to_tf32(vt));
-                    }
+                const int qz = g, qt = j * 8 + 2 * t + (r & 1);
+                float vr = 0.f, vs = 0.f, vt = 0.f;
+                if (qt < QT && qz < QZ) {
+                    const __nv_bfloat16* Gb = sG + (size_t)b * 6 * Nq + qz * QT + qt;
+                    const float g0 = __bfloat162float(Gb[0]), g1 = __bfloat162float(Gb[Nq]);
+                    const float g2 = __bfloat162float(Gb[2 * Nq]), g3 = __bfloat162float(Gb[3 * Nq]);
+                    const float g4 = __bfloat162float(Gb[4 * Nq]), g5 = __bfloat162float(Gb[5 * Nq]);
+                    vr = g0 * cr[r] + g1 * cs[r] + g2 * ct[r];
+                    vs = g1 * cr[r] + g3 * cs[r] + g4 * ct[r];
+                    vt = g2 * cr[r] + g4 * cs[r] + g5 * ct[r];
                 }
+                float* Vr = work + b * D::WORK + 2 * D::UW + qt * 8 + qz;
+                Vr[0] = __uint_as_float(to_tf32(vr));
+                Vr[D::VS] = __uint_as_float(to_tf32(vs));
+                Vr[2 * D::VS] = __uint_as_float(to_tf32(vt));
             }
         }
         __syncthreads();
         // the factors are consumed: stream in the next pass's while this one finishes
         if (tid == 0) {
             const int en = e0 + gridDim.x * EB;
-            if (en < E) issue_g<P>(G, en, min(EB, E - en), sG, bar);
+            if (en < E) bulk_copy(sG, G16 + (size_t)en * 6 * Nq, (uint32_t)min(EB, E - en) * 6u * Nq * 2u, barg);
         }
-        // backward contractions: warp task = (m-tile, GB elements)
-        for (int task = warp; task < D::MTB * (EB / D::GB); task += kTcWarps) {
-            const int mt = task % D::MTB, grp = task / D::MTB;
-            float xr[D::GB][4], xt[D::GB][4];
-#pragma unroll
-            for (int j = 0; j < D::GB; ++j)
-#pragma unroll
-                for (int r = 0; r < 4; ++r) xr[j][r] = xt[j][r] = 0.f;
-            const int arow = mt * 16 + (lane & 7) + ((lane >> 3) & 1) * 8;
-            const int acol = (lane >> 4) * 4;
+        // backward contractions: warp task = (element pair, node tile)
+        for (int task = warp; task < D::NPAIR * D::NTB; task += kTcWarps) {
+            const int pr = task / D::NTB, j = task - pr * D::NTB;
+            const float* V0 = work + (2 * pr) * D::WORK + 2 * D::UW;
+            const float* V1 = V0 + D::WORK;
+            float xr[4] = {0.f, 0.f, 0.f, 0.f}, xt[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 1
             for (int ks = 0; ks < D::KSB; ++ks) {
-                uint32_t ar[4], as[4], at[4];
-                ldsm_x4(smem_u32(sAB + (0 * D::MTB * 16 + arow) * D::LDB + ks * 8 + acol), ar);
-                ldsm_x4(smem_u32(sAB + (1 * D::MTB * 16 + arow) * D::LDB + ks * 8 + acol), as);
-                ldsm_x4(smem_u32(sAB + (2 * D::MTB * 16 + arow) * D::LDB + ks * 8 + acol), at);
+                const int o0 = (ks * 8 + t) * 8 + g, o1 = o0 + 32;
+                const int row = (j * 8 + g) * D::LDB + ks * 8 + t;
+                const float* B0 = sBB + row;
+                const float* B1 = B0 + D::NTB * 8 * D::LDB;
+                const float* B2 = B1 + D::NTB * 8 * D::LDB;
 #pragma unroll
-                for (int j = 0; j < D::GB; ++j) {
-                    const float* Vr = work + (grp * D::GB + j) * D::WORK + D::XS + 2 * D::US;
-                    const float* Vs = Vr + D::VS;
-                    const float* Vt = Vs + D::VS;
-                    const int o0 = (ks * 8 + t) * 8 + g, o1 = (ks * 8 + t + 4) * 8 + g;
-                    mma_tf32(xr[j], ar, __float_as_uint(Vr[o0]), __float_as_uint(Vr[o1]));
-                    mma_tf32(xr[j], as, __float_as_uint(Vs[o0]), __float_as_uint(Vs[o1]));
-                    mma_tf32(xt[j], at, __float_as_uint(Vt[o0]), __float_as_uint(Vt[o1]));
+                for (int m = 0; m < 3; ++m) {
+                    const float* A0 = V0 + m * D::VS;
+                    const float* A1 = V1 + m * D::VS;
+                    const uint32_t a[4] = {__float_as_uint(A0[o0]), __float_as_uint(A1[o0]), __float_as_uint(A0[o1]),
+                                           __float_as_uint(A1[o1])};
+                    const float* Bm = (m == 0) ? B0 : (m == 1 ? B1 : B2);
+                    if (m < 2) mma_tf32(xr, a, __float_as_uint(Bm[0]), __float_as_uint(Bm[4]));
+                    else mma_tf32(xt, a, __float_as_uint(Bm[0]), __float_as_uint(Bm[4]));
                 }
             }
 #pragma unroll
-            for (int j = 0; j < D::GB; ++j) {
-                const int b = grp * D::GB + j;
+            for (int r = 0; r < 4; ++r) {
+                const int b = 2 * pr + (r >> 1);
                 if (b >= nb) continue;
-                float* Xr = work + b * D::WORK + D::XS + 2 * D::US + 3 * D::VS;
-                float* Xt = Xr + D::RS;
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const int n = mt * 16 + g + ((r >> 1) << 3);
-                    const int qz = 2 * t + (r & 1);
-                    Xr[n * 8 + qz] = xr[j][r];
-                    Xt[n * 8 + qz] = xt[j][r];
-                }
+                const int n = j * 8 + 2 * t + (r & 1);
+                float* X = work + b * D::WORK + n * 8 + g;     // Xr over U, Xt over W
+                X[0] = xr[r];
+                X[D::UW] = xt[r];
             }
         }
         __syncthreads();
         // transposed vertical stage and direct-stiffness summation
         for (int i = tid; i < nb * NT; i += kTcThreads) {
             const int b = i / NT, n = i - b * NT;
-            const float* Xr = work + b * D::WORK + D::XS + 2 * D::US + 3 * D::VS + n * 8;
-            const float* Xt = Xr + D::RS;
+            const float* Xr = work + b * D::WORK + n * 8;
+            const float* Xt = Xr + D::UW;
             float xr[QZ], xt[QZ];
 #pragma unroll
             for (int qz = 0; qz < QZ; ++qz) {
@@ -344,12 +328,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
         }
         __syncthreads();
+        buf ^= 1;
     }
     if (s_fail) {
-        // a copy did not complete in time: report it, give it a second bounded wait, return
+        // a copy did not complete in time: report it, give the copies in flight a second
+        // bounded wait, return
         if (tid == 0) {
             atomicExch(err, 1);
-            mbar_wait(bar, parity);
+            mbar_wait(barm, pm);
+            mbar_wait(barg, pg);
         }
         __syncthreads();
     }
@@ -368,11 +355,18 @@ cudaError_t apply_tc_impl(const Level& L, const float* x, float* y, const int* s
         if (e != cudaSuccess) return e;
         configured[dev] = true;
     }
+    if (L.G16 == nullptr) return cudaErrorInvalidValue;
     const int passes = (L.E + D::EB - 1) / D::EB;
-    const int grid = passes < kTcSMs ? passes : kTcSMs;
+    const int grid = passes < 2 * kTcSMs ? passes : 2 * kTcSMs;
     if (grid < 1) return cudaSuccess;
-    k_apply_prism_tc<P><<<grid, kTcThreads, D::SMEM, s>>>(L.E, L.map, L.G32, L.ref32.m, x, y, skip, err);
+    k_apply_prism_tc<P><<<grid, kTcThreads, D::SMEM, s>>>(
+        L.E, L.map, reinterpret_cast<const __nv_bfloat16*>(L.G16), L.ref32.m, x, y, skip, err);
     return cudaGetLastError();
+}
+
+__global__ void k_to_bf16(long long n, const float* __restrict__ a, __nv_bfloat16* __restrict__ b) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        b[i] = __float2bfloat16_rn(a[i]);
 }
 
 }  // namespace
@@ -390,5 +384,22 @@ cudaError_t launch_apply_prism_tc(const Level& L, const float* x, float* y, cons
 }
 
 bool prism_tc_supported(int p) { return p >= 2 && p <= 6; }
+
+// BF16 copy of a prism level's FP32 geometric factors for the tensor-core apply
+// (+32 entries of padding for its 16-byte-rounded bulk copies).
+cudaError_t build_g16(Level& L, cudaStream_t s) {
+    if (L.dim != 3 || !prism_tc_supported(L.p) || L.G32 == nullptr) return cudaSuccess;
+    const long long n = (long long)L.E * L.ncomp * L.Nq;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, sizeof(__nv_bfloat16) * (size_t)(n + 32));
+    if (e != cudaSuccess) return e;
+    L.G16 = static_cast<unsigned short*>(p);
+    e = cudaMemsetAsync(p, 0, sizeof(__nv_bfloat16) * (size_t)(n + 32), s);
+    if (e != cudaSuccess) return e;
+    const long long blocks = (n + 255) / 256;
+    k_to_bf16<<<(int)(blocks < 4096 ? (blocks > 0 ? blocks : 1) : 4096), 256, 0, s>>>(
+        n, L.G32, static_cast<__nv_bfloat16*>(p));
+    return cudaGetLastError();
+}
 
 }  // namespace sem

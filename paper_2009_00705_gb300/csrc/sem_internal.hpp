@@ -38,6 +38,7 @@ struct Level {
     int* map = nullptr;
     double* G = nullptr;                   // [E][ncomp][Nq]
     float* G32 = nullptr;
+    unsigned short* G16 = nullptr;         // BF16 copy of G32 for the tensor-core apply (prisms, p >= 2)
     double* dinv = nullptr;                // 1/diag on free nodes, 0 on Dirichlet
     float* dinv32 = nullptr;
     long long* dir = nullptr;              // Dirichlet node ids
@@ -164,6 +165,7 @@ int prism_tile_elements(int P, int variant);
 cudaError_t launch_apply_prism_tc(const Level& L, const float* x, float* y, const int* skip, int* err,
                                   cudaStream_t s);
 bool prism_tc_supported(int p);
+cudaError_t build_g16(Level& L, cudaStream_t s);
 cudaError_t launch_geometry(Level& L, const double* vtri, const double* etaP, const double* BP,
                             const double* DrP, const double* DsP, int NTP, int nlayers, double depth,
                             cudaStream_t s);

@@ -198,7 +198,11 @@ sem_status build_level(sem_handle* h, const sem_mesh* m, int li, int p) {
     }
     std::vector<double> wm(L.N);
     for (long long i = 0; i < L.N; ++i) wm[i] = mult[i] > 0 ? 1.0 / mult[i] : 0.0;
-    CK(upload(&L.map, L.hmap));
+    {   // +16 ints of padding: the tensor-core apply's bulk copies of the map round up to 16 B
+        std::vector<int> padded(L.hmap);
+        padded.resize(L.hmap.size() + 16, 0);
+        CK(upload(&L.map, padded));
+    }
     CK(upload(&L.owner, owner));
     CK(upload(&L.wmult, wm));
     CK(upload(&L.wmult32, to_float(wm)));
@@ -254,6 +258,7 @@ sem_status build_geometry(sem_handle* h, const sem_mesh* m) {
         cudaFree(dDr);
         cudaFree(dDs);
         CK(e);
+        CK(build_g16(L, 0));
     }
     cudaFree(dvtri);
     cudaFree(detaP);

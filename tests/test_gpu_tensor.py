@@ -1,9 +1,10 @@
 """The TF32 tensor-core prism apply (Chebyshev sweeps of the MIXED_TF32 V-cycle).
 
-Tolerance: operands are rounded to TF32 (unit roundoff 2^-11 = 4.9e-4) and the
-products accumulate in FP32, so an entry of y = A x carries an error of order
-1e-3 of the terms it sums; for random x the entries are of the size of their
-terms, and the bound is 5e-3 of max|y| entrywise and 2e-3 of ||y||_2 overall.
+Tolerance: the MMA operands are rounded to TF32 (unit roundoff 2^-11 = 4.9e-4)
+and the geometric factors come from a BF16 copy (unit roundoff 2^-9 = 2.0e-3);
+products accumulate in FP32.  An entry of y = A x therefore carries an error of
+a few 1e-3 of the terms it sums; for random x the entries are of the size of
+their terms, and the bound is 1e-2 of max|y| entrywise and 4e-3 of ||y||_2.
 The solves that use the kernel still reach an FP64 residual of 1e-11, so their
 error against the oracle's direct solution is the tolerance's (1e-8)."""
 import numpy as np
@@ -43,8 +44,10 @@ def _solver(sem, mesh, prob, levels, **o):
 
 def _check_apply(y_tc, y_ref):
     scale = np.abs(y_ref).max()
-    assert np.abs(y_tc - y_ref).max() <= 5e-3 * scale, np.abs(y_tc - y_ref).max() / scale
-    assert np.linalg.norm(y_tc - y_ref) <= 2e-3 * np.linalg.norm(y_ref)
+    e_max = np.abs(y_tc - y_ref).max() / scale
+    e_2 = np.linalg.norm(y_tc - y_ref) / np.linalg.norm(y_ref)
+    print(f"tensor-core apply: max error {e_max:.2e} of max|y|, 2-norm error {e_2:.2e}")
+    assert e_max <= 1e-2 and e_2 <= 4e-3
 
 
 @pytest.mark.parametrize("name", list(SMALL))
@@ -74,8 +77,8 @@ def test_tensor_core_apply_matches_oracle_on_every_level(sem, name):
 
 
 def test_tensor_core_apply_many_passes_per_cta(sem):
-    # 19 x 19 x 3 prisms at P = 6: 2166 elements = 271 passes of 8 over at most 152
-    # CTAs, the last pass ragged (6 elements); rows sampled against the oracle
+    # 19 x 19 x 3 prisms at P = 6: 2166 elements = 542 passes of 4 over at most 304
+    # CTAs (two per SM), the last pass ragged (2 elements); rows sampled against the oracle
     mesh = W.box3d(19, 19, 3, eta_modes=W.eta_sinx_cosy(0.1))
     levels = [6, 3, 1]
     xy = sem.sem_mesh_nodes2d(mesh, 6)
@@ -95,7 +98,7 @@ def test_tensor_core_apply_many_passes_per_cta(sem):
         rows = np.random.default_rng(3).choice(N, 200, replace=False)
         ref = prob.apply_rows(0, x.astype(np.float64), rows)
         got = y_tc.cpu().numpy().astype(np.float64)[rows]
-        assert np.abs(got - ref).max() <= 5e-3 * np.abs(ref).max()
+        assert np.abs(got - ref).max() <= 1e-2 * np.abs(ref).max()
     finally:
         s.close()
 
