@@ -41,15 +41,18 @@ template <int P>
 struct TcTile {
     static constexpr int NT = (P + 1) * (P + 2) / 2, NZ = P + 1, QT = (P + 1) * (P + 1), QZ = P + 1;
     static constexpr int Np = NT * NZ, Nq = QT * QZ;
-    static_assert(QZ <= 8, "an element's vertical points fill 8 rows of the MMA");
+    static_assert(QZ <= 8 && NZ <= 8, "an element's vertical points / nodes fill 8 MMA rows");
     static constexpr int NTF = (QT + 7) / 8;       // forward n-tiles (qt)
     static constexpr int KSF = (NT + 7) / 8;       // forward k-steps (n)
     static constexpr int NTB = KSF;                // backward n-tiles (n)
     static constexpr int KSB = NTF;                // backward k-steps (qt)
-    // B-operand row strides (floats): stride/4 odd keeps the 8 rows of a fragment on
-    // distinct bank quads
-    static constexpr int LDF = KSF * 8 + 4;
-    static constexpr int LDB = KSB * 8 + 4;
+    // row strides (words) of ldmatrix operands: stride/4 odd puts the 8 rows of a
+    // fragment on distinct bank quads
+    static constexpr int LDF = KSF * 8 + 4;        // reference matrices as (qt, n)
+    static constexpr int LDB = KSB * 8 + 4;        // reference matrices as (n, qt)
+    static constexpr int LDU = KSF * 8 + 4;        // U, W as (qz, n)
+    static constexpr int LDV = KSB * 8 + 4;        // Vr, Vs, Vt as (qz, qt)
+    static constexpr int LDX = 20;                 // [Xr | Xt] as (n, 16): scalar fragment loads, 20/4 odd
     static constexpr int EB = tc_pass_elems(P);
     static constexpr int NPAIR = EB / 2;
     static_assert(EB % 2 == 0, "elements pair up into MMA rows");
@@ -60,14 +63,20 @@ struct TcTile {
     static constexpr int GSZ = r4((EB * 6 * Nq + 1) / 2);     // BF16 factors of a pass
     static constexpr int BF = 3 * NTF * 8 * LDF;              // Dr, Ds, Bt as [qt][n]
     static constexpr int BB = 3 * NTB * 8 * LDB;              // Dr, Ds, Bt as [n][qt]
-    static constexpr int ZZ = r4(2 * QZ * NZ);
     static constexpr int MAP = r4(EB * Np);                    // one map buffer (ints)
-    static constexpr int UW = KSF * 8 * 8;                     // U or W [n][8]; later Xr or Xt
-    static constexpr int VS = KSB * 8 * 8;                     // Vr, Vs or Vt [qt][8]
-    static constexpr int WORK = 2 * UW + 3 * VS;
-    static constexpr int TOTAL = GSZ + BF + BB + ZZ + 2 * MAP + EB * WORK;
+    // vertical-stage MMA tasks (element, node tile) of a pass per warp: each lane keeps the
+    // x values of its B fragments for the next pass in registers
+    static constexpr int TPW = (EB * NTB + kTcWarps - 1) / kTcWarps;
+    // per element: region R1 holds U, W [qz][n] until the forward contraction, then
+    // [Xr | Xt] [n][LDX]; V holds Vr, Vs, Vt [qz][qt]
+    static constexpr int UW = 8 * LDU;
+    static constexpr int XX = NTB * 8 * LDX;
+    static constexpr int R1 = (2 * UW > XX) ? 2 * UW : XX;
+    static constexpr int VS = 8 * LDV;
+    static constexpr int WORK = R1 + 3 * VS;
+    static constexpr int TOTAL = GSZ + BF + BB + 2 * MAP + EB * WORK;
     static constexpr size_t SMEM = 4 * (size_t)TOTAL;
-    static_assert(SMEM + 1024 + 128 <= 233472 / 2, "two CTAs per SM");
+    static_assert(SMEM + 1024 + 256 <= 233472 / 2, "two CTAs per SM");
 };
 
 __device__ __forceinline__ uint32_t to_tf32(float f) {
@@ -86,6 +95,16 @@ __device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], 
         "{%0,%1,%2,%3};"
         : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t (&a)[4]) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3])
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t& b0, uint32_t& b1) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(b0), "=r"(b1) : "r"(addr));
 }
 
 __device__ __forceinline__ unsigned long long tc_ns() {
@@ -129,7 +148,7 @@ __device__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint32_t b
 
 template <int P>
 __global__ void __launch_bounds__(kTcThreads, 2)
-    k_apply_prism_tc(int E, const int* __restrict__ map, const __nv_bfloat16* __restrict__ G16,
+    k_apply_prism_tc(int E, int N, const int* __restrict__ map, const __nv_bfloat16* __restrict__ G16,
                      const float* __restrict__ refm, const float* __restrict__ x, float* __restrict__ y,
                      const int* __restrict__ skip, int* err) {
     using D = TcTile<P>;
@@ -142,11 +161,14 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     __nv_bfloat16* sG = reinterpret_cast<__nv_bfloat16*>(sm);
     float* sBF = sm + D::GSZ;                  // [3][NTF*8][LDF]: Dr, Ds, Bt as (qt, n), TF32 bits
     float* sBB = sBF + D::BF;                  // [3][NTB*8][LDB]: Dr, Ds, Bt as (n, qt)
-    float* sZ = sBB + D::BB;                   // [Bz | Dz] as [QZ][NZ]
-    int* sMap0 = reinterpret_cast<int*>(sZ + D::ZZ);    // two map buffers of D::MAP ints
-    float* work = sZ + D::ZZ + 2 * D::MAP;    // per element: U, W (later Xr, Xt), Vr, Vs, Vt
+    int* sMap0 = reinterpret_cast<int*>(sBB + D::BB);   // two map buffers of D::MAP ints
+    float* work = sBB + D::BB + 2 * D::MAP;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = lane >> 2, t = lane & 3;
+    // ldmatrix lane addressing: A (16 x 8 tile of two elements' 8 rows): row lane&7 of
+    // element (lane>>3)&1 at column offset (lane>>4)*4; B (8 x 8 tile): row lane&7 at
+    // column offset ((lane>>3)&1)*4
+    const int lrow = lane & 7, lsel = (lane >> 3) & 1, lcolA = (lane >> 4) * 4, lcolB = lsel * 4;
 
     // every pad entry must be finite (and zero where it meets a non-zero operand)
     for (int i = tid; i < D::TOTAL; i += kTcThreads) sm[i] = 0.f;
@@ -161,9 +183,17 @@ __global__ void __launch_bounds__(kTcThreads, 2)
             sBB[(m * D::NTB * 8 + n) * D::LDB + qt] = __uint_as_float(to_tf32(v));
         }
     }
-    for (int i = tid; i < 2 * QZ * NZ; i += kTcThreads) sZ[i] = refm[6 * QT * NT + i];
-    const float* sBz = sZ;
-    const float* sDz = sZ + QZ * NZ;
+    // constant A operands of the vertical stages, in registers.  Forward: rows 0-7 Bz(qz, k),
+    // rows 8-15 Dz(qz, k).  Transposed: k-step 0 Bz(qz, k) as (k, qz), k-step 1 Dz(qz, k) as
+    // (k, qz), rows 8-15 zero.  refm ends with [Bz | Dz] as [QZ][NZ].
+    const float* rBz = refm + 6 * QT * NT;
+    const float* rDz = rBz + QZ * NZ;
+    auto zq = [&](const float* M, int qz, int k) -> uint32_t {
+        return (qz < QZ && k < NZ) ? to_tf32(M[qz * NZ + k]) : 0u;
+    };
+    const uint32_t av[4] = {zq(rBz, g, t), zq(rDz, g, t), zq(rBz, g, t + 4), zq(rDz, g, t + 4)};
+    const uint32_t at0[4] = {zq(rBz, t, g), 0u, zq(rBz, t + 4, g), 0u};
+    const uint32_t at1[4] = {zq(rDz, t, g), 0u, zq(rDz, t + 4, g), 0u};
     const uint32_t barg = smem_u32(&mbar[0]), barm = smem_u32(&mbar[1]);
     if (tid == 0) {
         s_fail = 0;
@@ -174,48 +204,67 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     __syncthreads();
     uint32_t pg = 0, pm = 0;
     int buf = 0;
+    const int stride = gridDim.x * EB;
+    // B fragments of the vertical-stage MMA for a pass: lane (g, t) of a warp's task
+    // (element b, node tile jj) holds x(k = t, n) and x(k = t + 4, n), n = 8 jj + g
+    uint32_t xf[D::TPW][2];
+    auto prefetch_x = [&](const int* mp, int nbx) {
+#pragma unroll
+        for (int q = 0; q < D::TPW; ++q) {
+            const int task = warp + q * kTcWarps;
+            const int b = task / D::NTB, n = (task - b * D::NTB) * 8 + g;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = t + 4 * h;
+                float v = 0.f;
+                if (b < nbx && n < NT && k < NZ) {
+                    const int m = mp[b * Np + k * NT + n];
+                    if (m >= 0 && m < N) v = x[m];      // every node id of a valid map is < N
+                }
+                xf[q][h] = to_tf32(v);
+            }
+        }
+    };
+    // Each mbarrier carries one copy at a time, and it is re-armed only after a barrier that
+    // every thread reaches after its wait: a phase never completes twice before all threads
+    // have observed the first completion (parity waits would then misread it).
     if (tid == 0 && blockIdx.x * EB < E) {
         const int e = blockIdx.x * EB, nb0 = min(EB, E - e);
         bulk_copy(sMap0, map + (size_t)e * Np, (uint32_t)nb0 * Np * 4u, barm);
         bulk_copy(sG, G16 + (size_t)e * 6 * Nq, (uint32_t)nb0 * 6u * Nq * 2u, barg);
     }
-
-    for (int e0 = blockIdx.x * EB; e0 < E; e0 += gridDim.x * EB) {
-        const int nb = min(EB, E - e0);
-        const int* sMap = sMap0 + buf * D::MAP;
-        if (!mbar_wait(barm, pm)) s_fail = 1;
-        __syncthreads();
-        if (s_fail) break;          // uniform: every thread read s_fail after the barrier
+    if (blockIdx.x * EB < E) {
+        // a map that did not arrive is never read: its indices would be arbitrary
+        const bool ok = mbar_wait(barm, pm);
+        if (!ok) s_fail = 1;
         pm ^= 1u;
-        // the next pass's map into the other buffer (its last reader, the previous pass's
-        // summation, finished before the barrier that closed that pass)
-        if (tid == 0) {
-            const int en = e0 + gridDim.x * EB;
-            if (en < E)
-                bulk_copy(sMap0 + (buf ^ 1) * D::MAP, map + (size_t)en * Np, (uint32_t)min(EB, E - en) * Np * 4u, barm);
-        }
-        // gather and vertical stage: U(n, qz) = sum_k Bz[qz][k] x(k, n), W likewise with Dz
-        for (int i = tid; i < nb * NT; i += kTcThreads) {
-            const int b = i / NT, n = i - b * NT;
-            float xk[NZ];
+        prefetch_x(sMap0, ok ? min(EB, E - blockIdx.x * EB) : 0);
+    }
+    __syncthreads();
+    if (tid == 0 && !s_fail) {
+        const int e1 = blockIdx.x * EB + stride;
+        if (e1 < E) bulk_copy(sMap0 + D::MAP, map + (size_t)e1 * Np, (uint32_t)min(EB, E - e1) * Np * 4u, barm);
+    }
+
+    for (int e0 = blockIdx.x * EB; e0 < E; e0 += stride) {
+        const int nb = min(EB, E - e0);
+        const int en = e0 + stride;
+        const int* sMap = sMap0 + buf * D::MAP;
+        // vertical stage on the tensor cores from the prefetched x: [U; W](qz; n) =
+        // [Bz; Dz](qz; k) X(k; n)
 #pragma unroll
-            for (int k = 0; k < NZ; ++k) {
-                const int m = sMap[b * Np + k * NT + n];
-                xk[k] = (m >= 0) ? x[m] : 0.f;
-            }
-            float* U = work + b * D::WORK + n * 8;
+        for (int q = 0; q < D::TPW; ++q) {
+            const int task = warp + q * kTcWarps;
+            const int b = task / D::NTB, j = task - b * D::NTB;
+            if (b >= nb) continue;
+            float c[4] = {0.f, 0.f, 0.f, 0.f};
+            mma_tf32(c, av, xf[q][0], xf[q][1]);
+            float* U = work + b * D::WORK + g * D::LDU + j * 8 + 2 * t;
             float* W = U + D::UW;
-#pragma unroll
-            for (int qz = 0; qz < QZ; ++qz) {
-                float u = 0.f, w = 0.f;
-#pragma unroll
-                for (int k = 0; k < NZ; ++k) {
-                    u += sBz[qz * NZ + k] * xk[k];
-                    w += sDz[qz * NZ + k] * xk[k];
-                }
-                U[qz] = __uint_as_float(to_tf32(u));
-                W[qz] = __uint_as_float(to_tf32(w));
-            }
+            U[0] = __uint_as_float(to_tf32(c[0]));
+            U[1] = __uint_as_float(to_tf32(c[1]));
+            W[0] = __uint_as_float(to_tf32(c[2]));
+            W[1] = __uint_as_float(to_tf32(c[3]));
         }
         // this pass's geometric factors
         if (!mbar_wait(barg, pg)) s_fail = 1;
@@ -225,25 +274,20 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         // forward contractions and the geometric factors: warp task = (element pair, qt tile)
         for (int task = warp; task < D::NPAIR * D::NTF; task += kTcWarps) {
             const int pr = task / D::NTF, j = task - pr * D::NTF;
-            const float* U0 = work + (2 * pr) * D::WORK;
-            const float* U1 = U0 + D::WORK;
-            const float* W0 = U0 + D::UW;
-            const float* W1 = U1 + D::UW;
+            const float* Ua = work + (2 * pr + lsel) * D::WORK + lrow * D::LDU + lcolA;
             float cr[4] = {0.f, 0.f, 0.f, 0.f}, cs[4] = {0.f, 0.f, 0.f, 0.f}, ct[4] = {0.f, 0.f, 0.f, 0.f};
+            const float* Bb = sBF + (j * 8 + lrow) * D::LDF + lcolB;
 #pragma unroll
             for (int ks = 0; ks < D::KSF; ++ks) {
-                const int o0 = (ks * 8 + t) * 8 + g, o1 = o0 + 32;
-                const uint32_t au[4] = {__float_as_uint(U0[o0]), __float_as_uint(U1[o0]), __float_as_uint(U0[o1]),
-                                        __float_as_uint(U1[o1])};
-                const uint32_t aw[4] = {__float_as_uint(W0[o0]), __float_as_uint(W1[o0]), __float_as_uint(W0[o1]),
-                                        __float_as_uint(W1[o1])};
-                const int row = (j * 8 + g) * D::LDF + ks * 8 + t;
-                const float* B0 = sBF + row;
-                const float* B1 = B0 + D::NTF * 8 * D::LDF;
-                const float* B2 = B1 + D::NTF * 8 * D::LDF;
-                mma_tf32(cr, au, __float_as_uint(B0[0]), __float_as_uint(B0[4]));
-                mma_tf32(cs, au, __float_as_uint(B1[0]), __float_as_uint(B1[4]));
-                mma_tf32(ct, aw, __float_as_uint(B2[0]), __float_as_uint(B2[4]));
+                uint32_t au[4], aw[4], br0, br1, bs0, bs1, bt0, bt1;
+                ldsm_x4(smem_u32(Ua + ks * 8), au);
+                ldsm_x4(smem_u32(Ua + D::UW + ks * 8), aw);
+                ldsm_x2(smem_u32(Bb + ks * 8), br0, br1);
+                ldsm_x2(smem_u32(Bb + D::NTF * 8 * D::LDF + ks * 8), bs0, bs1);
+                ldsm_x2(smem_u32(Bb + 2 * D::NTF * 8 * D::LDF + ks * 8), bt0, bt1);
+                mma_tf32(cr, au, br0, br1);
+                mma_tf32(cs, au, bs0, bs1);
+                mma_tf32(ct, aw, bt0, bt1);
             }
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
@@ -260,74 +304,75 @@ __global__ void __launch_bounds__(kTcThreads, 2)
                     vs = g1 * cr[r] + g3 * cs[r] + g4 * ct[r];
                     vt = g2 * cr[r] + g4 * cs[r] + g5 * ct[r];
                 }
-                float* Vr = work + b * D::WORK + 2 * D::UW + qt * 8 + qz;
-                Vr[0] = __uint_as_float(to_tf32(vr));
-                Vr[D::VS] = __uint_as_float(to_tf32(vs));
-                Vr[2 * D::VS] = __uint_as_float(to_tf32(vt));
+                float* V = work + b * D::WORK + D::R1 + qz * D::LDV + qt;
+                V[0] = __uint_as_float(to_tf32(vr));
+                V[D::VS] = __uint_as_float(to_tf32(vs));
+                V[2 * D::VS] = __uint_as_float(to_tf32(vt));
             }
         }
         __syncthreads();
-        // the factors are consumed: stream in the next pass's while this one finishes
-        if (tid == 0) {
-            const int en = e0 + gridDim.x * EB;
-            if (en < E) bulk_copy(sG, G16 + (size_t)en * 6 * Nq, (uint32_t)min(EB, E - en) * 6u * Nq * 2u, barg);
+        // the factors are consumed: stream in the next pass's while this one finishes, and
+        // start the next pass's gather (its map arrived during this pass)
+        if (tid == 0 && en < E)
+            bulk_copy(sG, G16 + (size_t)en * 6 * Nq, (uint32_t)min(EB, E - en) * 6u * Nq * 2u, barg);
+        if (en < E) {
+            const bool ok = mbar_wait(barm, pm);
+            if (!ok) s_fail = 1;
+            pm ^= 1u;
+            prefetch_x(sMap0 + (buf ^ 1) * D::MAP, ok ? min(EB, E - en) : 0);
         }
-        // backward contractions: warp task = (element pair, node tile)
+        // backward contractions: warp task = (element pair, node tile); [Xr | Xt] over R1
         for (int task = warp; task < D::NPAIR * D::NTB; task += kTcWarps) {
             const int pr = task / D::NTB, j = task - pr * D::NTB;
-            const float* V0 = work + (2 * pr) * D::WORK + 2 * D::UW;
-            const float* V1 = V0 + D::WORK;
+            const float* Va = work + (2 * pr + lsel) * D::WORK + D::R1 + lrow * D::LDV + lcolA;
+            const float* Bb = sBB + (j * 8 + lrow) * D::LDB + lcolB;
             float xr[4] = {0.f, 0.f, 0.f, 0.f}, xt[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 1
-            for (int ks = 0; ks < D::KSB; ++ks) {
-                const int o0 = (ks * 8 + t) * 8 + g, o1 = o0 + 32;
-                const int row = (j * 8 + g) * D::LDB + ks * 8 + t;
-                const float* B0 = sBB + row;
-                const float* B1 = B0 + D::NTB * 8 * D::LDB;
-                const float* B2 = B1 + D::NTB * 8 * D::LDB;
 #pragma unroll
-                for (int m = 0; m < 3; ++m) {
-                    const float* A0 = V0 + m * D::VS;
-                    const float* A1 = V1 + m * D::VS;
-                    const uint32_t a[4] = {__float_as_uint(A0[o0]), __float_as_uint(A1[o0]), __float_as_uint(A0[o1]),
-                                           __float_as_uint(A1[o1])};
-                    const float* Bm = (m == 0) ? B0 : (m == 1 ? B1 : B2);
-                    if (m < 2) mma_tf32(xr, a, __float_as_uint(Bm[0]), __float_as_uint(Bm[4]));
-                    else mma_tf32(xt, a, __float_as_uint(Bm[0]), __float_as_uint(Bm[4]));
-                }
+            for (int ks = 0; ks < D::KSB; ++ks) {
+                uint32_t a0[4], a1[4], a2[4], b00, b01, b10, b11, b20, b21;
+                ldsm_x4(smem_u32(Va + ks * 8), a0);
+                ldsm_x4(smem_u32(Va + D::VS + ks * 8), a1);
+                ldsm_x4(smem_u32(Va + 2 * D::VS + ks * 8), a2);
+                ldsm_x2(smem_u32(Bb + ks * 8), b00, b01);
+                ldsm_x2(smem_u32(Bb + D::NTB * 8 * D::LDB + ks * 8), b10, b11);
+                ldsm_x2(smem_u32(Bb + 2 * D::NTB * 8 * D::LDB + ks * 8), b20, b21);
+                mma_tf32(xr, a0, b00, b01);
+                mma_tf32(xr, a1, b10, b11);
+                mma_tf32(xt, a2, b20, b21);
             }
+            __syncwarp();
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 const int b = 2 * pr + (r >> 1);
                 if (b >= nb) continue;
                 const int n = j * 8 + 2 * t + (r & 1);
-                float* X = work + b * D::WORK + n * 8 + g;     // Xr over U, Xt over W
-                X[0] = xr[r];
-                X[D::UW] = xt[r];
+                float* X = work + b * D::WORK + n * D::LDX + g;
+                X[0] = __uint_as_float(to_tf32(xr[r]));
+                X[8] = __uint_as_float(to_tf32(xt[r]));
             }
         }
         __syncthreads();
-        // transposed vertical stage and direct-stiffness summation
-        for (int i = tid; i < nb * NT; i += kTcThreads) {
-            const int b = i / NT, n = i - b * NT;
-            const float* Xr = work + b * D::WORK + n * 8;
-            const float* Xt = Xr + D::UW;
-            float xr[QZ], xt[QZ];
-#pragma unroll
-            for (int qz = 0; qz < QZ; ++qz) {
-                xr[qz] = Xr[qz];
-                xt[qz] = Xt[qz];
-            }
-#pragma unroll
-            for (int k = 0; k < NZ; ++k) {
-                float s = 0.f;
-#pragma unroll
-                for (int qz = 0; qz < QZ; ++qz) s += sBz[qz * NZ + k] * xr[qz] + sDz[qz * NZ + k] * xt[qz];
-                const int m = sMap[b * Np + k * NT + n];
-                if (m >= 0) atomicAdd(&y[m], s);
+        // transposed vertical stage on the tensor cores and direct-stiffness summation:
+        // y(k; n) = Bz^T(k; qz) Xr(qz; n) + Dz^T(k; qz) Xt(qz; n), rows k < NZ of the tile
+        for (int task = warp; task < nb * D::NTB; task += kTcWarps) {
+            const int b = task / D::NTB, j = task - b * D::NTB;
+            const float* X = work + b * D::WORK + (j * 8 + g) * D::LDX + t;
+            float c[4] = {0.f, 0.f, 0.f, 0.f};
+            mma_tf32(c, at0, __float_as_uint(X[0]), __float_as_uint(X[4]));
+            mma_tf32(c, at1, __float_as_uint(X[8]), __float_as_uint(X[12]));
+            const int k = g, n = j * 8 + 2 * t;
+            if (k < NZ) {
+                const int* mp = sMap + b * Np + k * NT;
+                if (n < NT && mp[n] >= 0 && mp[n] < N) atomicAdd(&y[mp[n]], c[0]);
+                if (n + 1 < NT && mp[n + 1] >= 0 && mp[n + 1] < N) atomicAdd(&y[mp[n + 1]], c[1]);
             }
         }
         __syncthreads();
+        if (s_fail) break;          // a map wait ran out (uniform after the barrier)
+        // the map two passes ahead into the buffer this pass has finished with
+        if (tid == 0 && en + stride < E)
+            bulk_copy(sMap0 + buf * D::MAP, map + (size_t)(en + stride) * Np,
+                      (uint32_t)min(EB, E - en - stride) * Np * 4u, barm);
         buf ^= 1;
     }
     if (s_fail) {
@@ -360,7 +405,7 @@ cudaError_t apply_tc_impl(const Level& L, const float* x, float* y, const int* s
     const int grid = passes < 2 * kTcSMs ? passes : 2 * kTcSMs;
     if (grid < 1) return cudaSuccess;
     k_apply_prism_tc<P><<<grid, kTcThreads, D::SMEM, s>>>(
-        L.E, L.map, reinterpret_cast<const __nv_bfloat16*>(L.G16), L.ref32.m, x, y, skip, err);
+        L.E, (int)L.N, L.map, reinterpret_cast<const __nv_bfloat16*>(L.G16), L.ref32.m, x, y, skip, err);
     return cudaGetLastError();
 }
 
