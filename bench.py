@@ -180,6 +180,31 @@ def run_ncu_case(a):
     s.close()
 
 
+def run_ncu_solve(a):
+    """Profiler driver: `steps` solves of one form on the benchmark workload, stats only."""
+    import torch
+    import paper_2009_00705_gb300 as sem
+    import workloads as W
+    from paper_2009_00705_gb300 import build as B
+    B.build()
+    P = a.P
+    mesh = W.config_box3d(a.n, a.nlayers)
+    xy = sem.sem_mesh_nodes2d(mesh, P)
+    opts = {"fp64": dict(),
+            "mixed_fp32": dict(precision="mixed_fp32", outer="pdc", inner_imax=a.inner_imax, inner_rtol=a.inner_rtol),
+            "mixed_tf32": dict(precision="mixed_tf32", outer="pdc", inner_imax=a.inner_imax, inner_rtol=a.inner_rtol)}
+    s = sem.Solver(mesh, P, eta_nodal=mesh.eta(xy[:, 0], xy[:, 1]), levels=levels_for(P), coarse_rtol=a.coarse_rtol,
+                   **opts[a.ncu_solve])
+    C = s.coords(0)
+    phiD = torch.tensor(W.potential3d(*C[s.dirichlet_nodes(0)].T), device="cuda")
+    phi = torch.empty(s.query(0)["ndof"], dtype=torch.float64, device="cuda")
+    for _ in range(a.steps):
+        st = s.solve(phiD, phi, tol=1e-8)
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_solve": a.ncu_solve, "stats": st}))
+    s.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -203,6 +228,8 @@ def main():
     ap.add_argument("--ncu-case", type=int, default=0, metavar="N",
                     help="profiler driver: one short MIXED_TF32 solve on an N x N x 4 P=6 box (FP64, FP32 and "
                          "tensor-core applies, transfers and the coarse CG all launch); prints stats only")
+    ap.add_argument("--ncu-solve", default="", choices=["", "fp64", "mixed_fp32", "mixed_tf32"],
+                    help="profiler driver: --steps solves of one form on the benchmark workload; prints stats only")
     a = ap.parse_args()
     if a.warmup < 3:
         a.warmup = 3
@@ -210,6 +237,8 @@ def main():
         return run_reference(a)
     if a.ncu_case:
         return run_ncu_case(a)
+    if a.ncu_solve:
+        return run_ncu_solve(a)
 
     # CPU baseline first: a separate process, before any GPU work in this one
     rank = int(os.environ.get("RANK", "0"))

@@ -55,12 +55,18 @@ struct TcTile {
     static constexpr int LDX = 20;                 // [Xr | Xt] as (n, 16): scalar fragment loads, 20/4 odd
     static constexpr int EB = tc_pass_elems(P);
     static constexpr int NPAIR = EB / 2;
+    static constexpr int NGF = (NTF + 1) / 2;      // forward warp tasks per pair (2 qt tiles each)
+    static constexpr int NGB = (NTB + 1) / 2;      // backward warp tasks per pair (2 node tiles each)
+    // BF16 factors as [6][QZ][QTP], rows padded to even length so a lane's two points
+    // (qt, qt + 1), qt even, are one aligned 32-bit word
+    static constexpr int QTP = (QT + 1) / 2 * 2;
+    static constexpr int GE = 6 * QZ * QTP;        // BF16 entries per element
     static_assert(EB % 2 == 0, "elements pair up into MMA rows");
     static_assert((EB * Np * 4) % 16 == 0, "map blocks of a pass start on 16-byte boundaries");
-    static_assert((EB * 6 * Nq * 2) % 16 == 0, "factor blocks of a pass start on 16-byte boundaries");
+    static_assert((EB * GE * 2) % 16 == 0, "factor blocks of a pass start on 16-byte boundaries");
     __host__ __device__ static constexpr int r4(int v) { return (v + 3) / 4 * 4; }
     // shared-memory regions in 4-byte words, each a multiple of 4 words (16 bytes)
-    static constexpr int GSZ = r4((EB * 6 * Nq + 1) / 2);     // BF16 factors of a pass
+    static constexpr int GSZ = r4((EB * GE + 1) / 2);         // BF16 factors of a pass
     static constexpr int BF = 3 * NTF * 8 * LDF;              // Dr, Ds, Bt as [qt][n]
     static constexpr int BB = 3 * NTB * 8 * LDB;              // Dr, Ds, Bt as [n][qt]
     static constexpr int MAP = r4(EB * Np);                    // one map buffer (ints)
@@ -152,7 +158,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
                      const float* __restrict__ refm, const float* __restrict__ x, float* __restrict__ y,
                      const int* __restrict__ skip, int* err) {
     using D = TcTile<P>;
-    constexpr int NT = D::NT, NZ = D::NZ, QT = D::QT, QZ = D::QZ, Np = D::Np, Nq = D::Nq, EB = D::EB;
+    constexpr int NT = D::NT, NZ = D::NZ, QT = D::QT, QZ = D::QZ, Np = D::Np, EB = D::EB;
     if (skip != nullptr && *skip) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long mbar[2];   // [0] geometric factors, [1] element map
@@ -231,7 +237,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     if (tid == 0 && blockIdx.x * EB < E) {
         const int e = blockIdx.x * EB, nb0 = min(EB, E - e);
         bulk_copy(sMap0, map + (size_t)e * Np, (uint32_t)nb0 * Np * 4u, barm);
-        bulk_copy(sG, G16 + (size_t)e * 6 * Nq, (uint32_t)nb0 * 6u * Nq * 2u, barg);
+        bulk_copy(sG, G16 + (size_t)e * D::GE, (uint32_t)nb0 * D::GE * 2u, barg);
     }
     if (blockIdx.x * EB < E) {
         // a map that did not arrive is never read: its indices would be arbitrary
@@ -271,84 +277,126 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         __syncthreads();
         if (s_fail) break;
         pg ^= 1u;
-        // forward contractions and the geometric factors: warp task = (element pair, qt tile)
-        for (int task = warp; task < D::NPAIR * D::NTF; task += kTcWarps) {
-            const int pr = task / D::NTF, j = task - pr * D::NTF;
+        // forward contractions and the geometric factors: warp task = (element pair, two qt
+        // tiles); each A fragment serves both tiles
+        for (int task = warp; task < D::NPAIR * D::NGF; task += kTcWarps) {
+            const int pr = task / D::NGF, j0 = 2 * (task - pr * D::NGF);
+            const bool two = j0 + 1 < D::NTF;
             const float* Ua = work + (2 * pr + lsel) * D::WORK + lrow * D::LDU + lcolA;
-            float cr[4] = {0.f, 0.f, 0.f, 0.f}, cs[4] = {0.f, 0.f, 0.f, 0.f}, ct[4] = {0.f, 0.f, 0.f, 0.f};
-            const float* Bb = sBF + (j * 8 + lrow) * D::LDF + lcolB;
+            float cr[2][4], cs[2][4], ct[2][4];
+#pragma unroll
+            for (int jj = 0; jj < 2; ++jj)
+#pragma unroll
+                for (int r = 0; r < 4; ++r) cr[jj][r] = cs[jj][r] = ct[jj][r] = 0.f;
 #pragma unroll
             for (int ks = 0; ks < D::KSF; ++ks) {
-                uint32_t au[4], aw[4], br0, br1, bs0, bs1, bt0, bt1;
+                uint32_t au[4], aw[4];
                 ldsm_x4(smem_u32(Ua + ks * 8), au);
                 ldsm_x4(smem_u32(Ua + D::UW + ks * 8), aw);
-                ldsm_x2(smem_u32(Bb + ks * 8), br0, br1);
-                ldsm_x2(smem_u32(Bb + D::NTF * 8 * D::LDF + ks * 8), bs0, bs1);
-                ldsm_x2(smem_u32(Bb + 2 * D::NTF * 8 * D::LDF + ks * 8), bt0, bt1);
-                mma_tf32(cr, au, br0, br1);
-                mma_tf32(cs, au, bs0, bs1);
-                mma_tf32(ct, aw, bt0, bt1);
-            }
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int b = 2 * pr + (r >> 1);
-                if (b >= nb) continue;
-                const int qz = g, qt = j * 8 + 2 * t + (r & 1);
-                float vr = 0.f, vs = 0.f, vt = 0.f;
-                if (qt < QT && qz < QZ) {
-                    const __nv_bfloat16* Gb = sG + (size_t)b * 6 * Nq + qz * QT + qt;
-                    const float g0 = __bfloat162float(Gb[0]), g1 = __bfloat162float(Gb[Nq]);
-                    const float g2 = __bfloat162float(Gb[2 * Nq]), g3 = __bfloat162float(Gb[3 * Nq]);
-                    const float g4 = __bfloat162float(Gb[4 * Nq]), g5 = __bfloat162float(Gb[5 * Nq]);
-                    vr = g0 * cr[r] + g1 * cs[r] + g2 * ct[r];
-                    vs = g1 * cr[r] + g3 * cs[r] + g4 * ct[r];
-                    vt = g2 * cr[r] + g4 * cs[r] + g5 * ct[r];
+                for (int jj = 0; jj < 2; ++jj) {
+                    if (jj == 1 && !two) break;
+                    const float* Bb = sBF + ((j0 + jj) * 8 + lrow) * D::LDF + lcolB + ks * 8;
+                    uint32_t br0, br1, bs0, bs1, bt0, bt1;
+                    ldsm_x2(smem_u32(Bb), br0, br1);
+                    ldsm_x2(smem_u32(Bb + D::NTF * 8 * D::LDF), bs0, bs1);
+                    ldsm_x2(smem_u32(Bb + 2 * D::NTF * 8 * D::LDF), bt0, bt1);
+                    mma_tf32(cr[jj], au, br0, br1);
+                    mma_tf32(cs[jj], au, bs0, bs1);
+                    mma_tf32(ct[jj], aw, bt0, bt1);
                 }
-                float* V = work + b * D::WORK + D::R1 + qz * D::LDV + qt;
-                V[0] = __uint_as_float(to_tf32(vr));
-                V[D::VS] = __uint_as_float(to_tf32(vs));
-                V[2 * D::VS] = __uint_as_float(to_tf32(vt));
+            }
+            // lane (g, t) holds points (qz = g, qt0 + h), qt0 = 8 (j0 + jj) + 2 t, of both
+            // elements of the pair: fragment entries 2 e + h
+#pragma unroll
+            for (int jj = 0; jj < 2; ++jj) {
+                if (jj == 1 && !two) break;
+                const int qz = g, qt0 = (j0 + jj) * 8 + 2 * t;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int b = 2 * pr + e;
+                    if (b >= nb) continue;
+                    float vr[2] = {0.f, 0.f}, vs[2] = {0.f, 0.f}, vt[2] = {0.f, 0.f};
+                    if (qz < QZ && qt0 < QT) {
+                        const __nv_bfloat162* Gp = reinterpret_cast<const __nv_bfloat162*>(
+                            sG + (size_t)b * D::GE + qz * D::QTP + qt0);
+                        constexpr int FS = QZ * D::QTP / 2;      // factor stride in BF16 pairs
+                        const float2 g0 = __bfloat1622float2(Gp[0]), g1 = __bfloat1622float2(Gp[FS]);
+                        const float2 g2 = __bfloat1622float2(Gp[2 * FS]), g3 = __bfloat1622float2(Gp[3 * FS]);
+                        const float2 g4 = __bfloat1622float2(Gp[4 * FS]), g5 = __bfloat1622float2(Gp[5 * FS]);
+                        const float gg[6][2] = {{g0.x, g0.y}, {g1.x, g1.y}, {g2.x, g2.y},
+                                                {g3.x, g3.y}, {g4.x, g4.y}, {g5.x, g5.y}};
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            if (qt0 + h >= QT) continue;
+                            const float ur = cr[jj][2 * e + h], us = cs[jj][2 * e + h], ut = ct[jj][2 * e + h];
+                            vr[h] = gg[0][h] * ur + gg[1][h] * us + gg[2][h] * ut;
+                            vs[h] = gg[1][h] * ur + gg[3][h] * us + gg[4][h] * ut;
+                            vt[h] = gg[2][h] * ur + gg[4][h] * us + gg[5][h] * ut;
+                        }
+                    }
+                    float* V = work + b * D::WORK + D::R1 + qz * D::LDV + qt0;
+                    *reinterpret_cast<float2*>(V) =
+                        make_float2(__uint_as_float(to_tf32(vr[0])), __uint_as_float(to_tf32(vr[1])));
+                    *reinterpret_cast<float2*>(V + D::VS) =
+                        make_float2(__uint_as_float(to_tf32(vs[0])), __uint_as_float(to_tf32(vs[1])));
+                    *reinterpret_cast<float2*>(V + 2 * D::VS) =
+                        make_float2(__uint_as_float(to_tf32(vt[0])), __uint_as_float(to_tf32(vt[1])));
+                }
             }
         }
         __syncthreads();
         // the factors are consumed: stream in the next pass's while this one finishes, and
         // start the next pass's gather (its map arrived during this pass)
         if (tid == 0 && en < E)
-            bulk_copy(sG, G16 + (size_t)en * 6 * Nq, (uint32_t)min(EB, E - en) * 6u * Nq * 2u, barg);
+            bulk_copy(sG, G16 + (size_t)en * D::GE, (uint32_t)min(EB, E - en) * D::GE * 2u, barg);
         if (en < E) {
             const bool ok = mbar_wait(barm, pm);
             if (!ok) s_fail = 1;
             pm ^= 1u;
             prefetch_x(sMap0 + (buf ^ 1) * D::MAP, ok ? min(EB, E - en) : 0);
         }
-        // backward contractions: warp task = (element pair, node tile); [Xr | Xt] over R1
-        for (int task = warp; task < D::NPAIR * D::NTB; task += kTcWarps) {
-            const int pr = task / D::NTB, j = task - pr * D::NTB;
+        // backward contractions: warp task = (element pair, two node tiles); [Xr | Xt] over R1
+        for (int task = warp; task < D::NPAIR * D::NGB; task += kTcWarps) {
+            const int pr = task / D::NGB, j0 = 2 * (task - pr * D::NGB);
+            const bool two = j0 + 1 < D::NTB;
             const float* Va = work + (2 * pr + lsel) * D::WORK + D::R1 + lrow * D::LDV + lcolA;
-            const float* Bb = sBB + (j * 8 + lrow) * D::LDB + lcolB;
-            float xr[4] = {0.f, 0.f, 0.f, 0.f}, xt[4] = {0.f, 0.f, 0.f, 0.f};
+            float xr[2][4], xt[2][4];
+#pragma unroll
+            for (int jj = 0; jj < 2; ++jj)
+#pragma unroll
+                for (int r = 0; r < 4; ++r) xr[jj][r] = xt[jj][r] = 0.f;
 #pragma unroll
             for (int ks = 0; ks < D::KSB; ++ks) {
-                uint32_t a0[4], a1[4], a2[4], b00, b01, b10, b11, b20, b21;
+                uint32_t a0[4], a1[4], a2[4];
                 ldsm_x4(smem_u32(Va + ks * 8), a0);
                 ldsm_x4(smem_u32(Va + D::VS + ks * 8), a1);
                 ldsm_x4(smem_u32(Va + 2 * D::VS + ks * 8), a2);
-                ldsm_x2(smem_u32(Bb + ks * 8), b00, b01);
-                ldsm_x2(smem_u32(Bb + D::NTB * 8 * D::LDB + ks * 8), b10, b11);
-                ldsm_x2(smem_u32(Bb + 2 * D::NTB * 8 * D::LDB + ks * 8), b20, b21);
-                mma_tf32(xr, a0, b00, b01);
-                mma_tf32(xr, a1, b10, b11);
-                mma_tf32(xt, a2, b20, b21);
-            }
-            __syncwarp();
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int b = 2 * pr + (r >> 1);
-                if (b >= nb) continue;
-                const int n = j * 8 + 2 * t + (r & 1);
-                float* X = work + b * D::WORK + n * D::LDX + g;
-                X[0] = __uint_as_float(to_tf32(xr[r]));
-                X[8] = __uint_as_float(to_tf32(xt[r]));
+                for (int jj = 0; jj < 2; ++jj) {
+                    if (jj == 1 && !two) break;
+                    const float* Bb = sBB + ((j0 + jj) * 8 + lrow) * D::LDB + lcolB + ks * 8;
+                    uint32_t b00, b01, b10, b11, b20, b21;
+                    ldsm_x2(smem_u32(Bb), b00, b01);
+                    ldsm_x2(smem_u32(Bb + D::NTB * 8 * D::LDB), b10, b11);
+                    ldsm_x2(smem_u32(Bb + 2 * D::NTB * 8 * D::LDB), b20, b21);
+                    mma_tf32(xr[jj], a0, b00, b01);
+                    mma_tf32(xr[jj], a1, b10, b11);
+                    mma_tf32(xt[jj], a2, b20, b21);
+                }
+            }
+#pragma unroll
+            for (int jj = 0; jj < 2; ++jj) {
+                if (jj == 1 && !two) break;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int b = 2 * pr + (r >> 1);
+                    if (b >= nb) continue;
+                    const int n = (j0 + jj) * 8 + 2 * t + (r & 1);
+                    float* X = work + b * D::WORK + n * D::LDX + g;
+                    X[0] = __uint_as_float(to_tf32(xr[jj][r]));
+                    X[8] = __uint_as_float(to_tf32(xt[jj][r]));
+                }
             }
         }
         __syncthreads();
@@ -409,10 +457,6 @@ cudaError_t apply_tc_impl(const Level& L, const float* x, float* y, const int* s
     return cudaGetLastError();
 }
 
-__global__ void k_to_bf16(long long n, const float* __restrict__ a, __nv_bfloat16* __restrict__ b) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        b[i] = __float2bfloat16_rn(a[i]);
-}
 
 }  // namespace
 
@@ -430,11 +474,24 @@ cudaError_t launch_apply_prism_tc(const Level& L, const float* x, float* y, cons
 
 bool prism_tc_supported(int p) { return p >= 2 && p <= 6; }
 
-// BF16 copy of a prism level's FP32 geometric factors for the tensor-core apply
-// (+32 entries of padding for its 16-byte-rounded bulk copies).
+// BF16 copy of a prism level's FP32 geometric factors for the tensor-core apply, as
+// [E][6][QZ][QTP] with QTP = QT rounded up to even (pads zero), plus 64 bytes of padding
+// for its 16-byte-rounded bulk copies.
+__global__ void k_to_bf16_padded(long long E, int QT, int QZ, int QTP, const float* __restrict__ a,
+                                 __nv_bfloat16* __restrict__ b) {
+    const long long per = 6LL * QZ * QTP, n = E * per;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long e = i / per;
+        const int r = (int)(i - e * per);
+        const int row = r / QTP, qt = r - row * QTP;       // row = f * QZ + qz
+        b[i] = qt < QT ? __float2bfloat16_rn(a[e * 6 * QZ * QT + (long long)row * QT + qt]) : __float2bfloat16_rn(0.f);
+    }
+}
+
 cudaError_t build_g16(Level& L, cudaStream_t s) {
     if (L.dim != 3 || !prism_tc_supported(L.p) || L.G32 == nullptr) return cudaSuccess;
-    const long long n = (long long)L.E * L.ncomp * L.Nq;
+    const int QTP = (L.QT + 1) / 2 * 2;
+    const long long n = (long long)L.E * 6 * L.QZ * QTP;
     void* p = nullptr;
     cudaError_t e = cudaMalloc(&p, sizeof(__nv_bfloat16) * (size_t)(n + 32));
     if (e != cudaSuccess) return e;
@@ -442,8 +499,8 @@ cudaError_t build_g16(Level& L, cudaStream_t s) {
     e = cudaMemsetAsync(p, 0, sizeof(__nv_bfloat16) * (size_t)(n + 32), s);
     if (e != cudaSuccess) return e;
     const long long blocks = (n + 255) / 256;
-    k_to_bf16<<<(int)(blocks < 4096 ? (blocks > 0 ? blocks : 1) : 4096), 256, 0, s>>>(
-        n, L.G32, static_cast<__nv_bfloat16*>(p));
+    k_to_bf16_padded<<<(int)(blocks < 4096 ? (blocks > 0 ? blocks : 1) : 4096), 256, 0, s>>>(
+        L.E, L.QT, L.QZ, QTP, L.G32, static_cast<__nv_bfloat16*>(p));
     return cudaGetLastError();
 }
 
