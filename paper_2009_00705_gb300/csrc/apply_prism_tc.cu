@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
                     const int m = mp[b * Np + k * NT + n];
                     if (m >= 0 && m < N) v = x[m];      // every node id of a valid map is < N
                 }
-                xf[q][h] = to_tf32(v);
+                xf[q][h] = __float_as_uint(v);        // raw bits: nothing waits on the load here
             }
         }
     };
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
             const int b = task / D::NTB, j = task - b * D::NTB;
             if (b >= nb) continue;
             float c[4] = {0.f, 0.f, 0.f, 0.f};
-            mma_tf32(c, av, xf[q][0], xf[q][1]);
+            mma_tf32(c, av, to_tf32(__uint_as_float(xf[q][0])), to_tf32(__uint_as_float(xf[q][1])));
             float* U = work + b * D::WORK + g * D::LDU + j * 8 + 2 * t;
             float* W = U + D::UW;
             U[0] = __uint_as_float(to_tf32(c[0]));
