@@ -64,7 +64,8 @@ __device__ __forceinline__ void load_row(const T* __restrict__ src, T (&out)[N])
 template <int P, typename T, bool LIFT, int V>
 __global__ void __launch_bounds__(PrismTile<P, T, V>::NTHR)
     k_apply_prism(int E, const int* __restrict__ map, const T* __restrict__ G, const T* __restrict__ refm,
-                  const T* __restrict__ x, T* __restrict__ y, const int* __restrict__ skip) {
+                  const T* __restrict__ x, T* __restrict__ y, const int* __restrict__ skip,
+                  const int* __restrict__ elist) {
     using D = PrismTile<P, T, V>;
     constexpr int NT = D::NT, NZ = D::NZ, QT = D::QT, QZ = D::QZ, Np = D::Np, Nq = D::Nq, QZP = D::QZP, EB = D::EB;
     if (skip != nullptr && *skip) return;
@@ -89,7 +90,7 @@ __global__ void __launch_bounds__(PrismTile<P, T, V>::NTHR)
         const int nb = min(EB, E - e0);
         {   // pull the next pass's geometric factors and map into L2 while this pass computes
             const int en = e0 + gridDim.x * EB;
-            if (en < E) {
+            if (en < E && elist == nullptr) {
                 const int nn = min(EB, E - en);
                 const char* g0 = reinterpret_cast<const char*>(G + (size_t)en * 6 * Nq);
                 const size_t gbytes = (size_t)nn * 6 * Nq * sizeof(T);
@@ -103,7 +104,8 @@ __global__ void __launch_bounds__(PrismTile<P, T, V>::NTHR)
         // gather
         for (int i = threadIdx.x; i < nb * Np; i += blockDim.x) {
             const int b = i / Np, l = i - b * Np;
-            const int m = map[(size_t)(e0 + b) * Np + l];
+            const int e = elist ? elist[e0 + b] : e0 + b;
+            const int m = map[(size_t)e * Np + l];
             work[b * D::WORK + l] = (m >= 0) ? x[m] : (LIFT ? x[-m - 1] : T(0));
         }
         __syncthreads();
@@ -160,7 +162,7 @@ __global__ void __launch_bounds__(PrismTile<P, T, V>::NTHR)
                     ut[qz] += bt * wv[qz];
                 }
             }
-            const T* Ge = G + (size_t)(e0 + b) * 6 * Nq;
+            const T* Ge = G + (size_t)(elist ? elist[e0 + b] : e0 + b) * 6 * Nq;
             T* vr = wb + D::round4(Np) + 2 * D::round4(NT * QZP) + qt * QZP;
             T* vs = vr + D::round4(QT * QZP);
             T* vt = vs + D::round4(QT * QZP);
@@ -198,7 +200,7 @@ __global__ void __launch_bounds__(PrismTile<P, T, V>::NTHR)
                     xt[qz] += bt * d[qz];
                 }
             }
-            const int* me = map + (size_t)(e0 + b) * Np;
+            const int* me = map + (size_t)(elist ? elist[e0 + b] : e0 + b) * Np;
 #pragma unroll
             for (int k = 0; k < NZ; ++k) {
                 T s = 0;
@@ -225,11 +227,16 @@ cudaError_t apply_prism_impl(const Level& L, const T* refm, const T* G, const T*
         if (err != cudaSuccess) return err;
         if (per_sm < 1) per_sm = 1;
     }
-    const int batches = (L.E + D::EB - 1) / D::EB;
+    // the lifting apply (x zero on the free nodes) only needs the elements that touch a
+    // Dirichlet node: every other element gathers zeros
+    const bool sub = LIFT && L.lift_elems != nullptr;
+    const int E = sub ? L.nlift : L.E;
+    const int batches = (E + D::EB - 1) / D::EB;
     int grid = kSMs * per_sm;
     if (grid > batches) grid = batches;
     if (grid < 1) return cudaSuccess;
-    k_apply_prism<P, T, LIFT, V><<<grid, D::NTHR, D::SMEM, s>>>(L.E, L.map, G, refm, x, y, skip);
+    k_apply_prism<P, T, LIFT, V><<<grid, D::NTHR, D::SMEM, s>>>(E, L.map, G, refm, x, y, skip,
+                                                                sub ? L.lift_elems : nullptr);
     return cudaGetLastError();
 }
 

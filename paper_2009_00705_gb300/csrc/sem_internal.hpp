@@ -39,6 +39,8 @@ struct Level {
     double* G = nullptr;                   // [E][ncomp][Nq]
     float* G32 = nullptr;
     unsigned short* G16 = nullptr;         // BF16 copy of G32 for the tensor-core apply (prisms, p >= 2)
+    int* lift_elems = nullptr;             // finest prism level: elements with a Dirichlet node (lifting apply)
+    int nlift = 0;
     double* dinv = nullptr;                // 1/diag on free nodes, 0 on Dirichlet
     float* dinv32 = nullptr;
     long long* dir = nullptr;              // Dirichlet node ids

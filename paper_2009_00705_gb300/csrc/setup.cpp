@@ -203,6 +203,14 @@ sem_status build_level(sem_handle* h, const sem_mesh* m, int li, int p) {
         padded.resize(L.hmap.size() + 16, 0);
         CK(upload(&L.map, padded));
     }
+    if (li == 0 && L.dim == 3) {   // elements that touch a Dirichlet node (the lifting apply's)
+        std::vector<int> le;
+        for (int e = 0; e < L.E; ++e)
+            for (int l = 0; l < L.Np; ++l)
+                if (L.hmap[(size_t)e * L.Np + l] < 0) { le.push_back(e); break; }
+        L.nlift = (int)le.size();
+        if (!le.empty()) CK(upload(&L.lift_elems, le));
+    }
     CK(upload(&L.owner, owner));
     CK(upload(&L.wmult, wm));
     CK(upload(&L.wmult32, to_float(wm)));
