@@ -122,6 +122,9 @@ typedef struct {
     int autotune;               /* 1 (default): time the prism apply's tile shapes (elements per CTA pass)
                                    on every level at setup and keep the faster (cached per order,
                                    precision and element-count bucket for the process) */
+    double learned_tau;         /* the learned sweep's correction (minimal-residual step) is kept when it
+                                   brings ||r|| below learned_tau * ||r|| (default 0.5); after three
+                                   rejections and no acceptance a solve continues without it */
     int batch_mode;             /* laplace_solve_batch with this handle first in the list: 0 (default)
                                    the whole batch as one CUDA graph launch with the convergence test
                                    on the device, 1 host-stepped lockstep */

@@ -45,7 +45,7 @@ class SemOptions(Structure):
                 ("gmres_m", c_int), ("coarse_rtol", c_double), ("coarse_imax", c_int), ("profile", c_int),
                 ("inner_imax", c_int), ("inner_rtol", c_double), ("debug_barrier_extra", c_int),
                 ("smoother", c_int), ("mlp_hidden", c_int), ("mlp_seed", ctypes.c_ulonglong), ("batch", c_int),
-                ("autotune", c_int), ("batch_mode", c_int)]
+                ("autotune", c_int), ("learned_tau", c_double), ("batch_mode", c_int)]
 
 
 class SemStats(Structure):

@@ -211,17 +211,22 @@ __global__ void k_mul32(long long n, const float* __restrict__ a, const float* _
 }
 
 // accept = (rr_new < rr_old) for the learned sweep; counts accepts and fallbacks.
-__global__ void k_judge(const double* rr_old, const double* rr_new, int* flags, int accept_idx, int count_idx) {
-    const int acc = (*rr_new < *rr_old) ? 1 : 0;
+__global__ void k_judge_mr(const double* rr, const double* rq, const double* qq, double* alpha, int* flags,
+                           int accept_idx, int count_idx, double tau2) {
+    const double a = (*qq > 0.0) ? *rq / *qq : 0.0;
+    const double after = *rr - a * *rq;            // ||r - a q||^2 at the minimising a
+    const int acc = (a > 0.0 && isfinite(a) && after < tau2 * *rr) ? 1 : 0;
+    *alpha = acc ? a : 0.0;
     flags[accept_idx] = acc;
     flags[count_idx + (acc ? 0 : 1)] += 1;
 }
 
-// dst = src where flags[idx] is set
-__global__ void k_commit32(long long n, const int* flags, int idx, const float* __restrict__ src, float* __restrict__ dst) {
+__global__ void k_axpy_accepted32(long long n, const int* flags, int idx, const double* alpha,
+                                  const float* __restrict__ delta, float* __restrict__ u) {
     if (!flags[idx]) return;
+    const float a = (float)*alpha;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        dst[i] = src[i];
+        u[i] += a * delta[i];
 }
 
 // SplitMix64 (Steele, Lea & Flood 2014) of (seed, counter) mapped to a uniform in [-1, 1)
@@ -250,13 +255,14 @@ cudaError_t mul32(long long n, const float* a, const float* b, float* out, cudaS
     k_mul32<<<vgrid(n), 256, 0, s>>>(n, a, b, out);
     return cudaGetLastError();
 }
-cudaError_t judge(const double* rr_old, const double* rr_new, int* flags, int accept_idx, int count_idx,
-                  cudaStream_t s) {
-    k_judge<<<1, 1, 0, s>>>(rr_old, rr_new, flags, accept_idx, count_idx);
+cudaError_t judge_min_residual(const double* rr, const double* rq, const double* qq, double* alpha, int* flags,
+                               int accept_idx, int count_idx, double tau2, cudaStream_t s) {
+    k_judge_mr<<<1, 1, 0, s>>>(rr, rq, qq, alpha, flags, accept_idx, count_idx, tau2);
     return cudaGetLastError();
 }
-cudaError_t commit32(long long n, const int* flags, int idx, const float* src, float* dst, cudaStream_t s) {
-    k_commit32<<<vgrid(n), 256, 0, s>>>(n, flags, idx, src, dst);
+cudaError_t axpy_accepted32(long long n, const int* flags, int idx, const double* alpha, const float* delta, float* u,
+                            cudaStream_t s) {
+    k_axpy_accepted32<<<vgrid(n), 256, 0, s>>>(n, flags, idx, alpha, delta, u);
     return cudaGetLastError();
 }
 cudaError_t random_free(long long n, unsigned long long seed, const float* dinv, float* v, cudaStream_t s) {

@@ -38,9 +38,14 @@ cudaError_t scatter_correction(int E, int Np, const int* map, const float* w, co
                                float* d, cudaStream_t s);
 cudaError_t mul32(long long n, const float* a, const float* b, float* out, cudaStream_t s);
 cudaError_t axpby32(long long n, const float* a, const float* b, float sign, float* out, cudaStream_t s);
-cudaError_t judge(const double* rr_old, const double* rr_new, int* flags, int accept_idx, int count_idx,
-                  cudaStream_t s);
-cudaError_t commit32(long long n, const int* flags, int idx, const float* src, float* dst, cudaStream_t s);
+// Minimal-residual verdict on a correction delta with q = A delta: alpha = (r, q) / (q, q);
+// accepted (flags[accept_idx] = 1, *alpha kept) when alpha > 0 and the residual after the
+// step, rr - alpha (r, q), is below tau2 * rr; counts accepts / fallbacks at count_idx.
+cudaError_t judge_min_residual(const double* rr, const double* rq, const double* qq, double* alpha, int* flags,
+                               int accept_idx, int count_idx, double tau2, cudaStream_t s);
+// u += alpha * delta when flags[idx] is set
+cudaError_t axpy_accepted32(long long n, const int* flags, int idx, const double* alpha, const float* delta, float* u,
+                            cudaStream_t s);
 cudaError_t random_free(long long n, unsigned long long seed, const float* dinv, float* v, cudaStream_t s);
 
 }  // namespace sem

@@ -245,7 +245,7 @@ cudaError_t coarse_cg_persistent(const Level& C, const int* rowptr, const int* c
 enum {
     S_RR = 0, S_PQ = 1, S_DELTA0 = 2, S_DELTA1 = 3, S_FF = 4, S_TMP = 5,
     S_CG_RHO = 8, S_CG_PQ = 9, S_CG_RR = 10, S_CG_TOL2 = 11, S_CG_RHONEW = 12, S_CG_BETA = 13,
-    S_IRR = 6, S_IPQ = 7, S_IDELTA0 = 14, S_IDELTA1 = 15, S_L0 = 100, S_L1 = 101, S_LOSS = 102,
+    S_IRR = 6, S_IPQ = 7, S_IDELTA0 = 14, S_IDELTA1 = 15, S_L0 = 100, S_L1 = 101, S_LOSS = 102, S_RQ = 103, S_QQ = 104, S_ALPHA = 105,
     S_MULTI = 16                    // FGMRES dots start here (up to 64 + 1)
 };
 enum { F_CG_DONE = 0, F_CG_ITERS = 1, F_LEARN_ACCEPT = 2, F_LEARN_COUNT = 3 /* +0 accepts, +1 fallbacks */,

@@ -244,29 +244,32 @@ sem_status smooth<float>(sem_handle* h, int li, const float* f, float* u, bool z
     return SEM_OK;
 }
 
-// The learned sweep that stands in for the first finest-level post-smoothing sweep:
-// u_try = u + W sum_e Q_e^T s_e MLP(z_e / s_e), z = D^{-1}(f - A u), s_e = ||z_e||.
-// It is kept only if it lowers the residual norm; otherwise the Chebyshev sweep it
-// replaces runs instead (its kernels are predicated on the device-side verdict).
+// The learned sweep that stands in for the first finest-level post-smoothing sweep: the
+// network's correction delta = W sum_e Q_e^T s_e MLP(z_e / s_e), z = D^{-1}(f - A u),
+// s_e = ||z_e||, taken with the minimal-residual step alpha = (r, A delta) / ||A delta||^2
+// (the alpha minimising ||r - alpha A delta||, one apply as before).  It is kept only if it
+// lowers the residual norm below learned_tau times its value; otherwise the Chebyshev sweep
+// it replaces runs instead (its kernels are predicated on the device-side verdict).
 sem_status learned_sweep(sem_handle* h, const float* f, float* u, cudaStream_t s) {
     Level& L = h->lv[0];
     const long long N = L.N;
     Scratch& sc = h->sc;
     CKST(apply_level32(h, 0, u, L.y32, s));
-    K(axpby32(N, f, L.y32, -1.f, h->lr32, s));
+    K(axpby32(N, f, L.y32, -1.f, h->lr32, s));                     // r = f - A u
     K(dot32(N, h->lr32, h->lr32, sc, sc.scal + S_L0, s));
     K(mul32(N, L.dinv32, h->lr32, h->ld32, s));
     K(gather_scaled<float>(L.E, L.Np, L.map, h->ld32, (const float*)nullptr, h->mX, nullptr, h->mscale, s));
     CKS(mlp_forward(h->net, L.E, h->mX, h->mA1, h->mH1, h->mY, s));
     h->launches += 2;
     CKS(cudaMemsetAsync(h->ld32, 0, sizeof(float) * N, s));
-    K(scatter_correction(L.E, L.Np, L.map, L.wmult32, h->mY, h->mscale, h->ld32, s));
-    K(axpby32(N, u, h->ld32, 1.f, h->lu32, s));
-    CKST(apply_level32(h, 0, h->lu32, L.y32, s));
-    K(axpby32(N, f, L.y32, -1.f, h->lr32, s));
-    K(dot32(N, h->lr32, h->lr32, sc, sc.scal + S_L1, s));
-    K(judge(sc.scal + S_L0, sc.scal + S_L1, sc.flags, F_LEARN_ACCEPT, F_LEARN_COUNT, s));
-    K(commit32(N, sc.flags, F_LEARN_ACCEPT, h->lu32, u, s));
+    K(scatter_correction(L.E, L.Np, L.map, L.wmult32, h->mY, h->mscale, h->ld32, s));   // delta
+    CKST(apply_level32(h, 0, h->ld32, L.y32, s));                  // q = A delta
+    K(dot32(N, h->lr32, L.y32, sc, sc.scal + S_RQ, s));
+    K(dot32(N, L.y32, L.y32, sc, sc.scal + S_QQ, s));
+    const double tau = h->opts.learned_tau;
+    K(judge_min_residual(sc.scal + S_L0, sc.scal + S_RQ, sc.scal + S_QQ, sc.scal + S_ALPHA, sc.flags, F_LEARN_ACCEPT,
+                         F_LEARN_COUNT, tau * tau, s));
+    K(axpy_accepted32(N, sc.flags, F_LEARN_ACCEPT, sc.scal + S_ALPHA, h->ld32, u, s));
     return smooth<float>(h, 0, f, u, false, s, sc.flags + F_LEARN_ACCEPT);
 }
 
@@ -573,6 +576,7 @@ sem_status check_options(const sem_options& o, int P) {
     if (o.outer == SEM_OUTER_FGMRES && (o.gmres_m < 1 || o.gmres_m > 64)) { set_error("gmres_m in 1..64"); return SEM_EINVAL; }
     if (o.imax < 0 || o.coarse_imax < 1 || !(o.coarse_rtol > 0)) { set_error("iteration limits"); return SEM_EINVAL; }
     if (o.batch_mode < 0 || o.batch_mode > 1) { set_error("batch_mode 0 or 1"); return SEM_EINVAL; }
+    if (!(o.learned_tau > 0.0 && o.learned_tau <= 1.0)) { set_error("0 < learned_tau <= 1"); return SEM_EINVAL; }
     if (o.smoother != SEM_SMOOTH_CHEBYSHEV && o.smoother != SEM_SMOOTH_LEARNED) { set_error("smoother"); return SEM_EINVAL; }
     if (o.smoother == SEM_SMOOTH_LEARNED && (o.precision == SEM_PREC_FP64 || o.mlp_hidden < 1 || o.mlp_hidden > 4096)) {
         set_error("the learned smoother needs a mixed precision and 1 <= mlp_hidden <= 4096");
@@ -643,6 +647,18 @@ sem_status outer_pcg(sem_handle* h, double* u, double tol, sem_stats* st, cudaSt
     return ret;
 }
 
+// The learned sweep's verdict counts travel with the outer iteration's scalar read: once a
+// solve has rejected the network three times without accepting it once, the rest of the
+// solve runs the plain V-cycle (the sweep would only add its cost).
+static void learned_queue_counts(sem_handle* h, cudaStream_t s) {
+    if (h->opts.smoother == SEM_SMOOTH_LEARNED && h->learned_active)
+        cudaMemcpyAsync(h->sc.hflags + 5, h->sc.flags + F_LEARN_COUNT, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+}
+static void learned_review(sem_handle* h) {
+    if (h->opts.smoother == SEM_SMOOTH_LEARNED && h->learned_active && h->sc.hflags[5] == 0 && h->sc.hflags[6] >= 3)
+        h->learned_active = false;
+}
+
 sem_status outer_pdc(sem_handle* h, double* u, double tol, sem_stats* st, cudaStream_t s) {
     const long long N = h->lv[0].N;
     Scratch& sc = h->sc;
@@ -658,7 +674,9 @@ sem_status outer_pdc(sem_handle* h, double* u, double tol, sem_stats* st, cudaSt
         CKST(apply_level64(h, 0, u, h->q, false, s));
         K(residual64(N, h->fr, h->q, h->r, sc, sc.scal + S_RR, s));
         ++i;
+        learned_queue_counts(h, s);
         CKST(read_scalars(h, S_RR, 1, s));
+        learned_review(h);
         rn = std::sqrt(sc.hpinned[S_RR]);
         CKST(fail_nan(rn));
     }
@@ -786,6 +804,7 @@ void sem_default_options(sem_options* o, int P) {
     o->batch = 0;
     o->autotune = 1;
     o->batch_mode = 0;
+    o->learned_tau = 0.5;
 }
 
 sem_status sem_mesh_nodes2d(const sem_mesh* m, int p, long long* n2, double* xy) {
@@ -1034,6 +1053,8 @@ sem_status laplace_solve(sem_handle* h, const double* rhs, const double* eta, do
     h->launches = 0;
     h->inner_iters = 0;
     CKS(cudaMemsetAsync(h->sc.flags + F_LEARN_COUNT, 0, 2 * sizeof(int), s));
+    h->sc.hflags[5] = h->sc.hflags[6] = 0;
+    h->learned_active = true;
     h->ev_used = 0;
     cudaEvent_t e0, e1;
     CKS(cudaEventCreate(&e0));

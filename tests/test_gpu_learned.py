@@ -101,7 +101,13 @@ def test_training_and_what_the_network_gains(sem):
     ref = S.solve_laplace_direct(prob, phiD)
     err = np.abs(phi.cpu().numpy() - ref).max() / np.abs(ref).max()
     assert st_l["status"] == 0 and err < 1e-8
-    assert st_l["learned_accepts"] + st_l["learned_fallbacks"] == st_l["vcycles"]
+    # every V-cycle judges the network's sweep until a solve has rejected it three times
+    # without accepting it once; then the rest of the solve runs the plain cycle
+    acc, fb = st_l["learned_accepts"], st_l["learned_fallbacks"]
+    if acc == 0:
+        assert fb == min(3, st_l["vcycles"]), st_l
+    else:
+        assert acc + fb == st_l["vcycles"], st_l
     _, plain = _solver(sem, mesh, levels, smoother="chebyshev", imax=300)
     plain.solve(dD, phi, tol=1e-10)
     torch.cuda.synchronize()
