@@ -361,8 +361,8 @@ def main():
             ms_m, st_m = timed(ms_solver, a.steps, a.warmup, phi_m)
             ms_m = max_over_ranks(ms_m)
             err = float(np.abs(phi_m.cpu().numpy() - phi64).max() / np.abs(phi64).max())
-            smooth = ("TF32 tensor-core apply (mma.sync m16n8k8, FP32 accumulation) in the Chebyshev sweeps of "
-                      "the P and intermediate levels, FP32 apply elsewhere" if prec == "mixed_tf32"
+            smooth = ("TF32 tensor-core apply (mma.sync m16n8k8, FP32 accumulation, BF16 factors) in the Chebyshev sweeps and residuals of "
+                      "the V-cycle on the P and intermediate levels; FP32 apply in the inner PCG" if prec == "mixed_tf32"
                       else "FP32 SIMT apply throughout")
             obj = {"value": dof * a.steps * world / (ms_m / 1000.0), "unit": UNIT,
                    "ms_per_step": ms_m / a.steps, "outer_iters": st_m[-1]["iters"],

@@ -52,8 +52,10 @@ typedef enum {
 
 typedef enum { SEM_OUTER_PCG = 0, SEM_OUTER_FGMRES = 1, SEM_OUTER_PDC = 2 } sem_outer;
 /* MIXED_FP32: FP32 V-cycle (and optional FP32 inner PCG) inside an FP64 outer iteration with
- * FP64 residual and FP64 coarse solve.  MIXED_TF32: the same, with the Chebyshev sweeps of
- * prism levels of order 2..6 on the tensor cores (TF32 operands, FP32 accumulation). */
+ * FP64 residual and FP64 coarse solve.  MIXED_TF32: the same, with the V-cycle's operator on
+ * prism levels of order 2..6 (Chebyshev sweeps and the residual before restriction) on the
+ * tensor cores (TF32 operands, BF16 geometric factors, FP32 accumulation); the inner PCG's
+ * products stay FP32. */
 typedef enum { SEM_PREC_FP64 = 0, SEM_PREC_MIXED_FP32 = 1, SEM_PREC_MIXED_TF32 = 2 } sem_precision;
 typedef enum { SEM_SMOOTH_CHEBYSHEV = 0, SEM_SMOOTH_LEARNED = 1 } sem_smoother;
 

@@ -759,10 +759,13 @@ __global__ void k_coarse_assemble(int E, int dim, int Np, int Nq, const double* 
     }
 }
 
-// Whole CG on the assembled coarse matrix; three grid barriers per iteration
-// (after the SpMV with p^T q, after the update with r^T z and r^T r, after the
-// new direction).  Values written by other CTAs (p in the SpMV) are read
-// through L2 (__ldcg).
+// Whole CG on the assembled coarse matrix; two grid barriers per iteration.  The search
+// direction lives in two buffers that alternate: while forming q = A p the lane group that
+// owns a row writes p_new(row) = z(row) + beta p_old(row), and every gathered entry of p
+// is formed on the fly from z(c) = dinv(c) r(c) and p_old(c), so no barrier is needed
+// between the direction update and the product.  The caller's z buffer is the second
+// direction buffer (z itself is never stored).  Values written by other CTAs (r, p) are
+// read through L2 (__ldcg).
 __global__ void __launch_bounds__(512) k_coarse_cg(long long n, const int* __restrict__ rowptr,
                                                    const int* __restrict__ col, const double* __restrict__ vals,
                                                    const double* __restrict__ dinv, const double* __restrict__ b,
@@ -773,14 +776,15 @@ __global__ void __launch_bounds__(512) k_coarse_cg(long long n, const int* __res
     const unsigned expected = nb + extra_arrivals;   // extra_arrivals > 0 only in the timeout test
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long stride = (long long)gridDim.x * blockDim.x;
+    double* p_old = p;        // direction of the previous iteration (zero before the first)
+    double* p_new = z;
     double s0 = 0, s1 = 0;
     for (long long i = tid; i < n; i += stride) {
-        const double bi = b[i], zi = dinv[i] * bi;
+        const double bi = b[i];
         x[i] = 0;
         r[i] = bi;
-        z[i] = zi;
-        p[i] = zi;
-        s0 += bi * zi;
+        p_old[i] = 0;
+        s0 += bi * dinv[i] * bi;
         s1 += bi * bi;
     }
     s0 = block_sum(s0);
@@ -792,10 +796,12 @@ __global__ void __launch_bounds__(512) k_coarse_cg(long long n, const int* __res
     const double tol2 = rtol2 * bb;
     int it = 0;
     double rr = bb;
+    double beta = 0.0;
+    __shared__ double s_alpha, s_beta;
     while (rr > tol2 && rr > 0.0 && it < imax) {
-        // SpMV q = A p with 4 lanes per row; lane 0 of the group owns q[row] and p^T q.
-        // The loop runs over warp-uniform groups of 8 rows (all 32 lanes reach the
-        // shuffles); lanes past the last row contribute zero.
+        // q = A p with 4 lanes per row; lane 0 of the group owns q[row], p_new[row] and the
+        // row's share of p^T q.  The loop runs over warp-uniform groups of 8 rows (all 32
+        // lanes reach the shuffles); lanes past the last row contribute zero.
         double pq = 0;
         const int l4 = threadIdx.x & 3;
         const long long rstride = stride >> 2;                  // multiple of 8 (blockDim % 32 == 0)
@@ -815,7 +821,8 @@ __global__ void __launch_bounds__(512) k_coarse_cg(long long n, const int* __res
                         a[u] = (kk < k1) ? vals[kk] : 0.0;
                     }
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) pv[u] = c[u] >= 0 ? __ldcg(p + c[u]) : 0.0;
+                    for (int u = 0; u < 8; ++u)
+                        pv[u] = c[u] >= 0 ? dinv[c[u]] * __ldcg(r + c[u]) + beta * __ldcg(p_old + c[u]) : 0.0;
 #pragma unroll
                     for (int u = 0; u < 8; ++u) v += a[u] * pv[u];
                 }
@@ -823,14 +830,15 @@ __global__ void __launch_bounds__(512) k_coarse_cg(long long n, const int* __res
             v += __shfl_down_sync(0xffffffffu, v, 2, 4);
             v += __shfl_down_sync(0xffffffffu, v, 1, 4);
             if (active && l4 == 0) {
+                const double pn = dinv[row] * __ldcg(r + row) + beta * __ldcg(p_old + row);
+                p_new[row] = pn;
                 q[row] = v;
-                pq += __ldcg(p + row) * v;
+                pq += pn * v;
             }
         }
         pq = block_sum(pq);
         if (threadIdx.x == 0) part[2 * nb + blockIdx.x] = pq;
         if (!grid_barrier(bar, expected)) return;
-        __shared__ double s_alpha, s_beta;
         {
             const double pq_all = grid_total(part + 2 * nb);
             if (threadIdx.x == 0) s_alpha = rho / pq_all;
@@ -839,12 +847,10 @@ __global__ void __launch_bounds__(512) k_coarse_cg(long long n, const int* __res
         const double alpha = s_alpha;
         double t0 = 0, t1 = 0;
         for (long long i = tid; i < n; i += stride) {
-            x[i] += alpha * p[i];
-            const double ri = r[i] - alpha * __ldcg(q + i);   // q[i] was written by another lane group
+            x[i] += alpha * __ldcg(p_new + i);                // p_new[i], q[i] written by another lane group
+            const double ri = r[i] - alpha * __ldcg(q + i);
             r[i] = ri;
-            const double zi = dinv[i] * ri;
-            z[i] = zi;
-            t0 += ri * zi;
+            t0 += ri * dinv[i] * ri;
             t1 += ri * ri;
         }
         t0 = block_sum(t0);
@@ -855,12 +861,12 @@ __global__ void __launch_bounds__(512) k_coarse_cg(long long n, const int* __res
         rr = grid_total(part + nb);
         if (threadIdx.x == 0) s_beta = rho_new / rho;
         __syncthreads();
-        const double beta = s_beta;
+        beta = s_beta;
         rho = rho_new;
         ++it;
-        if (rr <= tol2) break;
-        for (long long i = tid; i < n; i += stride) p[i] = z[i] + beta * p[i];
-        if (!grid_barrier(bar, expected)) return;
+        double* t = p_old;
+        p_old = p_new;
+        p_new = t;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         flags[F_CG_ITERS] = it;

@@ -212,9 +212,10 @@ sem_status smooth<double>(sem_handle* h, int li, const double* f, double* u, boo
     return SEM_OK;
 }
 
-// The operator of an FP32 Chebyshev sweep: the TF32 tensor-core prism apply in MIXED_TF32
-// (orders 2..6), the FP32 apply otherwise.
-static sem_status apply_smooth32(sem_handle* h, int li, const float* x, float* y, cudaStream_t s, const int* skip) {
+// The operator inside the single-precision V-cycle (Chebyshev sweeps and the residual
+// before restriction): the TF32 tensor-core prism apply in MIXED_TF32 (orders 2..6), the
+// FP32 apply otherwise.  The inner PCG's own products keep the FP32 apply.
+static sem_status apply_vcycle32(sem_handle* h, int li, const float* x, float* y, cudaStream_t s, const int* skip) {
     const Level& L = h->lv[li];
     if (h->opts.precision != SEM_PREC_MIXED_TF32 || L.dim != 3 || !prism_tc_supported(L.p))
         return apply_level32(h, li, x, y, s, skip);
@@ -234,11 +235,11 @@ sem_status smooth<float>(sem_handle* h, int li, const float* f, float* u, bool z
     if (zero_init) {
         K(cheb_first<float>(L.N, (float)c.c0, L.dinv32, f, u, L.d32, s, skip));
     } else {
-        CKST(apply_smooth32(h, li, u, L.y32, s, skip));
+        CKST(apply_vcycle32(h, li, u, L.y32, s, skip));
         K(cheb_restart<float>(L.N, (float)c.c0, L.dinv32, f, L.y32, u, L.d32, s, skip));
     }
     for (int j = 1; j < h->opts.k_cheb; ++j) {
-        CKST(apply_smooth32(h, li, u, L.y32, s, skip));
+        CKST(apply_vcycle32(h, li, u, L.y32, s, skip));
         K(cheb_step<float>(L.N, (float)c.c1[j], (float)c.c2[j], L.dinv32, f, L.y32, u, L.d32, s, skip));
     }
     return SEM_OK;
@@ -323,7 +324,7 @@ sem_status vcycle32(sem_handle* h, const float* f0, float* u0, cudaStream_t s) {
             for (int m = 0; m < h->opts.nu1; ++m) CKST(smooth<float>(h, li, f, u, m == 0, s));
         if (h->opts.nu1 == 0 || skip_fine) CKS(cudaMemsetAsync(u, 0, sizeof(float) * L.N, s));
         if (skip_fine) CKS(cudaMemsetAsync(L.y32, 0, sizeof(float) * L.N, s));
-        else CKST(apply_level32(h, li, u, L.y32, s));
+        else CKST(apply_vcycle32(h, li, u, L.y32, s, nullptr));
         CKS(cudaMemsetAsync(C.f32, 0, sizeof(float) * C.N, s));
         K(launch_restrict32(L, C, f, L.y32, C.f32, s));
     }
