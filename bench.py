@@ -70,6 +70,30 @@ def apply_bytes(P, E, N, word=8, gword=None):
     return 2 * N * word + E * 6 * QT * QZ * gword + E * NT * NZ * 4
 
 
+def replica_barrier(world):
+    """Barrier of the replica ranks (no-op on one GPU)."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def replica_max(v, world, device="cuda"):
+    """Max of a per-rank value over the replica ranks: the timed region of the slowest rank."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step, steps, world, seconds):
+    """Units all ranks processed per second of the slowest rank (weak scaling: every rank
+    solves its own copy of the workload each step)."""
+    return units_per_rank_step * steps * world / seconds
+
+
 def kernels_sha():
     """Hash of the prism-apply kernel's source (apply_prism.cu)."""
     with open(os.path.join(ROOT, "paper_2009_00705_gb300", "csrc", "apply_prism.cu"), "rb") as f:
@@ -275,15 +299,10 @@ def main():
     stream = torch.cuda.current_stream()
 
     def barrier():
-        if world > 1:
-            torch.distributed.barrier()
+        replica_barrier(world)
 
     def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return replica_max(v, world, "cuda")
 
     def timed(slv, K, W_, out):
         for _ in range(W_):
@@ -306,7 +325,7 @@ def main():
     clk = clocks.stop()
     ms = max_over_ranks(ms)
     secs = ms / 1000.0
-    value = dof * a.steps * world / secs
+    value = whole_job_rate(dof, a.steps, world, secs)
     apply_ms = sum(s["apply_ms"] for s in stats)
     apply_n = sum(s["apply_launches"] for s in stats)
     launches = sum(s["kernel_launches"] for s in stats)
@@ -424,7 +443,7 @@ def main():
             mesh_t, P_t, modes = W.random_tank(1000 + i)
             xy_t = sem.sem_mesh_nodes2d(mesh_t, P_t)
             st_ = sem.Solver(mesh_t, P_t, eta_nodal=mesh_t.eta(xy_t[:, 0], xy_t[:, 1]), levels=levels_for(P_t),
-                             precision="mixed_fp32", outer="pdc", batch=1, coarse_rtol=a.coarse_rtol, imax=400)
+                             precision="mixed_tf32", outer="pdc", batch=1, coarse_rtol=a.coarse_rtol, imax=400)
             C_t = st_.coords(0)
             phiD_t = torch.tensor(W.tank_potential(*C_t[st_.dirichlet_nodes(0)].T, modes), device="cuda")
             q_t = st_.query(0)
@@ -443,7 +462,7 @@ def main():
         mesh0, P0, _ = W.random_tank(1000)
         xy0 = sem.sem_mesh_nodes2d(mesh0, P0)
         lock0 = sem.Solver(mesh0, P0, eta_nodal=mesh0.eta(xy0[:, 0], xy0[:, 1]), levels=levels_for(P0),
-                           precision="mixed_fp32", outer="pdc", batch=1, coarse_rtol=a.coarse_rtol, imax=400,
+                           precision="mixed_tf32", outer="pdc", batch=1, coarse_rtol=a.coarse_rtol, imax=400,
                            batch_mode=1)
         hs_lock = [lock0.h] + hs[1:]
         sem.laplace_solve_batch(hs_lock, etas, 1e-8, outs)
@@ -471,7 +490,7 @@ def main():
                    "iterations": sum(st_["iters"] for st_ in bstats),
                    "tile_shapes_fp32_fine": sorted({t[0].tile_shapes(0)[1] for t in tanks}),
                    "setup_s": t_setup,
-                   "form": "FP64 defect correction per tank (FP32 V-cycle, single-CTA FP64 coarse CG); the whole "
+                   "form": "FP64 defect correction per tank (MIXED_TF32 V-cycle: tensor-core sweeps, single-CTA FP64 coarse CG); the whole "
                            "batch one instantiated CUDA graph: per tank a branch with the lifting and a WHILE "
                            "conditional node around one iteration whose last kernel tests convergence on the "
                            "device; one graph launch and one host synchronisation per batch"}
