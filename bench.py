@@ -41,8 +41,8 @@ FALLBACK_HBM_GBS = 6800.0
 # apply, per launch, scaled from the 48x48x4-prism capture (18,432 elements;
 # profiles/apply_fp64_p6_box48.md) to the 32,768-element benchmark mesh by element
 # count; reported as null once apply_prism.cu differs from the captured source.
-TRAFFIC = {("apply_fp64", 6): (351.217920e6 + 14.461184e6) * 32768 / 18432}
-TRAFFIC_SRC_SHA = "e6295af0b8790d87"
+TRAFFIC = {("apply_fp64", 6): (350.192896e6 + 14.584064e6) * 32768 / 18432}
+TRAFFIC_SRC_SHA = "46bba8e8b3d917d9"
 
 
 def workload_name(n, nl, P):
