@@ -207,6 +207,20 @@ sem_status sem_apply(sem_handle* h, int level, const double* x_dev, double* y_de
 sem_status sem_apply32(sem_handle* h, int level, const float* x_dev, float* y_dev, int tensor_cores,
                        void* stream);
 
+/* Strategies for a new surface elevation (the paper's operator-reuse strategies I-III,
+ * Section 5): SEM_ETA_FINEST updates the finest operator only and keeps the smoothers and
+ * coarse operators of t = 0; SEM_ETA_LINEAR_COARSE also updates the finest smoother
+ * (diagonal, lambda_hat) and uses linear (flat-surface) operators on the coarse levels;
+ * SEM_ETA_ALL rebuilds every operator of every level from the new elevation. */
+typedef enum { SEM_ETA_FINEST = 0, SEM_ETA_LINEAR_COARSE = 1, SEM_ETA_ALL = 2 } sem_eta_strategy;
+
+/* New free-surface elevation for a 3D handle (time stepping): eta_nodal_host holds eta at
+ * the order-P 2D nodes (the order of sem_mesh_nodes2d, as sem_mesh.eta).  Recomputes the
+ * geometric factors and, per `strategy`, the diagonals, lambda_hat estimates and the
+ * assembled coarse matrix, in place (no allocation after the first call; captured batch
+ * graphs stay valid).  Synchronous.  SEM_EINVAL for a 2D handle or an unknown strategy. */
+sem_status sem_update_eta(sem_handle* h, const double* eta_nodal_host, int strategy);
+
 /* One V-cycle (Algorithm 1, zero initial guess on every level): z = M^{-1} r on
  * the finest level.  Dirichlet entries of r are ignored; those of z are 0. */
 sem_status pmg_vcycle(sem_handle* h, const double* r_dev, double* z_dev, void* stream);

@@ -27,7 +27,7 @@ SMOOTHER = {"chebyshev": 0, "learned": 1}
 
 EXPORTS = ("sem_default_options", "sem_mesh_nodes2d", "sem_setup", "sem_destroy", "sem_query",
            "sem_dirichlet_nodes", "sem_node_coords", "sem_element_map", "sem_lambda_max", "sem_diagonal",
-           "sem_apply", "sem_apply32", "pmg_vcycle", "laplace_solve", "laplace_solve_host", "sem_last_error",
+           "sem_apply", "sem_apply32", "sem_update_eta", "pmg_vcycle", "laplace_solve", "laplace_solve_host", "sem_last_error",
            "sem_cg_csr_noalloc", "sem_mlp_get_weights", "sem_mlp_set_weights", "sem_mlp_forward",
            "sem_mlp_gradient", "sem_learned_train", "laplace_solve_batch", "sem_tile_shapes")
 
@@ -96,6 +96,7 @@ def lib():
     L.sem_tile_shapes.restype = c_int
     L.sem_apply.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_void_p]
     L.sem_apply32.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_int, c_void_p]
+    L.sem_update_eta.argtypes = [c_void_p, POINTER(c_double), c_int]
     L.pmg_vcycle.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
     L.laplace_solve.argtypes = [c_void_p, c_void_p, c_void_p, c_double, c_void_p, POINTER(SemStats), c_void_p]
     L.laplace_solve_host.argtypes = [c_void_p, c_void_p, c_void_p, c_double, c_void_p, POINTER(SemStats),
@@ -117,7 +118,7 @@ def lib():
                  "sem_learned_train", "laplace_solve_batch"):
         getattr(L, name).restype = c_int
     for name in ("sem_mesh_nodes2d", "sem_setup", "sem_query", "sem_dirichlet_nodes", "sem_node_coords",
-                 "sem_element_map", "sem_lambda_max", "sem_diagonal", "sem_apply", "sem_apply32", "pmg_vcycle",
+                 "sem_element_map", "sem_lambda_max", "sem_diagonal", "sem_apply", "sem_apply32", "sem_update_eta", "pmg_vcycle",
                  "laplace_solve", "laplace_solve_host"):
         getattr(L, name).restype = c_int
     _lib = L
@@ -259,6 +260,16 @@ def sem_tile_shapes(h: int, level: int = 0):
 
 def sem_apply(h: int, level: int, x, y, stream=None) -> None:
     _check(lib().sem_apply(h, level, _ptr(x), _ptr(y), _stream(stream)))
+
+
+ETA_STRATEGY = {"finest": 0, "linear_coarse": 1, "all": 2}
+
+
+def sem_update_eta(h: int, eta_nodal, strategy="all") -> None:
+    """New surface elevation at the order-P 2D nodes; strategy 'finest', 'linear_coarse' or 'all'."""
+    e = np.ascontiguousarray(eta_nodal, dtype=np.float64)
+    st = ETA_STRATEGY[strategy] if isinstance(strategy, str) else int(strategy)
+    _check(lib().sem_update_eta(h, e.ctypes.data_as(POINTER(c_double)), st))
 
 
 def sem_apply32(h: int, level: int, x, y, tensor_cores: bool = False, stream=None) -> None:
@@ -407,6 +418,9 @@ class Solver:
 
     def apply(self, level, x, y, stream=None):
         sem_apply(self.h, level, x, y, stream)
+
+    def update_eta(self, eta_nodal, strategy="all"):
+        sem_update_eta(self.h, eta_nodal, strategy)
 
     def apply32(self, level, x, y, tensor_cores=False, stream=None):
         sem_apply32(self.h, level, x, y, tensor_cores, stream)

@@ -492,10 +492,13 @@ cudaError_t build_g16(Level& L, cudaStream_t s) {
     if (L.dim != 3 || !prism_tc_supported(L.p) || L.G32 == nullptr) return cudaSuccess;
     const int QTP = (L.QT + 1) / 2 * 2;
     const long long n = (long long)L.E * 6 * L.QZ * QTP;
-    void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, sizeof(__nv_bfloat16) * (size_t)(n + 32));
-    if (e != cudaSuccess) return e;
-    L.G16 = static_cast<unsigned short*>(p);
+    void* p = L.G16;
+    cudaError_t e = cudaSuccess;
+    if (p == nullptr) {          // first build; later ones (a new surface elevation) reuse it
+        e = cudaMalloc(&p, sizeof(__nv_bfloat16) * (size_t)(n + 32));
+        if (e != cudaSuccess) return e;
+        L.G16 = static_cast<unsigned short*>(p);
+    }
     e = cudaMemsetAsync(p, 0, sizeof(__nv_bfloat16) * (size_t)(n + 32), s);
     if (e != cudaSuccess) return e;
     const long long blocks = (n + 255) / 256;

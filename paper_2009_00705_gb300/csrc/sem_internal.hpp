@@ -62,6 +62,7 @@ struct Level {
     int* csr_rowptr = nullptr;             // coarse level: assembled matrix, free rows/cols
     int* csr_col = nullptr;
     double* csr_val = nullptr;
+    int* csr_slot = nullptr;               // [E][Np][Np] CSR position of each element entry (or -1)
     long long csr_nnz = 0;
 };
 
@@ -124,6 +125,7 @@ struct sem_handle {
     bool bgraph_failed = false;
     unsigned long long uid = 0;     // unique per sem_setup in this process
     sem::BatchPlan* bplan = nullptr;   // graph-resident batched solve (this handle first in the list)
+    bool coarse_flat = false;       // coarse levels built for a flat surface (sem_update_eta strategy 1)
     bool bplan_failed = false;
     long long bgraph_launches = 0, bgraph_applies = 0, bgraph_vcycles = 0;
     long long graph_iters = 0;

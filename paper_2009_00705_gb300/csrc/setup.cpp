@@ -234,26 +234,28 @@ sem_status build_level(sem_handle* h, const sem_mesh* m, int li, int p) {
     return SEM_OK;
 }
 
-sem_status build_geometry(sem_handle* h, const sem_mesh* m) {
+// Geometric factors (FP64, FP32, BF16) of levels [first, last) from the handle's mesh and
+// the order-P surface elevation h->eta2 (or a flat surface when `flat`).
+sem_status geometry_levels(sem_handle* h, int first, int last, bool flat) {
     const int P = h->P;
     const Level& L0 = h->lv[0];
-    std::vector<double> vtri((size_t)m->ntri * 6);
-    for (int b = 0; b < m->ntri; ++b)
+    const int ntri = (int)(h->tri.size() / 3);
+    std::vector<double> vtri((size_t)ntri * 6);
+    for (int b = 0; b < ntri; ++b)
         for (int k = 0; k < 3; ++k) {
-            vtri[6 * b + 2 * k] = m->vxy[2 * m->tri[3 * b + k]];
-            vtri[6 * b + 2 * k + 1] = m->vxy[2 * m->tri[3 * b + k] + 1];
+            vtri[6 * b + 2 * k] = h->vxy[2 * h->tri[3 * b + k]];
+            vtri[6 * b + 2 * k + 1] = h->vxy[2 * h->tri[3 * b + k] + 1];
         }
     double* dvtri = nullptr;
     CK(upload(&dvtri, vtri));
     const int NTP = L0.NT;
-    h->eta2.assign(L0.N2, 0.0);
-    if (m->dim == 3 && m->eta) std::memcpy(h->eta2.data(), m->eta, sizeof(double) * L0.N2);
-    std::vector<double> etaP((size_t)m->ntri * NTP);
-    for (int b = 0; b < m->ntri; ++b)
-        for (int n = 0; n < NTP; ++n) etaP[(size_t)b * NTP + n] = h->eta2[h->map2[0][(size_t)b * NTP + n]];
+    std::vector<double> etaP((size_t)ntri * NTP, 0.0);
+    if (!flat)
+        for (int b = 0; b < ntri; ++b)
+            for (int n = 0; n < NTP; ++n) etaP[(size_t)b * NTP + n] = h->eta2[h->map2[0][(size_t)b * NTP + n]];
     double* detaP = nullptr;
     CK(upload(&detaP, etaP));
-    for (size_t li = 0; li < h->lv.size(); ++li) {
+    for (int li = first; li < last; ++li) {
         Level& L = h->lv[li];
         std::vector<double> B, Dr, Ds;
         tri_lagrange(P, L.ref.tq.data(), L.QT, B, Dr, Ds);   // order-P map at level-p points
@@ -273,8 +275,16 @@ sem_status build_geometry(sem_handle* h, const sem_mesh* m) {
     return SEM_OK;
 }
 
-sem_status build_diagonals(sem_handle* h) {
-    for (Level& L : h->lv) {
+sem_status build_geometry(sem_handle* h, const sem_mesh* m) {
+    h->eta2.assign(h->lv[0].N2, 0.0);
+    if (m->dim == 3 && m->eta) std::memcpy(h->eta2.data(), m->eta, sizeof(double) * h->lv[0].N2);
+    return geometry_levels(h, 0, (int)h->lv.size(), false);
+}
+
+// Assembled diagonal of level li and its inverse on the free nodes (FP64 and FP32).
+sem_status diagonal_level(sem_handle* h, int li) {
+    {
+        Level& L = h->lv[li];
         double* dg = nullptr;
         CK(dalloc(&dg, L.N));
         CK(cudaMemset(dg, 0, sizeof(double) * L.N));
@@ -300,8 +310,18 @@ sem_status build_diagonals(sem_handle* h) {
     return SEM_OK;
 }
 
+sem_status build_diagonals(sem_handle* h) {
+    for (int li = 0; li < (int)h->lv.size(); ++li) {
+        const sem_status st = diagonal_level(h, li);
+        if (st != SEM_OK) return st;
+    }
+    return SEM_OK;
+}
+
 // Full reference gradients [dim][Nq][Np] of the coarsest level (thread-per-element apply
 // inside the persistent coarse CG).
+sem_status reassemble_coarse(sem_handle* h);
+
 sem_status build_coarse_gradients(sem_handle* h) {
     Level& C = h->lv.back();
     const RefLevel& r = C.ref;
@@ -349,15 +369,20 @@ sem_status build_coarse_gradients(sem_handle* h) {
             }
         }
     C.csr_nnz = (long long)col.size();
-    int* dslot = nullptr;
     CK(upload(&C.csr_rowptr, rowptr));
     CK(upload(&C.csr_col, col));
-    CK(upload(&dslot, slot));
+    CK(upload(&C.csr_slot, slot));          // kept: the values are reassembled when eta changes
     CK(dalloc(&C.csr_val, col.size()));
-    CK(cudaMemset(C.csr_val, 0, sizeof(double) * col.size()));
-    CK(coarse_assemble(C, C.gref, dslot, C.csr_val, 0));
+    return reassemble_coarse(h);
+}
+
+// Values of the assembled coarse matrix from the coarsest level's current geometric factors.
+sem_status reassemble_coarse(sem_handle* h) {
+    Level& C = h->lv.back();
+    if (C.csr_val == nullptr) return SEM_OK;
+    CK(cudaMemset(C.csr_val, 0, sizeof(double) * C.csr_nnz));
+    CK(coarse_assemble(C, C.gref, C.csr_slot, C.csr_val, 0));
     CK(cudaDeviceSynchronize());
-    cudaFree(dslot);
     return SEM_OK;
 }
 

@@ -27,6 +27,9 @@ sem_status build_geometry(sem_handle* h, const sem_mesh* m);
 sem_status build_diagonals(sem_handle* h);
 sem_status build_transfers(sem_handle* h);
 sem_status build_coarse_gradients(sem_handle* h);
+sem_status geometry_levels(sem_handle* h, int first, int last, bool flat);
+sem_status diagonal_level(sem_handle* h, int li);
+sem_status reassemble_coarse(sem_handle* h);
 sem_status build_mlp(sem_handle* h);
 sem_status build_workspace(sem_handle* h);
 }  // namespace sem
@@ -532,7 +535,7 @@ cudaError_t tune_prism(Level& L, bool fp32) {
 
 void free_level(Level& L) {
     void* ptrs[] = {L.map, L.G, L.G32, L.G16, L.lift_elems, L.dinv, L.dinv32, L.dir, L.ref64.m, L.ref32.m, L.It64, L.Iz64, L.It32, L.Iz32, L.gref,
-                    L.csr_rowptr, L.csr_col, L.csr_val,
+                    L.csr_rowptr, L.csr_col, L.csr_val, L.csr_slot,
                     L.owner, L.wmult, L.wmult32, L.u, L.f, L.y, L.d, L.u32, L.f32, L.y32, L.d32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -1027,6 +1030,42 @@ sem_status sem_apply32(sem_handle* h, int level, const float* x, float* y, int t
         CKST(apply_level32(h, level, x, y, s));
     }
     K(copy_dirichlet32((long long)L.hdir.size(), L.dir, x, y, s));
+    return SEM_OK;
+}
+
+sem_status sem_update_eta(sem_handle* h, const double* eta_nodal_host, int strategy) {
+    if (!h || !eta_nodal_host) { set_error("sem_update_eta: bad arguments"); return SEM_EINVAL; }
+    if (h->dim != 3) { set_error("sem_update_eta: the surface elevation moves only in 3D handles"); return SEM_EINVAL; }
+    if (strategy < SEM_ETA_FINEST || strategy > SEM_ETA_ALL) { set_error("sem_update_eta: strategy 0, 1 or 2"); return SEM_EINVAL; }
+    CKS(cudaDeviceSynchronize());
+    const Level& L0 = h->lv[0];
+    h->eta2.assign(eta_nodal_host, eta_nodal_host + L0.N2);
+    const int nl = (int)h->lv.size();
+    if (strategy == SEM_ETA_FINEST) {
+        // the finest operator only: smoothers (diagonal, lambda_hat) and coarse operators of t = 0
+        CKST(geometry_levels(h, 0, 1, false));
+    } else if (strategy == SEM_ETA_LINEAR_COARSE) {
+        // the finest operator and its smoother follow eta; the coarse levels use the linear
+        // (flat-surface) operators, built once and then fixed
+        CKST(geometry_levels(h, 0, 1, false));
+        CKST(diagonal_level(h, 0));
+        if (nl > 1) CKST(estimate_lambda(h, 0));
+        if (!h->coarse_flat && nl > 1) {
+            CKST(geometry_levels(h, 1, nl, true));
+            for (int li = 1; li < nl; ++li) CKST(diagonal_level(h, li));
+            CKST(reassemble_coarse(h));
+            for (int li = 1; li + 1 < nl; ++li) CKST(estimate_lambda(h, li));
+            h->coarse_flat = true;
+        }
+    } else {
+        // every operator of every level from the new eta
+        CKST(geometry_levels(h, 0, nl, false));
+        for (int li = 0; li < nl; ++li) CKST(diagonal_level(h, li));
+        CKST(reassemble_coarse(h));
+        for (int li = 0; li + 1 < nl; ++li) CKST(estimate_lambda(h, li));
+        h->coarse_flat = false;
+    }
+    CKS(cudaDeviceSynchronize());
     return SEM_OK;
 }
 
