@@ -242,6 +242,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-update", action="store_true")
     ap.add_argument("--batch-tanks", type=int, default=32,
                     help="random tanks (500-20000 prisms, P in 3..6) for the batched measurement; 0 to skip")
     ap.add_argument("--train-snapshots", type=int, default=60)
@@ -403,6 +404,25 @@ def main():
                 mixed = obj
             ms_solver.close()
 
+    # a new surface elevation between solves (time stepping): the cost of each operator-reuse
+    # strategy and the iterations of the solve that follows, on a handle of its own
+    update = None
+    if not a.no_update:
+        us = sem.Solver(mesh, P, eta_nodal=eta, levels=levels_for(P))
+        eta1 = W.box3d(n, n, nl, eta_modes=[(0.06, 2.0, 1.0, 0.3), (0.04, 1.0, 3.0, 1.1)]).eta(xy[:, 0], xy[:, 1])
+        update = {}
+        for strat, e_new in (("finest", eta1), ("linear_coarse", eta), ("all", eta1)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            us.update_eta(e_new, strat)
+            t_upd = time.perf_counter() - t0
+            st_u = us.solve(phiD, phi, tol=1e-8)
+            torch.cuda.synchronize()
+            update[strat] = {"update_ms": t_upd * 1e3, "solve_ms": st_u["ms"], "iters": st_u["iters"]}
+        us.close()
+        update["form"] = ("sem_update_eta between FP64 PCG solves: finest = strategy I (finest operator only), "
+                          "linear_coarse = II (finest operator and smoother, flat coarse operators), all = III")
+
     learned = None
     if not a.no_learned:
         ls = sem.Solver(mesh, P, eta_nodal=eta, levels=levels_for(P), precision="mixed_fp32", outer="pdc",
@@ -508,7 +528,8 @@ def main():
                            "l2": "no flush: every solve streams the 0.6 GB FP64 geometric factors (> 129 MB L2)",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "mixed_fp32": mixed, "mixed_tf32": mixed_tc, "learned": learned, "batched": batched}
+                "clocks": clk, "mixed_fp32": mixed, "mixed_tf32": mixed_tc, "learned": learned, "batched": batched,
+                "update_eta": update}
         print(json.dumps(line), flush=True)
     solver.close()
     if world > 1:

@@ -208,8 +208,10 @@ sem_status sem_apply32(sem_handle* h, int level, const float* x_dev, float* y_de
                        void* stream);
 
 /* Strategies for a new surface elevation (the paper's operator-reuse strategies I-III,
- * Section 5): SEM_ETA_FINEST updates the finest operator only and keeps the smoothers and
- * coarse operators of t = 0; SEM_ETA_LINEAR_COARSE also updates the finest smoother
+ * Section 5): SEM_ETA_FINEST updates the finest operator and keeps the diagonals and coarse
+ * operators of t = 0 (the finest lambda_hat is re-estimated against the new operator: the
+ * Chebyshev interval has to cover its spectrum); SEM_ETA_LINEAR_COARSE also updates the
+ * finest smoother
  * (diagonal, lambda_hat) and uses linear (flat-surface) operators on the coarse levels;
  * SEM_ETA_ALL rebuilds every operator of every level from the new elevation. */
 typedef enum { SEM_ETA_FINEST = 0, SEM_ETA_LINEAR_COARSE = 1, SEM_ETA_ALL = 2 } sem_eta_strategy;

@@ -629,7 +629,7 @@ sem_status outer_pcg(sem_handle* h, double* u, double tol, sem_stats* st, cudaSt
         int cur = S_DELTA0, nxt = S_DELTA1;
         K(dot64(N, h->z, h->r, sc, sc.scal + cur, s));
         while (true) {
-            if (i >= h->opts.imax) { ret = SEM_NOT_CONVERGED; break; }
+            if (i >= h->opts.imax) { set_error("the outer iteration reached imax"); ret = SEM_NOT_CONVERGED; break; }
             CKST(apply_level64(h, 0, h->p, h->q, false, s));
             K(dot64(N, h->p, h->q, sc, sc.scal + S_PQ, s));
             K(pcg_update(N, sc.scal + cur, sc.scal + S_PQ, h->p, h->q, u, h->r, sc, sc.scal + S_RR, s));
@@ -672,7 +672,7 @@ sem_status outer_pdc(sem_handle* h, double* u, double tol, sem_stats* st, cudaSt
     int i = 0;
     sem_status ret = SEM_OK;
     while (rn > tol) {
-        if (i >= h->opts.imax) { ret = SEM_NOT_CONVERGED; break; }
+        if (i >= h->opts.imax) { set_error("the outer iteration reached imax"); ret = SEM_NOT_CONVERGED; break; }
         CKST(precondition(h, h->r, h->z, s));
         K(axpy64(N, 1.0, h->z, u, s));
         CKST(apply_level64(h, 0, u, h->q, false, s));
@@ -702,7 +702,7 @@ sem_status outer_fgmres(sem_handle* h, double* u, double tol, sem_stats* st, cud
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
     double* dy = h->gm_y;
     while (beta > tol) {
-        if (it >= h->opts.imax) { ret = SEM_NOT_CONVERGED; break; }
+        if (it >= h->opts.imax) { set_error("the outer iteration reached imax"); ret = SEM_NOT_CONVERGED; break; }
         // v0 = r / beta
         h->sc.hpinned[S_TMP] = beta * beta;
         CKS(cudaMemcpyAsync(sc.scal + S_TMP, h->sc.hpinned + S_TMP, sizeof(double), cudaMemcpyHostToDevice, s));
@@ -1042,8 +1042,11 @@ sem_status sem_update_eta(sem_handle* h, const double* eta_nodal_host, int strat
     h->eta2.assign(eta_nodal_host, eta_nodal_host + L0.N2);
     const int nl = (int)h->lv.size();
     if (strategy == SEM_ETA_FINEST) {
-        // the finest operator only: smoothers (diagonal, lambda_hat) and coarse operators of t = 0
+        // the finest operator; the diagonal and the coarse operators of t = 0.  The Chebyshev
+        // interval must still cover the spectrum of D_0^{-1} A(eta), or the sweep amplifies its
+        // top: lambda_hat of the finest level is re-estimated against the new operator.
         CKST(geometry_levels(h, 0, 1, false));
+        if (nl > 1) CKST(estimate_lambda(h, 0));
     } else if (strategy == SEM_ETA_LINEAR_COARSE) {
         // the finest operator and its smoother follow eta; the coarse levels use the linear
         // (flat-surface) operators, built once and then fixed

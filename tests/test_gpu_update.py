@@ -3,9 +3,9 @@
 
 ALL must leave the handle equal to one set up from scratch with the new elevation
 (apply on every level and the diagonals to 1e-12, lambda_hat to 1e-10, the solve to the
-oracle's direct solution to 1e-10 at rtol 1e-13).  FINEST changes only the finest
-operator, so the solve still reaches the new problem's solution (the t = 0 V-cycle is a
-fixed preconditioner) while the coarse levels keep the old elevation's operators.
+oracle's direct solution to 1e-10 at rtol 1e-13).  FINEST changes the finest
+operator (and re-estimates its lambda_hat) while the diagonals and coarse levels keep the
+old elevation's operators; the solve still reaches the new problem's solution.
 LINEAR_COARSE puts the flat-surface operators on the coarse levels (compared with the
 oracle on a flat mesh)."""
 import numpy as np
@@ -93,13 +93,16 @@ def test_update_finest_keeps_the_t0_preconditioner(sem):
     _, _, old = _solver(sem, MODES0)
     _, _, s = _solver(sem, MODES0)
     try:
-        lam0 = s.lambdas()
+        lam0, diag0 = s.lambdas(), s.diagonal(0)
         s.update_eta(mesh1.eta(xy[:, 0], xy[:, 1]), "finest")
+        lam1 = s.lambdas()
         x0 = torch.tensor(W.random_vector(s.query(0)["ndof"], seed=3), device="cuda")
         assert _rel(_apply(s, 0, x0), _apply(fresh, 0, x0)) <= 1e-12
         x1 = torch.tensor(W.random_vector(s.query(1)["ndof"], seed=4), device="cuda")
         assert _rel(_apply(s, 1, x1), _apply(old, 1, x1)) <= 1e-12
-        assert np.array_equal(s.lambdas(), lam0)
+        # the diagonal of t = 0 stays; lambda_hat of the finest level follows the operator
+        assert np.array_equal(s.diagonal(0), diag0)
+        assert np.array_equal(lam1[1:], lam0[1:])
         _solve_vs_oracle(s, mesh1, 1e-11, 1e-8)
     finally:
         s.close()
