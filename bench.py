@@ -243,6 +243,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-update", action="store_true")
+    ap.add_argument("--no-configs", action="store_true")
     ap.add_argument("--batch-tanks", type=int, default=32,
                     help="random tanks (500-20000 prisms, P in 3..6) for the batched measurement; 0 to skip")
     ap.add_argument("--train-snapshots", type=int, default=60)
@@ -423,6 +424,67 @@ def main():
         update["form"] = ("sem_update_eta between FP64 PCG solves: finest = strategy I (finest operator only), "
                           "linear_coarse = II (finest operator and smoother, flat coarse operators), all = III")
 
+    # the other configurations: the 2D slice (FGMRES(30) + pMG 4-2-1 to 1e-10) and the 3D box
+    # at P = 4 (FP64 PCG to 1e-8); one handle each, timed like the main form
+    configs = None
+    if not a.no_configs:
+        configs = {}
+        m1 = W.config_slice2d()
+        s1 = sem.Solver(m1, 4, levels=[4, 2, 1], outer="fgmres", gmres_m=30, coarse_rtol=1e-12, imax=100)
+        C1 = s1.coords(0)
+        d1 = torch.tensor(W.airy2d(*C1[s1.dirichlet_nodes(0)].T), device="cuda")
+        p1 = torch.empty(s1.query(0)["ndof"], dtype=torch.float64, device="cuda")
+        for _ in range(a.warmup):
+            s1.solve(d1, p1, tol=1e-10)
+        torch.cuda.synchronize()
+        reps = 50
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            st1 = s1.solve(d1, p1, tol=1e-10)
+        torch.cuda.synchronize()
+        t1 = (time.perf_counter() - t0) / reps
+        q1 = s1.query(0)
+        configs["slice2d_p4"] = {"workload": "2D slice 2pi x 1, 16x4 quads -> 128 triangles, P=4, Airy-cos "
+                                             "Dirichlet top; FGMRES(30) + pMG 4-2-1 to rtol 1e-10",
+                                 "solves_per_s": 1.0 / t1, "ms_per_solve": t1 * 1e3, "iters": st1["iters"],
+                                 "dof_free": q1["ndof"] - q1["ndirichlet"],
+                                 "dof_per_s": (q1["ndof"] - q1["ndirichlet"]) / t1}
+        s1.close()
+        # the same slice as one CUDA graph launch per solve (FP64 defect correction, the
+        # convergence test on the device): the launch-latency-bound form of this config
+        g1 = sem.Solver(m1, 4, levels=[4, 2, 1], outer="pdc", batch=1, coarse_rtol=1e-12, imax=200)
+        for _ in range(a.warmup):
+            sem.laplace_solve_batch([g1.h], [d1], 1e-10, [p1])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            stg = sem.laplace_solve_batch([g1.h], [d1], 1e-10, [p1])
+        torch.cuda.synchronize()
+        tg = (time.perf_counter() - t0) / reps
+        configs["slice2d_p4_graph"] = {"workload": "the same slice; FP64 defect correction + pMG 4-2-1 to rtol 1e-10, "
+                                                   "one CUDA graph launch per solve (laplace_solve_batch of one tank)",
+                                       "solves_per_s": 1.0 / tg, "ms_per_solve": tg * 1e3, "iters": stg[0]["iters"],
+                                       "graph_iterations": stg[0]["graph_iterations"]}
+        g1.close()
+        xy4 = sem.sem_mesh_nodes2d(mesh, 4)
+        s4 = sem.Solver(mesh, 4, eta_nodal=mesh.eta(xy4[:, 0], xy4[:, 1]), levels=levels_for(4))
+        C4 = s4.coords(0)
+        d4 = torch.tensor(W.potential3d(*C4[s4.dirichlet_nodes(0)].T), device="cuda")
+        p4 = torch.empty(s4.query(0)["ndof"], dtype=torch.float64, device="cuda")
+        for _ in range(a.warmup):
+            s4.solve(d4, p4, tol=1e-8)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            st4 = s4.solve(d4, p4, tol=1e-8)
+        torch.cuda.synchronize()
+        t4 = (time.perf_counter() - t0) / a.steps
+        q4 = s4.query(0)
+        configs["box64_p4"] = {"workload": workload_name(n, nl, 4), "ms_per_solve": t4 * 1e3, "iters": st4["iters"],
+                               "dof_free": q4["ndof"] - q4["ndirichlet"],
+                               "dof_per_s": (q4["ndof"] - q4["ndirichlet"]) / t4}
+        s4.close()
+
     learned = None
     if not a.no_learned:
         ls = sem.Solver(mesh, P, eta_nodal=eta, levels=levels_for(P), precision="mixed_fp32", outer="pdc",
@@ -529,7 +591,7 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "mixed_fp32": mixed, "mixed_tf32": mixed_tc, "learned": learned, "batched": batched,
-                "update_eta": update}
+                "update_eta": update, "other_configs": configs}
         print(json.dumps(line), flush=True)
     solver.close()
     if world > 1:

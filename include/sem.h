@@ -127,6 +127,8 @@ typedef struct {
     double learned_tau;         /* the learned sweep's correction (minimal-residual step) is kept when it
                                    brings ||r|| below learned_tau * ||r|| (default 0.5); after three
                                    rejections and no acceptance a solve continues without it */
+    int surface_ops;            /* 1: prepare the free-surface operators of sem_fnpf_rhs / sem_fnpf_step
+                                   (3D meshes whose Dirichlet nodes are exactly the surface nodes) */
     int batch_mode;             /* laplace_solve_batch with this handle first in the list: 0 (default)
                                    the whole batch as one CUDA graph launch with the convergence test
                                    on the device, 1 host-stepped lockstep */
@@ -222,6 +224,26 @@ typedef enum { SEM_ETA_FINEST = 0, SEM_ETA_LINEAR_COARSE = 1, SEM_ETA_ALL = 2 } 
  * assembled coarse matrix, in place (no allocation after the first call; captured batch
  * graphs stay valid).  Synchronous.  SEM_EINVAL for a 2D handle or an unknown strategy. */
 sem_status sem_update_eta(sem_handle* h, const double* eta_nodal_host, int strategy);
+
+/* Free-surface time stepping around the Laplace solve (Section 2, Eqs. FSeta, FSphi), for
+ * handles set up with surface_ops = 1.  Surface fields live at the order-P 2D nodes (N2
+ * device doubles, the order of sem_mesh_nodes2d): eta (elevation) and phis (potential phi~).
+ * The right-hand sides
+ *   d eta/dt  = -grad eta . grad phi~ + w~ (1 + |grad eta|^2)
+ *   d phi~/dt = -g eta - (|grad phi~|^2 - w~^2 (1 + |grad eta|^2)) / 2
+ * take w~ = dphi/dz at the surface from laplace_solve with phi = phi~ on z = eta (to rtol
+ * tol), the geometry first moved to eta by sem_update_eta(strategy); grad is the horizontal
+ * gradient of the order-P interpolant on each surface triangle, averaged over the triangles
+ * sharing a node.  linear = 1: the small-amplitude form d eta/dt = w~, d phi~/dt = -g eta on
+ * the handle's fixed geometry (set it up with a flat surface).  Synchronous. */
+sem_status sem_fnpf_rhs(sem_handle* h, const double* eta_dev, const double* phis_dev, double g, int linear,
+                        int strategy, double tol, double* deta_dev, double* dphis_dev, void* stream);
+/* One step of the classical four-stage Runge-Kutta method (ERK4) on (eta, phis) in place: four
+ * right-hand sides, four Laplace solves.  stats (nullable): status, the solves' summed
+ * iterations (iters), fine-level applies and time (ms).  A failed solve stops the step and
+ * returns its status with eta and phis unchanged. */
+sem_status sem_fnpf_step(sem_handle* h, double* eta_dev, double* phis_dev, double dt, double g, int linear,
+                         int strategy, double tol, sem_stats* stats, void* stream);
 
 /* One V-cycle (Algorithm 1, zero initial guess on every level): z = M^{-1} r on
  * the finest level.  Dirichlet entries of r are ignored; those of z are 0. */

@@ -27,7 +27,7 @@ SMOOTHER = {"chebyshev": 0, "learned": 1}
 
 EXPORTS = ("sem_default_options", "sem_mesh_nodes2d", "sem_setup", "sem_destroy", "sem_query",
            "sem_dirichlet_nodes", "sem_node_coords", "sem_element_map", "sem_lambda_max", "sem_diagonal",
-           "sem_apply", "sem_apply32", "sem_update_eta", "pmg_vcycle", "laplace_solve", "laplace_solve_host", "sem_last_error",
+           "sem_apply", "sem_apply32", "sem_update_eta", "sem_fnpf_rhs", "sem_fnpf_step", "pmg_vcycle", "laplace_solve", "laplace_solve_host", "sem_last_error",
            "sem_cg_csr_noalloc", "sem_mlp_get_weights", "sem_mlp_set_weights", "sem_mlp_forward",
            "sem_mlp_gradient", "sem_learned_train", "laplace_solve_batch", "sem_tile_shapes")
 
@@ -45,7 +45,7 @@ class SemOptions(Structure):
                 ("gmres_m", c_int), ("coarse_rtol", c_double), ("coarse_imax", c_int), ("profile", c_int),
                 ("inner_imax", c_int), ("inner_rtol", c_double), ("debug_barrier_extra", c_int),
                 ("smoother", c_int), ("mlp_hidden", c_int), ("mlp_seed", ctypes.c_ulonglong), ("batch", c_int),
-                ("autotune", c_int), ("learned_tau", c_double), ("batch_mode", c_int)]
+                ("autotune", c_int), ("learned_tau", c_double), ("surface_ops", c_int), ("batch_mode", c_int)]
 
 
 class SemStats(Structure):
@@ -97,6 +97,10 @@ def lib():
     L.sem_apply.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_void_p]
     L.sem_apply32.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_int, c_void_p]
     L.sem_update_eta.argtypes = [c_void_p, POINTER(c_double), c_int]
+    L.sem_fnpf_rhs.argtypes = [c_void_p, c_void_p, c_void_p, c_double, c_int, c_int, c_double, c_void_p, c_void_p,
+                               c_void_p]
+    L.sem_fnpf_step.argtypes = [c_void_p, c_void_p, c_void_p, c_double, c_double, c_int, c_int, c_double,
+                                POINTER(SemStats), c_void_p]
     L.pmg_vcycle.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
     L.laplace_solve.argtypes = [c_void_p, c_void_p, c_void_p, c_double, c_void_p, POINTER(SemStats), c_void_p]
     L.laplace_solve_host.argtypes = [c_void_p, c_void_p, c_void_p, c_double, c_void_p, POINTER(SemStats),
@@ -118,7 +122,7 @@ def lib():
                  "sem_learned_train", "laplace_solve_batch"):
         getattr(L, name).restype = c_int
     for name in ("sem_mesh_nodes2d", "sem_setup", "sem_query", "sem_dirichlet_nodes", "sem_node_coords",
-                 "sem_element_map", "sem_lambda_max", "sem_diagonal", "sem_apply", "sem_apply32", "sem_update_eta", "pmg_vcycle",
+                 "sem_element_map", "sem_lambda_max", "sem_diagonal", "sem_apply", "sem_apply32", "sem_update_eta", "sem_fnpf_rhs", "sem_fnpf_step", "pmg_vcycle",
                  "laplace_solve", "laplace_solve_host"):
         getattr(L, name).restype = c_int
     _lib = L
@@ -272,6 +276,22 @@ def sem_update_eta(h: int, eta_nodal, strategy="all") -> None:
     _check(lib().sem_update_eta(h, e.ctypes.data_as(POINTER(c_double)), st))
 
 
+def sem_fnpf_rhs(h: int, eta, phis, deta, dphis, g=9.81, linear=False, strategy="all", tol=1e-10, stream=None):
+    """Right-hand sides of the free-surface conditions at the surface nodes (device arrays)."""
+    st = ETA_STRATEGY[strategy] if isinstance(strategy, str) else int(strategy)
+    _check(lib().sem_fnpf_rhs(h, _ptr(eta), _ptr(phis), float(g), int(bool(linear)), st, float(tol), _ptr(deta),
+                              _ptr(dphis), _stream(stream)))
+
+
+def sem_fnpf_step(h: int, eta, phis, dt, g=9.81, linear=False, strategy="all", tol=1e-10, stream=None) -> dict:
+    """One ERK4 step of (eta, phis) in place (device arrays); returns the summed solve stats."""
+    st = ETA_STRATEGY[strategy] if isinstance(strategy, str) else int(strategy)
+    out = SemStats()
+    _check(lib().sem_fnpf_step(h, _ptr(eta), _ptr(phis), float(dt), float(g), int(bool(linear)), st, float(tol),
+                               byref(out), _stream(stream)))
+    return out.as_dict()
+
+
 def sem_apply32(h: int, level: int, x, y, tensor_cores: bool = False, stream=None) -> None:
     """FP32 operator apply (x, y float32 device buffers); tensor_cores selects the TF32 MMA kernel."""
     _check(lib().sem_apply32(h, level, _ptr(x), _ptr(y), int(bool(tensor_cores)), _stream(stream)))
@@ -421,6 +441,12 @@ class Solver:
 
     def update_eta(self, eta_nodal, strategy="all"):
         sem_update_eta(self.h, eta_nodal, strategy)
+
+    def fnpf_rhs(self, eta, phis, deta, dphis, **kw):
+        sem_fnpf_rhs(self.h, eta, phis, deta, dphis, **kw)
+
+    def fnpf_step(self, eta, phis, dt, **kw):
+        return sem_fnpf_step(self.h, eta, phis, dt, **kw)
 
     def apply32(self, level, x, y, tensor_cores=False, stream=None):
         sem_apply32(self.h, level, x, y, tensor_cores, stream)

@@ -126,6 +126,15 @@ struct sem_handle {
     unsigned long long uid = 0;     // unique per sem_setup in this process
     sem::BatchPlan* bplan = nullptr;   // graph-resident batched solve (this handle first in the list)
     bool coarse_flat = false;       // coarse levels built for a flat surface (sem_update_eta strategy 1)
+    // free-surface time stepping (opts.surface_ops): surface operators and work fields
+    int* fs_map2 = nullptr;         // [ntri][NT] order-P 2D node ids
+    double *fs_vtri = nullptr, *fs_Drn = nullptr, *fs_Dsn = nullptr, *fs_Dtop = nullptr, *fs_invm = nullptr;
+    double* fs_eta = nullptr;       // the surface elevation the finest geometry was built with [N2]
+    double* fs_phi = nullptr;       // Laplace solution on the finest level [N]
+    double *fs_w = nullptr, *fs_ex = nullptr, *fs_ey = nullptr, *fs_px = nullptr, *fs_py = nullptr;   // [N2]
+    double* fs_k = nullptr;         // stage slopes: [4][N2] for eta, then [4][N2] for phi~
+    double *fs_se = nullptr, *fs_sp = nullptr;   // stage values [N2]
+    double* fs_hpin = nullptr;      // pinned host copy of a stage elevation [N2]
     bool bplan_failed = false;
     long long bgraph_launches = 0, bgraph_applies = 0, bgraph_vcycles = 0;
     long long graph_iters = 0;
@@ -170,6 +179,18 @@ cudaError_t launch_apply_prism_tc(const Level& L, const float* x, float* y, cons
                                   cudaStream_t s);
 bool prism_tc_supported(int p);
 cudaError_t build_g16(Level& L, cudaStream_t s);
+// fnpf.cu: surface fields of the free-surface time stepping
+cudaError_t surface_gradient(int ntri, int NT, long long N2, const int* map2, const double* vtri, const double* Drn,
+                             const double* Dsn, const double* inv_mult, const double* f2, double* gx, double* gy,
+                             cudaStream_t s);
+cudaError_t surface_w(long long N2, int NZ, long long k0, const double* Dtop, double depth, int nlayers,
+                      const double* phi, const double* eta, double* w, cudaStream_t s);
+cudaError_t fnpf_rhs(long long N2, int linear, double grav, const double* eta, const double* w, const double* ex,
+                     const double* ey, const double* px, const double* py, double* deta, double* dphi,
+                     cudaStream_t s);
+cudaError_t rk_stage(long long n, double c, const double* x0, const double* k0, const double* x1, const double* k1,
+                     double* o0, double* o1, cudaStream_t s);
+cudaError_t rk4_combine(long long n, double dt, const double* k, double* x, cudaStream_t s);
 cudaError_t launch_geometry(Level& L, const double* vtri, const double* etaP, const double* BP,
                             const double* DrP, const double* DsP, int NTP, int nlayers, double depth,
                             cudaStream_t s);

@@ -400,6 +400,46 @@ sem_status build_transfers(sem_handle* h) {
     return SEM_OK;
 }
 
+// Surface operators and work fields of the free-surface time stepping (surface_ops = 1):
+// the order-P surface is the top of the top sigma layer and must be exactly the Dirichlet set.
+sem_status build_surface(sem_handle* h) {
+    if (h->dim != 3) { set_error("surface_ops needs a 3D sigma-layer mesh"); return SEM_EINVAL; }
+    const Level& L0 = h->lv[0];
+    const long long N2 = L0.N2, k_top = (long long)h->nlayers * h->P;
+    bool top_only = (long long)L0.hdir.size() == N2;
+    for (long long i = 0; top_only && i < N2; ++i) top_only = L0.hdir[i] == k_top * N2 + i;
+    if (!top_only) {
+        set_error("surface_ops: the Dirichlet nodes must be exactly the free-surface nodes");
+        return SEM_EINVAL;
+    }
+    const int ntri = (int)(h->tri.size() / 3), NT = L0.NT;
+    std::vector<double> vtri((size_t)ntri * 6);
+    for (int b = 0; b < ntri; ++b)
+        for (int k = 0; k < 3; ++k) {
+            vtri[6 * b + 2 * k] = h->vxy[2 * h->tri[3 * b + k]];
+            vtri[6 * b + 2 * k + 1] = h->vxy[2 * h->tri[3 * b + k] + 1];
+        }
+    std::vector<double> B, Dr, Ds, Bz, Dz;
+    tri_lagrange(h->P, L0.ref.tnodes.data(), NT, B, Dr, Ds);        // derivatives at the nodes
+    const double one = 1.0;
+    lagrange1d(L0.ref.znodes, &one, 1, Bz, Dz);                      // h_k'(+1)
+    std::vector<double> mult(N2, 0.0);
+    for (size_t i = 0; i < h->map2[0].size(); ++i) mult[h->map2[0][i]] += 1.0;
+    for (double& m : mult) m = m > 0 ? 1.0 / m : 0.0;
+    CK(upload(&h->fs_map2, h->map2[0]));
+    CK(upload(&h->fs_vtri, vtri));
+    CK(upload(&h->fs_Drn, Dr));
+    CK(upload(&h->fs_Dsn, Ds));
+    CK(upload(&h->fs_Dtop, Dz));
+    CK(upload(&h->fs_invm, mult));
+    CK(upload(&h->fs_eta, h->eta2));
+    CK(dalloc(&h->fs_phi, L0.N));
+    for (double** v : {&h->fs_w, &h->fs_ex, &h->fs_ey, &h->fs_px, &h->fs_py, &h->fs_se, &h->fs_sp}) CK(dalloc(v, N2));
+    CK(dalloc(&h->fs_k, 8 * N2));
+    CK(cudaMallocHost((void**)&h->fs_hpin, sizeof(double) * N2));
+    return SEM_OK;
+}
+
 sem_status build_workspace(sem_handle* h) {
     const long long N = h->lv[0].N;
     const Level& Lc = h->lv.back();
@@ -429,6 +469,10 @@ sem_status build_workspace(sem_handle* h) {
     CK(dalloc(&h->st_eta, h->lv[0].hdir.size()));
     CK(dalloc(&h->st_rhs, N));
     CK(dalloc(&h->st_phi, N));
+    if (h->opts.surface_ops) {
+        const sem_status st = build_surface(h);
+        if (st != SEM_OK) return st;
+    }
     if (h->opts.profile) {
         h->ev.resize(512);
         h->ev_kind.assign(256, 0);

@@ -809,6 +809,7 @@ void sem_default_options(sem_options* o, int P) {
     o->autotune = 1;
     o->batch_mode = 0;
     o->learned_tau = 0.5;
+    o->surface_ops = 0;
 }
 
 sem_status sem_mesh_nodes2d(const sem_mesh* m, int p, long long* n2, double* xy) {
@@ -896,11 +897,14 @@ void sem_destroy(sem_handle* h) {
                     h->net.W1b, h->net.W2b, h->grads.dW1, h->grads.db1, h->grads.dW2, h->grads.db2,
                     h->adam.m[0], h->adam.m[1], h->adam.m[2], h->adam.m[3], h->adam.v[0], h->adam.v[1],
                     h->adam.v[2], h->adam.v[3], h->mX, h->mT, h->mA1, h->mH1, h->mY, h->mdY, h->mdH, h->mscale,
-                    h->lr32, h->ld32, h->lu32, h->te0, h->tf, h->tu, h->tz, h->bu};
+                    h->lr32, h->ld32, h->lu32, h->te0, h->tf, h->tu, h->tz, h->bu, h->fs_map2, h->fs_vtri,
+                    h->fs_Drn, h->fs_Dsn, h->fs_Dtop, h->fs_invm, h->fs_eta, h->fs_phi, h->fs_w, h->fs_ex,
+                    h->fs_ey, h->fs_px, h->fs_py, h->fs_k, h->fs_se, h->fs_sp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->sc.hpinned) cudaFreeHost(h->sc.hpinned);
     if (h->sc.hflags) cudaFreeHost(h->sc.hflags);
+    if (h->fs_hpin) cudaFreeHost(h->fs_hpin);
     for (auto& e : h->ev) cudaEventDestroy(e);
     if (h->bgraph) cudaGraphExecDestroy(h->bgraph);
     if (h->bplan) {
@@ -1040,6 +1044,7 @@ sem_status sem_update_eta(sem_handle* h, const double* eta_nodal_host, int strat
     CKS(cudaDeviceSynchronize());
     const Level& L0 = h->lv[0];
     h->eta2.assign(eta_nodal_host, eta_nodal_host + L0.N2);
+    if (h->fs_eta) CKS(cudaMemcpy(h->fs_eta, h->eta2.data(), sizeof(double) * L0.N2, cudaMemcpyHostToDevice));
     const int nl = (int)h->lv.size();
     if (strategy == SEM_ETA_FINEST) {
         // the finest operator; the diagonal and the coarse operators of t = 0.  The Chebyshev
@@ -1069,6 +1074,94 @@ sem_status sem_update_eta(sem_handle* h, const double* eta_nodal_host, int strat
         h->coarse_flat = false;
     }
     CKS(cudaDeviceSynchronize());
+    return SEM_OK;
+}
+
+// Right-hand sides of Eqs. FSeta / FSphi at the order-P surface nodes for the fields
+// (eta, phis); the nonlinear form first moves the geometry to eta with `strategy`.  The
+// solve's iterations and time are added to *acc.
+static sem_status fnpf_rhs_impl(sem_handle* h, const double* eta, const double* phis, double g, int linear,
+                                int strategy, double tol, double* deta, double* dphi, sem_stats* acc, cudaStream_t s) {
+    const Level& L0 = h->lv[0];
+    const long long N2 = L0.N2;
+    const int ntri = (int)(h->tri.size() / 3);
+    if (!linear) {
+        CKS(cudaMemcpyAsync(h->fs_hpin, eta, sizeof(double) * N2, cudaMemcpyDeviceToHost, s));
+        CKS(cudaStreamSynchronize(s));
+        CKST(sem_update_eta(h, h->fs_hpin, strategy));
+    }
+    sem_stats st{};
+    const sem_status rs = laplace_solve(h, nullptr, phis, tol, h->fs_phi, &st, s);
+    if (acc) {
+        acc->iters += st.iters;
+        acc->ms += st.ms;
+        acc->fine_applies += st.fine_applies;
+        acc->res_final = st.res_final;
+        acc->fnorm = st.fnorm;
+    }
+    if (rs != SEM_OK) return rs;
+    K(surface_w(N2, L0.NZ, (long long)(h->nlayers - 1) * h->P, h->fs_Dtop, h->depth, h->nlayers, h->fs_phi,
+                h->fs_eta, h->fs_w, s));
+    if (!linear) {
+        K(surface_gradient(ntri, L0.NT, N2, h->fs_map2, h->fs_vtri, h->fs_Drn, h->fs_Dsn, h->fs_invm, eta, h->fs_ex,
+                           h->fs_ey, s));
+        K(surface_gradient(ntri, L0.NT, N2, h->fs_map2, h->fs_vtri, h->fs_Drn, h->fs_Dsn, h->fs_invm, phis, h->fs_px,
+                           h->fs_py, s));
+    }
+    K(fnpf_rhs(N2, linear, g, eta, h->fs_w, h->fs_ex, h->fs_ey, h->fs_px, h->fs_py, deta, dphi, s));
+    return SEM_OK;
+}
+
+static sem_status fnpf_check(const sem_handle* h, const void* eta, const void* phis, int strategy, const char* who) {
+    if (!h || !eta || !phis) { set_error(std::string(who) + ": bad arguments"); return SEM_EINVAL; }
+    if (!h->fs_k) { set_error(std::string(who) + ": the handle was set up without surface_ops"); return SEM_EINVAL; }
+    if (strategy < SEM_ETA_FINEST || strategy > SEM_ETA_ALL) {
+        set_error(std::string(who) + ": strategy 0, 1 or 2");
+        return SEM_EINVAL;
+    }
+    return SEM_OK;
+}
+
+sem_status sem_fnpf_rhs(sem_handle* h, const double* eta, const double* phis, double g, int linear, int strategy,
+                        double tol, double* deta, double* dphis, void* stream) {
+    CKST(fnpf_check(h, eta, phis, strategy, "sem_fnpf_rhs"));
+    if (!deta || !dphis) { set_error("sem_fnpf_rhs: bad arguments"); return SEM_EINVAL; }
+    cudaStream_t s = as_stream(stream);
+    CKST(fnpf_rhs_impl(h, eta, phis, g, linear, strategy, tol, deta, dphis, nullptr, s));
+    CKS(cudaStreamSynchronize(s));
+    return SEM_OK;
+}
+
+sem_status sem_fnpf_step(sem_handle* h, double* eta, double* phis, double dt, double g, int linear, int strategy,
+                         double tol, sem_stats* stats, void* stream) {
+    CKST(fnpf_check(h, eta, phis, strategy, "sem_fnpf_step"));
+    if (!std::isfinite(dt)) { set_error("sem_fnpf_step: dt must be finite"); return SEM_EINVAL; }
+    cudaStream_t s = as_stream(stream);
+    const long long N2 = h->lv[0].N2;
+    double* ke = h->fs_k;            // slopes of eta, [4][N2]
+    double* kp = h->fs_k + 4 * N2;   // slopes of phi~
+    sem_stats acc{};
+    const double c[4] = {0.0, 0.5 * dt, 0.5 * dt, dt};
+    for (int j = 0; j < 4; ++j) {
+        const double* ej = eta;
+        const double* pj = phis;
+        if (j > 0) {
+            K(rk_stage(N2, c[j], eta, ke + (j - 1) * N2, phis, kp + (j - 1) * N2, h->fs_se, h->fs_sp, s));
+            ej = h->fs_se;
+            pj = h->fs_sp;
+        }
+        const sem_status r = fnpf_rhs_impl(h, ej, pj, g, linear, strategy, tol, ke + j * N2, kp + j * N2, &acc, s);
+        if (r != SEM_OK) {
+            acc.status = r;
+            if (stats) *stats = acc;
+            return r;
+        }
+    }
+    K(rk4_combine(N2, dt, ke, eta, s));
+    K(rk4_combine(N2, dt, kp, phis, s));
+    CKS(cudaStreamSynchronize(s));
+    acc.status = SEM_OK;
+    if (stats) *stats = acc;
     return SEM_OK;
 }
 
