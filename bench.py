@@ -244,6 +244,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-update", action="store_true")
     ap.add_argument("--no-configs", action="store_true")
+    ap.add_argument("--no-fnpf", action="store_true")
     ap.add_argument("--batch-tanks", type=int, default=32,
                     help="random tanks (500-20000 prisms, P in 3..6) for the batched measurement; 0 to skip")
     ap.add_argument("--train-snapshots", type=int, default=60)
@@ -485,6 +486,36 @@ def main():
                                "dof_per_s": (q4["ndof"] - q4["ndirichlet"]) / t4}
         s4.close()
 
+    # free-surface time stepping (ERK4, four Laplace solves per step) on the benchmark mesh:
+    # MIXED_TF32 solves to 1e-8, nonlinear with strategy I and small-amplitude (fixed geometry)
+    fnpf = None
+    if not a.no_fnpf:
+        fnpf = {}
+        for form, lin, strat in (("nonlinear_strategy_I", False, "finest"), ("linear", True, "finest")):
+            fs = sem.Solver(mesh, P, eta_nodal=(np.zeros_like(eta) if lin else eta), levels=levels_for(P),
+                            precision="mixed_tf32", outer="pdc", inner_imax=a.inner_imax, inner_rtol=a.inner_rtol,
+                            coarse_rtol=a.coarse_rtol, surface_ops=1)
+            x2, y2 = xy[:, 0], xy[:, 1]
+            e_s = torch.tensor(0.05 * np.cos(x2) * np.cos(y2), device="cuda")
+            p_s = torch.zeros_like(e_s)
+            dt = 0.05
+            fs.fnpf_step(e_s, p_s, dt, linear=lin, strategy=strat, tol=1e-8)
+            torch.cuda.synchronize()
+            nst = 3
+            t0 = time.perf_counter()
+            iters = 0
+            for _ in range(nst):
+                st_f = fs.fnpf_step(e_s, p_s, dt, linear=lin, strategy=strat, tol=1e-8)
+                iters += st_f["iters"]
+            torch.cuda.synchronize()
+            tf = (time.perf_counter() - t0) / nst
+            fnpf[form] = {"ms_per_step": tf * 1e3, "steps_per_s": 1.0 / tf, "outer_iters_per_step": iters / nst,
+                          "solve_ms_per_step": st_f["ms"]}
+            fs.close()
+        fnpf["form"] = ("ERK4 step of (eta, phi~) at the order-P surface nodes (Eqs. FSeta, FSphi): per stage the "
+                        "geometry moved to the stage elevation (nonlinear), a MIXED_TF32 Laplace solve to 1e-8, w~ "
+                        "and the surface gradients; dt = 0.05")
+
     learned = None
     if not a.no_learned:
         ls = sem.Solver(mesh, P, eta_nodal=eta, levels=levels_for(P), precision="mixed_fp32", outer="pdc",
@@ -591,7 +622,8 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "mixed_fp32": mixed, "mixed_tf32": mixed_tc, "learned": learned, "batched": batched,
-                "update_eta": update, "other_configs": configs}
+                "update_eta": update, "other_configs": configs,
+                "fnpf_time_stepping": fnpf}
         print(json.dumps(line), flush=True)
     solver.close()
     if world > 1:

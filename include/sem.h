@@ -222,7 +222,10 @@ typedef enum { SEM_ETA_FINEST = 0, SEM_ETA_LINEAR_COARSE = 1, SEM_ETA_ALL = 2 } 
  * the order-P 2D nodes (the order of sem_mesh_nodes2d, as sem_mesh.eta).  Recomputes the
  * geometric factors and, per `strategy`, the diagonals, lambda_hat estimates and the
  * assembled coarse matrix, in place (no allocation after the first call; captured batch
- * graphs stay valid).  Synchronous.  SEM_EINVAL for a 2D handle or an unknown strategy. */
+ * graphs stay valid).  A mixed-precision handle re-estimates lambda_hat with the FP32
+ * operator its V-cycle smooths with (the FP64 Lanczos recurrence is kept); sem_setup
+ * estimates with the FP64 operator in every precision.  Synchronous.  SEM_EINVAL for a 2D
+ * handle or an unknown strategy. */
 sem_status sem_update_eta(sem_handle* h, const double* eta_nodal_host, int strategy);
 
 /* Free-surface time stepping around the Laplace solve (Section 2, Eqs. FSeta, FSphi), for

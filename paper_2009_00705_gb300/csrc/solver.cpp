@@ -444,7 +444,7 @@ static double tridiag_max_eig(const std::vector<double>& a, const std::vector<do
 // Systems, Sec. 6.7.3).  The estimate is a lower bound of lambda_max; power
 // iteration converges too slowly on some sigma-prism meshes for the Chebyshev
 // interval to cover the top of the spectrum.
-sem_status estimate_lambda(sem_handle* h, int li) {
+sem_status estimate_lambda(sem_handle* h, int li, bool fp32_apply) {
     Level& L = h->lv[li];
     std::vector<double> x0(L.N, 0.0);
     std::vector<char> dm(L.N, 0);
@@ -457,8 +457,16 @@ sem_status estimate_lambda(sem_handle* h, int li) {
     K(cg_init(L.N, L.f, L.dinv, L.u, h->r, h->z, h->p, sc, 0.0, s));
     std::vector<double> alpha, beta;
     for (int it = 0; it < h->opts.lanczos_steps; ++it) {
-        CKS(cudaMemsetAsync(h->q, 0, sizeof(double) * L.N, s));
-        K(launch_apply64(L, h->p, h->q, false, nullptr, s));
+        if (fp32_apply) {
+            // the single-precision operator the mixed V-cycle smooths with (FP64 Lanczos recurrence)
+            K(to_f32(L.N, h->p, L.u32, s));
+            CKS(cudaMemsetAsync(L.y32, 0, sizeof(float) * L.N, s));
+            K(launch_apply32(L, L.u32, L.y32, s));
+            K(to_f64(L.N, L.y32, h->q, s));
+        } else {
+            CKS(cudaMemsetAsync(h->q, 0, sizeof(double) * L.N, s));
+            K(launch_apply64(L, h->p, h->q, false, nullptr, s));
+        }
         K(cg_pq(L.N, h->p, h->q, sc, s));
         double rp[2];                                          // rho_j, p_j^T A p_j
         CKS(cudaMemcpy(rp, sc.scal + S_CG_RHO, 2 * sizeof(double), cudaMemcpyDeviceToHost));
@@ -858,7 +866,7 @@ sem_status sem_setup(const sem_mesh* m, int P, const sem_options* opts, sem_hand
     if (st == SEM_OK) st = build_coarse_gradients(h);
     if (st == SEM_OK) st = build_mlp(h);
     if (st == SEM_OK) st = build_workspace(h);
-    for (int li = 0; li + 1 < o.nlevels && st == SEM_OK; ++li) st = estimate_lambda(h, li);
+    for (int li = 0; li + 1 < o.nlevels && st == SEM_OK; ++li) st = estimate_lambda(h, li, false);
     if (st == SEM_OK && o.autotune && m->dim == 3) {
         // u holds the Lanczos iterate on the smoothed levels; zero it on the coarsest
         for (Level& L : h->lv) {
@@ -1046,23 +1054,26 @@ sem_status sem_update_eta(sem_handle* h, const double* eta_nodal_host, int strat
     h->eta2.assign(eta_nodal_host, eta_nodal_host + L0.N2);
     if (h->fs_eta) CKS(cudaMemcpy(h->fs_eta, h->eta2.data(), sizeof(double) * L0.N2, cudaMemcpyHostToDevice));
     const int nl = (int)h->lv.size();
+    // a mixed-precision handle smooths with the single-precision operator: its lambda_hat is
+    // re-estimated with that operator (the estimate at setup uses the FP64 one)
+    const bool fp32 = h->opts.precision != SEM_PREC_FP64;
     if (strategy == SEM_ETA_FINEST) {
         // the finest operator; the diagonal and the coarse operators of t = 0.  The Chebyshev
         // interval must still cover the spectrum of D_0^{-1} A(eta), or the sweep amplifies its
         // top: lambda_hat of the finest level is re-estimated against the new operator.
         CKST(geometry_levels(h, 0, 1, false));
-        if (nl > 1) CKST(estimate_lambda(h, 0));
+        if (nl > 1) CKST(estimate_lambda(h, 0, fp32));
     } else if (strategy == SEM_ETA_LINEAR_COARSE) {
         // the finest operator and its smoother follow eta; the coarse levels use the linear
         // (flat-surface) operators, built once and then fixed
         CKST(geometry_levels(h, 0, 1, false));
         CKST(diagonal_level(h, 0));
-        if (nl > 1) CKST(estimate_lambda(h, 0));
+        if (nl > 1) CKST(estimate_lambda(h, 0, fp32));
         if (!h->coarse_flat && nl > 1) {
             CKST(geometry_levels(h, 1, nl, true));
             for (int li = 1; li < nl; ++li) CKST(diagonal_level(h, li));
             CKST(reassemble_coarse(h));
-            for (int li = 1; li + 1 < nl; ++li) CKST(estimate_lambda(h, li));
+            for (int li = 1; li + 1 < nl; ++li) CKST(estimate_lambda(h, li, fp32));
             h->coarse_flat = true;
         }
     } else {
@@ -1070,7 +1081,7 @@ sem_status sem_update_eta(sem_handle* h, const double* eta_nodal_host, int strat
         CKST(geometry_levels(h, 0, nl, false));
         for (int li = 0; li < nl; ++li) CKST(diagonal_level(h, li));
         CKST(reassemble_coarse(h));
-        for (int li = 0; li + 1 < nl; ++li) CKST(estimate_lambda(h, li));
+        for (int li = 0; li + 1 < nl; ++li) CKST(estimate_lambda(h, li, fp32));
         h->coarse_flat = false;
     }
     CKS(cudaDeviceSynchronize());

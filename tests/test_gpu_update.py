@@ -145,3 +145,18 @@ def test_update_rejects_2d_handles_and_unknown_strategies(sem):
     finally:
         s2.close()
         s3.close()
+
+
+def test_mixed_handles_reestimate_with_the_single_precision_operator(sem):
+    # the FP32 operator differs from the FP64 one by rounding (~1e-7 of its size), so the
+    # largest Ritz value of the same 30 Lanczos steps moves by about that much
+    mesh1, xy, fresh = _solver(sem, MODES1)
+    _, _, s = _solver(sem, MODES0, precision="mixed_fp32")
+    try:
+        s.update_eta(mesh1.eta(xy[:, 0], xy[:, 1]), "all")
+        lam, lam_f = s.lambdas(), fresh.lambdas()
+        assert np.all(np.abs(lam - lam_f) <= 1e-4 * np.abs(lam_f))
+        _solve_vs_oracle(s, mesh1, 1e-11, 1e-8)
+    finally:
+        s.close()
+        fresh.close()
