@@ -13,7 +13,8 @@ Readings of the paper used here (the CUDA library follows the same ones):
   by u <- u - delta is the same as u <- u + M^{-1} r.
 * Algorithm 3's "q <- A delta" is q <- A p (delta is a scalar).
 * Stop test ||r||_2 <= rtol ||f||_2 + atol on the unpreconditioned free residual.
-* Smoother (not in the paper, which uses additive Schwarz): Chebyshev
+* Smoother: the paper's overlapping additive Schwarz (smoother="asm", the readings
+  in oracle/schwarz.py), or Chebyshev
   iteration of degree k on D^{-1} A (D = diagonal of A) for the interval
   [lo*b, b], b = hi * lambda_hat.  lambda_hat is the largest Ritz value of
   30 Lanczos steps on D^{-1/2} A D^{-1/2} (free nodes) started from D^{-1/2} x0,
@@ -76,8 +77,9 @@ class MGOperators:
     """Matrices of every level for the free-node system (Dirichlet rows/cols zeroed)."""
 
     def __init__(self, prob: Problem, nu1=1, nu2=1, k_cheb=3, lo=0.25, hi=1.1,
-                 lanczos_steps=30, lambdas=None):
+                 lanczos_steps=30, lambdas=None, smoother="chebyshev", overlap=1):
         self.prob = prob
+        self.smoother = smoother
         self.L = len(prob.levels)
         self.nu1, self.nu2, self.k = nu1, nu2, k_cheb
         self.lo, self.hi = lo, hi
@@ -93,6 +95,14 @@ class MGOperators:
             self.Dinv.append(dinv)
         self.P = [prolongation(prob, li) for li in range(self.L - 1)]
         self.lam = []
+        self.asm = []
+        if smoother == "asm":
+            # the overlapping additive Schwarz smoother of Section 4.3 (oracle/schwarz.py)
+            from .schwarz import Schwarz
+            self.asm = [Schwarz(prob, li, self.A[li], overlap) for li in range(self.L - 1)]
+            lambdas = [float("nan")] * (self.L - 1)
+        elif smoother != "chebyshev":
+            raise ValueError("smoother: chebyshev or asm")
         for li in range(self.L - 1):
             lam = lanczos_lambda(self.A[li], self.Dinv[li], prob.levels[li].dmask, lanczos_steps) \
                 if lambdas is None else lambdas[li]
@@ -112,7 +122,9 @@ class MGOperators:
         out[self._cfree] = self._coarse.solve(f[self._cfree])
         return out
 
-    def smooth(self, li, f, x):
+    def smooth(self, li, f, x, post=False):
+        if self.asm:
+            return self.asm[li].smooth(self.A[li], f, x, adjoint=post)
         b = self.hi * self.lam[li]
         a = self.lo * b
         return chebyshev(lambda v: self.apply(li, v), self.Dinv[li], f, x, self.k, a, b)
@@ -134,7 +146,7 @@ class MGOperators:
         for li in range(L - 2, -1, -1):
             us[li] = us[li] + self.P[li] @ us[li + 1]
             for _ in range(self.nu2):
-                us[li] = self.smooth(li, fs[li], us[li])
+                us[li] = self.smooth(li, fs[li], us[li], post=True)
         return us[0]
 
 
