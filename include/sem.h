@@ -57,7 +57,16 @@ typedef enum { SEM_OUTER_PCG = 0, SEM_OUTER_FGMRES = 1, SEM_OUTER_PDC = 2 } sem_
  * tensor cores (TF32 operands, BF16 geometric factors, FP32 accumulation); the inner PCG's
  * products stay FP32. */
 typedef enum { SEM_PREC_FP64 = 0, SEM_PREC_MIXED_FP32 = 1, SEM_PREC_MIXED_TF32 = 2 } sem_precision;
-typedef enum { SEM_SMOOTH_CHEBYSHEV = 0, SEM_SMOOTH_LEARNED = 1 } sem_smoother;
+/* Smoothers: Chebyshev-Jacobi (default); LEARNED (see sem_options.smoother); ASM, the
+ * paper's overlapping additive Schwarz smoother (Section 4.3, Eqs. sec_form, Mass, weights):
+ * u <- u + S^{-1}(f - A u), S^{-1} = W sum_k R_k^T (R_k A R_k^T)^{-1} R_k with one subdomain
+ * per element (its nodes and those within asm_overlap lattice steps; a step joins two nodes
+ * of one element whose lattice indices (i, j) of the triangle and k of the vertical line
+ * differ by at most one in i, j, i + j and k), W = (sum_k R_k R_k^T)^{-1}.  Pre-smoothing
+ * applies S^{-1}, post-smoothing its adjoint sum_k R_k^T (R_k A R_k^T)^{-1} R_k W (a
+ * symmetric V-cycle).  The blocks are inverted at setup and held densely in the V-cycle's
+ * precision (FP64, or FP32 in the mixed precisions). */
+typedef enum { SEM_SMOOTH_CHEBYSHEV = 0, SEM_SMOOTH_LEARNED = 1, SEM_SMOOTH_ASM = 2 } sem_smoother;
 
 /* Mesh description (host memory, read during sem_setup only).
  * dim 2: ntri straight triangles in the (x, z) plane; vxy holds (x, z).
@@ -132,6 +141,10 @@ typedef struct {
     int batch_mode;             /* laplace_solve_batch with this handle first in the list: 0 (default)
                                    the whole batch as one CUDA graph launch with the convergence test
                                    on the device, 1 host-stepped lockstep */
+    int asm_overlap;            /* smoother = ASM: overlap in nodes (default 1; 0 = block Jacobi over the
+                                   element node sets; -1 = "refined Schwarz", ceil((p+1)/2) on the
+                                   order-p level).  Subdomains of more than 1600 (FP64) or 3200 (FP32)
+                                   nodes are refused with SEM_EINVAL */
 } sem_options;
 
 typedef struct {
@@ -155,6 +168,8 @@ typedef struct {
     long long apply32_launches;
     double apply_tc_ms;         /* profile = 1: same for the TF32 tensor-core applies (MIXED_TF32) */
     long long apply_tc_launches;
+    double asm_ms;              /* profile = 1: summed event time of the finest-level Schwarz block kernels */
+    long long asm_launches;
 } sem_stats;
 
 typedef struct sem_handle sem_handle;
@@ -209,6 +224,19 @@ sem_status sem_apply(sem_handle* h, int level, const double* x_dev, double* y_de
 sem_status sem_apply32(sem_handle* h, int level, const float* x_dev, float* y_dev, int tensor_cores,
                        void* stream);
 
+/* Subdomains of the additive Schwarz smoother on `level` (smoother = ASM; every level but
+ * the coarsest): ptr_host [nelem + 1] offsets (int64, may be NULL), nodes_host [ptr[nelem]]
+ * the free global node ids of element k's subdomain, ascending, at ptr[k] .. ptr[k+1]-1
+ * (int32, may be NULL).  SEM_EINVAL if the level has no Schwarz blocks. */
+sem_status sem_asm_subdomains(const sem_handle* h, int level, long long* ptr_host, int* nodes_host);
+
+/* z = S^{-1} r (adjoint = 0) or S^{-T} r (adjoint = 1) on `level`, Eq. Mass, with the
+ * handle's blocks: sem_asm_apply for FP64 handles (N device doubles), sem_asm_apply32
+ * for mixed-precision handles (N device floats); the Dirichlet entries of z are zero.
+ * SEM_EINVAL for the other precision or a level without blocks. */
+sem_status sem_asm_apply(sem_handle* h, int level, const double* r_dev, double* z_dev, int adjoint, void* stream);
+sem_status sem_asm_apply32(sem_handle* h, int level, const float* r_dev, float* z_dev, int adjoint, void* stream);
+
 /* Strategies for a new surface elevation (the paper's operator-reuse strategies I-III,
  * Section 5): SEM_ETA_FINEST updates the finest operator and keeps the diagonals and coarse
  * operators of t = 0 (the finest lambda_hat is re-estimated against the new operator: the
@@ -221,8 +249,11 @@ typedef enum { SEM_ETA_FINEST = 0, SEM_ETA_LINEAR_COARSE = 1, SEM_ETA_ALL = 2 } 
 /* New free-surface elevation for a 3D handle (time stepping): eta_nodal_host holds eta at
  * the order-P 2D nodes (the order of sem_mesh_nodes2d, as sem_mesh.eta).  Recomputes the
  * geometric factors and, per `strategy`, the diagonals, lambda_hat estimates and the
- * assembled coarse matrix, in place (no allocation after the first call; captured batch
- * graphs stay valid).  A mixed-precision handle re-estimates lambda_hat with the FP32
+ * assembled coarse matrix, in place (no allocation after the first call, except the
+ * temporary element matrices from which a Schwarz handle rebuilds its blocks; captured
+ * batch graphs stay valid).  With smoother = ASM the blocks follow the strategy: FINEST
+ * keeps those of t = 0, LINEAR_COARSE rebuilds the finest level's (coarse levels flat),
+ * ALL rebuilds every level's.  A mixed-precision handle re-estimates lambda_hat with the FP32
  * operator its V-cycle smooths with (the FP64 Lanczos recurrence is kept); sem_setup
  * estimates with the FP64 operator in every precision.  Synchronous.  SEM_EINVAL for a 2D
  * handle or an unknown strategy. */

@@ -23,13 +23,14 @@ SEM_OK, SEM_NOT_CONVERGED = 0, 1
 SEM_EINVAL, SEM_ECUDA, SEM_ENOMEM, SEM_NAN, SEM_BREAKDOWN, SEM_TIMEOUT = -1, -2, -3, -4, -5, -6
 OUTER = {"pcg": 0, "fgmres": 1, "pdc": 2}
 PRECISION = {"fp64": 0, "mixed_fp32": 1, "mixed_tf32": 2}
-SMOOTHER = {"chebyshev": 0, "learned": 1}
+SMOOTHER = {"chebyshev": 0, "learned": 1, "asm": 2}
 
 EXPORTS = ("sem_default_options", "sem_mesh_nodes2d", "sem_setup", "sem_destroy", "sem_query",
            "sem_dirichlet_nodes", "sem_node_coords", "sem_element_map", "sem_lambda_max", "sem_diagonal",
            "sem_apply", "sem_apply32", "sem_update_eta", "sem_fnpf_rhs", "sem_fnpf_step", "pmg_vcycle", "laplace_solve", "laplace_solve_host", "sem_last_error",
            "sem_cg_csr_noalloc", "sem_mlp_get_weights", "sem_mlp_set_weights", "sem_mlp_forward",
-           "sem_mlp_gradient", "sem_learned_train", "laplace_solve_batch", "sem_tile_shapes")
+           "sem_mlp_gradient", "sem_learned_train", "laplace_solve_batch", "sem_tile_shapes",
+           "sem_asm_subdomains", "sem_asm_apply", "sem_asm_apply32")
 
 
 class SemMesh(Structure):
@@ -45,7 +46,8 @@ class SemOptions(Structure):
                 ("gmres_m", c_int), ("coarse_rtol", c_double), ("coarse_imax", c_int), ("profile", c_int),
                 ("inner_imax", c_int), ("inner_rtol", c_double), ("debug_barrier_extra", c_int),
                 ("smoother", c_int), ("mlp_hidden", c_int), ("mlp_seed", ctypes.c_ulonglong), ("batch", c_int),
-                ("autotune", c_int), ("learned_tau", c_double), ("surface_ops", c_int), ("batch_mode", c_int)]
+                ("autotune", c_int), ("learned_tau", c_double), ("surface_ops", c_int), ("batch_mode", c_int),
+                ("asm_overlap", c_int)]
 
 
 class SemStats(Structure):
@@ -55,7 +57,8 @@ class SemStats(Structure):
                 ("apply_ms", c_double), ("apply_launches", c_longlong), ("kernel_launches", c_longlong),
                 ("inner_iters", c_longlong), ("learned_accepts", c_longlong), ("learned_fallbacks", c_longlong),
                 ("graph_iterations", c_longlong), ("apply32_ms", c_double), ("apply32_launches", c_longlong),
-                ("apply_tc_ms", c_double), ("apply_tc_launches", c_longlong)]
+                ("apply_tc_ms", c_double), ("apply_tc_launches", c_longlong), ("asm_ms", c_double),
+                ("asm_launches", c_longlong)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -97,6 +100,9 @@ def lib():
     L.sem_apply.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_void_p]
     L.sem_apply32.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_int, c_void_p]
     L.sem_update_eta.argtypes = [c_void_p, POINTER(c_double), c_int]
+    L.sem_asm_subdomains.argtypes = [c_void_p, c_int, POINTER(c_longlong), POINTER(c_int)]
+    L.sem_asm_apply.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_int, c_void_p]
+    L.sem_asm_apply32.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_int, c_void_p]
     L.sem_fnpf_rhs.argtypes = [c_void_p, c_void_p, c_void_p, c_double, c_int, c_int, c_double, c_void_p, c_void_p,
                                c_void_p]
     L.sem_fnpf_step.argtypes = [c_void_p, c_void_p, c_void_p, c_double, c_double, c_int, c_int, c_double,
@@ -264,6 +270,26 @@ def sem_tile_shapes(h: int, level: int = 0):
 
 def sem_apply(h: int, level: int, x, y, stream=None) -> None:
     _check(lib().sem_apply(h, level, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def sem_asm_subdomains(h: int, level: int = 0) -> list:
+    """Free global node ids of every element's Schwarz subdomain on `level` (ascending)."""
+    ne = sem_query(h, level)["nelem"]
+    ptr = np.zeros(ne + 1, dtype=np.int64)
+    _check(lib().sem_asm_subdomains(h, level, ptr.ctypes.data_as(POINTER(c_longlong)), None))
+    nodes = np.zeros(max(int(ptr[-1]), 1), dtype=np.int32)
+    _check(lib().sem_asm_subdomains(h, level, None, nodes.ctypes.data_as(POINTER(c_int))))
+    return [nodes[ptr[k]:ptr[k + 1]].astype(np.int64) for k in range(ne)]
+
+
+def sem_asm_apply(h: int, level: int, r, z, adjoint: bool = False, stream=None) -> None:
+    """z = S^{-1} r (or S^{-T} r) with the handle's Schwarz blocks (FP64 handles, double buffers)."""
+    _check(lib().sem_asm_apply(h, level, _ptr(r), _ptr(z), int(bool(adjoint)), _stream(stream)))
+
+
+def sem_asm_apply32(h: int, level: int, r, z, adjoint: bool = False, stream=None) -> None:
+    """The same with float buffers on a mixed-precision handle."""
+    _check(lib().sem_asm_apply32(h, level, _ptr(r), _ptr(z), int(bool(adjoint)), _stream(stream)))
 
 
 ETA_STRATEGY = {"finest": 0, "linear_coarse": 1, "all": 2}
@@ -450,6 +476,16 @@ class Solver:
 
     def apply32(self, level, x, y, tensor_cores=False, stream=None):
         sem_apply32(self.h, level, x, y, tensor_cores, stream)
+
+    # additive Schwarz smoother (smoother="asm")
+    def asm_subdomains(self, level=0):
+        return sem_asm_subdomains(self.h, level)
+
+    def asm_apply(self, level, r, z, adjoint=False, stream=None):
+        sem_asm_apply(self.h, level, r, z, adjoint, stream)
+
+    def asm_apply32(self, level, r, z, adjoint=False, stream=None):
+        sem_asm_apply32(self.h, level, r, z, adjoint, stream)
 
     def vcycle(self, r, z, stream=None):
         pmg_vcycle(self.h, r, z, stream)

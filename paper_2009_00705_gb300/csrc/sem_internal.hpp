@@ -64,6 +64,18 @@ struct Level {
     double* csr_val = nullptr;
     int* csr_slot = nullptr;               // [E][Np][Np] CSR position of each element entry (or -1)
     long long csr_nnz = 0;
+    // additive Schwarz smoother (smoother = ASM; every level but the coarsest)
+    int asm_nmax = 0;                      // largest subdomain (free nodes)
+    long long asm_words = 0;               // block storage (elements of the V-cycle's type)
+    int* asm_ptr = nullptr;                // [E+1] subdomain node-list offsets
+    int* asm_nodes = nullptr;              // free global ids, ascending per subdomain
+    long long* asm_off = nullptr;          // [E] offset of block k (row stride ld = n rounded up to 4)
+    int* asm_tptr = nullptr;               // [E+1] offsets of the elements touching each subdomain
+    int* asm_telems = nullptr;
+    double* asm_w = nullptr;               // diagonal of W (0 at Dirichlet nodes)
+    float* asm_w32 = nullptr;
+    void* asm_blk = nullptr;               // inverted blocks, double (FP64 handles) or float
+    std::vector<int> hasm_ptr, hasm_nodes;
 };
 
 // The whole batched solve of a list of tanks as one instantiated CUDA graph: per tank a
@@ -147,12 +159,14 @@ struct sem_handle {
     std::vector<std::vector<int>> map2;   // per level: [ntri][NT] 2D ids
     // profiling events
     std::vector<cudaEvent_t> ev;
-    std::vector<int> ev_kind;      // per event pair: 0 FP64, 1 FP32, 2 TF32 tensor-core apply
+    std::vector<int> ev_kind;      // per event pair: 0 FP64, 1 FP32, 2 TF32 tensor-core apply, 3 Schwarz blocks
     int ev_used = 0;
     double apply_ms = 0.0;         // FP64 finest-level applies
     long long apply_launches = 0;
     double apply32_ms = 0.0, apply_tc_ms = 0.0;
     long long apply32_launches = 0, apply_tc_launches = 0;
+    double asm_ms = 0.0;
+    long long asm_launches = 0;
     long long fine_applies = 0;
     long long launches = 0;        // kernels launched since the counter was reset
     long long vcycles = 0;
@@ -191,6 +205,14 @@ cudaError_t fnpf_rhs(long long N2, int linear, double grav, const double* eta, c
 cudaError_t rk_stage(long long n, double c, const double* x0, const double* k0, const double* x1, const double* k1,
                      double* o0, double* o1, cudaStream_t s);
 cudaError_t rk4_combine(long long n, double dt, const double* k, double* x, cudaStream_t s);
+// schwarz.cu: additive Schwarz smoother (subdomains, W, inverted blocks per level)
+sem_status build_asm_level(sem_handle* h, int li);
+sem_status refresh_asm_level(sem_handle* h, int li);   // new geometry: blocks recomputed in place
+void free_asm_level(Level& L);
+int asm_max_block(bool fp64);
+// u += W sum_k R_k^T B_k R_k (f - y) (adjoint 0) or u += sum_k R_k^T B_k R_k W (f - y); y may be null
+cudaError_t asm_apply64(const Level& L, const double* f, const double* y, int adjoint, double* u, cudaStream_t s);
+cudaError_t asm_apply32(const Level& L, const float* f, const float* y, int adjoint, float* u, cudaStream_t s);
 cudaError_t launch_geometry(Level& L, const double* vtri, const double* etaP, const double* BP,
                             const double* DrP, const double* DsP, int NTP, int nlayers, double depth,
                             cudaStream_t s);
@@ -272,6 +294,7 @@ enum {
     S_MULTI = 16                    // FGMRES dots start here (up to 64 + 1)
 };
 enum { F_CG_DONE = 0, F_CG_ITERS = 1, F_LEARN_ACCEPT = 2, F_LEARN_COUNT = 3 /* +0 accepts, +1 fallbacks */,
-       F_TC_ERR = 5, F_BATCH_ITERS = 6, F_BATCH_STATUS = 7 };
+       F_TC_ERR = 5, F_BATCH_ITERS = 6, F_BATCH_STATUS = 7, F_ASM_BAD = 8 };
+constexpr int kFlagCount = 16;
 
 }  // namespace sem

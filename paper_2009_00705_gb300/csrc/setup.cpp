@@ -449,10 +449,10 @@ sem_status build_workspace(sem_handle* h) {
     CK(cudaMemset(sc.counter, 0, 4 * sizeof(unsigned)));
     CK(dalloc(&sc.scal, 128));
     CK(cudaMemset(sc.scal, 0, 128 * sizeof(double)));
-    CK(dalloc(&sc.flags, 8));
-    CK(cudaMemset(sc.flags, 0, 8 * sizeof(int)));
+    CK(dalloc(&sc.flags, kFlagCount));
+    CK(cudaMemset(sc.flags, 0, kFlagCount * sizeof(int)));
     CK(cudaMallocHost((void**)&sc.hpinned, 128 * sizeof(double)));
-    CK(cudaMallocHost((void**)&sc.hflags, 8 * sizeof(int)));
+    CK(cudaMallocHost((void**)&sc.hflags, kFlagCount * sizeof(int)));
     for (double** v : {&h->r, &h->z, &h->p, &h->q, &h->x, &h->fr}) CK(dalloc(v, N));
     if (h->opts.outer == SEM_OUTER_FGMRES) {
         CK(dalloc(&h->V, (size_t)(h->opts.gmres_m + 1) * N));

@@ -96,7 +96,8 @@ static void timed_end(sem_handle* h, int kind, cudaStream_t s) {
     h->ev_used += 2;
     if (kind == 0) h->apply_launches += 1;
     else if (kind == 1) h->apply32_launches += 1;
-    else h->apply_tc_launches += 1;
+    else if (kind == 2) h->apply_tc_launches += 1;
+    else h->asm_launches += 1;
 }
 
 // Finest-level apply with optional event timing (profile = 1).
@@ -127,7 +128,7 @@ void flush_events(sem_handle* h) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]) != cudaSuccess) continue;
         const int kind = h->ev_kind[i / 2];
-        (kind == 0 ? h->apply_ms : kind == 1 ? h->apply32_ms : h->apply_tc_ms) += ms;
+        (kind == 0 ? h->apply_ms : kind == 1 ? h->apply32_ms : kind == 2 ? h->apply_tc_ms : h->asm_ms) += ms;
     }
     h->ev_used = 0;
 }
@@ -192,14 +193,28 @@ sem_status coarse_solve(sem_handle* h, const double* b, double* x, cudaStream_t 
     return SEM_OK;
 }
 
-// One Chebyshev-Jacobi sweep of level li (u = 0 on entry when zero_init).
+// One smoothing sweep of level li (u = 0 on entry when zero_init; post: after the
+// coarse-grid correction): Chebyshev-Jacobi, or the additive Schwarz step
+// u <- u + S^{-1}(f - A u) (Eq. sec_form) with the adjoint of S^{-1} after the correction.
 template <typename T>
-sem_status smooth(sem_handle* h, int li, const T* f, T* u, bool zero_init, cudaStream_t s,
+sem_status smooth(sem_handle* h, int li, const T* f, T* u, bool zero_init, bool post, cudaStream_t s,
                   const int* skip = nullptr);
 
+static sem_status asm_sweep64(sem_handle* h, int li, const double* f, double* u, bool zero_init, bool post,
+                              cudaStream_t s) {
+    Level& L = h->lv[li];
+    if (zero_init) CKS(cudaMemsetAsync(u, 0, sizeof(double) * L.N, s));
+    else CKST(apply_level64(h, li, u, L.y, false, s));
+    const bool timed = timed_begin(h, li, s);
+    K(asm_apply64(L, f, zero_init ? nullptr : L.y, post ? 1 : 0, u, s));
+    if (timed) timed_end(h, 3, s);
+    return SEM_OK;
+}
+
 template <>
-sem_status smooth<double>(sem_handle* h, int li, const double* f, double* u, bool zero_init, cudaStream_t s,
-                          const int*) {
+sem_status smooth<double>(sem_handle* h, int li, const double* f, double* u, bool zero_init, bool post,
+                          cudaStream_t s, const int*) {
+    if (h->opts.smoother == SEM_SMOOTH_ASM) return asm_sweep64(h, li, f, u, zero_init, post, s);
     const Level& L = h->lv[li];
     const Cheb c = cheb_coeffs(L.lam, h->opts);
     if (zero_init) {
@@ -230,9 +245,21 @@ static sem_status apply_vcycle32(sem_handle* h, int li, const float* x, float* y
     return SEM_OK;
 }
 
+static sem_status asm_sweep32(sem_handle* h, int li, const float* f, float* u, bool zero_init, bool post,
+                              cudaStream_t s) {
+    Level& L = h->lv[li];
+    if (zero_init) CKS(cudaMemsetAsync(u, 0, sizeof(float) * L.N, s));
+    else CKST(apply_vcycle32(h, li, u, L.y32, s, nullptr));
+    const bool timed = timed_begin(h, li, s);
+    K(asm_apply32(L, f, zero_init ? nullptr : L.y32, post ? 1 : 0, u, s));
+    if (timed) timed_end(h, 3, s);
+    return SEM_OK;
+}
+
 template <>
-sem_status smooth<float>(sem_handle* h, int li, const float* f, float* u, bool zero_init, cudaStream_t s,
-                         const int* skip) {
+sem_status smooth<float>(sem_handle* h, int li, const float* f, float* u, bool zero_init, bool post,
+                         cudaStream_t s, const int* skip) {
+    if (h->opts.smoother == SEM_SMOOTH_ASM) return asm_sweep32(h, li, f, u, zero_init, post, s);
     const Level& L = h->lv[li];
     const Cheb c = cheb_coeffs(L.lam, h->opts);
     if (zero_init) {
@@ -274,7 +301,7 @@ sem_status learned_sweep(sem_handle* h, const float* f, float* u, cudaStream_t s
     K(judge_min_residual(sc.scal + S_L0, sc.scal + S_RQ, sc.scal + S_QQ, sc.scal + S_ALPHA, sc.flags, F_LEARN_ACCEPT,
                          F_LEARN_COUNT, tau * tau, s));
     K(axpy_accepted32(N, sc.flags, F_LEARN_ACCEPT, sc.scal + S_ALPHA, h->ld32, u, s));
-    return smooth<float>(h, 0, f, u, false, s, sc.flags + F_LEARN_ACCEPT);
+    return smooth<float>(h, 0, f, u, false, true, s, sc.flags + F_LEARN_ACCEPT);
 }
 
 // Algorithm 1 with zero initial guess on every level, FP64 throughout.
@@ -287,7 +314,7 @@ sem_status vcycle64(sem_handle* h, const double* f0, double* u0, cudaStream_t s)
         Level& C = h->lv[li + 1];
         const double* f = (li == 0) ? f0 : L.f;
         double* u = (li == 0) ? u0 : L.u;
-        for (int m = 0; m < h->opts.nu1; ++m) CKST(smooth<double>(h, li, f, u, m == 0, s));
+        for (int m = 0; m < h->opts.nu1; ++m) CKST(smooth<double>(h, li, f, u, m == 0, false, s));
         if (h->opts.nu1 == 0) CKS(cudaMemsetAsync(u, 0, sizeof(double) * L.N, s));
         CKST(apply_level64(h, li, u, L.y, false, s));
         CKS(cudaMemsetAsync(C.f, 0, sizeof(double) * C.N, s));
@@ -301,7 +328,7 @@ sem_status vcycle64(sem_handle* h, const double* f0, double* u0, cudaStream_t s)
         const double* f = (li == 0) ? f0 : L.f;
         double* u = (li == 0) ? u0 : L.u;
         K(launch_prolong64(L, C, C.u, u, s));
-        for (int m = 0; m < h->opts.nu2; ++m) CKST(smooth<double>(h, li, f, u, false, s));
+        for (int m = 0; m < h->opts.nu2; ++m) CKST(smooth<double>(h, li, f, u, false, true, s));
     }
     return SEM_OK;
 }
@@ -324,7 +351,7 @@ sem_status vcycle32(sem_handle* h, const float* f0, float* u0, cudaStream_t s) {
         float* u = (li == 0) ? u0 : L.u32;
         const bool skip_fine = (li == 0) && h->cgc_only;
         if (!skip_fine)
-            for (int m = 0; m < h->opts.nu1; ++m) CKST(smooth<float>(h, li, f, u, m == 0, s));
+            for (int m = 0; m < h->opts.nu1; ++m) CKST(smooth<float>(h, li, f, u, m == 0, false, s));
         if (h->opts.nu1 == 0 || skip_fine) CKS(cudaMemsetAsync(u, 0, sizeof(float) * L.N, s));
         if (skip_fine) CKS(cudaMemsetAsync(L.y32, 0, sizeof(float) * L.N, s));
         else CKST(apply_vcycle32(h, li, u, L.y32, s, nullptr));
@@ -345,7 +372,7 @@ sem_status vcycle32(sem_handle* h, const float* f0, float* u0, cudaStream_t s) {
         if ((li == 0) && h->cgc_only) continue;
         for (int m = 0; m < h->opts.nu2; ++m) {
             if (learned && m == 0) CKST(learned_sweep(h, f, u, s));
-            else CKST(smooth<float>(h, li, f, u, false, s));
+            else CKST(smooth<float>(h, li, f, u, false, true, s));
         }
     }
     return SEM_OK;
@@ -547,6 +574,7 @@ void free_level(Level& L) {
                     L.owner, L.wmult, L.wmult32, L.u, L.f, L.y, L.d, L.u32, L.f32, L.y32, L.d32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    free_asm_level(L);
 }
 
 sem_status check_mesh(const sem_mesh* m, int P) {
@@ -589,7 +617,11 @@ sem_status check_options(const sem_options& o, int P) {
     if (o.imax < 0 || o.coarse_imax < 1 || !(o.coarse_rtol > 0)) { set_error("iteration limits"); return SEM_EINVAL; }
     if (o.batch_mode < 0 || o.batch_mode > 1) { set_error("batch_mode 0 or 1"); return SEM_EINVAL; }
     if (!(o.learned_tau > 0.0 && o.learned_tau <= 1.0)) { set_error("0 < learned_tau <= 1"); return SEM_EINVAL; }
-    if (o.smoother != SEM_SMOOTH_CHEBYSHEV && o.smoother != SEM_SMOOTH_LEARNED) { set_error("smoother"); return SEM_EINVAL; }
+    if (o.smoother < SEM_SMOOTH_CHEBYSHEV || o.smoother > SEM_SMOOTH_ASM) { set_error("smoother"); return SEM_EINVAL; }
+    if (o.smoother == SEM_SMOOTH_ASM && (o.asm_overlap < -1 || o.asm_overlap > 16)) {
+        set_error("asm_overlap in -1..16");
+        return SEM_EINVAL;
+    }
     if (o.smoother == SEM_SMOOTH_LEARNED && (o.precision == SEM_PREC_FP64 || o.mlp_hidden < 1 || o.mlp_hidden > 4096)) {
         set_error("the learned smoother needs a mixed precision and 1 <= mlp_hidden <= 4096");
         return SEM_EINVAL;
@@ -818,6 +850,7 @@ void sem_default_options(sem_options* o, int P) {
     o->batch_mode = 0;
     o->learned_tau = 0.5;
     o->surface_ops = 0;
+    o->asm_overlap = 1;
 }
 
 sem_status sem_mesh_nodes2d(const sem_mesh* m, int p, long long* n2, double* xy) {
@@ -866,6 +899,8 @@ sem_status sem_setup(const sem_mesh* m, int P, const sem_options* opts, sem_hand
     if (st == SEM_OK) st = build_coarse_gradients(h);
     if (st == SEM_OK) st = build_mlp(h);
     if (st == SEM_OK) st = build_workspace(h);
+    if (o.smoother == SEM_SMOOTH_ASM)
+        for (int li = 0; li + 1 < o.nlevels && st == SEM_OK; ++li) st = build_asm_level(h, li);
     for (int li = 0; li + 1 < o.nlevels && st == SEM_OK; ++li) st = estimate_lambda(h, li, false);
     if (st == SEM_OK && o.autotune && m->dim == 3) {
         // u holds the Lanczos iterate on the smoothed levels; zero it on the coarsest
@@ -1045,6 +1080,46 @@ sem_status sem_apply32(sem_handle* h, int level, const float* x, float* y, int t
     return SEM_OK;
 }
 
+static sem_status check_asm(const sem_handle* h, int level) {
+    CKST(check_level(h, level));
+    if (h->lv[level].asm_blk == nullptr) {
+        set_error("no Schwarz blocks on this level (smoother = ASM, every level but the coarsest)");
+        return SEM_EINVAL;
+    }
+    return SEM_OK;
+}
+
+sem_status sem_asm_subdomains(const sem_handle* h, int level, long long* ptr, int* nodes) {
+    CKST(check_asm(h, level));
+    const Level& L = h->lv[level];
+    if (ptr)
+        for (size_t i = 0; i < L.hasm_ptr.size(); ++i) ptr[i] = L.hasm_ptr[i];
+    if (nodes) std::memcpy(nodes, L.hasm_nodes.data(), sizeof(int) * L.hasm_nodes.size());
+    return SEM_OK;
+}
+
+sem_status sem_asm_apply(sem_handle* h, int level, const double* r, double* z, int adjoint, void* stream) {
+    CKST(check_asm(h, level));
+    if (h->opts.precision != SEM_PREC_FP64) { set_error("sem_asm_apply: FP64 handles (sem_asm_apply32 otherwise)"); return SEM_EINVAL; }
+    if (!r || !z || r == z) { set_error("sem_asm_apply: distinct r and z"); return SEM_EINVAL; }
+    const Level& L = h->lv[level];
+    cudaStream_t s = as_stream(stream);
+    CKS(cudaMemsetAsync(z, 0, sizeof(double) * L.N, s));
+    K(asm_apply64(L, r, nullptr, adjoint ? 1 : 0, z, s));
+    return SEM_OK;
+}
+
+sem_status sem_asm_apply32(sem_handle* h, int level, const float* r, float* z, int adjoint, void* stream) {
+    CKST(check_asm(h, level));
+    if (h->opts.precision == SEM_PREC_FP64) { set_error("sem_asm_apply32: mixed-precision handles (sem_asm_apply otherwise)"); return SEM_EINVAL; }
+    if (!r || !z || r == z) { set_error("sem_asm_apply32: distinct r and z"); return SEM_EINVAL; }
+    const Level& L = h->lv[level];
+    cudaStream_t s = as_stream(stream);
+    CKS(cudaMemsetAsync(z, 0, sizeof(float) * L.N, s));
+    K(asm_apply32(L, r, nullptr, adjoint ? 1 : 0, z, s));
+    return SEM_OK;
+}
+
 sem_status sem_update_eta(sem_handle* h, const double* eta_nodal_host, int strategy) {
     if (!h || !eta_nodal_host) { set_error("sem_update_eta: bad arguments"); return SEM_EINVAL; }
     if (h->dim != 3) { set_error("sem_update_eta: the surface elevation moves only in 3D handles"); return SEM_EINVAL; }
@@ -1057,23 +1132,28 @@ sem_status sem_update_eta(sem_handle* h, const double* eta_nodal_host, int strat
     // a mixed-precision handle smooths with the single-precision operator: its lambda_hat is
     // re-estimated with that operator (the estimate at setup uses the FP64 one)
     const bool fp32 = h->opts.precision != SEM_PREC_FP64;
+    const bool asm_on = h->opts.smoother == SEM_SMOOTH_ASM;
     if (strategy == SEM_ETA_FINEST) {
         // the finest operator; the diagonal and the coarse operators of t = 0.  The Chebyshev
         // interval must still cover the spectrum of D_0^{-1} A(eta), or the sweep amplifies its
         // top: lambda_hat of the finest level is re-estimated against the new operator.
         CKST(geometry_levels(h, 0, 1, false));
         if (nl > 1) CKST(estimate_lambda(h, 0, fp32));
+        // the Schwarz blocks of t = 0 stay (they are the smoother the strategy keeps)
     } else if (strategy == SEM_ETA_LINEAR_COARSE) {
         // the finest operator and its smoother follow eta; the coarse levels use the linear
         // (flat-surface) operators, built once and then fixed
         CKST(geometry_levels(h, 0, 1, false));
         CKST(diagonal_level(h, 0));
         if (nl > 1) CKST(estimate_lambda(h, 0, fp32));
+        if (asm_on && nl > 1) CKST(refresh_asm_level(h, 0));
         if (!h->coarse_flat && nl > 1) {
             CKST(geometry_levels(h, 1, nl, true));
             for (int li = 1; li < nl; ++li) CKST(diagonal_level(h, li));
             CKST(reassemble_coarse(h));
             for (int li = 1; li + 1 < nl; ++li) CKST(estimate_lambda(h, li, fp32));
+            if (asm_on)
+                for (int li = 1; li + 1 < nl; ++li) CKST(refresh_asm_level(h, li));
             h->coarse_flat = true;
         }
     } else {
@@ -1082,6 +1162,8 @@ sem_status sem_update_eta(sem_handle* h, const double* eta_nodal_host, int strat
         for (int li = 0; li < nl; ++li) CKST(diagonal_level(h, li));
         CKST(reassemble_coarse(h));
         for (int li = 0; li + 1 < nl; ++li) CKST(estimate_lambda(h, li, fp32));
+        if (asm_on)
+            for (int li = 0; li + 1 < nl; ++li) CKST(refresh_asm_level(h, li));
         h->coarse_flat = false;
     }
     CKS(cudaDeviceSynchronize());
@@ -1195,8 +1277,8 @@ sem_status laplace_solve(sem_handle* h, const double* rhs, const double* eta, do
     h->fine_applies = 0;
     h->vcycles = 0;
     h->coarse_iters_max = 0;
-    h->apply_ms = h->apply32_ms = h->apply_tc_ms = 0;
-    h->apply_launches = h->apply32_launches = h->apply_tc_launches = 0;
+    h->apply_ms = h->apply32_ms = h->apply_tc_ms = h->asm_ms = 0;
+    h->apply_launches = h->apply32_launches = h->apply_tc_launches = h->asm_launches = 0;
     h->launches = 0;
     h->inner_iters = 0;
     CKS(cudaMemsetAsync(h->sc.flags + F_LEARN_COUNT, 0, 2 * sizeof(int), s));
@@ -1253,6 +1335,8 @@ sem_status laplace_solve(sem_handle* h, const double* rhs, const double* eta, do
     st.apply32_launches = h->apply32_launches;
     st.apply_tc_ms = h->apply_tc_ms;
     st.apply_tc_launches = h->apply_tc_launches;
+    st.asm_ms = h->asm_ms;
+    st.asm_launches = h->asm_launches;
     st.kernel_launches = h->launches;
     st.inner_iters = h->inner_iters;
     if (h->opts.smoother == SEM_SMOOTH_LEARNED) {
