@@ -216,7 +216,8 @@ def run_ncu_solve(a):
     xy = sem.sem_mesh_nodes2d(mesh, P)
     opts = {"fp64": dict(),
             "mixed_fp32": dict(precision="mixed_fp32", outer="pdc", inner_imax=a.inner_imax, inner_rtol=a.inner_rtol),
-            "mixed_tf32": dict(precision="mixed_tf32", outer="pdc", inner_imax=a.inner_imax, inner_rtol=a.inner_rtol)}
+            "mixed_tf32": dict(precision="mixed_tf32", outer="pdc", inner_imax=a.inner_imax, inner_rtol=a.inner_rtol),
+            "asm": dict(precision="mixed_tf32", outer="pdc", smoother="asm", nu1=3, nu2=3)}
     s = sem.Solver(mesh, P, eta_nodal=mesh.eta(xy[:, 0], xy[:, 1]), levels=levels_for(P), coarse_rtol=a.coarse_rtol,
                    **opts[a.ncu_solve])
     C = s.coords(0)
@@ -245,6 +246,7 @@ def main():
     ap.add_argument("--no-update", action="store_true")
     ap.add_argument("--no-configs", action="store_true")
     ap.add_argument("--no-fnpf", action="store_true")
+    ap.add_argument("--no-asm", action="store_true")
     ap.add_argument("--batch-tanks", type=int, default=32,
                     help="random tanks (500-20000 prisms, P in 3..6) for the batched measurement; 0 to skip")
     ap.add_argument("--train-snapshots", type=int, default=60)
@@ -255,7 +257,7 @@ def main():
     ap.add_argument("--ncu-case", type=int, default=0, metavar="N",
                     help="profiler driver: one short MIXED_TF32 solve on an N x N x 4 P=6 box (FP64, FP32 and "
                          "tensor-core applies, transfers and the coarse CG all launch); prints stats only")
-    ap.add_argument("--ncu-solve", default="", choices=["", "fp64", "mixed_fp32", "mixed_tf32"],
+    ap.add_argument("--ncu-solve", default="", choices=["", "fp64", "mixed_fp32", "mixed_tf32", "asm"],
                     help="profiler driver: --steps solves of one form on the benchmark workload; prints stats only")
     a = ap.parse_args()
     if a.warmup < 3:
@@ -516,6 +518,76 @@ def main():
                         "geometry moved to the stage elevation (nonlinear), a MIXED_TF32 Laplace solve to 1e-8, w~ "
                         "and the surface gradients; dt = 0.05")
 
+    # the paper's overlapping additive Schwarz smoother (Section 4.3) with its (3,3) sweeps: the
+    # benchmark mesh with FP32 blocks inside the FP64 defect correction (MIXED_TF32), the block
+    # kernel's live event time against the HBM roofline; and the paper's table of iterations per
+    # tolerance (PCG / PDC with ASM against PCG with Chebyshev) on a 16x16x4 box in FP64
+    asm = None
+    if not a.no_asm:
+        asm = {}
+
+        def block_words(slv, li):
+            sub_ = slv.asm_subdomains(li)
+            ns = np.array([len(x) for x in sub_], dtype=np.int64)
+            return int((ns * ((ns + 3) // 4 * 4)).sum()), int(ns.sum()), int(ns.max())
+
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sa = sem.Solver(mesh, P, eta_nodal=eta, levels=levels_for(P), precision="mixed_tf32", outer="pdc",
+                        smoother="asm", nu1=3, nu2=3, coarse_rtol=a.coarse_rtol, profile=1, imax=200)
+        torch.cuda.synchronize()
+        t_setup = time.perf_counter() - t0
+        phi_a = torch.empty(N, dtype=torch.float64, device="cuda")
+        na = max(1, min(a.steps, 3))
+        ms_a, st_a = timed(sa, na, 1, phi_a)
+        ms_a = max_over_ranks(ms_a)
+        words, nsum, nmax = block_words(sa, 0)
+        a_ms = sum(x["asm_ms"] for x in st_a)
+        a_n = sum(x["asm_launches"] for x in st_a)
+        byts = words * 4 + nsum * 4 * 4          # FP32 blocks + gather of f, A u, W and the scatter into u
+        view = None
+        if a_n:
+            avg_s = a_ms / a_n / 1000.0
+            view = {"kernel": "k_asm_apply<float> (finest level: y_k = B_k R_k (f - A u), u += W R_k^T y_k)",
+                    "bound": "hbm", "avg_launch_ms": avg_s * 1e3, "launches": a_n, "algorithmic_bytes": byts,
+                    "achieved_gbs": byts / avg_s / 1e9, "peak_gbs": hbm_peak,
+                    "frac_of_hbm": byts / avg_s / 1e9 / hbm_peak}
+        err = float(np.abs(phi_a.cpu().numpy() - phi64).max() / np.abs(phi64).max())
+        asm["bench_mesh_mixed_tf32"] = {
+            "ms_per_step": ms_a / na, "value": dof * na * world / (ms_a / 1000.0), "unit": UNIT,
+            "outer_iters": st_a[-1]["iters"], "res_final_rel": st_a[-1]["res_final"] / st_a[-1]["fnorm"],
+            "max_rel_diff_vs_fp64_solution": err, "setup_s": t_setup,
+            "finest_blocks": {"subdomains": E, "largest": nmax, "mean": nsum / E, "bytes": words * 4},
+            "block_kernel": view,
+            "form": "FP64 defect correction (Algorithm 2) around one single-precision V-cycle per iteration, "
+                    "additive Schwarz smoothing (overlap 1, 3 pre- and 3 post-sweeps, FP32 blocks "
+                    "(R_k A R_k^T)^{-1} inverted at setup) on the P and intermediate levels, FP64 coarse CG"}
+        sa.close()
+        # the paper's iteration table: iterations to each tolerance from a zero start
+        mesh16 = W.box3d(16, 16, nl, eta_modes=W.eta_sinx_cosy(0.1))
+        xy16 = sem.sem_mesh_nodes2d(mesh16, P)
+        eta16 = mesh16.eta(xy16[:, 0], xy16[:, 1])
+        table = {}
+        for name, opts in (("PCG-pGMG(3,3) ASM", dict(smoother="asm", nu1=3, nu2=3)),
+                           ("PDC-pGMG(3,3) ASM", dict(smoother="asm", nu1=3, nu2=3, outer="pdc")),
+                           ("PDC-pGMG(3,3) ASM, MIXED_TF32 V-cycle", dict(smoother="asm", nu1=3, nu2=3, outer="pdc",
+                                                                          precision="mixed_tf32")),
+                           ("PCG-pGMG(1,1) Chebyshev", dict())):
+            s16 = sem.Solver(mesh16, P, eta_nodal=eta16, levels=levels_for(P), coarse_rtol=1e-10, imax=200, **opts)
+            C16 = s16.coords(0)
+            d16 = torch.tensor(W.potential3d(*C16[s16.dirichlet_nodes(0)].T), device="cuda")
+            p16 = torch.empty(s16.query(0)["ndof"], dtype=torch.float64, device="cuda")
+            row = {}
+            for tol in (1e-4, 1e-5, 1e-6, 1e-7, 1e-8):
+                st16 = s16.solve(d16, p16, tol=tol)
+                row[f"{tol:g}"] = {"iters": st16["iters"], "ms": st16["ms"]}
+            table[name] = row
+            s16.close()
+        asm["iterations_per_tolerance_box16_fp64"] = {
+            "workload": f"3D sigma-prism box 16x16 quads x {nl} layers = {2 * 16 * 16 * nl} prisms, P={P}, "
+                        "eta=0.1 sin(x)cos(y); FP64, coarse CG to 1e-10",
+            "table": table}
+
     learned = None
     if not a.no_learned:
         ls = sem.Solver(mesh, P, eta_nodal=eta, levels=levels_for(P), precision="mixed_fp32", outer="pdc",
@@ -623,7 +695,7 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "mixed_fp32": mixed, "mixed_tf32": mixed_tc, "learned": learned, "batched": batched,
                 "update_eta": update, "other_configs": configs,
-                "fnpf_time_stepping": fnpf}
+                "fnpf_time_stepping": fnpf, "asm": asm}
         print(json.dumps(line), flush=True)
     solver.close()
     if world > 1:

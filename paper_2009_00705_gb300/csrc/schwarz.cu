@@ -181,10 +181,10 @@ __global__ void __launch_bounds__(kAsmThreads) k_asm_assemble(int nsub, int Np, 
 // panel J of PB columns, with I the other indices and D = M_JJ:
 //   M_JJ <- D^{-1},  M_JI <- D^{-1} M_JI,  M_IJ <- -M_IJ D^{-1},  M_II <- M_II - M_IJ D^{-1} M_JI
 // (the right-hand sides use the values before the panel step).  The column panel
-// (nmax x PB) and the row panel (PB x nmax) are staged in shared memory; each warp
-// updates ROWS rows of M_II at a time with the column-panel rows held in registers.
+// (nmax x PB) and the row panel (PB x nmax) are staged in shared memory; M_II is updated
+// in register-tiled 64 x 64 tiles.
 // A pivot that is not positive (or not finite) sets *bad.
-template <typename T, int PB, int ROWS>
+template <typename T, int PB>
 __global__ void __launch_bounds__(kAsmThreads) k_asm_invert(int nsub, int nmax, const int* __restrict__ sptr,
                                                             const long long* __restrict__ off,
                                                             T* __restrict__ blocks, int* bad) {
@@ -192,8 +192,6 @@ __global__ void __launch_bounds__(kAsmThreads) k_asm_invert(int nsub, int nmax, 
     T* Cp = reinterpret_cast<T*>(inv_sm);    // [nmax][PB]
     T* Rp = Cp + (size_t)nmax * PB;          // [PB][nmax]
     __shared__ T D[PB][PB + 1];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int kWarps = kAsmThreads / 32;
     for (int k = blockIdx.x; k < nsub; k += gridDim.x) {
         const int n = sptr[k + 1] - sptr[k], ld = asm_ld(n);
         T* M = blocks + off[k];
@@ -229,6 +227,9 @@ __global__ void __launch_bounds__(kAsmThreads) k_asm_invert(int nsub, int nmax, 
                 if (r < PB) D[r][c] = v;
                 __syncthreads();
             }
+            // (D is read through a volatile pointer: kept in registers across the column loop it
+            // would take PB * PB of them)
+            const volatile T* Dv = &D[0][0];
             for (int c = threadIdx.x; c < n; c += kAsmThreads) {   // row panel R' = D^{-1} R
                 if (c >= J0 && c < J0 + pb) continue;
                 T col[PB], o[PB];
@@ -238,7 +239,7 @@ __global__ void __launch_bounds__(kAsmThreads) k_asm_invert(int nsub, int nmax, 
                 for (int m = 0; m < PB; ++m) {
                     T s = T(0);
 #pragma unroll
-                    for (int l = 0; l < PB; ++l) s += D[m][l] * col[l];
+                    for (int l = 0; l < PB; ++l) s += Dv[m * (PB + 1) + l] * col[l];
                     o[m] = m < pb ? s : T(0);
                 }
 #pragma unroll
@@ -261,30 +262,41 @@ __global__ void __launch_bounds__(kAsmThreads) k_asm_invert(int nsub, int nmax, 
                 const int r = idx / pb, c = idx - r * pb;
                 M[(size_t)(J0 + r) * ld + J0 + c] = D[r][c];
             }
-            for (int g = warp * ROWS; g < n; g += kWarps * ROWS) {           // M_II -= C R'
-                T creg[ROWS][PB];
-                bool ok[ROWS];
+            // M_II -= C R' in 64 x 64 tiles, a 4 x 4 register tile per thread (rows ty + 16 i,
+            // columns tx + 16 j): sixteen independent loads per thread in flight, C and R'
+            // read from shared memory (broadcast along the tile's rows and columns)
+            const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+            const int nt = (n + 63) >> 6;
+            for (int t = 0; t < nt * nt; ++t) {
+                const int r0 = (t / nt) * 64 + ty, c0 = (t % nt) * 64 + tx;
+                T acc[4][4];
+                bool ok[4][4];
 #pragma unroll
-                for (int r = 0; r < ROWS; ++r) {
-                    const int i = g + r;
-                    ok[r] = i < n && !(i >= J0 && i < J0 + pb);
+                for (int a = 0; a < 4; ++a)
 #pragma unroll
-                    for (int m = 0; m < PB; ++m) creg[r][m] = i < n ? Cp[(size_t)i * PB + m] : T(0);
-                }
-                for (int c = lane; c < n; c += 32) {
-                    if (c >= J0 && c < J0 + pb) continue;
-                    T rv[PB];
-#pragma unroll
-                    for (int m = 0; m < PB; ++m) rv[m] = Rp[(size_t)m * nmax + c];
-#pragma unroll
-                    for (int r = 0; r < ROWS; ++r) {
-                        if (!ok[r]) continue;
-                        T s = T(0);
-#pragma unroll
-                        for (int m = 0; m < PB; ++m) s += creg[r][m] * rv[m];
-                        M[(size_t)(g + r) * ld + c] -= s;
+                    for (int b = 0; b < 4; ++b) {
+                        const int r = r0 + 16 * a, c = c0 + 16 * b;
+                        ok[a][b] = r < n && c < n && !(r >= J0 && r < J0 + pb) && !(c >= J0 && c < J0 + pb);
+                        acc[a][b] = ok[a][b] ? M[(size_t)r * ld + c] : T(0);
                     }
+                for (int m = 0; m < pb; ++m) {
+                    T cv[4], rv[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        const int r = r0 + 16 * a, c = c0 + 16 * a;
+                        cv[a] = r < n ? Cp[(size_t)r * PB + m] : T(0);
+                        rv[a] = c < n ? Rp[(size_t)m * nmax + c] : T(0);
+                    }
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) acc[a][b] -= cv[a] * rv[b];
                 }
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b)
+                        if (ok[a][b]) M[(size_t)(r0 + 16 * a) * ld + c0 + 16 * b] = acc[a][b];
             }
             __syncthreads();
         }
@@ -311,7 +323,7 @@ __device__ inline double dot_vec(const double2& b, const double2& x) { return b.
 // the gathered r_k sits in shared memory, one warp per block row reads it with 16-byte
 // loads (rows are padded to ld = n rounded up to 4, padding columns are zero).
 template <typename T>
-__global__ void __launch_bounds__(kAsmThreads) k_asm_apply(int nsub, const int* __restrict__ sptr,
+__global__ void __launch_bounds__(kAsmThreads, 6) k_asm_apply(int nsub, const int* __restrict__ sptr,
                                                            const int* __restrict__ snodes,
                                                            const long long* __restrict__ off,
                                                            const T* __restrict__ blocks, const T* __restrict__ w,
@@ -339,16 +351,31 @@ __global__ void __launch_bounds__(kAsmThreads) k_asm_apply(int nsub, const int* 
         __syncthreads();
         const V* xv = reinterpret_cast<const V*>(xs);
         const int nv = ld / kv;
-        for (int i = warp; i < n; i += kWarps) {
+        // two rows per warp at a time, unrolled twice: four 16-byte loads per lane in flight
+        // (with 6 CTAs per SM this streams the blocks at the device's copy bandwidth)
+        for (int i = warp; i < n; i += 2 * kWarps) {
+            const int i2 = i + kWarps;
             const V* row = reinterpret_cast<const V*>(B + (size_t)i * ld);
-            T s = T(0);
-#pragma unroll 4
-            for (int j = lane; j < nv; j += 32) s += dot_vec(__ldcs(row + j), xv[j]);
+            const V* row2 = reinterpret_cast<const V*>(B + (size_t)(i2 < n ? i2 : i) * ld);
+            T s = T(0), s2 = T(0);
+#pragma unroll 2
+            for (int j = lane; j < nv; j += 32) {
+                const V b1 = __ldcs(row + j), b2 = __ldcs(row2 + j), x = xv[j];
+                s += dot_vec(b1, x);
+                s2 += dot_vec(b2, x);
+            }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            for (int o = 16; o > 0; o >>= 1) {
+                s += __shfl_xor_sync(0xffffffffu, s, o);
+                s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            }
             if (lane == 0) {
                 const int g = nodes[i];
                 atomicAdd(u + g, adjoint ? s : s * w[g]);
+                if (i2 < n) {
+                    const int g2 = nodes[i2];
+                    atomicAdd(u + g2, adjoint ? s2 : s2 * w[g2]);
+                }
             }
         }
         __syncthreads();
@@ -440,17 +467,15 @@ sem_status asm_blocks(Level& L, const T* G, int* dflag) {
     }
     if (e == cudaSuccess) e = cudaMemset(dflag, 0, sizeof(int));
     if (e == cudaSuccess) {
-        const int grid = std::min(L.E, sms * 4);
+        const int grid = L.E;                 // one CTA per block (balanced by the scheduler)
         const size_t PB16 = 2 * (size_t)L.asm_nmax * 16 * sizeof(T);
         if (PB16 <= 200 * 1024) {
-            constexpr int R = sizeof(T) == 8 ? 2 : 4;
-            auto kern = k_asm_invert<T, 16, R>;
+            auto kern = k_asm_invert<T, 16>;
             e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PB16);
             if (e == cudaSuccess) kern<<<grid, kAsmThreads, PB16>>>(L.E, L.asm_nmax, L.asm_ptr, L.asm_off, blk, dflag);
         } else {
             const size_t PB8 = PB16 / 2;
-            constexpr int R = sizeof(T) == 8 ? 4 : 8;
-            auto kern = k_asm_invert<T, 8, R>;
+            auto kern = k_asm_invert<T, 8>;
             e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PB8);
             if (e == cudaSuccess) kern<<<grid, kAsmThreads, PB8>>>(L.E, L.asm_nmax, L.asm_ptr, L.asm_off, blk, dflag);
         }
@@ -619,7 +644,9 @@ void free_asm_level(Level& L) {
 
 template <typename T>
 cudaError_t asm_apply(const Level& L, const T* w, const T* f, const T* y, int adjoint, T* u, cudaStream_t s) {
-    const int grid = std::min(L.E, device_sms() * 8);
+    // one CTA per subdomain: the hardware scheduler balances the waves (a grid-stride grid
+    // larger than the resident CTAs would leave a tail of lone CTAs per SM)
+    const int grid = L.E;
     const size_t smem = (size_t)asm_ld(L.asm_nmax) * sizeof(T);
     k_asm_apply<T><<<grid, kAsmThreads, smem, s>>>(L.E, L.asm_ptr, L.asm_nodes, L.asm_off,
                                                     static_cast<const T*>(L.asm_blk), w, f, y, adjoint, u);

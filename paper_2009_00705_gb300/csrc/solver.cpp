@@ -901,12 +901,16 @@ sem_status sem_setup(const sem_mesh* m, int P, const sem_options* opts, sem_hand
     if (st == SEM_OK) st = build_workspace(h);
     if (o.smoother == SEM_SMOOTH_ASM)
         for (int li = 0; li + 1 < o.nlevels && st == SEM_OK; ++li) st = build_asm_level(h, li);
-    for (int li = 0; li + 1 < o.nlevels && st == SEM_OK; ++li) st = estimate_lambda(h, li, false);
+    // lambda_hat sets the Chebyshev interval; the Schwarz smoother has none (reported as 0)
+    if (o.smoother != SEM_SMOOTH_ASM)
+        for (int li = 0; li + 1 < o.nlevels && st == SEM_OK; ++li) st = estimate_lambda(h, li, false);
     if (st == SEM_OK && o.autotune && m->dim == 3) {
-        // u holds the Lanczos iterate on the smoothed levels; zero it on the coarsest
+        // u holds the Lanczos iterate on the smoothed levels; zero it on the coarsest (and
+        // everywhere when no Lanczos estimate ran)
         for (Level& L : h->lv) {
             if (st != SEM_OK) break;
-            cudaError_t e = (&L == &h->lv.back()) ? cudaMemset(L.u, 0, sizeof(double) * L.N) : cudaSuccess;
+            const bool zero = &L == &h->lv.back() || o.smoother == SEM_SMOOTH_ASM;
+            cudaError_t e = zero ? cudaMemset(L.u, 0, sizeof(double) * L.N) : cudaSuccess;
             if (e == cudaSuccess) e = to_f32(L.N, L.u, L.u32, 0);
             if (e == cudaSuccess) e = tune_prism(L, false);
             if (e == cudaSuccess) e = tune_prism(L, true);
@@ -1133,25 +1137,26 @@ sem_status sem_update_eta(sem_handle* h, const double* eta_nodal_host, int strat
     // re-estimated with that operator (the estimate at setup uses the FP64 one)
     const bool fp32 = h->opts.precision != SEM_PREC_FP64;
     const bool asm_on = h->opts.smoother == SEM_SMOOTH_ASM;
+    auto lambda = [&](int li) { return asm_on ? SEM_OK : estimate_lambda(h, li, fp32); };
     if (strategy == SEM_ETA_FINEST) {
         // the finest operator; the diagonal and the coarse operators of t = 0.  The Chebyshev
         // interval must still cover the spectrum of D_0^{-1} A(eta), or the sweep amplifies its
         // top: lambda_hat of the finest level is re-estimated against the new operator.
         CKST(geometry_levels(h, 0, 1, false));
-        if (nl > 1) CKST(estimate_lambda(h, 0, fp32));
+        if (nl > 1) CKST(lambda(0));
         // the Schwarz blocks of t = 0 stay (they are the smoother the strategy keeps)
     } else if (strategy == SEM_ETA_LINEAR_COARSE) {
         // the finest operator and its smoother follow eta; the coarse levels use the linear
         // (flat-surface) operators, built once and then fixed
         CKST(geometry_levels(h, 0, 1, false));
         CKST(diagonal_level(h, 0));
-        if (nl > 1) CKST(estimate_lambda(h, 0, fp32));
+        if (nl > 1) CKST(lambda(0));
         if (asm_on && nl > 1) CKST(refresh_asm_level(h, 0));
         if (!h->coarse_flat && nl > 1) {
             CKST(geometry_levels(h, 1, nl, true));
             for (int li = 1; li < nl; ++li) CKST(diagonal_level(h, li));
             CKST(reassemble_coarse(h));
-            for (int li = 1; li + 1 < nl; ++li) CKST(estimate_lambda(h, li, fp32));
+            for (int li = 1; li + 1 < nl; ++li) CKST(lambda(li));
             if (asm_on)
                 for (int li = 1; li + 1 < nl; ++li) CKST(refresh_asm_level(h, li));
             h->coarse_flat = true;
@@ -1161,7 +1166,7 @@ sem_status sem_update_eta(sem_handle* h, const double* eta_nodal_host, int strat
         CKST(geometry_levels(h, 0, nl, false));
         for (int li = 0; li < nl; ++li) CKST(diagonal_level(h, li));
         CKST(reassemble_coarse(h));
-        for (int li = 0; li + 1 < nl; ++li) CKST(estimate_lambda(h, li, fp32));
+        for (int li = 0; li + 1 < nl; ++li) CKST(lambda(li));
         if (asm_on)
             for (int li = 0; li + 1 < nl; ++li) CKST(refresh_asm_level(h, li));
         h->coarse_flat = false;
