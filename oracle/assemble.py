@@ -26,15 +26,18 @@ from .refelem import RefPrism, RefTri, tri_basis
 class Problem:
     """Mesh + p-levels (finest first) + the order-P geometry.
 
+    ``levels``: orders p, or (p, pz) pairs for prisms whose vertical order differs
+    (semi-coarsening, Section 6).  The geometry is the order-P map of the finest triangle
+    order P (the sigma map is linear in t within a layer, so its vertical order is exact).
     ``eta_nodal``: eta at the finest level's 2D nodes (canonical numbering); by
     default the mesh's eta evaluated there."""
 
     def __init__(self, mesh, levels, eta_nodal=None):
         self.mesh = mesh
         self.dim = mesh.dim
-        self.levels = [Level(mesh, p) for p in levels]
+        self.levels = [Level(mesh, *(spec if isinstance(spec, (tuple, list)) else (spec,))) for spec in levels]
         fin = self.levels[0]
-        self.P = levels[0]
+        self.P = fin.p
         if mesh.dim == 3:
             if eta_nodal is None:
                 eta_nodal = np.zeros(fin.N2)
@@ -70,13 +73,13 @@ class Problem:
         if self.dim == 2:
             return xy2
         eta2 = self.eta_at_level(li)
-        zn = RefPrism(lev.p).zn
+        zn = RefPrism(lev.p, lev.pz).zn
         nl, h = mesh.nlayers, mesh.depth
         out = np.zeros((lev.N, 3))
-        for kz in range(nl * lev.p + 1):
-            l, k = divmod(kz, lev.p)
+        for kz in range(nl * lev.pz + 1):
+            l, k = divmod(kz, lev.pz)
             if l == nl:
-                l, k = nl - 1, lev.p
+                l, k = nl - 1, lev.pz
             sigma = (l + (zn[k] + 1.0) / 2.0) / nl
             sl = slice(kz * lev.N2, (kz + 1) * lev.N2)
             out[sl, :2] = xy2

@@ -56,11 +56,11 @@ def surface_w(prob: Problem, phi: np.ndarray, eta2: np.ndarray) -> np.ndarray:
     """d phi/dz at the surface nodes from phi on all nodes of the finest level; eta2 is the
     surface elevation the geometry was built with (zeros for the flat domain)."""
     lev, mesh = prob.levels[0], prob.mesh
-    p, nl, N2 = lev.p, mesh.nlayers, lev.N2
-    _, D = lagrange1d(gll(p), np.array([1.0]))      # h_k'(+1) of the GLL basis
+    pz, nl, N2 = lev.pz, mesh.nlayers, lev.N2
+    _, D = lagrange1d(gll(pz), np.array([1.0]))     # h_k'(+1) of the vertical GLL basis
     phit = np.zeros(N2)
-    for k in range(p + 1):
-        kz = (nl - 1) * p + k
+    for k in range(pz + 1):
+        kz = (nl - 1) * pz + k
         phit += D[0, k] * phi[kz * N2:(kz + 1) * N2]
     return phit / ((mesh.depth + eta2) / (2.0 * nl))
 
@@ -68,7 +68,7 @@ def surface_w(prob: Problem, phi: np.ndarray, eta2: np.ndarray) -> np.ndarray:
 def _surface_problem(mesh, levels, eta2):
     prob = Problem(mesh, levels, eta_nodal=eta2)
     lev = prob.levels[0]
-    top = (mesh.nlayers * lev.p) * lev.N2 + np.arange(lev.N2)
+    top = (mesh.nlayers * lev.pz) * lev.N2 + np.arange(lev.N2)
     if not np.array_equal(lev.dirichlet, top):
         raise ValueError("the free-surface fields need the surface nodes to be exactly the Dirichlet nodes")
     return prob

@@ -62,9 +62,10 @@ def tri_numbering(tri: np.ndarray, p: int):
 class Level:
     """One p-level of the mesh: numbering, Dirichlet set, reference element."""
 
-    def __init__(self, mesh, p: int):
+    def __init__(self, mesh, p: int, pz: int | None = None):
+        pz = p if pz is None else pz
         self.mesh = mesh
-        self.p = p
+        self.p, self.pz = p, pz                      # triangle order, vertical order (3D)
         self.dim = mesh.dim
         map2, N2 = tri_numbering(mesh.tri, p)
         self.map2, self.N2 = map2, N2
@@ -73,7 +74,7 @@ class Level:
             self.emap = map2
             self.N = N2
         else:
-            self.ref = RefPrism(p)
+            self.ref = RefPrism(p, pz)
             nl = mesh.nlayers
             NT = self.ref.NT
             E = mesh.tri.shape[0] * nl
@@ -81,11 +82,11 @@ class Level:
             for b in range(mesh.tri.shape[0]):
                 for l in range(nl):
                     e = b * nl + l
-                    for k in range(p + 1):
-                        kz = l * p + k
+                    for k in range(pz + 1):
+                        kz = l * pz + k
                         emap[e, k * NT:(k + 1) * NT] = kz * N2 + map2[b]
             self.emap = emap
-            self.N = N2 * (nl * p + 1)
+            self.N = N2 * (nl * pz + 1)
         dmask = np.zeros(self.N, dtype=bool)
         fb = mesh.face_bc
         faces = [np.asarray(self.ref.face_nodes(f)) for f in range(fb.shape[1])]

@@ -234,20 +234,22 @@ class RefTri:
 
 
 class RefPrism:
-    """Order-p reference prism T x [-1, 1]: nodes (triangle x GLL, index k*NT + n),
-    quadrature (collapsed (p+1)^2 on T times (p+1) Gauss-Legendre in t)."""
+    """Reference prism T x [-1, 1] of order p on the triangle and pz in the vertical
+    (pz = p unless given; Section 6 uses P_xy != P_z): nodes (triangle x GLL, index
+    k*NT + n), quadrature (collapsed (p+1)^2 on T times (pz+1) Gauss-Legendre in t)."""
 
-    def __init__(self, p: int):
-        self.p = p
+    def __init__(self, p: int, pz: int | None = None):
+        pz = p if pz is None else pz
+        self.p, self.pz = p, pz
         self.tri = RefTri(p)
         self.NT = self.tri.NT
-        self.NZ = p + 1
+        self.NZ = pz + 1
         self.Np = self.NT * self.NZ
-        self.zn = gll(p)
+        self.zn = gll(pz)
         tn = self.tri.nodes
         self.nodes = np.array([(tn[n, 0], tn[n, 1], self.zn[k])
                                for k in range(self.NZ) for n in range(self.NT)])
-        zq, zw = gauss_legendre(p + 1)
+        zq, zw = gauss_legendre(pz + 1)
         tq, tw = self.tri.qpts, self.tri.qw
         self.qpts = np.array([(tq[a, 0], tq[a, 1], zq[c]) for c in range(zq.size) for a in range(tw.size)])
         self.qw = np.array([tw[a] * zw[c] for c in range(zq.size) for a in range(tw.size)])
@@ -277,23 +279,22 @@ class RefPrism:
         if f < 3:
             tf = self.tri.face_nodes(f)
             return [k * self.NT + n for k in range(self.NZ) for n in tf]
-        k = 0 if f == 3 else self.p
+        k = 0 if f == 3 else self.pz
         return [k * self.NT + n for n in range(self.NT)]
 
 
-def ref_element(dim: int, p: int):
-    return RefTri(p) if dim == 2 else RefPrism(p)
+def ref_element(dim: int, p: int, pz: int | None = None):
+    return RefTri(p) if dim == 2 else RefPrism(p, pz)
 
 
-def interpolation_matrix(dim: int, pf: int, pc: int) -> np.ndarray:
-    """Element prolongation I [Np_f, Np_c]: order-pc Lagrange basis at the order-pf nodes.
+def interpolation_matrix(dim: int, pf: int, pc: int, pzf: int | None = None, pzc: int | None = None) -> np.ndarray:
+    """Element prolongation I [Np_f, Np_c]: the coarse basis (order pc, vertical pzc) at the
+    fine nodes (order pf, vertical pzf).
 
-    Nested spaces (Section 4.1): a coarse polynomial is reproduced exactly at the
-    fine nodes, so I is the element block of the global prolongation P."""
-    fine = ref_element(dim, pf)
-    coarse = ref_element(dim, pc)
-    if dim == 2:
-        B, _ = coarse.basis_at(fine.nodes)
-    else:
-        B, _ = coarse.basis_at(fine.nodes)
+    Nested spaces (Section 4.1; semi-coarsening of Section 6 lowers one direction only):
+    a coarse polynomial is reproduced exactly at the fine nodes, so I is the element block
+    of the global prolongation P."""
+    fine = ref_element(dim, pf, pzf)
+    coarse = ref_element(dim, pc, pzc)
+    B, _ = coarse.basis_at(fine.nodes)
     return B

@@ -39,18 +39,19 @@ from .assemble import Problem
 from .refelem import lattice
 
 
-def local_lattice(dim: int, p: int) -> np.ndarray:
+def local_lattice(dim: int, p: int, pz: int | None = None) -> np.ndarray:
     """Lattice indices (i, j, k) of the element's local nodes in local node order
-    (k = 0 for triangles)."""
+    (k = 0 for triangles; k = 0..pz on the vertical line, pz = p unless given)."""
     tl = lattice(p)
     if dim == 2:
         return np.array([(i, j, 0) for (i, j) in tl], dtype=np.int64)
-    return np.array([(i, j, k) for k in range(p + 1) for (i, j) in tl], dtype=np.int64)
+    pz = p if pz is None else pz
+    return np.array([(i, j, k) for k in range(pz + 1) for (i, j) in tl], dtype=np.int64)
 
 
-def lattice_steps(dim: int, p: int):
+def lattice_steps(dim: int, p: int, pz: int | None = None):
     """For every local node, the local nodes one lattice step away."""
-    lat = local_lattice(dim, p)
+    lat = local_lattice(dim, p, pz)
     out = []
     for a in range(lat.shape[0]):
         nb = []
@@ -65,8 +66,8 @@ def lattice_steps(dim: int, p: int):
 
 
 def overlap_of(p: int, overlap: int) -> int:
-    """Overlap in nodes on an order-p level; overlap < 0 selects the refined
-    Schwarz variant, ceil((p + 1) / 2)."""
+    """Overlap in nodes on an order-p level (p the triangle order); overlap < 0 selects
+    the refined Schwarz variant, ceil((p + 1) / 2)."""
     return math.ceil((p + 1) / 2) if overlap < 0 else overlap
 
 
@@ -74,7 +75,7 @@ def subdomains(prob: Problem, li: int, overlap: int = 1):
     """Sorted free global node ids of every element's subdomain on level li."""
     lev = prob.levels[li]
     ell = overlap_of(lev.p, overlap)
-    steps = lattice_steps(prob.dim, lev.p)
+    steps = lattice_steps(prob.dim, lev.p, lev.pz)
     incid = [[] for _ in range(lev.N)]                 # node -> (element, local index)
     for e in range(lev.emap.shape[0]):
         for a, g in enumerate(lev.emap[e]):

@@ -156,7 +156,7 @@ def prolongation(prob: Problem, li: int) -> sp.csr_matrix:
     P[i, J] = value of the coarse basis function J at fine node i (Section 4.1,
     nested spaces), taken from any element that contains node i."""
     fine, coarse = prob.levels[li], prob.levels[li + 1]
-    I = interpolation_matrix(prob.dim, fine.p, coarse.p)       # [Np_f, Np_c]
+    I = interpolation_matrix(prob.dim, fine.p, coarse.p, fine.pz, coarse.pz)   # [Np_f, Np_c]
     done = np.zeros(fine.N, dtype=bool)
     rows, cols, vals = [], [], []
     for e in range(fine.emap.shape[0]):
