@@ -94,7 +94,8 @@ typedef struct {
 } sem_mesh;
 
 /* Solver options; fill with sem_default_options and adjust.
- * level_p[0] = P > level_p[1] > ... > level_p[nlevels-1] = 1 (order per level).
+ * level_p[0] = P >= level_p[1] >= ... >= level_p[nlevels-1] = 1 (triangle order per level;
+ * prisms may give a separate vertical order per level in level_pz).
  * Smoother: k_cheb-step Chebyshev iteration on D^{-1}A over [cheb_lo*b, b],
  * b = cheb_hi * lambda_hat, lambda_hat = the largest Ritz value of lanczos_steps
  * Lanczos steps on D^{-1}A started from x_i = sin(i+1) on free nodes (a lower
@@ -145,6 +146,12 @@ typedef struct {
                                    element node sets; -1 = "refined Schwarz", ceil((p+1)/2) on the
                                    order-p level).  Subdomains of more than 1600 (FP64) or 3200 (FP32)
                                    nodes are refused with SEM_EINVAL */
+    int level_pz[SEM_MAX_LEVELS]; /* prisms: vertical order of each level (0 = level_p, the default).  With
+                                   level_pz[0] < P the finest prisms are anisotropic (P_xy = P, P_z =
+                                   level_pz[0]; Section 6); semi-coarsening lowers one order at a time,
+                                   e.g. (5,3) -> (3,3) -> (1,1).  Per level neither order may grow and one
+                                   must fall; the coarsest level is (1,1); the vertical order equals the
+                                   triangle order or lies one or two below it */
 } sem_options;
 
 typedef struct {

@@ -47,7 +47,7 @@ class SemOptions(Structure):
                 ("inner_imax", c_int), ("inner_rtol", c_double), ("debug_barrier_extra", c_int),
                 ("smoother", c_int), ("mlp_hidden", c_int), ("mlp_seed", ctypes.c_ulonglong), ("batch", c_int),
                 ("autotune", c_int), ("learned_tau", c_double), ("surface_ops", c_int), ("batch_mode", c_int),
-                ("asm_overlap", c_int)]
+                ("asm_overlap", c_int), ("level_pz", c_int * SEM_MAX_LEVELS)]
 
 
 class SemStats(Structure):
@@ -185,9 +185,12 @@ def sem_default_options(P: int, **overrides) -> SemOptions:
     lib().sem_default_options(byref(o), int(P))
     for k, v in overrides.items():
         if k == "levels":
+            # orders p, or (p, pz) pairs for anisotropic prism levels (semi-coarsening)
             o.nlevels = len(v)
             for i, p in enumerate(v):
+                p, pz = (p if isinstance(p, (tuple, list)) else (p, 0))
                 o.level_p[i] = int(p)
+                o.level_pz[i] = int(pz)
         elif k == "outer":
             o.outer = OUTER[v] if isinstance(v, str) else int(v)
         elif k == "precision":

@@ -20,9 +20,10 @@ constexpr int kSMs = 152;
 // registers, and in the transposed stage one thread owns a triangle node n and
 // keeps all QZ partial sums, so the transposed vertical stage and the
 // direct-stiffness summation follow without another pass through shared memory.
-template <int P, typename T, int V>
+template <int P, int PZ, typename T, int V>
 struct PrismTile {
-    static constexpr int NT = (P + 1) * (P + 2) / 2, NZ = P + 1, QT = (P + 1) * (P + 1), QZ = P + 1;
+    // triangle order P, vertical order PZ (= P unless the level is anisotropic)
+    static constexpr int NT = (P + 1) * (P + 2) / 2, NZ = PZ + 1, QT = (P + 1) * (P + 1), QZ = PZ + 1;
     static constexpr int Np = NT * NZ, Nq = QT * QZ;
     static constexpr int VEC = 16 / sizeof(T);                  // elements per 16-byte load
     static constexpr int QZP = (QZ + VEC - 1) / VEC * VEC;      // padded row length
@@ -61,12 +62,12 @@ __device__ __forceinline__ void load_row(const T* __restrict__ src, T (&out)[N])
     }
 }
 
-template <int P, typename T, bool LIFT, int V>
-__global__ void __launch_bounds__(PrismTile<P, T, V>::NTHR)
+template <int P, int PZ, typename T, bool LIFT, int V>
+__global__ void __launch_bounds__(PrismTile<P, PZ, T, V>::NTHR)
     k_apply_prism(int E, const int* __restrict__ map, const T* __restrict__ G, const T* __restrict__ refm,
                   const T* __restrict__ x, T* __restrict__ y, const int* __restrict__ skip,
                   const int* __restrict__ elist) {
-    using D = PrismTile<P, T, V>;
+    using D = PrismTile<P, PZ, T, V>;
     constexpr int NT = D::NT, NZ = D::NZ, QT = D::QT, QZ = D::QZ, Np = D::Np, Nq = D::Nq, QZP = D::QZP, EB = D::EB;
     if (skip != nullptr && *skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -214,16 +215,16 @@ __global__ void __launch_bounds__(PrismTile<P, T, V>::NTHR)
     }
 }
 
-template <int P, typename T, bool LIFT, int V>
+template <int P, int PZ, typename T, bool LIFT, int V>
 cudaError_t apply_prism_impl(const Level& L, const T* refm, const T* G, const T* x, T* y, const int* skip,
                              cudaStream_t s) {
-    using D = PrismTile<P, T, V>;
+    using D = PrismTile<P, PZ, T, V>;
     static int per_sm = 0;
     if (per_sm == 0) {
-        cudaError_t err = cudaFuncSetAttribute(k_apply_prism<P, T, LIFT, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)D::SMEM);
+        cudaError_t err = cudaFuncSetAttribute(k_apply_prism<P, PZ, T, LIFT, V>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D::SMEM);
         if (err != cudaSuccess) return err;
-        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_prism<P, T, LIFT, V>, D::NTHR, D::SMEM);
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_prism<P, PZ, T, LIFT, V>, D::NTHR, D::SMEM);
         if (err != cudaSuccess) return err;
         if (per_sm < 1) per_sm = 1;
     }
@@ -235,8 +236,8 @@ cudaError_t apply_prism_impl(const Level& L, const T* refm, const T* G, const T*
     int grid = kSMs * per_sm;
     if (grid > batches) grid = batches;
     if (grid < 1) return cudaSuccess;
-    k_apply_prism<P, T, LIFT, V><<<grid, D::NTHR, D::SMEM, s>>>(E, L.map, G, refm, x, y, skip,
-                                                                sub ? L.lift_elems : nullptr);
+    k_apply_prism<P, PZ, T, LIFT, V><<<grid, D::NTHR, D::SMEM, s>>>(E, L.map, G, refm, x, y, skip,
+                                                                    sub ? L.lift_elems : nullptr);
     return cudaGetLastError();
 }
 
@@ -245,15 +246,23 @@ cudaError_t apply_prism_impl(const Level& L, const T* refm, const T* G, const T*
 template <typename T, bool LIFT, int V>
 static cudaError_t prism_dispatch(const Level& L, const T* refm, const T* G, const T* x, T* y, const int* skip,
                                   cudaStream_t s) {
-    switch (L.p) {
-        case 1: return apply_prism_impl<1, T, LIFT, V>(L, refm, G, x, y, skip, s);
-        case 2: return apply_prism_impl<2, T, LIFT, V>(L, refm, G, x, y, skip, s);
-        case 3: return apply_prism_impl<3, T, LIFT, V>(L, refm, G, x, y, skip, s);
-        case 4: return apply_prism_impl<4, T, LIFT, V>(L, refm, G, x, y, skip, s);
-        case 5: return apply_prism_impl<5, T, LIFT, V>(L, refm, G, x, y, skip, s);
-        case 6: return apply_prism_impl<6, T, LIFT, V>(L, refm, G, x, y, skip, s);
+#define SEM_PRISM_PAIR(a, b) \
+    case (a) * 8 + (b): return apply_prism_impl<a, b, T, LIFT, V>(L, refm, G, x, y, skip, s);
+    switch (L.p * 8 + L.pz) {
+        // isotropic orders
+        SEM_PRISM_PAIR(1, 1) SEM_PRISM_PAIR(2, 2) SEM_PRISM_PAIR(3, 3)
+        SEM_PRISM_PAIR(4, 4) SEM_PRISM_PAIR(5, 5) SEM_PRISM_PAIR(6, 6)
+        // anisotropic orders (vertical order one or two below the triangle order)
+        SEM_PRISM_PAIR(2, 1) SEM_PRISM_PAIR(3, 2) SEM_PRISM_PAIR(3, 1)
+        SEM_PRISM_PAIR(4, 3) SEM_PRISM_PAIR(4, 2) SEM_PRISM_PAIR(5, 4)
+        SEM_PRISM_PAIR(5, 3) SEM_PRISM_PAIR(6, 5) SEM_PRISM_PAIR(6, 4)
         default: return cudaErrorInvalidValue;
     }
+#undef SEM_PRISM_PAIR
+}
+
+bool prism_pair_supported(int p, int pz) {
+    return p >= 1 && p <= 6 && (pz == p || (p >= 2 && (pz == p - 1 || (p >= 3 && pz == p - 2))));
 }
 
 cudaError_t launch_apply_prism64(const Level& L, const double* x, double* y, bool lift, const int* skip, int variant,

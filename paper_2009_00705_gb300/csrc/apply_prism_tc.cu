@@ -489,7 +489,7 @@ __global__ void k_to_bf16_padded(long long E, int QT, int QZ, int QTP, const flo
 }
 
 cudaError_t build_g16(Level& L, cudaStream_t s) {
-    if (L.dim != 3 || !prism_tc_supported(L.p) || L.G32 == nullptr) return cudaSuccess;
+    if (!level_tc(L) || L.G32 == nullptr) return cudaSuccess;
     const int QTP = (L.QT + 1) / 2 * 2;
     const long long n = (long long)L.E * 6 * L.QZ * QTP;
     void* p = L.G16;

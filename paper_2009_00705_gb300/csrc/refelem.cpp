@@ -242,9 +242,10 @@ void tri_lagrange(int p, const double* pts, int npt, std::vector<double>& B,
     }
 }
 
-void RefLevel::build(int dim_, int p_) {
+void RefLevel::build(int dim_, int p_, int pz_) {
     dim = dim_;
     p = p_;
+    pz = (dim_ == 3 && pz_ > 0) ? pz_ : p_;
     NT = (p + 1) * (p + 2) / 2;
     tnodes = tri_nodes(p);
     const int n = p + 1;
@@ -286,9 +287,9 @@ void RefLevel::build(int dim_, int p_) {
         for (int f = 0; f < 3; ++f) face_nodes.push_back(tf[f]);
         return;
     }
-    NZ = p + 1;
-    QZ = p + 1;
-    znodes = gll(p);
+    NZ = pz + 1;
+    QZ = pz + 1;
+    znodes = gll(pz);
     gauss_jacobi(QZ, 0.0, 0.0, zq, zw);
     lagrange1d(znodes, zq.data(), QZ, Bz, Dz);
     Np = NT * NZ;
@@ -300,12 +301,12 @@ void RefLevel::build(int dim_, int p_) {
         face_nodes.push_back(l);
     }
     std::vector<int> bot, top;
-    for (int m = 0; m < NT; ++m) { bot.push_back(m); top.push_back(p * NT + m); }
+    for (int m = 0; m < NT; ++m) { bot.push_back(m); top.push_back(pz * NT + m); }
     face_nodes.push_back(bot);
     face_nodes.push_back(top);
 }
 
-void interp_factors(int dim, int pf, int pc, std::vector<double>& Bt, std::vector<double>& Bz) {
+void interp_factors(int dim, int pf, int pc, int pzf, int pzc, std::vector<double>& Bt, std::vector<double>& Bz) {
     const std::vector<double> fn = tri_nodes(pf);
     const int NTf = (pf + 1) * (pf + 2) / 2;
     std::vector<double> Dr, Ds;
@@ -314,9 +315,9 @@ void interp_factors(int dim, int pf, int pc, std::vector<double>& Bt, std::vecto
         Bz.assign(1, 1.0);
         return;
     }
-    const std::vector<double> zf = gll(pf), zc = gll(pc);
+    const std::vector<double> zf = gll(pzf), zc = gll(pzc);
     std::vector<double> Dz;
-    lagrange1d(zc, zf.data(), pf + 1, Bz, Dz);
+    lagrange1d(zc, zf.data(), pzf + 1, Bz, Dz);
 }
 
 }  // namespace sem

@@ -27,7 +27,7 @@ void lagrange1d(const std::vector<double>& xn, const double* x, int npt,
 
 // Everything the kernels of one order-p level need.
 struct RefLevel {
-    int dim = 3, p = 1;
+    int dim = 3, p = 1, pz = 1;       // triangle order, vertical order (prisms; = p for triangles)
     int NT = 0, NZ = 1, QT = 0, QZ = 1, Np = 0, Nq = 0;
     std::vector<double> tnodes;      // [NT][2]
     std::vector<double> znodes;      // [NZ] GLL
@@ -36,12 +36,13 @@ struct RefLevel {
     std::vector<double> Bt, Drt, Dst; // [QT][NT]
     std::vector<double> Bz, Dz;      // [QZ][NZ]
     std::vector<std::vector<int>> face_nodes;   // local node lists per face
-    void build(int dim, int p);
+    void build(int dim, int p, int pz = 0);   // pz = 0: the same order as p
 };
 
-// Element prolongation (order-pc basis at the order-pf nodes) in tensor factors:
-// triangle part Bt [NT_f][NT_c] and vertical part Bz [NZ_f][NZ_c] ([1] for
-// triangles); I[(kf,nf)][(kc,nc)] = Bt[nf][nc] * Bz[kf][kc].
-void interp_factors(int dim, int pf, int pc, std::vector<double>& Bt, std::vector<double>& Bz);
+// Element prolongation (the coarse basis at the fine nodes) in tensor factors: triangle
+// part Bt [NT_f][NT_c] (orders pf -> pc) and vertical part Bz [NZ_f][NZ_c] (orders
+// pzf -> pzc; [1] for triangles); I[(kf,nf)][(kc,nc)] = Bt[nf][nc] * Bz[kf][kc].
+// Semi-coarsening lowers one of the two orders only.
+void interp_factors(int dim, int pf, int pc, int pzf, int pzc, std::vector<double>& Bt, std::vector<double>& Bz);
 
 }  // namespace sem

@@ -383,11 +383,12 @@ __global__ void __launch_bounds__(kAsmThreads, 6) k_asm_apply(int nsub, const in
 }
 
 // ------------------------------------------------------------ host side
-// Lattice steps of the level's reference element: for every local node, the local
-// nodes whose lattice indices differ by at most one in i, j, i + j and k.
-std::vector<std::vector<int>> lattice_steps(int dim, int p) {
+// Lattice steps of the level's reference element (triangle order p, vertical order pz):
+// for every local node, the local nodes whose lattice indices differ by at most one in
+// i, j, i + j and k.
+std::vector<std::vector<int>> lattice_steps(int dim, int p, int pz) {
     std::vector<int> li, lj, lk;
-    const int nz = dim == 3 ? p + 1 : 1;
+    const int nz = dim == 3 ? pz + 1 : 1;
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j <= p; ++j)
             for (int i = 0; i + j <= p; ++i) {
@@ -506,7 +507,7 @@ sem_status build_asm_level(sem_handle* h, int li) {
     Level& L = h->lv[li];
     const bool fp64 = h->opts.precision == SEM_PREC_FP64;
     const int ell = level_overlap(L.p, h->opts.asm_overlap);
-    const std::vector<std::vector<int>> steps = lattice_steps(L.dim, L.p);
+    const std::vector<std::vector<int>> steps = lattice_steps(L.dim, L.p, L.pz);
     const int Np = L.Np, E = L.E;
     const long long N = L.N;
     // node -> (element, local index) incidence

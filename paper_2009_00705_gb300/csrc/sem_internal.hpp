@@ -24,7 +24,7 @@ struct RefDev {
 };
 
 struct Level {
-    int dim = 3, p = 1;
+    int dim = 3, p = 1, pz = 1;            // triangle order, vertical order (prisms; = p in 2D)
     int NT = 0, NZ = 1, QT = 0, QZ = 1, Np = 0, Nq = 0, ncomp = 6;
     int E = 0;           // elements
     long long N = 0;     // global nodes
@@ -192,6 +192,10 @@ int prism_tile_elements(int P, int variant);
 cudaError_t launch_apply_prism_tc(const Level& L, const float* x, float* y, const int* skip, int* err,
                                   cudaStream_t s);
 bool prism_tc_supported(int p);
+// the tensor-core apply serves isotropic prism levels of order 2..6
+inline bool level_tc(const Level& L) { return L.dim == 3 && L.pz == L.p && prism_tc_supported(L.p); }
+// apply_prism.cu: (triangle order, vertical order) pairs the prism apply is compiled for
+bool prism_pair_supported(int p, int pz);
 cudaError_t build_g16(Level& L, cudaStream_t s);
 // fnpf.cu: surface fields of the free-surface time stepping
 cudaError_t surface_gradient(int ntri, int NT, long long N2, const int* map2, const double* vtri, const double* Drn,

@@ -139,11 +139,12 @@ std::vector<float> to_float(const std::vector<double>& v) {
         }                                                                                 \
     } while (0)
 
-sem_status build_level(sem_handle* h, const sem_mesh* m, int li, int p) {
+sem_status build_level(sem_handle* h, const sem_mesh* m, int li, int p, int pz) {
     Level& L = h->lv[li];
     L.dim = m->dim;
     L.p = p;
-    L.ref.build(m->dim, p);
+    L.pz = (m->dim == 3) ? pz : p;
+    L.ref.build(m->dim, p, L.pz);
     L.NT = L.ref.NT; L.NZ = L.ref.NZ; L.QT = L.ref.QT; L.QZ = L.ref.QZ;
     L.Np = L.ref.Np; L.Nq = L.ref.Nq;
     L.ncomp = (m->dim == 3) ? 6 : 3;
@@ -153,7 +154,7 @@ sem_status build_level(sem_handle* h, const sem_mesh* m, int li, int p) {
     L.N2 = N2;
     const int nl = (m->dim == 3) ? m->nlayers : 1;
     L.E = m->ntri * nl;
-    L.N = (m->dim == 3) ? N2 * (long long)(nl * p + 1) : N2;
+    L.N = (m->dim == 3) ? N2 * (long long)(nl * L.pz + 1) : N2;
     if (L.N >= (1LL << 31) - 1 || (long long)L.E * L.Np >= (1LL << 40)) {
         set_error("mesh too large for 32-bit node ids");
         return SEM_EINVAL;
@@ -163,9 +164,9 @@ sem_status build_level(sem_handle* h, const sem_mesh* m, int li, int p) {
         for (int b = 0; b < m->ntri; ++b)
             for (int l = 0; l < nl; ++l) {
                 const size_t e = (size_t)b * nl + l;
-                for (int k = 0; k <= p; ++k)
+                for (int k = 0; k <= L.pz; ++k)
                     for (int n = 0; n < L.NT; ++n)
-                        gmap[e * L.Np + k * L.NT + n] = (long long)(l * p + k) * N2 + map2[(size_t)b * L.NT + n];
+                        gmap[e * L.Np + k * L.NT + n] = (long long)(l * L.pz + k) * N2 + map2[(size_t)b * L.NT + n];
             }
     } else {
         for (size_t i = 0; i < gmap.size(); ++i) gmap[i] = map2[i];
@@ -391,7 +392,7 @@ sem_status build_transfers(sem_handle* h) {
         Level& F = h->lv[li];
         const Level& C = h->lv[li + 1];
         std::vector<double> Bt, Bz;
-        interp_factors(F.dim, F.p, C.p, Bt, Bz);
+        interp_factors(F.dim, F.p, C.p, F.pz, C.pz, Bt, Bz);
         CK(upload(&F.It64, Bt));
         CK(upload(&F.Iz64, Bz));
         CK(upload(&F.It32, to_float(Bt)));
@@ -405,7 +406,7 @@ sem_status build_transfers(sem_handle* h) {
 sem_status build_surface(sem_handle* h) {
     if (h->dim != 3) { set_error("surface_ops needs a 3D sigma-layer mesh"); return SEM_EINVAL; }
     const Level& L0 = h->lv[0];
-    const long long N2 = L0.N2, k_top = (long long)h->nlayers * h->P;
+    const long long N2 = L0.N2, k_top = (long long)h->nlayers * L0.pz;
     bool top_only = (long long)L0.hdir.size() == N2;
     for (long long i = 0; top_only && i < N2; ++i) top_only = L0.hdir[i] == k_top * N2 + i;
     if (!top_only) {

@@ -22,7 +22,7 @@ const char* last_error();
 void tri_numbering(int nvert, int ntri, const int* tri, int p, std::vector<int>& map2, long long& N2);
 void tri_coords(int ntri, const int* tri, const double* vxy, int p, const std::vector<int>& map2, long long N2,
                 std::vector<double>& xy);
-sem_status build_level(sem_handle* h, const sem_mesh* m, int li, int p);
+sem_status build_level(sem_handle* h, const sem_mesh* m, int li, int p, int pz);
 sem_status build_geometry(sem_handle* h, const sem_mesh* m);
 sem_status build_diagonals(sem_handle* h);
 sem_status build_transfers(sem_handle* h);
@@ -235,7 +235,7 @@ sem_status smooth<double>(sem_handle* h, int li, const double* f, double* u, boo
 // FP32 apply otherwise.  The inner PCG's own products keep the FP32 apply.
 static sem_status apply_vcycle32(sem_handle* h, int li, const float* x, float* y, cudaStream_t s, const int* skip) {
     const Level& L = h->lv[li];
-    if (h->opts.precision != SEM_PREC_MIXED_TF32 || L.dim != 3 || !prism_tc_supported(L.p))
+    if (h->opts.precision != SEM_PREC_MIXED_TF32 || !level_tc(L))
         return apply_level32(h, li, x, y, s, skip);
     CKS(cudaMemsetAsync(y, 0, sizeof(float) * L.N, s));
     const bool timed = timed_begin(h, li, s);
@@ -528,7 +528,7 @@ std::mutex g_tile_mutex;
 cudaError_t tune_prism(Level& L, bool fp32) {
     int bucket = 0;
     while ((1 << (bucket + 1)) <= L.E) ++bucket;
-    const auto key = std::make_tuple(L.p, fp32 ? 4 : 8, bucket);
+    const auto key = std::make_tuple(L.p * 8 + L.pz, fp32 ? 4 : 8, bucket);
     {
         std::lock_guard<std::mutex> lock(g_tile_mutex);
         auto it = g_tile_cache.find(key);
@@ -600,13 +600,44 @@ sem_status check_mesh(const sem_mesh* m, int P) {
     return SEM_OK;
 }
 
+// Vertical order of level li: level_pz[li] when set (prisms), else the triangle order.
+int level_pz(const sem_options& o, int li, int dim) {
+    return (dim == 3 && o.level_pz[li] > 0) ? o.level_pz[li] : o.level_p[li];
+}
+
+// Orders per level: neither order grows from one level to the next and at least one
+// falls (semi-coarsening lowers one direction only); the coarsest level is (1, 1);
+// anisotropic prism levels must be pairs the prism apply is compiled for.
+sem_status check_orders(const sem_options& o, int dim) {
+    for (int i = 0; i < o.nlevels; ++i) {
+        const int p = o.level_p[i], pz = level_pz(o, i, dim);
+        if (dim == 2 && o.level_pz[i] != 0 && o.level_pz[i] != p) {
+            set_error("level_pz: a separate vertical order needs a prism mesh");
+            return SEM_EINVAL;
+        }
+        if (p < 1 || p > 6 || pz < 1 || pz > 6) { set_error("orders in 1..6"); return SEM_EINVAL; }
+        if (dim == 3 && !prism_pair_supported(p, pz)) {
+            set_error("prism orders (" + std::to_string(p) + ", " + std::to_string(pz) +
+                      ") not compiled: the vertical order must equal the triangle order or lie one or two below it");
+            return SEM_EINVAL;
+        }
+        if (i > 0) {
+            const int pp = o.level_p[i - 1], ppz = level_pz(o, i - 1, dim);
+            if (p > pp || pz > ppz || (p == pp && pz == ppz)) {
+                set_error("level orders: neither may grow and one must fall from one level to the next");
+                return SEM_EINVAL;
+            }
+        }
+    }
+    if (level_pz(o, o.nlevels - 1, dim) != 1) { set_error("the coarsest level must be of order (1, 1)"); return SEM_EINVAL; }
+    return SEM_OK;
+}
+
 sem_status check_options(const sem_options& o, int P) {
     if (o.nlevels < 1 || o.nlevels > SEM_MAX_LEVELS || o.level_p[0] != P || o.level_p[o.nlevels - 1] != 1) {
         set_error("levels must run from P down to 1");
         return SEM_EINVAL;
     }
-    for (int i = 1; i < o.nlevels; ++i)
-        if (o.level_p[i] >= o.level_p[i - 1]) { set_error("level orders must decrease"); return SEM_EINVAL; }
     if (o.k_cheb < 1 || o.k_cheb > 15 || o.nu1 < 0 || o.nu2 < 0 || o.lanczos_steps < 1) {
         set_error("smoother parameters out of range");
         return SEM_EINVAL;
@@ -879,6 +910,7 @@ sem_status sem_setup(const sem_mesh* m, int P, const sem_options* opts, sem_hand
     sem_options o;
     if (opts) o = *opts; else sem_default_options(&o, P);
     CKST(check_options(o, P));
+    CKST(check_orders(o, m->dim));
     sem_handle* h = new (std::nothrow) sem_handle();
     if (!h) { set_error("host allocation failed"); return SEM_ENOMEM; }
     h->dim = m->dim;
@@ -892,7 +924,8 @@ sem_status sem_setup(const sem_mesh* m, int P, const sem_options* opts, sem_hand
     h->lv.resize(o.nlevels);
     h->map2.resize(o.nlevels);
     sem_status st = SEM_OK;
-    for (int li = 0; li < o.nlevels && st == SEM_OK; ++li) st = build_level(h, m, li, o.level_p[li]);
+    for (int li = 0; li < o.nlevels && st == SEM_OK; ++li)
+        st = build_level(h, m, li, o.level_p[li], level_pz(o, li, m->dim));
     if (st == SEM_OK) st = build_geometry(h, m);
     if (st == SEM_OK) st = build_diagonals(h);
     if (st == SEM_OK) st = build_transfers(h);
@@ -1036,7 +1069,7 @@ sem_status sem_node_coords(const sem_handle* h, int level, double* xyz) {
             for (int k = 0; k < L0.NT; ++k) v += B[(size_t)n * L0.NT + k] * h->eta2[h->map2[0][(size_t)b * L0.NT + k]];
             eta[h->map2[level][(size_t)b * L.NT + n]] = v;
         }
-    const int nl = h->nlayers, p = L.p;
+    const int nl = h->nlayers, p = L.pz;             // vertical order
     for (int kz = 0; kz <= nl * p; ++kz) {
         int l = kz / p, k = kz - l * p;
         if (l == nl) { l = nl - 1; k = p; }
@@ -1067,8 +1100,8 @@ sem_status sem_apply32(sem_handle* h, int level, const float* x, float* y, int t
     cudaStream_t s = as_stream(stream);
     const Level& L = h->lv[level];
     if (tensor_cores) {
-        if (L.dim != 3 || !prism_tc_supported(L.p)) {
-            set_error("sem_apply32: the tensor-core apply needs a prism level of order 2..6");
+        if (!level_tc(L)) {
+            set_error("sem_apply32: the tensor-core apply needs an isotropic prism level of order 2..6");
             return SEM_EINVAL;
         }
         CKS(cudaMemsetAsync(y, 0, sizeof(float) * L.N, s));
@@ -1198,7 +1231,7 @@ static sem_status fnpf_rhs_impl(sem_handle* h, const double* eta, const double* 
         acc->fnorm = st.fnorm;
     }
     if (rs != SEM_OK) return rs;
-    K(surface_w(N2, L0.NZ, (long long)(h->nlayers - 1) * h->P, h->fs_Dtop, h->depth, h->nlayers, h->fs_phi,
+    K(surface_w(N2, L0.NZ, (long long)(h->nlayers - 1) * L0.pz, h->fs_Dtop, h->depth, h->nlayers, h->fs_phi,
                 h->fs_eta, h->fs_w, s));
     if (!linear) {
         K(surface_gradient(ntri, L0.NT, N2, h->fs_map2, h->fs_vtri, h->fs_Drn, h->fs_Dsn, h->fs_invm, eta, h->fs_ex,
