@@ -247,6 +247,7 @@ def main():
     ap.add_argument("--no-configs", action="store_true")
     ap.add_argument("--no-fnpf", action="store_true")
     ap.add_argument("--no-asm", action="store_true")
+    ap.add_argument("--no-aniso", action="store_true")
     ap.add_argument("--batch-tanks", type=int, default=32,
                     help="random tanks (500-20000 prisms, P in 3..6) for the batched measurement; 0 to skip")
     ap.add_argument("--train-snapshots", type=int, default=60)
@@ -588,6 +589,47 @@ def main():
                         "eta=0.1 sin(x)cos(y); FP64, coarse CG to 1e-10",
             "table": table}
 
+    # anisotropic orders (Section 6): P_xy != P_z on the benchmark mesh, semi-coarsening (lower
+    # P_xy until the orders agree, then both) against standard coarsening (both orders to
+    # ceil((p+1)/2)); and the O(n) sweep of the (5,3) hierarchy over meshes of growing size at
+    # a fixed element aspect ratio d_xy / d_z = 3 (FP64 PCG to 1e-8)
+    aniso = None
+    if not a.no_aniso:
+        aniso = {"pairs": {}, "scaling_53": []}
+
+        def solve_rate(msh, P_, levels, reps=2, **opts):
+            xy_ = sem.sem_mesh_nodes2d(msh, P_)
+            sv = sem.Solver(msh, P_, eta_nodal=msh.eta(xy_[:, 0], xy_[:, 1]), levels=levels,
+                            coarse_rtol=a.coarse_rtol, **opts)
+            C_ = sv.coords(0)
+            d_ = torch.tensor(W.potential3d(*C_[sv.dirichlet_nodes(0)].T), device="cuda")
+            q_ = sv.query(0)
+            p_ = torch.empty(q_["ndof"], dtype=torch.float64, device="cuda")
+            sv.solve(d_, p_, tol=1e-8)
+            torch.cuda.synchronize()
+            t0_ = time.perf_counter()
+            for _ in range(reps):
+                st_ = sv.solve(d_, p_, tol=1e-8)
+            torch.cuda.synchronize()
+            t_ = (time.perf_counter() - t0_) / reps
+            sv.close()
+            dof_ = q_["ndof"] - q_["ndirichlet"]
+            return {"ms_per_solve": t_ * 1e3, "iters": st_["iters"], "dof_free": dof_, "dof_per_s": dof_ / t_,
+                    "elements": q_["nelem"], "levels": [list(x) for x in levels]}
+
+        for (pxy, pz) in ((4, 2), (5, 3), (6, 4)):
+            semi = [(pxy, pz)] + [(q, q) for q in levels_for(pz)]
+            c1 = ((pxy + 2) // 2, (pz + 2) // 2)
+            std = [(pxy, pz), c1] + ([(1, 1)] if c1 != (1, 1) else [])
+            aniso["pairs"][f"{pxy},{pz}"] = {"semi_coarsening": solve_rate(mesh, pxy, semi),
+                                             "standard_coarsening": solve_rate(mesh, pxy, std)}
+        for nn in (8, 16, 32, 64):
+            msh = W.box3d(nn, nn, 4, lx=0.75 * nn, ly=0.75 * nn, eta_modes=[(0.05, 2 * np.pi / 6.0, 0.0, 0.0)])
+            aniso["scaling_53"].append(solve_rate(msh, 5, [(5, 3), (3, 3), (1, 1)]))
+        aniso["form"] = ("FP64 PCG + p-multigrid V-cycle (Chebyshev-Jacobi k=5, nu=1+1) to rtol 1e-8 with anisotropic "
+                         "prisms (P_xy, P_z); semi = P_xy lowered to P_z first, then both; standard = both orders to "
+                         "ceil((p+1)/2); scaling_53: boxes of n x n quads x 4 layers, d_xy = 0.75 = 3 d_z")
+
     learned = None
     if not a.no_learned:
         ls = sem.Solver(mesh, P, eta_nodal=eta, levels=levels_for(P), precision="mixed_fp32", outer="pdc",
@@ -695,7 +737,7 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "mixed_fp32": mixed, "mixed_tf32": mixed_tc, "learned": learned, "batched": batched,
                 "update_eta": update, "other_configs": configs,
-                "fnpf_time_stepping": fnpf, "asm": asm}
+                "fnpf_time_stepping": fnpf, "asm": asm, "anisotropic": aniso}
         print(json.dumps(line), flush=True)
     solver.close()
     if world > 1:
