@@ -10,7 +10,11 @@ order-P geometry map x(xi) = sum_i X_i N^P_i(xi) (the finest order P, also on
 the coarse levels: coarse operators are re-discretised with the finest
 geometry, the "direct assembly" option of Section 4.4).  In 3D the nodes of the
 order-P map are x, y affine over the base triangle and z = -h + sigma (h + eta)
-in sigma layers, which reproduces the sigma-transform of Section 3.1.
+in sigma layers, which reproduces the sigma-transform of Section 3.1.  A mesh may
+instead give curved base triangles (x, y from the blended map of oracle.mesh at the
+order-P nodes) and layer interfaces z_k = a_k + b_k eta (two vertical zones around
+a hull): within layer l the node at local t sits at
+z = (1 - tau) z_l + tau z_{l+1}, tau = (t + 1)/2.
 
 The global matrix is A = sum_e Q_e^T A_e Q_e (COO with duplicates summed).
 """
@@ -19,7 +23,7 @@ from __future__ import annotations
 import numpy as np
 import scipy.sparse as sp
 
-from .mesh import Level
+from .mesh import Level, blended_xy, interfaces
 from .refelem import RefPrism, RefTri, tri_basis
 
 
@@ -41,9 +45,8 @@ class Problem:
         if mesh.dim == 3:
             if eta_nodal is None:
                 eta_nodal = np.zeros(fin.N2)
-                tn = RefTri(self.P).nodes
                 for b in range(mesh.tri.shape[0]):
-                    xy = fin.tri_node_xy(b, tn)
+                    xy = self.base_xy_P(b)
                     eta_nodal[fin.map2[b]] = mesh.eta(xy[:, 0], xy[:, 1])
             self.eta_nodal = np.asarray(eta_nodal, dtype=np.float64)
         else:
@@ -51,6 +54,29 @@ class Problem:
         self._A = {}
 
     # ----------------------------------------------------------- coordinates
+    def general(self) -> bool:
+        """True for meshes with curved base triangles, partial columns or given
+        layer interfaces (the hull tank)."""
+        m = self.mesh
+        return m.dim == 3 and (m.edge_arc is not None or m.col_layers is not None or m.z_iface is not None)
+
+    def base_xy_P(self, b: int) -> np.ndarray:
+        """(x, y) of the order-P nodes of base triangle b [NT_P, 2]."""
+        tn = RefTri(self.P).nodes
+        if self.mesh.dim == 3 and self.mesh.edge_arc is not None:
+            return blended_xy(self.mesh, b, tn)
+        return self.levels[0].tri_node_xy(b, tn)
+
+    def base_xy(self, li: int, b: int) -> np.ndarray:
+        """(x, y) of level li's 2D nodes in base triangle b: the order-P map (the
+        interpolant of the order-P nodes) at the level's nodes."""
+        lev = self.levels[li]
+        tn = RefTri(lev.p).nodes
+        if self.mesh.dim == 3 and self.mesh.edge_arc is not None:
+            B, _, _ = tri_basis(self.P, tn)
+            return B @ self.base_xy_P(b)
+        return lev.tri_node_xy(b, tn)
+
     def eta_at_level(self, li: int) -> np.ndarray:
         """eta_P (the order-P surface interpolant) at level li's 2D nodes."""
         lev, fin = self.levels[li], self.levels[0]
@@ -66,25 +92,33 @@ class Problem:
         """Physical coordinates [N, dim] of level li's global nodes; in 3D
         z = -h + sigma (h + eta_P) at the node."""
         lev, mesh = self.levels[li], self.mesh
-        tn = RefTri(lev.p).nodes
         xy2 = np.zeros((lev.N2, 2))
         for b in range(mesh.tri.shape[0]):
-            xy2[lev.map2[b]] = lev.tri_node_xy(b, tn)
+            xy2[lev.map2[b]] = self.base_xy(li, b)
         if self.dim == 2:
             return xy2
         eta2 = self.eta_at_level(li)
         zn = RefPrism(lev.p, lev.pz).zn
         nl, h = mesh.nlayers, mesh.depth
+        zif = interfaces(mesh)
         out = np.zeros((lev.N, 3))
         for kz in range(nl * lev.pz + 1):
             l, k = divmod(kz, lev.pz)
             if l == nl:
                 l, k = nl - 1, lev.pz
-            sigma = (l + (zn[k] + 1.0) / 2.0) / nl
             sl = slice(kz * lev.N2, (kz + 1) * lev.N2)
             out[sl, :2] = xy2
-            out[sl, 2] = -h + sigma * (h + eta2)
+            out[sl, 2] = self._z(l, zn[k], eta2, zif)
         return out
+
+    def _z(self, l, t, eta, zif):
+        """z of the point at local t in layer l over surface elevation eta."""
+        mesh = self.mesh
+        if not self.general():
+            nl, h = mesh.nlayers, mesh.depth
+            return -h + (l + (t + 1.0) / 2.0) / nl * (h + eta)
+        tau = (t + 1.0) / 2.0
+        return ((1 - tau) * (zif[l, 0] + zif[l, 1] * eta) + tau * (zif[l + 1, 0] + zif[l + 1, 1] * eta))
 
     # ----------------------------------------------------------- geometry
     def element_nodes_P(self, elements=None) -> np.ndarray:
@@ -99,17 +133,17 @@ class Problem:
                 X[i] = fin.tri_node_xy(b, tn)
             return X
         ref = RefPrism(P)
-        nl, h = mesh.nlayers, mesh.depth
+        cb, cl = mesh.columns()
+        zif = interfaces(mesh)
         X = np.empty((elems.size, ref.Np, 3))
         for i, e in enumerate(elems):
-            b, l = divmod(int(e), nl)
-            xy = fin.tri_node_xy(b, tn)
+            b, l = int(cb[e]), int(cl[e])
+            xy = self.base_xy_P(b)
             eta = self.eta_nodal[fin.map2[b]]
             for k in range(P + 1):
-                sigma = (l + (ref.zn[k] + 1.0) / 2.0) / nl
                 sl = slice(k * ref.NT, (k + 1) * ref.NT)
                 X[i, sl, :2] = xy
-                X[i, sl, 2] = -h + sigma * (h + eta)
+                X[i, sl, 2] = self._z(l, ref.zn[k], eta, zif)
         return X
 
     def jacobians(self, li: int, elements=None) -> np.ndarray:

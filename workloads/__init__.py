@@ -16,8 +16,10 @@ its own meshes, which are not available here:
 Face numbering follows the element conventions used by both the oracle and
 the CUDA library: triangle faces f0=(v0,v1), f1=(v1,v2), f2=(v2,v0); prism
 faces f0..f2 are the lateral quads over those edges, f3 the bottom (t=-1) and
-f4 the top (t=+1) triangle.  Prism e sits in column b = e // nlayers and layer
-l = e % nlayers (layer 0 at the bottom).
+f4 the top (t=+1) triangle.  Prisms are numbered column by column, bottom up:
+on a full mesh prism e sits in column b = e // nlayers and layer l = e % nlayers
+(layer 0 at the bottom); a mesh with ``col_layers`` (the hull tank) holds layers
+0 .. col_layers[b]-1 over base triangle b.
 """
 from __future__ import annotations
 
@@ -37,6 +39,13 @@ class Mesh:
     dim == 3: prisms extruded in ``nlayers`` sigma layers over the base
     triangulation; ``vxy`` holds (x, y); flat bottom z = -depth; the free
     surface is z = eta(x, y) given by ``eta_modes``.
+
+    Optional 3D fields (all None on the plain sigma-layer meshes):
+    ``col_layers`` [ntri]: layers present over each base triangle (from the bottom);
+    ``z_iface`` [nlayers+1, 2]: layer interface k lies at z = a_k + b_k eta(x, y)
+    (None: sigma layers, a_k = -depth (1 - k/nlayers), b_k = k/nlayers);
+    ``edge_arc`` [ntri, 3, 3]: per base edge f (f0=(v0,v1), f1=(v1,v2), f2=(v2,v0))
+    the circle (cx, cy, R) the edge follows between its vertices, R = 0 straight.
     """
     dim: int
     vxy: np.ndarray              # [nvert, 2] float64
@@ -45,10 +54,25 @@ class Mesh:
     depth: float = 1.0
     eta_modes: list = field(default_factory=list)   # [(a, kx, ky, phase)]: eta = sum a*cos(kx*x+ky*y+phase)
     face_bc: np.ndarray | None = None               # [nelem, nfaces] int8, 1 = Dirichlet
+    col_layers: np.ndarray | None = None            # [ntri] int32
+    z_iface: np.ndarray | None = None               # [nlayers+1, 2] float64
+    edge_arc: np.ndarray | None = None              # [ntri, 3, 3] float64
 
     @property
     def nelem(self) -> int:
+        if self.dim == 3 and self.col_layers is not None:
+            return int(np.sum(self.col_layers))
         return int(self.tri.shape[0]) * (self.nlayers if self.dim == 3 else 1)
+
+    def columns(self):
+        """(base triangle, layer) of every prism in element order (3D only)."""
+        ntri = int(self.tri.shape[0])
+        col = (np.full(ntri, self.nlayers, dtype=np.int64) if self.col_layers is None
+               else np.asarray(self.col_layers, dtype=np.int64))
+        b = np.repeat(np.arange(ntri), col)
+        start = np.concatenate([[0], np.cumsum(col)[:-1]])
+        l = np.arange(int(col.sum())) - np.repeat(start, col)
+        return b, l
 
     @property
     def nfaces(self) -> int:
@@ -190,24 +214,152 @@ def random_tank(i: int, count_range=(500, 20000)):
 def all_boundary_dirichlet(mesh: Mesh) -> Mesh:
     """Flag every boundary face of ``mesh`` Dirichlet (used for exact-reproduction tests).
 
-    2D: edges used by a single triangle.  3D: bottom and top faces of the bottom /
-    top layer, and lateral faces over base edges used by a single triangle."""
-    from collections import Counter
+    2D: edges used by a single triangle.  3D: the bottom face of every column's lowest
+    prism, the top face of its highest prism, and the lateral faces over base edges used
+    by a single triangle or whose neighbour column is lower than the prism's layer."""
     tri = mesh.tri
-    cnt = Counter()
-    for (v0, v1, v2) in tri:
+    owners: dict = {}
+    for t, (v0, v1, v2) in enumerate(tri):
         for (a, b) in ((v0, v1), (v1, v2), (v2, v0)):
-            cnt[(min(a, b), max(a, b))] += 1
+            owners.setdefault((min(a, b), max(a, b)), []).append(t)
     nf = mesh.nfaces
     fb = np.zeros((mesh.nelem, nf), dtype=np.int8)
-    nl = mesh.nlayers if mesh.dim == 3 else 1
-    for bidx, (v0, v1, v2) in enumerate(tri):
+    if mesh.dim == 2:
+        for t, (v0, v1, v2) in enumerate(tri):
+            for f, (a, b) in enumerate(((v0, v1), (v1, v2), (v2, v0))):
+                if len(owners[(min(a, b), max(a, b))]) == 1:
+                    fb[t, f] = 1
+        mesh.face_bc = fb
+        return mesh
+    cb, cl = mesh.columns()
+    ntri = tri.shape[0]
+    col = np.bincount(cb, minlength=ntri)
+    for e in range(cb.size):
+        t, l = int(cb[e]), int(cl[e])
+        v0, v1, v2 = tri[t]
         for f, (a, b) in enumerate(((v0, v1), (v1, v2), (v2, v0))):
-            if cnt[(min(a, b), max(a, b))] == 1:
-                for l in range(nl):
-                    fb[bidx * nl + l, f] = 1
-        if mesh.dim == 3:
-            fb[bidx * nl, 3] = 1
-            fb[bidx * nl + nl - 1, 4] = 1
+            nb = [o for o in owners[(min(a, b), max(a, b))] if o != t]
+            if not nb or col[nb[0]] <= l:
+                fb[e, f] = 1
+        if l == 0:
+            fb[e, 3] = 1
+        if l == col[t] - 1:
+            fb[e, 4] = 1
     mesh.face_bc = fb
     return mesh
+
+
+# ---------------------------------------------------------------- hull tank
+def _hull_axis(n: int, lo: float, hi: float, rc: float, length: float) -> np.ndarray:
+    """n+1 grid coordinates on [0, length] with lines at lo, lo+rc, hi-rc, hi: about
+    uniform cells, at least one cell per segment, the two corner segments alike."""
+    c = max(1, int(round(n * rc / length)))
+    m = max(1, int(round(n * (hi - lo - 2 * rc) / length)))
+    if (n - 2 * c - m) % 2:
+        m += 1
+    o = (n - 2 * c - m) // 2
+    if o < 1:
+        raise ValueError("grid too coarse for the hull footprint")
+    segs = [(0.0, lo, o), (lo, lo + rc, c), (lo + rc, hi - rc, m), (hi - rc, hi, c), (hi, length, o)]
+    pts = [np.linspace(a, b, k + 1)[:-1] for (a, b, k) in segs]
+    return np.concatenate(pts + [np.array([length])])
+
+
+def eta_powerlaw(nmodes: int = 32, seed: int = SEED, kmax: int = 8, amax: float = 0.1):
+    """Free surface as ``nmodes`` cosine modes with integer wavevectors (kx in 0..kmax,
+    ky in -kmax..kmax, not both zero), amplitudes proportional to |k|^-1.5, uniform
+    random phases; scaled so that sum |a| = amax (hence max |eta| <= amax)."""
+    rng = np.random.default_rng(seed)
+    modes = []
+    while len(modes) < nmodes:
+        kx = int(rng.integers(0, kmax + 1))
+        ky = int(rng.integers(-kmax, kmax + 1))
+        if kx == 0 and ky == 0:
+            continue
+        modes.append((math.hypot(kx, ky) ** -1.5, float(kx), float(ky), float(rng.uniform(0, 2 * math.pi))))
+    tot = sum(a for a, _, _, _ in modes)
+    return [(a * amax / tot, kx, ky, ph) for (a, kx, ky, ph) in modes]
+
+
+def hull_tank(n: int = 64, length: float = 2 * math.pi, depth: float = 1.0, hull_len: float = 0.3,
+              hull_width: float = 0.1, corner: float = 0.25, draft: float = 0.3, nl_lower: int = 2,
+              nl_upper: int = 2, eta_modes=None) -> Mesh:
+    """Wave tank [0, L]^2 x [-depth, eta] with a surface-piercing rounded-box hull.
+
+    The hull's footprint is centred, ``hull_len`` L long in x and ``hull_width`` L wide
+    in y, its corners rounded with radius ``corner`` x width; it reaches ``draft`` x depth
+    below z = 0.  Two vertical zones: the lower zone [-depth, -draft] in ``nl_lower`` flat
+    layers everywhere; the upper zone [-draft, eta] in ``nl_upper`` sigma layers outside
+    the footprint only (the hull is cut out).  The n x n base grid is graded so that grid
+    lines run along the footprint's straight sides and the corner arcs' end points; the
+    footprint-boundary vertices inside each corner square are moved radially onto the
+    arc, and the footprint-boundary edges between two arc points follow the arc.
+    Dirichlet on the free surface (top faces of full columns); homogeneous Neumann on the
+    bottom, the tank walls and the hull (its sides and its bottom)."""
+    xa, xb = 0.5 * length * (1 - hull_len), 0.5 * length * (1 + hull_len)
+    ya, yb = 0.5 * length * (1 - hull_width), 0.5 * length * (1 + hull_width)
+    rc = corner * hull_width * length
+    xs = _hull_axis(n, xa, xb, rc, length)
+    ys = _hull_axis(n, ya, yb, rc, length)
+    nx, ny = len(xs) - 1, len(ys) - 1
+    X, Y = np.meshgrid(xs, ys, indexing="xy")
+    vxy = np.stack([X.ravel(), Y.ravel()], axis=1).astype(np.float64)
+    tri, infoot = [], []
+    tol = 1e-9 * length
+    for j in range(ny):
+        for i in range(nx):
+            a = j * (nx + 1) + i
+            b, d = a + 1, a + (nx + 1)
+            c = d + 1
+            foot = xs[i] >= xa - tol and xs[i + 1] <= xb + tol and ys[j] >= ya - tol and ys[j + 1] <= yb + tol
+            tri += [(a, b, c), (a, c, d)]
+            infoot += [foot, foot]
+    tri = np.asarray(tri, dtype=np.int32)
+    infoot = np.asarray(infoot)
+    # corners: (corner point, arc centre)
+    corners = [((xa, ya), (xa + rc, ya + rc)), ((xb, ya), (xb - rc, ya + rc)),
+               ((xb, yb), (xb - rc, yb - rc)), ((xa, yb), (xa + rc, yb - rc))]
+    on_side = (((np.abs(vxy[:, 0] - xa) < tol) | (np.abs(vxy[:, 0] - xb) < tol)) & (vxy[:, 1] > ya - tol)
+               & (vxy[:, 1] < yb + tol)) | (((np.abs(vxy[:, 1] - ya) < tol) | (np.abs(vxy[:, 1] - yb) < tol))
+                                             & (vxy[:, 0] > xa - tol) & (vxy[:, 0] < xb + tol))
+    for (K, C) in corners:
+        inside = on_side & (np.abs(vxy[:, 0] - K[0]) < rc - tol) & (np.abs(vxy[:, 1] - K[1]) < rc - tol)
+        for v in np.flatnonzero(inside):
+            d = vxy[v] - np.asarray(C)
+            vxy[v] = np.asarray(C) + rc * d / np.linalg.norm(d)
+    owners: dict = {}
+    for t, (v0, v1, v2) in enumerate(tri):
+        for (a, b) in ((v0, v1), (v1, v2), (v2, v0)):
+            owners.setdefault((min(a, b), max(a, b)), []).append(t)
+    arc = np.zeros((tri.shape[0], 3, 3))
+    for t, (v0, v1, v2) in enumerate(tri):
+        for f, (a, b) in enumerate(((v0, v1), (v1, v2), (v2, v0))):
+            own = owners[(min(a, b), max(a, b))]
+            if len(own) != 2 or infoot[own[0]] == infoot[own[1]]:
+                continue
+            for (K, C) in corners:
+                near = all(abs(vxy[v, 0] - K[0]) <= rc + tol and abs(vxy[v, 1] - K[1]) <= rc + tol
+                           and abs(np.linalg.norm(vxy[v] - np.asarray(C)) - rc) < tol for v in (a, b))
+                if near:
+                    arc[t, f] = (C[0], C[1], rc)
+    nl = nl_lower + nl_upper
+    col = np.where(infoot, nl_lower, nl).astype(np.int32)
+    zif = np.zeros((nl + 1, 2))
+    for k in range(nl_lower + 1):
+        zif[k] = (-depth + k * (depth - draft * depth) / nl_lower, 0.0)
+    for k in range(1, nl_upper + 1):
+        zif[nl_lower + k] = (-draft * depth * (1.0 - k / nl_upper), k / nl_upper)
+    m = Mesh(dim=3, vxy=vxy, tri=tri, nlayers=nl, depth=depth, eta_modes=list(eta_modes or []),
+             col_layers=col, z_iface=zif, edge_arc=arc)
+    cb, cl = m.columns()
+    fb = np.zeros((m.nelem, 5), dtype=np.int8)
+    fb[(cl == nl - 1), 4] = 1
+    m.face_bc = fb
+    return m
+
+
+def config_hull(n: int = 64) -> Mesh:
+    """The learned-smoother tank: 64 x 64 base grid, rounded-box hull 0.3 L long, 0.1 L
+    wide, corner radius a quarter of the width, draft 0.3 h, 2 + 2 layers; eta a sum of
+    32 cosine modes with power-law amplitudes (max |eta| <= 0.1 h)."""
+    return hull_tank(n, eta_modes=eta_powerlaw(32))
