@@ -248,6 +248,7 @@ def main():
     ap.add_argument("--no-fnpf", action="store_true")
     ap.add_argument("--no-asm", action="store_true")
     ap.add_argument("--no-aniso", action="store_true")
+    ap.add_argument("--no-hull", action="store_true")
     ap.add_argument("--batch-tanks", type=int, default=32,
                     help="random tanks (500-20000 prisms, P in 3..6) for the batched measurement; 0 to skip")
     ap.add_argument("--train-snapshots", type=int, default=60)
@@ -662,6 +663,57 @@ def main():
         ls.close()
         ps.close()
 
+    # the learned smoother's own tank: rounded-box hull cutout (0.3 L x 0.1 L, draft 0.3 h, curved
+    # corners), 64 x 64 base grid, 2 + 2 layers, eta = 32 power-law cosine modes, P = 6
+    hull = None
+    if not a.no_hull:
+        hm = W.config_hull(n)
+        hxy = sem.sem_mesh_nodes2d(hm, P)
+        heta = hm.eta(hxy[:, 0], hxy[:, 1])
+
+        def hull_rate(reps=2, train=False, **opts):
+            sv = sem.Solver(hm, P, eta_nodal=heta, levels=levels_for(P), coarse_rtol=a.coarse_rtol, imax=400, **opts)
+            C_ = sv.coords(0)
+            d_ = torch.tensor(W.potential3d(*C_[sv.dirichlet_nodes(0)].T), device="cuda")
+            q_ = sv.query(0)
+            p_ = torch.empty(q_["ndof"], dtype=torch.float64, device="cuda")
+            extra = {}
+            if train:
+                torch.cuda.synchronize()
+                t0_ = time.perf_counter()
+                l0_, l1_ = sv.train(a.train_snapshots, a.train_steps, lr=1e-3, seed=7)
+                torch.cuda.synchronize()
+                extra["training"] = {"snapshots": a.train_snapshots, "steps_per_snapshot": a.train_steps,
+                                     "seconds": time.perf_counter() - t0_, "heldout_loss_before": l0_,
+                                     "heldout_loss_after": l1_}
+            sv.solve(d_, p_, tol=1e-8)
+            torch.cuda.synchronize()
+            t0_ = time.perf_counter()
+            for _ in range(reps):
+                st_ = sv.solve(d_, p_, tol=1e-8)
+            torch.cuda.synchronize()
+            t_ = (time.perf_counter() - t0_) / reps
+            sv.close()
+            dof_ = q_["ndof"] - q_["ndirichlet"]
+            out = {"ms_per_solve": t_ * 1e3, "iters": st_["iters"], "dof_per_s": dof_ / t_,
+                   "learned_accepts": st_["learned_accepts"], "learned_fallbacks": st_["learned_fallbacks"]}
+            out.update(extra)
+            return out, p_.cpu().numpy(), q_
+
+        r64, u64, hq = hull_rate()
+        rl, ul, _ = hull_rate(train=True, precision="mixed_fp32", outer="pdc", smoother="learned")
+        rp, up, _ = hull_rate(precision="mixed_fp32", outer="pdc")
+        rt, ut, _ = hull_rate(precision="mixed_tf32", outer="pdc", inner_imax=a.inner_imax, inner_rtol=a.inner_rtol)
+        den = np.abs(u64).max()
+        for r_, u_ in ((rl, ul), (rp, up), (rt, ut)):
+            r_["max_rel_diff_vs_fp64_solution"] = float(np.abs(u_ - u64).max() / den)
+        hull = {"workload": f"hull tank {n}x{n} base grid, 2+2 layers, rounded-box hull, P={P}",
+                "elements": hq["nelem"], "dof_free": hq["ndof"] - hq["ndirichlet"],
+                "fp64_pcg": r64, "learned_pdc": rl, "same_cycle_without_network": rp, "mixed_tf32_pdc_inner_pcg": rt,
+                "form": "rtol 1e-8; learned: FP64 defect correction around the FP32 V-cycle whose first "
+                        "finest-level post-smoothing sweep is the trained MLP (hidden 256, BF16 weights), kept when "
+                        "it lowers the residual enough, else the Chebyshev sweep"}
+
     batched = None
     if a.batch_tanks > 0:
         tanks = []
@@ -737,7 +789,7 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "mixed_fp32": mixed, "mixed_tf32": mixed_tc, "learned": learned, "batched": batched,
                 "update_eta": update, "other_configs": configs,
-                "fnpf_time_stepping": fnpf, "asm": asm, "anisotropic": aniso}
+                "fnpf_time_stepping": fnpf, "asm": asm, "anisotropic": aniso, "hull": hull}
         print(json.dumps(line), flush=True)
     solver.close()
     if world > 1:

@@ -80,7 +80,31 @@ typedef enum { SEM_SMOOTH_CHEBYSHEV = 0, SEM_SMOOTH_LEARNED = 1, SEM_SMOOTH_ASM 
  *      canonical order (see sem_mesh_nodes2d), or NULL for a flat surface.
  * face_bc: [nelem][nfaces] flags, 1 = Dirichlet (phi = phi~), 0 = homogeneous
  *      Neumann or interior.  Triangle faces: f0=(v0,v1), f1=(v1,v2), f2=(v2,v0).
- *      Prism faces: f0..f2 lateral quads over those edges, f3 bottom, f4 top. */
+ *      Prism faces: f0..f2 lateral quads over those edges, f3 bottom, f4 top.
+ *
+ * Optional dim-3 fields for a tank with a surface-piercing body (all NULL for the
+ * plain sigma-layer mesh above; NULL fields keep its rule):
+ * col_layers: [ntri], 1..nlayers: the prisms over base triangle b are its layers
+ *      0 .. col_layers[b]-1; prisms are numbered column by column, bottom up, so
+ *      nelem = sum col_layers.  Node ids keep the layout kz * N2 + g2; ids that lie
+ *      in no prism (above a body) are identity rows of every operator and are listed
+ *      with the Dirichlet nodes (their phi~ is copied through unchanged).
+ * z_iface: [nlayers+1][2] (a_k, b_k): layer interface k lies at z = a_k + b_k eta(x, y)
+ *      and the node at local t in [-1, 1] of layer l at
+ *      z = (1 - tau) z_l + tau z_{l+1}, tau = (t + 1)/2 (NULL: the sigma layers,
+ *      a_k = -depth (1 - k/nlayers), b_k = k/nlayers).  Two zones around a hull: flat
+ *      interfaces (b = 0) below its draft, sigma interfaces above.  Every layer must
+ *      keep a positive thickness at every surface node.
+ * edge_arc: [ntri][3][3]: for base edge f of triangle b (faces as above) the circle
+ *      (cx, cy, R) the edge follows between its two vertices (both on the circle,
+ *      at most a quarter turn apart), R = 0 for a straight edge.  The base triangle's
+ *      map is the affine map plus, per curved edge (a, b), the edge's displacement
+ *      from its chord times 4 l_a l_b / (1 - xi^2), xi = l_b - l_a (l barycentric),
+ *      the arc point taken at angle theta_a + (1 + xi)/2 (theta_b - theta_a) (the
+ *      triangle blending map of Szabo and Babuska, Finite Element Analysis, Ch. 6);
+ *      the element geometry is its order-P interpolant (isoparametric).
+ * sem_update_eta works on such meshes; the free-surface operators (surface_ops)
+ * need the plain sigma-layer mesh. */
 typedef struct {
     int dim;
     int nvert;
@@ -91,6 +115,9 @@ typedef struct {
     double depth;               /* dim 3 only (> 0) */
     const double* eta;          /* dim 3 only, [N2 at order P] or NULL */
     const signed char* face_bc; /* [nelem][nfaces] */
+    const int* col_layers;      /* dim 3 only, [ntri] or NULL */
+    const double* z_iface;      /* dim 3 only, [nlayers+1][2] or NULL */
+    const double* edge_arc;     /* dim 3 only, [ntri][3][3] or NULL */
 } sem_mesh;
 
 /* Solver options; fill with sem_default_options and adjust.
@@ -191,9 +218,10 @@ typedef struct sem_handle sem_handle;
 void sem_default_options(sem_options* opts, int P);
 
 /* Canonical order-p 2D node coordinates of the triangle mesh in `mesh`
- * (x, z for dim 2; x, y of the base mesh for dim 3).  Pass xy = NULL to get the
- * count in *n2 only; otherwise xy must hold 2 * (*n2) doubles.  Host only,
- * synchronous.  This is where the caller samples eta before sem_setup. */
+ * (x, z for dim 2; x, y of the base mesh for dim 3; with edge_arc, the blended map
+ * at the order-p reference nodes).  Pass xy = NULL to get the count in *n2 only;
+ * otherwise xy must hold 2 * (*n2) doubles.  Host only, synchronous.  This is where
+ * the caller samples eta before sem_setup. */
 sem_status sem_mesh_nodes2d(const sem_mesh* mesh, int p, long long* n2, double* xy);
 
 /* Build every level (numbering, geometric factors, Jacobi diagonals, Chebyshev
@@ -206,8 +234,9 @@ void sem_destroy(sem_handle* h);
 sem_status sem_query(const sem_handle* h, int level, long long* ndof, long long* ndirichlet,
                      long long* nelem, int* np);
 /* Host copies: Dirichlet node ids (ascending; the order of dirichlet_eta),
- * node coordinates [N][dim], the element map [E][Np] (global ids), the
- * lambda_hat estimate of every level (coarsest entry 0). */
+ * node coordinates [N][dim] (x, y of a level of order p < P on curved base
+ * triangles: the order-P geometry interpolated at the level's nodes), the element
+ * map [E][Np] (global ids), the lambda_hat estimate of every level (coarsest entry 0). */
 sem_status sem_dirichlet_nodes(const sem_handle* h, int level, long long* idx_host);
 sem_status sem_node_coords(const sem_handle* h, int level, double* xyz_host);
 sem_status sem_element_map(const sem_handle* h, int level, int* map_host);

@@ -36,7 +36,8 @@ EXPORTS = ("sem_default_options", "sem_mesh_nodes2d", "sem_setup", "sem_destroy"
 class SemMesh(Structure):
     _fields_ = [("dim", c_int), ("nvert", c_int), ("vxy", POINTER(c_double)), ("ntri", c_int),
                 ("tri", POINTER(c_int)), ("nlayers", c_int), ("depth", c_double),
-                ("eta", POINTER(c_double)), ("face_bc", POINTER(c_byte))]
+                ("eta", POINTER(c_double)), ("face_bc", POINTER(c_byte)), ("col_layers", POINTER(c_int)),
+                ("z_iface", POINTER(c_double)), ("edge_arc", POINTER(c_double))]
 
 
 class SemOptions(Structure):
@@ -173,10 +174,21 @@ class _MeshArgs:
         self.tri = np.ascontiguousarray(mesh.tri, dtype=np.int32)
         self.fb = np.ascontiguousarray(mesh.face_bc, dtype=np.int8)
         self.eta = None if eta_nodal is None else np.ascontiguousarray(eta_nodal, dtype=np.float64)
+
+        def opt(name, dtype):
+            v = getattr(mesh, name, None)
+            return None if v is None else np.ascontiguousarray(v, dtype=dtype)
+
+        self.col = opt("col_layers", np.int32)
+        self.zif = opt("z_iface", np.float64)
+        self.arc = opt("edge_arc", np.float64)
         self.s = SemMesh(int(mesh.dim), int(self.vxy.shape[0]), _dptr(self.vxy, c_double), int(self.tri.shape[0]),
                          _dptr(self.tri, c_int), int(getattr(mesh, "nlayers", 0) or 0),
                          float(getattr(mesh, "depth", 1.0)),
-                         _dptr(self.eta, c_double) if self.eta is not None else None, _dptr(self.fb, c_byte))
+                         _dptr(self.eta, c_double) if self.eta is not None else None, _dptr(self.fb, c_byte),
+                         _dptr(self.col, c_int) if self.col is not None else None,
+                         _dptr(self.zif, c_double) if self.zif is not None else None,
+                         _dptr(self.arc, c_double) if self.arc is not None else None)
 
 
 # ---------------------------------------------------------------- C ABI, same names

@@ -252,6 +252,63 @@ __global__ void k_geom_prism(int E, int nlayers, int QT, int QZ, int NTP, double
     }
 }
 
+// Prisms of a general mesh (curved base triangles, partial columns, given layer interfaces):
+// x, y = the order-P interpolant of the base triangle's node xy; in layer l
+// z = (1 - tau) z_l + tau z_{l+1}, tau = (t + 1)/2, z_k = a_k + b_k eta_P.  The Jacobian keeps
+// the block form [[M, 0], [z_r z_s, z_t]] with M = d(x, y)/d(r, s) now varying over the element.
+__global__ void k_geom_prism_general(int E, const int* __restrict__ eb, const int* __restrict__ el, int QT, int QZ,
+                                     int NTP, const double* __restrict__ xyP, const double* __restrict__ etaP,
+                                     const double* __restrict__ zif, const double* __restrict__ BP,
+                                     const double* __restrict__ DrP, const double* __restrict__ DsP,
+                                     const double* __restrict__ qinfo, double* __restrict__ G,
+                                     float* __restrict__ G32) {
+    const int Nq = QT * QZ;
+    const long long total = (long long)E * Nq;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int e = (int)(t / Nq), q = (int)(t - (long long)e * Nq);
+        const int qz = q / QT, qt = q - qz * QT;
+        const int b = eb[e], l = el[e];
+        const double* xy = xyP + 2 * (size_t)b * NTP;
+        const double* et = etaP + (size_t)b * NTP;
+        double m00 = 0, m01 = 0, m10 = 0, m11 = 0, eta = 0, er = 0, es = 0;
+        for (int n = 0; n < NTP; ++n) {
+            const double dr = DrP[qt * NTP + n], ds = DsP[qt * NTP + n], bb = BP[qt * NTP + n];
+            m00 += dr * xy[2 * n];
+            m01 += ds * xy[2 * n];
+            m10 += dr * xy[2 * n + 1];
+            m11 += ds * xy[2 * n + 1];
+            eta += bb * et[n];
+            er += dr * et[n];
+            es += ds * et[n];
+        }
+        const double tw = qinfo[qt], zq = qinfo[QT + qz], zw = qinfo[QT + QZ + qz];
+        const double tau = 0.5 * (zq + 1.0);
+        const double a0 = zif[2 * l], b0 = zif[2 * l + 1], a1 = zif[2 * l + 2], b1 = zif[2 * l + 3];
+        const double bl = (1.0 - tau) * b0 + tau * b1;
+        const double zr = bl * er, zs = bl * es, zt = 0.5 * ((a1 - a0) + (b1 - b0) * eta);
+        const double a2 = m00 * m11 - m01 * m10;
+        const double i00 = m11 / a2, i01 = -m01 / a2, i10 = -m10 / a2, i11 = m00 / a2;
+        const double gr[3] = {i00, i01, 0.0};
+        const double gs[3] = {i10, i11, 0.0};
+        const double gt[3] = {-(zr * i00 + zs * i10) / zt, -(zr * i01 + zs * i11) / zt, 1.0 / zt};
+        const double wdet = tw * zw * fabs(zt * a2);
+        const double c[6] = {
+            wdet * (gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]),
+            wdet * (gr[0] * gs[0] + gr[1] * gs[1] + gr[2] * gs[2]),
+            wdet * (gr[0] * gt[0] + gr[1] * gt[1] + gr[2] * gt[2]),
+            wdet * (gs[0] * gs[0] + gs[1] * gs[1] + gs[2] * gs[2]),
+            wdet * (gs[0] * gt[0] + gs[1] * gt[1] + gs[2] * gt[2]),
+            wdet * (gt[0] * gt[0] + gt[1] * gt[1] + gt[2] * gt[2])};
+        double* Ge = G + (size_t)e * 6 * Nq;
+        float* Ge32 = G32 + (size_t)e * 6 * Nq;
+        for (int k = 0; k < 6; ++k) {
+            Ge[k * Nq + q] = c[k];
+            Ge32[k * Nq + q] = (float)c[k];
+        }
+    }
+}
+
 // Straight triangle in the (x, z) plane: constant Jacobian M, G = w |det M| M^{-1} M^{-T}.
 __global__ void k_geom_tri(int E, int QT, const double* __restrict__ vtri, const double* __restrict__ qinfo,
                            double* __restrict__ G, float* __restrict__ G32) {
@@ -1106,6 +1163,28 @@ cudaError_t launch_geometry(Level& L, const double* vtri, const double* etaP, co
                                               L.G32);
         else
             k_geom_tri<<<grid, 256, 0, s>>>(L.E, L.QT, vtri, dq, L.G, L.G32);
+        err = cudaGetLastError();
+    }
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    cudaFree(dq);
+    return err != cudaSuccess ? err : e2;
+}
+
+cudaError_t launch_geometry_general(Level& L, const int* eb, const int* el, const double* xyP, const double* etaP,
+                                    const double* zif, const double* BP, const double* DrP, const double* DsP,
+                                    int NTP, cudaStream_t s) {
+    std::vector<double> qi(L.ref.tw);
+    qi.insert(qi.end(), L.ref.zq.begin(), L.ref.zq.end());
+    qi.insert(qi.end(), L.ref.zw.begin(), L.ref.zw.end());
+    double* dq = nullptr;
+    cudaError_t err = cudaMalloc(&dq, qi.size() * sizeof(double));
+    if (err != cudaSuccess) return err;
+    err = cudaMemcpyAsync(dq, qi.data(), qi.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (err == cudaSuccess) {
+        const long long total = (long long)L.E * L.Nq;
+        const int grid = (int)std::min<long long>((total + 255) / 256, kSMs * 32);
+        k_geom_prism_general<<<grid, 256, 0, s>>>(L.E, eb, el, L.QT, L.QZ, NTP, xyP, etaP, zif, BP, DrP, DsP, dq,
+                                                  L.G, L.G32);
         err = cudaGetLastError();
     }
     cudaError_t e2 = cudaStreamSynchronize(s);

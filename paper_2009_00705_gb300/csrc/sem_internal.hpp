@@ -157,6 +157,13 @@ struct sem_handle {
     std::vector<int> tri;
     std::vector<double> eta2;      // eta at order-P 2D nodes
     std::vector<std::vector<int>> map2;   // per level: [ntri][NT] 2D ids
+    // prisms: base triangle and layer of every element (column by column, bottom up)
+    std::vector<int> elem_b, elem_l;
+    // optional geometry of a tank with a body (sem_mesh.col_layers / z_iface / edge_arc)
+    bool general = false;          // any of them given: the general geometry kernel
+    std::vector<double> zif;       // [nlayers+1][2] interfaces z = a + b eta (always filled in 3D)
+    std::vector<double> arc;       // [ntri][3][3] or empty
+    std::vector<double> xyP;       // [ntri][NT_P][2] order-P node xy (general meshes)
     // profiling events
     std::vector<cudaEvent_t> ev;
     std::vector<int> ev_kind;      // per event pair: 0 FP64, 1 FP32, 2 TF32 tensor-core apply, 3 Schwarz blocks
@@ -220,6 +227,11 @@ cudaError_t asm_apply32(const Level& L, const float* f, const float* y, int adjo
 cudaError_t launch_geometry(Level& L, const double* vtri, const double* etaP, const double* BP,
                             const double* DrP, const double* DsP, int NTP, int nlayers, double depth,
                             cudaStream_t s);
+// prisms of a general mesh: per-element (base triangle, layer), order-P node xy per base
+// triangle, layer interfaces z = a + b eta
+cudaError_t launch_geometry_general(Level& L, const int* eb, const int* el, const double* xyP, const double* etaP,
+                                    const double* zif, const double* BP, const double* DrP, const double* DsP,
+                                    int NTP, cudaStream_t s);
 cudaError_t launch_diag(const Level& L, double* diag, cudaStream_t s);
 cudaError_t launch_restrict64(const Level& F, const Level& C, const double* f, const double* y,
                               double* fc, cudaStream_t s);

@@ -90,6 +90,78 @@ void tri_coords(int ntri, const int* tri, const double* vxy, int p, const std::v
     }
 }
 
+// Exact map of a base triangle with vertices v [3][2] at reference point (r, s): the affine
+// map plus, for every curved edge f = (a, b) of arcs [3][3] (cx, cy, R; R = 0 straight), the
+// displacement of the arc point from the chord times the blending factor 4 l_a l_b / (1 - xi^2),
+// xi = l_b - l_a, l the barycentric coordinates (the triangle blending map of Szabo and
+// Babuska).  The arc point lies at angle theta_a + (1 + xi)/2 (theta_b - theta_a), the angle
+// difference taken the short way round.  The factor is one on the edge and zero on the two
+// others; at the edge's end points it is 0/0 and the displacement is zero.
+void blended_point(const double* v, const double* arcs, double r, double s, double* out) {
+    const double lam[3] = {-0.5 * (r + s), 0.5 * (1.0 + r), 0.5 * (1.0 + s)};
+    out[0] = lam[0] * v[0] + lam[1] * v[2] + lam[2] * v[4];
+    out[1] = lam[0] * v[1] + lam[1] * v[3] + lam[2] * v[5];
+    if (!arcs) return;
+    static const int ends[3][2] = {{0, 1}, {1, 2}, {2, 0}};
+    for (int f = 0; f < 3; ++f) {
+        const double cx = arcs[3 * f], cy = arcs[3 * f + 1], R = arcs[3 * f + 2];
+        if (!(R > 0.0)) continue;
+        const int a = ends[f][0], b = ends[f][1];
+        const double xi = lam[b] - lam[a], den = 1.0 - xi * xi;
+        if (!(den > 1e-13)) continue;
+        const double ta = std::atan2(v[2 * a + 1] - cy, v[2 * a] - cx);
+        const double tb = std::atan2(v[2 * b + 1] - cy, v[2 * b] - cx);
+        const double dth = std::remainder(tb - ta, 2.0 * M_PI);
+        const double th = ta + 0.5 * (1.0 + xi) * dth;
+        const double px = cx + R * std::cos(th), py = cy + R * std::sin(th);
+        const double qx = 0.5 * (1.0 - xi) * v[2 * a] + 0.5 * (1.0 + xi) * v[2 * b];
+        const double qy = 0.5 * (1.0 - xi) * v[2 * a + 1] + 0.5 * (1.0 + xi) * v[2 * b + 1];
+        const double fac = 4.0 * lam[a] * lam[b] / den;
+        out[0] += fac * (px - qx);
+        out[1] += fac * (py - qy);
+    }
+}
+
+// The blended map of every base triangle at the order-p reference nodes, [ntri][NT][2].
+void blended_nodes(int ntri, const int* tri, const double* vxy, const double* arc, int p, std::vector<double>& out) {
+    const std::vector<double> tn = tri_nodes(p);
+    const int NT = (p + 1) * (p + 2) / 2;
+    out.assign((size_t)ntri * NT * 2, 0.0);
+    for (int b = 0; b < ntri; ++b) {
+        double v[6];
+        for (int k = 0; k < 3; ++k) {
+            v[2 * k] = vxy[2 * tri[3 * b + k]];
+            v[2 * k + 1] = vxy[2 * tri[3 * b + k] + 1];
+        }
+        for (int n = 0; n < NT; ++n)
+            blended_point(v, arc ? arc + 9 * (size_t)b : nullptr, tn[2 * n], tn[2 * n + 1], &out[((size_t)b * NT + n) * 2]);
+    }
+}
+
+// 2D coordinates of the order-p nodes of a general mesh: the order-P geometry (node xy xyP
+// [ntri][NT_P][2]) interpolated at the order-p nodes (first appearance wins).
+void tri_coords_mapped(int ntri, int P, const std::vector<double>& xyP, int p, const std::vector<int>& map2,
+                       long long N2, std::vector<double>& xy) {
+    const int NT = (p + 1) * (p + 2) / 2, NTP = (P + 1) * (P + 2) / 2;
+    std::vector<double> B, Dr, Ds;
+    tri_lagrange(P, tri_nodes(p).data(), NT, B, Dr, Ds);
+    xy.assign(2 * N2, 0.0);
+    std::vector<char> seen(N2, 0);
+    for (int e = 0; e < ntri; ++e)
+        for (int n = 0; n < NT; ++n) {
+            const int g = map2[(size_t)e * NT + n];
+            if (seen[g]) continue;
+            seen[g] = 1;
+            double x = 0, y = 0;
+            for (int k = 0; k < NTP; ++k) {
+                x += B[(size_t)n * NTP + k] * xyP[((size_t)e * NTP + k) * 2];
+                y += B[(size_t)n * NTP + k] * xyP[((size_t)e * NTP + k) * 2 + 1];
+            }
+            xy[2 * g] = x;
+            xy[2 * g + 1] = y;
+        }
+}
+
 namespace {
 
 template <typename T>
@@ -153,7 +225,7 @@ sem_status build_level(sem_handle* h, const sem_mesh* m, int li, int p, int pz) 
     tri_numbering(m->nvert, m->ntri, m->tri, p, map2, N2);
     L.N2 = N2;
     const int nl = (m->dim == 3) ? m->nlayers : 1;
-    L.E = m->ntri * nl;
+    L.E = (m->dim == 3) ? (int)h->elem_b.size() : m->ntri;
     L.N = (m->dim == 3) ? N2 * (long long)(nl * L.pz + 1) : N2;
     if (L.N >= (1LL << 31) - 1 || (long long)L.E * L.Np >= (1LL << 40)) {
         set_error("mesh too large for 32-bit node ids");
@@ -161,13 +233,12 @@ sem_status build_level(sem_handle* h, const sem_mesh* m, int li, int p, int pz) 
     }
     std::vector<long long> gmap((size_t)L.E * L.Np);
     if (m->dim == 3) {
-        for (int b = 0; b < m->ntri; ++b)
-            for (int l = 0; l < nl; ++l) {
-                const size_t e = (size_t)b * nl + l;
-                for (int k = 0; k <= L.pz; ++k)
-                    for (int n = 0; n < L.NT; ++n)
-                        gmap[e * L.Np + k * L.NT + n] = (long long)(l * L.pz + k) * N2 + map2[(size_t)b * L.NT + n];
-            }
+        for (size_t e = 0; e < (size_t)L.E; ++e) {
+            const int b = h->elem_b[e], l = h->elem_l[e];
+            for (int k = 0; k <= L.pz; ++k)
+                for (int n = 0; n < L.NT; ++n)
+                    gmap[e * L.Np + k * L.NT + n] = (long long)(l * L.pz + k) * N2 + map2[(size_t)b * L.NT + n];
+        }
     } else {
         for (size_t i = 0; i < gmap.size(); ++i) gmap[i] = map2[i];
     }
@@ -177,6 +248,12 @@ sem_status build_level(sem_handle* h, const sem_mesh* m, int li, int p, int pz) 
         for (int f = 0; f < nf; ++f)
             if (m->face_bc[(size_t)e * nf + f])
                 for (int l : L.ref.face_nodes[f]) dmask[gmap[(size_t)e * L.Np + l]] = 1;
+    {   // ids in no element (above a body): identity rows, listed with the Dirichlet nodes
+        std::vector<char> held(L.N, 0);
+        for (long long g : gmap) held[g] = 1;
+        for (long long i = 0; i < L.N; ++i)
+            if (!held[i]) dmask[i] = 1;
+    }
     L.hdir.clear();
     for (long long i = 0; i < L.N; ++i)
         if (dmask[i]) L.hdir.push_back(i);
@@ -256,6 +333,14 @@ sem_status geometry_levels(sem_handle* h, int first, int last, bool flat) {
             for (int n = 0; n < NTP; ++n) etaP[(size_t)b * NTP + n] = h->eta2[h->map2[0][(size_t)b * NTP + n]];
     double* detaP = nullptr;
     CK(upload(&detaP, etaP));
+    int *deb = nullptr, *del = nullptr;
+    double *dxyP = nullptr, *dzif = nullptr;
+    if (h->general) {
+        CK(upload(&deb, h->elem_b));
+        CK(upload(&del, h->elem_l));
+        CK(upload(&dxyP, h->xyP));
+        CK(upload(&dzif, h->zif));
+    }
     for (int li = first; li < last; ++li) {
         Level& L = h->lv[li];
         std::vector<double> B, Dr, Ds;
@@ -264,7 +349,9 @@ sem_status geometry_levels(sem_handle* h, int first, int last, bool flat) {
         CK(upload(&dB, B));
         CK(upload(&dDr, Dr));
         CK(upload(&dDs, Ds));
-        cudaError_t e = launch_geometry(L, dvtri, detaP, dB, dDr, dDs, NTP, h->nlayers, h->depth, 0);
+        cudaError_t e = h->general
+                            ? launch_geometry_general(L, deb, del, dxyP, detaP, dzif, dB, dDr, dDs, NTP, 0)
+                            : launch_geometry(L, dvtri, detaP, dB, dDr, dDs, NTP, h->nlayers, h->depth, 0);
         cudaFree(dB);
         cudaFree(dDr);
         cudaFree(dDs);
@@ -273,12 +360,35 @@ sem_status geometry_levels(sem_handle* h, int first, int last, bool flat) {
     }
     cudaFree(dvtri);
     cudaFree(detaP);
+    if (h->general) {
+        cudaFree(deb);
+        cudaFree(del);
+        cudaFree(dxyP);
+        cudaFree(dzif);
+    }
+    return SEM_OK;
+}
+
+// Every layer of a mesh with given interfaces keeps a positive thickness at every order-P
+// surface node: (a_{k+1} - a_k) + (b_{k+1} - b_k) eta > 0.
+sem_status check_layers(const sem_handle* h, const std::vector<double>& eta) {
+    if (!h->general || h->dim != 3) return SEM_OK;
+    for (int k = 0; k < h->nlayers; ++k) {
+        const double da = h->zif[2 * k + 2] - h->zif[2 * k], db = h->zif[2 * k + 3] - h->zif[2 * k + 1];
+        for (double e : eta)
+            if (!(da + db * e > 0.0)) {
+                set_error("layer " + std::to_string(k) + " has no positive thickness at some surface node");
+                return SEM_EINVAL;
+            }
+    }
     return SEM_OK;
 }
 
 sem_status build_geometry(sem_handle* h, const sem_mesh* m) {
     h->eta2.assign(h->lv[0].N2, 0.0);
     if (m->dim == 3 && m->eta) std::memcpy(h->eta2.data(), m->eta, sizeof(double) * h->lv[0].N2);
+    const sem_status lay = check_layers(h, h->eta2);
+    if (lay != SEM_OK) return lay;
     return geometry_levels(h, 0, (int)h->lv.size(), false);
 }
 
@@ -404,7 +514,7 @@ sem_status build_transfers(sem_handle* h) {
 // Surface operators and work fields of the free-surface time stepping (surface_ops = 1):
 // the order-P surface is the top of the top sigma layer and must be exactly the Dirichlet set.
 sem_status build_surface(sem_handle* h) {
-    if (h->dim != 3) { set_error("surface_ops needs a 3D sigma-layer mesh"); return SEM_EINVAL; }
+    if (h->dim != 3 || h->general) { set_error("surface_ops needs a 3D sigma-layer mesh"); return SEM_EINVAL; }
     const Level& L0 = h->lv[0];
     const long long N2 = L0.N2, k_top = (long long)h->nlayers * L0.pz;
     bool top_only = (long long)L0.hdir.size() == N2;

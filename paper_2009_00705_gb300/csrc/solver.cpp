@@ -22,6 +22,10 @@ const char* last_error();
 void tri_numbering(int nvert, int ntri, const int* tri, int p, std::vector<int>& map2, long long& N2);
 void tri_coords(int ntri, const int* tri, const double* vxy, int p, const std::vector<int>& map2, long long N2,
                 std::vector<double>& xy);
+void blended_nodes(int ntri, const int* tri, const double* vxy, const double* arc, int p, std::vector<double>& out);
+void tri_coords_mapped(int ntri, int P, const std::vector<double>& xyP, int p, const std::vector<int>& map2,
+                       long long N2, std::vector<double>& xy);
+sem_status check_layers(const sem_handle* h, const std::vector<double>& eta);
 sem_status build_level(sem_handle* h, const sem_mesh* m, int li, int p, int pz);
 sem_status build_geometry(sem_handle* h, const sem_mesh* m);
 sem_status build_diagonals(sem_handle* h);
@@ -597,6 +601,39 @@ sem_status check_mesh(const sem_mesh* m, int P) {
         set_error("dim 3 needs nlayers >= 1 and depth > 0");
         return SEM_EINVAL;
     }
+    if (m->dim == 2 && (m->col_layers || m->z_iface || m->edge_arc)) {
+        set_error("col_layers, z_iface and edge_arc describe prism meshes only");
+        return SEM_EINVAL;
+    }
+    if (m->col_layers)
+        for (int b = 0; b < m->ntri; ++b)
+            if (m->col_layers[b] < 1 || m->col_layers[b] > m->nlayers) {
+                set_error("col_layers entries must lie in 1..nlayers");
+                return SEM_EINVAL;
+            }
+    if (m->z_iface)
+        for (int k = 0; k <= 2 * m->nlayers + 1; ++k)
+            if (!std::isfinite(m->z_iface[k])) { set_error("z_iface entries must be finite"); return SEM_EINVAL; }
+    if (m->edge_arc)
+        for (int b = 0; b < m->ntri; ++b)
+            for (int f = 0; f < 3; ++f) {
+                const double* c = m->edge_arc + 9 * (size_t)b + 3 * f;
+                if (!(c[2] >= 0.0) || !std::isfinite(c[0]) || !std::isfinite(c[1]) || !std::isfinite(c[2])) {
+                    set_error("edge_arc: radius must be >= 0 and finite");
+                    return SEM_EINVAL;
+                }
+                if (c[2] == 0.0) continue;
+                const double* va = m->vxy + 2 * m->tri[3 * b + f];
+                const double* vb = m->vxy + 2 * m->tri[3 * b + (f + 1) % 3];
+                const double ra = std::hypot(va[0] - c[0], va[1] - c[1]), rb = std::hypot(vb[0] - c[0], vb[1] - c[1]);
+                const double dth = std::remainder(std::atan2(vb[1] - c[1], vb[0] - c[0]) -
+                                                      std::atan2(va[1] - c[1], va[0] - c[0]), 2.0 * M_PI);
+                if (std::fabs(ra - c[2]) > 1e-9 * c[2] || std::fabs(rb - c[2]) > 1e-9 * c[2] ||
+                    !(std::fabs(dth) < 0.5 * M_PI + 1e-12)) {
+                    set_error("edge_arc: a curved edge's vertices must lie on its circle, at most a quarter turn apart");
+                    return SEM_EINVAL;
+                }
+            }
     return SEM_OK;
 }
 
@@ -897,7 +934,23 @@ sem_status sem_mesh_nodes2d(const sem_mesh* m, int p, long long* n2, double* xy)
     *n2 = N2;
     if (xy) {
         std::vector<double> c;
-        tri_coords(m->ntri, m->tri, m->vxy, p, map2, N2, c);
+        if (m->dim == 3 && m->edge_arc) {
+            // the blended map at the order-p nodes, first appearance wins
+            std::vector<double> nodes;
+            blended_nodes(m->ntri, m->tri, m->vxy, m->edge_arc, p, nodes);
+            const int NT = (p + 1) * (p + 2) / 2;
+            c.assign(2 * N2, 0.0);
+            std::vector<char> seen(N2, 0);
+            for (size_t i = 0; i < (size_t)m->ntri * NT; ++i) {
+                const int g = map2[i];
+                if (seen[g]) continue;
+                seen[g] = 1;
+                c[2 * g] = nodes[2 * i];
+                c[2 * g + 1] = nodes[2 * i + 1];
+            }
+        } else {
+            tri_coords(m->ntri, m->tri, m->vxy, p, map2, N2, c);
+        }
         std::memcpy(xy, c.data(), sizeof(double) * c.size());
     }
     return SEM_OK;
@@ -921,6 +974,23 @@ sem_status sem_setup(const sem_mesh* m, int P, const sem_options* opts, sem_hand
     cudaGetDevice(&h->device);
     h->vxy.assign(m->vxy, m->vxy + 2 * (size_t)m->nvert);
     h->tri.assign(m->tri, m->tri + 3 * (size_t)m->ntri);
+    if (m->dim == 3) {
+        const int nl = m->nlayers;
+        for (int b = 0; b < m->ntri; ++b)
+            for (int l = 0; l < (m->col_layers ? m->col_layers[b] : nl); ++l) {
+                h->elem_b.push_back(b);
+                h->elem_l.push_back(l);
+            }
+        h->general = m->col_layers || m->z_iface || m->edge_arc;
+        h->zif.resize(2 * (size_t)(nl + 1));
+        for (int k = 0; k <= nl; ++k) {
+            h->zif[2 * k] = m->z_iface ? m->z_iface[2 * k] : -m->depth * (1.0 - (double)k / nl);
+            h->zif[2 * k + 1] = m->z_iface ? m->z_iface[2 * k + 1] : (double)k / nl;
+        }
+        if (m->edge_arc) h->arc.assign(m->edge_arc, m->edge_arc + 9 * (size_t)m->ntri);
+        if (h->general)
+            blended_nodes(m->ntri, m->tri, m->vxy, m->edge_arc, P, h->xyP);
+    }
     h->lv.resize(o.nlevels);
     h->map2.resize(o.nlevels);
     sem_status st = SEM_OK;
@@ -1052,7 +1122,10 @@ sem_status sem_node_coords(const sem_handle* h, int level, double* xyz) {
     if (!xyz) { set_error("xyz is NULL"); return SEM_EINVAL; }
     const Level& L = h->lv[level];
     std::vector<double> xy;
-    tri_coords((int)(h->tri.size() / 3), h->tri.data(), h->vxy.data(), L.p, h->map2[level], L.N2, xy);
+    if (h->general)
+        tri_coords_mapped((int)(h->tri.size() / 3), h->P, h->xyP, L.p, h->map2[level], L.N2, xy);
+    else
+        tri_coords((int)(h->tri.size() / 3), h->tri.data(), h->vxy.data(), L.p, h->map2[level], L.N2, xy);
     if (h->dim == 2) {
         std::memcpy(xyz, xy.data(), sizeof(double) * xy.size());
         return SEM_OK;
@@ -1074,11 +1147,14 @@ sem_status sem_node_coords(const sem_handle* h, int level, double* xyz) {
         int l = kz / p, k = kz - l * p;
         if (l == nl) { l = nl - 1; k = p; }
         const double sigma = (l + 0.5 * (L.ref.znodes[k] + 1.0)) / nl;
+        const double tau = 0.5 * (L.ref.znodes[k] + 1.0);
+        const double* zi = h->zif.data() + 2 * l;   // interfaces l and l + 1
         for (long long g = 0; g < L.N2; ++g) {
             const long long id = (long long)kz * L.N2 + g;
             xyz[3 * id] = xy[2 * g];
             xyz[3 * id + 1] = xy[2 * g + 1];
-            xyz[3 * id + 2] = -h->depth + sigma * (h->depth + eta[g]);
+            xyz[3 * id + 2] = h->general ? (1.0 - tau) * (zi[0] + zi[1] * eta[g]) + tau * (zi[2] + zi[3] * eta[g])
+                                         : -h->depth + sigma * (h->depth + eta[g]);
         }
     }
     return SEM_OK;
@@ -1163,6 +1239,7 @@ sem_status sem_update_eta(sem_handle* h, const double* eta_nodal_host, int strat
     if (strategy < SEM_ETA_FINEST || strategy > SEM_ETA_ALL) { set_error("sem_update_eta: strategy 0, 1 or 2"); return SEM_EINVAL; }
     CKS(cudaDeviceSynchronize());
     const Level& L0 = h->lv[0];
+    CKST(check_layers(h, std::vector<double>(eta_nodal_host, eta_nodal_host + L0.N2)));
     h->eta2.assign(eta_nodal_host, eta_nodal_host + L0.N2);
     if (h->fs_eta) CKS(cudaMemcpy(h->fs_eta, h->eta2.data(), sizeof(double) * L0.N2, cudaMemcpyHostToDevice));
     const int nl = (int)h->lv.size();

@@ -102,3 +102,29 @@ def test_ctypes_structs_mirror_the_header(sem, cname, pyname):
 def test_unknown_option_is_an_error(sem):
     with pytest.raises(TypeError):
         sem.sem_default_options(4, no_such_option=1)
+
+
+@pytest.mark.parametrize("p", [1, 3, 6])
+def test_host_blended_nodes_match_oracle(sem, p):
+    # the library's curved-triangle map (host side) against the oracle's at the order-p nodes
+    from oracle.mesh import Level, blended_xy
+    from oracle.refelem import RefTri
+    mesh = W.hull_tank(8)
+    lev = Level(mesh, p)
+    xy = sem.sem_mesh_nodes2d(mesh, p)
+    tn = RefTri(p).nodes
+    for b in np.flatnonzero((mesh.edge_arc[:, :, 2] > 0).any(1)):
+        np.testing.assert_allclose(xy[lev.map2[b]], blended_xy(mesh, b, tn), atol=1e-13)
+    straight = np.flatnonzero(~(mesh.edge_arc[:, :, 2] > 0).any(1))[:20]
+    for b in straight:
+        np.testing.assert_allclose(xy[lev.map2[b]], lev.tri_node_xy(b, tn), atol=1e-13)
+
+
+def test_bad_arc_is_rejected_without_gpu(sem):
+    m = W.hull_tank(8)
+    m.edge_arc = m.edge_arc.copy()
+    b, f = np.argwhere(m.edge_arc[:, :, 2] > 0)[0]
+    m.edge_arc[b, f, 2] *= 1.1             # the vertices no longer lie on the circle
+    with pytest.raises(sem.SemError) as e:
+        sem.sem_setup(m, 2)
+    assert e.value.status == sem.SEM_EINVAL and "circle" in sem.sem_last_error()
