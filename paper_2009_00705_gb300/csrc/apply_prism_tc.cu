@@ -57,6 +57,9 @@ struct TcTile {
     static constexpr int NPAIR = EB / 2;
     static constexpr int NGF = (NTF + 1) / 2;      // forward warp tasks per pair (2 qt tiles each)
     static constexpr int NGB = (NTB + 1) / 2;      // backward warp tasks per pair (2 node tiles each)
+    // forward tasks fill the warps exactly: every warp keeps one task, so the B fragments of
+    // its two qt tiles stay in registers for the whole launch (P = 2, 3, 6)
+    static constexpr bool FSTAT = NPAIR * NGF == kTcWarps;
     // BF16 factors as [6][QZ][QTP], rows padded to even length so a lane's two points
     // (qt, qt + 1), qt even, are one aligned 32-bit word
     static constexpr int QTP = (QT + 1) / 2 * 2;
@@ -208,6 +211,25 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    // register-resident B fragments of the forward contraction (FSTAT): [tile][k-step][Dr, Ds, Bt pairs]
+    uint32_t bst[2][D::KSF][6];
+    if constexpr (D::FSTAT) {
+        const int j0 = 2 * (warp % D::NGF);
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj)
+#pragma unroll
+            for (int ks = 0; ks < D::KSF; ++ks) {
+                if (j0 + jj < D::NTF) {
+                    const float* Bb = sBF + ((j0 + jj) * 8 + lrow) * D::LDF + lcolB + ks * 8;
+                    ldsm_x2(smem_u32(Bb), bst[jj][ks][0], bst[jj][ks][1]);
+                    ldsm_x2(smem_u32(Bb + D::NTF * 8 * D::LDF), bst[jj][ks][2], bst[jj][ks][3]);
+                    ldsm_x2(smem_u32(Bb + 2 * D::NTF * 8 * D::LDF), bst[jj][ks][4], bst[jj][ks][5]);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 6; ++r) bst[jj][ks][r] = 0u;
+                }
+            }
+    }
     uint32_t pg = 0, pm = 0;
     int buf = 0;
     const int stride = gridDim.x * EB;
@@ -296,11 +318,17 @@ __global__ void __launch_bounds__(kTcThreads, 2)
 #pragma unroll
                 for (int jj = 0; jj < 2; ++jj) {
                     if (jj == 1 && !two) break;
-                    const float* Bb = sBF + ((j0 + jj) * 8 + lrow) * D::LDF + lcolB + ks * 8;
                     uint32_t br0, br1, bs0, bs1, bt0, bt1;
-                    ldsm_x2(smem_u32(Bb), br0, br1);
-                    ldsm_x2(smem_u32(Bb + D::NTF * 8 * D::LDF), bs0, bs1);
-                    ldsm_x2(smem_u32(Bb + 2 * D::NTF * 8 * D::LDF), bt0, bt1);
+                    if constexpr (D::FSTAT) {
+                        br0 = bst[jj][ks][0]; br1 = bst[jj][ks][1];
+                        bs0 = bst[jj][ks][2]; bs1 = bst[jj][ks][3];
+                        bt0 = bst[jj][ks][4]; bt1 = bst[jj][ks][5];
+                    } else {
+                        const float* Bb = sBF + ((j0 + jj) * 8 + lrow) * D::LDF + lcolB + ks * 8;
+                        ldsm_x2(smem_u32(Bb), br0, br1);
+                        ldsm_x2(smem_u32(Bb + D::NTF * 8 * D::LDF), bs0, bs1);
+                        ldsm_x2(smem_u32(Bb + 2 * D::NTF * 8 * D::LDF), bt0, bt1);
+                    }
                     mma_tf32(cr[jj], au, br0, br1);
                     mma_tf32(cs[jj], au, bs0, bs1);
                     mma_tf32(ct[jj], aw, bt0, bt1);

@@ -173,3 +173,59 @@ def test_hull_rejects_surface_ops_and_thin_layers(sem):
     with pytest.raises(sem.SemError) as e:
         sem.Solver(mesh, 2, eta_nodal=np.full(prob.levels[0].N2, -0.5), levels=levels)
     assert "thickness" in sem.sem_last_error()
+
+
+# ---------------------------------------------------------------- the benchmark's hull tank
+@pytest.fixture(scope="module")
+def hull_full(sem):
+    # 64 x 64 base grid, 2 + 2 layers, 32,128 prisms, P = 6, eta of 32 power-law modes:
+    # the oracle computes sampled rows one by one from the elements around each node
+    mesh = W.config_hull()
+    prob = Problem(mesh, [6, 3, 1])
+    solver = sem.Solver(mesh, 6, eta_nodal=prob.eta_nodal, levels=[6, 3, 1])
+    yield mesh, prob, solver
+    solver.close()
+
+
+def test_hull_full_size_apply_sampled_rows(hull_full):
+    mesh, prob, solver = hull_full
+    rng = np.random.default_rng(15)
+    for li in (0, 1):
+        lev = prob.levels[li]
+        # free rows, Dirichlet rows, rows above the hull (identity) and rows on the curved corners
+        held = np.zeros(lev.N, bool)
+        held[lev.emap.ravel()] = True
+        curved = np.flatnonzero((mesh.edge_arc[:, :, 2] > 0).any(1))
+        corner = np.unique(lev.emap[np.isin(mesh.columns()[0], curved)][:, :3])
+        rows = np.concatenate([rng.choice(lev.free, 40, replace=False),
+                               rng.choice(np.flatnonzero(lev.dmask & held), 6, replace=False),
+                               rng.choice(np.flatnonzero(~held), 4, replace=False), corner[:8]])
+        x = W.random_vector(lev.N, seed=19)
+        y = torch.empty(lev.N, dtype=torch.float64, device="cuda")
+        solver.apply(li, torch.tensor(x, device="cuda"), y)
+        got = y.cpu().numpy()[rows]
+        ref = prob.apply_rows(li, x, rows)
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), li
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_tf32"])
+def test_hull_full_size_solve_residual(hull_full, sem, precision):
+    mesh, prob, solver = hull_full
+    lev = prob.levels[0]
+    if precision != "fp64":
+        solver = sem.Solver(mesh, 6, eta_nodal=prob.eta_nodal, levels=[6, 3, 1], precision=precision,
+                            outer="pdc", inner_imax=40, imax=400)
+    C = solver.coords(0)
+    dn = solver.dirichlet_nodes(0)
+    phiD = W.potential3d(*C[dn].T)
+    phi = torch.empty(lev.N, dtype=torch.float64, device="cuda")
+    st = solver.solve(torch.tensor(phiD, device="cuda"), phi, tol=1e-8)
+    torch.cuda.synchronize()
+    assert st["status"] == 0 and st["res_final"] <= 1e-8 * st["fnorm"]
+    u = phi.cpu().numpy()
+    np.testing.assert_array_equal(u[dn], phiD)
+    rows = np.random.default_rng(16).choice(lev.free, 40, replace=False)
+    r = prob.apply_rows(0, u, rows, masked=False)
+    assert np.abs(r).max() <= 1e-8 * st["fnorm"]
+    if precision != "fp64":
+        solver.close()
