@@ -38,11 +38,11 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_NOMINAL_TFLOPS = 1.25          # GB300 FP64 (profiling recipe's nominal table)
 FALLBACK_HBM_GBS = 6800.0
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the FP64 prism
-# apply, per launch, scaled from the 48x48x4-prism capture (18,432 elements;
-# profiles/apply_fp64_p6_box48.md) to the 32,768-element benchmark mesh by element
-# count; reported as null once apply_prism.cu differs from the captured source.
-TRAFFIC = {("apply_fp64", 6): (350.192896e6 + 14.584064e6) * 32768 / 18432}
-TRAFFIC_SRC_SHA = "46bba8e8b3d917d9"
+# apply, per launch (mean of four launches), scaled from the 48x48x4-prism capture
+# (18,432 elements; profiles/apply_fp64_p6_box48.md) to the 32,768-element benchmark
+# mesh by element count; reported as null once apply_prism.cu differs from the captured source.
+TRAFFIC = {("apply_fp64", 6): (350.860352e6 + 12.227136e6) * 32768 / 18432}
+TRAFFIC_SRC_SHA = "a51bb5326e701863"
 
 
 def workload_name(n, nl, P):
