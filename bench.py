@@ -255,7 +255,7 @@ def main():
     ap.add_argument("--train-steps", type=int, default=6)
     ap.add_argument("--inner-imax", type=int, default=40)
     ap.add_argument("--inner-rtol", type=float, default=1e-4)
-    ap.add_argument("--coarse-rtol", type=float, default=1e-3)
+    ap.add_argument("--coarse-rtol", type=float, default=1e-2)
     ap.add_argument("--ncu-case", type=int, default=0, metavar="N",
                     help="profiler driver: one short MIXED_TF32 solve on an N x N x 4 P=6 box (FP64, FP32 and "
                          "tensor-core applies, transfers and the coarse CG all launch); prints stats only")
@@ -387,7 +387,7 @@ def main():
             ms_m, st_m = timed(ms_solver, a.steps, a.warmup, phi_m)
             ms_m = max_over_ranks(ms_m)
             err = float(np.abs(phi_m.cpu().numpy() - phi64).max() / np.abs(phi64).max())
-            smooth = ("TF32 tensor-core apply (mma.sync m16n8k8, FP32 accumulation, BF16 factors) in the Chebyshev sweeps and residuals of "
+            smooth = ("TF32 tensor-core apply (warp-level mma.sync m16n8k8, FP32 accumulation, BF16 factors) in the Chebyshev sweeps and residuals of "
                       "the V-cycle on the P and intermediate levels; FP32 apply in the inner PCG" if prec == "mixed_tf32"
                       else "FP32 SIMT apply throughout")
             obj = {"value": dof * a.steps * world / (ms_m / 1000.0), "unit": UNIT,
@@ -405,6 +405,23 @@ def main():
             if prec == "mixed_tf32":
                 obj["apply_tf32_tensor_cores"] = apply_view(sum(x["apply_tc_ms"] for x in st_m),
                                                             sum(x["apply_tc_launches"] for x in st_m), 4, gword=2)
+                # the order-6 operator through sem_apply32 (memset of y, kernel, Dirichlet copy) with
+                # the warp-MMA kernel the V-cycle uses and with the tcgen05 kernel
+                xa = torch.rand(N, dtype=torch.float32, device="cuda")
+                ya = torch.empty(N, dtype=torch.float32, device="cuda")
+                calls = {}
+                for form, tcv in (("warp_mma", 1), ("tcgen05", 2)):
+                    for _ in range(3):
+                        ms_solver.apply32(0, xa, ya, tensor_cores=tcv)
+                    torch.cuda.synchronize()
+                    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    ev0.record(stream)
+                    for _ in range(20):
+                        ms_solver.apply32(0, xa, ya, tensor_cores=tcv)
+                    ev1.record(stream)
+                    torch.cuda.synchronize()
+                    calls[form] = ev0.elapsed_time(ev1) / 20
+                obj["apply32_call_ms_order6"] = calls
                 mixed_tc = obj
             else:
                 mixed = obj

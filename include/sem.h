@@ -211,7 +211,7 @@ typedef struct sem_handle sem_handle;
 /* Defaults for finest order P: PCG, FP64, nu1 = nu2 = 1, k_cheb = 5,
  * cheb_lo = 0.01, cheb_hi = 1.05, lanczos_steps = 30, levels P -> ... -> 1 from the
  * table {6:6,3,1; 5:5,3,1; 4:4,2,1; 3:3,2,1; 2:2,1; 1:1}, rtol 1e-8, atol 0,
- * imax 200, gmres_m 30, coarse_rtol 1e-3, coarse_imax 5000, inner_imax 0,
+ * imax 200, gmres_m 30, coarse_rtol 1e-2, coarse_imax 5000, inner_imax 0,
  * inner_rtol 1e-4.  The smoother and coarse-tolerance defaults minimise the
  * time to a 1e-8 residual on the 64x64x4-prism P = 6 box; a coarse_rtol of
  * 1e-14 makes the V-cycle the exact-coarse-solve Algorithm 1 to rounding. */
@@ -253,10 +253,12 @@ sem_status sem_apply(sem_handle* h, int level, const double* x_dev, double* y_de
 
 /* The same operator in single precision, as the mixed V-cycle applies it: the FP32
  * kernel (tensor_cores = 0) or the TF32 tensor-core kernel of the MIXED_TF32
- * Chebyshev sweeps (tensor_cores = 1; prism levels of order 2..6, else SEM_EINVAL;
- * operands rounded to TF32, FP32 accumulation).  x_dev, y_dev: N floats, distinct;
- * y_D = x_D.  The tensor-core form synchronises the stream and returns SEM_TIMEOUT
- * if a geometric-factor copy inside the kernel did not complete within 1 s. */
+ * Chebyshev sweeps (tensor_cores = 1: warp-level MMA; prism levels of order 2..6, else
+ * SEM_EINVAL; operands rounded to TF32, FP32 accumulation).  tensor_cores = 2 runs the
+ * same operator on tcgen05 (TMEM accumulators, operands read by descriptor; order 6
+ * only, else SEM_EINVAL), a second kernel that the V-cycle does not use.  x_dev, y_dev:
+ * N floats, distinct; y_D = x_D.  The tensor-core forms synchronise the stream and
+ * return SEM_TIMEOUT if a copy or an MMA inside the kernel did not complete within 1 s. */
 sem_status sem_apply32(sem_handle* h, int level, const float* x_dev, float* y_dev, int tensor_cores,
                        void* stream);
 

@@ -199,6 +199,17 @@ int prism_tile_elements(int P, int variant);
 cudaError_t launch_apply_prism_tc(const Level& L, const float* x, float* y, const int* skip, int* err,
                                   cudaStream_t s);
 bool prism_tc_supported(int p);
+// apply_prism_t5.cu: the order-6 prism apply on tcgen05 (TMEM accumulators, operands read from
+// shared memory by descriptor); same arguments and error flag as launch_apply_prism_tc
+cudaError_t launch_apply_prism_t5(const Level& L, const float* x, float* y, const int* skip, int* err,
+                                  cudaStream_t s);
+bool prism_t5_supported(int p);
+// the tensor-core apply of a level: the warp-MMA kernel (the V-cycle's), or the tcgen05 kernel
+// where it is compiled (order 6) when tcgen05 is set
+inline cudaError_t launch_apply_tensor(const Level& L, const float* x, float* y, const int* skip, int* err,
+                                       cudaStream_t s, bool tcgen05 = false) {
+    return tcgen05 ? launch_apply_prism_t5(L, x, y, skip, err, s) : launch_apply_prism_tc(L, x, y, skip, err, s);
+}
 // the tensor-core apply serves isotropic prism levels of order 2..6
 inline bool level_tc(const Level& L) { return L.dim == 3 && L.pz == L.p && prism_tc_supported(L.p); }
 // apply_prism.cu: (triangle order, vertical order) pairs the prism apply is compiled for

@@ -243,7 +243,7 @@ static sem_status apply_vcycle32(sem_handle* h, int li, const float* x, float* y
         return apply_level32(h, li, x, y, s, skip);
     CKS(cudaMemsetAsync(y, 0, sizeof(float) * L.N, s));
     const bool timed = timed_begin(h, li, s);
-    K(launch_apply_prism_tc(L, x, y, skip, h->sc.flags + F_TC_ERR, s));
+    K(launch_apply_tensor(L, x, y, skip, h->sc.flags + F_TC_ERR, s));
     if (timed) timed_end(h, 2, s);
     if (li == 0) h->fine_applies += 1;
     return SEM_OK;
@@ -904,7 +904,7 @@ void sem_default_options(sem_options* o, int P) {
     o->atol = 0.0;
     o->imax = 200;
     o->gmres_m = 30;
-    o->coarse_rtol = 1e-3;
+    o->coarse_rtol = 1e-2;
     o->coarse_imax = 5000;
     o->profile = 0;
     o->inner_imax = 0;
@@ -1175,13 +1175,18 @@ sem_status sem_apply32(sem_handle* h, int level, const float* x, float* y, int t
     if (!x || !y || x == y) { set_error("sem_apply32: x and y must be distinct device buffers"); return SEM_EINVAL; }
     cudaStream_t s = as_stream(stream);
     const Level& L = h->lv[level];
+    if (tensor_cores < 0 || tensor_cores > 2) { set_error("sem_apply32: tensor_cores 0, 1 or 2"); return SEM_EINVAL; }
     if (tensor_cores) {
         if (!level_tc(L)) {
             set_error("sem_apply32: the tensor-core apply needs an isotropic prism level of order 2..6");
             return SEM_EINVAL;
         }
+        if (tensor_cores == 2 && !prism_t5_supported(L.p)) {
+            set_error("sem_apply32: the tcgen05 apply is compiled for order 6 only");
+            return SEM_EINVAL;
+        }
         CKS(cudaMemsetAsync(y, 0, sizeof(float) * L.N, s));
-        K(launch_apply_prism_tc(L, x, y, nullptr, h->sc.flags + F_TC_ERR, s));
+        K(launch_apply_tensor(L, x, y, nullptr, h->sc.flags + F_TC_ERR, s, tensor_cores == 2));
         CKS(cudaStreamSynchronize(s));
         sem_status ret = SEM_OK;
         CKST(check_tc_flag(h, &ret, true));

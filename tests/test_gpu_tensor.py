@@ -141,3 +141,43 @@ def test_mixed_tf32_solve_matches_oracle(sem, name):
             s.close()
     # the smoothing operator's rounding leaves the convergence essentially unchanged
     assert its["mixed_tf32"][1] <= its["mixed_fp32"][1] + 3, its
+
+
+@pytest.mark.parametrize("n,nl", [(3, 3), (40, 4)])
+def test_tcgen05_apply_against_warp_mma_and_oracle(sem, n, nl):
+    # order 6: the tcgen05 kernel (16 elements per pass, M = 128 rows) against the warp-MMA kernel,
+    # the FP32 apply and the oracle's rows; 3x3x3 = 54 prisms is four passes, the last ragged (6
+    # elements); 40x40x4 = 12,800 prisms is 800 passes, five or six per CTA
+    mesh = W.box3d(n, n, nl, eta_modes=W.eta_sinx_cosy(0.1))
+    xy = sem.sem_mesh_nodes2d(mesh, 6)
+    s = sem.Solver(mesh, 6, eta_nodal=mesh.eta(xy[:, 0], xy[:, 1]), levels=[6, 3, 1])
+    try:
+        N = s.query(0)["ndof"]
+        x = W.random_vector(N, seed=29).astype(np.float32)
+        xd = torch.tensor(x, device="cuda")
+        ys = {k: torch.zeros(N, dtype=torch.float32, device="cuda") for k in (0, 1, 2)}
+        for k, y in ys.items():
+            s.apply32(0, xd, y, tensor_cores=k)
+        torch.cuda.synchronize()
+        y32, ymma, y5 = (ys[k].cpu().numpy().astype(np.float64) for k in (0, 1, 2))
+        _check_apply(y5, y32)
+        _check_apply(ymma, y32)
+        # the two tensor-core forms round alike (TF32 operands, BF16 factors): they agree more
+        # closely with each other than either with the FP32 apply
+        assert np.linalg.norm(y5 - ymma) <= 2e-3 * np.linalg.norm(y32)
+        prob = Problem(mesh, [6, 1])
+        rows = np.random.default_rng(4).choice(N, 120, replace=False)
+        ref = prob.apply_rows(0, x.astype(np.float64), rows)
+        assert np.abs(y5[rows] - ref).max() <= 1e-2 * np.abs(ref).max()
+        # repeated launches give the same result up to the order of the atomic summation
+        y2 = torch.zeros(N, dtype=torch.float32, device="cuda")
+        s.apply32(0, xd, y2, tensor_cores=2)
+        torch.cuda.synchronize()
+        assert np.abs(y2.cpu().numpy() - y5).max() <= 1e-5 * np.abs(y5).max()
+        # the tcgen05 kernel exists for order 6 only
+        if n == 3:
+            xc = torch.zeros(s.query(1)["ndof"], dtype=torch.float32, device="cuda")
+            with pytest.raises(sem.SemError):
+                s.apply32(1, xc, torch.zeros_like(xc), tensor_cores=2)
+    finally:
+        s.close()
