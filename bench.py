@@ -200,6 +200,14 @@ def run_ncu_case(a):
     phi = torch.empty(s.query(0)["ndof"], dtype=torch.float64, device="cuda")
     st = s.solve(phiD, phi, tol=1e-8, allow_not_converged=True)
     torch.cuda.synchronize()
+    if a.ncu_tcgen05 and P == 6:
+        # three launches of the tcgen05 form of the order-6 apply on the same mesh
+        N = s.query(0)["ndof"]
+        xa = torch.rand(N, dtype=torch.float32, device="cuda")
+        ya = torch.empty(N, dtype=torch.float32, device="cuda")
+        for _ in range(3):
+            s.apply32(0, xa, ya, tensor_cores=2)
+        torch.cuda.synchronize()
     print(json.dumps({"ncu_case": a.ncu_case, "elements": s.query(0)["nelem"], "stats": st}))
     s.close()
 
@@ -259,6 +267,8 @@ def main():
     ap.add_argument("--ncu-case", type=int, default=0, metavar="N",
                     help="profiler driver: one short MIXED_TF32 solve on an N x N x 4 P=6 box (FP64, FP32 and "
                          "tensor-core applies, transfers and the coarse CG all launch); prints stats only")
+    ap.add_argument("--ncu-tcgen05", action="store_true",
+                    help="with --ncu-case: also launch the tcgen05 order-6 apply three times after the solve")
     ap.add_argument("--ncu-solve", default="", choices=["", "fp64", "mixed_fp32", "mixed_tf32", "asm"],
                     help="profiler driver: --steps solves of one form on the benchmark workload; prints stats only")
     a = ap.parse_args()
