@@ -689,6 +689,40 @@ def main():
                            "it lowers the residual, else the Chebyshev sweep"}
         ls.close()
         ps.close()
+        # the same comparison on a 16 x 16 x 4 box (element aspect ratio d_z / d_xy 0.64 instead of 2.5):
+        # longer training (200 snapshots x 20 steps) and the judge at tau = 0.7
+        sm = W.config_box3d(16, nl)
+        sxy = sem.sem_mesh_nodes2d(sm, P)
+        seta = sm.eta(sxy[:, 0], sxy[:, 1])
+        box16 = {}
+        for form in ("same_cycle_without_network", "learned_tau_0.7"):
+            o = dict(levels=levels_for(P), precision="mixed_fp32", outer="pdc", coarse_rtol=a.coarse_rtol, imax=400)
+            if form != "same_cycle_without_network":
+                o.update(smoother="learned", learned_tau=0.7)
+            sv = sem.Solver(sm, P, eta_nodal=seta, **o)
+            C_ = sv.coords(0)
+            d_ = torch.tensor(W.potential3d(*C_[sv.dirichlet_nodes(0)].T), device="cuda")
+            p_ = torch.empty(sv.query(0)["ndof"], dtype=torch.float64, device="cuda")
+            tr = None
+            if form != "same_cycle_without_network":
+                torch.cuda.synchronize()
+                t0_ = time.perf_counter()
+                l0_, l1_ = sv.train(200, 20, lr=1e-3, seed=7)
+                torch.cuda.synchronize()
+                tr = {"snapshots": 200, "steps_per_snapshot": 20, "seconds": time.perf_counter() - t0_,
+                      "heldout_loss_before": l0_, "heldout_loss_after": l1_}
+            for _ in range(2):
+                sv.solve(d_, p_, tol=1e-8)
+            torch.cuda.synchronize()
+            t0_ = time.perf_counter()
+            for _ in range(5):
+                st_ = sv.solve(d_, p_, tol=1e-8)
+            torch.cuda.synchronize()
+            box16[form] = {"ms_per_solve": (time.perf_counter() - t0_) / 5 * 1e3, "outer_iters": st_["iters"],
+                           "learned_accepts": st_["learned_accepts"], "learned_fallbacks": st_["learned_fallbacks"],
+                           "training": tr}
+            sv.close()
+        learned["box16x16x4"] = box16
 
     # the learned smoother's own tank: rounded-box hull cutout (0.3 L x 0.1 L, draft 0.3 h, curved
     # corners), 64 x 64 base grid, 2 + 2 layers, eta = 32 power-law cosine modes, P = 6
