@@ -128,3 +128,25 @@ def test_bad_arc_is_rejected_without_gpu(sem):
     with pytest.raises(sem.SemError) as e:
         sem.sem_setup(m, 2)
     assert e.value.status == sem.SEM_EINVAL and "circle" in sem.sem_last_error()
+
+
+def test_bad_hull_fields_are_rejected_without_gpu(sem):
+    # column heights outside 1..nlayers, non-finite interfaces, and the prism-only fields on a
+    # 2D mesh are refused before any device work
+    m = W.hull_tank(8)
+    m.col_layers = m.col_layers.copy()
+    m.col_layers[3] = m.nlayers + 1
+    with pytest.raises(sem.SemError) as e:
+        sem.sem_setup(m, 2)
+    assert e.value.status == sem.SEM_EINVAL and "col_layers" in sem.sem_last_error()
+    m = W.hull_tank(8)
+    m.z_iface = m.z_iface.copy()
+    m.z_iface[2, 1] = np.nan
+    with pytest.raises(sem.SemError) as e:
+        sem.sem_setup(m, 2)
+    assert "z_iface" in sem.sem_last_error()
+    s2 = W.config_slice2d()
+    s2.col_layers = np.ones(s2.tri.shape[0], dtype=np.int32)
+    with pytest.raises(sem.SemError) as e:
+        sem.sem_setup(s2, 2)
+    assert "prism meshes only" in sem.sem_last_error()
