@@ -690,7 +690,7 @@ def main():
         ls.close()
         ps.close()
         # the same comparison on a 16 x 16 x 4 box (element aspect ratio d_z / d_xy 0.64 instead of 2.5):
-        # longer training (200 snapshots x 20 steps) and the judge at tau = 0.7
+        # longer training (200 snapshots x 20 steps) and the residual test at tau = 0.7
         sm = W.config_box3d(16, nl)
         sxy = sem.sem_mesh_nodes2d(sm, P)
         seta = sm.eta(sxy[:, 0], sxy[:, 1])
