@@ -50,6 +50,7 @@ def test_default_options(sem):
     assert o.k_cheb == 5 and o.nu1 == 1 and o.nu2 == 1 and o.rtol == 1e-8 and o.cheb_lo == 0.01
     assert o.cheb_hi == 1.05 and o.lanczos_steps == 30 and o.learned_tau == 0.5 and o.batch_mode == 0 and o.autotune == 1
     assert o.asm_overlap == 1 and o.smoother == 0
+    assert o.coarse_rtol == 1e-2 and o.coarse_imax == 5000
 
 
 @pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6])
