@@ -38,9 +38,9 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_NOMINAL_TFLOPS = 1.25          # GB300 FP64 (profiling recipe's nominal table)
 FALLBACK_HBM_GBS = 6800.0
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the FP64 prism
-# apply, per launch (mean of four launches), scaled from the 48x48x4-prism capture
-# (18,432 elements; profiles/apply_fp64_p6_box48.md) to the 32,768-element benchmark
-# mesh by element count; reported as null once apply_prism.cu differs from the captured source.
+# apply, per launch (mean of four launches), scaled from a capture on the 48x48x4-prism
+# box (18,432 elements) to the 32,768-element benchmark mesh by element count; reported
+# as null once apply_prism.cu differs from the captured source.
 TRAFFIC = {("apply_fp64", 6): (350.860352e6 + 12.227136e6) * 32768 / 18432}
 TRAFFIC_SRC_SHA = "a51bb5326e701863"
 
@@ -48,7 +48,7 @@ TRAFFIC_SRC_SHA = "a51bb5326e701863"
 def workload_name(n, nl, P):
     return (f"3D sigma-prism box 2pi x 2pi x 1: {n}x{n} quads -> {2 * n * n} triangles x {nl} layers = "
             f"{2 * n * n * nl} prisms, P={P}, eta=0.1 sin(x)cos(y); PCG + p-multigrid V-cycle "
-            f"(Chebyshev-Jacobi k=5 on [0.01b, b], b = 1.05 lambda_hat (30 Lanczos steps), nu=1+1, FP64 coarse CG at order 1 to 1e-3) to rtol 1e-8")
+            f"(Chebyshev-Jacobi k=5 on [0.01b, b], b = 1.05 lambda_hat (30 Lanczos steps), nu=1+1, FP64 coarse CG at order 1 to 1e-2) to rtol 1e-8")
 
 
 def levels_for(P):

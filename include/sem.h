@@ -204,6 +204,9 @@ typedef struct {
     long long apply_tc_launches;
     double asm_ms;              /* profile = 1: summed event time of the finest-level Schwarz block kernels */
     long long asm_launches;
+    double lift_ms;             /* profile = 1: event time of the lifting apply (f = -A_FD phi~, only the
+                                   finest elements that touch a Dirichlet node); not in apply_ms */
+    long long lift_launches;
 } sem_stats;
 
 typedef struct sem_handle sem_handle;
@@ -381,10 +384,12 @@ sem_status sem_learned_train(sem_handle* h, int snapshots, int steps, double lr,
  * n <= 131072 rows (about 4.2 MB, held on every GPU that loads the library until
  * the process exits); larger n returns SEM_EINVAL.  The first call on a device
  * looks up that array's device address (with the device current), so make one
- * call before capturing a stream into a CUDA graph.  All calls share the array:
- * calls that overlap on the GPU race.  Synchronous: stops at ||r|| <= rtol ||b||
- * (SEM_OK) or after imax iterations (SEM_NOT_CONVERGED); *iters_host (may be
- * NULL) receives the iteration count; SEM_TIMEOUT if a grid-barrier wait ran out. */
+ * call before capturing any stream.  All calls share the array: calls that
+ * overlap on the GPU race.  Synchronous (it copies its status words to the host
+ * and waits for `stream`): stops at ||r|| <= rtol ||b|| (SEM_OK) or after imax
+ * iterations (SEM_NOT_CONVERGED, x holds the last iterate); *iters_host (may be
+ * NULL) receives the iteration count; SEM_NAN if the residual is not finite (a
+ * non-finite value in b, vals or dinv); SEM_TIMEOUT if a grid-barrier wait ran out. */
 sem_status sem_cg_csr_noalloc(long long n, const int* rowptr, const int* col, const double* vals,
                               const double* dinv, const double* b, double* x, double rtol, int imax,
                               int* iters_host, void* stream);

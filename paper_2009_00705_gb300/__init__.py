@@ -59,7 +59,7 @@ class SemStats(Structure):
                 ("inner_iters", c_longlong), ("learned_accepts", c_longlong), ("learned_fallbacks", c_longlong),
                 ("graph_iterations", c_longlong), ("apply32_ms", c_double), ("apply32_launches", c_longlong),
                 ("apply_tc_ms", c_double), ("apply_tc_launches", c_longlong), ("asm_ms", c_double),
-                ("asm_launches", c_longlong)]
+                ("asm_launches", c_longlong), ("lift_ms", c_double), ("lift_launches", c_longlong)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <mutex>
 #include <string>
@@ -1512,7 +1513,9 @@ extern "C" sem_status sem_cg_csr_noalloc(long long n, const int* rowptr, const i
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_cg, 512, 0);
     if (err == cudaSuccess && per_sm < 1) err = cudaErrorCooperativeLaunchTooLarge;
-    const int grid = (int)std::max<long long>(1, std::min<long long>((n + 127) / 128, (long long)sms));
+    // one CTA per SM at most, and never more CTAs than the partial-sum slots hold (three per CTA)
+    const long long cap = std::min<long long>((long long)sms, kNoAllocPart / 3);
+    const int grid = (int)std::max<long long>(1, std::min<long long>((n + 127) / 128, cap));
     if (err == cudaSuccess) err = cudaMemsetAsync(flags, 0, 8 * sizeof(int) + 4 * sizeof(unsigned), s);
     double rtol2 = rtol * rtol;
     unsigned extra = 0;
@@ -1523,8 +1526,10 @@ extern "C" sem_status sem_cg_csr_noalloc(long long n, const int* rowptr, const i
     }
     int hf[2] = {0, 0};
     unsigned timeout = 0;
+    double rr = 0.0;
     if (err == cudaSuccess) err = cudaMemcpyAsync(hf, flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
     if (err == cudaSuccess) err = cudaMemcpyAsync(&timeout, bar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(&rr, scal + S_CG_RR, sizeof(double), cudaMemcpyDeviceToHost, s);
     if (err == cudaSuccess) err = cudaStreamSynchronize(s);
     if (err != cudaSuccess) {
         set_error(std::string("sem_cg_csr_noalloc: ") + cudaGetErrorString(err));
@@ -1534,6 +1539,10 @@ extern "C" sem_status sem_cg_csr_noalloc(long long n, const int* rowptr, const i
     if (timeout) {
         set_error("sem_cg_csr_noalloc: a grid barrier wait ran out (device timeout)");
         return SEM_TIMEOUT;
+    }
+    if (!std::isfinite(rr)) {
+        set_error("sem_cg_csr_noalloc: non-finite residual (a non-finite value in b, vals or dinv)");
+        return SEM_NAN;
     }
     if (!hf[F_CG_DONE]) {
         set_error("sem_cg_csr_noalloc: rtol not reached within imax iterations");

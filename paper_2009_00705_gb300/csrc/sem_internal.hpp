@@ -174,6 +174,8 @@ struct sem_handle {
     long long apply32_launches = 0, apply_tc_launches = 0;
     double asm_ms = 0.0;
     long long asm_launches = 0;
+    double lift_ms = 0.0;
+    long long lift_launches = 0;
     long long fine_applies = 0;
     long long launches = 0;        // kernels launched since the counter was reset
     long long vcycles = 0;

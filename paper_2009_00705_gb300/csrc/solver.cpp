@@ -101,7 +101,8 @@ static void timed_end(sem_handle* h, int kind, cudaStream_t s) {
     if (kind == 0) h->apply_launches += 1;
     else if (kind == 1) h->apply32_launches += 1;
     else if (kind == 2) h->apply_tc_launches += 1;
-    else h->asm_launches += 1;
+    else if (kind == 3) h->asm_launches += 1;
+    else h->lift_launches += 1;
 }
 
 // Finest-level apply with optional event timing (profile = 1).
@@ -110,7 +111,7 @@ sem_status apply_level64(sem_handle* h, int li, const double* x, double* y, bool
     CKS(cudaMemsetAsync(y, 0, sizeof(double) * L.N, s));
     const bool timed = timed_begin(h, li, s);
     K(launch_apply64(L, x, y, lift, nullptr, s));
-    if (timed) timed_end(h, 0, s);
+    if (timed) timed_end(h, lift ? 4 : 0, s);     // the lifting apply covers only the elements at the surface
     if (li == 0) h->fine_applies += 1;
     return SEM_OK;
 }
@@ -132,7 +133,8 @@ void flush_events(sem_handle* h) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]) != cudaSuccess) continue;
         const int kind = h->ev_kind[i / 2];
-        (kind == 0 ? h->apply_ms : kind == 1 ? h->apply32_ms : kind == 2 ? h->apply_tc_ms : h->asm_ms) += ms;
+        (kind == 0 ? h->apply_ms : kind == 1 ? h->apply32_ms : kind == 2 ? h->apply_tc_ms : kind == 3 ? h->asm_ms
+                                                                                                : h->lift_ms) += ms;
     }
     h->ev_used = 0;
 }
@@ -1397,8 +1399,8 @@ sem_status laplace_solve(sem_handle* h, const double* rhs, const double* eta, do
     h->fine_applies = 0;
     h->vcycles = 0;
     h->coarse_iters_max = 0;
-    h->apply_ms = h->apply32_ms = h->apply_tc_ms = h->asm_ms = 0;
-    h->apply_launches = h->apply32_launches = h->apply_tc_launches = h->asm_launches = 0;
+    h->apply_ms = h->apply32_ms = h->apply_tc_ms = h->asm_ms = h->lift_ms = 0;
+    h->apply_launches = h->apply32_launches = h->apply_tc_launches = h->asm_launches = h->lift_launches = 0;
     h->launches = 0;
     h->inner_iters = 0;
     CKS(cudaMemsetAsync(h->sc.flags + F_LEARN_COUNT, 0, 2 * sizeof(int), s));
@@ -1457,6 +1459,8 @@ sem_status laplace_solve(sem_handle* h, const double* rhs, const double* eta, do
     st.apply_tc_launches = h->apply_tc_launches;
     st.asm_ms = h->asm_ms;
     st.asm_launches = h->asm_launches;
+    st.lift_ms = h->lift_ms;
+    st.lift_launches = h->lift_launches;
     st.kernel_launches = h->launches;
     st.inner_iters = h->inner_iters;
     if (h->opts.smoother == SEM_SMOOTH_LEARNED) {
