@@ -13,7 +13,9 @@ Modules:
   assemble  geometric factors and the assembled stiffness matrix (Eq. laplaceproblemdiscrete)
   solvers   Dirichlet lifting, direct solve, transfers (Section 4.1), Chebyshev
             smoothing, V-cycle (Algorithm 1), PDC (Algorithm 2), PCG (Algorithm 3), FGMRES
-  mlp       the per-element correction network (forward / backward) in FP64
+  mlp       the per-element correction network (forward / backward / Adam) in FP64
+  learned   one learned correction sweep (network correction, minimal-residual step,
+            residual verdict with the Chebyshev fallback)
 
 Parity pins: every function is pinned by tests in ``tests/test_oracle_*.py``
 against closed forms, invariants, brute force and library routines; functions

@@ -211,3 +211,27 @@ def test_airy_spectral_convergence_in_p():
     assert errs[-1] < 1e-7
     rates = errs[2:] / errs[1:-1]
     assert np.all(rates < 0.35), errs
+
+
+@pytest.mark.parametrize("mesh_fn,levels", [(lambda: W.slice2d(4, 2), [4, 2, 1]),
+                                            (lambda: W.config_box3d(3, 2), [3, 1]),
+                                            (lambda: W.hull_tank(8), [2, 1])])
+def test_apply_rows_equal_the_assembled_product(mesh_fn, levels):
+    # the row-by-row apply (used for sampled rows at full size) against the assembled
+    # sparse product, masked (y_F = A_FF x_F, y_D = x_D) and plain (y = A x), on rows that
+    # include Dirichlet nodes, nodes shared by many elements and the last node
+    prob = Problem(mesh_fn(), levels)
+    for li in range(len(levels)):
+        lev = prob.levels[li]
+        x = W.random_vector(lev.N, seed=40 + li)
+        rng = np.random.default_rng(li)
+        rows = np.unique(np.concatenate([rng.choice(lev.N, size=min(25, lev.N), replace=False),
+                                         lev.dirichlet[:3], lev.emap[0], [lev.N - 1]]))
+        full_m = prob.masked_apply(li, x)
+        full_p = prob.stiffness(li) @ x
+        got_m = prob.apply_rows(li, x, rows, masked=True)
+        got_p = prob.apply_rows(li, x, rows, masked=False)
+        scale = np.abs(full_p).max()
+        assert np.abs(got_m - full_m[rows]).max() <= 1e-12 * scale
+        assert np.abs(got_p - full_p[rows]).max() <= 1e-12 * scale
+        assert lev.dmask[rows].any() and (~lev.dmask[rows]).any()
