@@ -357,6 +357,22 @@ sem_status sem_mlp_forward(sem_handle* h, int B, const float* X_dev, float* Y_de
  * like the weights), for B <= number of finest elements; synchronous. */
 sem_status sem_mlp_gradient(sem_handle* h, int B, const float* X_dev, const float* T_dev, double* loss_host,
                             float* dW1, float* db1, float* dW2, float* db2, void* stream);
+/* One Adam step (Kingma & Ba; beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) of the
+ * network's FP32 master weights with caller-supplied gradients (host arrays shaped like
+ * the weights), the kernel sem_learned_train uses after each gradient; the BF16 copies
+ * are refreshed.  reset = 1 zeroes the moments and the step count first.  Synchronous. */
+sem_status sem_mlp_adam(sem_handle* h, const float* dW1, const float* db1, const float* dW2, const float* db2,
+                        double lr, int reset, void* stream);
+/* One learned sweep on the finest level, as it runs inside the FP32 V-cycle (the
+ * analogue of the weighted Schwarz correction of Section 4.3, Eqs. Mass and weights):
+ * r = f - A u, z = D^{-1} r, per element s_e = ||z_e||, delta = W sum_e Q_e^T s_e
+ * MLP(z_e / s_e) (W: inverse node multiplicity), alpha = (r, A delta) / ||A delta||^2;
+ * u <- u + alpha delta when alpha > 0 and ||r - alpha A delta|| < learned_tau ||r||,
+ * otherwise the Chebyshev sweep it replaces.  f, u: FP32 device vectors of the finest
+ * level with zero Dirichlet entries; u is updated in place.  *accepted and *alpha
+ * (host, may be NULL) receive the verdict and the step (0 when rejected).  Synchronous. */
+sem_status sem_learned_sweep(sem_handle* h, const float* f_dev, float* u_dev, int* accepted_host,
+                             double* alpha_host, void* stream);
 /* Train the network with Adam (learning rate lr) on residual/error pairs that the plain
  * solver generates: for each of `snapshots` seeded random errors e0 (SplitMix64 of
  * (seed, snapshot, node)), the plain FP32 V-cycle iteration for A u = A e0 from u = 0

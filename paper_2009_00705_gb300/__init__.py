@@ -29,7 +29,7 @@ EXPORTS = ("sem_default_options", "sem_mesh_nodes2d", "sem_setup", "sem_destroy"
            "sem_dirichlet_nodes", "sem_node_coords", "sem_element_map", "sem_lambda_max", "sem_diagonal",
            "sem_apply", "sem_apply32", "sem_update_eta", "sem_fnpf_rhs", "sem_fnpf_step", "pmg_vcycle", "laplace_solve", "laplace_solve_host", "sem_last_error",
            "sem_cg_csr_noalloc", "sem_mlp_get_weights", "sem_mlp_set_weights", "sem_mlp_forward",
-           "sem_mlp_gradient", "sem_learned_train", "laplace_solve_batch", "sem_tile_shapes",
+           "sem_mlp_gradient", "sem_mlp_adam", "sem_learned_sweep", "sem_learned_train", "laplace_solve_batch", "sem_tile_shapes",
            "sem_asm_subdomains", "sem_asm_apply", "sem_asm_apply32")
 
 
@@ -123,10 +123,12 @@ def lib():
     L.sem_mlp_gradient.argtypes = [c_void_p, c_int, c_void_p, c_void_p, POINTER(c_double), fp, fp, fp, fp, c_void_p]
     L.sem_learned_train.argtypes = [c_void_p, c_int, c_int, c_double, ctypes.c_ulonglong, POINTER(c_double),
                                     POINTER(c_double), c_void_p]
+    L.sem_mlp_adam.argtypes = [c_void_p, fp, fp, fp, fp, c_double, c_int, c_void_p]
+    L.sem_learned_sweep.argtypes = [c_void_p, c_void_p, c_void_p, POINTER(c_int), POINTER(c_double), c_void_p]
     L.laplace_solve_batch.argtypes = [POINTER(c_void_p), c_int, POINTER(c_void_p), c_double, POINTER(c_void_p),
                                       POINTER(SemStats), c_void_p]
     for name in ("sem_mlp_get_weights", "sem_mlp_set_weights", "sem_mlp_forward", "sem_mlp_gradient",
-                 "sem_learned_train", "laplace_solve_batch"):
+                 "sem_mlp_adam", "sem_learned_sweep", "sem_learned_train", "laplace_solve_batch"):
         getattr(L, name).restype = c_int
     for name in ("sem_mesh_nodes2d", "sem_setup", "sem_query", "sem_dirichlet_nodes", "sem_node_coords",
                  "sem_element_map", "sem_lambda_max", "sem_diagonal", "sem_apply", "sem_apply32", "sem_update_eta", "sem_fnpf_rhs", "sem_fnpf_step", "pmg_vcycle",
@@ -408,6 +410,23 @@ def sem_mlp_gradient(h: int, hidden: int, B: int, X, T, stream=None):
     return loss.value, g
 
 
+def sem_mlp_adam(h: int, grads: dict, lr: float, reset: bool = False, stream=None) -> None:
+    """One Adam step of the network's master weights with the given gradients (host arrays
+    shaped like the weights: keys W1, b1, W2, b2)."""
+    fp = POINTER(ctypes.c_float)
+    g = {k: np.ascontiguousarray(grads[k], dtype=np.float32) for k in ("W1", "b1", "W2", "b2")}
+    _check(lib().sem_mlp_adam(h, *(g[k].ctypes.data_as(fp) for k in ("W1", "b1", "W2", "b2")), float(lr),
+                              1 if reset else 0, _stream(stream)))
+
+
+def sem_learned_sweep(h: int, f, u, stream=None):
+    """One learned sweep on the finest level (FP32 device vectors; u updated in place).
+    Returns (accepted, alpha)."""
+    acc, alpha = c_int(0), c_double(0.0)
+    _check(lib().sem_learned_sweep(h, _ptr(f), _ptr(u), byref(acc), byref(alpha), _stream(stream)))
+    return bool(acc.value), alpha.value
+
+
 def sem_learned_train(h: int, snapshots: int, steps: int, lr: float = 1e-3, seed: int = 1, stream=None):
     """(loss of the first step, loss of the last step)."""
     l0, l1 = c_double(0.0), c_double(0.0)
@@ -524,6 +543,12 @@ class Solver:
 
     def mlp_forward(self, B, X, Y, stream=None):
         sem_mlp_forward(self.h, B, X, Y, stream)
+
+    def adam_step(self, grads, lr, reset=False, stream=None):
+        sem_mlp_adam(self.h, grads, lr, reset, stream)
+
+    def learned_sweep(self, f, u, stream=None):
+        return sem_learned_sweep(self.h, f, u, stream)
 
     def train(self, snapshots, steps, lr=1e-3, seed=1, stream=None):
         return sem_learned_train(self.h, snapshots, steps, lr, seed, stream)

@@ -1528,6 +1528,46 @@ sem_status sem_mlp_forward(sem_handle* h, int B, const float* X, float* Y, void*
     return SEM_OK;
 }
 
+sem_status sem_mlp_adam(sem_handle* h, const float* dW1, const float* db1, const float* dW2, const float* db2,
+                        double lr, int reset, void* stream) {
+    CKST(check_mlp(h));
+    if (!dW1 || !db1 || !dW2 || !db2 || !(lr > 0.0)) { set_error("sem_mlp_adam: NULL gradient or lr <= 0"); return SEM_EINVAL; }
+    cudaStream_t s = as_stream(stream);
+    MlpNet& n = h->net;
+    const long long cnt[4] = {(long long)n.H * n.nin, n.H, (long long)n.nout * n.H, n.nout};
+    if (reset) {
+        for (int k = 0; k < 4; ++k) {
+            CKS(cudaMemsetAsync(h->adam.m[k], 0, sizeof(float) * cnt[k], s));
+            CKS(cudaMemsetAsync(h->adam.v[k], 0, sizeof(float) * cnt[k], s));
+        }
+        h->adam.t = 0;
+    }
+    CKS(cudaMemcpyAsync(h->grads.dW1, dW1, sizeof(float) * cnt[0], cudaMemcpyHostToDevice, s));
+    CKS(cudaMemcpyAsync(h->grads.db1, db1, sizeof(float) * cnt[1], cudaMemcpyHostToDevice, s));
+    CKS(cudaMemcpyAsync(h->grads.dW2, dW2, sizeof(float) * cnt[2], cudaMemcpyHostToDevice, s));
+    CKS(cudaMemcpyAsync(h->grads.db2, db2, sizeof(float) * cnt[3], cudaMemcpyHostToDevice, s));
+    CKS(mlp_adam(n, h->grads, h->adam, (float)lr, s));
+    CKS(cudaStreamSynchronize(s));
+    h->mlp_trained = true;
+    return SEM_OK;
+}
+
+sem_status sem_learned_sweep(sem_handle* h, const float* f, float* u, int* accepted, double* alpha, void* stream) {
+    CKST(check_mlp(h));
+    if (!f || !u) { set_error("sem_learned_sweep: NULL vector"); return SEM_EINVAL; }
+    cudaStream_t s = as_stream(stream);
+    CKS(cudaMemsetAsync(h->sc.flags + F_LEARN_ACCEPT, 0, sizeof(int), s));
+    CKST(learned_sweep(h, f, u, s));
+    int acc = 0;
+    double a = 0.0;
+    CKS(cudaMemcpyAsync(&acc, h->sc.flags + F_LEARN_ACCEPT, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CKS(cudaMemcpyAsync(&a, h->sc.scal + S_ALPHA, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CKS(cudaStreamSynchronize(s));
+    if (accepted) *accepted = acc;
+    if (alpha) *alpha = a;
+    return SEM_OK;
+}
+
 sem_status sem_mlp_gradient(sem_handle* h, int B, const float* X, const float* T, double* loss, float* dW1,
                             float* db1, float* dW2, float* db2, void* stream) {
     CKST(check_mlp(h));

@@ -1,6 +1,7 @@
-"""The learned smoothing sweep: network forward/gradients against the FP64 oracle,
-training on solver-generated residual/error pairs, the residual judge with its
-Chebyshev fallback, and what the trained network gains over the plain method."""
+"""The learned smoothing sweep: network forward/gradients and Adam against the FP64
+oracle, one whole sweep (network correction, minimal-residual step, verdict,
+Chebyshev fallback) against the oracle's sweep, training on solver-generated
+residual/error pairs, and what the trained network gains over the plain method."""
 import time
 
 import numpy as np
@@ -11,6 +12,7 @@ import workloads as W
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+from oracle import learned as L  # noqa: E402
 from oracle import mlp as M  # noqa: E402
 from oracle import solvers as S  # noqa: E402
 from oracle.assemble import Problem  # noqa: E402
@@ -151,3 +153,84 @@ def test_trained_sweep_gains_on_a_16x16x4_box(sem):
     print(f"\n16x16x4 box: PDC iterations plain {its['plain'][0]}, with the trained sweep {its['learned'][0]} "
           f"({its['learned'][1]} sweeps accepted)")
     assert its["learned"][0] < its["plain"][0] and its["learned"][1] > 0, its
+
+
+def test_adam_kernel_matches_the_oracle_over_three_steps(sem):
+    # the library's Adam (FP32 masters) against oracle.mlp.adam_step in FP64 from the same
+    # FP32 weights and gradients: three steps with different gradients, so the bias
+    # corrections and both decay rates matter; a wrong beta moves a weight by ~1e-4 here
+    mesh = W.config_box3d(3, 2)
+    prob, s = _solver(sem, mesh, [3, 2, 1], mlp_hidden=24)
+    npe = prob.levels[0].ref.Np
+    rng = np.random.default_rng(23)
+    w = {"W1": rng.standard_normal((24, npe)) * 0.3, "b1": rng.standard_normal(24) * 0.1,
+         "W2": rng.standard_normal((npe, 24)) * 0.3, "b2": rng.standard_normal(npe) * 0.1}
+    w = {k: v.astype(np.float32) for k, v in w.items()}
+    s.set_mlp_weights(w["W1"], w["b1"], w["W2"], w["b2"])
+    keys = ("W1", "b1", "W2", "b2")
+    params = [w[k].astype(np.float64) for k in keys]
+    m = [np.zeros_like(p) for p in params]
+    v = [np.zeros_like(p) for p in params]
+    lr = 1e-2
+    for t in range(1, 4):
+        g = {k: rng.standard_normal(w[k].shape).astype(np.float32) for k in keys}
+        s.adam_step(g, lr, reset=(t == 1))
+        M.adam_step(params, [g[k].astype(np.float64) for k in keys], m, v, t=t, lr=lr)
+    got = s.mlp_weights()
+    for k, ref in zip(keys, params):
+        assert np.abs(got[k] - ref).max() <= 1e-6, k
+    s.close()
+
+
+def _sweep_case(sem, hidden, tau, weights_fn):
+    mesh = W.config_box3d(3, 2)
+    levels = [3, 2, 1]
+    prob, s = _solver(sem, mesh, levels, mlp_hidden=hidden, learned_tau=tau)
+    lev = prob.levels[0]
+    npe = lev.ref.Np
+    W1, b1, W2, b2 = weights_fn(npe, hidden)
+    s.set_mlp_weights(W1, b1, W2, b2)
+    ops = S.MGOperators(prob, k_cheb=5, lo=0.01, hi=1.05)    # the library's default smoother
+    f = np.where(lev.dmask, 0.0, W.random_vector(lev.N, seed=51)).astype(np.float32)
+    u = (0.3 * np.where(lev.dmask, 0.0, W.random_vector(lev.N, seed=52))).astype(np.float32)
+    fd = torch.tensor(f, device="cuda")
+    ud = torch.tensor(u, device="cuda")
+    acc, alpha = s.learned_sweep(fd, ud)
+    # the oracle takes the weights the GEMMs read (BF16 copies of W1, W2)
+    net = (M.bf16_round(W1), b1.astype(np.float64), M.bf16_round(W2), b2.astype(np.float64))
+    ref = L.learned_sweep(ops, net, f.astype(np.float64), u.astype(np.float64), tau)
+    s.close()
+    return acc, alpha, ud.cpu().numpy().astype(np.float64), ref
+
+
+# FP32 arithmetic throughout the sweep (apply, Jacobi scaling, network with K <= 2 Np
+# accumulations, scatter): each result within a few 1e-6 of the FP64 oracle; 5e-5 is the bound
+SWEEP_TOL = 5e-5
+
+
+def test_learned_sweep_with_an_identity_network_matches_the_oracle(sem):
+    def identity(npe, H):
+        I = np.eye(npe, dtype=np.float32)
+        return (np.vstack([I, -I]), np.zeros(H, np.float32), np.hstack([I, -I]), np.zeros(npe, np.float32))
+    acc, alpha, u, ref = _sweep_case(sem, 80, 1.0, identity)
+    assert ref.accepted and acc
+    assert abs(alpha - ref.alpha) <= SWEEP_TOL * ref.alpha
+    assert np.abs(u - ref.u).max() <= SWEEP_TOL * np.abs(ref.u).max()
+
+
+@pytest.mark.parametrize("tau", [1.0, 0.05])
+def test_learned_sweep_with_a_random_network_matches_the_oracle(sem, tau):
+    def rand(npe, H):
+        rng = np.random.default_rng(61)
+        return ((rng.standard_normal((H, npe)) * 0.2).astype(np.float32), (rng.standard_normal(H) * 0.05).astype(np.float32),
+                (rng.standard_normal((npe, H)) * 0.2).astype(np.float32), (rng.standard_normal(npe) * 0.05).astype(np.float32))
+    acc, alpha, u, ref = _sweep_case(sem, 32, tau, rand)
+    # the verdict is compared where the oracle's margin from the threshold exceeds the FP32 error
+    margin = abs(ref.rr_after - tau * tau * ref.rr) / ref.rr
+    if margin > 1e-3:
+        assert acc == ref.accepted
+    if acc == ref.accepted:
+        assert abs(alpha - ref.alpha) <= SWEEP_TOL * max(abs(ref.alpha), 1e-30)
+        assert np.abs(u - ref.u).max() <= SWEEP_TOL * np.abs(ref.u).max()
+    if tau == 0.05:
+        assert not ref.accepted          # the Chebyshev fallback path
