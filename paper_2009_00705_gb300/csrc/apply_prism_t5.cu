@@ -1,26 +1,37 @@
 // Prism apply of order 6 on the fifth-generation tensor cores (tcgen05) for the
 // smoothing sweeps of the mixed-precision V-cycle (Eq. laplaceproblemdiscrete; the
-// same contraction as apply_prism.cu and apply_prism_tc.cu).  Per CTA pass of 16
-// elements the two triangle contractions are TF32 tcgen05.mma with M = 128 rows
-// (16 elements x 8 vertical points, the eighth zero) and FP32 accumulators in
-// tensor memory:
+// same contraction as apply_prism.cu and apply_prism_tc.cu).  A CTA pass takes 16
+// elements; the two triangle contractions are TF32 tcgen05.mma with M = 128 rows,
+// row r = 16 qz + b (vertical point qz = 0..7, the eighth zero, element b = 0..15),
+// and FP32 accumulators in tensor memory:
 //
-//   forward   [Ur | Us](e,qz; qt) = U(e,qz; n) [Dr | Ds](n; qt),  Ut = W(e,qz; n) Bt(n; qt)
+//   forward   [Ur | Us](r; qt) = U(r; n) [Dr | Ds](n; qt),  Ut = W(r; n) Bt(n; qt)
 //             (K = n: 28 -> 32, N = qt: 49 -> 64, three accumulators of 64 columns)
-//   backward  Xr(e,qz; n) = Vr(e,qz; qt) Dr(qt; n) + Vs Ds,  Xt = Vt Bt
+//   backward  Xr(r; n) = Vr(r; qt) Dr(qt; n) + Vs Ds,  Xt = Vt Bt
 //             (K = qt: 49 -> 56, N = n: 28 -> 32, two accumulators of 32 columns)
 //
-// The forward operands come from shared memory through matrix descriptors (K-major, no
-// swizzle: 8-row x 16-byte core matrices, K-adjacent ones 128 B apart, row groups K * 32 B
-// apart), so the contractions put no load on the LSU pipe that bounds the warp-MMA form.
-// Between the two, each thread owns one accumulator row (tcgen05.ld from its warp's lane
-// quarter), applies the BF16 geometric factors and writes V over the accumulators it read
-// (tcgen05.st): the backward MMAs take V as their A operand straight from tensor memory,
-// so no shared memory holds it.  The vertical stages, the gather and the direct-stiffness
-// summation stay on the SIMT pipes.  One thread issues the MMAs and commits them to an
-// mbarrier; every wait is bounded (1 s), after which the kernel sets an error flag and
-// returns with its tensor memory freed.  Two CTAs per SM (102 KB of shared memory and 256
-// of the SM's 512 TMEM columns each), so one computes while the other waits.
+// The kernel is warp-specialised and pipelined over passes, one CTA per SM:
+//   * warps 0-3 and 4-7 are two compute groups that take alternate passes, each with
+//     its own 256 TMEM columns and operand buffers, so one group's memory waits
+//     overlap the other's arithmetic.  A group gathers x through the element map
+//     and forms U = Bz x, W = Dz x (SIMT, written as K-major TF32 operands), one of
+//     its threads issues the forward MMAs, the group applies the geometric factors
+//     between tcgen05.ld and tcgen05.st (V overwrites the accumulators and is the A
+//     operand of the backward MMAs straight from tensor memory), then stages Xr, Xt
+//     through shared memory for the transposed vertical stage and the atomic
+//     direct-stiffness summation;
+//   * warp 8 streams each pass's element map (bulk copy, two buffers per group);
+//   * warp 9 streams the BF16 geometric factors through a ring of six slots, one
+//     8-column chunk of quadrature points per slot: the factors are stored per pass
+//     of 16 elements chunk by chunk ([chunk][factor][qz][element][8 qt]), so the
+//     next pass's chunk streams in as soon as this pass's has been used, and every
+//     read of a slot is a conflict-free 16-byte load.
+// The operands sit in shared memory in the canonical no-swizzle K-major layout
+// (8-row x 16-byte core matrices, K-adjacent ones 128 B apart, row groups K * 32 B
+// apart); the row order r = 16 qz + b makes the gather's operand stores conflict-free.
+// Every mbarrier wait is bounded (1 s); a wait that runs out sets the error flag, the
+// other roles stop at their next wait or group barrier, every role gives the copies and
+// MMAs it started a second bounded wait, and the tensor memory is freed.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -32,39 +43,49 @@ namespace sem {
 
 namespace {
 
-constexpr int kT5SMs = 152;
-constexpr int kT5Threads = 256;
-constexpr unsigned long long kT5WaitNs = 1000000000ULL;
+constexpr int kT6Threads = 320;                   // 8 compute warps + 2 producer warps
+constexpr unsigned long long kT6WaitNs = 1000000000ULL;
 
-constexpr int NT = 28, NZ = 7, QT = 49, QZ = 7, Np = NT * NZ, QTP = 50, GE = 6 * QZ * QTP;
-constexpr int EB = 16;                 // elements per pass: 16 x 8 rows = M = 128
+constexpr int NT = 28, NZ = 7, QT = 49, QZ = 7, Np = NT * NZ;
+constexpr int EB = 16;                 // elements per pass
 constexpr int KF = 32, NF = 64;        // forward K (n) and N (qt), padded
 constexpr int KB = 56, NB = 32;        // backward K (qt) and N (n), padded
+constexpr int NCH = 7;                 // factor chunks per pass: 6 x 8 quadrature points + 1
+constexpr int NSLOT = 6;               // factor ring slots
+constexpr uint32_t CH_BYTES = 6 * QZ * EB * 8 * 2;             // 10752
+constexpr uint32_t CH_LAST = 6 * QZ * EB * 1 * 2;              // 1344
+constexpr uint32_t PASS_G = 6 * CH_BYTES + CH_LAST;            // 65856 bytes of factors per pass
+static_assert(PASS_G == (uint32_t)EB * 6 * QZ * QT * 2, "factor chunks cover the pass");
+constexpr uint32_t MAP_BYTES = EB * Np * 4;                    // 12544
+constexpr int XS = 8 * 16 + 16;        // X staging: floats per node n ([n][qz][b], padded)
 
 // byte offset of entry (r, k) of a K-major operand with K columns
 __host__ __device__ constexpr uint32_t opoff(int r, int k, int K) {
     return (uint32_t)((r >> 3) * (K * 32) + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4);
 }
 
-constexpr uint32_t SZ_BF = NF * KF * 4;          // one forward reference operand
-constexpr uint32_t SZ_BB = NB * KB * 4;          // one backward reference operand
-constexpr uint32_t SZ_AF = 128 * KF * 4;         // U, W
-constexpr uint32_t SZ_MAP = EB * Np * 4;
-constexpr uint32_t OFF_BF = 0;                   // Dr, Ds, Bt as (qt, n)
-constexpr uint32_t OFF_BB = OFF_BF + 3 * SZ_BF;  // Dr, Ds, Bt as (n, qt)
-constexpr uint32_t OFF_U = OFF_BB + 3 * SZ_BB;  // U, W; after the forward MMAs: Xr, Xt staging
-constexpr uint32_t OFF_W = OFF_U + SZ_AF;
-constexpr uint32_t OFF_X = OFF_U;
-constexpr uint32_t OFF_MAP = OFF_W + SZ_AF;      // two map buffers
-constexpr uint32_t OFF_Z = OFF_MAP + 2 * SZ_MAP; // Bz, Dz as [QZ][NZ] floats
-constexpr uint32_t SMEM = OFF_Z + 2 * QZ * NZ * 4 + 8;   // multiple of 16
-constexpr uint32_t SZ_X = EB * NT * 8 * 4;       // Xr or Xt staging, [EB][NT][8]
-static_assert(SMEM % 16 == 0 && 2 * (SMEM + 2048) <= 233472, "two CTAs per SM");
-static_assert(2 * SZ_X <= 2 * SZ_AF, "X staging fits in the U, W region");
-static_assert(OFF_MAP % 16 == 0 && SZ_MAP % 16 == 0, "bulk copies of the map land on 16-byte boundaries");
-static_assert((EB * Np * 4) % 16 == 0, "every pass's map block starts on a 16-byte boundary");
+constexpr uint32_t SZ_BF = NF * KF * 4;           // one forward reference operand (8192)
+constexpr uint32_t SZ_BB = NB * KB * 4;           // one backward reference operand (7168)
+constexpr uint32_t SZ_A = 128 * KF * 4;           // U or W (16384)
+constexpr uint32_t OFF_BF = 0;                    // Dr, Ds, Bt as (qt, n)
+constexpr uint32_t OFF_BB = OFF_BF + 3 * SZ_BF;   // Dr, Ds, Bt as (n, qt)
+constexpr uint32_t OFF_UW = OFF_BB + 3 * SZ_BB;   // per group: U, W; after the forward MMAs Xr, Xt staging
+constexpr uint32_t OFF_MAP = OFF_UW + 4 * SZ_A;   // [group][buffer] element maps
+constexpr uint32_t OFF_G = OFF_MAP + 4 * MAP_BYTES;   // factor ring
+constexpr uint32_t SMEM = OFF_G + NSLOT * CH_BYTES;
+static_assert(SMEM <= 232448 - 512, "within one CTA's shared memory");
+static_assert(OFF_UW % 1024 == 0 && OFF_MAP % 16 == 0 && OFF_G % 16 == 0 && CH_BYTES % 16 == 0, "alignment");
+static_assert((NT * XS) * 4 <= SZ_A, "Xr / Xt staging fits in U / W");
 
-constexpr uint32_t TM_DR = 0, TM_DS = 64, TM_DT = 128, TM_XR = 192, TM_XT = 224, TM_COLS = 256;
+// tensor memory columns of a group (base 0 or 256)
+constexpr uint32_t TM_UR = 0, TM_US = 64, TM_UT = 128, TM_XR = 192, TM_XT = 224, TM_GROUP = 256;
+
+// the vertical factors Bz, Dz ([QZ][NZ]) as a kernel argument: every FMA of the vertical
+// stages reads its coefficient from the constant bank
+struct Vert {
+    float bz[QZ * NZ];
+    float dz[QZ * NZ];
+};
 
 // instruction descriptor of kind::tf32: F32 accumulator, TF32 A and B, both K-major
 __host__ __device__ constexpr uint32_t idesc(int M, int N) {
@@ -88,43 +109,62 @@ __device__ __forceinline__ uint32_t to_tf32(float f) {
     return r;
 }
 
-__device__ __forceinline__ unsigned long long t5_ns() {
+__device__ __forceinline__ unsigned long long t6_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
 
-__device__ bool t5_wait(uint32_t bar, uint32_t parity) {
-    const unsigned long long t0 = t5_ns();
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Wait for phase `parity` of mbarrier `bar`.  Returns false when another role has failed
+// (honour_fail) or after kT6WaitNs, in which case the failure is recorded.
+__device__ bool t6_wait(uint32_t bar, uint32_t parity, volatile int* fail, int* err, bool honour_fail = true) {
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = t6_ns();
     for (;;) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if (t5_ns() - t0 > kT5WaitNs) return false;
+        if (mbar_try(bar, parity)) return true;
+        if (honour_fail && *fail) return false;
+        if (t6_ns() - t0 > kT6WaitNs) {
+            *fail = 1;
+            atomicExch(err, 1);
+            return false;
+        }
     }
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 // one thread: bulk-copy `bytes` (a multiple of 16) from global to shared, completing on `bar`
-__device__ void t5_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+__device__ void t6_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-    const char* s = reinterpret_cast<const char*>(src);
-    for (uint32_t off = 0; off < bytes; off += 16384u) {
-        const uint32_t n = (bytes - off < 16384u) ? (bytes - off) : 16384u;
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                         dst + off),
-                     "l"(s + off), "r"(n), "r"(bar)
-                     : "memory");
-    }
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
 }
 
 __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
         "l"(a), "l"(b), "r"(id), "r"(acc)
+        : "memory");
+}
+
+// D (tensor memory) = A (tensor memory) B^T (shared memory)
+__device__ __forceinline__ void mma_tf32_ta(uint32_t tmem, uint32_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}" ::"r"(tmem),
+        "r"(a), "l"(b), "r"(id), "r"(acc)
         : "memory");
 }
 
@@ -152,36 +192,52 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8])
                  : "memory");
 }
 
-// D (tensor memory) = A (tensor memory) B^T (shared memory)
-__device__ __forceinline__ void mma_tf32_ta(uint32_t tmem, uint32_t a, uint64_t b, uint32_t id, uint32_t acc) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}" ::"r"(tmem),
-        "r"(a), "l"(b), "r"(id), "r"(acc)
-        : "memory");
-}
-
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// barrier of one compute group (128 threads; ids 1 and 2)
+__device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory"); }
+// the same barrier returning whether any thread of the group passed v = true (uniform result)
+__device__ __forceinline__ bool group_sync_any(int g, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, 128, p;\n selp.u32 %0, 1, 0, q;\n}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(1 + g)
+        : "memory");
+    return r != 0;
+}
 
-__global__ void __launch_bounds__(kT5Threads, 2)
-    k_apply_prism_t5(int E, int N, const int* __restrict__ map, const __nv_bfloat16* __restrict__ G16,
-                     const float* __restrict__ refm, const float* __restrict__ x, float* __restrict__ y,
-                     const int* __restrict__ skip, int* err) {
+__device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
+
+__global__ void __launch_bounds__(kT6Threads, 1)
+    k_apply_prism_t6(int E, int N, int npass, const int* __restrict__ map, const __nv_bfloat16* __restrict__ G6,
+                     const float* __restrict__ refm, const __grid_constant__ Vert vc, const float* __restrict__ x,
+                     float* __restrict__ y, const int* __restrict__ skip, int* err) {
     if (skip != nullptr && *skip) return;
     extern __shared__ __align__(1024) unsigned char sm[];
-    __shared__ __align__(8) unsigned long long mbar[2];   // [0] MMA completion, [1] element-map copies
+    // [0..3] map full [g][buf], [4..7] map empty, [8..13] factor slot full, [14..19] slot empty,
+    // [20, 21] MMA completion of group 0 / 1
+    __shared__ __align__(8) unsigned long long mbar[22];
     __shared__ uint32_t s_tmem;
     __shared__ int s_fail;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t sbase = smem_u32(sm);
-    const uint32_t bara = smem_u32(&mbar[0]), barm = smem_u32(&mbar[1]);
+    const uint32_t mb0 = smem_u32(&mbar[0]);
+    auto bar_mapf = [&](int g, int b) { return mb0 + 8u * (uint32_t)(2 * g + b); };
+    auto bar_mape = [&](int g, int b) { return mb0 + 8u * (uint32_t)(4 + 2 * g + b); };
+    auto bar_slotf = [&](int s) { return mb0 + 8u * (uint32_t)(8 + s); };
+    auto bar_slote = [&](int s) { return mb0 + 8u * (uint32_t)(14 + s); };
+    auto bar_mma = [&](int g) { return mb0 + 8u * (uint32_t)(20 + g); };
+    volatile int* fail = &s_fail;
 
     // every pad entry of every operand must be zero
-    for (uint32_t i = tid; i < SMEM / 16; i += kT5Threads) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
+    for (uint32_t i = tid; i < OFF_MAP / 16; i += kT6Threads) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
     __syncthreads();
-    for (int i = tid; i < QT * NT; i += kT5Threads) {
+    for (int i = tid; i < QT * NT; i += kT6Threads) {
         const int qt = i / NT, n = i - qt * NT;
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
@@ -191,18 +247,18 @@ __global__ void __launch_bounds__(kT5Threads, 2)
             *reinterpret_cast<float*>(sm + OFF_BB + m * SZ_BB + opoff(n, qt, KB)) = v;
         }
     }
-    float* sZ = reinterpret_cast<float*>(sm + OFF_Z);
-    for (int i = tid; i < 2 * QZ * NZ; i += kT5Threads) sZ[i] = refm[6 * QT * NT + i];   // Bz, Dz as [QZ][NZ]
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                     "r"(TM_COLS)
+                     "r"(2 * TM_GROUP)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
         s_fail = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bara) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barm) : "memory");
+        for (int i = 0; i < 22; ++i) {
+            const uint32_t cnt = (i >= 14 && i < 20) ? 4u : 1u;      // slot empty: one arrival per consumer warp
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb0 + 8u * i), "r"(cnt) : "memory");
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     fence_async_smem();
@@ -210,208 +266,291 @@ __global__ void __launch_bounds__(kT5Threads, 2)
     __syncthreads();
     fence_after();
     const uint32_t tmem = s_tmem;
-    const uint32_t idF = idesc(128, NF), idB = idesc(128, NB);
-    const int stride = gridDim.x * EB;
-    uint32_t pa = 0, pm = 0;
-    int buf = 0;
-    if (tid == 0 && blockIdx.x * EB < E) {
-        fence_async_smem();
-        const int e = blockIdx.x * EB;
-        t5_copy(sbase + OFF_MAP, map + (size_t)e * Np, (uint32_t)min(EB, E - e) * Np * 4u, barm);
-    }
-    // this thread's accumulator row in the epilogues: lane quarter of its warp
-    const int q4 = warp & 3, half = warp >> 2;
-    const int row = 32 * q4 + lane, rb = row >> 3, rqz = row & 7;
-    const uint32_t trow = tmem + ((uint32_t)(32 * q4) << 16);
+    const int first = blockIdx.x, step = gridDim.x;
 
-    for (int e0 = blockIdx.x * EB; e0 < E; e0 += stride) {
-        const int nb = min(EB, E - e0);
-        const int* sMap = reinterpret_cast<const int*>(sm + OFF_MAP + buf * SZ_MAP);
-        if (!t5_wait(barm, pm)) s_fail = 1; else pm ^= 1u;
-        __syncthreads();
-        if (s_fail) break;
-        // the next pass's map into the other buffer (its last reader finished last pass)
-        if (tid == 0 && e0 + stride < E) {
-            fence_async_smem();
-            const int en = e0 + stride;
-            t5_copy(sbase + OFF_MAP + (buf ^ 1) * SZ_MAP, map + (size_t)en * Np, (uint32_t)min(EB, E - en) * Np * 4u,
-                    barm);
-        }
-        {   // the next pass's factors into L2 while this one computes
-            const int en = e0 + stride;
-            if (en < E) {
-                const char* g0 = reinterpret_cast<const char*>(G16 + (size_t)en * GE);
-                const size_t gb = (size_t)min(EB, E - en) * GE * 2;
-                for (size_t off = (size_t)tid * 128; off < gb; off += (size_t)kT5Threads * 128)
-                    asm volatile("prefetch.global.L2 [%0];" ::"l"(g0 + off));
+    if (warp == 8) {
+        // ------------------------------------------------------------ element-map producer
+        if (lane == 0) {
+            int issued[4] = {-1, -1, -1, -1};       // last use issued per (group, buffer)
+            for (int k = 0, p = first; p < npass; ++k, p += step) {
+                const int g = k & 1, b = (k >> 1) & 1, use = k >> 2;
+                if (use > 0 && !t6_wait(bar_mape(g, b), (uint32_t)((use - 1) & 1), fail, err)) break;
+                if (*fail) break;
+                const int e0 = p * EB, nb = min(EB, E - e0);
+                t6_copy(sbase + OFF_MAP + (uint32_t)(2 * g + b) * MAP_BYTES, map + (size_t)e0 * Np,
+                        (uint32_t)nb * Np * 4u, bar_mapf(g, b));
+                issued[2 * g + b] = use;
             }
+            // every copy this warp started has landed before the CTA exits
+            for (int i = 0; i < 4; ++i)
+                if (issued[i] >= 0) t6_wait(bar_mapf(i >> 1, i & 1), (uint32_t)(issued[i] & 1), fail, err, false);
         }
-        // pads of U and W (the last pass's X staging overwrote them): columns n = 28..31 of every
-        // row (one core-matrix row each) and the eighth vertical row of every element
-        for (int i = tid; i < 2 * 128 + 2 * EB * (NT / 4); i += kT5Threads) {
-            uint32_t o;
-            if (i < 256) {
-                o = (i < 128 ? OFF_U : OFF_W) + opoff(i & 127, NT, KF);
-            } else {
-                const int j = i - 256, mtx = j / (EB * (NT / 4)), jj = j - mtx * (EB * (NT / 4));
-                o = (mtx ? OFF_W : OFF_U) + opoff(8 * (jj / (NT / 4)) + 7, 4 * (jj % (NT / 4)), KF);
-            }
-            *reinterpret_cast<uint4*>(sm + o) = make_uint4(0, 0, 0, 0);
-        }
-        // gather and vertical stage: U(e,qz; n) = Bz(qz; k) x(k; n), W = Dz x
-        for (int i = tid; i < EB * NT; i += kT5Threads) {
-            const int b = i / NT, n = i - b * NT;
-            float xk[NZ];
-#pragma unroll
-            for (int k = 0; k < NZ; ++k) {
-                float v = 0.f;
-                if (b < nb) {
-                    const int m = sMap[b * Np + k * NT + n];
-                    if (m >= 0 && m < N) v = x[m];
+    } else if (warp == 9) {
+        // ------------------------------------------------------------ geometric-factor producer
+        if (lane == 0) {
+            int issued[NSLOT];
+            for (int s = 0; s < NSLOT; ++s) issued[s] = -1;
+            int j = 0;
+            bool stop = false;
+            for (int p = first; p < npass && !stop; p += step) {
+                const char* src = reinterpret_cast<const char*>(G6) + (size_t)p * PASS_G;
+                for (int c = 0; c < NCH; ++c, ++j) {
+                    const int s = j % NSLOT, use = j / NSLOT;
+                    if (use > 0 && !t6_wait(bar_slote(s), (uint32_t)((use - 1) & 1), fail, err)) { stop = true; break; }
+                    if (*fail) { stop = true; break; }
+                    t6_copy(sbase + OFF_G + (uint32_t)s * CH_BYTES, src + (size_t)c * CH_BYTES,
+                            c < NCH - 1 ? CH_BYTES : CH_LAST, bar_slotf(s));
+                    issued[s] = use;
                 }
-                xk[k] = v;
             }
-#pragma unroll
-            for (int qz = 0; qz < QZ; ++qz) {
-                float u = 0.f, w = 0.f;
-#pragma unroll
-                for (int k = 0; k < NZ; ++k) {
-                    u += sZ[qz * NZ + k] * xk[k];
-                    w += sZ[QZ * NZ + qz * NZ + k] * xk[k];
+            for (int s = 0; s < NSLOT; ++s)
+                if (issued[s] >= 0) t6_wait(bar_slotf(s), (uint32_t)(issued[s] & 1), fail, err, false);
+        }
+    } else {
+        // ------------------------------------------------------------ compute groups
+        const int g = warp >> 2, q4 = warp & 3, gt = tid & 127;
+        const uint32_t tg = tmem + (uint32_t)g * TM_GROUP;
+        const uint32_t trow = tg + ((uint32_t)(32 * q4) << 16);
+        unsigned char* U = sm + OFF_UW + (uint32_t)g * 2 * SZ_A;
+        unsigned char* Wm = U + SZ_A;
+        const uint32_t uaddr = sbase + OFF_UW + (uint32_t)g * 2 * SZ_A, waddr = uaddr + SZ_A;
+        float* Xr = reinterpret_cast<float*>(U);
+        float* Xt = reinterpret_cast<float*>(Wm);
+        // this thread's accumulator row: r = 32 q4 + lane = 16 qz + b
+        const int row = 32 * q4 + lane, rqz = row >> 4, rb = row & 15;
+        const uint32_t idF = idesc(128, NF), idB = idesc(128, NB);
+        int pend = -1;              // thread 0 of the group: parity of a commit not yet seen complete
+        for (int k = g, p = first + g * step; p < npass; k += 2, p += 2 * step) {
+            const int b = (k >> 1) & 1, use = k >> 2;
+            const int e0 = p * EB, nb = min(EB, E - e0);
+            const int* sMap = reinterpret_cast<const int*>(sm + OFF_MAP + (uint32_t)(2 * g + b) * MAP_BYTES);
+            // pads of U and W (the last pass's X staging overwrote them): columns n = 28..31 of
+            // every row and the rows of the eighth vertical point
+            for (int i = gt; i < 2 * 128 + 2 * 16 * (NT / 4); i += 128) {
+                uint32_t o;
+                if (i < 256) {
+                    o = (i < 128 ? 0u : SZ_A) + opoff(i & 127, NT, KF);
+                } else {
+                    const int jj = i - 256, mtx = jj / (16 * (NT / 4)), t = jj - mtx * (16 * (NT / 4));
+                    o = (mtx ? SZ_A : 0u) + opoff(112 + t / (NT / 4), 4 * (t % (NT / 4)), KF);
                 }
-                *reinterpret_cast<float*>(sm + OFF_U + opoff(8 * b + qz, n, KF)) = __uint_as_float(to_tf32(u));
-                *reinterpret_cast<float*>(sm + OFF_W + opoff(8 * b + qz, n, KF)) = __uint_as_float(to_tf32(w));
+                *reinterpret_cast<uint4*>(U + o) = make_uint4(0, 0, 0, 0);
             }
-        }
-        fence_async_smem();
-        fence_before();
-        __syncthreads();
-        fence_after();
-        if (tid == 0) {
+            t6_wait(bar_mapf(g, b), (uint32_t)(use & 1), fail, err);
+            // gather and vertical stage: U(qz, b; n) = Bz(qz; k) x(k; n), W = Dz x.  Warp task
+            // wt = (bh, nh): lane -> element 8 bh + lane / 4, node 4 nh + lane % 4, so the 32 lanes
+            // of every operand store fall on 32 distinct banks
+            if (!*fail) {
+                float xv[4][NZ];
 #pragma unroll
-            for (int ks = 0; ks < KF / 8; ++ks) {
-                const uint64_t au = sdesc(sbase + OFF_U + ks * 256, KF * 32);
-                const uint64_t aw = sdesc(sbase + OFF_W + ks * 256, KF * 32);
-                mma_tf32(tmem + TM_DR, au, sdesc(sbase + OFF_BF + ks * 256, KF * 32), idF, ks);
-                mma_tf32(tmem + TM_DS, au, sdesc(sbase + OFF_BF + SZ_BF + ks * 256, KF * 32), idF, ks);
-                mma_tf32(tmem + TM_DT, aw, sdesc(sbase + OFF_BF + 2 * SZ_BF + ks * 256, KF * 32), idF, ks);
-            }
-            mma_commit(bara);
-        }
-        if (!t5_wait(bara, pa)) s_fail = 1; else pa ^= 1u;
-        fence_after();
-        __syncthreads();
-        if (s_fail) break;
-        // geometric factors: thread (row, half) takes the 8-column chunks c = half, half + 2, half + 4,
-        // half + 6 (qt in [8c, 8c + 8), c < 7 = K of the backward MMAs) and writes V over them
-        {
-            const bool valid = rb < nb && rqz < QZ;
-            const __nv_bfloat16* Ge = G16 + (size_t)(e0 + (valid ? rb : 0)) * GE + rqz * QTP;
+                for (int t = 0; t < 4; ++t) {
+                    const int wt = q4 + 4 * t;
+                    const int eb = (lane >> 2) + 8 * (wt / 7), n = 4 * (wt % 7) + (lane & 3);
 #pragma unroll
-            for (int cc = 0; cc < 4; ++cc) {
-                const int c = half + 2 * cc;
-                if (c >= KB / 8) continue;
-                const int c0 = 8 * c;
-                float g[4][6][2];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int qt = c0 + 2 * j;
-#pragma unroll
-                    for (int m = 0; m < 6; ++m) {
-                        float2 f = make_float2(0.f, 0.f);
-                        if (valid && qt < QT)
-                            f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(Ge + m * QZ * QTP + qt));
-                        g[j][m][0] = f.x;
-                        g[j][m][1] = f.y;
+                    for (int kk = 0; kk < NZ; ++kk) {
+                        float v = 0.f;
+                        if (wt < 14 && eb < nb) {
+                            const int m = sMap[eb * Np + kk * NT + n];
+                            if (m >= 0 && m < N) v = __ldg(x + m);   // Dirichlet ids (m < 0) act as zero
+                        }
+                        xv[t][kk] = v;
                     }
                 }
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int wt = q4 + 4 * t;
+                    if (wt >= 14) continue;
+                    const int eb = (lane >> 2) + 8 * (wt / 7), n = 4 * (wt % 7) + (lane & 3);
+#pragma unroll
+                    for (int qz = 0; qz < QZ; ++qz) {
+                        float u = 0.f, w = 0.f;
+#pragma unroll
+                        for (int kk = 0; kk < NZ; ++kk) {
+                            u = fmaf(vc.bz[qz * NZ + kk], xv[t][kk], u);
+                            w = fmaf(vc.dz[qz * NZ + kk], xv[t][kk], w);
+                        }
+                        const uint32_t o = opoff(16 * qz + eb, n, KF);
+                        *reinterpret_cast<uint32_t*>(U + o) = to_tf32(u);
+                        *reinterpret_cast<uint32_t*>(Wm + o) = to_tf32(w);
+                    }
+                }
+            }
+            fence_async_smem();
+            fence_before();
+            if (group_sync_any(g, *fail)) break;
+            if (gt == 0) {
+                fence_after();
+#pragma unroll
+                for (int ks = 0; ks < KF / 8; ++ks) {
+                    const uint64_t au = sdesc(uaddr + ks * 256, KF * 32);
+                    const uint64_t aw = sdesc(waddr + ks * 256, KF * 32);
+                    mma_tf32(tg + TM_UR, au, sdesc(sbase + OFF_BF + ks * 256, KF * 32), idF, ks);
+                    mma_tf32(tg + TM_US, au, sdesc(sbase + OFF_BF + SZ_BF + ks * 256, KF * 32), idF, ks);
+                    mma_tf32(tg + TM_UT, aw, sdesc(sbase + OFF_BF + 2 * SZ_BF + ks * 256, KF * 32), idF, ks);
+                }
+                mma_commit(bar_mma(g));
+                pend = 0;
+            }
+            if (t6_wait(bar_mma(g), 0u, fail, err) && gt == 0) pend = -1;
+            fence_after();
+            // geometric factors, chunk by chunk: V over the accumulators
+            const bool valid = rqz < QZ && rb < nb;
+            for (int c = 0; c < NCH; ++c) {
+                const int j = k * NCH + c, s = j % NSLOT;      // the producer's chunk sequence
+                const int c0 = 8 * c;
                 uint32_t ur[8], us[8], ut[8];
-                tmem_ld8(trow + TM_DR + c0, ur);
-                tmem_ld8(trow + TM_DS + c0, us);
-                tmem_ld8(trow + TM_DT + c0, ut);
+                tmem_ld8(trow + TM_UR + c0, ur);
+                tmem_ld8(trow + TM_US + c0, us);
+                tmem_ld8(trow + TM_UT + c0, ut);
+                const bool ok = t6_wait(bar_slotf(s), (uint32_t)((j / NSLOT) & 1), fail, err);
+                const unsigned char* slot = sm + OFF_G + (uint32_t)s * CH_BYTES;
+                float gf[6][8];
+                if (c < NCH - 1) {
+#pragma unroll
+                    for (int f = 0; f < 6; ++f) {
+                        uint4 v = make_uint4(0, 0, 0, 0);
+                        if (ok && valid) v = *reinterpret_cast<const uint4*>(slot + ((f * QZ + rqz) * EB + rb) * 16);
+                        gf[f][0] = bf16_lo(v.x); gf[f][1] = bf16_hi(v.x);
+                        gf[f][2] = bf16_lo(v.y); gf[f][3] = bf16_hi(v.y);
+                        gf[f][4] = bf16_lo(v.z); gf[f][5] = bf16_hi(v.z);
+                        gf[f][6] = bf16_lo(v.w); gf[f][7] = bf16_hi(v.w);
+                    }
+                } else {
+#pragma unroll
+                    for (int f = 0; f < 6; ++f) {
+                        uint32_t v = 0;
+                        if (ok && valid) v = *reinterpret_cast<const unsigned short*>(slot + ((f * QZ + rqz) * EB + rb) * 2);
+                        gf[f][0] = bf16_lo(v);
+#pragma unroll
+                        for (int h = 1; h < 8; ++h) gf[f][h] = 0.f;     // quadrature columns 49..55 are padding
+                    }
+                }
+                // the slot may be refilled once every lane has read it (not after a failed wait: its
+                // copy may still be in flight)
+                if (__all_sync(0xffffffffu, ok) && lane == 0) mbar_arrive(bar_slote(s));
                 tmem_wait_ld();
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const float* gg[6] = {g[k >> 1][0], g[k >> 1][1], g[k >> 1][2], g[k >> 1][3], g[k >> 1][4], g[k >> 1][5]};
-                    const int hh = k & 1;
-                    const float a = __uint_as_float(ur[k]), b = __uint_as_float(us[k]), t = __uint_as_float(ut[k]);
-                    const float vr = gg[0][hh] * a + gg[1][hh] * b + gg[2][hh] * t;
-                    const float vs = gg[1][hh] * a + gg[3][hh] * b + gg[4][hh] * t;
-                    const float vt = gg[2][hh] * a + gg[4][hh] * b + gg[5][hh] * t;
-                    ur[k] = to_tf32(vr);
-                    us[k] = to_tf32(vs);
-                    ut[k] = to_tf32(vt);
+                for (int h = 0; h < 8; ++h) {
+                    const float a = __uint_as_float(ur[h]), bb = __uint_as_float(us[h]), t = __uint_as_float(ut[h]);
+                    const float vr = gf[0][h] * a + gf[1][h] * bb + gf[2][h] * t;
+                    const float vs = gf[1][h] * a + gf[3][h] * bb + gf[4][h] * t;
+                    const float vt = gf[2][h] * a + gf[4][h] * bb + gf[5][h] * t;
+                    ur[h] = to_tf32(vr);
+                    us[h] = to_tf32(vs);
+                    ut[h] = to_tf32(vt);
                 }
-                tmem_st8(trow + TM_DR + c0, ur);
-                tmem_st8(trow + TM_DS + c0, us);
-                tmem_st8(trow + TM_DT + c0, ut);
+                tmem_st8(trow + TM_UR + c0, ur);
+                tmem_st8(trow + TM_US + c0, us);
+                tmem_st8(trow + TM_UT + c0, ut);
             }
-            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-        }
-        fence_before();
-        __syncthreads();
-        fence_after();
-        if (tid == 0) {
+            tmem_wait_st();
+            fence_before();
+            if (group_sync_any(g, *fail)) break;
+            if (gt == 0) {
+                fence_after();
 #pragma unroll
-            for (int ks = 0; ks < KB / 8; ++ks) {
-                const uint32_t o = ks * 256;
-                mma_tf32_ta(tmem + TM_XR, tmem + TM_DR + 8 * ks, sdesc(sbase + OFF_BB + o, KB * 32), idB, ks);
-                mma_tf32_ta(tmem + TM_XR, tmem + TM_DS + 8 * ks, sdesc(sbase + OFF_BB + SZ_BB + o, KB * 32), idB, 1);
-                mma_tf32_ta(tmem + TM_XT, tmem + TM_DT + 8 * ks, sdesc(sbase + OFF_BB + 2 * SZ_BB + o, KB * 32), idB, ks);
+                for (int ks = 0; ks < KB / 8; ++ks) {
+                    const uint32_t o = ks * 256;
+                    mma_tf32_ta(tg + TM_XR, tg + TM_UR + 8 * ks, sdesc(sbase + OFF_BB + o, KB * 32), idB, ks);
+                    mma_tf32_ta(tg + TM_XR, tg + TM_US + 8 * ks, sdesc(sbase + OFF_BB + SZ_BB + o, KB * 32), idB, 1);
+                    mma_tf32_ta(tg + TM_XT, tg + TM_UT + 8 * ks, sdesc(sbase + OFF_BB + 2 * SZ_BB + o, KB * 32), idB, ks);
+                }
+                mma_commit(bar_mma(g));
+                pend = 1;
             }
-            mma_commit(bara);
-        }
-        if (!t5_wait(bara, pa)) s_fail = 1; else pa ^= 1u;
-        fence_after();
-        __syncthreads();
-        if (s_fail) break;
-        {   // Xr (warps 0-3) or Xt (warps 4-7) of this row into the staging area [e][n][qz]
-            uint32_t xa[16], xb[16];
-            const uint32_t col = half ? TM_XT : TM_XR;
-            tmem_ld16(trow + col, xa);
-            tmem_ld16(trow + col + 16, xb);
-            tmem_wait_ld();
-            float* X = reinterpret_cast<float*>(sm + OFF_X + half * SZ_X) + rb * NT * 8 + rqz;
+            if (t6_wait(bar_mma(g), 1u, fail, err) && gt == 0) pend = -1;
+            fence_after();
+            {   // Xr, Xt of this row into the staging areas [n][qz][b] (row stride XS per node)
+                uint32_t xa[16], xb[16], ta[16], tb[16];
+                tmem_ld16(trow + TM_XR, xa);
+                tmem_ld16(trow + TM_XR + 16, xb);
+                tmem_ld16(trow + TM_XT, ta);
+                tmem_ld16(trow + TM_XT + 16, tb);
+                tmem_wait_ld();
+                if (rqz < QZ) {
+                    float* pr = Xr + rqz * 16 + rb;
+                    float* pt = Xt + rqz * 16 + rb;
 #pragma unroll
-            for (int n = 0; n < 16; ++n) X[n * 8] = __uint_as_float(xa[n]);
+                    for (int n = 0; n < 16; ++n) {
+                        pr[n * XS] = __uint_as_float(xa[n]);
+                        pt[n * XS] = __uint_as_float(ta[n]);
+                    }
 #pragma unroll
-            for (int n = 16; n < NT; ++n) X[n * 8] = __uint_as_float(xb[n - 16]);
-        }
-        fence_before();
-        __syncthreads();
-        // transposed vertical stage and direct-stiffness summation:
-        // y(k; n) = Bz(qz; k) Xr(qz; n) + Dz(qz; k) Xt(qz; n)
-        for (int i = tid; i < nb * NT; i += kT5Threads) {
-            const int b = i / NT, n = i - b * NT;
-            const float4* pr = reinterpret_cast<const float4*>(sm + OFF_X + (b * NT + n) * 32);
-            const float4* pt = reinterpret_cast<const float4*>(sm + OFF_X + SZ_X + (b * NT + n) * 32);
-            const float4 r0 = pr[0], r1 = pr[1], t0 = pt[0], t1 = pt[1];
-            const float xr[QZ] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z};
-            const float xt[QZ] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z};
-#pragma unroll
-            for (int k = 0; k < NZ; ++k) {
-                float s = 0.f;
-#pragma unroll
-                for (int qz = 0; qz < QZ; ++qz) s += sZ[qz * NZ + k] * xr[qz] + sZ[QZ * NZ + qz * NZ + k] * xt[qz];
-                const int m = sMap[b * Np + k * NT + n];
-                if (m >= 0 && m < N) atomicAdd(&y[m], s);
+                    for (int n = 16; n < NT; ++n) {
+                        pr[n * XS] = __uint_as_float(xb[n - 16]);
+                        pt[n * XS] = __uint_as_float(tb[n - 16]);
+                    }
+                }
             }
+            fence_before();
+            group_sync(g);
+            // transposed vertical stage and direct-stiffness summation:
+            // y(k; n) = Bz(qz; k) Xr(qz; n) + Dz(qz; k) Xt(qz; n).  Warp task nt: lane -> element
+            // lane % 16, node 2 nt + lane / 16
+            if (!*fail) {
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int nt = q4 + 4 * t;
+                    if (nt >= 14) continue;
+                    const int eb = lane & 15, n = 2 * nt + (lane >> 4);
+                    float xr[QZ], xt[QZ];
+#pragma unroll
+                    for (int qz = 0; qz < QZ; ++qz) {
+                        xr[qz] = Xr[n * XS + qz * 16 + eb];
+                        xt[qz] = Xt[n * XS + qz * 16 + eb];
+                    }
+                    if (eb < nb) {
+#pragma unroll
+                        for (int kk = 0; kk < NZ; ++kk) {
+                            float s = 0.f;
+#pragma unroll
+                            for (int qz = 0; qz < QZ; ++qz) {
+                                s = fmaf(vc.bz[qz * NZ + kk], xr[qz], s);
+                                s = fmaf(vc.dz[qz * NZ + kk], xt[qz], s);
+                            }
+                            const int m = sMap[eb * Np + kk * NT + n];
+                            if (m >= 0 && m < N) atomicAdd(&y[m], s);
+                        }
+                    }
+                }
+            }
+            if (group_sync_any(g, *fail)) break;
+            // this pass's map buffer may be refilled
+            if (gt == 0) mbar_arrive(bar_mape(g, b));
         }
-        __syncthreads();
-        buf ^= 1;
-    }
-    if (s_fail && tid == 0) {
-        // a wait ran out: report it and give the copy or MMAs it waited for a second bounded wait
-        // (the parity of a wait that ran out was not advanced)
-        atomicExch(err, 1);
-        t5_wait(barm, pm);
-        t5_wait(bara, pa);
+        // MMAs this group started and did not see complete get a second bounded wait
+        if (gt == 0 && pend >= 0) t6_wait(bar_mma(g), (uint32_t)pend, fail, err, false);
     }
     fence_before();
     __syncthreads();
     if (warp == 0) {
         fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TM_COLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TM_GROUP) : "memory");
+    }
+}
+
+// The order-6 factors in the kernel's layout: per pass of 16 elements, chunk c of 8
+// quadrature points (the seventh chunk holds the 49th point) as [factor][qz][element][8 qt]
+// (BF16; elements past E are zero).
+__global__ void k_factors_t6(int E, int npass, const float* __restrict__ G32, __nv_bfloat16* __restrict__ out) {
+    constexpr int PER = (int)(PASS_G / 2);            // BF16 entries per pass
+    constexpr int CH = (int)(CH_BYTES / 2);
+    const long long n = (long long)npass * PER;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int p = (int)(i / PER);
+        const int r = (int)(i - (long long)p * PER);
+        int c, rr, wc;
+        if (r < 6 * CH) { c = r / CH; rr = r - c * CH; wc = 8; }
+        else { c = 6; rr = r - 6 * CH; wc = 1; }
+        const int w = rr % wc;
+        int t = rr / wc;
+        const int e = t % EB;
+        t /= EB;
+        const int qz = t % QZ, f = t / QZ;
+        const int ea = p * EB + e, qt = 8 * c + w;
+        float v = 0.f;
+        if (ea < E) v = G32[((size_t)ea * 6 + f) * (QZ * QT) + qz * QT + qt];
+        out[i] = __float2bfloat16_rn(v);
     }
 }
 
@@ -419,25 +558,49 @@ __global__ void __launch_bounds__(kT5Threads, 2)
 
 bool prism_t5_supported(int p) { return p == 6; }
 
+cudaError_t build_g16_t6(Level& L, cudaStream_t s) {
+    if (!(L.dim == 3 && L.p == 6 && L.pz == 6) || L.G32 == nullptr) return cudaSuccess;
+    const int npass = (L.E + EB - 1) / EB;
+    cudaError_t e = cudaSuccess;
+    if (L.G16T == nullptr) {
+        void* p = nullptr;
+        e = cudaMalloc(&p, (size_t)npass * PASS_G);
+        if (e != cudaSuccess) return e;
+        L.G16T = static_cast<unsigned short*>(p);
+    }
+    const long long n = (long long)npass * (PASS_G / 2);
+    const long long blocks = (n + 255) / 256;
+    k_factors_t6<<<(int)(blocks < 8192 ? (blocks > 0 ? blocks : 1) : 8192), 256, 0, s>>>(
+        L.E, npass, L.G32, static_cast<__nv_bfloat16*>(static_cast<void*>(L.G16T)));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_apply_prism_t5(const Level& L, const float* x, float* y, const int* skip, int* err, cudaStream_t s) {
-    if (L.p != 6 || L.pz != 6 || L.dim != 3) return cudaErrorInvalidValue;
+    if (L.p != 6 || L.pz != 6 || L.dim != 3 || L.G16T == nullptr) return cudaErrorInvalidValue;
     static bool configured[64] = {};
+    static int sms[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!configured[dev]) {
-        e = cudaFuncSetAttribute(k_apply_prism_t5, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+        e = cudaFuncSetAttribute(k_apply_prism_t6, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
         configured[dev] = true;
     }
-    if (L.G16 == nullptr) return cudaErrorInvalidValue;
-    const int passes = (L.E + EB - 1) / EB;
-    const int grid = passes < 2 * kT5SMs ? passes : 2 * kT5SMs;
+    Vert vc;
+    for (int i = 0; i < QZ * NZ; ++i) {
+        vc.bz[i] = (float)L.ref.Bz[i];
+        vc.dz[i] = (float)L.ref.Dz[i];
+    }
+    const int npass = (L.E + EB - 1) / EB;
+    const int grid = npass < sms[dev] ? npass : sms[dev];
     if (grid < 1) return cudaSuccess;
-    k_apply_prism_t5<<<grid, kT5Threads, SMEM, s>>>(L.E, (int)L.N, L.map,
-                                                    reinterpret_cast<const __nv_bfloat16*>(L.G16), L.ref32.m, x, y,
-                                                    skip, err);
+    k_apply_prism_t6<<<grid, kT6Threads, SMEM, s>>>(L.E, (int)L.N, npass, L.map,
+                                                   reinterpret_cast<const __nv_bfloat16*>(L.G16T), L.ref32.m, vc, x,
+                                                   y, skip, err);
     return cudaGetLastError();
 }
 

@@ -39,6 +39,7 @@ struct Level {
     double* G = nullptr;                   // [E][ncomp][Nq]
     float* G32 = nullptr;
     unsigned short* G16 = nullptr;         // BF16 copy of G32 for the tensor-core apply (prisms, p >= 2)
+    unsigned short* G16T = nullptr;        // order-6 prisms: BF16 factors in the tcgen05 apply's chunked layout
     int* lift_elems = nullptr;             // finest prism level: elements with a Dirichlet node (lifting apply)
     int nlift = 0;
     double* dinv = nullptr;                // 1/diag on free nodes, 0 on Dirichlet
@@ -217,6 +218,8 @@ inline bool level_tc(const Level& L) { return L.dim == 3 && L.pz == L.p && prism
 // apply_prism.cu: (triangle order, vertical order) pairs the prism apply is compiled for
 bool prism_pair_supported(int p, int pz);
 cudaError_t build_g16(Level& L, cudaStream_t s);
+// apply_prism_t5.cu: the factors of an order-6 prism level in the tcgen05 kernel's layout
+cudaError_t build_g16_t6(Level& L, cudaStream_t s);
 // fnpf.cu: surface fields of the free-surface time stepping
 cudaError_t surface_gradient(int ntri, int NT, long long N2, const int* map2, const double* vtri, const double* Drn,
                              const double* Dsn, const double* inv_mult, const double* f2, double* gx, double* gy,

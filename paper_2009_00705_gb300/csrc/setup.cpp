@@ -357,6 +357,7 @@ sem_status geometry_levels(sem_handle* h, int first, int last, bool flat) {
         cudaFree(dDs);
         CK(e);
         CK(build_g16(L, 0));
+        CK(build_g16_t6(L, 0));
     }
     cudaFree(dvtri);
     cudaFree(detaP);

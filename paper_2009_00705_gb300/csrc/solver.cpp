@@ -575,7 +575,7 @@ cudaError_t tune_prism(Level& L, bool fp32) {
 }
 
 void free_level(Level& L) {
-    void* ptrs[] = {L.map, L.G, L.G32, L.G16, L.lift_elems, L.dinv, L.dinv32, L.dir, L.ref64.m, L.ref32.m, L.It64, L.Iz64, L.It32, L.Iz32, L.gref,
+    void* ptrs[] = {L.map, L.G, L.G32, L.G16, L.G16T, L.lift_elems, L.dinv, L.dinv32, L.dir, L.ref64.m, L.ref32.m, L.It64, L.Iz64, L.It32, L.Iz32, L.gref,
                     L.csr_rowptr, L.csr_col, L.csr_val, L.csr_slot,
                     L.owner, L.wmult, L.wmult32, L.u, L.f, L.y, L.d, L.u32, L.f32, L.y32, L.d32};
     for (void* p : ptrs)
