@@ -397,9 +397,14 @@ def main():
             ms_m, st_m = timed(ms_solver, a.steps, a.warmup, phi_m)
             ms_m = max_over_ranks(ms_m)
             err = float(np.abs(phi_m.cpu().numpy() - phi64).max() / np.abs(phi64).max())
-            smooth = ("TF32 tensor-core apply (warp-level mma.sync m16n8k8, FP32 accumulation, BF16 factors) in the Chebyshev sweeps and residuals of "
-                      "the V-cycle on the P and intermediate levels; FP32 apply in the inner PCG" if prec == "mixed_tf32"
-                      else "FP32 SIMT apply throughout")
+            if prec == "mixed_tf32":
+                kinds = {1: "warp-level mma.sync m16n8k8", 2: "tcgen05.mma with TMEM accumulators"}
+                fine_kind = ms_solver.tc_kernel(0)
+                smooth = (f"TF32 tensor-core apply (FP32 accumulation, BF16 factors) in the Chebyshev sweeps and residuals "
+                          f"of the V-cycle: {kinds.get(fine_kind, 'FP32')} on the order-{P} level (chosen at setup by "
+                          f"timing both), warp-level MMA on the intermediate levels; FP32 apply in the inner PCG")
+            else:
+                smooth = "FP32 SIMT apply throughout"
             obj = {"value": dof * a.steps * world / (ms_m / 1000.0), "unit": UNIT,
                    "ms_per_step": ms_m / a.steps, "outer_iters": st_m[-1]["iters"],
                    "inner_iters": st_m[-1]["inner_iters"], "res_final_rel": st_m[-1]["res_final"] / st_m[-1]["fnorm"],

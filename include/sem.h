@@ -246,6 +246,10 @@ sem_status sem_element_map(const sem_handle* h, int level, int* map_host);
 sem_status sem_lambda_max(const sem_handle* h, double* lam_host);
 /* Elements per CTA pass of the prism apply chosen for a level (FP64 and FP32 kernels). */
 sem_status sem_tile_shapes(const sem_handle* h, int level, int* elems_fp64, int* elems_fp32);
+/* The operator of a level's Chebyshev sweeps under MIXED_TF32: 0 the FP32 apply (not a
+ * tensor-core level), 1 the warp-level MMA kernel, 2 the tcgen05 kernel (order 6; chosen at
+ * setup by timing both when autotune is set, else the tcgen05 kernel). */
+sem_status sem_tc_kernel(const sem_handle* h, int level, int* kind);
 /* The assembled diagonal of A at a level (all nodes), host copy. */
 sem_status sem_diagonal(const sem_handle* h, int level, double* diag_host);
 

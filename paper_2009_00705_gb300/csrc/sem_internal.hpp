@@ -60,6 +60,8 @@ struct Level {
     float *u32 = nullptr, *f32 = nullptr, *y32 = nullptr, *d32 = nullptr;
     double* gref = nullptr;                // [dim][Nq][Np] full reference gradients (coarse level)
     int tile64 = 0, tile32 = 0;            // prism apply tile-shape variant (autotuned)
+    int tc_kind = 1;                       // tensor-core smoothing operator (MIXED_TF32): 0 warp-level MMA,
+                                           // 1 tcgen05 where compiled (order 6); autotuned at setup
     int* csr_rowptr = nullptr;             // coarse level: assembled matrix, free rows/cols
     int* csr_col = nullptr;
     double* csr_val = nullptr;

@@ -245,7 +245,7 @@ static sem_status apply_vcycle32(sem_handle* h, int li, const float* x, float* y
         return apply_level32(h, li, x, y, s, skip);
     CKS(cudaMemsetAsync(y, 0, sizeof(float) * L.N, s));
     const bool timed = timed_begin(h, li, s);
-    K(launch_apply_tensor(L, x, y, skip, h->sc.flags + F_TC_ERR, s));
+    K(launch_apply_tensor(L, x, y, skip, h->sc.flags + F_TC_ERR, s, L.tc_kind == 1 && L.G16T != nullptr));
     if (timed) timed_end(h, 2, s);
     if (li == 0) h->fine_applies += 1;
     return SEM_OK;
@@ -571,6 +571,54 @@ cudaError_t tune_prism(Level& L, bool fp32) {
     (fp32 ? L.tile32 : L.tile64) = choice;
     std::lock_guard<std::mutex> lock(g_tile_mutex);
     g_tile_cache[key] = choice;
+    return cudaSuccess;
+}
+
+// The tensor-core smoothing operator of an order-6 level: times the warp-level MMA kernel and
+// the tcgen05 kernel on the level's own mesh and keeps the faster (cached like the tile shapes).
+std::map<std::pair<int, int>, int> g_tc_cache;
+
+cudaError_t tune_tc(Level& L) {
+    L.tc_kind = 0;
+    if (!level_tc(L) || L.G16T == nullptr || !prism_t5_supported(L.p)) return cudaSuccess;
+    int bucket = 0;
+    while ((1 << (bucket + 1)) <= L.E) ++bucket;
+    const auto key = std::make_pair(L.p, bucket);
+    {
+        std::lock_guard<std::mutex> lock(g_tile_mutex);
+        auto it = g_tc_cache.find(key);
+        if (it != g_tc_cache.end()) {
+            L.tc_kind = it->second;
+            return cudaSuccess;
+        }
+    }
+    int* err = nullptr;
+    cudaError_t e = cudaMalloc(&err, sizeof(int));
+    if (e != cudaSuccess) return e;
+    cudaEvent_t e0, e1;
+    e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best = 1e30f;
+    int choice = 0;
+    for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+        for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+            if (rep == 1) e = cudaEventRecord(e0, 0);
+            cudaMemsetAsync(L.y32, 0, sizeof(float) * L.N, 0);
+            if (e == cudaSuccess) e = launch_apply_tensor(L, L.u32, L.y32, nullptr, err, 0, v == 1);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, 0);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best) { best = ms; choice = v; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(err);
+    if (e != cudaSuccess) return e;
+    L.tc_kind = choice;
+    std::lock_guard<std::mutex> lock(g_tile_mutex);
+    g_tc_cache[key] = choice;
     return cudaSuccess;
 }
 
@@ -1019,6 +1067,7 @@ sem_status sem_setup(const sem_mesh* m, int P, const sem_options* opts, sem_hand
             if (e == cudaSuccess) e = to_f32(L.N, L.u, L.u32, 0);
             if (e == cudaSuccess) e = tune_prism(L, false);
             if (e == cudaSuccess) e = tune_prism(L, true);
+            if (e == cudaSuccess && o.precision == SEM_PREC_MIXED_TF32) e = tune_tc(L);
             if (e != cudaSuccess) { set_error(std::string("autotune: ") + cudaGetErrorString(e)); st = SEM_ECUDA; }
         }
     }
@@ -1109,6 +1158,14 @@ sem_status sem_tile_shapes(const sem_handle* h, int level, int* elems_fp64, int*
     const Level& L = h->lv[level];
     if (elems_fp64) *elems_fp64 = L.dim == 3 ? prism_tile_elements(L.p, L.tile64) : 1;
     if (elems_fp32) *elems_fp32 = L.dim == 3 ? prism_tile_elements(L.p, L.tile32) : 1;
+    return SEM_OK;
+}
+
+sem_status sem_tc_kernel(const sem_handle* h, int level, int* kind) {
+    CKST(check_level(h, level));
+    if (!kind) { set_error("kind is NULL"); return SEM_EINVAL; }
+    const Level& L = h->lv[level];
+    *kind = (h->opts.precision != SEM_PREC_MIXED_TF32 || !level_tc(L)) ? 0 : (L.tc_kind == 1 && L.G16T ? 2 : 1);
     return SEM_OK;
 }
 

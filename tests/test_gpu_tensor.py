@@ -181,3 +181,30 @@ def test_tcgen05_apply_against_warp_mma_and_oracle(sem, n, nl):
                 s.apply32(1, xc, torch.zeros_like(xc), tensor_cores=2)
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("autotune", [0, 1])
+def test_mixed_tf32_solve_with_the_tcgen05_smoother_matches_oracle(sem, autotune):
+    # the V-cycle's Chebyshev sweeps on the order-6 level run the tcgen05 kernel (autotune = 0
+    # takes it; autotune = 1 keeps whichever kernel is faster on the mesh and says which); the
+    # solve still reaches the FP64 residual and the oracle's direct solution
+    mesh = W.box3d(6, 6, 3, eta_modes=W.eta_sinx_cosy(0.1))
+    levels = [6, 3, 1]
+    prob = Problem(mesh, levels)
+    lev = prob.levels[0]
+    C = prob.coords(0)
+    phiD = W.potential3d(*C[lev.dirichlet].T)
+    phi_ref = S.solve_laplace_direct(prob, phiD)
+    s = _solver(sem, mesh, prob, levels, outer="pdc", precision="mixed_tf32", inner_imax=50, inner_rtol=1e-4,
+                imax=100, autotune=autotune)
+    try:
+        kind = s.tc_kernel(0)
+        assert kind == 2 if autotune == 0 else kind in (1, 2)
+        assert s.tc_kernel(1) == 1 and s.tc_kernel(2) == 0      # order 3: warp MMA; order 1: FP32
+        phi = torch.zeros(lev.N, dtype=torch.float64, device="cuda")
+        st = s.solve(torch.tensor(phiD, device="cuda"), phi, tol=1e-11)
+        torch.cuda.synchronize()
+        assert st["status"] == 0 and st["res_final"] <= 1e-11 * st["fnorm"]
+        assert np.abs(phi.cpu().numpy() - phi_ref).max() <= 1e-8 * np.abs(phi_ref).max()
+    finally:
+        s.close()
