@@ -145,23 +145,61 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_run(n, nl, P, solves, warmup=0, timeout=900):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-m", "oracle.timing", "--n", str(n), "--nlayers", str(nl), "--P", str(P),
-                        "--solves", str(solves), "--warmup", str(warmup)], cwd=ROOT, env=env,
+def oracle_cmd(n, nl, P, solves, warmup=0, direct=0):
+    return [sys.executable, "-m", "oracle.timing", "--n", str(n), "--nlayers", str(nl), "--P", str(P),
+            "--solves", str(solves), "--warmup", str(warmup), "--direct", str(direct)]
+
+
+ORACLE_ENV = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+
+
+def oracle_run(n, nl, P, solves, warmup=0, timeout=900, direct=0):
+    r = subprocess.run(oracle_cmd(n, nl, P, solves, warmup, direct), cwd=ROOT, env=ORACLE_ENV,
                        capture_output=True, text=True, timeout=timeout)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+def oracle_replicas(n, nl, P, solves, copies, timeout=900):
+    """`copies` single-threaded oracle processes at once, one per host core: the oracle's
+    throughput on all the cores (independent solves; SciPy's sparse products are serial)."""
+    procs = [subprocess.Popen(oracle_cmd(n, nl, P, solves), cwd=ROOT, env=ORACLE_ENV, stdout=subprocess.PIPE,
+                              stderr=subprocess.PIPE, text=True) for _ in range(copies)]
+    outs = []
+    for pr in procs:
+        o, e = pr.communicate(timeout=timeout)
+        if pr.returncode != 0:
+            raise RuntimeError(e[-2000:])
+        outs.append(json.loads(o.strip().splitlines()[-1]))
+    return outs
+
+
 def cpu_baseline_obj(P, nl, sample_n=8, solves=4):
-    o = oracle_run(sample_n, nl, P, solves)
-    return {"value": o["dof_per_s"], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{solves} oracle PCG-pMG solves to rtol 1e-8 on the {sample_n}x{sample_n}x{nl} P={P} "
-                      f"box ({o['dof_free']} free DOF, same eta/levels/smoother, exact coarse solve; assembled "
-                      f"CSR + SciPy, single thread), {o['seconds']:.1f} s; iterations {o['iters']}",
-            "solves_per_s_sample": o["solves_per_s"]}
+    one = oracle_run(sample_n, nl, P, solves, direct=1)
+    cores = max(1, min(64, os.cpu_count() or 1))
+    many = oracle_replicas(sample_n, nl, P, 2, cores) if cores > 1 else [one]
+    total = sum(o["dof_per_s"] for o in many)
+    cpu_model = ""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                cpu_model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"value": total, "unit": UNIT, "cores": len(many), "kind": "oracle",
+            "sample": f"{len(many)} concurrent single-threaded oracle processes, one per host core, each 2 PCG-pMG "
+                      f"solves to rtol 1e-8 on the {sample_n}x{sample_n}x{nl} P={P} box ({one['dof_free']} free DOF, "
+                      f"same eta/levels/smoother, exact coarse solve; assembled CSR + SciPy); value = the sum of their "
+                      f"DOF/s; DOF/s carries over to the full mesh under O(n) multigrid work",
+            "host": {"cpu_count": os.cpu_count(), "cpu": cpu_model},
+            "one_core": {"value": one["dof_per_s"], "unit": UNIT, "solves": solves, "seconds": one["seconds"],
+                         "iterations": one["iters"], "solves_per_s_sample": one["solves_per_s"]},
+            "direct_one_core": {"value": one["direct"]["dof_per_s"], "unit": UNIT,
+                                "ms_per_solve": one["direct"]["ms_per_solve"],
+                                "form": "sparse LU (SuperLU, MMD ordering) of the free-node matrix, factorised per "
+                                        "solve, plus one refinement step: the paper's direct baseline"}}
 
 
 def run_reference(a):
@@ -257,7 +295,9 @@ def main():
     ap.add_argument("--no-asm", action="store_true")
     ap.add_argument("--no-aniso", action="store_true")
     ap.add_argument("--no-hull", action="store_true")
-    ap.add_argument("--batch-tanks", type=int, default=32,
+    ap.add_argument("--no-config3-256", action="store_true",
+                    help="skip the 256x256x6 P=6 box (85 M free DOF; FP64 and MIXED_TF32 solves, about 2 minutes)")
+    ap.add_argument("--batch-tanks", type=int, default=256,
                     help="random tanks (500-20000 prisms, P in 3..6) for the batched measurement; 0 to skip")
     ap.add_argument("--train-snapshots", type=int, default=60)
     ap.add_argument("--train-steps", type=int, default=6)
@@ -349,6 +389,7 @@ def main():
     avg_apply_s = apply_ms / apply_n / 1000.0
     flops = apply_flops_per_elem(P) * E
     fp64_peak = FP64_NOMINAL_TFLOPS
+    fp64_probe = max(sem.sem_fp64_rate() for _ in range(3))
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     hbm_peak = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
     achieved_tf = flops / avg_apply_s / 1e12
@@ -357,7 +398,10 @@ def main():
                 "frac": achieved_tf / fp64_peak, "traffic": traffic,
                 "kernel": f"k_apply<P={P}, prism, double> (finest-level FP64 operator apply)",
                 "flops_per_launch": flops, "avg_launch_ms": avg_apply_s * 1e3, "launches": apply_n,
-                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (profiling recipe)",
+                "peak_source": f"nominal GB300 FP64 1.25 TFLOP/s (profiling recipe); probed on this GPU: "
+                               f"{fp64_probe:.3f} TFLOP/s (sixteen independent FMA chains per thread on every SM, "
+                               f"CUDA events, sem_fp64_rate), of which the apply reaches {achieved_tf / fp64_probe:.3f}",
+                "fp64_probe_tflops": fp64_probe, "frac_of_probe": achieved_tf / fp64_probe,
                 "hbm_view": {"algorithmic_bytes": apply_bytes(P, E, N),
                              "achieved_gbs": apply_bytes(P, E, N) / avg_apply_s / 1e9,
                              "peak_gbs": hbm_peak, "frac": apply_bytes(P, E, N) / avg_apply_s / 1e9 / hbm_peak}}
@@ -842,6 +886,55 @@ def main():
         for t in tanks:
             t[0].close()
 
+    # config 3's large variant: the 256 x 256 x 6 box at P = 6 (786,432 prisms, 85.0 M free DOF),
+    # MIXED_TF32 (one warm-up and two timed solves) and FP64 PCG (one timed solve: ~40 s)
+    big = None
+    if not a.no_config3_256:
+        mesh_b = W.config_box3d(256, 6)
+        xyb = sem.sem_mesh_nodes2d(mesh_b, P)
+        eta_b = mesh_b.eta(xyb[:, 0], xyb[:, 1])
+        big = {"workload": workload_name(256, 6, P).replace("eta=0.1 sin(x)cos(y); PCG", "eta=0.1 sin(x)cos(y); "
+                                                                                       "each form below"),
+               "time_budget": "MIXED_TF32: 1 warm-up + 2 timed solves; FP64 PCG: 1 timed solve (no warm-up)"}
+        sol = {}
+        for form, warm, reps in (("mixed_tf32", 1, 2), ("fp64", 0, 1)):
+            o = dict(levels=levels_for(P), imax=400, coarse_rtol=a.coarse_rtol)
+            if form == "mixed_tf32":
+                o.update(precision="mixed_tf32", outer="pdc", inner_imax=a.inner_imax, inner_rtol=a.inner_rtol)
+            t0 = time.perf_counter()
+            sb = sem.Solver(mesh_b, P, eta_nodal=eta_b, **o)
+            torch.cuda.synchronize()
+            setup_s = time.perf_counter() - t0
+            qb = sb.query(0)
+            Cb = sb.coords(0)
+            dnb = sb.dirichlet_nodes(0)
+            phiDb = torch.tensor(W.potential3d(*Cb[dnb].T), device="cuda")
+            phib = torch.empty(qb["ndof"], dtype=torch.float64, device="cuda")
+            for _ in range(warm):
+                sb.solve(phiDb, phib, tol=1e-8)
+            torch.cuda.synchronize()
+            eb0, eb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            eb0.record(stream)
+            for _ in range(reps):
+                stb = sb.solve(phiDb, phib, tol=1e-8)
+            eb1.record(stream)
+            torch.cuda.synchronize()
+            msb = eb0.elapsed_time(eb1) / reps
+            dofb = qb["ndof"] - qb["ndirichlet"]
+            sol[form] = phib.cpu().numpy()
+            exact_err = float(np.abs(sol[form] - W.potential3d(*Cb.T)).max())
+            big[form] = {"value": dofb / (msb / 1e3), "unit": UNIT, "ms_per_solve": msb, "timed_solves": reps,
+                         "iters": stb["iters"], "inner_iters": stb.get("inner_iters", 0),
+                         "res_final_rel": stb["res_final"] / stb["fnorm"], "setup_s": setup_s,
+                         "max_abs_error_vs_exact_potential": exact_err}
+            big["dof_free"], big["dof_total"], big["elements"] = dofb, qb["ndof"], qb["nelem"]
+            sb.close()
+            del Cb
+        big["mixed_tf32"]["max_rel_diff_vs_fp64_solution"] = float(
+            np.abs(sol["mixed_tf32"] - sol["fp64"]).max() / np.abs(sol["fp64"]).max())
+        big["mixed_tf32"]["speedup_vs_fp64"] = big["fp64"]["ms_per_solve"] / big["mixed_tf32"]["ms_per_solve"]
+        del sol
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
@@ -854,7 +947,7 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "mixed_fp32": mixed, "mixed_tf32": mixed_tc, "learned": learned, "batched": batched,
-                "update_eta": update, "other_configs": configs,
+                "update_eta": update, "other_configs": configs, "config3_256": big,
                 "fnpf_time_stepping": fnpf, "asm": asm, "anisotropic": aniso, "hull": hull}
         print(json.dumps(line), flush=True)
     solver.close()

@@ -414,6 +414,12 @@ sem_status sem_cg_csr_noalloc(long long n, const int* rowptr, const int* col, co
                               const double* dinv, const double* b, double* x, double rtol, int imax,
                               int* iters_host, void* stream);
 
+/* Measured FP64 rate of the current device in TFLOP/s: sixteen independent FMA chains per
+ * thread on every SM, timed with CUDA events.  The paper has no counterpart: it is the
+ * denominator of the FP64 operator apply's roofline (the FP64 pipe, not HBM, bounds that
+ * kernel on this device).  Synchronous; about 10 ms. */
+sem_status sem_fp64_rate(double* tflops_host);
+
 /* Solve n independent problems (tanks), each set up by its own sem_setup with
  * batch = 1 and inner_imax = 0 (Section 4.1-4.4 per tank, Algorithm 2 outer iteration:
  * u <- u + M^{-1} r with the handle's V-cycle in its precision, FP64 residual).

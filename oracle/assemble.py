@@ -60,9 +60,17 @@ class Problem:
         m = self.mesh
         return m.dim == 3 and (m.edge_arc is not None or m.col_layers is not None or m.z_iface is not None)
 
+    def _tri_nodes(self, p: int) -> np.ndarray:
+        """Reference nodes of the order-p triangle (built once per order: the per-triangle
+        loops below would otherwise rebuild the same reference element thousands of times)."""
+        cache = self.__dict__.setdefault("_tn_cache", {})
+        if p not in cache:
+            cache[p] = RefTri(p).nodes
+        return cache[p]
+
     def base_xy_P(self, b: int) -> np.ndarray:
         """(x, y) of the order-P nodes of base triangle b [NT_P, 2]."""
-        tn = RefTri(self.P).nodes
+        tn = self._tri_nodes(self.P)
         if self.mesh.dim == 3 and self.mesh.edge_arc is not None:
             return blended_xy(self.mesh, b, tn)
         return self.levels[0].tri_node_xy(b, tn)
@@ -71,7 +79,7 @@ class Problem:
         """(x, y) of level li's 2D nodes in base triangle b: the order-P map (the
         interpolant of the order-P nodes) at the level's nodes."""
         lev = self.levels[li]
-        tn = RefTri(lev.p).nodes
+        tn = self._tri_nodes(lev.p)
         if self.mesh.dim == 3 and self.mesh.edge_arc is not None:
             B, _, _ = tri_basis(self.P, tn)
             return B @ self.base_xy_P(b)

@@ -4,9 +4,10 @@ Used only by bench.py's CPU baseline and reference arm, as a separate process
 (so that thread limits apply before NumPy loads).  The oracle runs as it
 stands: assembled CSR matrices, SciPy sparse products, sparse LU coarse solve.
 
-    python -m oracle.timing --n 8 --P 6 --nlayers 4 --solves 4 [--warmup 0]
+    python -m oracle.timing --n 8 --P 6 --nlayers 4 --solves 4 [--warmup 0] [--direct 2]
 
-prints one JSON line: free DOF, solves, seconds, DOF/s, iterations.
+prints one JSON line: free DOF, solves, seconds, DOF/s, iterations (and the direct
+solves' time with --direct).
 """
 from __future__ import annotations
 
@@ -26,6 +27,9 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=0)
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--per-solve", action="store_true", help="print one line per timed solve")
+    ap.add_argument("--direct", type=int, default=0,
+                    help="also time this many direct solves (sparse LU of the free-node matrix, factorised "
+                         "in every solve, plus one refinement step)")
     a = ap.parse_args(argv)
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if root not in sys.path:
@@ -60,9 +64,18 @@ def main(argv=None):
             print(json.dumps({"solve_s": times[-1], "iters": res.iters}), flush=True)
     dof = int(lev.free.size)
     tot = float(np.sum(times))
-    print(json.dumps({"dof_free": dof, "solves": a.solves, "seconds": tot, "dof_per_s": dof * a.solves / tot,
-                      "solves_per_s": a.solves / tot, "iters": iters, "setup_s": setup_s,
-                      "mesh": f"{a.n}x{a.n}x{a.nlayers} P={a.P}"}))
+    out = {"dof_free": dof, "solves": a.solves, "seconds": tot, "dof_per_s": dof * a.solves / tot,
+           "solves_per_s": a.solves / tot, "iters": iters, "setup_s": setup_s,
+           "mesh": f"{a.n}x{a.n}x{a.nlayers} P={a.P}"}
+    if a.direct > 0:
+        dt = []
+        for _ in range(a.direct):
+            t = time.perf_counter()
+            S.solve_laplace_direct(prob, phiD)
+            dt.append(time.perf_counter() - t)
+        out["direct"] = {"solves": a.direct, "seconds": float(np.sum(dt)),
+                         "ms_per_solve": 1e3 * float(np.mean(dt)), "dof_per_s": dof * a.direct / float(np.sum(dt))}
+    print(json.dumps(out))
 
 
 if __name__ == "__main__":

@@ -29,7 +29,7 @@ EXPORTS = ("sem_default_options", "sem_mesh_nodes2d", "sem_setup", "sem_destroy"
            "sem_dirichlet_nodes", "sem_node_coords", "sem_element_map", "sem_lambda_max", "sem_diagonal",
            "sem_apply", "sem_apply32", "sem_update_eta", "sem_fnpf_rhs", "sem_fnpf_step", "pmg_vcycle", "laplace_solve", "laplace_solve_host", "sem_last_error",
            "sem_cg_csr_noalloc", "sem_mlp_get_weights", "sem_mlp_set_weights", "sem_mlp_forward",
-           "sem_mlp_gradient", "sem_mlp_adam", "sem_learned_sweep", "sem_learned_train", "laplace_solve_batch", "sem_tile_shapes", "sem_tc_kernel",
+           "sem_mlp_gradient", "sem_mlp_adam", "sem_learned_sweep", "sem_learned_train", "laplace_solve_batch", "sem_tile_shapes", "sem_tc_kernel", "sem_fp64_rate",
            "sem_asm_subdomains", "sem_asm_apply", "sem_asm_apply32")
 
 
@@ -100,6 +100,8 @@ def lib():
     L.sem_tile_shapes.restype = c_int
     L.sem_tc_kernel.argtypes = [c_void_p, c_int, POINTER(c_int)]
     L.sem_tc_kernel.restype = c_int
+    L.sem_fp64_rate.argtypes = [POINTER(c_double)]
+    L.sem_fp64_rate.restype = c_int
     L.sem_apply.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_void_p]
     L.sem_apply32.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_int, c_void_p]
     L.sem_update_eta.argtypes = [c_void_p, POINTER(c_double), c_int]
@@ -278,6 +280,13 @@ def sem_diagonal(h: int, level: int = 0) -> np.ndarray:
     out = np.zeros(q["ndof"])
     _check(lib().sem_diagonal(h, level, _dptr(out, c_double)))
     return out
+
+
+def sem_fp64_rate() -> float:
+    """Measured FP64 FMA rate of the current device (TFLOP/s)."""
+    r = c_double(0.0)
+    _check(lib().sem_fp64_rate(byref(r)))
+    return r.value
 
 
 def sem_tc_kernel(h: int, level: int = 0) -> int:

@@ -1438,6 +1438,67 @@ cudaError_t cg_direction(long long n, const double* z, double* p, Scratch& sc, c
 }
 
 
+// ====================================================================== FP64 pipe rate
+// Sixteen independent fused multiply-add chains per thread on every SM: the FP64 rate the
+// device reaches on plain dependent-free arithmetic, the denominator of the FP64 apply's
+// roofline.
+constexpr int kFmaChains = 16;
+
+__global__ void k_fp64_fma_chains(int iters, double seed, double* sink) {
+    double a[kFmaChains];
+#pragma unroll
+    for (int j = 0; j < kFmaChains; ++j) a[j] = seed + 1e-3 * (threadIdx.x + j);
+    const double m = 0.9999999, c = 1e-9;
+#pragma unroll 4
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < kFmaChains; ++j) a[j] = fma(a[j], m, c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < kFmaChains; ++j) s += a[j];
+    if (s == 12345.678) sink[0] = s;          // never true: keeps the chains alive
+}
+
+}  // namespace sem
+
+extern "C" sem_status sem_fp64_rate(double* tflops_host) {
+    using namespace sem;
+    if (!tflops_host) {
+        set_error("sem_fp64_rate: NULL result");
+        return SEM_EINVAL;
+    }
+    int dev = 0, sms = kSMs;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int threads = 256, blocks = 8 * sms, iters = 1 << 13;
+    cudaEvent_t e0, e1;
+    cudaError_t err = cudaEventCreate(&e0);
+    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    float ms = 0.f;
+    if (err == cudaSuccess) {
+        k_fp64_fma_chains<<<blocks, threads>>>(256, 1.0, nullptr);      // warm-up
+        err = cudaEventRecord(e0, 0);
+    }
+    if (err == cudaSuccess) {
+        k_fp64_fma_chains<<<blocks, threads>>>(iters, 1.0, nullptr);
+        err = cudaGetLastError();
+    }
+    if (err == cudaSuccess) err = cudaEventRecord(e1, 0);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess || !(ms > 0.f)) {
+        set_error(std::string("sem_fp64_rate: ") + cudaGetErrorString(err));
+        return SEM_ECUDA;
+    }
+    *tflops_host = 2.0 * kFmaChains * iters * (double)threads * blocks / (ms * 1e-3) / 1e12;
+    return SEM_OK;
+}
+
+namespace sem {
+
 // ====================================================================== no-allocation CG
 // A variant of the coarse CG launch for callers that cannot allocate device
 // memory: the CG vectors r, z, p, q, the reduction partials, the barrier state
