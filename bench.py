@@ -295,6 +295,7 @@ def main():
     ap.add_argument("--no-asm", action="store_true")
     ap.add_argument("--no-aniso", action="store_true")
     ap.add_argument("--no-hull", action="store_true")
+    ap.add_argument("--no-deterministic", action="store_true")
     ap.add_argument("--no-config3-256", action="store_true",
                     help="skip the 256x256x6 P=6 box (85 M free DOF; FP64 and MIXED_TF32 solves, about 2 minutes)")
     ap.add_argument("--batch-tanks", type=int, default=256,
@@ -405,6 +406,27 @@ def main():
                 "hbm_view": {"algorithmic_bytes": apply_bytes(P, E, N),
                              "achieved_gbs": apply_bytes(P, E, N) / avg_apply_s / 1e9,
                              "peak_gbs": hbm_peak, "frac": apply_bytes(P, E, N) / avg_apply_s / 1e9 / hbm_peak}}
+
+    # the same FP64 solve with the atomic-free direct-stiffness summation (deterministic = 1):
+    # element results summed per node over the precomputed node -> slot map, bit-reproducible
+    det = None
+    if not a.no_deterministic:
+        dsolver = sem.Solver(mesh, P, eta_nodal=eta, levels=levels_for(P), profile=1, deterministic=1)
+        phi_d = torch.empty(N, dtype=torch.float64, device="cuda")
+        ms_d, st_d = timed(dsolver, 3, 1, phi_d)
+        ms_d = max_over_ranks(ms_d)
+        dsolver.solve(phiD, phi_d, tol=1e-8)
+        phi_d2 = phi_d.clone()
+        dsolver.solve(phiD, phi_d, tol=1e-8)
+        torch.cuda.synchronize()
+        det = {"value": dof * 3 * world / (ms_d / 1000.0), "unit": UNIT, "ms_per_step": ms_d / 3,
+               "iters": st_d[-1]["iters"], "bit_identical_repeat": bool(torch.equal(phi_d, phi_d2)),
+               "apply_fp64_avg_launch_ms": sum(x["apply_ms"] for x in st_d) / max(1, sum(x["apply_launches"] for x in st_d)),
+               "apply_fp64_atomic_avg_launch_ms": avg_apply_s * 1e3,
+               "max_rel_diff_vs_atomic_solution": float((phi_d - phi).abs().max().item() / phi.abs().max().item()),
+               "form": "FP64 PCG as the headline, the FP64 applies and restrictions summed per node in a fixed "
+                       "order (element results + node -> slot map, no atomics); apply time includes the node sums"}
+        dsolver.close()
 
     # end to end through the host-buffer C-ABI call (copies inside the timed region)
     phiD_pin = torch.tensor(phiD_h).pin_memory()
@@ -947,7 +969,7 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "mixed_fp32": mixed, "mixed_tf32": mixed_tc, "learned": learned, "batched": batched,
-                "update_eta": update, "other_configs": configs, "config3_256": big,
+                "update_eta": update, "other_configs": configs, "config3_256": big, "fp64_deterministic": det,
                 "fnpf_time_stepping": fnpf, "asm": asm, "anisotropic": aniso, "hull": hull}
         print(json.dumps(line), flush=True)
     solver.close()

@@ -179,6 +179,11 @@ typedef struct {
                                    e.g. (5,3) -> (3,3) -> (1,1).  Per level neither order may grow and one
                                    must fall; the coarsest level is (1,1); the vertical order equals the
                                    triangle order or lies one or two below it */
+    int deterministic;          /* 3D meshes: 1 = the FP64 operator applies and restrictions write element
+                                   results that each node then sums over a precomputed node -> element-slot
+                                   map in a fixed order (no atomics), so FP64 solves are bit-reproducible run
+                                   to run; 0 (default) = atomic summation.  The single-precision applies
+                                   keep atomic summation */
 } sem_options;
 
 typedef struct {

@@ -66,7 +66,7 @@ template <int P, int PZ, typename T, bool LIFT, int V>
 __global__ void __launch_bounds__(PrismTile<P, PZ, T, V>::NTHR)
     k_apply_prism(int E, const int* __restrict__ map, const T* __restrict__ G, const T* __restrict__ refm,
                   const T* __restrict__ x, T* __restrict__ y, const int* __restrict__ skip,
-                  const int* __restrict__ elist) {
+                  const int* __restrict__ elist, T* __restrict__ ye) {
     using D = PrismTile<P, PZ, T, V>;
     constexpr int NT = D::NT, NZ = D::NZ, QT = D::QT, QZ = D::QZ, Np = D::Np, Nq = D::Nq, QZP = D::QZP, EB = D::EB;
     if (skip != nullptr && *skip) return;
@@ -201,14 +201,20 @@ __global__ void __launch_bounds__(PrismTile<P, PZ, T, V>::NTHR)
                     xt[qz] += bt * d[qz];
                 }
             }
-            const int* me = map + (size_t)(elist ? elist[e0 + b] : e0 + b) * Np;
+            const size_t eid = (size_t)(elist ? elist[e0 + b] : e0 + b);
+            const int* me = map + eid * Np;
 #pragma unroll
             for (int k = 0; k < NZ; ++k) {
                 T s = 0;
 #pragma unroll
                 for (int qz = 0; qz < QZ; ++qz) s += sBz[qz * NZ + k] * xr[qz] + sDz[qz * NZ + k] * xt[qz];
-                const int m = me[k * NT + n];
-                if (m >= 0) atomicAdd(&y[m], s);
+                // element results (deterministic summation afterwards by node) or atomic summation
+                if (ye != nullptr) {
+                    ye[eid * Np + k * NT + n] = s;
+                } else {
+                    const int m = me[k * NT + n];
+                    if (m >= 0) atomicAdd(&y[m], s);
+                }
             }
         }
         __syncthreads();
@@ -216,7 +222,7 @@ __global__ void __launch_bounds__(PrismTile<P, PZ, T, V>::NTHR)
 }
 
 template <int P, int PZ, typename T, bool LIFT, int V>
-cudaError_t apply_prism_impl(const Level& L, const T* refm, const T* G, const T* x, T* y, const int* skip,
+cudaError_t apply_prism_impl(const Level& L, const T* refm, const T* G, const T* x, T* y, const int* skip, T* ye,
                              cudaStream_t s) {
     using D = PrismTile<P, PZ, T, V>;
     static int per_sm = 0;
@@ -230,14 +236,14 @@ cudaError_t apply_prism_impl(const Level& L, const T* refm, const T* G, const T*
     }
     // the lifting apply (x zero on the free nodes) only needs the elements that touch a
     // Dirichlet node: every other element gathers zeros
-    const bool sub = LIFT && L.lift_elems != nullptr;
+    const bool sub = LIFT && L.lift_elems != nullptr && ye == nullptr;   // element results need every element
     const int E = sub ? L.nlift : L.E;
     const int batches = (E + D::EB - 1) / D::EB;
     int grid = kSMs * per_sm;
     if (grid > batches) grid = batches;
     if (grid < 1) return cudaSuccess;
     k_apply_prism<P, PZ, T, LIFT, V><<<grid, D::NTHR, D::SMEM, s>>>(E, L.map, G, refm, x, y, skip,
-                                                                    sub ? L.lift_elems : nullptr);
+                                                                    sub ? L.lift_elems : nullptr, ye);
     return cudaGetLastError();
 }
 
@@ -245,9 +251,9 @@ cudaError_t apply_prism_impl(const Level& L, const T* refm, const T* G, const T*
 
 template <typename T, bool LIFT, int V>
 static cudaError_t prism_dispatch(const Level& L, const T* refm, const T* G, const T* x, T* y, const int* skip,
-                                  cudaStream_t s) {
+                                  T* ye, cudaStream_t s) {
 #define SEM_PRISM_PAIR(a, b) \
-    case (a) * 8 + (b): return apply_prism_impl<a, b, T, LIFT, V>(L, refm, G, x, y, skip, s);
+    case (a) * 8 + (b): return apply_prism_impl<a, b, T, LIFT, V>(L, refm, G, x, y, skip, ye, s);
     switch (L.p * 8 + L.pz) {
         // isotropic orders
         SEM_PRISM_PAIR(1, 1) SEM_PRISM_PAIR(2, 2) SEM_PRISM_PAIR(3, 3)
@@ -267,16 +273,21 @@ bool prism_pair_supported(int p, int pz) {
 
 cudaError_t launch_apply_prism64(const Level& L, const double* x, double* y, bool lift, const int* skip, int variant,
                                  cudaStream_t s) {
-    if (lift) return variant ? prism_dispatch<double, true, 1>(L, L.ref64.m, L.G, x, y, skip, s)
-                             : prism_dispatch<double, true, 0>(L, L.ref64.m, L.G, x, y, skip, s);
-    return variant ? prism_dispatch<double, false, 1>(L, L.ref64.m, L.G, x, y, skip, s)
-                   : prism_dispatch<double, false, 0>(L, L.ref64.m, L.G, x, y, skip, s);
+    // deterministic handles: element results, then the per-node sums in a fixed order
+    double* ye = L.ye64;
+    cudaError_t e;
+    if (lift) e = variant ? prism_dispatch<double, true, 1>(L, L.ref64.m, L.G, x, y, skip, ye, s)
+                          : prism_dispatch<double, true, 0>(L, L.ref64.m, L.G, x, y, skip, ye, s);
+    else e = variant ? prism_dispatch<double, false, 1>(L, L.ref64.m, L.G, x, y, skip, ye, s)
+                     : prism_dispatch<double, false, 0>(L, L.ref64.m, L.G, x, y, skip, ye, s);
+    if (e != cudaSuccess || ye == nullptr) return e;
+    return dss_gather64(L, ye, y, skip, s, true);
 }
 
 cudaError_t launch_apply_prism32(const Level& L, const float* x, float* y, const int* skip, int variant,
                                  cudaStream_t s) {
-    return variant ? prism_dispatch<float, false, 1>(L, L.ref32.m, L.G32, x, y, skip, s)
-                   : prism_dispatch<float, false, 0>(L, L.ref32.m, L.G32, x, y, skip, s);
+    return variant ? prism_dispatch<float, false, 1>(L, L.ref32.m, L.G32, x, y, skip, nullptr, s)
+                   : prism_dispatch<float, false, 0>(L, L.ref32.m, L.G32, x, y, skip, nullptr, s);
 }
 
 int prism_tile_elements(int P, int variant) { return (variant == 0 ? 8 : 4) * (P <= 2 ? 4 : (P == 3 ? 2 : 1)); }

@@ -337,7 +337,8 @@ __global__ void k_geom_tri(int E, int QT, const double* __restrict__ vtri, const
 // diag(A)_i = sum over elements of sum_q grad N_l^T G_q grad N_l, sum-factorised
 // over the vertical direction for prisms.
 __global__ void k_diag(int E, int dim, int NT, int NZ, int QT, int QZ, const int* __restrict__ map,
-                       const double* __restrict__ G, const double* __restrict__ refm, double* __restrict__ diag) {
+                       const double* __restrict__ G, const double* __restrict__ refm, double* __restrict__ diag,
+                       double* __restrict__ ye) {
     extern __shared__ double sdiag[];       // [6][NT][QZ]
     const int Nq = QT * QZ, Np = NT * NZ;
     const int nc = (dim == 3) ? 6 : 3;
@@ -380,7 +381,8 @@ __global__ void k_diag(int E, int dim, int NT, int NZ, int QT, int QZ, const int
                      2.0 * bz * dz * (sdiag[2 * NT * QZ + j] + sdiag[4 * NT * QZ + j]) +
                      dz * dz * sdiag[5 * NT * QZ + j];
             }
-            atomicAdd(&diag[decode(map[(size_t)e * Np + i])], v);
+            if (ye != nullptr) ye[(size_t)e * Np + i] = v;      // summed by node afterwards
+            else atomicAdd(&diag[decode(map[(size_t)e * Np + i])], v);
         }
         __syncthreads();
     }
@@ -392,6 +394,35 @@ __global__ void k_diag(int E, int dim, int NT, int NZ, int QT, int QZ, const int
 // coarse 1D basis at the fine GLL nodes (Bz = [1] for triangles), so both
 // transfers are applied in two sum-factorised stages.  A CTA handles kTrEB
 // elements per pass.
+// Direct-stiffness summation without atomics (deterministic handles): node g sums the
+// element results of its slots ye[e Np + l] in the fixed order of the node's segment
+// [ptr[g], ptr[g+1]) of the precomputed node -> slot map (ascending element, then local
+// index).  masked: Dirichlet nodes (negative map entries) get 0, as in the masked operator;
+// nodes in no element get 0.
+__global__ void k_dss_gather(long long N, const int* __restrict__ ptr, const int* __restrict__ slot,
+                             const int* __restrict__ map, int masked, const double* __restrict__ ye,
+                             double* __restrict__ y, const int* __restrict__ skip) {
+    if (skip != nullptr && *skip) return;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x) {
+        const int a = ptr[g], b = ptr[g + 1];
+        double v = 0.0;
+        if (!(masked && b > a && map[slot[a]] < 0))
+            for (int i = a; i < b; ++i) v += ye[slot[i]];
+        y[g] = v;
+    }
+}
+
+}  // namespace
+
+cudaError_t dss_gather64(const Level& L, const double* ye, double* y, const int* skip, cudaStream_t s, bool masked) {
+    if (L.dss_ptr == nullptr || L.dss_slot == nullptr) return cudaErrorInvalidValue;
+    k_dss_gather<<<vec_grid(L.N), kVecThreads, 0, s>>>(L.N, L.dss_ptr, L.dss_slot, L.map, masked ? 1 : 0, ye, y,
+                                                        skip);
+    return cudaGetLastError();
+}
+
+namespace {
+
 constexpr int kTrEB = 8;
 
 // Restriction (R = P^T): fine residual r = f - y weighted by 1/multiplicity,
@@ -401,7 +432,7 @@ template <typename T>
 __global__ void k_restrict(int E, int NTf, int NZf, int NTc, int NZc, const int* __restrict__ mapf,
                            const int* __restrict__ mapc, const T* __restrict__ wmult, const T* __restrict__ Bt,
                            const T* __restrict__ Bz, const T* __restrict__ f, const T* __restrict__ y,
-                           T* __restrict__ fc) {
+                           T* __restrict__ fc, T* __restrict__ yec) {
     extern __shared__ __align__(16) unsigned char smr[];
     const int Npf = NTf * NZf, Npc = NTc * NZc;
     T* sBt = reinterpret_cast<T*>(smr);
@@ -433,7 +464,8 @@ __global__ void k_restrict(int E, int NTf, int NZf, int NTc, int NZc, const int*
             if (m < 0) continue;
             T v = 0;
             for (int kf = 0; kf < NZf; ++kf) v += sBz[kf * NZc + kc] * tt[b * NZf * NTc + kf * NTc + nc];
-            atomicAdd(&fc[m], v);
+            if (yec != nullptr) yec[(size_t)(e0 + b) * Npc + c] = v;    // summed by node afterwards
+            else atomicAdd(&fc[m], v);
         }
     }
 }
@@ -780,12 +812,23 @@ __device__ double grid_total(const double* part) {
     return t;
 }
 
+// Deterministic coarse assembly: CSR entry k sums its element entries ev[eidx[i]],
+// i in [eptr[k], eptr[k+1]), in that fixed order.
+__global__ void k_entry_sums(long long nnz, const int* __restrict__ eptr, const int* __restrict__ eidx,
+                             const double* __restrict__ ev, double* __restrict__ vals) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nnz; k += (long long)gridDim.x * blockDim.x) {
+        double v = 0.0;
+        for (int i = eptr[k]; i < eptr[k + 1]; ++i) v += ev[eidx[i]];
+        vals[k] = v;
+    }
+}
+
 // Element matrices of the coarsest level summed into its CSR matrix (free rows and
 // columns only): A_e[i][j] = sum_q sum_ab gref[a][q][i] G_ab(q) gref[b][q][j];
 // slot[e][i][j] is the CSR position of (map_i, map_j) or -1.  One thread per (e, i).
 __global__ void k_coarse_assemble(int E, int dim, int Np, int Nq, const double* __restrict__ G,
                                   const double* __restrict__ gref, const int* __restrict__ slot,
-                                  double* __restrict__ vals) {
+                                  double* __restrict__ vals, double* __restrict__ ev) {
     const int nc = dim == 3 ? 6 : 3;
     const long long total = (long long)E * Np;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
@@ -812,7 +855,8 @@ __global__ void k_coarse_assemble(int E, int dim, int Np, int Nq, const double* 
                 for (int a = 0; a < dim; ++a)
                     for (int c = 0; c < dim; ++c) v += gi[a] * g[a][c] * gj[c];
             }
-            atomicAdd(&vals[sl], v);
+            if (ev != nullptr) ev[((size_t)e * Np + i) * Np + j] = v;    // summed per entry afterwards
+            else atomicAdd(&vals[sl], v);
         }
     }
 }
@@ -1196,8 +1240,10 @@ cudaError_t launch_geometry_general(Level& L, const int* eb, const int* el, cons
 cudaError_t launch_diag(const Level& L, double* diag, cudaStream_t s) {
     const size_t smem = sizeof(double) * 6 * L.NT * L.QZ;
     const int grid = std::min(L.E, kSMs * 8);
-    k_diag<<<grid, 128, smem, s>>>(L.E, L.dim, L.NT, L.NZ, L.QT, L.QZ, L.map, L.G, L.ref64.m, diag);
-    return cudaGetLastError();
+    k_diag<<<grid, 128, smem, s>>>(L.E, L.dim, L.NT, L.NZ, L.QT, L.QZ, L.map, L.G, L.ref64.m, diag, L.ye64);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || L.ye64 == nullptr) return e;
+    return dss_gather64(L, L.ye64, diag, nullptr, s, false);
 }
 
 template <typename T>
@@ -1205,8 +1251,13 @@ static cudaError_t restrict_t(const Level& F, const Level& C, const T* wm, const
                               const T* y, T* fc, cudaStream_t s) {
     const int grid = std::min((F.E + kTrEB - 1) / kTrEB, kSMs * 8);
     const size_t smem = sizeof(T) * (F.NT * C.NT + F.NZ * C.NZ + kTrEB * (F.Np + F.NZ * C.NT));
-    k_restrict<T><<<grid, 256, smem, s>>>(F.E, F.NT, F.NZ, C.NT, C.NZ, F.map, C.map, wm, Bt, Bz, f, y, fc);
-    return cudaGetLastError();
+    T* yec = nullptr;
+    if constexpr (sizeof(T) == sizeof(double)) yec = C.ye64;
+    k_restrict<T><<<grid, 256, smem, s>>>(F.E, F.NT, F.NZ, C.NT, C.NZ, F.map, C.map, wm, Bt, Bz, f, y, fc, yec);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || yec == nullptr) return e;
+    if constexpr (sizeof(T) == sizeof(double)) return dss_gather64(C, C.ye64, fc, nullptr, s, true);
+    return e;
 }
 
 template <typename T>
@@ -1375,7 +1426,10 @@ cudaError_t scale64(long long n, const double* w, const double* nrm2, double* v,
 cudaError_t coarse_assemble(const Level& C, const double* gref, const int* slot, double* vals, cudaStream_t s) {
     const long long total = (long long)C.E * C.Np;
     const int grid = (int)std::min<long long>((total + 255) / 256, kSMs * 16);
-    k_coarse_assemble<<<grid, 256, 0, s>>>(C.E, C.dim, C.Np, C.Nq, C.G, gref, slot, vals);
+    k_coarse_assemble<<<grid, 256, 0, s>>>(C.E, C.dim, C.Np, C.Nq, C.G, gref, slot, vals, C.csr_ev);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || C.csr_ev == nullptr) return e;
+    k_entry_sums<<<vec_grid(C.csr_nnz), kVecThreads, 0, s>>>(C.csr_nnz, C.csr_eptr, C.csr_eidx, C.csr_ev, vals);
     return cudaGetLastError();
 }
 

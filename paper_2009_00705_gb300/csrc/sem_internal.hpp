@@ -66,6 +66,13 @@ struct Level {
     int* csr_col = nullptr;
     double* csr_val = nullptr;
     int* csr_slot = nullptr;               // [E][Np][Np] CSR position of each element entry (or -1)
+    // deterministic handles (prisms): node -> element-slot map and the FP64 element results
+    int* dss_ptr = nullptr;                // [N + 1] segment of each node in dss_slot
+    int* dss_slot = nullptr;               // slots e * Np + l of the free nodes, ascending (e, l) per node
+    double* ye64 = nullptr;                // [E][Np] element results of the FP64 apply / restriction / diagonal
+    int* csr_eptr = nullptr;               // coarse level: CSR entry -> element entries (e Np + i) Np + j, ascending
+    int* csr_eidx = nullptr;
+    double* csr_ev = nullptr;              // [E][Np][Np] element-matrix entries before their fixed-order sums
     long long csr_nnz = 0;
     // additive Schwarz smoother (smoother = ASM; every level but the coarsest)
     int asm_nmax = 0;                      // largest subdomain (free nodes)
@@ -220,6 +227,10 @@ inline bool level_tc(const Level& L) { return L.dim == 3 && L.pz == L.p && prism
 // apply_prism.cu: (triangle order, vertical order) pairs the prism apply is compiled for
 bool prism_pair_supported(int p, int pz);
 cudaError_t build_g16(Level& L, cudaStream_t s);
+// kernels.cu: y[g] = sum of the element results ye over node g's slots (fixed order); masked:
+// 0 at the Dirichlet nodes
+cudaError_t dss_gather64(const Level& L, const double* ye, double* y, const int* skip, cudaStream_t s,
+                         bool masked);
 // apply_prism_t5.cu: the factors of an order-6 prism level in the tcgen05 kernel's layout
 cudaError_t build_g16_t6(Level& L, cudaStream_t s);
 // fnpf.cu: surface fields of the free-surface time stepping

@@ -485,6 +485,21 @@ sem_status build_coarse_gradients(sem_handle* h) {
     CK(upload(&C.csr_col, col));
     CK(upload(&C.csr_slot, slot));          // kept: the values are reassembled when eta changes
     CK(dalloc(&C.csr_val, col.size()));
+    if (h->opts.deterministic) {
+        // every CSR entry sums its element entries in a fixed (ascending) order: the entry ->
+        // element-entry map by a counting sort over slot
+        std::vector<int> eptr((size_t)C.csr_nnz + 1, 0);
+        for (size_t t = 0; t < slot.size(); ++t)
+            if (slot[t] >= 0) ++eptr[(size_t)slot[t] + 1];
+        for (long long k = 0; k < C.csr_nnz; ++k) eptr[(size_t)k + 1] += eptr[(size_t)k];
+        std::vector<int> fill(eptr.begin(), eptr.end() - 1), eidx((size_t)eptr[(size_t)C.csr_nnz]);
+        for (size_t t = 0; t < slot.size(); ++t)
+            if (slot[t] >= 0) eidx[(size_t)fill[(size_t)slot[t]]++] = (int)t;
+        CK(upload(&C.csr_eptr, eptr));
+        CK(upload(&C.csr_eidx, eidx));
+        CK(dalloc(&C.csr_ev, slot.size()));
+        CK(cudaMemset(C.csr_ev, 0, sizeof(double) * slot.size()));
+    }
     return reassemble_coarse(h);
 }
 
@@ -493,7 +508,7 @@ sem_status reassemble_coarse(sem_handle* h) {
     Level& C = h->lv.back();
     if (C.csr_val == nullptr) return SEM_OK;
     CK(cudaMemset(C.csr_val, 0, sizeof(double) * C.csr_nnz));
-    CK(coarse_assemble(C, C.gref, C.csr_slot, C.csr_val, 0));
+    CK(coarse_assemble(C, C.gref, C.csr_slot, C.csr_val, 0));    // atomic, or fixed-order sums (deterministic)
     CK(cudaDeviceSynchronize());
     return SEM_OK;
 }

@@ -622,9 +622,39 @@ cudaError_t tune_tc(Level& L) {
     return cudaSuccess;
 }
 
+// The node -> element-slot map of a level for the atomic-free direct-stiffness summation:
+// for every node g, the slots e * Np + l whose map entry names g (free or Dirichlet) in
+// ascending (e, l) order (a counting sort over the element map), and the FP64
+// element-result buffer.
+sem_status build_dss(Level& L) {
+    const long long slots = (long long)L.E * L.Np;
+    if (slots >= (1LL << 31) || L.N >= (1LL << 31)) {
+        set_error("deterministic: the level has too many element slots for 32-bit indices");
+        return SEM_EINVAL;
+    }
+    auto node = [&](long long i) -> long long { const int m = L.hmap[i]; return m >= 0 ? m : -(long long)m - 1; };
+    std::vector<int> ptr((size_t)L.N + 1, 0);
+    for (long long i = 0; i < slots; ++i) ++ptr[(size_t)node(i) + 1];
+    for (long long g = 0; g < L.N; ++g) ptr[(size_t)g + 1] += ptr[(size_t)g];
+    std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+    std::vector<int> slot((size_t)slots);
+    for (long long i = 0; i < slots; ++i) slot[(size_t)fill[(size_t)node(i)]++] = (int)i;
+    void* p = nullptr;
+    CKS(cudaMalloc(&p, sizeof(int) * ptr.size()));
+    L.dss_ptr = static_cast<int*>(p);
+    CKS(cudaMemcpy(L.dss_ptr, ptr.data(), sizeof(int) * ptr.size(), cudaMemcpyHostToDevice));
+    CKS(cudaMalloc(&p, sizeof(int) * (slot.empty() ? 1 : slot.size())));
+    L.dss_slot = static_cast<int*>(p);
+    if (!slot.empty()) CKS(cudaMemcpy(L.dss_slot, slot.data(), sizeof(int) * slot.size(), cudaMemcpyHostToDevice));
+    CKS(cudaMalloc(&p, sizeof(double) * (size_t)slots));
+    L.ye64 = static_cast<double*>(p);
+    CKS(cudaMemset(L.ye64, 0, sizeof(double) * (size_t)slots));
+    return SEM_OK;
+}
+
 void free_level(Level& L) {
     void* ptrs[] = {L.map, L.G, L.G32, L.G16, L.G16T, L.lift_elems, L.dinv, L.dinv32, L.dir, L.ref64.m, L.ref32.m, L.It64, L.Iz64, L.It32, L.Iz32, L.gref,
-                    L.csr_rowptr, L.csr_col, L.csr_val, L.csr_slot,
+                    L.csr_rowptr, L.csr_col, L.csr_val, L.csr_slot, L.dss_ptr, L.dss_slot, L.ye64, L.csr_eptr, L.csr_eidx, L.csr_ev,
                     L.owner, L.wmult, L.wmult32, L.u, L.f, L.y, L.d, L.u32, L.f32, L.y32, L.d32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -969,6 +999,7 @@ void sem_default_options(sem_options* o, int P) {
     o->learned_tau = 0.5;
     o->surface_ops = 0;
     o->asm_overlap = 1;
+    o->deterministic = 0;
 }
 
 sem_status sem_mesh_nodes2d(const sem_mesh* m, int p, long long* n2, double* xy) {
@@ -1046,6 +1077,11 @@ sem_status sem_setup(const sem_mesh* m, int P, const sem_options* opts, sem_hand
     sem_status st = SEM_OK;
     for (int li = 0; li < o.nlevels && st == SEM_OK; ++li)
         st = build_level(h, m, li, o.level_p[li], level_pz(o, li, m->dim));
+    if (st == SEM_OK && o.deterministic && m->dim == 3)
+        for (Level& L : h->lv) {
+            if (st != SEM_OK) break;
+            st = build_dss(L);
+        }
     if (st == SEM_OK) st = build_geometry(h, m);
     if (st == SEM_OK) st = build_diagonals(h);
     if (st == SEM_OK) st = build_transfers(h);
