@@ -271,11 +271,12 @@ cudaError_t random_free(long long n, unsigned long long seed, const float* dinv,
 }
 
 cudaError_t mlp_forward(const MlpNet& net, int B, const float* X, float* A1, float* H1, float* Y, cudaStream_t s) {
-    cudaError_t e = gemm<false, true, __nv_bfloat16, EPI_BIAS_RELU>(B, net.H, net.nin, X, net.nin, net.W1b, net.nin, H1,
-                                                                     net.H, net.b1, A1, 1, s);
+    // H1 = relu(X W1^T + b1) (A1 the pre-activation), Y = H1 W2^T + b2 on the tensor cores
+    cudaError_t e = gemm_t5<false, true, __nv_bfloat16, EPI_BIAS_RELU>(B, net.H, net.nin, X, net.nin, net.W1b, net.nin,
+                                                                        H1, net.H, net.b1, A1, 1, net.err, s);
     if (e != cudaSuccess) return e;
-    return gemm<false, true, __nv_bfloat16, EPI_BIAS>(B, net.nout, net.H, H1, net.H, net.W2b, net.H, Y, net.nout,
-                                                       net.b2, nullptr, 1, s);
+    return gemm_t5<false, true, __nv_bfloat16, EPI_BIAS>(B, net.nout, net.H, H1, net.H, net.W2b, net.H, Y, net.nout,
+                                                          net.b2, nullptr, 1, net.err, s);
 }
 
 cudaError_t mlp_backward(const MlpNet& net, int B, const float* X, const float* T, float* A1, float* H1, float* Y,
@@ -291,20 +292,20 @@ cudaError_t mlp_backward(const MlpNet& net, int B, const float* X, const float* 
     if ((e = cudaMemsetAsync(g.db2, 0, sizeof(float) * net.nout, s)) != cudaSuccess) return e;
     const int split = std::max(1, std::min(128, B / 256));
     // dW2 [nout][H] = dY^T H1
-    if ((e = gemm<true, false, float, EPI_ATOMIC>(net.nout, net.H, B, dY, net.nout, H1, net.H, g.dW2, net.H, nullptr,
-                                                  nullptr, split, s)) != cudaSuccess)
+    if ((e = gemm_t5<true, false, float, EPI_ATOMIC>(net.nout, net.H, B, dY, net.nout, H1, net.H, g.dW2, net.H,
+                                                     nullptr, nullptr, split, net.err, s)) != cudaSuccess)
         return e;
     k_colsum<<<std::min(B, 1024), 256, 0, s>>>(B, net.nout, dY, g.db2);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // dH [B][H] = dY W2, then the ReLU derivative
-    if ((e = gemm<false, false, __nv_bfloat16, EPI_STORE>(B, net.H, net.nout, dY, net.nout, net.W2b, net.H, dH, net.H,
-                                                          nullptr, nullptr, 1, s)) != cudaSuccess)
+    if ((e = gemm_t5<false, false, __nv_bfloat16, EPI_STORE>(B, net.H, net.nout, dY, net.nout, net.W2b, net.H, dH,
+                                                             net.H, nullptr, nullptr, 1, net.err, s)) != cudaSuccess)
         return e;
     k_relu_back<<<vgrid(nh), 256, 0, s>>>(nh, A1, dH);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // dW1 [H][nin] = dA1^T X
-    if ((e = gemm<true, false, float, EPI_ATOMIC>(net.H, net.nin, B, dH, net.H, X, net.nin, g.dW1, net.nin, nullptr,
-                                                  nullptr, split, s)) != cudaSuccess)
+    if ((e = gemm_t5<true, false, float, EPI_ATOMIC>(net.H, net.nin, B, dH, net.H, X, net.nin, g.dW1, net.nin,
+                                                     nullptr, nullptr, split, net.err, s)) != cudaSuccess)
         return e;
     k_colsum<<<std::min(B, 1024), 256, 0, s>>>(B, net.H, dH, g.db1);
     return cudaGetLastError();

@@ -12,7 +12,15 @@ struct MlpNet {
     int nin = 0, H = 0, nout = 0;
     float *W1 = nullptr, *b1 = nullptr, *W2 = nullptr, *b2 = nullptr;
     __nv_bfloat16 *W1b = nullptr, *W2b = nullptr;
+    int* err = nullptr;         // device flag set when a bounded wait of the tensor-core GEMMs ran out
 };
+
+// mlp_gemm_t5.cu: C[M][N] = A(m, k) B(k, n) on the tensor cores (TF32, FP32 accumulation),
+// A(m, k) = TA ? A[k lda + m] : A[m lda + k], B(k, n) = TB ? B[n ldb + k] : B[k ldb + n];
+// epilogues EPI_*; splitk chunks of K for EPI_ATOMIC
+template <bool TA, bool TB, typename TBt, int EPI>
+cudaError_t gemm_t5(int M, int N, int K, const float* A, int lda, const TBt* B, int ldb, float* C, int ldc,
+                    const float* bias, float* Cpre, int splitk, int* err, cudaStream_t s);
 
 struct MlpGrads {
     float *dW1 = nullptr, *db1 = nullptr, *dW2 = nullptr, *db2 = nullptr;

@@ -578,6 +578,7 @@ sem_status build_workspace(sem_handle* h) {
     CK(cudaMemset(sc.scal, 0, 128 * sizeof(double)));
     CK(dalloc(&sc.flags, kFlagCount));
     CK(cudaMemset(sc.flags, 0, kFlagCount * sizeof(int)));
+    h->net.err = sc.flags + F_TC_ERR;          // the network's tensor-core GEMMs report on the same flag
     CK(cudaMallocHost((void**)&sc.hpinned, 128 * sizeof(double)));
     CK(cudaMallocHost((void**)&sc.hflags, kFlagCount * sizeof(int)));
     for (double** v : {&h->r, &h->z, &h->p, &h->q, &h->x, &h->fr}) CK(dalloc(v, N));
