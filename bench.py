@@ -302,6 +302,8 @@ def main():
                     help="random tanks (500-20000 prisms, P in 3..6) for the batched measurement; 0 to skip")
     ap.add_argument("--train-snapshots", type=int, default=60)
     ap.add_argument("--train-steps", type=int, default=6)
+    ap.add_argument("--hull-train-snapshots", type=int, default=1667,
+                    help="snapshots of the hull tank's training (x --train-steps pairs: 10^4 by default)")
     ap.add_argument("--inner-imax", type=int, default=40)
     ap.add_argument("--inner-rtol", type=float, default=1e-4)
     ap.add_argument("--coarse-rtol", type=float, default=1e-2)
@@ -803,7 +805,7 @@ def main():
         hxy = sem.sem_mesh_nodes2d(hm, P)
         heta = hm.eta(hxy[:, 0], hxy[:, 1])
 
-        def hull_rate(reps=2, train=False, **opts):
+        def hull_rate(reps=2, train=False, weights=None, **opts):
             sv = sem.Solver(hm, P, eta_nodal=heta, levels=levels_for(P), coarse_rtol=a.coarse_rtol, imax=400, **opts)
             C_ = sv.coords(0)
             d_ = torch.tensor(W.potential3d(*C_[sv.dirichlet_nodes(0)].T), device="cuda")
@@ -813,11 +815,15 @@ def main():
             if train:
                 torch.cuda.synchronize()
                 t0_ = time.perf_counter()
-                l0_, l1_ = sv.train(a.train_snapshots, a.train_steps, lr=1e-3, seed=7)
+                l0_, l1_ = sv.train(a.hull_train_snapshots, a.train_steps, lr=1e-3, seed=7)
                 torch.cuda.synchronize()
-                extra["training"] = {"snapshots": a.train_snapshots, "steps_per_snapshot": a.train_steps,
+                extra["training"] = {"snapshots": a.hull_train_snapshots, "steps_per_snapshot": a.train_steps,
+                                     "pairs": a.hull_train_snapshots * a.train_steps,
                                      "seconds": time.perf_counter() - t0_, "heldout_loss_before": l0_,
                                      "heldout_loss_after": l1_}
+                extra["_weights"] = sv.mlp_weights()
+            if weights is not None:
+                sv.set_mlp_weights(weights["W1"], weights["b1"], weights["W2"], weights["b2"])
             sv.solve(d_, p_, tol=1e-8)
             torch.cuda.synchronize()
             t0_ = time.perf_counter()
@@ -834,17 +840,25 @@ def main():
 
         r64, u64, hq = hull_rate()
         rl, ul, _ = hull_rate(train=True, precision="mixed_fp32", outer="pdc", smoother="learned")
+        wts = rl.pop("_weights")
+        # the same trained network inside flexible GMRES (the cycle is nonlinear), and the plain
+        # cycle inside flexible GMRES beside it
+        rgl, ugl, _ = hull_rate(weights=wts, precision="mixed_fp32", outer="fgmres", smoother="learned")
+        rgp, ugp, _ = hull_rate(precision="mixed_fp32", outer="fgmres")
         rp, up, _ = hull_rate(precision="mixed_fp32", outer="pdc")
         rt, ut, _ = hull_rate(precision="mixed_tf32", outer="pdc", inner_imax=a.inner_imax, inner_rtol=a.inner_rtol)
         den = np.abs(u64).max()
-        for r_, u_ in ((rl, ul), (rp, up), (rt, ut)):
+        for r_, u_ in ((rl, ul), (rp, up), (rt, ut), (rgl, ugl), (rgp, ugp)):
             r_["max_rel_diff_vs_fp64_solution"] = float(np.abs(u_ - u64).max() / den)
         hull = {"workload": f"hull tank {n}x{n} base grid, 2+2 layers, rounded-box hull, P={P}",
                 "elements": hq["nelem"], "dof_free": hq["ndof"] - hq["ndirichlet"],
                 "fp64_pcg": r64, "learned_pdc": rl, "same_cycle_without_network": rp, "mixed_tf32_pdc_inner_pcg": rt,
-                "form": "rtol 1e-8; learned: FP64 defect correction around the FP32 V-cycle whose first "
-                        "finest-level post-smoothing sweep is the trained MLP (hidden 256, BF16 weights), kept when "
-                        "it lowers the residual enough, else the Chebyshev sweep"}
+                "learned_fgmres": rgl, "same_cycle_without_network_fgmres": rgp,
+                "form": "rtol 1e-8; learned: FP64 defect correction (learned_pdc) or flexible GMRES(30) "
+                        "(learned_fgmres, the same trained weights) around the FP32 V-cycle whose first "
+                        "finest-level post-smoothing sweep is the trained MLP (hidden 256, BF16 weights, GEMMs on "
+                        "the tensor cores), kept when it lowers the residual enough, else the Chebyshev sweep; "
+                        "training streams snapshots x steps residual/error pairs (10^4 by default), none stored"}
 
     batched = None
     if a.batch_tanks > 0:
