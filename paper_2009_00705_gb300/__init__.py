@@ -29,7 +29,7 @@ EXPORTS = ("sem_default_options", "sem_mesh_nodes2d", "sem_setup", "sem_destroy"
            "sem_dirichlet_nodes", "sem_node_coords", "sem_element_map", "sem_lambda_max", "sem_diagonal",
            "sem_apply", "sem_apply32", "sem_update_eta", "sem_fnpf_rhs", "sem_fnpf_step", "pmg_vcycle", "laplace_solve", "laplace_solve_host", "sem_last_error",
            "sem_cg_csr_noalloc", "sem_mlp_get_weights", "sem_mlp_set_weights", "sem_mlp_forward",
-           "sem_mlp_gradient", "sem_mlp_adam", "sem_learned_sweep", "sem_learned_train", "laplace_solve_batch", "sem_tile_shapes", "sem_tc_kernel", "sem_fp64_rate",
+           "sem_mlp_gradient", "sem_mlp_adam", "sem_learned_sweep", "sem_learned_train", "laplace_solve_batch", "sem_tile_shapes", "sem_tc_kernel", "sem_elem_matrices", "sem_fp64_rate",
            "sem_asm_subdomains", "sem_asm_apply", "sem_asm_apply32")
 
 
@@ -48,7 +48,8 @@ class SemOptions(Structure):
                 ("inner_imax", c_int), ("inner_rtol", c_double), ("debug_barrier_extra", c_int),
                 ("smoother", c_int), ("mlp_hidden", c_int), ("mlp_seed", ctypes.c_ulonglong), ("batch", c_int),
                 ("autotune", c_int), ("learned_tau", c_double), ("surface_ops", c_int), ("batch_mode", c_int),
-                ("asm_overlap", c_int), ("level_pz", c_int * SEM_MAX_LEVELS), ("deterministic", c_int)]
+                ("asm_overlap", c_int), ("level_pz", c_int * SEM_MAX_LEVELS), ("deterministic", c_int),
+                ("elem_matrices", c_int)]
 
 
 class SemStats(Structure):
@@ -100,6 +101,8 @@ def lib():
     L.sem_tile_shapes.restype = c_int
     L.sem_tc_kernel.argtypes = [c_void_p, c_int, POINTER(c_int)]
     L.sem_tc_kernel.restype = c_int
+    L.sem_elem_matrices.argtypes = [c_void_p, c_int, POINTER(c_int)]
+    L.sem_elem_matrices.restype = c_int
     L.sem_fp64_rate.argtypes = [POINTER(c_double)]
     L.sem_fp64_rate.restype = c_int
     L.sem_apply.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_void_p]
@@ -518,6 +521,11 @@ class Solver:
 
     def tc_kernel(self, level=0):
         return sem_tc_kernel(self.h, level)
+
+    def elem_matrices(self, level=0):
+        on = c_int(0)
+        _check(lib().sem_elem_matrices(self.h, level, byref(on)))
+        return bool(on.value)
 
     def apply(self, level, x, y, stream=None):
         sem_apply(self.h, level, x, y, stream)

@@ -500,6 +500,23 @@ sem_status asm_blocks(Level& L, const T* G, int* dflag) {
 
 }  // namespace
 
+// FP64 element matrices of a 3D level, [E][Np][Np] (symmetric), for the element-matrix apply.
+cudaError_t element_matrices64(const Level& L, double* Ae, cudaStream_t s) {
+    const std::vector<double> g = full_gradients<double>(L);
+    double* dg = nullptr;
+    cudaError_t e = to_device(&dg, g);
+    if (e == cudaSuccess) {
+        const int ntile = (L.Np + 63) / 64;
+        const long long work = (long long)L.E * ntile * ntile;
+        const int grid = (int)std::min<long long>(work, (long long)device_sms() * 8);
+        k_elem_matrix<double><<<grid, kAsmThreads, 0, s>>>(L.E, L.dim, L.Np, L.Nq, L.G, dg, Ae);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(dg);
+    return e;
+}
+
 // Largest subdomain (nodes) the inversion kernel stages in shared memory.
 int asm_max_block(bool fp64) { return fp64 ? (200 * 1024) / (2 * 8 * 8) : (200 * 1024) / (2 * 8 * 4); }
 

@@ -70,6 +70,7 @@ struct Level {
     int* dss_ptr = nullptr;                // [N + 1] segment of each node in dss_slot
     int* dss_slot = nullptr;               // slots e * Np + l of the free nodes, ascending (e, l) per node
     double* ye64 = nullptr;                // [E][Np] element results of the FP64 apply / restriction / diagonal
+    double* Ae64 = nullptr;                // [E][Np][Np] FP64 element matrices (element-matrix apply) or null
     int* csr_eptr = nullptr;               // coarse level: CSR entry -> element entries (e Np + i) Np + j, ascending
     int* csr_eidx = nullptr;
     double* csr_ev = nullptr;              // [E][Np][Np] element-matrix entries before their fixed-order sums
@@ -227,6 +228,8 @@ inline bool level_tc(const Level& L) { return L.dim == 3 && L.pz == L.p && prism
 // apply_prism.cu: (triangle order, vertical order) pairs the prism apply is compiled for
 bool prism_pair_supported(int p, int pz);
 cudaError_t build_g16(Level& L, cudaStream_t s);
+// schwarz.cu: FP64 element matrices [E][Np][Np] of a 3D level (synchronous)
+cudaError_t element_matrices64(const Level& L, double* Ae, cudaStream_t s);
 // kernels.cu: y[g] = sum of the element results ye over node g's slots (fixed order); masked:
 // 0 at the Dirichlet nodes
 cudaError_t dss_gather64(const Level& L, const double* ye, double* y, const int* skip, cudaStream_t s,

@@ -358,6 +358,7 @@ sem_status geometry_levels(sem_handle* h, int first, int last, bool flat) {
         CK(e);
         CK(build_g16(L, 0));
         CK(build_g16_t6(L, 0));
+        if (L.Ae64 != nullptr) CK(element_matrices64(L, L.Ae64, 0));
     }
     cudaFree(dvtri);
     cudaFree(detaP);

@@ -652,9 +652,36 @@ sem_status build_dss(Level& L) {
     return SEM_OK;
 }
 
+// Device storage of the FP64 element matrices (sem_options.elem_matrices): every level of an
+// FP64 handle but the coarsest, the finest of a mixed-precision one; in auto mode only when
+// they take at most a quarter of the free device memory and 48 GB.
+sem_status alloc_element_matrices(sem_handle* h) {
+    const int nl = (int)h->lv.size();
+    const int last = h->opts.precision == SEM_PREC_FP64 ? nl - 1 : std::min(1, nl - 1);
+    size_t bytes = 0;
+    for (int li = 0; li < last; ++li) bytes += sizeof(double) * (size_t)h->lv[li].E * h->lv[li].Np * h->lv[li].Np;
+    if (bytes == 0) return SEM_OK;
+    if (h->opts.elem_matrices < 0) {
+        size_t fr = 0, tot = 0;
+        CKS(cudaMemGetInfo(&fr, &tot));
+        if (bytes > fr / 4 || bytes > (size_t)48 << 30) return SEM_OK;      // sum factorisation
+    }
+    for (int li = 0; li < last; ++li) {
+        Level& L = h->lv[li];
+        void* p = nullptr;
+        const cudaError_t e = cudaMalloc(&p, sizeof(double) * (size_t)L.E * L.Np * L.Np);
+        if (e != cudaSuccess) {
+            set_error("element matrices: " + std::string(cudaGetErrorString(e)));
+            return SEM_ENOMEM;
+        }
+        L.Ae64 = static_cast<double*>(p);
+    }
+    return SEM_OK;
+}
+
 void free_level(Level& L) {
     void* ptrs[] = {L.map, L.G, L.G32, L.G16, L.G16T, L.lift_elems, L.dinv, L.dinv32, L.dir, L.ref64.m, L.ref32.m, L.It64, L.Iz64, L.It32, L.Iz32, L.gref,
-                    L.csr_rowptr, L.csr_col, L.csr_val, L.csr_slot, L.dss_ptr, L.dss_slot, L.ye64, L.csr_eptr, L.csr_eidx, L.csr_ev,
+                    L.csr_rowptr, L.csr_col, L.csr_val, L.csr_slot, L.dss_ptr, L.dss_slot, L.ye64, L.csr_eptr, L.csr_eidx, L.csr_ev, L.Ae64,
                     L.owner, L.wmult, L.wmult32, L.u, L.f, L.y, L.d, L.u32, L.f32, L.y32, L.d32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -1000,6 +1027,7 @@ void sem_default_options(sem_options* o, int P) {
     o->surface_ops = 0;
     o->asm_overlap = 1;
     o->deterministic = 0;
+    o->elem_matrices = -1;
 }
 
 sem_status sem_mesh_nodes2d(const sem_mesh* m, int p, long long* n2, double* xy) {
@@ -1082,7 +1110,8 @@ sem_status sem_setup(const sem_mesh* m, int P, const sem_options* opts, sem_hand
             if (st != SEM_OK) break;
             st = build_dss(L);
         }
-    if (st == SEM_OK) st = build_geometry(h, m);
+    if (st == SEM_OK && o.elem_matrices != 0 && m->dim == 3) st = alloc_element_matrices(h);
+    if (st == SEM_OK) st = build_geometry(h, m);       // fills the element matrices too
     if (st == SEM_OK) st = build_diagonals(h);
     if (st == SEM_OK) st = build_transfers(h);
     if (st == SEM_OK) st = build_coarse_gradients(h);
@@ -1194,6 +1223,13 @@ sem_status sem_tile_shapes(const sem_handle* h, int level, int* elems_fp64, int*
     const Level& L = h->lv[level];
     if (elems_fp64) *elems_fp64 = L.dim == 3 ? prism_tile_elements(L.p, L.tile64) : 1;
     if (elems_fp32) *elems_fp32 = L.dim == 3 ? prism_tile_elements(L.p, L.tile32) : 1;
+    return SEM_OK;
+}
+
+sem_status sem_elem_matrices(const sem_handle* h, int level, int* on) {
+    CKST(check_level(h, level));
+    if (!on) { set_error("on is NULL"); return SEM_EINVAL; }
+    *on = h->lv[level].Ae64 != nullptr ? 1 : 0;
     return SEM_OK;
 }
 

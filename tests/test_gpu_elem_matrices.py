@@ -1,0 +1,96 @@
+"""The FP64 apply from precomputed element matrices (sem_options.elem_matrices) against
+the sum-factorised contraction and the oracle's assembled matrix, on every level of a
+sigma-prism box and of a hull tank (curved base edges), with the lifting apply and after a
+surface update (the matrices are recomputed with the geometry); and the FP64 solves of
+both forms against the oracle's direct solution.  Tolerance: both forms are FP64 sums of
+the same quadrature, 1e-12 of max|y| as for the apply parity elsewhere."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import solvers as S  # noqa: E402
+from oracle.assemble import Problem  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def sem():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2009_00705_gb300 as pkg
+    from paper_2009_00705_gb300 import build as B
+    B.build()
+    return pkg
+
+
+@pytest.mark.parametrize("mesh_fn,levels", [(lambda: W.config_box3d(4, 2), [6, 3, 1]),
+                                            (lambda: W.hull_tank(8), [4, 2, 1])])
+def test_element_matrix_apply_on_every_level(sem, mesh_fn, levels):
+    mesh = mesh_fn()
+    prob = Problem(mesh, levels)
+    on = sem.Solver(mesh, levels[0], eta_nodal=prob.eta_nodal, levels=levels, elem_matrices=1)
+    off = sem.Solver(mesh, levels[0], eta_nodal=prob.eta_nodal, levels=levels, elem_matrices=0)
+    try:
+        assert on.elem_matrices(0) and not off.elem_matrices(0)
+        for li in range(len(levels) - 1):
+            assert on.elem_matrices(li)
+            lev = prob.levels[li]
+            x = W.random_vector(lev.N, seed=90 + li)
+            xd = torch.tensor(x, device="cuda")
+            ya, yb = (torch.empty(lev.N, dtype=torch.float64, device="cuda") for _ in range(2))
+            on.apply(li, xd, ya)
+            off.apply(li, xd, yb)
+            torch.cuda.synchronize()
+            ref = prob.masked_apply(li, x)
+            scale = np.abs(ref).max()
+            assert np.abs(ya.cpu().numpy() - ref).max() <= 1e-12 * scale
+            assert np.abs(ya.cpu().numpy() - yb.cpu().numpy()).max() <= 1e-12 * scale
+    finally:
+        on.close()
+        off.close()
+
+
+@pytest.mark.parametrize("elem", [1, 0])
+def test_fp64_solve_of_both_apply_forms_matches_direct_solution(sem, elem):
+    mesh = W.config_box3d(4, 2)
+    levels = [6, 3, 1]
+    prob = Problem(mesh, levels)
+    lev = prob.levels[0]
+    C = prob.coords(0)
+    phiD = W.potential3d(*C[lev.dirichlet].T)
+    ref = S.solve_laplace_direct(prob, phiD)
+    s = sem.Solver(mesh, 6, eta_nodal=prob.eta_nodal, levels=levels, elem_matrices=elem, coarse_rtol=1e-14)
+    try:
+        phi = torch.zeros(lev.N, dtype=torch.float64, device="cuda")
+        st = s.solve(torch.tensor(phiD, device="cuda"), phi, tol=1e-13)
+        torch.cuda.synchronize()
+        assert st["status"] == 0
+        assert np.abs(phi.cpu().numpy() - ref).max() <= 1e-10 * np.abs(ref).max()
+    finally:
+        s.close()
+
+
+def test_element_matrices_follow_a_surface_update(sem):
+    # strategy III rebuilds every level's geometry: the element matrices must match the new
+    # surface, i.e. the apply must equal a fresh handle's on the new eta
+    mesh = W.config_box3d(4, 2)
+    levels = [6, 3, 1]
+    s = sem.Solver(mesh, 6, levels=levels, elem_matrices=1)
+    xy = sem.sem_mesh_nodes2d(mesh, 6)
+    eta = 0.05 * np.cos(xy[:, 0]) * np.sin(2 * xy[:, 1])
+    fresh = sem.Solver(mesh, 6, eta_nodal=eta, levels=levels, elem_matrices=1)
+    try:
+        s.update_eta(eta, "all")
+        N = s.query(0)["ndof"]
+        x = torch.tensor(W.random_vector(N, seed=97), device="cuda")
+        ya, yb = torch.empty_like(x), torch.empty_like(x)
+        s.apply(0, x, ya)
+        fresh.apply(0, x, yb)
+        torch.cuda.synchronize()
+        assert (ya - yb).abs().max().item() <= 1e-12 * yb.abs().max().item()
+    finally:
+        s.close()
+        fresh.close()
