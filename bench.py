@@ -37,12 +37,13 @@ UNIT = "DOF/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_NOMINAL_TFLOPS = 1.25          # GB300 FP64 (profiling recipe's nominal table)
 FALLBACK_HBM_GBS = 6800.0
-# ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the FP64 prism
-# apply, per launch (mean of four launches), scaled from a capture on the 48x48x4-prism
-# box (18,432 elements) to the 32,768-element benchmark mesh by element count; reported
-# as null once apply_prism.cu differs from the captured source.
-TRAFFIC = {("apply_fp64", 6): (350.860352e6 + 12.227136e6) * 32768 / 18432}
-TRAFFIC_SRC_SHA = "a51bb5326e701863"
+# ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the FP64 element-matrix
+# apply, per launch, from a capture on the 24x24x4-prism box (4,608 elements) scaled to the
+# 32,768-element benchmark mesh by element count (the traffic is the element matrices, in
+# proportion); reported as null once apply_prism.cu differs from the captured source or the
+# handle runs the sum-factorised form.
+TRAFFIC = {("elem64", 6): (1428.006e6 + 4.251648e6) * 32768 / 4608}
+TRAFFIC_SRC_SHA = "69b2f03361d0470d"
 
 
 def workload_name(n, nl, P):
@@ -402,7 +403,7 @@ def main():
     achieved_tf = flops / avg_apply_s / 1e12
     # bytes one apply must move: x in and y out, the map, and the element matrices or the factors
     hbytes = (2 * N * 8 + E * Np_ * 4 + E * Np_ * Np_ * 8) if elem_mat else apply_bytes(P, E, N)
-    traffic = TRAFFIC.get(("apply_fp64", P)) if TRAFFIC_SRC_SHA == kernels_sha() else None
+    traffic = TRAFFIC.get(("elem64", P)) if (elem_mat and TRAFFIC_SRC_SHA == kernels_sha()) else None
     roofline = {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
                 "frac": achieved_tf / fp64_peak, "traffic": traffic,
                 "kernel": (f"k_apply_elem64 (finest-level FP64 operator apply from precomputed element matrices, "
