@@ -71,6 +71,30 @@ def apply_bytes(P, E, N, word=8, gword=None):
     return 2 * N * word + E * 6 * QT * QZ * gword + E * NT * NZ * 4
 
 
+def df_tile_pairs(Np):
+    """(hi, lo) float pairs per element in the double-FP32 element-matrix layout: NB row blocks
+    of T rows, NB (NB + 1) / 2 tiles of T x S pairs (S odd), each padded to an even count."""
+    nb = (Np + 31) // 32
+    t = (Np + nb - 1) // nb
+    st = t if t & 1 else t + 1
+    return nb * (nb + 1) // 2 * ((t * st + 1) // 2 * 2)
+
+
+def fp64_apply_cost(kind, P, E, N):
+    """(flops, algorithmic bytes, kernel) of one finest-level FP64 apply in the form a handle runs:
+    0 sum-factorised, 1 FP64 element matrices (2 Np^2 flops, Np^2 doubles per element),
+    2 double-FP32 element matrices (the same product, the packed upper block triangle)."""
+    Np_ = (P + 1) * (P + 1) * (P + 2) // 2
+    if kind == 1:
+        return (2 * Np_ * Np_ * E, 2 * N * 8 + E * Np_ * 4 + E * Np_ * Np_ * 8,
+                f"k_apply_elem64 (FP64 element matrices, {Np_}x{Np_} per element, streamed)")
+    if kind == 2:
+        return (2 * Np_ * Np_ * E, 2 * N * 8 + E * Np_ * 4 + E * df_tile_pairs(Np_) * 8,
+                f"k_apply_elem_df (double-FP32 element matrices, upper block triangle of {Np_}x{Np_}, streamed)")
+    return (apply_flops_per_elem(P) * E, apply_bytes(P, E, N),
+            f"k_apply_prism<P={P}, double> (sum-factorised)")
+
+
 def replica_barrier(world):
     """Barrier of the replica ranks (no-op on one GPU)."""
     if world > 1:
@@ -233,7 +257,7 @@ def run_ncu_case(a):
     mesh = W.config_box3d(a.ncu_case, a.nlayers)
     xy = sem.sem_mesh_nodes2d(mesh, P)
     s = sem.Solver(mesh, P, eta_nodal=mesh.eta(xy[:, 0], xy[:, 1]), levels=levels_for(P), precision="mixed_tf32",
-                   outer="pdc", inner_imax=2, inner_rtol=1e-4, imax=1)
+                   outer="pdc", inner_imax=2, inner_rtol=1e-4, imax=1, elem_matrices=a.ncu_elem)
     C = s.coords(0)
     phiD = torch.tensor(W.potential3d(*C[s.dirichlet_nodes(0)].T), device="cuda")
     phi = torch.empty(s.query(0)["ndof"], dtype=torch.float64, device="cuda")
@@ -297,6 +321,7 @@ def main():
     ap.add_argument("--no-aniso", action="store_true")
     ap.add_argument("--no-hull", action="store_true")
     ap.add_argument("--no-deterministic", action="store_true")
+    ap.add_argument("--no-df32", action="store_true")
     ap.add_argument("--no-config3-256", action="store_true",
                     help="skip the 256x256x6 P=6 box (85 M free DOF; FP64 and MIXED_TF32 solves, about 2 minutes)")
     ap.add_argument("--batch-tanks", type=int, default=256,
@@ -311,6 +336,8 @@ def main():
     ap.add_argument("--ncu-case", type=int, default=0, metavar="N",
                     help="profiler driver: one short MIXED_TF32 solve on an N x N x 4 P=6 box (FP64, FP32 and "
                          "tensor-core applies, transfers and the coarse CG all launch); prints stats only")
+    ap.add_argument("--ncu-elem", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="with --ncu-case: form of the FP64 residual apply (elem_matrices; -1 the default)")
     ap.add_argument("--ncu-tcgen05", action="store_true",
                     help="with --ncu-case: also launch the tcgen05 order-6 apply three times after the solve")
     ap.add_argument("--ncu-solve", default="", choices=["", "fp64", "mixed_fp32", "mixed_tf32", "asm"],
@@ -392,23 +419,17 @@ def main():
     launches = sum(s["kernel_launches"] for s in stats)
     avg_apply_s = apply_ms / apply_n / 1000.0
     elem_mat = solver.elem_matrices(0)
-    Np_ = (P + 1) * (P + 1) * (P + 2) // 2
-    # algorithmic flops of the apply form the handle runs: 2 Np^2 per element with precomputed
-    # element matrices, the sum-factorised count otherwise
-    flops = (2 * Np_ * Np_ if elem_mat else apply_flops_per_elem(P)) * E
+    # algorithmic flops and bytes of the apply form the handle runs
+    flops, hbytes, kname = fp64_apply_cost(elem_mat, P, E, N)
     fp64_peak = FP64_NOMINAL_TFLOPS
     fp64_probe = max(sem.sem_fp64_rate() for _ in range(3))
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     hbm_peak = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
     achieved_tf = flops / avg_apply_s / 1e12
-    # bytes one apply must move: x in and y out, the map, and the element matrices or the factors
-    hbytes = (2 * N * 8 + E * Np_ * 4 + E * Np_ * Np_ * 8) if elem_mat else apply_bytes(P, E, N)
-    traffic = TRAFFIC.get(("elem64", P)) if (elem_mat and TRAFFIC_SRC_SHA == kernels_sha()) else None
+    traffic = TRAFFIC.get(("elem64", P)) if (elem_mat == 1 and TRAFFIC_SRC_SHA == kernels_sha()) else None
     roofline = {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
                 "frac": achieved_tf / fp64_peak, "traffic": traffic,
-                "kernel": (f"k_apply_elem64 (finest-level FP64 operator apply from precomputed element matrices, "
-                           f"{Np_}x{Np_} per element, streamed)" if elem_mat else
-                           f"k_apply_prism<P={P}, double> (finest-level FP64 operator apply, sum-factorised)"),
+                "kernel": "finest-level FP64 operator apply: " + kname,
                 "flops_per_launch": flops, "avg_launch_ms": avg_apply_s * 1e3, "launches": apply_n,
                 "peak_source": f"nominal GB300 FP64 1.25 TFLOP/s (profiling recipe); probed on this GPU: "
                                f"{fp64_probe:.3f} TFLOP/s (sixteen independent FMA chains per thread on every SM, "
@@ -453,6 +474,35 @@ def main():
            "d2h_bytes_per_step": int(N * 8)}
     phi64 = phi.cpu().numpy()
 
+    def fp64_view(ms_total, launches, kind):
+        """Live event time of the finest-level FP64 applies of a handle against the HBM roofline."""
+        if not launches:
+            return None
+        avg_s = ms_total / launches / 1000.0
+        fl, byts, kn = fp64_apply_cost(kind, P, E, N)
+        return {"kernel": kn, "avg_launch_ms": avg_s * 1e3, "launches": launches, "algorithmic_bytes": byts,
+                "achieved_gbs": byts / avg_s / 1e9, "peak_gbs": hbm_peak, "frac_of_hbm": byts / avg_s / 1e9 / hbm_peak,
+                "achieved_tflops": fl / avg_s / 1e12}
+
+    # the FP64 PCG solve with its FP64 applies from the double-FP32 element matrices
+    # (compensated FP32 arithmetic on the FP32 pipe, the packed upper block triangle streamed)
+    df32 = None
+    if not a.no_df32:
+        fsolver = sem.Solver(mesh, P, eta_nodal=eta, levels=levels_for(P), profile=1, elem_matrices=2)
+        phi_f = torch.empty(N, dtype=torch.float64, device="cuda")
+        ms_f, st_f = timed(fsolver, a.steps, a.warmup, phi_f)
+        ms_f = max_over_ranks(ms_f)
+        df32 = {"value": dof * a.steps * world / (ms_f / 1000.0), "unit": UNIT, "ms_per_step": ms_f / a.steps,
+                "iters": st_f[-1]["iters"], "res_final_rel": st_f[-1]["res_final"] / st_f[-1]["fnorm"],
+                "max_rel_diff_vs_fp64_solution": float((phi_f - phi).abs().max().item() / phi.abs().max().item()),
+                "apply": fp64_view(sum(x["apply_ms"] for x in st_f), sum(x["apply_launches"] for x in st_f),
+                                   fsolver.elem_matrices(0)),
+                "form": "FP64 PCG + FP64 V-cycle as the headline; every FP64 apply but the coarsest multiplies "
+                        "by double-FP32 element matrices (hi/lo float pairs of the upper block triangle, "
+                        "TwoProduct/TwoSum in FP32, FP64 sums per 28-column block): a row's error within a few "
+                        "1e-13 of sum |A_ij x_j|"}
+        fsolver.close()
+
     def apply_view(ms_total, launches, word, gword=None):
         """Live event time of the finest-level applies against the HBM roofline."""
         if not launches:
@@ -487,13 +537,16 @@ def main():
                    "inner_iters": st_m[-1]["inner_iters"], "res_final_rel": st_m[-1]["res_final"] / st_m[-1]["fnorm"],
                    "speedup_vs_fp64": (dof * a.steps * world / (ms_m / 1000.0)) / value,
                    "max_rel_diff_vs_fp64_solution": err,
-                   "outer": "FP64 defect correction (Algorithm 2) with FP64 residual",
+                   "outer": "FP64 defect correction (Algorithm 2) with FP64 residual" + (
+                       " (its apply from double-FP32 element matrices: compensated FP32 products, FP64 sums "
+                       "per block)" if ms_solver.elem_matrices(0) == 2 else ""),
                    "inner": f"FP32 PCG to {a.inner_rtol:g} (<= {a.inner_imax} its) preconditioned by the "
                             f"single-precision V-cycle; FP64 coarse CG to {a.coarse_rtol:g}",
                    "smoothing_operator": smooth,
                    "apply_fp32": apply_view(sum(x["apply32_ms"] for x in st_m),
                                             sum(x["apply32_launches"] for x in st_m), 4),
-                   "apply_fp64": apply_view(sum(x["apply_ms"] for x in st_m), sum(x["apply_launches"] for x in st_m), 8)}
+                   "apply_fp64": fp64_view(sum(x["apply_ms"] for x in st_m), sum(x["apply_launches"] for x in st_m),
+                                           ms_solver.elem_matrices(0))}
             if prec == "mixed_tf32":
                 obj["apply_tf32_tensor_cores"] = apply_view(sum(x["apply_tc_ms"] for x in st_m),
                                                             sum(x["apply_tc_launches"] for x in st_m), 4, gword=2)
@@ -992,7 +1045,7 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "mixed_fp32": mixed, "mixed_tf32": mixed_tc, "learned": learned, "batched": batched,
-                "update_eta": update, "other_configs": configs, "config3_256": big, "fp64_deterministic": det,
+                "update_eta": update, "other_configs": configs, "config3_256": big, "fp64_deterministic": det, "fp64_df32": df32,
                 "fnpf_time_stepping": fnpf, "asm": asm, "anisotropic": aniso, "hull": hull}
         print(json.dumps(line), flush=True)
     solver.close()

@@ -67,6 +67,9 @@ typedef enum { SEM_PREC_FP64 = 0, SEM_PREC_MIXED_FP32 = 1, SEM_PREC_MIXED_TF32 =
  * symmetric V-cycle).  The blocks are inverted at setup and held densely in the V-cycle's
  * precision (FP64, or FP32 in the mixed precisions). */
 typedef enum { SEM_SMOOTH_CHEBYSHEV = 0, SEM_SMOOTH_LEARNED = 1, SEM_SMOOTH_ASM = 2 } sem_smoother;
+/* Forms of the FP64 operator apply (sem_options.elem_matrices): sum-factorised contraction,
+ * FP64 element matrices, or double-FP32 element matrices (upper block triangle). */
+typedef enum { SEM_ELEM_OFF = 0, SEM_ELEM_FP64 = 1, SEM_ELEM_DF32 = 2 } sem_elem_form;
 
 /* Mesh description (host memory, read during sem_setup only).
  * dim 2: ntri straight triangles in the (x, z) plane; vxy holds (x, z).
@@ -184,13 +187,20 @@ typedef struct {
                                    map in a fixed order (no atomics), so FP64 solves are bit-reproducible run
                                    to run; 0 (default) = atomic summation.  The single-precision applies
                                    keep atomic summation */
-    int elem_matrices;          /* 3D meshes: the FP64 operator applies multiply by precomputed FP64
-                                   element matrices A_e (2 Np^2 flops per element, 42 % fewer than the
-                                   sum-factorised contraction at P = 6; Np^2 doubles per element held on
-                                   the device and recomputed when eta changes) on every level of an FP64
-                                   handle but the coarsest, and on the finest level of a mixed-precision
-                                   one: 1 = on, 0 = off (sum factorisation), -1 (default) = on when they
-                                   take at most a quarter of the free device memory and 48 GB */
+    int elem_matrices;          /* 3D meshes: the FP64 operator applies multiply by precomputed element
+                                   matrices A_e (2 Np^2 flops per element, 42 % fewer than the
+                                   sum-factorised contraction at P = 6; held on the device and recomputed
+                                   when eta changes) on every level of an FP64 handle but the coarsest,
+                                   and on the finest level (the residual) of a mixed-precision one.
+                                   SEM_ELEM_FP64 (1): FP64 matrices, FP64 arithmetic (Np^2 doubles per
+                                   element).  SEM_ELEM_DF32 (2): the upper block triangle as double-FP32
+                                   pairs, multiplied in compensated FP32 arithmetic (TwoProduct/TwoSum)
+                                   with FP64 sums per block: a row's error stays within a few 1e-13 of
+                                   sum_j |A_ij x_j| (FP64: about 1e-15), on the FP32 pipe (182 KB per
+                                   element at P = 6 against 307 KB).  SEM_ELEM_OFF (0): sum
+                                   factorisation.  -1 (default): SEM_ELEM_FP64 for FP64 handles and
+                                   SEM_ELEM_DF32 for mixed-precision ones, when they take at most a
+                                   quarter of the free device memory and 48 GB, else off */
 } sem_options;
 
 typedef struct {
@@ -262,9 +272,10 @@ sem_status sem_tile_shapes(const sem_handle* h, int level, int* elems_fp64, int*
  * tensor-core level), 1 the warp-level MMA kernel, 2 the tcgen05 kernel (order 6; chosen at
  * setup by timing both when autotune is set, else the tcgen05 kernel). */
 sem_status sem_tc_kernel(const sem_handle* h, int level, int* kind);
-/* 1 when a level's FP64 applies multiply by precomputed element matrices (sem_options.elem_matrices),
- * 0 when they use the sum-factorised contraction. */
-sem_status sem_elem_matrices(const sem_handle* h, int level, int* on);
+/* The form of a level's FP64 applies (sem_options.elem_matrices): SEM_ELEM_FP64 or SEM_ELEM_DF32
+ * when they multiply by precomputed element matrices, SEM_ELEM_OFF for the sum-factorised
+ * contraction. */
+sem_status sem_elem_matrices(const sem_handle* h, int level, int* kind);
 /* The assembled diagonal of A at a level (all nodes), host copy. */
 sem_status sem_diagonal(const sem_handle* h, int level, double* diag_host);
 

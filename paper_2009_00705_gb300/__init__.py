@@ -523,9 +523,11 @@ class Solver:
         return sem_tc_kernel(self.h, level)
 
     def elem_matrices(self, level=0):
-        on = c_int(0)
-        _check(lib().sem_elem_matrices(self.h, level, byref(on)))
-        return bool(on.value)
+        """Form of the level's FP64 applies: 0 sum-factorised, 1 FP64 element matrices,
+        2 double-FP32 element matrices."""
+        kind = c_int(0)
+        _check(lib().sem_elem_matrices(self.h, level, byref(kind)))
+        return kind.value
 
     def apply(self, level, x, y, stream=None):
         sem_apply(self.h, level, x, y, stream)

@@ -339,6 +339,7 @@ bool prism_pair_supported(int p, int pz) {
 
 cudaError_t launch_apply_prism64(const Level& L, const double* x, double* y, bool lift, const int* skip, int variant,
                                  cudaStream_t s) {
+    if (L.Adf != nullptr) return apply_elem_df(L, x, y, lift, skip, s);
     if (L.Ae64 != nullptr) return apply_elem64(L, x, y, lift, skip, s);
     // deterministic handles: element results, then the per-node sums in a fixed order
     double* ye = L.ye64;

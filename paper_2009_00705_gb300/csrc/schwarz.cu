@@ -498,6 +498,31 @@ sem_status asm_blocks(Level& L, const T* G, int* dflag) {
     return SEM_OK;
 }
 
+
+// The double-FP32 block layout of a chunk of element matrices Ae [n][Np][Np]: tile t of
+// element e (row block I, column block J, in the order of df_tiles_of) holds rows I T + r,
+// columns J T + c as (hi, lo) = (fl32(a), fl32(a - hi)), zero in the padding.
+__global__ void k_pack_df(long long n, int Np, int T, int NB, int S, int TS, const double* __restrict__ Ae,
+                          float2* __restrict__ out) {
+    const int ntiles = NB * (NB + 1) / 2;
+    const long long total = n * ntiles * TS;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long e = idx / ((long long)ntiles * TS);
+        const int rem = (int)(idx - e * ntiles * TS);
+        const int t = rem / TS, q = rem - t * TS;
+        int I = 0, k = t;
+        while (k >= df_tiles_of(I, NB)) k -= df_tiles_of(I++, NB);
+        const int J = (I + k) % NB;
+        const int r = q / S, c = q - r * S;
+        const int row = I * T + r, col = J * T + c;
+        double v = 0.0;
+        if (r < T && c < T && row < Np && col < Np) v = Ae[((size_t)e * Np + row) * Np + col];
+        const float hi = __double2float_rn(v);
+        out[idx] = make_float2(hi, __double2float_rn(v - (double)hi));
+    }
+}
+
 }  // namespace
 
 // FP64 element matrices of a 3D level, [E][Np][Np] (symmetric), for the element-matrix apply.
@@ -513,6 +538,35 @@ cudaError_t element_matrices64(const Level& L, double* Ae, cudaStream_t s) {
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(dg);
+    return e;
+}
+
+cudaError_t element_matrices_df(const Level& L, float2* Adf, cudaStream_t s) {
+    const std::vector<double> g = full_gradients<double>(L);
+    const int Np = L.Np, Nq = L.Nq, nc = L.dim == 3 ? 6 : 3;
+    const int ntiles = L.df_NB * (L.df_NB + 1) / 2;
+    // FP64 matrices of up to 4096 elements at a time (1.2 GB at order 6), then packed
+    const long long chunk = std::min<long long>(L.E, 4096);
+    double *dg = nullptr, *Ae = nullptr;
+    cudaError_t e = to_device(&dg, g);
+    if (e == cudaSuccess) e = cudaMalloc(&Ae, sizeof(double) * (size_t)chunk * Np * Np);
+    const int ntile = (Np + 63) / 64;
+    for (long long e0 = 0; e == cudaSuccess && e0 < L.E; e0 += chunk) {
+        const long long n = std::min<long long>(chunk, L.E - e0);
+        const int grid = (int)std::min<long long>(n * ntile * ntile, (long long)device_sms() * 8);
+        k_elem_matrix<double><<<grid, kAsmThreads, 0, s>>>((int)n, L.dim, Np, Nq, L.G + (size_t)e0 * nc * Nq, dg, Ae);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) {
+            const long long total = n * ntiles * L.df_TS;
+            const int pg = (int)std::min<long long>((total + 255) / 256, (long long)device_sms() * 16);
+            k_pack_df<<<pg, 256, 0, s>>>(n, Np, L.df_T, L.df_NB, L.df_S, L.df_TS, Ae,
+                                         Adf + (size_t)e0 * ntiles * L.df_TS);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(Ae);
     cudaFree(dg);
     return e;
 }

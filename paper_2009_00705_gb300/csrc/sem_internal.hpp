@@ -71,6 +71,10 @@ struct Level {
     int* dss_slot = nullptr;               // slots e * Np + l of the free nodes, ascending (e, l) per node
     double* ye64 = nullptr;                // [E][Np] element results of the FP64 apply / restriction / diagonal
     double* Ae64 = nullptr;                // [E][Np][Np] FP64 element matrices (element-matrix apply) or null
+    float2* Adf = nullptr;                 // [E][tiles][TS] upper block triangle of the element matrices as
+                                           // (hi, lo) float pairs (double-FP32 apply) or null
+    int df_T = 0, df_NB = 0, df_S = 0, df_TS = 0;   // its block layout (df_layout)
+    int* df_err = nullptr;                 // set when a tile copy of that apply misses its wait bound
     int* csr_eptr = nullptr;               // coarse level: CSR entry -> element entries (e Np + i) Np + j, ascending
     int* csr_eidx = nullptr;
     double* csr_ev = nullptr;              // [E][Np][Np] element-matrix entries before their fixed-order sums
@@ -186,6 +190,7 @@ struct sem_handle {
     double asm_ms = 0.0;
     long long asm_launches = 0;
     double lift_ms = 0.0;
+    size_t auto_elem_bytes = 0;     // element matrices allocated by the auto rule (process-wide budget)
     long long lift_launches = 0;
     long long fine_applies = 0;
     long long launches = 0;        // kernels launched since the counter was reset
@@ -230,6 +235,18 @@ bool prism_pair_supported(int p, int pz);
 cudaError_t build_g16(Level& L, cudaStream_t s);
 // schwarz.cu: FP64 element matrices [E][Np][Np] of a 3D level (synchronous)
 cudaError_t element_matrices64(const Level& L, double* Ae, cudaStream_t s);
+// apply_elem_df.cu: the FP64-accurate apply from the double-FP32 element matrices (L.Adf), and
+// their block layout for Np nodes per element
+cudaError_t apply_elem_df(const Level& L, const double* x, double* y, bool lift, const int* skip, cudaStream_t s);
+void df_layout(int Np, int* T, int* NB, int* S, int* TS);
+// tiles (w, w + d mod NB) of row block w in that layout: d = 0 .. NB/2, the last difference of an
+// even NB only for w < NB/2, so every unordered block pair appears once
+#if defined(__CUDACC__)
+__host__ __device__
+#endif
+inline int df_tiles_of(int w, int NB) { return (NB & 1) || w < NB / 2 ? NB / 2 + 1 : NB / 2; }
+// schwarz.cu: the double-FP32 element matrices of a 3D level in that layout (synchronous)
+cudaError_t element_matrices_df(const Level& L, float2* Adf, cudaStream_t s);
 // kernels.cu: y[g] = sum of the element results ye over node g's slots (fixed order); masked:
 // 0 at the Dirichlet nodes
 cudaError_t dss_gather64(const Level& L, const double* ye, double* y, const int* skip, cudaStream_t s,

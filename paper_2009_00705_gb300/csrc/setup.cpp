@@ -359,6 +359,7 @@ sem_status geometry_levels(sem_handle* h, int first, int last, bool flat) {
         CK(build_g16(L, 0));
         CK(build_g16_t6(L, 0));
         if (L.Ae64 != nullptr) CK(element_matrices64(L, L.Ae64, 0));
+        if (L.Adf != nullptr) CK(element_matrices_df(L, L.Adf, 0));
     }
     cudaFree(dvtri);
     cudaFree(detaP);
@@ -580,6 +581,7 @@ sem_status build_workspace(sem_handle* h) {
     CK(dalloc(&sc.flags, kFlagCount));
     CK(cudaMemset(sc.flags, 0, kFlagCount * sizeof(int)));
     h->net.err = sc.flags + F_TC_ERR;          // the network's tensor-core GEMMs report on the same flag
+    for (Level& L : h->lv) L.df_err = sc.flags + F_TC_ERR;     // and the double-FP32 apply's tile copies
     CK(cudaMallocHost((void**)&sc.hpinned, 128 * sizeof(double)));
     CK(cudaMallocHost((void**)&sc.hflags, kFlagCount * sizeof(int)));
     for (double** v : {&h->r, &h->z, &h->p, &h->q, &h->x, &h->fr}) CK(dalloc(v, N));

@@ -652,36 +652,54 @@ sem_status build_dss(Level& L) {
     return SEM_OK;
 }
 
-// Device storage of the FP64 element matrices (sem_options.elem_matrices): every level of an
-// FP64 handle but the coarsest, the finest of a mixed-precision one; in auto mode only when
-// they take at most a quarter of the free device memory and 48 GB.
+// Element matrices held by all live handles that took them by the auto rule.
+std::atomic<size_t> g_auto_elem_bytes{0};
+constexpr size_t kAutoElemBudget = (size_t)48 << 30;
+
+// Device storage of the element matrices of the FP64 applies (sem_options.elem_matrices): every
+// level of an FP64 handle but the coarsest, the finest of a mixed-precision one; FP64 matrices or
+// the double-FP32 block triangle; in auto mode only when they take at most a quarter of the free
+// device memory and, with those of the other live handles (many batched tanks), 48 GB.
 sem_status alloc_element_matrices(sem_handle* h) {
     const int nl = (int)h->lv.size();
     const int last = h->opts.precision == SEM_PREC_FP64 ? nl - 1 : std::min(1, nl - 1);
+    int kind = h->opts.elem_matrices;
+    if (kind < 0) kind = h->opts.precision == SEM_PREC_FP64 ? SEM_ELEM_FP64 : SEM_ELEM_DF32;
+    auto level_bytes = [&](Level& L) -> size_t {
+        if (kind == SEM_ELEM_FP64) return sizeof(double) * (size_t)L.E * L.Np * L.Np;
+        df_layout(L.Np, &L.df_T, &L.df_NB, &L.df_S, &L.df_TS);
+        return sizeof(float2) * (size_t)L.E * (L.df_NB * (L.df_NB + 1) / 2) * L.df_TS;
+    };
     size_t bytes = 0;
-    for (int li = 0; li < last; ++li) bytes += sizeof(double) * (size_t)h->lv[li].E * h->lv[li].Np * h->lv[li].Np;
+    for (int li = 0; li < last; ++li) bytes += level_bytes(h->lv[li]);
     if (bytes == 0) return SEM_OK;
     if (h->opts.elem_matrices < 0) {
         size_t fr = 0, tot = 0;
         CKS(cudaMemGetInfo(&fr, &tot));
-        if (bytes > fr / 4 || bytes > (size_t)48 << 30) return SEM_OK;      // sum factorisation
+        if (bytes > fr / 4) return SEM_OK;                                   // sum factorisation
+        size_t cur = g_auto_elem_bytes.load();
+        do {
+            if (cur + bytes > kAutoElemBudget) return SEM_OK;
+        } while (!g_auto_elem_bytes.compare_exchange_weak(cur, cur + bytes));
+        h->auto_elem_bytes = bytes;
     }
     for (int li = 0; li < last; ++li) {
         Level& L = h->lv[li];
         void* p = nullptr;
-        const cudaError_t e = cudaMalloc(&p, sizeof(double) * (size_t)L.E * L.Np * L.Np);
+        const cudaError_t e = cudaMalloc(&p, level_bytes(L));
         if (e != cudaSuccess) {
             set_error("element matrices: " + std::string(cudaGetErrorString(e)));
             return SEM_ENOMEM;
         }
-        L.Ae64 = static_cast<double*>(p);
+        if (kind == SEM_ELEM_FP64) L.Ae64 = static_cast<double*>(p);
+        else L.Adf = static_cast<float2*>(p);
     }
     return SEM_OK;
 }
 
 void free_level(Level& L) {
     void* ptrs[] = {L.map, L.G, L.G32, L.G16, L.G16T, L.lift_elems, L.dinv, L.dinv32, L.dir, L.ref64.m, L.ref32.m, L.It64, L.Iz64, L.It32, L.Iz32, L.gref,
-                    L.csr_rowptr, L.csr_col, L.csr_val, L.csr_slot, L.dss_ptr, L.dss_slot, L.ye64, L.csr_eptr, L.csr_eidx, L.csr_ev, L.Ae64,
+                    L.csr_rowptr, L.csr_col, L.csr_val, L.csr_slot, L.dss_ptr, L.dss_slot, L.ye64, L.csr_eptr, L.csr_eidx, L.csr_ev, L.Ae64, L.Adf,
                     L.owner, L.wmult, L.wmult32, L.u, L.f, L.y, L.d, L.u32, L.f32, L.y32, L.d32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -805,19 +823,26 @@ sem_status check_options(const sem_options& o, int P) {
         set_error("inner_imax >= 0 and 0 < inner_rtol < 1");
         return SEM_EINVAL;
     }
+    if (o.elem_matrices < -1 || o.elem_matrices > SEM_ELEM_DF32) {
+        set_error("elem_matrices must be -1, SEM_ELEM_OFF, SEM_ELEM_FP64 or SEM_ELEM_DF32");
+        return SEM_EINVAL;
+    }
     return SEM_OK;
 }
 
-// A timed-out geometric-factor copy inside the tensor-core apply (flag set on the device):
-// turns *ret into SEM_TIMEOUT and clears the flag.  Synchronous; reads the flag of
-// MIXED_TF32 handles, or of any handle when `always`.
+// A timed-out copy inside the tensor-core apply, the network's GEMMs or the double-FP32 apply
+// (flag set on the device): turns *ret into SEM_TIMEOUT and clears the flag.  Synchronous;
+// reads the flag of MIXED_TF32 handles and of handles with double-FP32 element matrices, or
+// of any handle when `always`.
 sem_status check_tc_flag(sem_handle* h, sem_status* ret, bool always = false) {
-    if (!always && h->opts.precision != SEM_PREC_MIXED_TF32) return SEM_OK;
+    bool df = false;
+    for (const Level& L : h->lv) df = df || L.Adf != nullptr;
+    if (!always && !df && h->opts.precision != SEM_PREC_MIXED_TF32) return SEM_OK;
     int terr = 0;
     CKS(cudaMemcpy(&terr, h->sc.flags + F_TC_ERR, sizeof(int), cudaMemcpyDeviceToHost));
     if (terr) {
         CKS(cudaMemset(h->sc.flags + F_TC_ERR, 0, sizeof(int)));
-        set_error("tensor-core apply: a geometric-factor copy did not complete within its wait bound");
+        set_error("a bulk copy of the tensor-core or double-FP32 apply did not complete within its wait bound");
         *ret = SEM_TIMEOUT;
     }
     return SEM_OK;
@@ -1157,6 +1182,7 @@ void sem_destroy(sem_handle* h) {
     if (h->bstream) cudaStreamSynchronize(h->bstream);
     cudaDeviceSynchronize();
     for (Level& L : h->lv) free_level(L);
+    if (h->auto_elem_bytes) g_auto_elem_bytes.fetch_sub(h->auto_elem_bytes);
     void* ptrs[] = {h->sc.part, h->sc.counter, h->sc.scal, h->sc.flags, h->r, h->z, h->p, h->q, h->x, h->fr,
                     h->V, h->Zb, h->cx, h->cr, h->cz, h->cp, h->cq, h->cb, h->st_eta, h->st_rhs, h->st_phi,
                     h->ir, h->iz, h->ip, h->iq, h->ie, h->gm_y, h->net.W1, h->net.b1, h->net.W2, h->net.b2,
@@ -1226,10 +1252,11 @@ sem_status sem_tile_shapes(const sem_handle* h, int level, int* elems_fp64, int*
     return SEM_OK;
 }
 
-sem_status sem_elem_matrices(const sem_handle* h, int level, int* on) {
+sem_status sem_elem_matrices(const sem_handle* h, int level, int* kind) {
     CKST(check_level(h, level));
-    if (!on) { set_error("on is NULL"); return SEM_EINVAL; }
-    *on = h->lv[level].Ae64 != nullptr ? 1 : 0;
+    if (!kind) { set_error("kind is NULL"); return SEM_EINVAL; }
+    const Level& L = h->lv[level];
+    *kind = L.Adf != nullptr ? SEM_ELEM_DF32 : (L.Ae64 != nullptr ? SEM_ELEM_FP64 : SEM_ELEM_OFF);
     return SEM_OK;
 }
 
