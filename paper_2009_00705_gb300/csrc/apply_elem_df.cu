@@ -81,23 +81,53 @@ __device__ __forceinline__ void df_copy(uint32_t dst, const void* src, uint32_t 
                  : "memory");
 }
 
+// (s, l) += (a, b): the heads by Knuth's TwoSum (s + a = t + d exactly), d and b into l.
+// Rounded intrinsics keep the compiler from contracting or reassociating.
+__device__ __forceinline__ void df_add(float& s, float& l, float a, float b) {
+    const float t = __fadd_rn(s, a);
+    const float bp = __fsub_rn(t, s);
+    const float d = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(a, bp));
+    s = t;
+    l = __fadd_rn(l, __fadd_rn(d, b));
+}
+
 // (s, l, c1, c2) += a x in double-FP32 arithmetic: s the running head sum, l its TwoSum and
-// TwoProduct errors, c1 and c2 the cross terms a_hi x_lo and a_lo x_hi.  Rounded intrinsics
-// keep the compiler from contracting the product into the sum.
+// TwoProduct errors, c1 and c2 the cross terms a_hi x_lo and a_lo x_hi.
 __device__ __forceinline__ void df_mac(float& s, float& l, float& c1, float& c2, const float2 a, const float2 x) {
     const float p = __fmul_rn(a.x, x.x);
     const float e = __fmaf_rn(a.x, x.x, -p);          // a_hi x_hi = p + e exactly
     c1 = __fmaf_rn(a.x, x.y, c1);
     c2 = __fmaf_rn(a.y, x.x, c2);
-    const float t = __fadd_rn(s, p);                  // s + p = t + d exactly
-    const float bp = __fsub_rn(t, s);
-    const float d = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
-    s = t;
-    l = __fadd_rn(l, __fadd_rn(d, e));
+    df_add(s, l, p, e);
 }
 
-__device__ __forceinline__ double df_fold(float s, float l, float c1, float c2) {
-    return (double)s + (double)__fadd_rn(l, __fadd_rn(c1, c2));
+// one block row (lane r: row r of the tile) and, off the diagonal, one block column (lane c)
+template <int TT, bool OFF>
+__device__ __forceinline__ void df_tile(const float2* __restrict__ A, int T, int S, int lane, const float2* xJ,
+                                        const float2* xI, float& zs, float& zl, float& z1, float& z2, float& ws,
+                                        float& wl, float& w1, float& w2) {
+    if constexpr (TT > 0) {
+        // even T: the x blocks start on 16-byte boundaries, two pairs per shared-memory load
+        static_assert(TT % 2 == 0, "even block size");
+        constexpr int SS = TT | 1;
+#pragma unroll
+        for (int c = 0; c < TT; c += 2) {
+            const float4 xj = *reinterpret_cast<const float4*>(xJ + c);
+            df_mac(zs, zl, z1, z2, A[lane * SS + c], make_float2(xj.x, xj.y));
+            df_mac(zs, zl, z1, z2, A[lane * SS + c + 1], make_float2(xj.z, xj.w));
+            if constexpr (OFF) {
+                const float4 xi = *reinterpret_cast<const float4*>(xI + c);
+                df_mac(ws, wl, w1, w2, A[c * SS + lane], make_float2(xi.x, xi.y));
+                df_mac(ws, wl, w1, w2, A[(c + 1) * SS + lane], make_float2(xi.z, xi.w));
+            }
+        }
+    } else {
+#pragma unroll 4
+        for (int c = 0; c < T; ++c) {
+            df_mac(zs, zl, z1, z2, A[lane * S + c], xJ[c]);
+            if constexpr (OFF) df_mac(ws, wl, w1, w2, A[c * S + lane], xI[c]);
+        }
+    }
 }
 
 __device__ __forceinline__ float2 df_split(double v) {
@@ -124,7 +154,7 @@ __global__ void __launch_bounds__(256) k_apply_elem_df(int E, int Np, int Tr, in
     extern __shared__ __align__(16) unsigned char df_smem[];
     float2* ring = reinterpret_cast<float2*>(df_smem);              // [NB][2][TS]
     float2* xs = ring + (size_t)NB * 2 * TS;                         // [2][NT]
-    double* part = reinterpret_cast<double*>(xs + 2 * NT);          // [2][H + 1][NB][T]
+    float2* part = xs + 2 * NT;                                      // [2][H + 1][NB][T] (head, tail)
     uint64_t* bars = reinterpret_cast<uint64_t*>(part + (size_t)2 * (H + 1) * NB * T);   // [NB][2]
     float2* myring = ring + (size_t)warp * 2 * TS;
     const uint32_t bar0 = saddr(bars + 2 * warp), bar1 = bar0 + 8;
@@ -143,16 +173,15 @@ __global__ void __launch_bounds__(256) k_apply_elem_df(int E, int Np, int Tr, in
     };
     const long long njobs = count * nd;
     const uint32_t tile_bytes = (uint32_t)TS * 8u;
-    auto issue = [&](long long j) {            // lane 0: tile k of this warp for the element of job j
-        const long long it = j / nd;
-        const int k = (int)(j - it * nd);
+    // lane 0: job j = it * nd + k, tile k of this warp for element `it`, into slot j & 1
+    auto issue = [&](long long j, long long it, int k) {
         const float2* src = Adf + ((size_t)elem(it) * ntiles + off + k) * TS;
         df_copy(saddr(myring + (size_t)(j & 1) * TS), src, tile_bytes, (j & 1) ? bar1 : bar0);
     };
     bool failed = false;
     long long pend0 = -1, pend1 = -1;          // job in flight in slot 0 / 1 (lane 0's view)
     if (lane == 0 && njobs > 0) {
-        issue(0);
+        issue(0, 0, 0);
         pend0 = 0;
     }
 
@@ -179,12 +208,17 @@ __global__ void __launch_bounds__(256) k_apply_elem_df(int E, int Np, int Tr, in
         }
         if (it >= 2 && tid < Np) {
             const int b = tid / T, r = tid - b * T;
-            const double* pp = part + (size_t)slot * (H + 1) * NB * T;
-            double v = pp[(size_t)b * T + r];
+            const float2* pp = part + (size_t)slot * (H + 1) * NB * T;
+            float2 q = pp[(size_t)b * T + r];
+            float hs = q.x, hl = q.y;
             for (int d = 1; d <= H; ++d) {
-                const int w = (b - d + NB) % NB;
-                if (d < df_tiles_of(w, NB)) v += pp[((size_t)d * NB + b) * T + r];
+                const int w = b - d < 0 ? b - d + NB : b - d;
+                if (d < df_tiles_of(w, NB)) {
+                    q = pp[((size_t)d * NB + b) * T + r];
+                    df_add(hs, hl, q.x, q.y);
+                }
             }
+            const double v = (double)hs + (double)hl;
             if (ye != nullptr) ye[(size_t)elem(it - 2) * Np + tid] = v;
             else if (m_prev2 >= 0) atomicAdd(&y[m_prev2], v);
         }
@@ -193,14 +227,15 @@ __global__ void __launch_bounds__(256) k_apply_elem_df(int E, int Np, int Tr, in
 
         // ---- phase B: this warp's tiles of element `it`
         const float2* xv = xs + slot * NT;
-        double* pp = part + (size_t)slot * (H + 1) * NB * T;
-        double zacc = 0.0;
+        float2* pp = part + (size_t)slot * (H + 1) * NB * T;
+        float zs = 0.f, zl = 0.f;            // this warp's block row, all its tiles
         for (int k = 0; k < nd; ++k) {
             const long long j = it * nd + k;
             if (lane == 0 && !failed && j + 1 < njobs) {
                 // the slot was last read by job j - 1 (generic proxy); order that before the copy
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue(j + 1);
+                if (k + 1 < nd) issue(j + 1, it, k + 1);
+                else issue(j + 1, it + 1, 0);
                 if ((j + 1) & 1) pend1 = j + 1;
                 else pend0 = j + 1;
             }
@@ -211,29 +246,24 @@ __global__ void __launch_bounds__(256) k_apply_elem_df(int E, int Np, int Tr, in
                 if (j & 1) pend1 = -1;
                 else pend0 = -1;
             }
-            const int J = (warp + k) % NB;
+            const int J = warp + k < NB ? warp + k : warp + k - NB;
             if (!failed && lane < T) {
                 const float2* A = myring + (size_t)(j & 1) * TS;
-                const float2* xJ = xv + J * T;
-                const float2* xI = xv + warp * T;
-                float zs = 0.f, zl = 0.f, z1 = 0.f, z2 = 0.f;
-                if (k == 0) {
-#pragma unroll 4
-                    for (int c = 0; c < T; ++c) df_mac(zs, zl, z1, z2, A[lane * S + c], xJ[c]);
-                } else {
-                    float ws = 0.f, wl = 0.f, w1 = 0.f, w2 = 0.f;
-#pragma unroll 4
-                    for (int c = 0; c < T; ++c) {
-                        df_mac(zs, zl, z1, z2, A[lane * S + c], xJ[c]);
-                        df_mac(ws, wl, w1, w2, A[c * S + lane], xI[c]);
-                    }
-                    pp[((size_t)k * NB + J) * T + lane] = df_fold(ws, wl, w1, w2);
-                }
-                zacc += df_fold(zs, zl, z1, z2);
+                float z1 = 0.f, z2 = 0.f, ws = 0.f, wl = 0.f, w1 = 0.f, w2 = 0.f;
+                if (k == 0)
+                    df_tile<TT, false>(A, T, S, lane, xv + J * T, nullptr, zs, zl, z1, z2, ws, wl, w1, w2);
+                else
+                    df_tile<TT, true>(A, T, S, lane, xv + J * T, xv + warp * T, zs, zl, z1, z2, ws, wl, w1, w2);
+                // renormalise the row sum once per tile (s + l exact, |l| <= ulp(s) / 2), so that
+                // the compensation sums never gather more than one tile's rounding errors
+                const float c = __fadd_rn(__fadd_rn(zl, z1), z2);
+                zl = 0.f;
+                df_add(zs, zl, c, 0.f);
+                if (k > 0) pp[((size_t)k * NB + J) * T + lane] = make_float2(ws, __fadd_rn(__fadd_rn(wl, w1), w2));
             }
             __syncwarp();
         }
-        if (lane < T) pp[(size_t)warp * T + lane] = failed ? 0.0 : zacc;
+        if (lane < T) pp[(size_t)warp * T + lane] = failed ? make_float2(0.f, 0.f) : make_float2(zs, zl);
     }
     // copies still in flight after a failed wait: let them land before the CTA exits
     if (lane == 0) {
@@ -283,7 +313,7 @@ void df_layout(int Np, int* T, int* NB, int* S, int* TS) {
 }
 
 cudaError_t apply_elem_df(const Level& L, const double* x, double* y, bool lift, const int* skip, cudaStream_t s) {
-    if (L.df_NB < 1 || L.df_NB > 7 || L.df_T > 32) return cudaErrorInvalidValue;
+    if (L.df_NB < 1 || L.df_NB > 7 || L.df_T > 32 || L.df_S != (L.df_T | 1)) return cudaErrorInvalidValue;
     double* ye = L.ye64;
     const bool sub = lift && L.lift_elems != nullptr && ye == nullptr;
     const int E = sub ? L.nlift : L.E;
