@@ -131,7 +131,7 @@ typedef struct {
  * Lanczos steps on D^{-1}A started from x_i = sin(i+1) on free nodes (a lower
  * bound of lambda_max); nu1 pre- and nu2 post-sweeps (Algorithm 1).
  * Stop test ||r||_2 <= rtol*||f||_2 + atol on the FP64 free-node residual.
- * The coarse order-1 system is solved by FP64 Jacobi-CG to coarse_rtol
+ * The coarse order-1 system is solved by FP64 block-Jacobi or Jacobi CG (coarse_bj) to coarse_rtol
  * relative residual (at most coarse_imax iterations). */
 typedef struct {
     int outer;                  /* sem_outer */
@@ -201,6 +201,13 @@ typedef struct {
                                    factorisation.  -1 (default): SEM_ELEM_FP64 for FP64 handles and
                                    SEM_ELEM_DF32 for mixed-precision ones, when they take at most a
                                    quarter of the free device memory and 48 GB, else off */
+    int coarse_bj;              /* 1 (default) = the coarse CG is preconditioned by block Jacobi: the free
+                                   order-1 nodes are cut into compact patches of at most 128 (recursive
+                                   coordinate bisection in the horizontal), each patch's diagonal block is
+                                   inverted at setup (and whenever the coarse matrix is reassembled) and
+                                   applied from shared memory, one CTA per patch (about half the CG
+                                   iterations of point Jacobi); used when every patch fits one co-resident
+                                   CTA and the handle is not batched.  0 = point-Jacobi CG */
 } sem_options;
 
 typedef struct {

@@ -977,6 +977,176 @@ __global__ void __launch_bounds__(512) k_coarse_cg(long long n, const int* __res
     }
 }
 
+// Block-Jacobi preconditioned CG on the assembled coarse matrix.  CTA b owns the free rows
+// brows[bptr[b] .. bptr[b+1]) (a compact patch of the mesh, at most kBjMax rows) and holds the
+// inverse of their diagonal block in shared memory, in FP32 (symmetrised before rounding, so
+// the preconditioner is an exactly symmetric positive definite matrix).  z = M r is then local
+// to the CTA: r, q and the previous z of its rows stay in shared memory, and only z and the
+// direction, which neighbouring rows read in the product, go through global memory (read
+// through L2).  The direction is formed on the fly inside the product from two alternating
+// buffers, as in k_coarse_cg, so an iteration has two grid barriers.  beta takes the
+// Polak-Ribiere form (r_new, z_new - z_old) / (r_old, z_old), which absorbs the FP32 rounding
+// of the block products (Golub and Ye, "Inexact preconditioned conjugate gradient method
+// with inner-outer iteration", 1999).  Partial sums: part[b] (r, z), part[nb + b] (r, r),
+// part[2 nb + b] (p, q), part[3 nb + b] (r, z_old).
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// z_k = sum_j inv[k][j] rf[j] for the CTA's nk rows, one warp per row; written to out[k]
+__device__ void bj_block_product(const float* inv, const float* rf, int nk, double* out) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = wid; k < nk; k += nw) {
+        float v = 0.f;
+        for (int j = lane; j < nk; j += 32) v = fmaf(inv[k * kBjMax + j], rf[j], v);
+        v = warp_sumf(v);
+        if (lane == 0) out[k] = (double)v;
+    }
+}
+
+__global__ void __launch_bounds__(512) k_coarse_bjcg(long long n, const int* __restrict__ rowptr,
+                                                     const int* __restrict__ col, const double* __restrict__ vals,
+                                                     const int* __restrict__ bptr, const int* __restrict__ brows,
+                                                     const float* __restrict__ binv, const double* __restrict__ b,
+                                                     double* x, double* zg, double* pa, double* pb, double* part,
+                                                     unsigned* bar, double* scal, int* flags, double rtol2, int imax,
+                                                     unsigned extra_arrivals) {
+    extern __shared__ __align__(16) unsigned char bj_smem[];
+    float* inv = reinterpret_cast<float*>(bj_smem);                  // [kBjMax][kBjMax]
+    double* rs = reinterpret_cast<double*>(inv + kBjMax * kBjMax);   // r of the CTA's rows
+    double* zo = rs + kBjMax;                                        // z of the previous iteration
+    double* qs = zo + kBjMax;                                        // q, then the new z
+    double* pn = qs + kBjMax;                                        // the new direction
+    float* rf = reinterpret_cast<float*>(pn + kBjMax);               // r rounded to FP32
+    int* rw = reinterpret_cast<int*>(rf + kBjMax);                   // global row ids
+    const unsigned nb = gridDim.x;
+    const unsigned expected = nb + extra_arrivals;   // extra_arrivals > 0 only in the timeout test
+    const int t = threadIdx.x;
+    const int k0 = bptr[blockIdx.x], nk = bptr[blockIdx.x + 1] - k0;
+    {
+        const float4* src = reinterpret_cast<const float4*>(binv + (size_t)blockIdx.x * kBjMax * kBjMax);
+        float4* dst = reinterpret_cast<float4*>(inv);
+        for (int i = t; i < kBjMax * kBjMax / 4; i += blockDim.x) dst[i] = src[i];
+    }
+    for (long long i = blockIdx.x * (long long)blockDim.x + t; i < n; i += (long long)gridDim.x * blockDim.x) x[i] = 0.0;
+    double* p_old = pa;       // direction of the previous iteration (zero before the first)
+    double* p_new = pb;
+    if (t < nk) {
+        const int row = brows[k0 + t];
+        rw[t] = row;
+        rs[t] = b[row];
+        rf[t] = (float)rs[t];
+        p_old[row] = 0.0;
+    }
+    __syncthreads();
+    bj_block_product(inv, rf, nk, zo);
+    __syncthreads();
+    double s0 = 0, s1 = 0;
+    if (t < nk) {
+        zg[rw[t]] = zo[t];
+        s0 = rs[t] * zo[t];
+        s1 = rs[t] * rs[t];
+    }
+    s0 = block_sum(s0);
+    s1 = block_sum(s1);
+    if (t == 0) { part[blockIdx.x] = s0; part[nb + blockIdx.x] = s1; }
+    if (!grid_barrier(bar, expected)) return;
+    double rho = grid_total(part);
+    const double bb = grid_total(part + nb);
+    const double tol2 = rtol2 * bb;
+    int it = 0;
+    double rr = bb;
+    double beta = 0.0;
+    __shared__ double s_alpha, s_beta;
+    while (rr > tol2 && rr > 0.0 && it < imax) {
+        // q = A p for the CTA's rows, 4 lanes per row (blockDim = 4 kBjMax: one pass); p formed
+        // on the fly from z and the previous direction
+        double pq = 0;
+        {
+            const int k = t >> 2, l4 = t & 3;
+            double v = 0;
+            if (k < nk) {
+                const int row = rw[k];
+                const int a0 = rowptr[row], a1 = rowptr[row + 1];
+                for (int a = a0 + l4; a < a1; a += 32) {      // up to 8 independent gathers per lane
+                    int c[8];
+                    double av[8], pv[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int aa = a + 4 * u;
+                        c[u] = aa < a1 ? col[aa] : -1;
+                        av[u] = aa < a1 ? vals[aa] : 0.0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        pv[u] = c[u] >= 0 ? __ldcg(zg + c[u]) + beta * __ldcg(p_old + c[u]) : 0.0;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) v += av[u] * pv[u];
+                }
+            }
+            v += __shfl_down_sync(0xffffffffu, v, 2, 4);
+            v += __shfl_down_sync(0xffffffffu, v, 1, 4);
+            if (k < nk && l4 == 0) {
+                const int row = rw[k];
+                const double pv = __ldcg(zg + row) + beta * __ldcg(p_old + row);
+                p_new[row] = pv;
+                pn[k] = pv;
+                qs[k] = v;
+                pq = pv * v;
+            }
+        }
+        pq = block_sum(pq);
+        if (t == 0) part[2 * nb + blockIdx.x] = pq;
+        if (!grid_barrier(bar, expected)) return;
+        {
+            const double pq_all = grid_total(part + 2 * nb);
+            if (t == 0) s_alpha = rho / pq_all;
+            __syncthreads();
+        }
+        const double alpha = s_alpha;
+        if (t < nk) {
+            x[rw[t]] += alpha * pn[t];
+            rs[t] -= alpha * qs[t];
+            rf[t] = (float)rs[t];
+        }
+        __syncthreads();
+        bj_block_product(inv, rf, nk, qs);       // the new z, over q (no longer needed)
+        __syncthreads();
+        double t0 = 0, t1 = 0, t3 = 0;
+        if (t < nk) {
+            const double zn = qs[t];
+            t0 = rs[t] * zn;
+            t1 = rs[t] * rs[t];
+            t3 = rs[t] * zo[t];
+            zg[rw[t]] = zn;
+            zo[t] = zn;
+        }
+        t0 = block_sum(t0);
+        t1 = block_sum(t1);
+        t3 = block_sum(t3);
+        if (t == 0) { part[blockIdx.x] = t0; part[nb + blockIdx.x] = t1; part[3 * nb + blockIdx.x] = t3; }
+        if (!grid_barrier(bar, expected)) return;
+        const double rho_new = grid_total(part);
+        rr = grid_total(part + nb);
+        const double rzo = grid_total(part + 3 * nb);
+        if (t == 0) s_beta = (rho_new - rzo) / rho;
+        __syncthreads();
+        beta = s_beta;
+        rho = rho_new;
+        ++it;
+        double* tmp = p_old;
+        p_old = p_new;
+        p_new = tmp;
+    }
+    if (blockIdx.x == 0 && t == 0) {
+        flags[F_CG_ITERS] = it;
+        flags[F_CG_DONE] = (rr <= tol2 || rr == 0.0) ? 1 : 0;
+        scal[S_CG_RR] = rr;
+    }
+}
+
 // Whole coarse CG in one CTA (no grid barrier, so any number of these may run
 // concurrently and inside captured graphs): used for batched tanks and small
 // coarse problems.  Global-memory writes of the CTA's threads are ordered by
@@ -1458,6 +1628,52 @@ cudaError_t coarse_cg_persistent(const Level& C, const int* rowptr, const int* c
     void* args[] = {&n,    &rowptr, &col,  &vals,  &dinv,  &b,     &x,    &r,   &z,
                     &p,    &q,      &part, &bar,   &scal,  &flags, &rtol2, &imax, &extra_arrivals};
     err = cudaLaunchCooperativeKernel((void*)k_coarse_cg, grid, 512, args, 0, s);
+    if (err != cudaSuccess) return err;
+    return cudaGetLastError();
+}
+
+size_t coarse_bj_smem() {
+    return sizeof(float) * kBjMax * kBjMax + sizeof(double) * 4 * kBjMax + sizeof(float) * kBjMax + sizeof(int) * kBjMax;
+}
+
+// Largest number of blocks the block-Jacobi CG can take (all CTAs co-resident), 0 if none.
+int coarse_bj_capacity() {
+    static int cap = -1;
+    if (cap >= 0) return cap;
+    cap = 0;
+    if (cudaFuncSetAttribute(k_coarse_bjcg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)coarse_bj_smem()) !=
+        cudaSuccess)
+        return cap;
+    int per_sm = 0, dev = 0, sms = kSMs;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_bjcg, 4 * kBjMax, coarse_bj_smem()) !=
+        cudaSuccess)
+        return cap;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cap = per_sm * sms;
+    return cap;
+}
+
+cudaError_t coarse_cg_bj(const Level& C, const double* b, double* x, double* z, double* pa, double* pb, Scratch& sc,
+                         double rtol2, int imax, unsigned extra_arrivals, cudaStream_t s) {
+    const int grid = C.bj_nb;
+    if (grid < 1 || grid > coarse_bj_capacity()) return cudaErrorCooperativeLaunchTooLarge;
+    cudaError_t err = cudaMemsetAsync(sc.counter + 1, 0, 3 * sizeof(unsigned), s);
+    if (err != cudaSuccess) return err;
+    long long n = C.N;
+    const int* rowptr = C.csr_rowptr;
+    const int* col = C.csr_col;
+    const double* vals = C.csr_val;
+    const int* bptr = C.bj_ptr;
+    const int* brows = C.bj_rows;
+    const float* binv = C.bj_inv;
+    double* part = sc.part;
+    unsigned* bar = sc.counter + 1;
+    double* scal = sc.scal;
+    int* flags = sc.flags;
+    void* args[] = {&n,  &rowptr, &col,  &vals, &bptr,  &brows, &binv,  &b,    &x,
+                    &z,  &pa,     &pb,   &part, &bar,   &scal,  &flags, &rtol2, &imax, &extra_arrivals};
+    err = cudaLaunchCooperativeKernel((void*)k_coarse_bjcg, grid, 4 * kBjMax, args, coarse_bj_smem(), s);
     if (err != cudaSuccess) return err;
     return cudaGetLastError();
 }

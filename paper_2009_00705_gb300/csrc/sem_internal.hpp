@@ -79,6 +79,12 @@ struct Level {
     int* csr_eidx = nullptr;
     double* csr_ev = nullptr;              // [E][Np][Np] element-matrix entries before their fixed-order sums
     long long csr_nnz = 0;
+    // coarse level, block-Jacobi CG: blocks of free rows (compact patches), their FP32 inverses
+    int bj_nb = 0;                         // number of blocks (0: point-Jacobi CG)
+    int* bj_ptr = nullptr;                 // [bj_nb + 1] offsets into bj_rows
+    int* bj_rows = nullptr;                // free row ids, block by block
+    float* bj_inv = nullptr;               // [bj_nb][kBjMax][kBjMax] symmetric inverse of each diagonal block
+    std::vector<int> hbj_ptr, hbj_rows;
     // additive Schwarz smoother (smoother = ASM; every level but the coarsest)
     int asm_nmax = 0;                      // largest subdomain (free nodes)
     long long asm_words = 0;               // block storage (elements of the V-cycle's type)
@@ -350,6 +356,12 @@ cudaError_t coarse_cg_single(const Level& C, const int* rowptr, const int* col, 
 cudaError_t coarse_cg_persistent(const Level& C, const int* rowptr, const int* col, const double* vals,
                                  const double* b, double* x, double* r, double* z, double* p, double* q, Scratch& sc,
                                  double rtol2, int imax, unsigned extra_arrivals, cudaStream_t s);
+// block-Jacobi preconditioned CG (one CTA per block of C.bj_ptr / C.bj_rows, the FP32 block
+// inverses C.bj_inv in shared memory), one cooperative launch; same flags as the above
+constexpr int kBjMax = 128;                 // rows per block at most
+int coarse_bj_capacity();                   // blocks that can be co-resident (0: none)
+cudaError_t coarse_cg_bj(const Level& C, const double* b, double* x, double* z, double* pa, double* pb, Scratch& sc,
+                         double rtol2, int imax, unsigned extra_arrivals, cudaStream_t s);
 
 // scalar slots in Scratch::scal
 enum {

@@ -10,6 +10,7 @@
 #include <cstring>
 #include <string>
 #include <random>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -505,14 +506,144 @@ sem_status build_coarse_gradients(sem_handle* h) {
     return reassemble_coarse(h);
 }
 
-// Values of the assembled coarse matrix from the coarsest level's current geometric factors.
+// Recursive coordinate bisection of idx[lo, hi) into `parts` contiguous runs (the longer
+// horizontal extent is cut, in proportion to the parts on each side); ptr gets the run ends.
+void rcb_split(std::vector<int>& idx, int lo, int hi, int parts, const std::vector<double>& xyz,
+               std::vector<int>& ptr) {
+    if (parts <= 1 || hi - lo <= 1) {
+        ptr.push_back(hi);
+        return;
+    }
+    double mn[2] = {1e300, 1e300}, mx[2] = {-1e300, -1e300};
+    for (int i = lo; i < hi; ++i)
+        for (int a = 0; a < 2; ++a) {
+            mn[a] = std::min(mn[a], xyz[3 * (size_t)idx[i] + a]);
+            mx[a] = std::max(mx[a], xyz[3 * (size_t)idx[i] + a]);
+        }
+    const int ax = (mx[1] - mn[1] > mx[0] - mn[0]) ? 1 : 0;
+    std::stable_sort(idx.begin() + lo, idx.begin() + hi, [&](int a, int b) {
+        const double va = xyz[3 * (size_t)a + ax], vb = xyz[3 * (size_t)b + ax];
+        return va < vb || (va == vb && xyz[3 * (size_t)a + 2] < xyz[3 * (size_t)b + 2]);
+    });
+    const int p1 = parts / 2;
+    const int cut = lo + (int)std::llround((double)(hi - lo) * p1 / parts);
+    rcb_split(idx, lo, cut, p1, xyz, ptr);
+    rcb_split(idx, cut, hi, parts - p1, xyz, ptr);
+}
+
+// Inverse of the SPD matrix a (n x n, row major) by Cholesky, in place; false if a pivot is
+// not positive.
+bool spd_inverse(std::vector<double>& a, int n) {
+    for (int j = 0; j < n; ++j) {                       // a = L L^T, L in the lower triangle
+        double d = a[(size_t)j * n + j];
+        for (int k = 0; k < j; ++k) d -= a[(size_t)j * n + k] * a[(size_t)j * n + k];
+        if (!(d > 0.0)) return false;
+        d = std::sqrt(d);
+        a[(size_t)j * n + j] = d;
+        for (int i = j + 1; i < n; ++i) {
+            double v = a[(size_t)i * n + j];
+            for (int k = 0; k < j; ++k) v -= a[(size_t)i * n + k] * a[(size_t)j * n + k];
+            a[(size_t)i * n + j] = v / d;
+        }
+    }
+    std::vector<double> li((size_t)n * n, 0.0);        // L^{-1}, lower triangular
+    for (int j = 0; j < n; ++j) {
+        li[(size_t)j * n + j] = 1.0 / a[(size_t)j * n + j];
+        for (int i = j + 1; i < n; ++i) {
+            double v = 0.0;
+            for (int k = j; k < i; ++k) v -= a[(size_t)i * n + k] * li[(size_t)k * n + j];
+            li[(size_t)i * n + j] = v / a[(size_t)i * n + i];
+        }
+    }
+    for (int i = 0; i < n; ++i)                         // A^{-1} = L^{-T} L^{-1}, symmetric
+        for (int j = 0; j <= i; ++j) {
+            double v = 0.0;
+            for (int k = i; k < n; ++k) v += li[(size_t)k * n + i] * li[(size_t)k * n + j];
+            a[(size_t)i * n + j] = a[(size_t)j * n + i] = v;
+        }
+    return true;
+}
+
+// Block-Jacobi preconditioner of the coarse CG (sem_options.coarse_bj): the free rows cut into
+// patches of at most kBjMax (about 120) by coordinate bisection, once; the FP32 inverse of each
+// patch's diagonal block from the current coarse matrix, every time it is reassembled.
+sem_status build_coarse_bj(sem_handle* h) {
+    Level& C = h->lv.back();
+    if (!h->opts.coarse_bj || h->opts.batch != 0 || C.csr_val == nullptr) return SEM_OK;
+    const long long N = C.N;
+    std::vector<int> rowptr(N + 1), col((size_t)C.csr_nnz);
+    std::vector<double> val((size_t)C.csr_nnz);
+    CK(cudaMemcpy(rowptr.data(), C.csr_rowptr, sizeof(int) * (N + 1), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(col.data(), C.csr_col, sizeof(int) * col.size(), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(val.data(), C.csr_val, sizeof(double) * val.size(), cudaMemcpyDeviceToHost));
+    if (C.hbj_ptr.empty()) {
+        std::vector<int> freer;
+        for (long long i = 0; i < N; ++i)
+            if (rowptr[i + 1] > rowptr[i]) freer.push_back((int)i);
+        const int nf = (int)freer.size();
+        const int nb = (nf + 119) / 120;
+        if (nf == 0 || nb > coarse_bj_capacity()) return SEM_OK;       // point-Jacobi CG
+        std::vector<double> xyz(3 * (size_t)N);
+        const sem_status cst = sem_node_coords(h, (int)h->lv.size() - 1, xyz.data());
+        if (cst != SEM_OK) return cst;
+        std::vector<int> ptr{0};
+        rcb_split(freer, 0, nf, nb, xyz, ptr);
+        for (size_t b = 0; b + 1 < ptr.size(); ++b)
+            if (ptr[b + 1] - ptr[b] > kBjMax) return SEM_OK;
+        C.hbj_ptr = ptr;
+        C.hbj_rows = freer;
+        CK(upload(&C.bj_ptr, ptr));
+        CK(upload(&C.bj_rows, freer));
+        CK(dalloc(&C.bj_inv, (size_t)(ptr.size() - 1) * kBjMax * kBjMax));
+    }
+    const int nb = (int)C.hbj_ptr.size() - 1;
+    std::vector<float> inv((size_t)nb * kBjMax * kBjMax, 0.f);
+    std::vector<char> ok(nb, 1);
+    auto work = [&](int b0, int b1) {
+        for (int b = b0; b < b1; ++b) {
+            const int k0 = C.hbj_ptr[b], n = C.hbj_ptr[b + 1] - k0;
+            std::unordered_map<int, int> loc;
+            for (int k = 0; k < n; ++k) loc[C.hbj_rows[k0 + k]] = k;
+            std::vector<double> a((size_t)n * n, 0.0);
+            for (int k = 0; k < n; ++k) {
+                const int row = C.hbj_rows[k0 + k];
+                for (int t = rowptr[row]; t < rowptr[row + 1]; ++t) {
+                    const auto it = loc.find(col[t]);
+                    if (it != loc.end()) a[(size_t)k * n + it->second] = val[t];
+                }
+            }
+            for (int i = 0; i < n; ++i)                 // the assembled block, symmetrised
+                for (int j = 0; j < i; ++j)
+                    a[(size_t)i * n + j] = a[(size_t)j * n + i] = 0.5 * (a[(size_t)i * n + j] + a[(size_t)j * n + i]);
+            if (!spd_inverse(a, n)) { ok[b] = 0; continue; }
+            float* dst = inv.data() + (size_t)b * kBjMax * kBjMax;
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < n; ++j) dst[(size_t)i * kBjMax + j] = (float)a[(size_t)i * n + j];
+        }
+    };
+    const int nt = std::max(1, std::min<int>(16, (int)std::thread::hardware_concurrency()));
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nt; ++t) pool.emplace_back(work, (int)((long long)nb * t / nt), (int)((long long)nb * (t + 1) / nt));
+    for (std::thread& th : pool) th.join();
+    for (int b = 0; b < nb; ++b)
+        if (!ok[b]) {
+            set_error("coarse block-Jacobi: a diagonal block is not positive definite");
+            return SEM_BREAKDOWN;
+        }
+    CK(cudaMemcpy(C.bj_inv, inv.data(), sizeof(float) * inv.size(), cudaMemcpyHostToDevice));
+    C.bj_nb = nb;
+    return SEM_OK;
+}
+
+// Values of the assembled coarse matrix from the coarsest level's current geometric factors,
+// and the block-Jacobi inverses that depend on them.
 sem_status reassemble_coarse(sem_handle* h) {
     Level& C = h->lv.back();
     if (C.csr_val == nullptr) return SEM_OK;
     CK(cudaMemset(C.csr_val, 0, sizeof(double) * C.csr_nnz));
     CK(coarse_assemble(C, C.gref, C.csr_slot, C.csr_val, 0));    // atomic, or fixed-order sums (deterministic)
     CK(cudaDeviceSynchronize());
-    return SEM_OK;
+    return build_coarse_bj(h);
 }
 
 sem_status build_transfers(sem_handle* h) {

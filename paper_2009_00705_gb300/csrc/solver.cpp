@@ -139,7 +139,7 @@ void flush_events(sem_handle* h) {
     h->ev_used = 0;
 }
 
-// FP64 Jacobi-CG on the coarsest level: x = A_c^{-1} b to coarse_rtol.  The coarse
+// FP64 block-Jacobi or Jacobi CG on the coarsest level: x = A_c^{-1} b to coarse_rtol.  The coarse
 // matrix is assembled in CSR at setup and the whole CG runs in one persistent
 // cooperative launch; coarse levels too large to assemble (high-order single-level
 // configurations) launch one kernel per CG step, predicated on a device-side done
@@ -152,7 +152,10 @@ sem_status coarse_solve(sem_handle* h, const double* b, double* x, cudaStream_t 
         // one CTA for batched tanks (tanks run concurrently; no inter-CTA waits), the
         // cooperative multi-CTA kernel otherwise
         const bool single = h->opts.batch != 0;
-        if (single)
+        if (!single && C.bj_nb > 0)
+            K(coarse_cg_bj(C, b, x, h->cz, h->cp, h->cq, sc, rt * rt, h->opts.coarse_imax,
+                           (unsigned)h->opts.debug_barrier_extra, s));
+        else if (single)
             K(coarse_cg_single(C, C.csr_rowptr, C.csr_col, C.csr_val, b, x, h->cr, h->cz, h->cp, h->cq, sc, rt * rt,
                                h->opts.coarse_imax, s));
         else
@@ -699,7 +702,7 @@ sem_status alloc_element_matrices(sem_handle* h) {
 
 void free_level(Level& L) {
     void* ptrs[] = {L.map, L.G, L.G32, L.G16, L.G16T, L.lift_elems, L.dinv, L.dinv32, L.dir, L.ref64.m, L.ref32.m, L.It64, L.Iz64, L.It32, L.Iz32, L.gref,
-                    L.csr_rowptr, L.csr_col, L.csr_val, L.csr_slot, L.dss_ptr, L.dss_slot, L.ye64, L.csr_eptr, L.csr_eidx, L.csr_ev, L.Ae64, L.Adf,
+                    L.csr_rowptr, L.csr_col, L.csr_val, L.csr_slot, L.dss_ptr, L.dss_slot, L.ye64, L.csr_eptr, L.csr_eidx, L.csr_ev, L.Ae64, L.Adf, L.bj_ptr, L.bj_rows, L.bj_inv,
                     L.owner, L.wmult, L.wmult32, L.u, L.f, L.y, L.d, L.u32, L.f32, L.y32, L.d32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -823,6 +826,7 @@ sem_status check_options(const sem_options& o, int P) {
         set_error("inner_imax >= 0 and 0 < inner_rtol < 1");
         return SEM_EINVAL;
     }
+    if (o.coarse_bj < 0 || o.coarse_bj > 1) { set_error("coarse_bj must be 0 or 1"); return SEM_EINVAL; }
     if (o.elem_matrices < -1 || o.elem_matrices > SEM_ELEM_DF32) {
         set_error("elem_matrices must be -1, SEM_ELEM_OFF, SEM_ELEM_FP64 or SEM_ELEM_DF32");
         return SEM_EINVAL;
@@ -1053,6 +1057,7 @@ void sem_default_options(sem_options* o, int P) {
     o->asm_overlap = 1;
     o->deterministic = 0;
     o->elem_matrices = -1;
+    o->coarse_bj = 1;
 }
 
 sem_status sem_mesh_nodes2d(const sem_mesh* m, int p, long long* n2, double* xy) {

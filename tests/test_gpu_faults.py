@@ -30,8 +30,10 @@ def _solve(sem, **opts):
     return s, phiD, phi
 
 
-def test_coarse_barrier_wait_runs_out_into_sem_timeout(sem):
-    s, phiD, phi = _solve(sem, debug_barrier_extra=1)
+@pytest.mark.parametrize("bj", [1, 0])
+def test_coarse_barrier_wait_runs_out_into_sem_timeout(sem, bj):
+    # the block-Jacobi and the point-Jacobi coarse CG both wait on the same bounded barrier
+    s, phiD, phi = _solve(sem, debug_barrier_extra=1, coarse_bj=bj)
     with pytest.raises(sem.SemError) as e:
         s.solve(phiD, phi, tol=1e-8)
     assert e.value.status == sem.SEM_TIMEOUT
