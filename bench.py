@@ -285,9 +285,12 @@ def run_ncu_solve(a):
     P = a.P
     mesh = W.config_box3d(a.n, a.nlayers)
     xy = sem.sem_mesh_nodes2d(mesh, P)
+    # mixed_tf32 without the setup-time kernel timing (under the profiler it is distorted): the
+    # tcgen05 kernel on the order-6 level, as the timed runs choose
     opts = {"fp64": dict(),
             "mixed_fp32": dict(precision="mixed_fp32", outer="pdc", inner_imax=a.inner_imax, inner_rtol=a.inner_rtol),
-            "mixed_tf32": dict(precision="mixed_tf32", outer="pdc", inner_imax=a.inner_imax, inner_rtol=a.inner_rtol),
+            "mixed_tf32": dict(precision="mixed_tf32", outer="pdc", inner_imax=a.inner_imax, inner_rtol=a.inner_rtol,
+                               autotune=0),
             "asm": dict(precision="mixed_tf32", outer="pdc", smoother="asm", nu1=3, nu2=3)}
     s = sem.Solver(mesh, P, eta_nodal=mesh.eta(xy[:, 0], xy[:, 1]), levels=levels_for(P), coarse_rtol=a.coarse_rtol,
                    **opts[a.ncu_solve])

@@ -6,10 +6,12 @@
 // a_lo x_hi up to 2^-48 |a x|.  The head product a_hi x_hi is split exactly into p + e with
 // one FMA (the TwoProduct of Ogita, Rump and Oishi, "Accurate sum and dot product", 2005),
 // p is added to a running FP32 sum with Knuth's TwoSum (exact), and the rounding errors, e
-// and the two cross terms go to three FP32 compensation sums.  Every 28 or so terms the
-// sums are folded into an FP64 accumulator, so the error of a row stays below a few
-// 1e-13 of sum_j |A_ij x_j|: FP64-class results at the FP32 pipe's rate, which on GB300 is
-// dozens of times the FP64 pipe's.
+// and the two cross terms go to three FP32 compensation sums.  After every tile (28 or so
+// terms) the compensation sums are renormalised into the head by another TwoSum, so they
+// never gather more than one tile's rounding errors; the partial sums of a node meet as
+// (head, tail) pairs and become one FP64 value at the end.  A row's error stays within
+// about 3e-12 of sum_j |A_ij x_j| in the worst case and near 1e-14 in practice: FP64-class
+// results at the FP32 pipe's rate, which on GB300 is dozens of times the FP64 pipe's.
 //
 // A_e is symmetric, so only its upper block triangle is stored: the Np rows are cut into NB
 // blocks of T (T <= 32, one warp lane per row or column), and the NB (NB + 1) / 2 tiles

@@ -766,35 +766,39 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Grid barrier for co-resident CTAs.  bar[0]: arrivals, bar[1]: generation,
-// bar[2]: timeout flag.  `expected` is the number of arrivals that releases the
-// barrier (gridDim.x in normal use).
-__device__ bool grid_barrier(unsigned* bar, unsigned expected) {
+// Grid barrier for co-resident CTAs.  bar[0] counts the arrivals of the whole launch (it is
+// zeroed before the launch), bar[2] is the timeout flag.  Each CTA counts its barriers
+// (epoch); the k-th releases when bar[0] reaches k * expected (`expected` arrivals per
+// barrier, gridDim.x in normal use), so an arrival is one fenced atomic and the release needs
+// no reset and no generation word: the last arrival's own atomic is what the others see.
+// A wait that runs out sets the flag and returns false; every other CTA then runs out on its
+// own wait.
+__device__ bool grid_barrier(unsigned* bar, unsigned expected, unsigned& epoch) {
+    __shared__ int ok;
     __syncthreads();
+    epoch += 1;
     if (threadIdx.x == 0) {
-        volatile unsigned* vgen = bar + 1;
-        volatile unsigned* verr = bar + 2;
-        const unsigned gen = *vgen;
+        const unsigned target = epoch * expected;
+        int good = 1;
         __threadfence();
-        const unsigned arrived = atomicAdd(bar, 1u);
-        if (arrived == expected - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
+        const unsigned old = atomicAdd(bar, 1u);
+        if (old + 1 < target) {
+            volatile unsigned* vcount = bar;
             const unsigned long long t0 = global_ns();
-            while (*vgen == gen && *verr == 0u) {
+            while (*vcount < target) {
                 if (global_ns() - t0 > kBarrierTimeoutNs) {
                     atomicExch(bar + 2, 1u);
+                    good = 0;
                     break;
                 }
-                __nanosleep(100);
+                __nanosleep(32);
             }
         }
         __threadfence();
+        ok = good;
     }
     __syncthreads();
-    return ((volatile unsigned*)bar)[2] == 0u;
+    return ok != 0;
 }
 
 // sum of part[0..gridDim) in a fixed order; every CTA gets the same value
@@ -876,6 +880,7 @@ __global__ void __launch_bounds__(512) k_coarse_cg(long long n, const int* __res
                                                    double rtol2, int imax, unsigned extra_arrivals) {
     const unsigned nb = gridDim.x;
     const unsigned expected = nb + extra_arrivals;   // extra_arrivals > 0 only in the timeout test
+    unsigned epoch = 0;                               // grid barriers passed
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long stride = (long long)gridDim.x * blockDim.x;
     double* p_old = p;        // direction of the previous iteration (zero before the first)
@@ -892,7 +897,7 @@ __global__ void __launch_bounds__(512) k_coarse_cg(long long n, const int* __res
     s0 = block_sum(s0);
     s1 = block_sum(s1);
     if (threadIdx.x == 0) { part[blockIdx.x] = s0; part[nb + blockIdx.x] = s1; }
-    if (!grid_barrier(bar, expected)) return;
+    if (!grid_barrier(bar, expected, epoch)) return;
     double rho = grid_total(part);
     const double bb = grid_total(part + nb);
     const double tol2 = rtol2 * bb;
@@ -940,7 +945,7 @@ __global__ void __launch_bounds__(512) k_coarse_cg(long long n, const int* __res
         }
         pq = block_sum(pq);
         if (threadIdx.x == 0) part[2 * nb + blockIdx.x] = pq;
-        if (!grid_barrier(bar, expected)) return;
+        if (!grid_barrier(bar, expected, epoch)) return;
         {
             const double pq_all = grid_total(part + 2 * nb);
             if (threadIdx.x == 0) s_alpha = rho / pq_all;
@@ -958,7 +963,7 @@ __global__ void __launch_bounds__(512) k_coarse_cg(long long n, const int* __res
         t0 = block_sum(t0);
         t1 = block_sum(t1);
         if (threadIdx.x == 0) { part[blockIdx.x] = t0; part[nb + blockIdx.x] = t1; }
-        if (!grid_barrier(bar, expected)) return;
+        if (!grid_barrier(bar, expected, epoch)) return;
         const double rho_new = grid_total(part);
         rr = grid_total(part + nb);
         if (threadIdx.x == 0) s_beta = rho_new / rho;
@@ -978,17 +983,19 @@ __global__ void __launch_bounds__(512) k_coarse_cg(long long n, const int* __res
 }
 
 // Block-Jacobi preconditioned CG on the assembled coarse matrix.  CTA b owns the free rows
-// brows[bptr[b] .. bptr[b+1]) (a compact patch of the mesh, at most kBjMax rows) and holds the
-// inverse of their diagonal block in shared memory, in FP32 (symmetrised before rounding, so
-// the preconditioner is an exactly symmetric positive definite matrix).  z = M r is then local
+// brows[bptr[b] .. bptr[b+1]) (a compact patch of the mesh, at most kBjMax rows) and holds in
+// shared memory their rows of the matrix (a local CSR copy, at most nnzmax entries) and the
+// inverse of their diagonal block in FP32 (symmetrised before rounding, so the
+// preconditioner is an exactly symmetric positive definite matrix).  z = M r is then local
 // to the CTA: r, q and the previous z of its rows stay in shared memory, and only z and the
 // direction, which neighbouring rows read in the product, go through global memory (read
 // through L2).  The direction is formed on the fly inside the product from two alternating
-// buffers, as in k_coarse_cg, so an iteration has two grid barriers.  beta takes the
-// Polak-Ribiere form (r_new, z_new - z_old) / (r_old, z_old), which absorbs the FP32 rounding
-// of the block products (Golub and Ye, "Inexact preconditioned conjugate gradient method
-// with inner-outer iteration", 1999).  Partial sums: part[b] (r, z), part[nb + b] (r, r),
-// part[2 nb + b] (p, q), part[3 nb + b] (r, z_old).
+// buffers, as in k_coarse_cg, so an iteration has two grid barriers; the partial sums of a
+// phase are reduced together.  beta takes the Polak-Ribiere form (r_new, z_new - z_old) /
+// (r_old, z_old), which absorbs the FP32 rounding of the block products (Golub and Ye,
+// "Inexact preconditioned conjugate gradient method with inner-outer iteration", 1999).
+// Partial sums: part[b] (r, z), part[nb + b] (r, r), part[2 nb + b] (p, q), part[3 nb + b]
+// (r, z_old).
 __device__ __forceinline__ float warp_sumf(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -1006,23 +1013,73 @@ __device__ void bj_block_product(const float* inv, const float* rf, int nk, doub
     }
 }
 
+// Block sums (fixed tree) of NV values per thread, written by thread 0 to part[o[i] * nb + b].
+template <int NV>
+__device__ void bj_partials(const double (&v)[NV], const int (&o)[NV], double* part) {
+    __shared__ double ws[NV][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double w[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) w[i] = warp_sum(v[i]);
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) ws[i][wid] = w[i];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            double u = lane < (int)(blockDim.x >> 5) ? ws[i][lane] : 0.0;
+            u = warp_sum(u);
+            if (lane == 0) part[(size_t)o[i] * gridDim.x + blockIdx.x] = u;
+        }
+    }
+}
+
+// Totals of NV partial arrays part[o[i] * nb ...], summed in a fixed order; every CTA gets the
+// same values
+template <int NV>
+__device__ void bj_totals(const double* part, const int (&o)[NV], double (&t)[NV]) {
+    __shared__ double tot[NV];
+    if (threadIdx.x < 32) {
+        double v[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) v[i] = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32)
+#pragma unroll
+            for (int i = 0; i < NV; ++i) v[i] += ((volatile const double*)part)[(size_t)o[i] * gridDim.x + b];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            v[i] = warp_sum(v[i]);
+            if (threadIdx.x == 0) tot[i] = v[i];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NV; ++i) t[i] = tot[i];
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(512) k_coarse_bjcg(long long n, const int* __restrict__ rowptr,
                                                      const int* __restrict__ col, const double* __restrict__ vals,
                                                      const int* __restrict__ bptr, const int* __restrict__ brows,
-                                                     const float* __restrict__ binv, const double* __restrict__ b,
-                                                     double* x, double* zg, double* pa, double* pb, double* part,
-                                                     unsigned* bar, double* scal, int* flags, double rtol2, int imax,
-                                                     unsigned extra_arrivals) {
+                                                     const float* __restrict__ binv, int nnzmax,
+                                                     const double* __restrict__ b, double* x, double* zg, double* pa,
+                                                     double* pb, double* part, unsigned* bar, double* scal, int* flags,
+                                                     double rtol2, int imax, unsigned extra_arrivals) {
     extern __shared__ __align__(16) unsigned char bj_smem[];
     float* inv = reinterpret_cast<float*>(bj_smem);                  // [kBjMax][kBjMax]
     double* rs = reinterpret_cast<double*>(inv + kBjMax * kBjMax);   // r of the CTA's rows
     double* zo = rs + kBjMax;                                        // z of the previous iteration
     double* qs = zo + kBjMax;                                        // q, then the new z
     double* pn = qs + kBjMax;                                        // the new direction
-    float* rf = reinterpret_cast<float*>(pn + kBjMax);               // r rounded to FP32
+    double* lval = pn + kBjMax;                                      // [nnzmax] the rows' entries
+    float* rf = reinterpret_cast<float*>(lval + nnzmax);             // r rounded to FP32
     int* rw = reinterpret_cast<int*>(rf + kBjMax);                   // global row ids
+    int* lptr = rw + kBjMax;                                         // [kBjMax + 1] local row offsets
+    int* lcol = lptr + kBjMax + 1;                                   // [nnzmax] global column ids
     const unsigned nb = gridDim.x;
     const unsigned expected = nb + extra_arrivals;   // extra_arrivals > 0 only in the timeout test
+    unsigned epoch = 0;                               // grid barriers passed
     const int t = threadIdx.x;
     const int k0 = bptr[blockIdx.x], nk = bptr[blockIdx.x + 1] - k0;
     {
@@ -1040,26 +1097,43 @@ __global__ void __launch_bounds__(512) k_coarse_bjcg(long long n, const int* __r
         rf[t] = (float)rs[t];
         p_old[row] = 0.0;
     }
+    if (t == 0) {                                     // local row offsets (prefix sum of the lengths)
+        int acc = 0;
+        for (int k = 0; k < nk; ++k) {
+            lptr[k] = acc;
+            const int row = brows[k0 + k];
+            acc += rowptr[row + 1] - rowptr[row];
+        }
+        lptr[nk] = acc;
+    }
     __syncthreads();
+    for (int k = t >> 5; k < nk; k += blockDim.x >> 5) {   // one warp per row copies its entries
+        const int row = rw[k], a0 = rowptr[row], len = rowptr[row + 1] - a0;
+        for (int a = t & 31; a < len; a += 32) {
+            lcol[lptr[k] + a] = col[a0 + a];
+            lval[lptr[k] + a] = vals[a0 + a];
+        }
+    }
     bj_block_product(inv, rf, nk, zo);
     __syncthreads();
-    double s0 = 0, s1 = 0;
-    if (t < nk) {
-        zg[rw[t]] = zo[t];
-        s0 = rs[t] * zo[t];
-        s1 = rs[t] * rs[t];
+    {
+        double v[2] = {0.0, 0.0};
+        if (t < nk) {
+            zg[rw[t]] = zo[t];
+            v[0] = rs[t] * zo[t];
+            v[1] = rs[t] * rs[t];
+        }
+        bj_partials<2>(v, {0, 1}, part);
     }
-    s0 = block_sum(s0);
-    s1 = block_sum(s1);
-    if (t == 0) { part[blockIdx.x] = s0; part[nb + blockIdx.x] = s1; }
-    if (!grid_barrier(bar, expected)) return;
-    double rho = grid_total(part);
-    const double bb = grid_total(part + nb);
+    if (!grid_barrier(bar, expected, epoch)) return;
+    double tt[2];
+    bj_totals<2>(part, {0, 1}, tt);
+    double rho = tt[0];
+    const double bb = tt[1];
     const double tol2 = rtol2 * bb;
     int it = 0;
     double rr = bb;
     double beta = 0.0;
-    __shared__ double s_alpha, s_beta;
     while (rr > tol2 && rr > 0.0 && it < imax) {
         // q = A p for the CTA's rows, 4 lanes per row (blockDim = 4 kBjMax: one pass); p formed
         // on the fly from z and the previous direction
@@ -1068,22 +1142,11 @@ __global__ void __launch_bounds__(512) k_coarse_bjcg(long long n, const int* __r
             const int k = t >> 2, l4 = t & 3;
             double v = 0;
             if (k < nk) {
-                const int row = rw[k];
-                const int a0 = rowptr[row], a1 = rowptr[row + 1];
-                for (int a = a0 + l4; a < a1; a += 32) {      // up to 8 independent gathers per lane
-                    int c[8];
-                    double av[8], pv[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int aa = a + 4 * u;
-                        c[u] = aa < a1 ? col[aa] : -1;
-                        av[u] = aa < a1 ? vals[aa] : 0.0;
-                    }
-#pragma unroll
-                    for (int u = 0; u < 8; ++u)
-                        pv[u] = c[u] >= 0 ? __ldcg(zg + c[u]) + beta * __ldcg(p_old + c[u]) : 0.0;
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) v += av[u] * pv[u];
+                const int a1 = lptr[k + 1];
+#pragma unroll 4
+                for (int a = lptr[k] + l4; a < a1; a += 4) {
+                    const int c = lcol[a];
+                    v += lval[a] * (__ldcg(zg + c) + beta * __ldcg(p_old + c));
                 }
             }
             v += __shfl_down_sync(0xffffffffu, v, 2, 4);
@@ -1097,15 +1160,14 @@ __global__ void __launch_bounds__(512) k_coarse_bjcg(long long n, const int* __r
                 pq = pv * v;
             }
         }
-        pq = block_sum(pq);
-        if (t == 0) part[2 * nb + blockIdx.x] = pq;
-        if (!grid_barrier(bar, expected)) return;
         {
-            const double pq_all = grid_total(part + 2 * nb);
-            if (t == 0) s_alpha = rho / pq_all;
-            __syncthreads();
+            const double v[1] = {pq};
+            bj_partials<1>(v, {2}, part);
         }
-        const double alpha = s_alpha;
+        if (!grid_barrier(bar, expected, epoch)) return;
+        double ta[1];
+        bj_totals<1>(part, {2}, ta);
+        const double alpha = rho / ta[0];
         if (t < nk) {
             x[rw[t]] += alpha * pn[t];
             rs[t] -= alpha * qs[t];
@@ -1114,27 +1176,24 @@ __global__ void __launch_bounds__(512) k_coarse_bjcg(long long n, const int* __r
         __syncthreads();
         bj_block_product(inv, rf, nk, qs);       // the new z, over q (no longer needed)
         __syncthreads();
-        double t0 = 0, t1 = 0, t3 = 0;
-        if (t < nk) {
-            const double zn = qs[t];
-            t0 = rs[t] * zn;
-            t1 = rs[t] * rs[t];
-            t3 = rs[t] * zo[t];
-            zg[rw[t]] = zn;
-            zo[t] = zn;
+        {
+            double v[3] = {0.0, 0.0, 0.0};
+            if (t < nk) {
+                const double zn = qs[t];
+                v[0] = rs[t] * zn;
+                v[1] = rs[t] * rs[t];
+                v[2] = rs[t] * zo[t];
+                zg[rw[t]] = zn;
+                zo[t] = zn;
+            }
+            bj_partials<3>(v, {0, 1, 3}, part);
         }
-        t0 = block_sum(t0);
-        t1 = block_sum(t1);
-        t3 = block_sum(t3);
-        if (t == 0) { part[blockIdx.x] = t0; part[nb + blockIdx.x] = t1; part[3 * nb + blockIdx.x] = t3; }
-        if (!grid_barrier(bar, expected)) return;
-        const double rho_new = grid_total(part);
-        rr = grid_total(part + nb);
-        const double rzo = grid_total(part + 3 * nb);
-        if (t == 0) s_beta = (rho_new - rzo) / rho;
-        __syncthreads();
-        beta = s_beta;
-        rho = rho_new;
+        if (!grid_barrier(bar, expected, epoch)) return;
+        double tb[3];
+        bj_totals<3>(part, {0, 1, 3}, tb);
+        rr = tb[1];
+        beta = (tb[0] - tb[2]) / rho;
+        rho = tb[0];
         ++it;
         double* tmp = p_old;
         p_old = p_new;
@@ -1632,32 +1691,34 @@ cudaError_t coarse_cg_persistent(const Level& C, const int* rowptr, const int* c
     return cudaGetLastError();
 }
 
-size_t coarse_bj_smem() {
-    return sizeof(float) * kBjMax * kBjMax + sizeof(double) * 4 * kBjMax + sizeof(float) * kBjMax + sizeof(int) * kBjMax;
+size_t coarse_bj_smem(int nnzmax) {
+    return sizeof(float) * kBjMax * kBjMax + sizeof(double) * (4 * kBjMax + nnzmax) + sizeof(float) * kBjMax +
+           sizeof(int) * (2 * kBjMax + 1 + nnzmax);
 }
 
-// Largest number of blocks the block-Jacobi CG can take (all CTAs co-resident), 0 if none.
-int coarse_bj_capacity() {
-    static int cap = -1;
-    if (cap >= 0) return cap;
-    cap = 0;
-    if (cudaFuncSetAttribute(k_coarse_bjcg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)coarse_bj_smem()) !=
-        cudaSuccess)
-        return cap;
+// Largest number of blocks the block-Jacobi CG can take (all CTAs co-resident) when no block
+// holds more than nnzmax matrix entries, 0 if none.
+int coarse_bj_capacity(int nnzmax) {
+    const size_t smem = coarse_bj_smem(nnzmax);
+    if (smem > 200 * 1024) return 0;
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_coarse_bjcg, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
+            return 0;
+        attr = true;
+    }
     int per_sm = 0, dev = 0, sms = kSMs;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_bjcg, 4 * kBjMax, coarse_bj_smem()) !=
-        cudaSuccess)
-        return cap;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_bjcg, 4 * kBjMax, smem) != cudaSuccess) return 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cap = per_sm * sms;
-    return cap;
+    return per_sm * sms;
 }
 
 cudaError_t coarse_cg_bj(const Level& C, const double* b, double* x, double* z, double* pa, double* pb, Scratch& sc,
                          double rtol2, int imax, unsigned extra_arrivals, cudaStream_t s) {
     const int grid = C.bj_nb;
-    if (grid < 1 || grid > coarse_bj_capacity()) return cudaErrorCooperativeLaunchTooLarge;
+    int nnzmax = C.bj_nnzmax;
+    if (grid < 1 || grid > coarse_bj_capacity(nnzmax)) return cudaErrorCooperativeLaunchTooLarge;
     cudaError_t err = cudaMemsetAsync(sc.counter + 1, 0, 3 * sizeof(unsigned), s);
     if (err != cudaSuccess) return err;
     long long n = C.N;
@@ -1671,9 +1732,9 @@ cudaError_t coarse_cg_bj(const Level& C, const double* b, double* x, double* z, 
     unsigned* bar = sc.counter + 1;
     double* scal = sc.scal;
     int* flags = sc.flags;
-    void* args[] = {&n,  &rowptr, &col,  &vals, &bptr,  &brows, &binv,  &b,    &x,
-                    &z,  &pa,     &pb,   &part, &bar,   &scal,  &flags, &rtol2, &imax, &extra_arrivals};
-    err = cudaLaunchCooperativeKernel((void*)k_coarse_bjcg, grid, 4 * kBjMax, args, coarse_bj_smem(), s);
+    void* args[] = {&n, &rowptr, &col,  &vals, &bptr, &brows, &binv,  &nnzmax, &b,    &x,
+                    &z, &pa,     &pb,   &part, &bar,  &scal,  &flags, &rtol2,  &imax, &extra_arrivals};
+    err = cudaLaunchCooperativeKernel((void*)k_coarse_bjcg, grid, 4 * kBjMax, args, coarse_bj_smem(nnzmax), s);
     if (err != cudaSuccess) return err;
     return cudaGetLastError();
 }

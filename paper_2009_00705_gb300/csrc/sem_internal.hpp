@@ -81,6 +81,7 @@ struct Level {
     long long csr_nnz = 0;
     // coarse level, block-Jacobi CG: blocks of free rows (compact patches), their FP32 inverses
     int bj_nb = 0;                         // number of blocks (0: point-Jacobi CG)
+    int bj_nnzmax = 0;                     // most matrix entries in the rows of one block
     int* bj_ptr = nullptr;                 // [bj_nb + 1] offsets into bj_rows
     int* bj_rows = nullptr;                // free row ids, block by block
     float* bj_inv = nullptr;               // [bj_nb][kBjMax][kBjMax] symmetric inverse of each diagonal block
@@ -359,7 +360,7 @@ cudaError_t coarse_cg_persistent(const Level& C, const int* rowptr, const int* c
 // block-Jacobi preconditioned CG (one CTA per block of C.bj_ptr / C.bj_rows, the FP32 block
 // inverses C.bj_inv in shared memory), one cooperative launch; same flags as the above
 constexpr int kBjMax = 128;                 // rows per block at most
-int coarse_bj_capacity();                   // blocks that can be co-resident (0: none)
+int coarse_bj_capacity(int nnzmax);         // blocks that can be co-resident with nnzmax entries each
 cudaError_t coarse_cg_bj(const Level& C, const double* b, double* x, double* z, double* pa, double* pb, Scratch& sc,
                          double rtol2, int imax, unsigned extra_arrivals, cudaStream_t s);
 

@@ -582,14 +582,21 @@ sem_status build_coarse_bj(sem_handle* h) {
             if (rowptr[i + 1] > rowptr[i]) freer.push_back((int)i);
         const int nf = (int)freer.size();
         const int nb = (nf + 119) / 120;
-        if (nf == 0 || nb > coarse_bj_capacity()) return SEM_OK;       // point-Jacobi CG
+        if (nf == 0) return SEM_OK;
         std::vector<double> xyz(3 * (size_t)N);
         const sem_status cst = sem_node_coords(h, (int)h->lv.size() - 1, xyz.data());
         if (cst != SEM_OK) return cst;
         std::vector<int> ptr{0};
         rcb_split(freer, 0, nf, nb, xyz, ptr);
-        for (size_t b = 0; b + 1 < ptr.size(); ++b)
-            if (ptr[b + 1] - ptr[b] > kBjMax) return SEM_OK;
+        int nnzmax = 0;
+        for (size_t b = 0; b + 1 < ptr.size(); ++b) {
+            if (ptr[b + 1] - ptr[b] > kBjMax) return SEM_OK;               // point-Jacobi CG
+            int nnz = 0;
+            for (int k = ptr[b]; k < ptr[b + 1]; ++k) nnz += rowptr[freer[k] + 1] - rowptr[freer[k]];
+            nnzmax = std::max(nnzmax, nnz);
+        }
+        if (nb > coarse_bj_capacity(nnzmax)) return SEM_OK;               // point-Jacobi CG
+        C.bj_nnzmax = nnzmax;
         C.hbj_ptr = ptr;
         C.hbj_rows = freer;
         CK(upload(&C.bj_ptr, ptr));
