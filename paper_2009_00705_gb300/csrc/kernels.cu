@@ -1013,23 +1013,28 @@ __device__ void bj_block_product(const float* inv, const float* rf, int nk, doub
     }
 }
 
-// Block sums (fixed tree) of NV values per thread, written by thread 0 to part[o[i] * nb + b].
+// Block sums (fixed tree) of NV values per thread, of which only threads below nact hold any,
+// written by thread 0 to part[o[i] * nb + b].  The warps past nact skip their shuffle sums:
+// FP64 adds run on GB300's narrow FP64 pipe.
 template <int NV>
-__device__ void bj_partials(const double (&v)[NV], const int (&o)[NV], double* part) {
+__device__ void bj_partials(const double (&v)[NV], const int (&o)[NV], double* part, int nact) {
     __shared__ double ws[NV][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    double w[NV];
+    const int nw = (nact + 31) >> 5;
+    if (wid < nw) {
+        double w[NV];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) w[i] = warp_sum(v[i]);
-    if (lane == 0)
+        for (int i = 0; i < NV; ++i) w[i] = warp_sum(v[i]);
+        if (lane == 0)
 #pragma unroll
-        for (int i = 0; i < NV; ++i) ws[i][wid] = w[i];
+            for (int i = 0; i < NV; ++i) ws[i][wid] = w[i];
+    }
     __syncthreads();
     if (wid == 0) {
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
-            double u = lane < (int)(blockDim.x >> 5) ? ws[i][lane] : 0.0;
-            u = warp_sum(u);
+            double u = lane < nw ? ws[i][lane] : 0.0;
+            if (nw > 1) u = warp_sum(u);
             if (lane == 0) part[(size_t)o[i] * gridDim.x + blockIdx.x] = u;
         }
     }
@@ -1062,8 +1067,9 @@ __device__ void bj_totals(const double* part, const int (&o)[NV], double (&t)[NV
 __global__ void __launch_bounds__(512) k_coarse_bjcg(long long n, const int* __restrict__ rowptr,
                                                      const int* __restrict__ col, const double* __restrict__ vals,
                                                      const int* __restrict__ bptr, const int* __restrict__ brows,
-                                                     const float* __restrict__ binv, int nnzmax,
-                                                     const double* __restrict__ b, double* x, double* zg, double* pa,
+                                                     const float* __restrict__ binv, const int* __restrict__ blptr, const int* __restrict__ blidx,
+                                                     int nnzmax, const double* __restrict__ b, double* x, double* zg,
+                                                     double* pa,
                                                      double* pb, double* part, unsigned* bar, double* scal, int* flags,
                                                      double rtol2, int imax, unsigned extra_arrivals) {
     extern __shared__ __align__(16) unsigned char bj_smem[];
@@ -1097,22 +1103,12 @@ __global__ void __launch_bounds__(512) k_coarse_bjcg(long long n, const int* __r
         rf[t] = (float)rs[t];
         p_old[row] = 0.0;
     }
-    if (t == 0) {                                     // local row offsets (prefix sum of the lengths)
-        int acc = 0;
-        for (int k = 0; k < nk; ++k) {
-            lptr[k] = acc;
-            const int row = brows[k0 + k];
-            acc += rowptr[row + 1] - rowptr[row];
-        }
-        lptr[nk] = acc;
-    }
+    if (t <= nk) lptr[t] = blptr[(size_t)blockIdx.x * (kBjMax + 1) + t];   // local row offsets
     __syncthreads();
-    for (int k = t >> 5; k < nk; k += blockDim.x >> 5) {   // one warp per row copies its entries
-        const int row = rw[k], a0 = rowptr[row], len = rowptr[row + 1] - a0;
-        for (int a = t & 31; a < len; a += 32) {
-            lcol[lptr[k] + a] = col[a0 + a];
-            lval[lptr[k] + a] = vals[a0 + a];
-        }
+    for (int e = t; e < lptr[nk]; e += blockDim.x) {      // the rows' entries, by their CSR positions
+        const int g = blidx[(size_t)blockIdx.x * nnzmax + e];
+        lcol[e] = col[g];
+        lval[e] = vals[g];
     }
     bj_block_product(inv, rf, nk, zo);
     __syncthreads();
@@ -1123,7 +1119,7 @@ __global__ void __launch_bounds__(512) k_coarse_bjcg(long long n, const int* __r
             v[0] = rs[t] * zo[t];
             v[1] = rs[t] * rs[t];
         }
-        bj_partials<2>(v, {0, 1}, part);
+        bj_partials<2>(v, {0, 1}, part, nk);
     }
     if (!grid_barrier(bar, expected, epoch)) return;
     double tt[2];
@@ -1162,7 +1158,7 @@ __global__ void __launch_bounds__(512) k_coarse_bjcg(long long n, const int* __r
         }
         {
             const double v[1] = {pq};
-            bj_partials<1>(v, {2}, part);
+            bj_partials<1>(v, {2}, part, 4 * nk);     // held by the lane groups of the rows
         }
         if (!grid_barrier(bar, expected, epoch)) return;
         double ta[1];
@@ -1186,7 +1182,7 @@ __global__ void __launch_bounds__(512) k_coarse_bjcg(long long n, const int* __r
                 zg[rw[t]] = zn;
                 zo[t] = zn;
             }
-            bj_partials<3>(v, {0, 1, 3}, part);
+            bj_partials<3>(v, {0, 1, 3}, part, nk);
         }
         if (!grid_barrier(bar, expected, epoch)) return;
         double tb[3];
@@ -1198,6 +1194,158 @@ __global__ void __launch_bounds__(512) k_coarse_bjcg(long long n, const int* __r
         double* tmp = p_old;
         p_old = p_new;
         p_new = tmp;
+    }
+    if (blockIdx.x == 0 && t == 0) {
+        flags[F_CG_ITERS] = it;
+        flags[F_CG_DONE] = (rr <= tol2 || rr == 0.0) ? 1 : 0;
+        scal[S_CG_RR] = rr;
+    }
+}
+
+// The same block-Jacobi CG in its pipelined form (Ghysels and Vanroose, "Hiding global
+// synchronization latency in the preconditioned Conjugate Gradient algorithm", 2014): the
+// recurrences for w = A u, m = M w, n = A m, z, q and s let the dot products of an iteration
+// be reduced while the next product is formed, so an iteration has ONE grid barrier: read the
+// totals, n = A m (m of the neighbouring rows from the other CTAs), update the CTA's rows,
+// m = M w in shared memory, write m and the partial sums, barrier.  Only m goes through
+// global memory (two alternating buffers ma / mb); every other vector of the CTA's rows
+// stays in shared memory.  Its recurrences drift from the true residual by more rounding
+// than the plain form's, so it serves loose coarse tolerances (coarse_rtol >= 1e-6).
+// Partial sums of gamma = (r, u), (r, r) and delta = (w, u) in part[(o + i) nb + b], o = 0 and
+// 3 alternating: a CTA writes a set again only after every CTA has passed the barrier that
+// follows its reading of that set.
+__global__ void __launch_bounds__(512) k_coarse_bjpcg(long long n, const int* __restrict__ rowptr,
+                                                      const int* __restrict__ col, const double* __restrict__ vals,
+                                                      const int* __restrict__ bptr, const int* __restrict__ brows,
+                                                      const float* __restrict__ binv, const int* __restrict__ blptr, const int* __restrict__ blidx,
+                                                      int nnzmax, const double* __restrict__ b, double* x, double* ma,
+                                                      double* mb,
+                                                      double* part, unsigned* bar, double* scal, int* flags,
+                                                      double rtol2, int imax, unsigned extra_arrivals) {
+    extern __shared__ __align__(16) unsigned char bj_smem[];
+    float* inv = reinterpret_cast<float*>(bj_smem);                  // [kBjMax][kBjMax]
+    double* vr = reinterpret_cast<double*>(inv + kBjMax * kBjMax);   // r, u, w, m, z, q, s, p of the rows
+    double* vu = vr + kBjMax;
+    double* vw = vu + kBjMax;
+    double* vm = vw + kBjMax;
+    double* vz = vm + kBjMax;
+    double* vq = vz + kBjMax;
+    double* vs = vq + kBjMax;
+    double* vp = vs + kBjMax;
+    double* sn = vp + kBjMax;                                        // n = A m
+    double* lval = sn + kBjMax;                                      // [nnzmax] the rows' entries
+    float* rf = reinterpret_cast<float*>(lval + nnzmax);             // block-product input in FP32
+    int* rw = reinterpret_cast<int*>(rf + kBjMax);                   // global row ids
+    int* lptr = rw + kBjMax;                                         // [kBjMax + 1] local row offsets
+    int* lcol = lptr + kBjMax + 1;                                   // [nnzmax] global column ids
+    const unsigned nb = gridDim.x;
+    const unsigned expected = nb + extra_arrivals;   // extra_arrivals > 0 only in the timeout test
+    unsigned epoch = 0;                               // grid barriers passed
+    const int t = threadIdx.x;
+    const int k0 = bptr[blockIdx.x], nk = bptr[blockIdx.x + 1] - k0;
+    {
+        const float4* src = reinterpret_cast<const float4*>(binv + (size_t)blockIdx.x * kBjMax * kBjMax);
+        float4* dst = reinterpret_cast<float4*>(inv);
+        for (int i = t; i < kBjMax * kBjMax / 4; i += blockDim.x) dst[i] = src[i];
+    }
+    for (long long i = blockIdx.x * (long long)blockDim.x + t; i < n; i += (long long)gridDim.x * blockDim.x) x[i] = 0.0;
+    if (t < nk) {
+        const int row = brows[k0 + t];
+        rw[t] = row;
+        vr[t] = b[row];
+        rf[t] = (float)vr[t];
+        vz[t] = vq[t] = vs[t] = vp[t] = 0.0;
+    }
+    if (t <= nk) lptr[t] = blptr[(size_t)blockIdx.x * (kBjMax + 1) + t];   // local row offsets
+    __syncthreads();
+    for (int e = t; e < lptr[nk]; e += blockDim.x) {      // the rows' entries, by their CSR positions
+        const int g = blidx[(size_t)blockIdx.x * nnzmax + e];
+        lcol[e] = col[g];
+        lval[e] = vals[g];
+    }
+    bj_block_product(inv, rf, nk, vu);           // u = M r
+    __syncthreads();
+    if (t < nk) ma[rw[t]] = vu[t];
+    // out[k] = (A v)(row k) for the CTA's rows, v read from global memory, 4 lanes per row
+    auto product = [&](const double* v, double* out) {
+        const int k = t >> 2, l4 = t & 3;
+        double a = 0;
+        if (k < nk) {
+            const int a1 = lptr[k + 1];
+#pragma unroll 4
+            for (int e = lptr[k] + l4; e < a1; e += 4) a += lval[e] * __ldcg(v + lcol[e]);
+        }
+        a += __shfl_down_sync(0xffffffffu, a, 2, 4);
+        a += __shfl_down_sync(0xffffffffu, a, 1, 4);
+        if (k < nk && l4 == 0) out[k] = a;
+    };
+    if (!grid_barrier(bar, expected, epoch)) return;
+    product(ma, vw);                             // w = A u
+    __syncthreads();
+    if (t < nk) rf[t] = (float)vw[t];
+    __syncthreads();
+    bj_block_product(inv, rf, nk, vm);           // m = M w
+    __syncthreads();
+    double* mcur = mb;
+    double* mnext = ma;
+    {
+        double v[3] = {0.0, 0.0, 0.0};
+        if (t < nk) {
+            mcur[rw[t]] = vm[t];
+            v[0] = vr[t] * vu[t];
+            v[1] = vr[t] * vr[t];
+            v[2] = vw[t] * vu[t];
+        }
+        bj_partials<3>(v, {0, 1, 2}, part, nk);
+    }
+    if (!grid_barrier(bar, expected, epoch)) return;
+    double tot[3];
+    bj_totals<3>(part, {0, 1, 2}, tot);
+    const double bb = tot[1];
+    const double tol2 = rtol2 * bb;
+    double rr = bb, gamma_old = 0.0, alpha_old = 1.0;
+    int it = 0;
+    while (rr > tol2 && rr > 0.0 && it < imax) {
+        const double gamma = tot[0], delta = tot[2];
+        const double beta = it > 0 ? gamma / gamma_old : 0.0;
+        const double alpha = it > 0 ? gamma / (delta - beta * gamma / alpha_old) : gamma / delta;
+        product(mcur, sn);                       // n = A m
+        __syncthreads();
+        if (t < nk) {
+            vz[t] = sn[t] + beta * vz[t];
+            vq[t] = vm[t] + beta * vq[t];
+            vs[t] = vw[t] + beta * vs[t];
+            vp[t] = vu[t] + beta * vp[t];
+            x[rw[t]] += alpha * vp[t];
+            vr[t] -= alpha * vs[t];
+            vu[t] -= alpha * vq[t];
+            vw[t] -= alpha * vz[t];
+            rf[t] = (float)vw[t];
+        }
+        __syncthreads();
+        bj_block_product(inv, rf, nk, vm);       // m = M w
+        __syncthreads();
+        {
+            double v[3] = {0.0, 0.0, 0.0};
+            if (t < nk) {
+                mnext[rw[t]] = vm[t];
+                v[0] = vr[t] * vu[t];
+                v[1] = vr[t] * vr[t];
+                v[2] = vw[t] * vu[t];
+            }
+            if (it & 1) bj_partials<3>(v, {0, 1, 2}, part, nk);
+            else bj_partials<3>(v, {3, 4, 5}, part, nk);
+        }
+        if (!grid_barrier(bar, expected, epoch)) return;
+        if (it & 1) bj_totals<3>(part, {0, 1, 2}, tot);
+        else bj_totals<3>(part, {3, 4, 5}, tot);
+        rr = tot[1];
+        gamma_old = gamma;
+        alpha_old = alpha;
+        ++it;
+        double* tmp = mcur;
+        mcur = mnext;
+        mnext = tmp;
     }
     if (blockIdx.x == 0 && t == 0) {
         flags[F_CG_ITERS] = it;
@@ -1691,9 +1839,11 @@ cudaError_t coarse_cg_persistent(const Level& C, const int* rowptr, const int* c
     return cudaGetLastError();
 }
 
-size_t coarse_bj_smem(int nnzmax) {
-    return sizeof(float) * kBjMax * kBjMax + sizeof(double) * (4 * kBjMax + nnzmax) + sizeof(float) * kBjMax +
-           sizeof(int) * (2 * kBjMax + 1 + nnzmax);
+// shared memory of the block-Jacobi CG kernels (the pipelined one keeps 9 vectors of its rows,
+// the plain one 4)
+size_t coarse_bj_smem(int nnzmax, bool pipelined = true) {
+    return sizeof(float) * kBjMax * kBjMax + sizeof(double) * ((pipelined ? 9 : 4) * kBjMax + nnzmax) +
+           sizeof(float) * kBjMax + sizeof(int) * (2 * kBjMax + 1 + nnzmax);
 }
 
 // Largest number of blocks the block-Jacobi CG can take (all CTAs co-resident) when no block
@@ -1703,12 +1853,17 @@ int coarse_bj_capacity(int nnzmax) {
     if (smem > 200 * 1024) return 0;
     static bool attr = false;
     if (!attr) {
-        if (cudaFuncSetAttribute(k_coarse_bjcg, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
+        if (cudaFuncSetAttribute(k_coarse_bjcg, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess ||
+            cudaFuncSetAttribute(k_coarse_bjpcg, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
             return 0;
         attr = true;
     }
-    int per_sm = 0, dev = 0, sms = kSMs;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_bjcg, 4 * kBjMax, smem) != cudaSuccess) return 0;
+    int per_sm = 0, per_sm2 = 0, dev = 0, sms = kSMs;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_bjcg, 4 * kBjMax, coarse_bj_smem(nnzmax, false)) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_coarse_bjpcg, 4 * kBjMax, smem) != cudaSuccess)
+        return 0;
+    per_sm = std::min(per_sm, per_sm2);
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     return per_sm * sms;
@@ -1728,13 +1883,24 @@ cudaError_t coarse_cg_bj(const Level& C, const double* b, double* x, double* z, 
     const int* bptr = C.bj_ptr;
     const int* brows = C.bj_rows;
     const float* binv = C.bj_inv;
+    const int* blptr = C.bj_lptr;
+    const int* blidx = C.bj_lidx;
     double* part = sc.part;
     unsigned* bar = sc.counter + 1;
     double* scal = sc.scal;
     int* flags = sc.flags;
-    void* args[] = {&n, &rowptr, &col,  &vals, &bptr, &brows, &binv,  &nnzmax, &b,    &x,
-                    &z, &pa,     &pb,   &part, &bar,  &scal,  &flags, &rtol2,  &imax, &extra_arrivals};
-    err = cudaLaunchCooperativeKernel((void*)k_coarse_bjcg, grid, 4 * kBjMax, args, coarse_bj_smem(nnzmax), s);
+    // loose tolerances (>= 1e-6): the pipelined form, one grid barrier per iteration
+    const bool pipelined = rtol2 >= 1e-12;
+    if (pipelined) {
+        void* args[] = {&n,  &rowptr, &col,  &vals, &bptr, &brows, &binv,  &blptr, &blidx, &nnzmax, &b,
+                        &x,  &pa,     &pb,   &part, &bar,  &scal,  &flags, &rtol2, &imax,   &extra_arrivals};
+        err = cudaLaunchCooperativeKernel((void*)k_coarse_bjpcg, grid, 4 * kBjMax, args, coarse_bj_smem(nnzmax, true), s);
+        if (err != cudaSuccess) return err;
+        return cudaGetLastError();
+    }
+    void* args[] = {&n, &rowptr, &col, &vals, &bptr,  &brows, &binv,  &blptr, &blidx, &nnzmax, &b,  &x,
+                    &z, &pa,     &pb,  &part, &bar,   &scal,  &flags, &rtol2, &imax,   &extra_arrivals};
+    err = cudaLaunchCooperativeKernel((void*)k_coarse_bjcg, grid, 4 * kBjMax, args, coarse_bj_smem(nnzmax, false), s);
     if (err != cudaSuccess) return err;
     return cudaGetLastError();
 }

@@ -85,6 +85,8 @@ struct Level {
     int* bj_ptr = nullptr;                 // [bj_nb + 1] offsets into bj_rows
     int* bj_rows = nullptr;                // free row ids, block by block
     float* bj_inv = nullptr;               // [bj_nb][kBjMax][kBjMax] symmetric inverse of each diagonal block
+    int* bj_lptr = nullptr;                // [bj_nb][kBjMax + 1] offsets of the block's rows in its local CSR copy
+    int* bj_lidx = nullptr;                // [bj_nb][bj_nnzmax] global CSR position of each local entry
     std::vector<int> hbj_ptr, hbj_rows;
     // additive Schwarz smoother (smoother = ASM; every level but the coarsest)
     int asm_nmax = 0;                      // largest subdomain (free nodes)

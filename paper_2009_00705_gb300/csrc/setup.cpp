@@ -596,11 +596,22 @@ sem_status build_coarse_bj(sem_handle* h) {
             nnzmax = std::max(nnzmax, nnz);
         }
         if (nb > coarse_bj_capacity(nnzmax)) return SEM_OK;               // point-Jacobi CG
+        std::vector<int> lptr((ptr.size() - 1) * (kBjMax + 1), 0), lidx((ptr.size() - 1) * (size_t)nnzmax, 0);
+        for (size_t b = 0; b + 1 < ptr.size(); ++b) {
+            int acc = 0;
+            for (int k = ptr[b]; k < ptr[b + 1]; ++k) {
+                lptr[b * (kBjMax + 1) + (k - ptr[b])] = acc;
+                for (int a = rowptr[freer[k]]; a < rowptr[freer[k] + 1]; ++a) lidx[b * (size_t)nnzmax + acc++] = a;
+            }
+            lptr[b * (kBjMax + 1) + (ptr[b + 1] - ptr[b])] = acc;
+        }
         C.bj_nnzmax = nnzmax;
         C.hbj_ptr = ptr;
         C.hbj_rows = freer;
         CK(upload(&C.bj_ptr, ptr));
         CK(upload(&C.bj_rows, freer));
+        CK(upload(&C.bj_lptr, lptr));
+        CK(upload(&C.bj_lidx, lidx));
         CK(dalloc(&C.bj_inv, (size_t)(ptr.size() - 1) * kBjMax * kBjMax));
     }
     const int nb = (int)C.hbj_ptr.size() - 1;

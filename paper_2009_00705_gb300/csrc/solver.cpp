@@ -702,7 +702,7 @@ sem_status alloc_element_matrices(sem_handle* h) {
 
 void free_level(Level& L) {
     void* ptrs[] = {L.map, L.G, L.G32, L.G16, L.G16T, L.lift_elems, L.dinv, L.dinv32, L.dir, L.ref64.m, L.ref32.m, L.It64, L.Iz64, L.It32, L.Iz32, L.gref,
-                    L.csr_rowptr, L.csr_col, L.csr_val, L.csr_slot, L.dss_ptr, L.dss_slot, L.ye64, L.csr_eptr, L.csr_eidx, L.csr_ev, L.Ae64, L.Adf, L.bj_ptr, L.bj_rows, L.bj_inv,
+                    L.csr_rowptr, L.csr_col, L.csr_val, L.csr_slot, L.dss_ptr, L.dss_slot, L.ye64, L.csr_eptr, L.csr_eidx, L.csr_ev, L.Ae64, L.Adf, L.bj_ptr, L.bj_rows, L.bj_inv, L.bj_lptr, L.bj_lidx,
                     L.owner, L.wmult, L.wmult32, L.u, L.f, L.y, L.d, L.u32, L.f32, L.y32, L.d32};
     for (void* p : ptrs)
         if (p) cudaFree(p);

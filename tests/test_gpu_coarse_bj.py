@@ -1,6 +1,8 @@
 """The block-Jacobi preconditioned coarse CG (sem_options.coarse_bj): the coarse solve of a
 single-level order-1 handle against a sparse direct solve of the oracle's free-node matrix
-(coarse_rtol 1e-12, so 1e-9 relative), on a sigma-prism box and on a hull tank; fewer
+(coarse_rtol 1e-12, so 1e-9 relative), on a sigma-prism box and on a hull tank; the
+pipelined form that loose tolerances take (coarse_rtol >= 1e-6) through the true residual
+of the oracle's matrix; fewer
 coarse iterations than the point-Jacobi CG at the default tolerance with the same FP64
 solution of the full problem; and the block inverses follow a surface update (strategy III
 reassembles the coarse matrix: the next solve equals a fresh handle's)."""
@@ -46,6 +48,27 @@ def test_coarse_solve_matches_sparse_direct_solve(sem, mesh_fn, bj):
         got = z.cpu().numpy()
         assert np.abs(got - exact).max() <= 1e-9 * np.abs(exact).max()
         assert np.all(got[lev.dirichlet] == 0.0)
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("mesh_fn", [lambda: W.config_box3d(24, 4), lambda: W.hull_tank(8)])
+def test_pipelined_coarse_solve_reaches_its_tolerance(sem, mesh_fn):
+    mesh = mesh_fn()
+    prob = Problem(mesh, [1])
+    lev = prob.levels[0]
+    A = prob.free_matrix(0).tocsr()
+    s = sem.Solver(mesh, 1, eta_nodal=prob.eta_nodal, levels=[1], coarse_rtol=1e-6, coarse_bj=1)
+    try:
+        for seed in (34, 35):
+            r = np.zeros(lev.N)
+            r[lev.free] = W.random_vector(len(lev.free), seed=seed)
+            z = torch.zeros(lev.N, dtype=torch.float64, device="cuda")
+            s.vcycle(torch.tensor(r, device="cuda"), z)
+            torch.cuda.synchronize()
+            got = z.cpu().numpy()
+            res = np.linalg.norm(A @ got[lev.free] - r[lev.free]) / np.linalg.norm(r[lev.free])
+            assert res <= 2e-6, res
     finally:
         s.close()
 
