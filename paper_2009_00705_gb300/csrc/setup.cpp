@@ -506,9 +506,10 @@ sem_status build_coarse_gradients(sem_handle* h) {
     return reassemble_coarse(h);
 }
 
-// Recursive coordinate bisection of idx[lo, hi) into `parts` contiguous runs (the longer
-// horizontal extent is cut, in proportion to the parts on each side); ptr gets the run ends.
-void rcb_split(std::vector<int>& idx, int lo, int hi, int parts, const std::vector<double>& xyz,
+// Recursive coordinate bisection of idx[lo, hi) into `parts` contiguous runs (the longer extent
+// of the first two coordinates is cut, in proportion to the parts on each side; xyz holds `st`
+// coordinates per node, the third, if any, breaks ties); ptr gets the run ends.
+void rcb_split(std::vector<int>& idx, int lo, int hi, int parts, const std::vector<double>& xyz, int st,
                std::vector<int>& ptr) {
     if (parts <= 1 || hi - lo <= 1) {
         ptr.push_back(hi);
@@ -517,18 +518,18 @@ void rcb_split(std::vector<int>& idx, int lo, int hi, int parts, const std::vect
     double mn[2] = {1e300, 1e300}, mx[2] = {-1e300, -1e300};
     for (int i = lo; i < hi; ++i)
         for (int a = 0; a < 2; ++a) {
-            mn[a] = std::min(mn[a], xyz[3 * (size_t)idx[i] + a]);
-            mx[a] = std::max(mx[a], xyz[3 * (size_t)idx[i] + a]);
+            mn[a] = std::min(mn[a], xyz[st * (size_t)idx[i] + a]);
+            mx[a] = std::max(mx[a], xyz[st * (size_t)idx[i] + a]);
         }
     const int ax = (mx[1] - mn[1] > mx[0] - mn[0]) ? 1 : 0;
     std::stable_sort(idx.begin() + lo, idx.begin() + hi, [&](int a, int b) {
-        const double va = xyz[3 * (size_t)a + ax], vb = xyz[3 * (size_t)b + ax];
-        return va < vb || (va == vb && xyz[3 * (size_t)a + 2] < xyz[3 * (size_t)b + 2]);
+        const double va = xyz[st * (size_t)a + ax], vb = xyz[st * (size_t)b + ax];
+        return va < vb || (va == vb && st > 2 && xyz[st * (size_t)a + 2] < xyz[st * (size_t)b + 2]);
     });
     const int p1 = parts / 2;
     const int cut = lo + (int)std::llround((double)(hi - lo) * p1 / parts);
-    rcb_split(idx, lo, cut, p1, xyz, ptr);
-    rcb_split(idx, cut, hi, parts - p1, xyz, ptr);
+    rcb_split(idx, lo, cut, p1, xyz, st, ptr);
+    rcb_split(idx, cut, hi, parts - p1, xyz, st, ptr);
 }
 
 // Inverse of the SPD matrix a (n x n, row major) by Cholesky, in place; false if a pivot is
@@ -587,7 +588,7 @@ sem_status build_coarse_bj(sem_handle* h) {
         const sem_status cst = sem_node_coords(h, (int)h->lv.size() - 1, xyz.data());
         if (cst != SEM_OK) return cst;
         std::vector<int> ptr{0};
-        rcb_split(freer, 0, nf, nb, xyz, ptr);
+        rcb_split(freer, 0, nf, nb, xyz, h->dim == 3 ? 3 : 2, ptr);   // 2D: (x, z) per node
         int nnzmax = 0;
         for (size_t b = 0; b + 1 < ptr.size(); ++b) {
             if (ptr[b + 1] - ptr[b] > kBjMax) return SEM_OK;               // point-Jacobi CG
