@@ -208,6 +208,13 @@ typedef struct {
                                    applied from shared memory, one CTA per patch (about half the CG
                                    iterations of point Jacobi); used when every patch fits one co-resident
                                    CTA and the handle is not batched.  0 = point-Jacobi CG */
+    int fused_small;            /* 1 (default) = small FP64 problems (finest level at most 8,192 nodes
+                                   and E Np^2 <= 2^18, FGMRES or PCG outside, Chebyshev smoother, an
+                                   assembled coarse level of at most 2,048 nodes, not batched) are solved
+                                   in one kernel launch by one CTA: lifting, outer iteration and V-cycle
+                                   with every level's operator as FP64 element matrices and the coarse
+                                   level solved directly by a dense inverse formed at setup (coarse_rtol
+                                   does not apply).  0 = the multi-kernel path */
 } sem_options;
 
 typedef struct {

@@ -49,7 +49,7 @@ class SemOptions(Structure):
                 ("smoother", c_int), ("mlp_hidden", c_int), ("mlp_seed", ctypes.c_ulonglong), ("batch", c_int),
                 ("autotune", c_int), ("learned_tau", c_double), ("surface_ops", c_int), ("batch_mode", c_int),
                 ("asm_overlap", c_int), ("level_pz", c_int * SEM_MAX_LEVELS), ("deterministic", c_int),
-                ("elem_matrices", c_int), ("coarse_bj", c_int)]
+                ("elem_matrices", c_int), ("coarse_bj", c_int), ("fused_small", c_int)]
 
 
 class SemStats(Structure):

@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libsem_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
          "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]
-SOURCES = ["refelem.cpp", "setup.cpp", "solver.cpp", "kernels.cu", "apply_prism.cu", "apply_prism_tc.cu", "apply_prism_t5.cu", "apply_elem_df.cu", "mlp.cu", "mlp_gemm_t5.cu", "fnpf.cu", "schwarz.cu"]
+SOURCES = ["refelem.cpp", "setup.cpp", "solver.cpp", "kernels.cu", "apply_prism.cu", "apply_prism_tc.cu", "apply_prism_t5.cu", "apply_elem_df.cu", "small_solve.cu", "mlp.cu", "mlp_gemm_t5.cu", "fnpf.cu", "schwarz.cu"]
 
 
 def nvcc() -> str:

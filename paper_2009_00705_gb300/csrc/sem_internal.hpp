@@ -200,6 +200,7 @@ struct sem_handle {
     long long asm_launches = 0;
     double lift_ms = 0.0;
     size_t auto_elem_bytes = 0;     // element matrices allocated by the auto rule (process-wide budget)
+    void* small = nullptr;          // plan of the one-launch solve of small problems (small_solve.cu)
     long long lift_launches = 0;
     long long fine_applies = 0;
     long long launches = 0;        // kernels launched since the counter was reset
@@ -209,6 +210,35 @@ struct sem_handle {
 };
 
 namespace sem {
+
+// Chebyshev coefficients of one sweep (three-term recurrence on [a, b]).
+struct Cheb {
+    double c0;               // first step: d = c0 D^{-1} r
+    double c1[16], c2[16];   // step j >= 1: d = c1 d + c2 D^{-1} r
+};
+
+inline Cheb cheb_coeffs(double lam, const sem_options& o) {
+    Cheb c{};
+    const double b = o.cheb_hi * lam, a = o.cheb_lo * b;
+    const double theta = 0.5 * (b + a), delta = 0.5 * (b - a), sigma = theta / delta;
+    c.c0 = 1.0 / theta;
+    double rho = 1.0 / sigma;
+    for (int j = 1; j < o.k_cheb && j < 16; ++j) {
+        const double rn = 1.0 / (2.0 * sigma - rho);
+        c.c1[j] = rn * rho;
+        c.c2[j] = 2.0 * rn / delta;
+        rho = rn;
+    }
+    return c;
+}
+
+// small_solve.cu: the whole solve of a small FP64 problem in one launch (sem_options.fused_small)
+sem_status build_small_plan(sem_handle* h);
+void free_small_plan(sem_handle* h);
+sem_status small_solve(sem_handle* h, const double* rhs, const double* eta, double rtol, double* phi, sem_stats* st,
+                       cudaStream_t s);
+// setup.cpp: inverse of an SPD matrix (n x n, row major) in place by Cholesky; false if not SPD
+bool spd_inverse(std::vector<double>& a, int n);
 
 // ---------------------------------------------------------------- kernels.cu
 int reduce_blocks();

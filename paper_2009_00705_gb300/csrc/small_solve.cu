@@ -1,0 +1,608 @@
+// The whole Laplace solve of a small problem in one CTA and one launch: lifting of the
+// Dirichlet data (Eq. laplaceproblem), the outer FGMRES(m) or PCG iteration, and its
+// preconditioner, the p-multigrid V-cycle of Algorithm 1 with Chebyshev-Jacobi sweeps and
+// the direct coarse solve that the algorithm names (a dense inverse of the order-1
+// free-node matrix, formed at setup).  FP64 throughout.
+//
+// Launch latency, not bandwidth, bounds such problems: the 2D slice of 128 triangles at
+// P = 4 (1,040 free nodes) takes a few hundred kernels per FGMRES iteration on the
+// multi-kernel path.  Here every level's operator is a set of precomputed FP64 element
+// matrices (y = sum_e Q_e^T A_e Q_e x with the sums in shared memory), the transfers use
+// the reference interpolation matrix of each level pair, every vector stays in global
+// memory that only this CTA touches (L1/L2-resident), and the phases are separated by
+// CTA barriers.  The host reads the result once.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sem_internal.hpp"
+
+namespace sem {
+
+struct SmallLevel {
+    int N, E, Np, Npc;                 // nodes, elements, nodes per element (this and the next coarser level)
+    const int* map;                    // [E][Np], negative for Dirichlet nodes (-id - 1)
+    const int* mapc;                   // [E][Npc] of the next coarser level (null on the coarsest)
+    const double* Ae;                  // [E][Np][Np] symmetric FP64 element matrices
+    const double* dinv;                // [N] inverse assembled diagonal, 0 at Dirichlet nodes
+    const double* wmult;               // [N] inverse multiplicities (restriction weights)
+    const unsigned char* owner;        // [E][Np] the element that writes a prolonged node
+    const double* I;                   // [Np][Npc] interpolation from the next coarser level
+    double c0, c1[16], c2[16];         // Chebyshev coefficients of the level
+    double *u, *f, *y, *d;             // work vectors [N]
+};
+
+struct SmallPlan {
+    int nl, k_cheb, nu1, nu2, outer, m, imax, nd, Nc;
+    const long long* dir;              // Dirichlet node ids of the finest level
+    const double* Cinv;                // [Nc][Nc] inverse of the coarse free-node matrix (zero at Dirichlet)
+    double *V, *Z, *r, *q, *fr, *x, *p, *z;
+    double* out;                       // iterations, fnorm, final residual, status, V-cycles, finest applies
+    SmallLevel lv[SEM_MAX_LEVELS];
+};
+
+struct SmallHost {
+    SmallPlan plan{};                  // host copy (device pointers)
+    SmallPlan* dplan = nullptr;        // device copy
+    std::vector<void*> owned;          // device buffers of the plan
+    size_t smem = 0;
+    int N0 = 0;
+};
+
+namespace {
+
+constexpr int kSmallThreads = 1024;
+constexpr int kSmallMaxN = 8192;                 // finest nodes (the shared-memory accumulator)
+constexpr long long kSmallMaxWork = 1LL << 18;   // E Np^2 of the finest level: one apply on one SM
+
+__device__ __forceinline__ double sw_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// sum over the CTA of one value per thread (fixed order); every thread gets the total
+__device__ double cta_sum(double v, double* red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = sw_sum(v);
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        double w = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+        w = sw_sum(w);
+        if (lane == 0) red[32] = w;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+__device__ double cta_dot(const double* a, const double* b, int n, double* red) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v += a[i] * b[i];
+    return cta_sum(v, red);
+}
+
+// y = A x on a level (free rows; y = 0 at Dirichlet nodes); lift: x also at the Dirichlet
+// nodes (the lifting product A_FD x_D), else x there counts as zero
+__device__ void s_apply(const SmallLevel& L, const double* x, double* y, bool lift, double* acc) {
+    for (int i = threadIdx.x; i < L.N; i += blockDim.x) acc[i] = 0.0;
+    __syncthreads();
+    const int rows = L.E * L.Np;
+    for (int t = threadIdx.x; t < rows; t += blockDim.x) {
+        const int mi = L.map[t];
+        if (mi < 0) continue;
+        const int e = t / L.Np, i = t - e * L.Np;
+        const int* me = L.map + (size_t)e * L.Np;
+        const double* A = L.Ae + (size_t)e * L.Np * L.Np + i;      // column i = row i (symmetric)
+        double v = 0.0;
+        for (int j = 0; j < L.Np; ++j) {
+            const int mj = me[j];
+            const double xj = mj >= 0 ? x[mj] : (lift ? x[-mj - 1] : 0.0);
+            v = fma(A[(size_t)j * L.Np], xj, v);
+        }
+        atomicAdd(&acc[mi], v);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < L.N; i += blockDim.x) y[i] = acc[i];
+    __syncthreads();
+}
+
+// one Chebyshev-Jacobi sweep of k_cheb steps (u = 0 on entry when zero_init)
+__device__ void s_sweep(const SmallLevel& L, int k, const double* f, double* u, bool zero_init, double* acc) {
+    if (zero_init) {
+        for (int i = threadIdx.x; i < L.N; i += blockDim.x) {
+            const double v = L.c0 * L.dinv[i] * f[i];
+            L.d[i] = v;
+            u[i] = v;
+        }
+        __syncthreads();
+    } else {
+        s_apply(L, u, L.y, false, acc);
+        for (int i = threadIdx.x; i < L.N; i += blockDim.x) {
+            const double v = L.c0 * L.dinv[i] * (f[i] - L.y[i]);
+            L.d[i] = v;
+            u[i] += v;
+        }
+        __syncthreads();
+    }
+    for (int j = 1; j < k; ++j) {
+        s_apply(L, u, L.y, false, acc);
+        for (int i = threadIdx.x; i < L.N; i += blockDim.x) {
+            const double v = L.c1[j] * L.d[i] + L.c2[j] * L.dinv[i] * (f[i] - L.y[i]);
+            L.d[i] = v;
+            u[i] += v;
+        }
+        __syncthreads();
+    }
+}
+
+// fc = R (f - y) onto the next coarser level C (R = P^T, fine values weighted by 1/multiplicity)
+__device__ void s_restrict(const SmallLevel& F, const SmallLevel& C, const double* f, const double* y, double* fc,
+                           double* acc) {
+    for (int i = threadIdx.x; i < C.N; i += blockDim.x) acc[i] = 0.0;
+    __syncthreads();
+    const int rows = F.E * F.Npc;
+    for (int t = threadIdx.x; t < rows; t += blockDim.x) {
+        const int mc = F.mapc[t];
+        if (mc < 0) continue;
+        const int e = t / F.Npc, nc = t - e * F.Npc;
+        const int* mf = F.map + (size_t)e * F.Np;
+        double v = 0.0;
+        for (int nf = 0; nf < F.Np; ++nf) {
+            const int m = mf[nf];
+            if (m >= 0) v = fma(F.I[(size_t)nf * F.Npc + nc], F.wmult[m] * (f[m] - y[m]), v);
+        }
+        atomicAdd(&acc[mc], v);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < C.N; i += blockDim.x) fc[i] = acc[i];
+    __syncthreads();
+}
+
+// uf += P uc from the next coarser level (each fine node written by its owner element)
+__device__ void s_prolong(const SmallLevel& F, const double* uc, double* uf) {
+    const int rows = F.E * F.Np;
+    for (int t = threadIdx.x; t < rows; t += blockDim.x) {
+        const int m = F.map[t];
+        if (m < 0 || !F.owner[t]) continue;
+        const int e = t / F.Np, nf = t - e * F.Np;
+        const int* mc = F.mapc + (size_t)e * F.Npc;
+        double v = 0.0;
+        for (int nc = 0; nc < F.Npc; ++nc) {
+            const int c = mc[nc];
+            if (c >= 0) v = fma(F.I[(size_t)nf * F.Npc + nc], uc[c], v);
+        }
+        uf[m] += v;
+    }
+    __syncthreads();
+}
+
+// u = A_c^{-1} f on the coarsest level (the dense inverse is symmetric: column i read as row i)
+__device__ void s_coarse(const SmallPlan& P, const double* f, double* u) {
+    for (int i = threadIdx.x; i < P.Nc; i += blockDim.x) {
+        double v = 0.0;
+        for (int j = 0; j < P.Nc; ++j) v = fma(P.Cinv[(size_t)j * P.Nc + i], f[j], v);
+        u[i] = v;
+    }
+    __syncthreads();
+}
+
+// z = M^{-1} f: Algorithm 1 with u = 0 on entry at every level
+__device__ void s_vcycle(const SmallPlan& P, const double* f0, double* u0, double* acc) {
+    const int nl = P.nl;
+    if (nl == 1) {
+        s_coarse(P, f0, u0);
+        return;
+    }
+    for (int li = 0; li + 1 < nl; ++li) {
+        const SmallLevel& L = P.lv[li];
+        const double* f = li == 0 ? f0 : L.f;
+        double* u = li == 0 ? u0 : L.u;
+        for (int m = 0; m < P.nu1; ++m) s_sweep(L, P.k_cheb, f, u, m == 0, acc);
+        if (P.nu1 == 0) {
+            for (int i = threadIdx.x; i < L.N; i += blockDim.x) u[i] = 0.0;
+            __syncthreads();
+        }
+        s_apply(L, u, L.y, false, acc);
+        s_restrict(L, P.lv[li + 1], f, L.y, P.lv[li + 1].f, acc);
+    }
+    s_coarse(P, P.lv[nl - 1].f, P.lv[nl - 1].u);
+    for (int li = nl - 2; li >= 0; --li) {
+        const SmallLevel& L = P.lv[li];
+        const double* f = li == 0 ? f0 : L.f;
+        double* u = li == 0 ? u0 : L.u;
+        s_prolong(L, P.lv[li + 1].u, u);
+        for (int m = 0; m < P.nu2; ++m) s_sweep(L, P.k_cheb, f, u, false, acc);
+    }
+}
+
+// The solve: lifting, then FGMRES(m) (classical Gram-Schmidt twice, Givens rotations,
+// restarts) or PCG, each preconditioned by one V-cycle, to ||f - A u|| <= rtol ||f|| + atol.
+// Shared memory: the accumulator of the element sums [N0], reduction scratch, and the
+// Hessenberg matrix, rotations and right-hand side of FGMRES.
+__global__ void __launch_bounds__(kSmallThreads) k_small_solve(const SmallPlan* __restrict__ plan,
+                                                              const double* __restrict__ rhs,
+                                                              const double* __restrict__ eta, double* phi,
+                                                              double rtol, double atol) {
+    __shared__ SmallPlan P;
+    __shared__ double sc[8];                   // broadcast scalars
+    __shared__ int si[4];
+    {
+        const int* src = reinterpret_cast<const int*>(plan);
+        int* dst = reinterpret_cast<int*>(&P);
+        for (int i = threadIdx.x; i < (int)(sizeof(SmallPlan) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    const SmallLevel& L0 = P.lv[0];
+    const int N = L0.N, m = P.m;
+    extern __shared__ __align__(16) double ssm[];
+    double* acc = ssm;                         // [N0]
+    double* red = acc + N;                     // [40]
+    double* H = red + 40;                      // [(m + 1) m]
+    double* cs = H + (size_t)(m + 1) * m;      // [m]
+    double* sn = cs + m;                       // [m]
+    double* g = sn + m;                        // [m + 1]
+    double* yv = g + m + 1;                    // [m]
+    double* hk = yv + m;                       // [2 (m + 1)] the two Gram-Schmidt passes
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
+    int vcycles = 0, applies = 0;
+
+    // lifting: f = rhs - A_FD phi_D on the free nodes
+    for (int i = t; i < N; i += blockDim.x) P.x[i] = 0.0;
+    __syncthreads();
+    for (int k = t; k < P.nd; k += blockDim.x) P.x[P.dir[k]] = eta[k];
+    __syncthreads();
+    s_apply(L0, P.x, P.q, true, acc);
+    for (int i = t; i < N; i += blockDim.x) P.fr[i] = (rhs != nullptr ? rhs[i] : 0.0) - P.q[i];
+    __syncthreads();
+    for (int k = t; k < P.nd; k += blockDim.x) P.fr[P.dir[k]] = 0.0;
+    __syncthreads();
+    const double fnorm = sqrt(cta_dot(P.fr, P.fr, N, red));
+    const double thr = rtol * fnorm + atol;
+    for (int i = t; i < N; i += blockDim.x) phi[i] = 0.0;
+    __syncthreads();
+    int status = isfinite(fnorm) ? (int)SEM_OK : (int)SEM_NAN;
+    int it = 0;
+    double res = fnorm;
+    if (status == SEM_OK && P.outer == SEM_OUTER_FGMRES) {
+        for (int i = t; i < N; i += blockDim.x) P.r[i] = P.fr[i];
+        __syncthreads();
+        double beta = fnorm;
+        while (beta > thr) {
+            if (it >= P.imax) { status = SEM_NOT_CONVERGED; break; }
+            for (int i = t; i < N; i += blockDim.x) P.V[i] = P.r[i] / beta;
+            for (int i = t; i < (m + 1) * m; i += blockDim.x) H[i] = 0.0;
+            for (int i = t; i <= m; i += blockDim.x) g[i] = 0.0;
+            __syncthreads();
+            if (t == 0) g[0] = beta;
+            int j = 0;
+            while (j < m && it < P.imax) {
+                const double* vj = P.V + (size_t)j * N;
+                double* zj = P.Z + (size_t)j * N;
+                double* w = P.V + (size_t)(j + 1) * N;
+                s_vcycle(P, vj, zj, acc);
+                ++vcycles;
+                s_apply(L0, zj, w, false, acc);
+                ++applies;
+                for (int pass = 0; pass < 2; ++pass) {           // classical Gram-Schmidt, twice
+                    for (int k = wid; k <= j; k += nw) {
+                        const double* vk = P.V + (size_t)k * N;
+                        double v = 0.0;
+                        for (int i = lane; i < N; i += 32) v += vk[i] * w[i];
+                        v = sw_sum(v);
+                        if (lane == 0) hk[pass * (m + 1) + k] = v;
+                    }
+                    __syncthreads();
+                    for (int i = t; i < N; i += blockDim.x) {
+                        double wi = w[i];
+                        for (int k = 0; k <= j; ++k) wi -= hk[pass * (m + 1) + k] * P.V[(size_t)k * N + i];
+                        w[i] = wi;
+                    }
+                    __syncthreads();
+                }
+                const double hn = sqrt(cta_dot(w, w, N, red));
+                if (t == 0) {
+                    for (int k = 0; k <= j; ++k) H[(size_t)k * m + j] = hk[k] + hk[m + 1 + k];
+                    H[(size_t)(j + 1) * m + j] = hn;
+                    for (int k = 0; k < j; ++k) {
+                        const double a = cs[k] * H[(size_t)k * m + j] + sn[k] * H[(size_t)(k + 1) * m + j];
+                        H[(size_t)(k + 1) * m + j] = -sn[k] * H[(size_t)k * m + j] + cs[k] * H[(size_t)(k + 1) * m + j];
+                        H[(size_t)k * m + j] = a;
+                    }
+                    const double den = hypot(H[(size_t)j * m + j], H[(size_t)(j + 1) * m + j]);
+                    cs[j] = H[(size_t)j * m + j] / den;
+                    sn[j] = H[(size_t)(j + 1) * m + j] / den;
+                    H[(size_t)j * m + j] = den;
+                    H[(size_t)(j + 1) * m + j] = 0.0;
+                    g[j + 1] = -sn[j] * g[j];
+                    g[j] = cs[j] * g[j];
+                    sc[0] = fabs(g[j + 1]);
+                }
+                if (hn > 0.0)
+                    for (int i = t; i < N; i += blockDim.x) w[i] /= hn;
+                __syncthreads();
+                ++j;
+                ++it;
+                res = sc[0];
+                if (!isfinite(hn)) { status = SEM_NAN; break; }
+                if (res <= thr || hn == 0.0) break;
+            }
+            if (status != SEM_OK) break;
+            if (t == 0)
+                for (int k = j - 1; k >= 0; --k) {
+                    double v = g[k];
+                    for (int l = k + 1; l < j; ++l) v -= H[(size_t)k * m + l] * yv[l];
+                    yv[k] = v / H[(size_t)k * m + k];
+                }
+            __syncthreads();
+            for (int i = t; i < N; i += blockDim.x) {
+                double u = phi[i];
+                for (int k = 0; k < j; ++k) u += yv[k] * P.Z[(size_t)k * N + i];
+                phi[i] = u;
+            }
+            __syncthreads();
+            s_apply(L0, phi, P.q, false, acc);
+            ++applies;
+            for (int i = t; i < N; i += blockDim.x) P.r[i] = P.fr[i] - P.q[i];
+            __syncthreads();
+            beta = sqrt(cta_dot(P.r, P.r, N, red));
+            res = beta;
+            if (!isfinite(beta)) { status = SEM_NAN; break; }
+        }
+    } else if (status == SEM_OK) {                          // PCG
+        for (int i = t; i < N; i += blockDim.x) P.r[i] = P.fr[i];
+        __syncthreads();
+        if (res > thr) {
+            s_vcycle(P, P.r, P.z, acc);
+            ++vcycles;
+            for (int i = t; i < N; i += blockDim.x) P.p[i] = P.z[i];
+            __syncthreads();
+            double rz = cta_dot(P.z, P.r, N, red);
+            for (;;) {
+                if (it >= P.imax) { status = SEM_NOT_CONVERGED; break; }
+                s_apply(L0, P.p, P.q, false, acc);
+                ++applies;
+                const double pq = cta_dot(P.p, P.q, N, red);
+                const double alpha = rz / pq;
+                for (int i = t; i < N; i += blockDim.x) {
+                    phi[i] += alpha * P.p[i];
+                    P.r[i] -= alpha * P.q[i];
+                }
+                __syncthreads();
+                ++it;
+                res = sqrt(cta_dot(P.r, P.r, N, red));
+                if (!isfinite(res)) { status = SEM_NAN; break; }
+                if (!(pq > 0.0)) { status = SEM_BREAKDOWN; break; }
+                if (res <= thr) break;
+                s_vcycle(P, P.r, P.z, acc);
+                ++vcycles;
+                const double rzn = cta_dot(P.z, P.r, N, red);
+                const double beta = rzn / rz;
+                rz = rzn;
+                for (int i = t; i < N; i += blockDim.x) P.p[i] = P.z[i] + beta * P.p[i];
+                __syncthreads();
+            }
+        }
+    }
+    for (int k = t; k < P.nd; k += blockDim.x) phi[P.dir[k]] = eta[k];
+    if (t == 0) {
+        P.out[0] = it;
+        P.out[1] = fnorm;
+        P.out[2] = res;
+        P.out[3] = status;
+        P.out[4] = vcycles;
+        P.out[5] = applies;
+    }
+    (void)si;
+}
+
+}  // namespace
+
+namespace {
+
+template <typename T>
+cudaError_t small_alloc(SmallHost& S, T** p, size_t count) {
+    void* q = nullptr;
+    const cudaError_t e = cudaMalloc(&q, sizeof(T) * std::max<size_t>(count, 1));
+    if (e != cudaSuccess) return e;
+    S.owned.push_back(q);
+    *p = static_cast<T*>(q);
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t small_upload(SmallHost& S, T** p, const std::vector<T>& h) {
+    cudaError_t e = small_alloc(S, p, h.size());
+    if (e == cudaSuccess && !h.empty()) e = cudaMemcpy(*p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice);
+    return e;
+}
+
+void small_release(SmallHost* S) {
+    if (S == nullptr) return;
+    for (void* q : S->owned) cudaFree(q);
+    delete S;
+}
+
+}  // namespace
+
+void free_small_plan(sem_handle* h) {
+    small_release(static_cast<SmallHost*>(h->small));
+    h->small = nullptr;
+}
+
+// The one-launch plan of a small problem (sem_options.fused_small): FP64 handles with the
+// Chebyshev smoother, FGMRES or PCG outside, not batched, whose finest level has at most
+// kSmallMaxN nodes and E Np^2 <= kSmallMaxWork, and whose coarse level is assembled (at most
+// 2,048 nodes).  Anything else keeps the multi-kernel path.  Rebuilt when the geometry changes.
+sem_status build_small_plan(sem_handle* h) {
+    free_small_plan(h);
+    const sem_options& o = h->opts;
+    // (debug_barrier_extra targets the coarse CG kernel of the multi-kernel path)
+    if (!o.fused_small || o.precision != SEM_PREC_FP64 || o.smoother != SEM_SMOOTH_CHEBYSHEV || o.batch != 0 ||
+        (o.outer != SEM_OUTER_FGMRES && o.outer != SEM_OUTER_PCG) || o.k_cheb > 16 || o.debug_barrier_extra != 0)
+        return SEM_OK;
+    const int nl = (int)h->lv.size();
+    const Level& L0 = h->lv[0];
+    const Level& Cl = h->lv[nl - 1];
+    if (L0.N > kSmallMaxN || (long long)L0.E * L0.Np * L0.Np > kSmallMaxWork || Cl.csr_val == nullptr || Cl.N > 2048)
+        return SEM_OK;
+    SmallHost* S = new SmallHost();
+    SmallPlan& P = S->plan;
+    P.nl = nl;
+    P.k_cheb = o.k_cheb;
+    P.nu1 = o.nu1;
+    P.nu2 = o.nu2;
+    P.outer = o.outer;
+    P.m = o.outer == SEM_OUTER_FGMRES ? o.gmres_m : 1;
+    P.imax = o.imax;
+    P.nd = (int)L0.hdir.size();
+    P.dir = L0.dir;
+    P.Nc = (int)Cl.N;
+    cudaError_t e = cudaSuccess;
+    for (int li = 0; li < nl && e == cudaSuccess; ++li) {
+        const Level& L = h->lv[li];
+        SmallLevel& D = P.lv[li];
+        D.N = (int)L.N;
+        D.E = L.E;
+        D.Np = L.Np;
+        D.map = L.map;
+        D.dinv = L.dinv;
+        D.wmult = L.wmult;
+        D.owner = L.owner;
+        for (double** v : {&D.u, &D.f, &D.y, &D.d})
+            if (e == cudaSuccess) e = small_alloc(*S, v, L.N);
+        if (li + 1 == nl) break;
+        const Level& C = h->lv[li + 1];
+        D.Npc = C.Np;
+        D.mapc = C.map;
+        double* Ae = nullptr;
+        if (e == cudaSuccess) e = small_alloc(*S, &Ae, (size_t)L.E * L.Np * L.Np);
+        if (e == cudaSuccess) e = element_matrices64(L, Ae, 0);
+        D.Ae = Ae;
+        // interpolation from C: I[nf][nc] = Bt[n_f][n_c] Bz[k_f][k_c], node l = k NT + n
+        std::vector<double> Bt, Bz, I((size_t)L.Np * C.Np);
+        interp_factors(L.dim, L.p, C.p, L.pz, C.pz, Bt, Bz);
+        for (int kf = 0; kf < L.NZ; ++kf)
+            for (int nf = 0; nf < L.NT; ++nf)
+                for (int kc = 0; kc < C.NZ; ++kc)
+                    for (int nc = 0; nc < C.NT; ++nc)
+                        I[(size_t)(kf * L.NT + nf) * C.Np + kc * C.NT + nc] = Bt[(size_t)nf * C.NT + nc] * Bz[(size_t)kf * C.NZ + kc];
+        double* dI = nullptr;
+        if (e == cudaSuccess) e = small_upload(*S, &dI, I);
+        D.I = dI;
+        const Cheb c = cheb_coeffs(L.lam, o);
+        D.c0 = c.c0;
+        for (int j = 0; j < 16; ++j) {
+            D.c1[j] = c.c1[j];
+            D.c2[j] = c.c2[j];
+        }
+    }
+    // the coarsest level's operator for the lifting of a single-level handle, and its inverse
+    if (e == cudaSuccess && nl == 1) {
+        double* Ae = nullptr;
+        e = small_alloc(*S, &Ae, (size_t)Cl.E * Cl.Np * Cl.Np);
+        if (e == cudaSuccess) e = element_matrices64(Cl, Ae, 0);
+        P.lv[0].Ae = Ae;
+    }
+    if (e == cudaSuccess) {
+        const long long Nc = Cl.N;
+        std::vector<int> rowptr(Nc + 1), col((size_t)Cl.csr_nnz);
+        std::vector<double> val((size_t)Cl.csr_nnz);
+        e = cudaMemcpy(rowptr.data(), Cl.csr_rowptr, sizeof(int) * (Nc + 1), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(col.data(), Cl.csr_col, sizeof(int) * col.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(val.data(), Cl.csr_val, sizeof(double) * val.size(), cudaMemcpyDeviceToHost);
+        std::vector<int> fr;
+        for (long long i = 0; i < Nc; ++i)
+            if (rowptr[i + 1] > rowptr[i]) fr.push_back((int)i);
+        const int nf = (int)fr.size();
+        std::vector<int> pos(Nc, -1);
+        for (int k = 0; k < nf; ++k) pos[fr[k]] = k;
+        std::vector<double> a((size_t)nf * nf, 0.0);
+        for (int k = 0; k < nf; ++k)
+            for (int t = rowptr[fr[k]]; t < rowptr[fr[k] + 1]; ++t)
+                if (pos[col[t]] >= 0) a[(size_t)k * nf + pos[col[t]]] = val[t];
+        for (int i = 0; i < nf; ++i)
+            for (int j = 0; j < i; ++j)
+                a[(size_t)i * nf + j] = a[(size_t)j * nf + i] = 0.5 * (a[(size_t)i * nf + j] + a[(size_t)j * nf + i]);
+        if (e == cudaSuccess && !spd_inverse(a, nf)) {
+            small_release(S);
+            set_error("fused small solve: the coarse matrix is not positive definite");
+            return SEM_BREAKDOWN;
+        }
+        std::vector<double> cinv((size_t)Nc * Nc, 0.0);
+        for (int i = 0; i < nf; ++i)
+            for (int j = 0; j < nf; ++j) cinv[(size_t)fr[i] * Nc + fr[j]] = a[(size_t)i * nf + j];
+        double* dC = nullptr;
+        if (e == cudaSuccess) e = small_upload(*S, &dC, cinv);
+        P.Cinv = dC;
+    }
+    const size_t N0 = L0.N;
+    const int m = P.m;
+    if (e == cudaSuccess) e = small_alloc(*S, &P.V, (size_t)(m + 1) * N0);
+    if (e == cudaSuccess) e = small_alloc(*S, &P.Z, (size_t)m * N0);
+    for (double** v : {&P.r, &P.q, &P.fr, &P.x, &P.p, &P.z})
+        if (e == cudaSuccess) e = small_alloc(*S, v, N0);
+    if (e == cudaSuccess) e = small_alloc(*S, &P.out, 8);
+    if (e == cudaSuccess) e = small_alloc(*S, &S->dplan, 1);
+    if (e == cudaSuccess) e = cudaMemcpy(S->dplan, &P, sizeof(SmallPlan), cudaMemcpyHostToDevice);
+    S->N0 = (int)N0;
+    S->smem = sizeof(double) * (N0 + 40 + (size_t)(m + 1) * m + 2 * (size_t)m + (m + 1) + m + 2 * (size_t)(m + 1));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_small_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S->smem);
+    if (e != cudaSuccess) {
+        small_release(S);
+        set_error(std::string("fused small solve: ") + cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? SEM_ENOMEM : SEM_ECUDA;
+    }
+    h->small = S;
+    return SEM_OK;
+}
+
+// One launch of the fused solve; fills the statistics and returns its status.
+sem_status small_solve(sem_handle* h, const double* rhs, const double* eta, double rtol, double* phi, sem_stats* st,
+                       cudaStream_t s) {
+    SmallHost* S = static_cast<SmallHost*>(h->small);
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) {
+        k_small_solve<<<1, kSmallThreads, S->smem, s>>>(S->dplan, rhs, eta, phi, rtol, h->opts.atol);
+        e = cudaGetLastError();
+    }
+    double out[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->sc.hpinned + 110, S->plan.out, 6 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        set_error(std::string("fused small solve: ") + cudaGetErrorString(e));
+        return SEM_ECUDA;
+    }
+    std::memcpy(out, h->sc.hpinned + 110, 6 * sizeof(double));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    sem_stats r{};
+    r.iters = (int)out[0];
+    r.fnorm = out[1];
+    r.res0 = out[1];
+    r.res_final = out[2];
+    r.status = (int)out[3];
+    r.vcycles = (long long)out[4];
+    r.fine_applies = (long long)out[5];
+    r.ms = ms;
+    r.kernel_launches = 1;
+    if (st) *st = r;
+    if (r.status == SEM_NOT_CONVERGED) set_error("the outer iteration reached imax");
+    else if (r.status == SEM_NAN) set_error("non-finite residual");
+    else if (r.status == SEM_BREAKDOWN) set_error("PCG breakdown: p^T A p <= 0");
+    return (sem_status)r.status;
+}
+
+}  // namespace sem

@@ -64,27 +64,6 @@ using namespace sem;
 
 namespace {
 
-// Chebyshev coefficients of one sweep (three-term recurrence on [a, b]).
-struct Cheb {
-    double c0;               // first step: d = c0 D^{-1} r
-    double c1[16], c2[16];   // step j >= 1: d = c1 d + c2 D^{-1} r
-};
-
-Cheb cheb_coeffs(double lam, const sem_options& o) {
-    Cheb c{};
-    const double b = o.cheb_hi * lam, a = o.cheb_lo * b;
-    const double theta = 0.5 * (b + a), delta = 0.5 * (b - a), sigma = theta / delta;
-    c.c0 = 1.0 / theta;
-    double rho = 1.0 / sigma;
-    for (int j = 1; j < o.k_cheb && j < 16; ++j) {
-        const double rn = 1.0 / (2.0 * sigma - rho);
-        c.c1[j] = rn * rho;
-        c.c2[j] = 2.0 * rn / delta;
-        rho = rn;
-    }
-    return c;
-}
-
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 // Event timing of finest-level applies (profile = 1, outside graph capture): the pair of
@@ -827,6 +806,7 @@ sem_status check_options(const sem_options& o, int P) {
         return SEM_EINVAL;
     }
     if (o.coarse_bj < 0 || o.coarse_bj > 1) { set_error("coarse_bj must be 0 or 1"); return SEM_EINVAL; }
+    if (o.fused_small < 0 || o.fused_small > 1) { set_error("fused_small must be 0 or 1"); return SEM_EINVAL; }
     if (o.elem_matrices < -1 || o.elem_matrices > SEM_ELEM_DF32) {
         set_error("elem_matrices must be -1, SEM_ELEM_OFF, SEM_ELEM_FP64 or SEM_ELEM_DF32");
         return SEM_EINVAL;
@@ -1058,6 +1038,7 @@ void sem_default_options(sem_options* o, int P) {
     o->deterministic = 0;
     o->elem_matrices = -1;
     o->coarse_bj = 1;
+    o->fused_small = 1;
 }
 
 sem_status sem_mesh_nodes2d(const sem_mesh* m, int p, long long* n2, double* xy) {
@@ -1170,6 +1151,7 @@ sem_status sem_setup(const sem_mesh* m, int P, const sem_options* opts, sem_hand
         cudaError_t e = cudaDeviceSynchronize();
         if (e != cudaSuccess) { set_error(std::string("setup: ") + cudaGetErrorString(e)); st = SEM_ECUDA; }
     }
+    if (st == SEM_OK) st = build_small_plan(h);
     if (st != SEM_OK) {
         sem_destroy(h);
         return st;
@@ -1186,6 +1168,7 @@ void sem_destroy(sem_handle* h) {
     // no kernel or copy of this handle may still be in flight when its memory goes away
     if (h->bstream) cudaStreamSynchronize(h->bstream);
     cudaDeviceSynchronize();
+    free_small_plan(h);
     for (Level& L : h->lv) free_level(L);
     if (h->auto_elem_bytes) g_auto_elem_bytes.fetch_sub(h->auto_elem_bytes);
     void* ptrs[] = {h->sc.part, h->sc.counter, h->sc.scal, h->sc.flags, h->r, h->z, h->p, h->q, h->x, h->fr,
@@ -1450,6 +1433,7 @@ sem_status sem_update_eta(sem_handle* h, const double* eta_nodal_host, int strat
         h->coarse_flat = false;
     }
     CKS(cudaDeviceSynchronize());
+    if (h->small != nullptr) CKST(build_small_plan(h));     // element matrices, lambda_hat, coarse inverse
     return SEM_OK;
 }
 
@@ -1556,6 +1540,13 @@ sem_status laplace_solve(sem_handle* h, const double* rhs, const double* eta, do
     cudaStream_t s = as_stream(stream);
     const Level& L = h->lv[0];
     const long long N = L.N, nd = (long long)L.hdir.size();
+    if (h->small != nullptr && !h->capturing) {
+        // small problems: the whole solve in one launch
+        sem_stats sst{};
+        const sem_status r = small_solve(h, rhs, eta, (tol > 0) ? tol : h->opts.rtol, phi, &sst, s);
+        if (stats) *stats = sst;
+        return r;
+    }
     sem_stats st{};
     h->fine_applies = 0;
     h->vcycles = 0;
