@@ -275,6 +275,25 @@ def run_ncu_case(a):
     s.close()
 
 
+def run_ncu_small(a):
+    """Profiler driver: three one-launch solves of the 2D slice (128 triangles, P = 4, FGMRES(30))."""
+    import torch
+    import paper_2009_00705_gb300 as sem
+    import workloads as W
+    from paper_2009_00705_gb300 import build as B
+    B.build()
+    m1 = W.config_slice2d()
+    s1 = sem.Solver(m1, 4, levels=[4, 2, 1], outer="fgmres", gmres_m=30, imax=100)
+    C1 = s1.coords(0)
+    d1 = torch.tensor(W.airy2d(*C1[s1.dirichlet_nodes(0)].T), device="cuda")
+    p1 = torch.empty(s1.query(0)["ndof"], dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        st = s1.solve(d1, p1, tol=1e-10)
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_small": "slice2d_p4", "stats": st}))
+    s1.close()
+
+
 def run_ncu_solve(a):
     """Profiler driver: `steps` solves of one form on the benchmark workload, stats only."""
     import torch
@@ -343,6 +362,8 @@ def main():
                     help="with --ncu-case: form of the FP64 residual apply (elem_matrices; -1 the default)")
     ap.add_argument("--ncu-tcgen05", action="store_true",
                     help="with --ncu-case: also launch the tcgen05 order-6 apply three times after the solve")
+    ap.add_argument("--ncu-small", action="store_true",
+                    help="profiler driver: three one-launch solves of the 2D slice; prints stats only")
     ap.add_argument("--ncu-solve", default="", choices=["", "fp64", "mixed_fp32", "mixed_tf32", "asm"],
                     help="profiler driver: --steps solves of one form on the benchmark workload; prints stats only")
     a = ap.parse_args()
@@ -354,6 +375,8 @@ def main():
         return run_ncu_case(a)
     if a.ncu_solve:
         return run_ncu_solve(a)
+    if a.ncu_small:
+        return run_ncu_small(a)
 
     # CPU baseline first: a separate process, before any GPU work in this one
     rank = int(os.environ.get("RANK", "0"))
@@ -616,10 +639,43 @@ def main():
         q1 = s1.query(0)
         configs["slice2d_p4"] = {"workload": "2D slice 2pi x 1, 16x4 quads -> 128 triangles, P=4, Airy-cos "
                                              "Dirichlet top; FGMRES(30) + pMG 4-2-1 to rtol 1e-10",
+                                 "form": "one kernel launch per solve (fused_small: lifting, FGMRES and the V-cycle "
+                                         "with FP64 element matrices and a direct coarse solve in one CTA)",
                                  "solves_per_s": 1.0 / t1, "ms_per_solve": t1 * 1e3, "iters": st1["iters"],
+                                 "kernel_launches_per_solve": st1["kernel_launches"],
+                                 "device_ms_per_solve": st1["ms"],
                                  "dof_free": q1["ndof"] - q1["ndirichlet"],
                                  "dof_per_s": (q1["ndof"] - q1["ndirichlet"]) / t1}
         s1.close()
+        # the same solve on the multi-kernel path (coarse CG to 1e-12)
+        s1m = sem.Solver(m1, 4, levels=[4, 2, 1], outer="fgmres", gmres_m=30, coarse_rtol=1e-12, imax=100,
+                         fused_small=0)
+        for _ in range(a.warmup):
+            s1m.solve(d1, p1, tol=1e-10)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            st1m = s1m.solve(d1, p1, tol=1e-10)
+        torch.cuda.synchronize()
+        t1m = (time.perf_counter() - t0) / reps
+        configs["slice2d_p4_multi_kernel"] = {"workload": "the same slice and solve on the multi-kernel path",
+                                              "solves_per_s": 1.0 / t1m, "ms_per_solve": t1m * 1e3,
+                                              "iters": st1m["iters"],
+                                              "kernel_launches_per_solve": st1m["kernel_launches"]}
+        s1m.close()
+        # the oracle on one host core, the same problem and method (and its sparse direct solve)
+        if rank == 0:
+            try:
+                r = subprocess.run([sys.executable, "-m", "oracle.timing", "--slice", "--solves", "40", "--direct", "5"],
+                                   cwd=ROOT, env=ORACLE_ENV, capture_output=True, text=True, timeout=600)
+                o1 = json.loads(r.stdout.strip().splitlines()[-1])
+                configs["slice2d_p4_oracle_one_core"] = {
+                    "solves_per_s": o1["solves_per_s"], "ms_per_solve": o1["ms_per_solve"], "iters": o1["iters"][-1],
+                    "direct_ms_per_solve": o1["direct_ms_per_solve"],
+                    "form": "oracle FGMRES(30) + the same V-cycle (exact coarse LU), SciPy sparse products, one "
+                            "thread; direct: sparse LU of the free-node matrix per solve"}
+            except Exception as ex:      # the oracle leg is context, not the measurement
+                configs["slice2d_p4_oracle_one_core"] = {"error": str(ex)[-300:]}
         # the same slice as one CUDA graph launch per solve (FP64 defect correction, the
         # convergence test on the device): the launch-latency-bound form of this config
         g1 = sem.Solver(m1, 4, levels=[4, 2, 1], outer="pdc", batch=1, coarse_rtol=1e-12, imax=200)

@@ -5,9 +5,11 @@ Used only by bench.py's CPU baseline and reference arm, as a separate process
 stands: assembled CSR matrices, SciPy sparse products, sparse LU coarse solve.
 
     python -m oracle.timing --n 8 --P 6 --nlayers 4 --solves 4 [--warmup 0] [--direct 2]
+    python -m oracle.timing --slice --solves 20
 
 prints one JSON line: free DOF, solves, seconds, DOF/s, iterations (and the direct
-solves' time with --direct).
+solves' time with --direct).  --slice times the 2D slice of 16 x 4 quads (128 triangles)
+at P = 4 instead: FGMRES(30) preconditioned by the V-cycle 4-2-1, to rtol 1e-10.
 """
 from __future__ import annotations
 
@@ -27,6 +29,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=0)
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--per-solve", action="store_true", help="print one line per timed solve")
+    ap.add_argument("--slice", action="store_true", help="the 2D slice at P = 4 with FGMRES(30) to 1e-10")
     ap.add_argument("--direct", type=int, default=0,
                     help="also time this many direct solves (sparse LU of the free-node matrix, factorised "
                          "in every solve, plus one refinement step)")
@@ -40,6 +43,8 @@ def main(argv=None):
     from oracle import solvers as S
     from oracle.assemble import Problem
 
+    if a.slice:
+        return slice_timing(a)
     levels = {6: [6, 3, 1], 5: [5, 3, 1], 4: [4, 2, 1], 3: [3, 2, 1], 2: [2, 1], 1: [1]}[a.P]
     mesh = W.config_box3d(a.n, a.nlayers)
     t0 = time.perf_counter()
@@ -78,5 +83,37 @@ def main(argv=None):
     print(json.dumps(out))
 
 
+def slice_timing(a):
+    import numpy as np
+
+    import workloads as W
+    from oracle import solvers as S
+    from oracle.assemble import Problem
+
+    mesh = W.config_slice2d()
+    prob = Problem(mesh, [4, 2, 1])
+    lev = prob.levels[0]
+    C = prob.coords(0)
+    phiD = W.airy2d(*C[lev.dirichlet].T)
+    ops = S.MGOperators(prob, k_cheb=5, lo=0.01, hi=1.05)
+    times, iters = [], []
+    for _ in range(a.solves):
+        t = time.perf_counter()
+        res = S.fgmres(ops, S.lift(prob, phiD), rtol=1e-10, m=30)
+        times.append(time.perf_counter() - t)
+        iters.append(res.iters)
+    dt = []
+    for _ in range(max(1, a.direct)):
+        t = time.perf_counter()
+        S.solve_laplace_direct(prob, phiD)
+        dt.append(time.perf_counter() - t)
+    tot = float(np.sum(times))
+    print(json.dumps({"dof_free": int(lev.free.size), "solves": a.solves, "seconds": tot,
+                      "solves_per_s": a.solves / tot, "ms_per_solve": 1e3 * tot / a.solves, "iters": iters,
+                      "direct_ms_per_solve": 1e3 * float(np.mean(dt)),
+                      "mesh": "2D slice 16x4 quads, 128 triangles, P=4, FGMRES(30) + pMG 4-2-1 to rtol 1e-10"}))
+
+
 if __name__ == "__main__":
     main()
+

@@ -87,25 +87,57 @@ __device__ double cta_dot(const double* a, const double* b, int n, double* red) 
     return cta_sum(v, red);
 }
 
-// y = A x on a level (free rows; y = 0 at Dirichlet nodes); lift: x also at the Dirichlet
-// nodes (the lifting product A_FD x_D), else x there counts as zero
-__device__ void s_apply(const SmallLevel& L, const double* x, double* y, bool lift, double* acc) {
-    for (int i = threadIdx.x; i < L.N; i += blockDim.x) acc[i] = 0.0;
-    __syncthreads();
-    const int rows = L.E * L.Np;
+// the element rows of one level: acc[map_i] += sum_j A_e[i][j] xs[map_j] (xs in shared memory;
+// NP > 0 fixes the nodes per element at compile time so the row is unrolled)
+template <int NP>
+__device__ void s_rows(const SmallLevel& L, const double* xs, bool lift, double* acc) {
+    const int Np = NP > 0 ? NP : L.Np;
+    const int rows = L.E * Np;
     for (int t = threadIdx.x; t < rows; t += blockDim.x) {
         const int mi = L.map[t];
         if (mi < 0) continue;
-        const int e = t / L.Np, i = t - e * L.Np;
-        const int* me = L.map + (size_t)e * L.Np;
-        const double* A = L.Ae + (size_t)e * L.Np * L.Np + i;      // column i = row i (symmetric)
-        double v = 0.0;
-        for (int j = 0; j < L.Np; ++j) {
+        const int e = t / Np, i = t - e * Np;
+        const int* me = L.map + (size_t)e * Np;
+        const double* A = L.Ae + (size_t)e * Np * Np + i;          // column i = row i (symmetric)
+        double v0 = 0.0, v1 = 0.0;
+#pragma unroll
+        for (int j = 0; j < (NP > 0 ? NP : 1); ++j) {
+            if (NP == 0) break;
             const int mj = me[j];
-            const double xj = mj >= 0 ? x[mj] : (lift ? x[-mj - 1] : 0.0);
-            v = fma(A[(size_t)j * L.Np], xj, v);
+            const double xj = mj >= 0 ? xs[mj] : (lift ? xs[-mj - 1] : 0.0);
+            if (j & 1) v1 = fma(A[(size_t)j * Np], xj, v1);
+            else v0 = fma(A[(size_t)j * Np], xj, v0);
         }
-        atomicAdd(&acc[mi], v);
+        if (NP == 0)
+            for (int j = 0; j < Np; ++j) {
+                const int mj = me[j];
+                const double xj = mj >= 0 ? xs[mj] : (lift ? xs[-mj - 1] : 0.0);
+                v0 = fma(A[(size_t)j * Np], xj, v0);
+            }
+        atomicAdd(&acc[mi], v0 + v1);
+    }
+}
+
+// y = A x on a level (free rows; y = 0 at Dirichlet nodes); lift: x also at the Dirichlet
+// nodes (the lifting product A_FD x_D), else x there counts as zero.  x is staged in shared
+// memory (xs), the element sums gather in acc.
+__device__ void s_apply(const SmallLevel& L, const double* x, double* y, bool lift, double* acc) {
+    double* xs = acc + L.N;
+    for (int i = threadIdx.x; i < L.N; i += blockDim.x) {
+        acc[i] = 0.0;
+        xs[i] = x[i];
+    }
+    __syncthreads();
+    switch (L.Np) {
+        case 3: s_rows<3>(L, xs, lift, acc); break;
+        case 6: s_rows<6>(L, xs, lift, acc); break;
+        case 10: s_rows<10>(L, xs, lift, acc); break;
+        case 15: s_rows<15>(L, xs, lift, acc); break;
+        case 18: s_rows<18>(L, xs, lift, acc); break;
+        case 21: s_rows<21>(L, xs, lift, acc); break;
+        case 28: s_rows<28>(L, xs, lift, acc); break;
+        case 40: s_rows<40>(L, xs, lift, acc); break;
+        default: s_rows<0>(L, xs, lift, acc); break;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < L.N; i += blockDim.x) y[i] = acc[i];
@@ -241,8 +273,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_solve(const SmallPlan* 
     const SmallLevel& L0 = P.lv[0];
     const int N = L0.N, m = P.m;
     extern __shared__ __align__(16) double ssm[];
-    double* acc = ssm;                         // [N0]
-    double* red = acc + N;                     // [40]
+    double* acc = ssm;                         // [N0] element sums, then [N0] staged x (s_apply)
+    double* red = acc + 2 * N;                 // [40]
     double* H = red + 40;                      // [(m + 1) m]
     double* cs = H + (size_t)(m + 1) * m;      // [m]
     double* sn = cs + m;                       // [m]
@@ -551,7 +583,7 @@ sem_status build_small_plan(sem_handle* h) {
     if (e == cudaSuccess) e = small_alloc(*S, &S->dplan, 1);
     if (e == cudaSuccess) e = cudaMemcpy(S->dplan, &P, sizeof(SmallPlan), cudaMemcpyHostToDevice);
     S->N0 = (int)N0;
-    S->smem = sizeof(double) * (N0 + 40 + (size_t)(m + 1) * m + 2 * (size_t)m + (m + 1) + m + 2 * (size_t)(m + 1));
+    S->smem = sizeof(double) * (2 * N0 + 40 + (size_t)(m + 1) * m + 2 * (size_t)m + (m + 1) + m + 2 * (size_t)(m + 1));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_small_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S->smem);
     if (e != cudaSuccess) {
