@@ -200,7 +200,11 @@ typedef struct {
                                    element at P = 6 against 307 KB).  SEM_ELEM_OFF (0): sum
                                    factorisation.  -1 (default): SEM_ELEM_FP64 for FP64 handles and
                                    SEM_ELEM_DF32 for mixed-precision ones, when they take at most a
-                                   quarter of the free device memory and 48 GB, else off */
+                                   quarter of the free device memory and 48 GB (across all live handles)
+                                   and the handle is not batched, else off; matrices taken by this rule
+                                   are dropped at the first sem_update_eta (a moving surface would
+                                   recompute them at every update, seconds at the benchmark size), while
+                                   explicitly requested ones are recomputed */
     int coarse_bj;              /* 1 (default) = the coarse CG is preconditioned by block Jacobi: the free
                                    order-1 nodes are cut into compact patches of at most 128 (recursive
                                    coordinate bisection in the horizontal), each patch's diagonal block is

@@ -656,6 +656,7 @@ sem_status alloc_element_matrices(sem_handle* h) {
     for (int li = 0; li < last; ++li) bytes += level_bytes(h->lv[li]);
     if (bytes == 0) return SEM_OK;
     if (h->opts.elem_matrices < 0) {
+        if (h->opts.batch != 0) return SEM_OK;          // many small tanks: setup time would dominate
         size_t fr = 0, tot = 0;
         CKS(cudaMemGetInfo(&fr, &tot));
         if (bytes > fr / 4) return SEM_OK;                                   // sum factorisation
@@ -1394,6 +1395,19 @@ sem_status sem_update_eta(sem_handle* h, const double* eta_nodal_host, int strat
     h->eta2.assign(eta_nodal_host, eta_nodal_host + L0.N2);
     if (h->fs_eta) CKS(cudaMemcpy(h->fs_eta, h->eta2.data(), sizeof(double) * L0.N2, cudaMemcpyHostToDevice));
     const int nl = (int)h->lv.size();
+    // element matrices taken by the auto rule serve a fixed geometry: recomputing them costs
+    // seconds at the benchmark size (Np^2 entries, each a quadrature sum), far more than the
+    // sum-factorised applies lose, so a moving surface returns the handle to sum factorisation
+    if (h->auto_elem_bytes) {
+        for (Level& L : h->lv) {
+            if (L.Ae64) cudaFree(L.Ae64);
+            if (L.Adf) cudaFree(L.Adf);
+            L.Ae64 = nullptr;
+            L.Adf = nullptr;
+        }
+        g_auto_elem_bytes.fetch_sub(h->auto_elem_bytes);
+        h->auto_elem_bytes = 0;
+    }
     // a mixed-precision handle smooths with the single-precision operator: its lambda_hat is
     // re-estimated with that operator (the estimate at setup uses the FP64 one)
     const bool fp32 = h->opts.precision != SEM_PREC_FP64;

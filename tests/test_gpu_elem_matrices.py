@@ -143,3 +143,28 @@ def test_deterministic_double_fp32_apply_is_bit_identical(sem):
         assert np.abs(y1.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
     finally:
         s.close()
+
+
+def test_auto_element_matrices_give_way_to_a_moving_surface(sem):
+    # the auto rule serves a fixed geometry: the first surface update returns the handle to the
+    # sum-factorised apply, which then equals a fresh handle's element-matrix apply
+    mesh = W.config_box3d(4, 2)
+    levels = [6, 3, 1]
+    s = sem.Solver(mesh, 6, levels=levels)
+    xy = sem.sem_mesh_nodes2d(mesh, 6)
+    eta = 0.04 * np.sin(xy[:, 0]) * np.sin(xy[:, 1])
+    fresh = sem.Solver(mesh, 6, eta_nodal=eta, levels=levels)
+    try:
+        assert s.elem_matrices(0) == 1 and fresh.elem_matrices(0) == 1
+        s.update_eta(eta, "finest")
+        assert s.elem_matrices(0) == 0 and s.elem_matrices(1) == 0
+        N = s.query(0)["ndof"]
+        x = torch.tensor(W.random_vector(N, seed=99), device="cuda")
+        ya, yb = torch.empty_like(x), torch.empty_like(x)
+        s.apply(0, x, ya)
+        fresh.apply(0, x, yb)
+        torch.cuda.synchronize()
+        assert (ya - yb).abs().max().item() <= 1e-12 * yb.abs().max().item()
+    finally:
+        s.close()
+        fresh.close()
