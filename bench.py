@@ -294,6 +294,33 @@ def run_ncu_small(a):
     s1.close()
 
 
+def run_ncu_batch(a):
+    """Profiler driver: one batched solve (one graph launch) of the first N random tanks."""
+    import torch
+    import paper_2009_00705_gb300 as sem
+    import workloads as W
+    from paper_2009_00705_gb300 import build as B
+    B.build()
+    tanks = []
+    for i in range(a.ncu_batch):
+        mesh_t, P_t, modes = W.random_tank(1000 + i)
+        xy_t = sem.sem_mesh_nodes2d(mesh_t, P_t)
+        st_ = sem.Solver(mesh_t, P_t, eta_nodal=mesh_t.eta(xy_t[:, 0], xy_t[:, 1]), levels=levels_for(P_t),
+                         precision="mixed_tf32", outer="pdc", batch=1, coarse_rtol=a.coarse_rtol, imax=400)
+        C_t = st_.coords(0)
+        phiD_t = torch.tensor(W.tank_potential(*C_t[st_.dirichlet_nodes(0)].T, modes), device="cuda")
+        tanks.append((st_, phiD_t, torch.empty(st_.query(0)["ndof"], dtype=torch.float64, device="cuda")))
+    stats = sem.laplace_solve_batch([t[0].h for t in tanks], [t[1] for t in tanks], 1e-8, [t[2] for t in tanks])
+    torch.cuda.synchronize()
+    # the same tanks one by one (plain launches, which a launch list can resolve; the batch's
+    # graph nodes sit inside conditional loops)
+    single = [t[0].solve(t[1], t[2], tol=1e-8)["iters"] for t in tanks]
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_batch": a.ncu_batch, "iters": [s_["iters"] for s_ in stats], "iters_one_by_one": single}))
+    for t in tanks:
+        t[0].close()
+
+
 def run_ncu_solve(a):
     """Profiler driver: `steps` solves of one form on the benchmark workload, stats only."""
     import torch
@@ -362,6 +389,8 @@ def main():
                     help="with --ncu-case: form of the FP64 residual apply (elem_matrices; -1 the default)")
     ap.add_argument("--ncu-tcgen05", action="store_true",
                     help="with --ncu-case: also launch the tcgen05 order-6 apply three times after the solve")
+    ap.add_argument("--ncu-batch", type=int, default=0, metavar="N",
+                    help="profiler driver: one batched solve of the first N random tanks; prints iterations only")
     ap.add_argument("--ncu-small", action="store_true",
                     help="profiler driver: three one-launch solves of the 2D slice; prints stats only")
     ap.add_argument("--ncu-solve", default="", choices=["", "fp64", "mixed_fp32", "mixed_tf32", "asm"],
@@ -377,6 +406,8 @@ def main():
         return run_ncu_solve(a)
     if a.ncu_small:
         return run_ncu_small(a)
+    if a.ncu_batch:
+        return run_ncu_batch(a)
 
     # CPU baseline first: a separate process, before any GPU work in this one
     rank = int(os.environ.get("RANK", "0"))

@@ -271,7 +271,9 @@ sem_status sem_mesh_nodes2d(const sem_mesh* mesh, int p, long long* n2, double* 
  * bounds, transfers, coarse workspace) and allocate all device memory on the
  * current CUDA device.  Synchronous.  P in 1..6; opts NULL = defaults. */
 sem_status sem_setup(const sem_mesh* mesh, int P, const sem_options* opts, sem_handle** out);
-void sem_destroy(sem_handle* h);
+/* Free a handle (synchronises the device first).  Not named sem_destroy: that is the POSIX
+ * semaphore call, which the statically linked CUDA runtime inside the library uses. */
+void sem_teardown(sem_handle* h);
 
 /* Sizes of a level: global nodes, Dirichlet nodes, elements, nodes per element. */
 sem_status sem_query(const sem_handle* h, int level, long long* ndof, long long* ndirichlet,

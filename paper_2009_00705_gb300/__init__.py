@@ -25,7 +25,7 @@ OUTER = {"pcg": 0, "fgmres": 1, "pdc": 2}
 PRECISION = {"fp64": 0, "mixed_fp32": 1, "mixed_tf32": 2}
 SMOOTHER = {"chebyshev": 0, "learned": 1, "asm": 2}
 
-EXPORTS = ("sem_default_options", "sem_mesh_nodes2d", "sem_setup", "sem_destroy", "sem_query",
+EXPORTS = ("sem_default_options", "sem_mesh_nodes2d", "sem_setup", "sem_teardown", "sem_query",
            "sem_dirichlet_nodes", "sem_node_coords", "sem_element_map", "sem_lambda_max", "sem_diagonal",
            "sem_apply", "sem_apply32", "sem_update_eta", "sem_fnpf_rhs", "sem_fnpf_step", "pmg_vcycle", "laplace_solve", "laplace_solve_host", "sem_last_error",
            "sem_cg_csr_noalloc", "sem_mlp_get_weights", "sem_mlp_set_weights", "sem_mlp_forward",
@@ -88,8 +88,8 @@ def lib():
     L.sem_default_options.restype = None
     L.sem_mesh_nodes2d.argtypes = [POINTER(SemMesh), c_int, POINTER(c_longlong), POINTER(c_double)]
     L.sem_setup.argtypes = [POINTER(SemMesh), c_int, POINTER(SemOptions), POINTER(c_void_p)]
-    L.sem_destroy.argtypes = [c_void_p]
-    L.sem_destroy.restype = None
+    L.sem_teardown.argtypes = [c_void_p]
+    L.sem_teardown.restype = None
     L.sem_query.argtypes = [c_void_p, c_int, POINTER(c_longlong), POINTER(c_longlong), POINTER(c_longlong),
                             POINTER(c_int)]
     L.sem_dirichlet_nodes.argtypes = [c_void_p, c_int, POINTER(c_longlong)]
@@ -241,8 +241,8 @@ def sem_setup(mesh, P: int, opts: SemOptions | None = None, eta_nodal=None) -> i
     return h.value
 
 
-def sem_destroy(h: int) -> None:
-    lib().sem_destroy(h)
+def sem_teardown(h: int) -> None:
+    lib().sem_teardown(h)
 
 
 def sem_query(h: int, level: int = 0) -> dict:
@@ -489,7 +489,7 @@ class Solver:
 
     def close(self):
         if self.h:
-            sem_destroy(self.h)
+            sem_teardown(self.h)
             self.h = None
 
     def __del__(self):

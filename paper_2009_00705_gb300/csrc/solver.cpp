@@ -1154,7 +1154,7 @@ sem_status sem_setup(const sem_mesh* m, int P, const sem_options* opts, sem_hand
     }
     if (st == SEM_OK) st = build_small_plan(h);
     if (st != SEM_OK) {
-        sem_destroy(h);
+        sem_teardown(h);
         return st;
     }
     h->fine_applies = 0;
@@ -1164,7 +1164,7 @@ sem_status sem_setup(const sem_mesh* m, int P, const sem_options* opts, sem_hand
     return SEM_OK;
 }
 
-void sem_destroy(sem_handle* h) {
+void sem_teardown(sem_handle* h) {
     if (!h) return;
     // no kernel or copy of this handle may still be in flight when its memory goes away
     if (h->bstream) cudaStreamSynchronize(h->bstream);

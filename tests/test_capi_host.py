@@ -31,8 +31,16 @@ def declared_functions():
 
 def test_header_declares_the_boundary():
     names = declared_functions()
-    for required in ("sem_setup", "sem_apply", "pmg_vcycle", "laplace_solve", "sem_destroy", "sem_last_error"):
+    for required in ("sem_setup", "sem_apply", "pmg_vcycle", "laplace_solve", "sem_teardown", "sem_last_error"):
         assert required in names
+
+
+def test_no_entry_point_takes_a_posix_semaphore_name():
+    # the CUDA runtime linked into the library calls the POSIX sem_* functions; an entry point of
+    # the same name would capture those calls inside the library
+    posix = {"sem_init", "sem_destroy", "sem_post", "sem_wait", "sem_trywait", "sem_timedwait", "sem_clockwait",
+             "sem_open", "sem_close", "sem_unlink", "sem_getvalue"}
+    assert not posix & set(declared_functions())
 
 
 def test_library_exports_every_declared_symbol(sem):
