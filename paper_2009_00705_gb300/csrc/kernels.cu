@@ -9,7 +9,6 @@
 //  * the assembled diagonal (Jacobi smoother), p-restriction R = P^T and
 //    prolongation P (Section 4.1, Eq. rest), Chebyshev smoothing updates and
 //    the FP64 reductions of the Krylov iterations (Algorithms 2, 3).
-#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -1369,96 +1368,6 @@ __device__ double block_allsum(double v) {
     return v;
 }
 
-// The same CG in one thread-block cluster (launched with a cluster dimension equal to the
-// grid): a cluster's CTAs are scheduled together, so its hardware barrier cannot wait on CTAs
-// of other tanks, and the concurrent tanks of a batch may each run one.  CTA k of the cluster
-// owns a contiguous range of rows; the direction p, written by its owner and read by the
-// neighbouring rows' products, goes through L2 (__ldcg); each reduction gathers the CTAs'
-// partial sums from distributed shared memory in rank order, so every CTA computes the same
-// totals and takes the same branches.  Three cluster barriers per iteration.
-__device__ double cluster_allsum(double v, double* slot, int& parity) {
-    namespace cg = cooperative_groups;
-    cg::cluster_group cl = cg::this_cluster();
-    v = block_sum(v);
-    if (threadIdx.x == 0) slot[parity] = v;
-    cl.sync();
-    __shared__ double tot;
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (unsigned k = 0; k < cl.num_blocks(); ++k) t += cl.map_shared_rank(slot, k)[parity];
-        tot = t;
-    }
-    __syncthreads();
-    const double t = tot;
-    __syncthreads();
-    parity ^= 1;
-    return t;
-}
-
-__global__ void __launch_bounds__(1024) k_coarse_cg_cluster(long long n, const int* __restrict__ rowptr,
-                                                            const int* __restrict__ col,
-                                                            const double* __restrict__ vals,
-                                                            const double* __restrict__ dinv,
-                                                            const double* __restrict__ b, double* x, double* r,
-                                                            double* z, double* p, double* q, double* scal, int* flags,
-                                                            double rtol2, int imax) {
-    namespace cg = cooperative_groups;
-    cg::cluster_group cl = cg::this_cluster();
-    __shared__ double slot[2];
-    int parity = 0;
-    const long long nb = cl.num_blocks(), rank = cl.block_rank();
-    const long long r0 = n * rank / nb, r1 = n * (rank + 1) / nb;
-    double s0 = 0, s1 = 0;
-    for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-        const double bi = b[i], zi = dinv[i] * bi;
-        x[i] = 0;
-        r[i] = bi;
-        z[i] = zi;
-        p[i] = zi;
-        s0 += bi * zi;
-        s1 += bi * bi;
-    }
-    double rho = cluster_allsum(s0, slot, parity);
-    const double bb = cluster_allsum(s1, slot, parity);
-    const double tol2 = rtol2 * bb;
-    double rr = bb;
-    int it = 0;
-    while (rr > tol2 && rr > 0.0 && it < imax) {
-        double pq = 0;
-        for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-            double v = 0;
-            for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) v += vals[k] * __ldcg(p + col[k]);
-            q[i] = v;
-            pq += p[i] * v;
-        }
-        const double alpha = rho / cluster_allsum(pq, slot, parity);
-        double t0 = 0, t1 = 0;
-        for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-            x[i] += alpha * p[i];
-            const double ri = r[i] - alpha * q[i];
-            r[i] = ri;
-            const double zi = dinv[i] * ri;
-            z[i] = zi;
-            t0 += ri * zi;
-            t1 += ri * ri;
-        }
-        const double rho_new = cluster_allsum(t0, slot, parity);
-        rr = cluster_allsum(t1, slot, parity);
-        ++it;
-        if (rr <= tol2) break;
-        const double beta = rho_new / rho;
-        rho = rho_new;
-        for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) p[i] = z[i] + beta * p[i];
-        cl.sync();                                  // p complete before the next products
-    }
-    if (rank == 0 && threadIdx.x == 0) {
-        flags[F_CG_ITERS] = it;
-        flags[F_CG_DONE] = (rr <= tol2 || rr == 0.0) ? 1 : 0;
-        scal[S_CG_RR] = rr;
-    }
-    cl.sync();                                      // no CTA leaves while others may read its slots
-}
-
 __global__ void __launch_bounds__(1024) k_coarse_cg_block(long long n, const int* __restrict__ rowptr,
                                                           const int* __restrict__ col,
                                                           const double* __restrict__ vals,
@@ -1996,58 +1905,12 @@ cudaError_t coarse_cg_bj(const Level& C, const double* b, double* x, double* z, 
     return cudaGetLastError();
 }
 
-// CTAs per cluster of the cluster CG: 16 where the device allows that size (non-portable), else 8
-int coarse_cluster_size() {
-    static int cs = 0;
-    if (cs) return cs;
-    cs = 8;
-    if (cudaFuncSetAttribute(k_coarse_cg_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
-        cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = 16;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.gridDim = dim3(16);
-        cfg.blockDim = dim3(1024);
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        int nclusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&nclusters, k_coarse_cg_cluster, &cfg) == cudaSuccess && nclusters > 0) cs = 16;
-    }
-    cudaGetLastError();
-    return cs;
-}
-
-// Batched tanks: one CTA for small coarse levels, one cluster otherwise (tanks run
-// concurrently; neither form waits on CTAs outside itself).
 cudaError_t coarse_cg_single(const Level& C, const int* rowptr, const int* col, const double* vals, const double* b,
                              double* x, double* r, double* z, double* p, double* q, Scratch& sc, double rtol2, int imax,
                              cudaStream_t s) {
-    if (C.N < 4096) {
-        k_coarse_cg_block<<<1, 1024, 0, s>>>(C.N, rowptr, col, vals, C.dinv, b, x, r, z, p, q, sc.scal, sc.flags, rtol2,
-                                             imax);
-        return cudaGetLastError();
-    }
-    const int cs = coarse_cluster_size();
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = cs;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(cs);
-    cfg.blockDim = dim3(1024);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    long long n = C.N;
-    const double* dinv = C.dinv;
-    double* scal = sc.scal;
-    int* flags = sc.flags;
-    return cudaLaunchKernelEx(&cfg, k_coarse_cg_cluster, n, rowptr, col, vals, dinv, b, x, r, z, p, q, scal, flags, rtol2,
-                              imax);
+    k_coarse_cg_block<<<1, 1024, 0, s>>>(C.N, rowptr, col, vals, C.dinv, b, x, r, z, p, q, sc.scal, sc.flags, rtol2,
+                                         imax);
+    return cudaGetLastError();
 }
 
 cudaError_t cg_init(long long n, const double* b, const double* dinv, double* x, double* r, double* z, double* p,
