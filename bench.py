@@ -43,7 +43,7 @@ FALLBACK_HBM_GBS = 6800.0
 # proportion); reported as null once apply_prism.cu differs from the captured source or the
 # handle runs the sum-factorised form.
 TRAFFIC = {("elem64", 6): (1428.006e6 + 4.251648e6) * 32768 / 4608}
-TRAFFIC_SRC_SHA = "69b2f03361d0470d"
+TRAFFIC_SRC_SHA = "242d002323a12534"
 
 
 def workload_name(n, nl, P):
@@ -120,9 +120,13 @@ def whole_job_rate(units_per_rank_step, steps, world, seconds):
 
 
 def kernels_sha():
-    """Hash of the prism-apply kernel's source (apply_prism.cu)."""
+    """Hash of the source of the FP64 element-matrix apply (k_apply_elem64 and its launcher in
+    apply_prism.cu): the captured traffic stands while this text is unchanged."""
     with open(os.path.join(ROOT, "paper_2009_00705_gb300", "csrc", "apply_prism.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+        src = f.read()
+    a = src.index(b"__global__ void __launch_bounds__(256) k_apply_elem64")
+    b = src.index(b"cudaError_t apply_prism_impl")
+    return hashlib.sha256(src[a:b]).hexdigest()[:16]
 
 
 class Clocks:
