@@ -40,8 +40,8 @@ FALLBACK_HBM_GBS = 6800.0
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the FP64 element-matrix
 # apply, per launch, from a capture on the 24x24x4-prism box (4,608 elements) scaled to the
 # 32,768-element benchmark mesh by element count (the traffic is the element matrices, in
-# proportion); reported as null once apply_prism.cu differs from the captured source or the
-# handle runs the sum-factorised form.
+# proportion); reported as null once the kernel's source text (kernels_sha) differs from the
+# captured one or the handle runs another apply form.
 TRAFFIC = {("elem64", 6): (1428.006e6 + 4.251648e6) * 32768 / 4608}
 TRAFFIC_SRC_SHA = "242d002323a12534"
 
