@@ -626,12 +626,30 @@ __global__ void k_pcg_dir(long long n, const double* num, const double* den, con
 }
 
 // FP32 data, FP64 accumulation (inner PCG of the mixed-precision path)
+// A thread's share of an FP32 dot product, summed without FP64 arithmetic per element (the FP64
+// pipe of GB300 is a small fraction of the FP32 one): each product a b = p + e exactly (one FMA),
+// p added to the running sum by Knuth's TwoSum, the errors into a compensation term; one
+// conversion to FP64 per thread.  The result carries about the FP64 sum's accuracy.
+struct Dot32 {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float a, float b) {
+        const float p = __fmul_rn(a, b);
+        const float e = __fmaf_rn(a, b, -p);
+        const float t = __fadd_rn(s, p);
+        const float bp = __fsub_rn(t, s);
+        const float d = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(d, e));
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 __global__ void k_dot32(long long n, const float* __restrict__ a, const float* __restrict__ b, double* part,
                         unsigned* counter, double* out) {
-    double s = 0;
+    Dot32 acc;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        s += (double)a[i] * (double)b[i];
-    double v[1] = {block_sum(s)};
+        acc.add(a[i], b[i]);
+    double v[1] = {block_sum(acc.value())};
     if (partials_done<1>(v, part, counter)) {
         double r[1];
         final_sums<1>(part, r);
@@ -643,14 +661,14 @@ __global__ void k_pcg_update32(long long n, const double* num, const double* den
                                const float* __restrict__ q, float* __restrict__ u, float* __restrict__ r,
                                double* part, unsigned* counter, double* out) {
     const float alpha = (float)block_ratio(num, den);
-    double s = 0;
+    Dot32 acc;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         u[i] += alpha * p[i];
         const float v = r[i] - alpha * q[i];
         r[i] = v;
-        s += (double)v * v;
+        acc.add(v, v);
     }
-    double v[1] = {block_sum(s)};
+    double v[1] = {block_sum(acc.value())};
     if (partials_done<1>(v, part, counter)) {
         double rr[1];
         final_sums<1>(part, rr);
