@@ -1572,7 +1572,14 @@ __global__ void k_to_f64(long long n, const float* __restrict__ a, double* __res
 }  // namespace
 
 // ====================================================================== launchers
-int reduce_blocks() { return 2 * kSMs; }
+// Largest grid of the reduction kernels (their partial-sum arrays are sized for it); a launch
+// takes about four elements per thread, so that a stream of several vectors keeps enough loads
+// in flight for HBM.
+int reduce_blocks() { return 8 * kSMs; }
+static int red_grid(long long n) {
+    const long long g = (n + 4LL * kRedThreads - 1) / (4LL * kRedThreads);
+    return (int)std::max<long long>(1, std::min<long long>(g, reduce_blocks()));
+}
 
 cudaError_t launch_apply64(const Level& L, const double* x, double* y, bool lift, const int* skip, cudaStream_t s) {
     if (L.dim == 3) return launch_apply_prism64(L, x, y, lift, skip, L.tile64, s);
@@ -1710,7 +1717,7 @@ template cudaError_t cheb_step<float>(long long, float, float, const float*, con
                                       float*, cudaStream_t, const int*);
 
 cudaError_t dot64(long long n, const double* a, const double* b, Scratch& sc, double* out, cudaStream_t s) {
-    k_dot<<<reduce_blocks(), kRedThreads, 0, s>>>(n, a, b, sc.part, sc.counter, out);
+    k_dot<<<red_grid(n), kRedThreads, 0, s>>>(n, a, b, sc.part, sc.counter, out);
     return cudaGetLastError();
 }
 __global__ void k_batch_loop(double* scal, int* flags, double rtol, double atol, int imax,
@@ -1746,12 +1753,12 @@ cudaError_t batch_loop_check(double* scal, int* flags, double rtol, double atol,
 
 cudaError_t residual64(long long n, const double* f, const double* y, double* r, Scratch& sc, double* rr,
                        cudaStream_t s) {
-    k_residual<<<reduce_blocks(), kRedThreads, 0, s>>>(n, f, y, r, sc.part, sc.counter, rr);
+    k_residual<<<red_grid(n), kRedThreads, 0, s>>>(n, f, y, r, sc.part, sc.counter, rr);
     return cudaGetLastError();
 }
 cudaError_t pcg_update(long long n, const double* num, const double* den, const double* p, const double* q, double* u,
                        double* r, Scratch& sc, double* rr, cudaStream_t s) {
-    k_pcg_update<<<reduce_blocks(), kRedThreads, 0, s>>>(n, num, den, p, q, u, r, sc.part, sc.counter, rr);
+    k_pcg_update<<<red_grid(n), kRedThreads, 0, s>>>(n, num, den, p, q, u, r, sc.part, sc.counter, rr);
     return cudaGetLastError();
 }
 cudaError_t pcg_direction(long long n, const double* num, const double* den, const double* z, double* p,
@@ -1760,12 +1767,12 @@ cudaError_t pcg_direction(long long n, const double* num, const double* den, con
     return cudaGetLastError();
 }
 cudaError_t dot32(long long n, const float* a, const float* b, Scratch& sc, double* out, cudaStream_t s) {
-    k_dot32<<<reduce_blocks(), kRedThreads, 0, s>>>(n, a, b, sc.part, sc.counter, out);
+    k_dot32<<<red_grid(n), kRedThreads, 0, s>>>(n, a, b, sc.part, sc.counter, out);
     return cudaGetLastError();
 }
 cudaError_t pcg_update32(long long n, const double* num, const double* den, const float* p, const float* q, float* u,
                          float* r, Scratch& sc, double* rr, cudaStream_t s) {
-    k_pcg_update32<<<reduce_blocks(), kRedThreads, 0, s>>>(n, num, den, p, q, u, r, sc.part, sc.counter, rr);
+    k_pcg_update32<<<red_grid(n), kRedThreads, 0, s>>>(n, num, den, p, q, u, r, sc.part, sc.counter, rr);
     return cudaGetLastError();
 }
 cudaError_t pcg_direction32(long long n, const double* num, const double* den, const float* z, float* p,
@@ -1807,7 +1814,7 @@ cudaError_t to_f64(long long n, const float* a, double* b, cudaStream_t s) {
 }
 cudaError_t multidot64(long long n, int k, const double* V, const double* w, Scratch& sc, double* out, cudaStream_t s) {
     if (k > kMaxMulti) return cudaErrorInvalidValue;
-    k_multidot<<<reduce_blocks(), kRedThreads, 0, s>>>(n, k, V, w, sc.part, sc.counter, out);
+    k_multidot<<<red_grid(n), kRedThreads, 0, s>>>(n, k, V, w, sc.part, sc.counter, out);
     return cudaGetLastError();
 }
 cudaError_t multiaxpy64(long long n, int k, const double* V, const double* c, double sign, double* w, cudaStream_t s) {
@@ -1933,17 +1940,17 @@ cudaError_t coarse_cg_single(const Level& C, const int* rowptr, const int* col, 
 
 cudaError_t cg_init(long long n, const double* b, const double* dinv, double* x, double* r, double* z, double* p,
                     Scratch& sc, double rtol2, cudaStream_t s) {
-    k_cg_init<<<reduce_blocks(), kRedThreads, 0, s>>>(n, b, dinv, x, r, z, p, sc.part, sc.counter, sc.scal, sc.flags,
+    k_cg_init<<<red_grid(n), kRedThreads, 0, s>>>(n, b, dinv, x, r, z, p, sc.part, sc.counter, sc.scal, sc.flags,
                                                        rtol2);
     return cudaGetLastError();
 }
 cudaError_t cg_pq(long long n, const double* p, const double* q, Scratch& sc, cudaStream_t s) {
-    k_cg_pq<<<reduce_blocks(), kRedThreads, 0, s>>>(n, p, q, sc.part, sc.counter, sc.scal, sc.flags);
+    k_cg_pq<<<red_grid(n), kRedThreads, 0, s>>>(n, p, q, sc.part, sc.counter, sc.scal, sc.flags);
     return cudaGetLastError();
 }
 cudaError_t cg_update(long long n, const double* dinv, double* x, double* r, double* z, const double* p,
                       const double* q, Scratch& sc, cudaStream_t s) {
-    k_cg_update<<<reduce_blocks(), kRedThreads, 0, s>>>(n, dinv, x, r, z, p, q, sc.part, sc.counter, sc.scal,
+    k_cg_update<<<red_grid(n), kRedThreads, 0, s>>>(n, dinv, x, r, z, p, q, sc.part, sc.counter, sc.scal,
                                                          sc.flags);
     return cudaGetLastError();
 }
