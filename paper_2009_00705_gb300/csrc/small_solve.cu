@@ -1,4 +1,4 @@
-// The whole Laplace solve of a small problem in one CTA and one launch: lifting of the
+// The whole Laplace solve of a small problem in one launch of one thread-block cluster: lifting of the
 // Dirichlet data (Eq. laplaceproblem), the outer FGMRES(m) or PCG iteration, and its
 // preconditioner, the p-multigrid V-cycle of Algorithm 1 with Chebyshev-Jacobi sweeps and
 // the direct coarse solve that the algorithm names (a dense inverse of the order-1
@@ -7,10 +7,15 @@
 // Launch latency, not bandwidth, bounds such problems: the 2D slice of 128 triangles at
 // P = 4 (1,040 free nodes) takes a few hundred kernels per FGMRES iteration on the
 // multi-kernel path.  Here every level's operator is a set of precomputed FP64 element
-// matrices (y = sum_e Q_e^T A_e Q_e x with the sums in shared memory), the transfers use
-// the reference interpolation matrix of each level pair, every vector stays in global
-// memory that only this CTA touches (L1/L2-resident), and the phases are separated by
-// CTA barriers.  The host reads the result once.
+// matrices (y = sum_e Q_e^T A_e Q_e x), the transfers use the reference interpolation matrix
+// of each level pair, and every vector stays in global memory that only this launch touches
+// (L2-resident).  One CTA would leave the solve bound by the FP64 pipe of a single SM (GB300
+// executes about two FP64 FMAs per clock per SM), so a cluster of up to eight CTAs shares the
+// work: each CTA takes a range of elements (its element sums in its own shared memory, summed
+// across the cluster through distributed shared memory) and a range of nodes for the vector
+// operations; the phases are separated by the cluster's hardware barrier, which its CTAs,
+// scheduled together, cannot wait on from outside.  The host reads the result once.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -51,13 +56,34 @@ struct SmallHost {
     std::vector<void*> owned;          // device buffers of the plan
     size_t smem = 0;
     int N0 = 0;
+    int cluster = 1;                   // CTAs of the launch's one cluster
 };
 
 namespace {
 
+namespace cg = cooperative_groups;
+
 constexpr int kSmallThreads = 1024;
-constexpr int kSmallMaxN = 8192;                 // finest nodes (the shared-memory accumulator)
-constexpr long long kSmallMaxWork = 1LL << 18;   // E Np^2 of the finest level: one apply on one SM
+constexpr int kSmallMaxN = 8192;                 // finest nodes (the shared-memory sums)
+constexpr long long kSmallMaxWork = 1LL << 20;   // E Np^2 of the finest level
+constexpr int kSmallCluster = 8;                 // CTAs of the cluster at most (portable size)
+constexpr int kSlot = 72;                        // partial sums exchanged per reduction
+
+// Per-CTA state: the cluster, this CTA's shared-memory buffers.  The CTAs of the cluster
+// split every element loop by elements and every vector loop by node ranges; data written by
+// one CTA and read by another crosses a cluster barrier (global memory read through L2).
+struct Ctx {
+    int rank, size;
+    double* acc;        // [N0] this CTA's element sums
+    double* xs;         // [N0] staged input vector
+    double* slot;       // [2][kSlot] this CTA's partial sums (read by the others)
+    double* tot;        // [kSlot] totals
+    int parity;
+};
+
+__device__ __forceinline__ void csync() { cg::this_cluster().sync(); }
+__device__ __forceinline__ int lo_of(int n, const Ctx& c) { return (int)((long long)n * c.rank / c.size); }
+__device__ __forceinline__ int hi_of(int n, const Ctx& c) { return (int)((long long)n * (c.rank + 1) / c.size); }
 
 __device__ __forceinline__ double sw_sum(double v) {
 #pragma unroll
@@ -65,38 +91,58 @@ __device__ __forceinline__ double sw_sum(double v) {
     return v;
 }
 
-// sum over the CTA of one value per thread (fixed order); every thread gets the total
-__device__ double cta_sum(double v, double* red) {
+// the cluster totals of nv values, entry i of this CTA's partials already in slot[parity][i]
+// (written by its threads before the call); every CTA sums the ranks in order, so all hold
+// the same totals, in tot[0 .. nv)
+__device__ void c_totals(Ctx& c, int nv) {
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+        double v[kSmallCluster];
+#pragma unroll
+        for (int r = 0; r < kSmallCluster; ++r)          // all remote loads first, then the sum in rank order
+            v[r] = r < c.size ? cl.map_shared_rank(c.slot, r)[c.parity * kSlot + i] : 0.0;
+        double t = 0.0;
+#pragma unroll
+        for (int r = 0; r < kSmallCluster; ++r) t += v[r];
+        c.tot[i] = t;
+    }
+    __syncthreads();
+    c.parity ^= 1;      // the other half is next; this one is rewritten only after another barrier
+}
+
+// cluster sum of one value per thread
+__device__ double c_sum(Ctx& c, double v, double* red) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     v = sw_sum(v);
-    __syncthreads();
     if (lane == 0) red[wid] = v;
     __syncthreads();
     if (wid == 0) {
         double w = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
         w = sw_sum(w);
-        if (lane == 0) red[32] = w;
+        if (lane == 0) c.slot[c.parity * kSlot] = w;
     }
-    __syncthreads();
-    return red[32];
+    c_totals(c, 1);
+    return c.tot[0];
 }
 
-__device__ double cta_dot(const double* a, const double* b, int n, double* red) {
+// (a, b) over the cluster (each CTA its node range)
+__device__ double c_dot(Ctx& c, const double* a, const double* b, int n, double* red) {
     double v = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) v += a[i] * b[i];
-    return cta_sum(v, red);
+    for (int i = lo_of(n, c) + threadIdx.x; i < hi_of(n, c); i += blockDim.x) v += __ldcg(a + i) * __ldcg(b + i);
+    return c_sum(c, v, red);
 }
 
-// the element rows of one level: acc[map_i] += sum_j A_e[i][j] xs[map_j] (xs in shared memory;
-// NP > 0 fixes the nodes per element at compile time so the row is unrolled)
+// the element rows of this CTA's elements: acc[map_i] += sum_j A_e[i][j] xs[map_j]
 template <int NP>
-__device__ void s_rows(const SmallLevel& L, const double* xs, bool lift, double* acc) {
+__device__ void s_rows(const SmallLevel& L, const double* xs, bool lift, double* acc, int e0, int e1) {
     const int Np = NP > 0 ? NP : L.Np;
-    const int rows = L.E * Np;
+    const int rows = (e1 - e0) * Np;
     for (int t = threadIdx.x; t < rows; t += blockDim.x) {
-        const int mi = L.map[t];
+        const int row = e0 * Np + t;
+        const int mi = L.map[row];
         if (mi < 0) continue;
-        const int e = t / Np, i = t - e * Np;
+        const int e = row / Np, i = row - e * Np;
         const int* me = L.map + (size_t)e * Np;
         const double* A = L.Ae + (size_t)e * Np * Np + i;          // column i = row i (symmetric)
         double v0 = 0.0, v1 = 0.0;
@@ -118,152 +164,178 @@ __device__ void s_rows(const SmallLevel& L, const double* xs, bool lift, double*
     }
 }
 
-// y = A x on a level (free rows; y = 0 at Dirichlet nodes); lift: x also at the Dirichlet
-// nodes (the lifting product A_FD x_D), else x there counts as zero.  x is staged in shared
-// memory (xs), the element sums gather in acc.
-__device__ void s_apply(const SmallLevel& L, const double* x, double* y, bool lift, double* acc) {
-    double* xs = acc + L.N;
-    for (int i = threadIdx.x; i < L.N; i += blockDim.x) {
-        acc[i] = 0.0;
-        xs[i] = x[i];
+// y_i = sum over the cluster's CTAs of acc[i] for this CTA's node range of n nodes, handed to
+// epi(i, y_i), which writes what the next phase reads
+template <typename Epi>
+__device__ void c_gather_sums(Ctx& c, int n, Epi epi) {
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();                                        // every CTA's sums are complete
+    for (int i = lo_of(n, c) + threadIdx.x; i < hi_of(n, c); i += blockDim.x) {
+        double v[kSmallCluster];
+#pragma unroll
+        for (int r = 0; r < kSmallCluster; ++r) v[r] = r < c.size ? cl.map_shared_rank(c.acc, r)[i] : 0.0;
+        double t = 0.0;
+#pragma unroll
+        for (int r = 0; r < kSmallCluster; ++r) t += v[r];
+        epi(i, t);
     }
-    __syncthreads();
-    switch (L.Np) {
-        case 3: s_rows<3>(L, xs, lift, acc); break;
-        case 6: s_rows<6>(L, xs, lift, acc); break;
-        case 10: s_rows<10>(L, xs, lift, acc); break;
-        case 15: s_rows<15>(L, xs, lift, acc); break;
-        case 18: s_rows<18>(L, xs, lift, acc); break;
-        case 21: s_rows<21>(L, xs, lift, acc); break;
-        case 28: s_rows<28>(L, xs, lift, acc); break;
-        case 40: s_rows<40>(L, xs, lift, acc); break;
-        default: s_rows<0>(L, xs, lift, acc); break;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < L.N; i += blockDim.x) y[i] = acc[i];
-    __syncthreads();
+    cl.sync();                                        // results complete; acc free for reuse
 }
 
-// one Chebyshev-Jacobi sweep of k_cheb steps (u = 0 on entry when zero_init)
-__device__ void s_sweep(const SmallLevel& L, int k, const double* f, double* u, bool zero_init, double* acc) {
+// The element sums acc of y = A x on a level (free rows; y = 0 at Dirichlet nodes); lift: x
+// also at the Dirichlet nodes (the lifting product A_FD x_D), else x there counts as zero
+__device__ void c_rows(Ctx& c, const SmallLevel& L, const double* x, bool lift) {
+    for (int i = threadIdx.x; i < L.N; i += blockDim.x) {
+        c.acc[i] = 0.0;
+        c.xs[i] = __ldcg(x + i);
+    }
+    __syncthreads();
+    const int e0 = lo_of(L.E, c), e1 = hi_of(L.E, c);
+    switch (L.Np) {
+        case 3: s_rows<3>(L, c.xs, lift, c.acc, e0, e1); break;
+        case 6: s_rows<6>(L, c.xs, lift, c.acc, e0, e1); break;
+        case 10: s_rows<10>(L, c.xs, lift, c.acc, e0, e1); break;
+        case 15: s_rows<15>(L, c.xs, lift, c.acc, e0, e1); break;
+        case 18: s_rows<18>(L, c.xs, lift, c.acc, e0, e1); break;
+        case 21: s_rows<21>(L, c.xs, lift, c.acc, e0, e1); break;
+        case 28: s_rows<28>(L, c.xs, lift, c.acc, e0, e1); break;
+        case 40: s_rows<40>(L, c.xs, lift, c.acc, e0, e1); break;
+        default: s_rows<0>(L, c.xs, lift, c.acc, e0, e1); break;
+    }
+}
+
+// y = A x.  Ends with a cluster barrier, as does every phase below that writes a vector another
+// CTA reads.
+__device__ void c_apply(Ctx& c, const SmallLevel& L, const double* x, double* y, bool lift) {
+    c_rows(c, L, x, lift);
+    c_gather_sums(c, L.N, [&](int i, double v) { y[i] = v; });
+}
+
+// one Chebyshev-Jacobi sweep of k steps (u = 0 on entry when zero_init), node ranges
+__device__ void c_sweep(Ctx& c, const SmallLevel& L, int k, const double* f, double* u, bool zero_init) {
+    const int n0 = lo_of(L.N, c), n1 = hi_of(L.N, c);
     if (zero_init) {
-        for (int i = threadIdx.x; i < L.N; i += blockDim.x) {
-            const double v = L.c0 * L.dinv[i] * f[i];
+        for (int i = n0 + threadIdx.x; i < n1; i += blockDim.x) {
+            const double v = L.c0 * L.dinv[i] * __ldcg(f + i);
             L.d[i] = v;
             u[i] = v;
         }
-        __syncthreads();
+        csync();
     } else {
-        s_apply(L, u, L.y, false, acc);
-        for (int i = threadIdx.x; i < L.N; i += blockDim.x) {
-            const double v = L.c0 * L.dinv[i] * (f[i] - L.y[i]);
+        c_rows(c, L, u, false);
+        c_gather_sums(c, L.N, [&](int i, double y) {          // the step on the fly from (A u)_i
+            const double v = L.c0 * L.dinv[i] * (__ldcg(f + i) - y);
             L.d[i] = v;
-            u[i] += v;
-        }
-        __syncthreads();
+            u[i] = __ldcg(u + i) + v;
+        });
     }
     for (int j = 1; j < k; ++j) {
-        s_apply(L, u, L.y, false, acc);
-        for (int i = threadIdx.x; i < L.N; i += blockDim.x) {
-            const double v = L.c1[j] * L.d[i] + L.c2[j] * L.dinv[i] * (f[i] - L.y[i]);
+        c_rows(c, L, u, false);
+        const double c1 = L.c1[j], c2 = L.c2[j];
+        c_gather_sums(c, L.N, [&](int i, double y) {
+            const double v = c1 * L.d[i] + c2 * L.dinv[i] * (__ldcg(f + i) - y);
             L.d[i] = v;
-            u[i] += v;
-        }
-        __syncthreads();
+            u[i] = __ldcg(u + i) + v;
+        });
     }
 }
 
 // fc = R (f - y) onto the next coarser level C (R = P^T, fine values weighted by 1/multiplicity)
-__device__ void s_restrict(const SmallLevel& F, const SmallLevel& C, const double* f, const double* y, double* fc,
-                           double* acc) {
-    for (int i = threadIdx.x; i < C.N; i += blockDim.x) acc[i] = 0.0;
+__device__ void c_restrict(Ctx& c, const SmallLevel& F, const SmallLevel& C, const double* f, const double* y,
+                           double* fc) {
+    for (int i = threadIdx.x; i < C.N; i += blockDim.x) c.acc[i] = 0.0;
     __syncthreads();
-    const int rows = F.E * F.Npc;
+    const int e0 = lo_of(F.E, c), e1 = hi_of(F.E, c);
+    const int rows = (e1 - e0) * F.Npc;
     for (int t = threadIdx.x; t < rows; t += blockDim.x) {
-        const int mc = F.mapc[t];
+        const int row = e0 * F.Npc + t;
+        const int mc = F.mapc[row];
         if (mc < 0) continue;
-        const int e = t / F.Npc, nc = t - e * F.Npc;
+        const int e = row / F.Npc, nc = row - e * F.Npc;
         const int* mf = F.map + (size_t)e * F.Np;
         double v = 0.0;
         for (int nf = 0; nf < F.Np; ++nf) {
             const int m = mf[nf];
-            if (m >= 0) v = fma(F.I[(size_t)nf * F.Npc + nc], F.wmult[m] * (f[m] - y[m]), v);
+            if (m >= 0) v = fma(F.I[(size_t)nf * F.Npc + nc], F.wmult[m] * (__ldcg(f + m) - __ldcg(y + m)), v);
         }
-        atomicAdd(&acc[mc], v);
+        atomicAdd(&c.acc[mc], v);
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < C.N; i += blockDim.x) fc[i] = acc[i];
-    __syncthreads();
+    c_gather_sums(c, C.N, [&](int i, double v) { fc[i] = v; });
 }
 
 // uf += P uc from the next coarser level (each fine node written by its owner element)
-__device__ void s_prolong(const SmallLevel& F, const double* uc, double* uf) {
-    const int rows = F.E * F.Np;
+__device__ void c_prolong(Ctx& c, const SmallLevel& F, const double* uc, double* uf) {
+    const int e0 = lo_of(F.E, c), e1 = hi_of(F.E, c);
+    const int rows = (e1 - e0) * F.Np;
     for (int t = threadIdx.x; t < rows; t += blockDim.x) {
-        const int m = F.map[t];
-        if (m < 0 || !F.owner[t]) continue;
-        const int e = t / F.Np, nf = t - e * F.Np;
+        const int row = e0 * F.Np + t;
+        const int m = F.map[row];
+        if (m < 0 || !F.owner[row]) continue;
+        const int e = row / F.Np, nf = row - e * F.Np;
         const int* mc = F.mapc + (size_t)e * F.Npc;
         double v = 0.0;
         for (int nc = 0; nc < F.Npc; ++nc) {
-            const int c = mc[nc];
-            if (c >= 0) v = fma(F.I[(size_t)nf * F.Npc + nc], uc[c], v);
+            const int cc = mc[nc];
+            if (cc >= 0) v = fma(F.I[(size_t)nf * F.Npc + nc], __ldcg(uc + cc), v);
         }
-        uf[m] += v;
+        uf[m] = __ldcg(uf + m) + v;
     }
-    __syncthreads();
+    csync();
 }
 
 // u = A_c^{-1} f on the coarsest level (the dense inverse is symmetric: column i read as row i)
-__device__ void s_coarse(const SmallPlan& P, const double* f, double* u) {
-    for (int i = threadIdx.x; i < P.Nc; i += blockDim.x) {
+__device__ void c_coarse(Ctx& c, const SmallPlan& P, const double* f, double* u) {
+    for (int i = lo_of(P.Nc, c) + threadIdx.x; i < hi_of(P.Nc, c); i += blockDim.x) {
         double v = 0.0;
-        for (int j = 0; j < P.Nc; ++j) v = fma(P.Cinv[(size_t)j * P.Nc + i], f[j], v);
+        for (int j = 0; j < P.Nc; ++j) v = fma(P.Cinv[(size_t)j * P.Nc + i], __ldcg(f + j), v);
         u[i] = v;
     }
-    __syncthreads();
+    csync();
 }
 
 // z = M^{-1} f: Algorithm 1 with u = 0 on entry at every level
-__device__ void s_vcycle(const SmallPlan& P, const double* f0, double* u0, double* acc) {
+__device__ void c_vcycle(Ctx& c, const SmallPlan& P, const double* f0, double* u0) {
     const int nl = P.nl;
     if (nl == 1) {
-        s_coarse(P, f0, u0);
+        c_coarse(c, P, f0, u0);
         return;
     }
     for (int li = 0; li + 1 < nl; ++li) {
         const SmallLevel& L = P.lv[li];
         const double* f = li == 0 ? f0 : L.f;
         double* u = li == 0 ? u0 : L.u;
-        for (int m = 0; m < P.nu1; ++m) s_sweep(L, P.k_cheb, f, u, m == 0, acc);
+        for (int m = 0; m < P.nu1; ++m) c_sweep(c, L, P.k_cheb, f, u, m == 0);
         if (P.nu1 == 0) {
-            for (int i = threadIdx.x; i < L.N; i += blockDim.x) u[i] = 0.0;
-            __syncthreads();
+            for (int i = lo_of(L.N, c) + threadIdx.x; i < hi_of(L.N, c); i += blockDim.x) u[i] = 0.0;
+            csync();
         }
-        s_apply(L, u, L.y, false, acc);
-        s_restrict(L, P.lv[li + 1], f, L.y, P.lv[li + 1].f, acc);
+        c_apply(c, L, u, L.y, false);
+        c_restrict(c, L, P.lv[li + 1], f, L.y, P.lv[li + 1].f);
     }
-    s_coarse(P, P.lv[nl - 1].f, P.lv[nl - 1].u);
+    c_coarse(c, P, P.lv[nl - 1].f, P.lv[nl - 1].u);
     for (int li = nl - 2; li >= 0; --li) {
         const SmallLevel& L = P.lv[li];
         const double* f = li == 0 ? f0 : L.f;
         double* u = li == 0 ? u0 : L.u;
-        s_prolong(L, P.lv[li + 1].u, u);
-        for (int m = 0; m < P.nu2; ++m) s_sweep(L, P.k_cheb, f, u, false, acc);
+        c_prolong(c, L, P.lv[li + 1].u, u);
+        for (int m = 0; m < P.nu2; ++m) c_sweep(c, L, P.k_cheb, f, u, false);
     }
 }
 
 // The solve: lifting, then FGMRES(m) (classical Gram-Schmidt twice, Givens rotations,
 // restarts) or PCG, each preconditioned by one V-cycle, to ||f - A u|| <= rtol ||f|| + atol.
-// Shared memory: the accumulator of the element sums [N0], reduction scratch, and the
-// Hessenberg matrix, rotations and right-hand side of FGMRES.
+// Every CTA of the cluster runs the same control flow: the loop tests read totals that all
+// CTAs compute alike, and the small dense work (rotations, the triangular solve) is repeated
+// by thread 0 of every CTA on identical data.
 __global__ void __launch_bounds__(kSmallThreads) k_small_solve(const SmallPlan* __restrict__ plan,
                                                               const double* __restrict__ rhs,
                                                               const double* __restrict__ eta, double* phi,
                                                               double rtol, double atol) {
     __shared__ SmallPlan P;
-    __shared__ double sc[8];                   // broadcast scalars
-    __shared__ int si[4];
+    __shared__ double sc[4];
+    __shared__ double red[33];
+    __shared__ double slot[2 * kSlot];
+    __shared__ double tot[kSlot];
     {
         const int* src = reinterpret_cast<const int*>(plan);
         int* dst = reinterpret_cast<int*>(&P);
@@ -273,71 +345,82 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_solve(const SmallPlan* 
     const SmallLevel& L0 = P.lv[0];
     const int N = L0.N, m = P.m;
     extern __shared__ __align__(16) double ssm[];
-    double* acc = ssm;                         // [N0] element sums, then [N0] staged x (s_apply)
-    double* red = acc + 2 * N;                 // [40]
-    double* H = red + 40;                      // [(m + 1) m]
+    Ctx c;
+    c.rank = (int)cg::this_cluster().block_rank();
+    c.size = (int)cg::this_cluster().num_blocks();
+    c.acc = ssm;                                // [N0]
+    c.xs = ssm + N;                             // [N0]
+    c.slot = slot;
+    c.tot = tot;
+    c.parity = 0;
+    double* H = ssm + 2 * N;                    // [(m + 1) m]
     double* cs = H + (size_t)(m + 1) * m;      // [m]
     double* sn = cs + m;                       // [m]
     double* g = sn + m;                        // [m + 1]
     double* yv = g + m + 1;                    // [m]
     double* hk = yv + m;                       // [2 (m + 1)] the two Gram-Schmidt passes
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
+    const int n0 = lo_of(N, c), n1 = hi_of(N, c);
+    const int d0 = lo_of(P.nd, c), d1 = hi_of(P.nd, c);
     int vcycles = 0, applies = 0;
 
     // lifting: f = rhs - A_FD phi_D on the free nodes
-    for (int i = t; i < N; i += blockDim.x) P.x[i] = 0.0;
-    __syncthreads();
-    for (int k = t; k < P.nd; k += blockDim.x) P.x[P.dir[k]] = eta[k];
-    __syncthreads();
-    s_apply(L0, P.x, P.q, true, acc);
-    for (int i = t; i < N; i += blockDim.x) P.fr[i] = (rhs != nullptr ? rhs[i] : 0.0) - P.q[i];
-    __syncthreads();
-    for (int k = t; k < P.nd; k += blockDim.x) P.fr[P.dir[k]] = 0.0;
-    __syncthreads();
-    const double fnorm = sqrt(cta_dot(P.fr, P.fr, N, red));
+    for (int i = n0 + t; i < n1; i += blockDim.x) P.x[i] = 0.0;
+    csync();
+    for (int k = d0 + t; k < d1; k += blockDim.x) P.x[P.dir[k]] = eta[k];
+    csync();
+    c_apply(c, L0, P.x, P.q, true);
+    for (int i = n0 + t; i < n1; i += blockDim.x) P.fr[i] = (rhs != nullptr ? rhs[i] : 0.0) - __ldcg(P.q + i);
+    csync();
+    for (int k = d0 + t; k < d1; k += blockDim.x) P.fr[P.dir[k]] = 0.0;
+    csync();
+    const double fnorm = sqrt(c_dot(c, P.fr, P.fr, N, red));
     const double thr = rtol * fnorm + atol;
-    for (int i = t; i < N; i += blockDim.x) phi[i] = 0.0;
-    __syncthreads();
+    for (int i = n0 + t; i < n1; i += blockDim.x) phi[i] = 0.0;
+    csync();
     int status = isfinite(fnorm) ? (int)SEM_OK : (int)SEM_NAN;
     int it = 0;
     double res = fnorm;
     if (status == SEM_OK && P.outer == SEM_OUTER_FGMRES) {
-        for (int i = t; i < N; i += blockDim.x) P.r[i] = P.fr[i];
-        __syncthreads();
+        for (int i = n0 + t; i < n1; i += blockDim.x) P.r[i] = __ldcg(P.fr + i);
+        csync();
         double beta = fnorm;
         while (beta > thr) {
             if (it >= P.imax) { status = SEM_NOT_CONVERGED; break; }
-            for (int i = t; i < N; i += blockDim.x) P.V[i] = P.r[i] / beta;
+            for (int i = n0 + t; i < n1; i += blockDim.x) P.V[i] = __ldcg(P.r + i) / beta;
             for (int i = t; i < (m + 1) * m; i += blockDim.x) H[i] = 0.0;
             for (int i = t; i <= m; i += blockDim.x) g[i] = 0.0;
-            __syncthreads();
+            csync();
             if (t == 0) g[0] = beta;
             int j = 0;
             while (j < m && it < P.imax) {
                 const double* vj = P.V + (size_t)j * N;
                 double* zj = P.Z + (size_t)j * N;
                 double* w = P.V + (size_t)(j + 1) * N;
-                s_vcycle(P, vj, zj, acc);
+                c_vcycle(c, P, vj, zj);
                 ++vcycles;
-                s_apply(L0, zj, w, false, acc);
+                c_apply(c, L0, zj, w, false);
                 ++applies;
                 for (int pass = 0; pass < 2; ++pass) {           // classical Gram-Schmidt, twice
                     for (int k = wid; k <= j; k += nw) {
                         const double* vk = P.V + (size_t)k * N;
                         double v = 0.0;
-                        for (int i = lane; i < N; i += 32) v += vk[i] * w[i];
+                        for (int i = n0 + lane; i < n1; i += 32) v += __ldcg(vk + i) * __ldcg(w + i);
                         v = sw_sum(v);
-                        if (lane == 0) hk[pass * (m + 1) + k] = v;
+                        if (lane == 0) c.slot[c.parity * kSlot + k] = v;
                     }
                     __syncthreads();
-                    for (int i = t; i < N; i += blockDim.x) {
-                        double wi = w[i];
-                        for (int k = 0; k <= j; ++k) wi -= hk[pass * (m + 1) + k] * P.V[(size_t)k * N + i];
+                    c_totals(c, j + 1);
+                    for (int k = t; k <= j; k += blockDim.x) hk[pass * (m + 1) + k] = c.tot[k];
+                    __syncthreads();
+                    for (int i = n0 + t; i < n1; i += blockDim.x) {
+                        double wi = __ldcg(w + i);
+                        for (int k = 0; k <= j; ++k) wi -= hk[pass * (m + 1) + k] * __ldcg(P.V + (size_t)k * N + i);
                         w[i] = wi;
                     }
-                    __syncthreads();
+                    csync();
                 }
-                const double hn = sqrt(cta_dot(w, w, N, red));
+                const double hn = sqrt(c_dot(c, w, w, N, red));
                 if (t == 0) {
                     for (int k = 0; k <= j; ++k) H[(size_t)k * m + j] = hk[k] + hk[m + 1 + k];
                     H[(size_t)(j + 1) * m + j] = hn;
@@ -356,8 +439,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_solve(const SmallPlan* 
                     sc[0] = fabs(g[j + 1]);
                 }
                 if (hn > 0.0)
-                    for (int i = t; i < N; i += blockDim.x) w[i] /= hn;
-                __syncthreads();
+                    for (int i = n0 + t; i < n1; i += blockDim.x) w[i] = __ldcg(w + i) / hn;
+                csync();
                 ++j;
                 ++it;
                 res = sc[0];
@@ -372,57 +455,57 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_solve(const SmallPlan* 
                     yv[k] = v / H[(size_t)k * m + k];
                 }
             __syncthreads();
-            for (int i = t; i < N; i += blockDim.x) {
-                double u = phi[i];
-                for (int k = 0; k < j; ++k) u += yv[k] * P.Z[(size_t)k * N + i];
+            for (int i = n0 + t; i < n1; i += blockDim.x) {
+                double u = __ldcg(phi + i);
+                for (int k = 0; k < j; ++k) u += yv[k] * __ldcg(P.Z + (size_t)k * N + i);
                 phi[i] = u;
             }
-            __syncthreads();
-            s_apply(L0, phi, P.q, false, acc);
+            csync();
+            c_apply(c, L0, phi, P.q, false);
             ++applies;
-            for (int i = t; i < N; i += blockDim.x) P.r[i] = P.fr[i] - P.q[i];
-            __syncthreads();
-            beta = sqrt(cta_dot(P.r, P.r, N, red));
+            for (int i = n0 + t; i < n1; i += blockDim.x) P.r[i] = __ldcg(P.fr + i) - __ldcg(P.q + i);
+            csync();
+            beta = sqrt(c_dot(c, P.r, P.r, N, red));
             res = beta;
             if (!isfinite(beta)) { status = SEM_NAN; break; }
         }
     } else if (status == SEM_OK) {                          // PCG
-        for (int i = t; i < N; i += blockDim.x) P.r[i] = P.fr[i];
-        __syncthreads();
+        for (int i = n0 + t; i < n1; i += blockDim.x) P.r[i] = __ldcg(P.fr + i);
+        csync();
         if (res > thr) {
-            s_vcycle(P, P.r, P.z, acc);
+            c_vcycle(c, P, P.r, P.z);
             ++vcycles;
-            for (int i = t; i < N; i += blockDim.x) P.p[i] = P.z[i];
-            __syncthreads();
-            double rz = cta_dot(P.z, P.r, N, red);
+            for (int i = n0 + t; i < n1; i += blockDim.x) P.p[i] = __ldcg(P.z + i);
+            csync();
+            double rz = c_dot(c, P.z, P.r, N, red);
             for (;;) {
                 if (it >= P.imax) { status = SEM_NOT_CONVERGED; break; }
-                s_apply(L0, P.p, P.q, false, acc);
+                c_apply(c, L0, P.p, P.q, false);
                 ++applies;
-                const double pq = cta_dot(P.p, P.q, N, red);
+                const double pq = c_dot(c, P.p, P.q, N, red);
                 const double alpha = rz / pq;
-                for (int i = t; i < N; i += blockDim.x) {
-                    phi[i] += alpha * P.p[i];
-                    P.r[i] -= alpha * P.q[i];
+                for (int i = n0 + t; i < n1; i += blockDim.x) {
+                    phi[i] = __ldcg(phi + i) + alpha * __ldcg(P.p + i);
+                    P.r[i] = __ldcg(P.r + i) - alpha * __ldcg(P.q + i);
                 }
-                __syncthreads();
+                csync();
                 ++it;
-                res = sqrt(cta_dot(P.r, P.r, N, red));
+                res = sqrt(c_dot(c, P.r, P.r, N, red));
                 if (!isfinite(res)) { status = SEM_NAN; break; }
                 if (!(pq > 0.0)) { status = SEM_BREAKDOWN; break; }
                 if (res <= thr) break;
-                s_vcycle(P, P.r, P.z, acc);
+                c_vcycle(c, P, P.r, P.z);
                 ++vcycles;
-                const double rzn = cta_dot(P.z, P.r, N, red);
+                const double rzn = c_dot(c, P.z, P.r, N, red);
                 const double beta = rzn / rz;
                 rz = rzn;
-                for (int i = t; i < N; i += blockDim.x) P.p[i] = P.z[i] + beta * P.p[i];
-                __syncthreads();
+                for (int i = n0 + t; i < n1; i += blockDim.x) P.p[i] = __ldcg(P.z + i) + beta * __ldcg(P.p + i);
+                csync();
             }
         }
     }
-    for (int k = t; k < P.nd; k += blockDim.x) phi[P.dir[k]] = eta[k];
-    if (t == 0) {
+    for (int k = d0 + t; k < d1; k += blockDim.x) phi[P.dir[k]] = eta[k];
+    if (c.rank == 0 && t == 0) {
         P.out[0] = it;
         P.out[1] = fnorm;
         P.out[2] = res;
@@ -430,7 +513,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_solve(const SmallPlan* 
         P.out[4] = vcycles;
         P.out[5] = applies;
     }
-    (void)si;
+    csync();            // no CTA leaves while another may still read its shared memory
 }
 
 }  // namespace
@@ -583,6 +666,7 @@ sem_status build_small_plan(sem_handle* h) {
     if (e == cudaSuccess) e = small_alloc(*S, &S->dplan, 1);
     if (e == cudaSuccess) e = cudaMemcpy(S->dplan, &P, sizeof(SmallPlan), cudaMemcpyHostToDevice);
     S->N0 = (int)N0;
+    S->cluster = std::max(1, std::min(kSmallCluster, L0.E / 16));     // at least 16 elements per CTA
     S->smem = sizeof(double) * (2 * N0 + 40 + (size_t)(m + 1) * m + 2 * (size_t)m + (m + 1) + m + 2 * (size_t)(m + 1));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_small_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S->smem);
@@ -604,8 +688,21 @@ sem_status small_solve(sem_handle* h, const double* rhs, const double* eta, doub
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     if (e == cudaSuccess) e = cudaEventRecord(e0, s);
     if (e == cudaSuccess) {
-        k_small_solve<<<1, kSmallThreads, S->smem, s>>>(S->dplan, rhs, eta, phi, rtol, h->opts.atol);
-        e = cudaGetLastError();
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)S->cluster;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)S->cluster);
+        cfg.blockDim = dim3(kSmallThreads);
+        cfg.dynamicSmemBytes = S->smem;
+        cfg.stream = s;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        const SmallPlan* dp = S->dplan;
+        const double at_ = h->opts.atol;
+        e = cudaLaunchKernelEx(&cfg, k_small_solve, dp, rhs, eta, phi, rtol, at_);
     }
     double out[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (e == cudaSuccess) e = cudaEventRecord(e1, s);
