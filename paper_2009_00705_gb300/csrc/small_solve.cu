@@ -63,10 +63,10 @@ namespace {
 
 namespace cg = cooperative_groups;
 
-constexpr int kSmallThreads = 1024;
+constexpr int kSmallThreads = 256;
 constexpr int kSmallMaxN = 8192;                 // finest nodes (the shared-memory sums)
 constexpr long long kSmallMaxWork = 1LL << 20;   // E Np^2 of the finest level
-constexpr int kSmallCluster = 8;                 // CTAs of the cluster at most (portable size)
+constexpr int kSmallCluster = 8;                 // CTAs of the cluster at most (portable size; 16 was no faster)
 constexpr int kSlot = 72;                        // partial sums exchanged per reduction
 
 // Per-CTA state: the cluster, this CTA's shared-memory buffers.  The CTAs of the cluster
@@ -666,8 +666,8 @@ sem_status build_small_plan(sem_handle* h) {
     if (e == cudaSuccess) e = small_alloc(*S, &S->dplan, 1);
     if (e == cudaSuccess) e = cudaMemcpy(S->dplan, &P, sizeof(SmallPlan), cudaMemcpyHostToDevice);
     S->N0 = (int)N0;
-    S->cluster = std::max(1, std::min(kSmallCluster, L0.E / 16));     // at least 16 elements per CTA
     S->smem = sizeof(double) * (2 * N0 + 40 + (size_t)(m + 1) * m + 2 * (size_t)m + (m + 1) + m + 2 * (size_t)(m + 1));
+    S->cluster = std::max(1, std::min(kSmallCluster, L0.E / 16));     // at least 16 elements per CTA
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_small_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S->smem);
     if (e != cudaSuccess) {
