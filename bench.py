@@ -609,8 +609,21 @@ def main():
                    "apply_fp64": fp64_view(sum(x["apply_ms"] for x in st_m), sum(x["apply_launches"] for x in st_m),
                                            ms_solver.elem_matrices(0))}
             if prec == "mixed_tf32":
-                obj["apply_tf32_tensor_cores"] = apply_view(sum(x["apply_tc_ms"] for x in st_m),
-                                                            sum(x["apply_tc_launches"] for x in st_m), 4, gword=2)
+                tcv = apply_view(sum(x["apply_tc_ms"] for x in st_m),
+                                 sum(x["apply_tc_launches"] for x in st_m), 4, gword=2)
+                if tcv is not None:
+                    # the tensor-pipe view: the two triangle contractions of the sum-factorised apply
+                    # (forward [Dr|Ds] and Bt, backward) run on the tensor cores, TF32 dense peak
+                    # taken as half the measured BF16 peak (the nominal TF32 : BF16 ratio)
+                    NT_, QT_, QZ_ = (P + 1) * (P + 2) // 2, (P + 1) ** 2, P + 1
+                    mma_flops = 2 * 2 * 3 * QT_ * NT_ * QZ_ * E
+                    tf32_peak = peaks.get("bf16_tflops", 1900.0) / 2.0
+                    tcv["tensor_view"] = {"mma_flops_per_launch": mma_flops,
+                                          "achieved_tflops": mma_flops / (tcv["avg_launch_ms"] / 1e3) / 1e12,
+                                          "tf32_peak_tflops": tf32_peak,
+                                          "frac_of_tensor_peak": mma_flops / (tcv["avg_launch_ms"] / 1e3) / 1e12 / tf32_peak,
+                                          "peak_source": "half the measured bf16 GEMM peak (MEASURED_PEAKS.json)"}
+                obj["apply_tf32_tensor_cores"] = tcv
                 # the order-6 operator through sem_apply32 (memset of y, kernel, Dirichlet copy) with
                 # the warp-MMA kernel the V-cycle uses and with the tcgen05 kernel
                 xa = torch.rand(N, dtype=torch.float32, device="cuda")
