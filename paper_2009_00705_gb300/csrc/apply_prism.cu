@@ -224,31 +224,41 @@ __global__ void __launch_bounds__(PrismTile<P, PZ, T, V>::NTHR)
 // FP64 apply from precomputed element matrices: y_e = A_e x_e with A_e = sum_q sum_ab
 // D_a^T G_ab D_b (Eq. laplaceproblemdiscrete at the same quadrature), 2 Np^2 flops per element
 // against 132 k for the sum-factorised contraction at P = 6; A_e streamed once per apply.
-// EPC elements per CTA pass, TPE threads per element (Np rounded up to a warp); thread i of an
-// element forms row i of A_e x_e from column i of the symmetric A_e (coalesced across the warp),
-// with four partial sums.  Gather masking, lifting, element lists and the element-result output
-// as in k_apply_prism.
+// The rows of all elements form one flat index space, kElemRows consecutive rows per CTA
+// pass, so every lane of every warp holds a row (no lanes idle at element boundaries: the FP64
+// pipe bounds this kernel).  A pass stages x of the elements its rows touch in shared memory
+// (an element at either end may be shared with the neighbouring pass); thread t forms row
+// i = r mod Np of element e = r / Np from column i of the symmetric A_e (coalesced across the
+// warp), with four partial sums.  Gather masking, lifting, element lists and the element-result
+// output as in k_apply_prism.
+constexpr int kElemRows = 512;
+
 template <bool LIFT>
-__global__ void __launch_bounds__(256) k_apply_elem64(int E, int Np, int TPE, int EPC, const int* __restrict__ map,
-                                                      const double* __restrict__ Ae, const double* __restrict__ x,
-                                                      double* __restrict__ y, const int* __restrict__ skip,
-                                                      const int* __restrict__ elist, double* __restrict__ ye) {
+__global__ void __launch_bounds__(kElemRows) k_apply_elem64(int E, int Np, const int* __restrict__ map,
+                                                         const double* __restrict__ Ae, const double* __restrict__ x,
+                                                         double* __restrict__ y, const int* __restrict__ skip,
+                                                         const int* __restrict__ elist, double* __restrict__ ye) {
     if (skip != nullptr && *skip) return;
-    extern __shared__ __align__(16) double xs[];      // [EPC][Np]
-    const int slot = threadIdx.x / TPE, i = threadIdx.x - slot * TPE;
-    for (long long e0 = (long long)blockIdx.x * EPC; e0 < E; e0 += (long long)gridDim.x * EPC) {
-        const long long eb = e0 + slot;
-        const bool act = slot < EPC && eb < E && i < Np;
-        const size_t e = act ? (size_t)(elist ? elist[eb] : eb) : 0;
-        int m = -1;
-        if (act) {
-            m = map[e * Np + i];
-            xs[slot * Np + i] = (m >= 0) ? x[m] : (LIFT ? x[-m - 1] : 0.0);
+    extern __shared__ __align__(16) double xs[];      // [elements of the pass][Np]
+    const long long R = (long long)E * Np;
+    for (long long r0 = (long long)blockIdx.x * kElemRows; r0 < R; r0 += (long long)gridDim.x * kElemRows) {
+        const long long r1 = r0 + kElemRows < R ? r0 + kElemRows : R;
+        const long long ea = r0 / Np, eb = (r1 - 1) / Np;        // first and last element of the pass
+        const int nx = (int)(eb - ea + 1) * Np;
+        for (int k = threadIdx.x; k < nx; k += blockDim.x) {
+            const long long el = ea + k / Np;
+            const size_t e = (size_t)(elist ? elist[el] : el);
+            const int m = map[e * Np + (k % Np)];
+            xs[k] = (m >= 0) ? x[m] : (LIFT ? x[-m - 1] : 0.0);
         }
         __syncthreads();
-        if (act) {
+        const long long r = r0 + threadIdx.x;
+        if (r < r1) {
+            const long long el = r / Np;
+            const int i = (int)(r - el * Np);
+            const size_t e = (size_t)(elist ? elist[el] : el);
             const double* A = Ae + e * (size_t)Np * Np + i;
-            const double* xv = xs + slot * Np;
+            const double* xv = xs + (el - ea) * Np;
             double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
             int j = 0;
             for (; j + 3 < Np; j += 4) {
@@ -260,28 +270,29 @@ __global__ void __launch_bounds__(256) k_apply_elem64(int E, int Np, int TPE, in
             for (; j < Np; ++j) s0 = fma(__ldcs(A + (size_t)j * Np), xv[j], s0);
             const double v = (s0 + s1) + (s2 + s3);
             if (ye != nullptr) ye[e * Np + i] = v;
-            else if (m >= 0) atomicAdd(&y[m], v);
+            else {
+                const int m = map[e * Np + i];
+                if (m >= 0) atomicAdd(&y[m], v);
+            }
         }
         __syncthreads();
     }
 }
 
 cudaError_t apply_elem64(const Level& L, const double* x, double* y, bool lift, const int* skip, cudaStream_t s) {
-    const int TPE = (L.Np + 31) / 32 * 32;
-    const int EPC = TPE >= 256 ? 1 : 256 / TPE;
-    const int threads = EPC * TPE;
     double* ye = L.ye64;
     const bool sub = lift && L.lift_elems != nullptr && ye == nullptr;
     const int E = sub ? L.nlift : L.E;
-    const long long passes = ((long long)E + EPC - 1) / EPC;
-    const int grid = (int)std::min<long long>(passes, (long long)kSMs * 8);
+    const long long passes = ((long long)E * L.Np + kElemRows - 1) / kElemRows;
+    const int grid = (int)std::min<long long>(passes, (long long)kSMs * 4);
     if (grid < 1) return cudaSuccess;
-    const size_t smem = sizeof(double) * (size_t)EPC * L.Np;
+    // a pass touches at most kElemRows / Np + 2 elements
+    const size_t smem = sizeof(double) * (size_t)(kElemRows / L.Np + 2) * L.Np;
     if (lift)
-        k_apply_elem64<true><<<grid, threads, smem, s>>>(E, L.Np, TPE, EPC, L.map, L.Ae64, x, y, skip,
-                                                          sub ? L.lift_elems : nullptr, ye);
+        k_apply_elem64<true><<<grid, kElemRows, smem, s>>>(E, L.Np, L.map, L.Ae64, x, y, skip,
+                                                           sub ? L.lift_elems : nullptr, ye);
     else
-        k_apply_elem64<false><<<grid, threads, smem, s>>>(E, L.Np, TPE, EPC, L.map, L.Ae64, x, y, skip, nullptr, ye);
+        k_apply_elem64<false><<<grid, kElemRows, smem, s>>>(E, L.Np, L.map, L.Ae64, x, y, skip, nullptr, ye);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || ye == nullptr) return e;
     return dss_gather64(L, ye, y, skip, s, true);

@@ -1964,8 +1964,7 @@ cudaError_t cg_direction(long long n, const double* z, double* p, Scratch& sc, c
 // Sixteen independent fused multiply-add chains per thread on every SM: the FP64 rate the
 // device reaches on plain dependent-free arithmetic, the denominator of the FP64 apply's
 // roofline.
-constexpr int kFmaChains = 16;
-
+template <int kFmaChains>
 __global__ void k_fp64_fma_chains(int iters, double seed, double* sink) {
     double a[kFmaChains];
 #pragma unroll
@@ -1984,6 +1983,35 @@ __global__ void k_fp64_fma_chains(int iters, double seed, double* sink) {
 
 }  // namespace sem
 
+namespace {
+// one timed launch of the chain kernel with `chains` independent FMA chains per thread
+template <int chains>
+cudaError_t fp64_rate_run(int blocks, int threads, int iters, double* tflops) {
+    cudaEvent_t e0, e1;
+    cudaError_t err = cudaEventCreate(&e0);
+    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    float ms = 0.f;
+    if (err == cudaSuccess) {
+        sem::k_fp64_fma_chains<chains><<<blocks, threads>>>(iters / 8, 1.0, nullptr);      // warm-up
+        err = cudaEventRecord(e0, 0);
+    }
+    if (err == cudaSuccess) {
+        sem::k_fp64_fma_chains<chains><<<blocks, threads>>>(iters, 1.0, nullptr);
+        err = cudaGetLastError();
+    }
+    if (err == cudaSuccess) err = cudaEventRecord(e1, 0);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err == cudaSuccess && !(ms > 0.f)) err = cudaErrorUnknown;
+    if (err == cudaSuccess) *tflops = 2.0 * chains * iters * (double)threads * blocks / (ms * 1e-3) / 1e12;
+    return err;
+}
+}  // namespace
+
+// The best of three shapes (8, 16 and 24 independent chains per thread, as many threads as fit):
+// the FP64 pipe's rate on this device as a roofline denominator beside the nominal one.
 extern "C" sem_status sem_fp64_rate(double* tflops_host) {
     using namespace sem;
     if (!tflops_host) {
@@ -1994,28 +2022,15 @@ extern "C" sem_status sem_fp64_rate(double* tflops_host) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int threads = 256, blocks = 8 * sms, iters = 1 << 13;
-    cudaEvent_t e0, e1;
-    cudaError_t err = cudaEventCreate(&e0);
-    if (err == cudaSuccess) err = cudaEventCreate(&e1);
-    float ms = 0.f;
-    if (err == cudaSuccess) {
-        k_fp64_fma_chains<<<blocks, threads>>>(256, 1.0, nullptr);      // warm-up
-        err = cudaEventRecord(e0, 0);
-    }
-    if (err == cudaSuccess) {
-        k_fp64_fma_chains<<<blocks, threads>>>(iters, 1.0, nullptr);
-        err = cudaGetLastError();
-    }
-    if (err == cudaSuccess) err = cudaEventRecord(e1, 0);
-    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
-    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (err != cudaSuccess || !(ms > 0.f)) {
+    double r8 = 0, r16 = 0, r24 = 0;
+    cudaError_t err = fp64_rate_run<8>(blocks, threads, 2 * iters, &r8);
+    if (err == cudaSuccess) err = fp64_rate_run<16>(blocks, threads, iters, &r16);
+    if (err == cudaSuccess) err = fp64_rate_run<24>(blocks, threads, iters, &r24);
+    if (err != cudaSuccess) {
         set_error(std::string("sem_fp64_rate: ") + cudaGetErrorString(err));
         return SEM_ECUDA;
     }
-    *tflops_host = 2.0 * kFmaChains * iters * (double)threads * blocks / (ms * 1e-3) / 1e12;
+    *tflops_host = std::max(r8, std::max(r16, r24));
     return SEM_OK;
 }
 
