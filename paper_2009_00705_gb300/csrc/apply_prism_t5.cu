@@ -43,7 +43,10 @@ namespace sem {
 
 namespace {
 
-constexpr int kT6Threads = 320;                   // 8 compute warps + 2 producer warps
+// threads of a CTA with compute groups of gw warps: two groups + 2 producer warps.  With eight-
+// warp groups the 18 warps put five on one SM sub-partition, whose 16,384 registers then allow 96
+// per thread: the launch bounds hold ptxas to that (the epilogue keeps its factors packed to fit)
+__host__ __device__ constexpr int t6_threads(int gw) { return (2 * gw + 2) * 32; }
 constexpr unsigned long long kT6WaitNs = 1000000000ULL;
 
 constexpr int NT = 28, NZ = 7, QT = 49, QZ = 7, Np = NT * NZ;
@@ -197,15 +200,19 @@ __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-// barrier of one compute group (128 threads; ids 1 and 2)
-__device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory"); }
+// barrier of one compute group of GW warps (ids 1 and 2)
+template <int GW>
+__device__ __forceinline__ void group_sync(int g) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "n"(32 * GW) : "memory");
+}
 // the same barrier returning whether any thread of the group passed v = true (uniform result)
+template <int GW>
 __device__ __forceinline__ bool group_sync_any(int g, bool v) {
     uint32_t r;
     asm volatile(
-        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, 128, p;\n selp.u32 %0, 1, 0, q;\n}"
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}"
         : "=r"(r)
-        : "r"((uint32_t)v), "r"(1 + g)
+        : "r"((uint32_t)v), "r"(1 + g), "n"(32 * GW)
         : "memory");
     return r != 0;
 }
@@ -213,7 +220,8 @@ __device__ __forceinline__ bool group_sync_any(int g, bool v) {
 __device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
 
-__global__ void __launch_bounds__(kT6Threads, 1)
+template <int GW>
+__global__ void __launch_bounds__(t6_threads(GW), 1)
     k_apply_prism_t6(int E, int N, int npass, const int* __restrict__ map, const __nv_bfloat16* __restrict__ G6,
                      const float* __restrict__ refm, const __grid_constant__ Vert vc, const float* __restrict__ x,
                      float* __restrict__ y, const int* __restrict__ skip, int* err) {
@@ -235,9 +243,10 @@ __global__ void __launch_bounds__(kT6Threads, 1)
     volatile int* fail = &s_fail;
 
     // every pad entry of every operand must be zero
-    for (uint32_t i = tid; i < OFF_MAP / 16; i += kT6Threads) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
+    constexpr int NTHR = t6_threads(GW);
+    for (uint32_t i = tid; i < OFF_MAP / 16; i += NTHR) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
     __syncthreads();
-    for (int i = tid; i < QT * NT; i += kT6Threads) {
+    for (int i = tid; i < QT * NT; i += NTHR) {
         const int qt = i / NT, n = i - qt * NT;
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
@@ -268,7 +277,7 @@ __global__ void __launch_bounds__(kT6Threads, 1)
     const uint32_t tmem = s_tmem;
     const int first = blockIdx.x, step = gridDim.x;
 
-    if (warp == 8) {
+    if (warp == 2 * GW) {
         // ------------------------------------------------------------ element-map producer
         if (lane == 0) {
             int issued[4] = {-1, -1, -1, -1};       // last use issued per (group, buffer)
@@ -285,7 +294,7 @@ __global__ void __launch_bounds__(kT6Threads, 1)
             for (int i = 0; i < 4; ++i)
                 if (issued[i] >= 0) t6_wait(bar_mapf(i >> 1, i & 1), (uint32_t)(issued[i] & 1), fail, err, false);
         }
-    } else if (warp == 9) {
+    } else if (warp == 2 * GW + 1) {
         // ------------------------------------------------------------ geometric-factor producer
         if (lane == 0) {
             int issued[NSLOT];
@@ -308,7 +317,10 @@ __global__ void __launch_bounds__(kT6Threads, 1)
         }
     } else {
         // ------------------------------------------------------------ compute groups
-        const int g = warp >> 2, q4 = warp & 3, gt = tid & 127;
+        // group g, warp wg of the group; q4 = the TMEM lane quarter this warp may access
+        // (warp index mod 4); the group's warps of half hh take the factor chunks c = hh mod NH
+        constexpr int GT = 32 * GW, TPW = 16 / GW, NH = GW / 4;
+        const int g = warp / GW, wg = warp - g * GW, q4 = warp & 3, hh = wg >> 2, gt = tid - g * GT;
         const uint32_t tg = tmem + (uint32_t)g * TM_GROUP;
         const uint32_t trow = tg + ((uint32_t)(32 * q4) << 16);
         unsigned char* U = sm + OFF_UW + (uint32_t)g * 2 * SZ_A;
@@ -326,7 +338,7 @@ __global__ void __launch_bounds__(kT6Threads, 1)
             const int* sMap = reinterpret_cast<const int*>(sm + OFF_MAP + (uint32_t)(2 * g + b) * MAP_BYTES);
             // pads of U and W (the last pass's X staging overwrote them): columns n = 28..31 of
             // every row and the rows of the eighth vertical point
-            for (int i = gt; i < 2 * 128 + 2 * 16 * (NT / 4); i += 128) {
+            for (int i = gt; i < 2 * 128 + 2 * 16 * (NT / 4); i += GT) {
                 uint32_t o;
                 if (i < 256) {
                     o = (i < 128 ? 0u : SZ_A) + opoff(i & 127, NT, KF);
@@ -341,10 +353,10 @@ __global__ void __launch_bounds__(kT6Threads, 1)
             // wt = (bh, nh): lane -> element 8 bh + lane / 4, node 4 nh + lane % 4, so the 32 lanes
             // of every operand store fall on 32 distinct banks
             if (!*fail) {
-                float xv[4][NZ];
+                float xv[TPW][NZ];
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int wt = q4 + 4 * t;
+                for (int t = 0; t < TPW; ++t) {
+                    const int wt = wg + GW * t;
                     const int eb = (lane >> 2) + 8 * (wt / 7), n = 4 * (wt % 7) + (lane & 3);
 #pragma unroll
                     for (int kk = 0; kk < NZ; ++kk) {
@@ -357,8 +369,8 @@ __global__ void __launch_bounds__(kT6Threads, 1)
                     }
                 }
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int wt = q4 + 4 * t;
+                for (int t = 0; t < TPW; ++t) {
+                    const int wt = wg + GW * t;
                     if (wt >= 14) continue;
                     const int eb = (lane >> 2) + 8 * (wt / 7), n = 4 * (wt % 7) + (lane & 3);
 #pragma unroll
@@ -377,7 +389,7 @@ __global__ void __launch_bounds__(kT6Threads, 1)
             }
             fence_async_smem();
             fence_before();
-            if (group_sync_any(g, *fail)) break;
+            if (group_sync_any<GW>(g, *fail)) break;
             if (gt == 0) {
                 fence_after();
 #pragma unroll
@@ -395,7 +407,7 @@ __global__ void __launch_bounds__(kT6Threads, 1)
             fence_after();
             // geometric factors, chunk by chunk: V over the accumulators
             const bool valid = rqz < QZ && rb < nb;
-            for (int c = 0; c < NCH; ++c) {
+            for (int c = hh; c < NCH; c += NH) {
                 const int j = k * NCH + c, s = j % NSLOT;      // the producer's chunk sequence
                 const int c0 = 8 * c;
                 uint32_t ur[8], us[8], ut[8];
@@ -404,25 +416,23 @@ __global__ void __launch_bounds__(kT6Threads, 1)
                 tmem_ld8(trow + TM_UT + c0, ut);
                 const bool ok = t6_wait(bar_slotf(s), (uint32_t)((j / NSLOT) & 1), fail, err);
                 const unsigned char* slot = sm + OFF_G + (uint32_t)s * CH_BYTES;
-                float gf[6][8];
+                // the six factors of the row's eight quadrature points, kept packed (two BF16 per
+                // word) and widened where they are used
+                uint32_t gw[6][4];
                 if (c < NCH - 1) {
 #pragma unroll
                     for (int f = 0; f < 6; ++f) {
                         uint4 v = make_uint4(0, 0, 0, 0);
                         if (ok && valid) v = *reinterpret_cast<const uint4*>(slot + ((f * QZ + rqz) * EB + rb) * 16);
-                        gf[f][0] = bf16_lo(v.x); gf[f][1] = bf16_hi(v.x);
-                        gf[f][2] = bf16_lo(v.y); gf[f][3] = bf16_hi(v.y);
-                        gf[f][4] = bf16_lo(v.z); gf[f][5] = bf16_hi(v.z);
-                        gf[f][6] = bf16_lo(v.w); gf[f][7] = bf16_hi(v.w);
+                        gw[f][0] = v.x; gw[f][1] = v.y; gw[f][2] = v.z; gw[f][3] = v.w;
                     }
                 } else {
 #pragma unroll
                     for (int f = 0; f < 6; ++f) {
                         uint32_t v = 0;
                         if (ok && valid) v = *reinterpret_cast<const unsigned short*>(slot + ((f * QZ + rqz) * EB + rb) * 2);
-                        gf[f][0] = bf16_lo(v);
-#pragma unroll
-                        for (int h = 1; h < 8; ++h) gf[f][h] = 0.f;     // quadrature columns 49..55 are padding
+                        gw[f][0] = v;     // quadrature columns 49..55 are padding (zero)
+                        gw[f][1] = gw[f][2] = gw[f][3] = 0u;
                     }
                 }
                 // the slot may be refilled once every lane has read it (not after a failed wait: its
@@ -431,10 +441,13 @@ __global__ void __launch_bounds__(kT6Threads, 1)
                 tmem_wait_ld();
 #pragma unroll
                 for (int h = 0; h < 8; ++h) {
+                    float gf[6];
+#pragma unroll
+                    for (int f = 0; f < 6; ++f) gf[f] = (h & 1) ? bf16_hi(gw[f][h >> 1]) : bf16_lo(gw[f][h >> 1]);
                     const float a = __uint_as_float(ur[h]), bb = __uint_as_float(us[h]), t = __uint_as_float(ut[h]);
-                    const float vr = gf[0][h] * a + gf[1][h] * bb + gf[2][h] * t;
-                    const float vs = gf[1][h] * a + gf[3][h] * bb + gf[4][h] * t;
-                    const float vt = gf[2][h] * a + gf[4][h] * bb + gf[5][h] * t;
+                    const float vr = gf[0] * a + gf[1] * bb + gf[2] * t;
+                    const float vs = gf[1] * a + gf[3] * bb + gf[4] * t;
+                    const float vt = gf[2] * a + gf[4] * bb + gf[5] * t;
                     ur[h] = to_tf32(vr);
                     us[h] = to_tf32(vs);
                     ut[h] = to_tf32(vt);
@@ -445,7 +458,7 @@ __global__ void __launch_bounds__(kT6Threads, 1)
             }
             tmem_wait_st();
             fence_before();
-            if (group_sync_any(g, *fail)) break;
+            if (group_sync_any<GW>(g, *fail)) break;
             if (gt == 0) {
                 fence_after();
 #pragma unroll
@@ -460,7 +473,21 @@ __global__ void __launch_bounds__(kT6Threads, 1)
             }
             if (t6_wait(bar_mma(g), 1u, fail, err) && gt == 0) pend = -1;
             fence_after();
-            {   // Xr, Xt of this row into the staging areas [n][qz][b] (row stride XS per node)
+            if constexpr (NH == 2) {
+                // Xr (half 0) or Xt (half 1) of this row into its staging area [n][qz][b]
+                uint32_t va[16], vb[16];
+                const uint32_t col = hh == 0 ? TM_XR : TM_XT;
+                tmem_ld16(trow + col, va);
+                tmem_ld16(trow + col + 16, vb);
+                tmem_wait_ld();
+                if (rqz < QZ) {
+                    float* pr = (hh == 0 ? Xr : Xt) + rqz * 16 + rb;
+#pragma unroll
+                    for (int n = 0; n < 16; ++n) pr[n * XS] = __uint_as_float(va[n]);
+#pragma unroll
+                    for (int n = 16; n < NT; ++n) pr[n * XS] = __uint_as_float(vb[n - 16]);
+                }
+            } else {   // Xr, Xt of this row into the staging areas [n][qz][b] (row stride XS per node)
                 uint32_t xa[16], xb[16], ta[16], tb[16];
                 tmem_ld16(trow + TM_XR, xa);
                 tmem_ld16(trow + TM_XR + 16, xb);
@@ -483,14 +510,14 @@ __global__ void __launch_bounds__(kT6Threads, 1)
                 }
             }
             fence_before();
-            group_sync(g);
+            group_sync<GW>(g);
             // transposed vertical stage and direct-stiffness summation:
             // y(k; n) = Bz(qz; k) Xr(qz; n) + Dz(qz; k) Xt(qz; n).  Warp task nt: lane -> element
             // lane % 16, node 2 nt + lane / 16
             if (!*fail) {
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int nt = q4 + 4 * t;
+                for (int t = 0; t < TPW; ++t) {
+                    const int nt = wg + GW * t;
                     if (nt >= 14) continue;
                     const int eb = lane & 15, n = 2 * nt + (lane >> 4);
                     float xr[QZ], xt[QZ];
@@ -514,7 +541,7 @@ __global__ void __launch_bounds__(kT6Threads, 1)
                     }
                 }
             }
-            if (group_sync_any(g, *fail)) break;
+            if (group_sync_any<GW>(g, *fail)) break;
             // this pass's map buffer may be refilled
             if (gt == 0) mbar_arrive(bar_mape(g, b));
         }
@@ -575,8 +602,11 @@ cudaError_t build_g16_t6(Level& L, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_apply_prism_t5(const Level& L, const float* x, float* y, const int* skip, int* err, cudaStream_t s) {
+cudaError_t launch_apply_prism_t5(const Level& L, const float* x, float* y, const int* skip, int* err, cudaStream_t s,
+                                  int gw) {
     if (L.p != 6 || L.pz != 6 || L.dim != 3 || L.G16T == nullptr) return cudaErrorInvalidValue;
+    if (gw == 0) gw = L.t6_warps;
+    if (gw != 4 && gw != 8) return cudaErrorInvalidValue;
     static bool configured[64] = {};
     static int sms[64] = {};
     int dev = 0;
@@ -584,7 +614,9 @@ cudaError_t launch_apply_prism_t5(const Level& L, const float* x, float* y, cons
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!configured[dev]) {
-        e = cudaFuncSetAttribute(k_apply_prism_t6, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+        e = cudaFuncSetAttribute(k_apply_prism_t6<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_apply_prism_t6<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
@@ -598,9 +630,13 @@ cudaError_t launch_apply_prism_t5(const Level& L, const float* x, float* y, cons
     const int npass = (L.E + EB - 1) / EB;
     const int grid = npass < sms[dev] ? npass : sms[dev];
     if (grid < 1) return cudaSuccess;
-    k_apply_prism_t6<<<grid, kT6Threads, SMEM, s>>>(L.E, (int)L.N, npass, L.map,
-                                                   reinterpret_cast<const __nv_bfloat16*>(L.G16T), L.ref32.m, vc, x,
-                                                   y, skip, err);
+    const __nv_bfloat16* g6 = reinterpret_cast<const __nv_bfloat16*>(L.G16T);
+    if (gw == 8)
+        k_apply_prism_t6<8><<<grid, t6_threads(8), SMEM, s>>>(L.E, (int)L.N, npass, L.map, g6, L.ref32.m, vc, x, y,
+                                                               skip, err);
+    else
+        k_apply_prism_t6<4><<<grid, t6_threads(4), SMEM, s>>>(L.E, (int)L.N, npass, L.map, g6, L.ref32.m, vc, x, y,
+                                                               skip, err);
     return cudaGetLastError();
 }
 
