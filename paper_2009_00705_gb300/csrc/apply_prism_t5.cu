@@ -148,12 +148,23 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
+// L2 policy of the streamed operands (factors, element maps: each byte read once per apply):
+// evicted first, so that the stream does not push x and y, which the gathers and the atomic
+// summation reuse, out of L2
+__device__ __forceinline__ uint64_t t6_stream_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
 // one thread: bulk-copy `bytes` (a multiple of 16) from global to shared, completing on `bar`
-__device__ void t6_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+__device__ void t6_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar, uint64_t pol) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            dst),
+        "l"(src), "r"(bytes), "r"(bar), "l"(pol)
+        : "memory");
 }
 
 __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
@@ -242,26 +253,8 @@ __global__ void __launch_bounds__(t6_threads(GW), 1)
     auto bar_mma = [&](int g) { return mb0 + 8u * (uint32_t)(20 + g); };
     volatile int* fail = &s_fail;
 
-    // every pad entry of every operand must be zero
-    constexpr int NTHR = t6_threads(GW);
-    for (uint32_t i = tid; i < OFF_MAP / 16; i += NTHR) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
-    __syncthreads();
-    for (int i = tid; i < QT * NT; i += NTHR) {
-        const int qt = i / NT, n = i - qt * NT;
-#pragma unroll
-        for (int m = 0; m < 3; ++m) {
-            // reference blocks in refm: Bt, Dr, Ds as [QT][NT]; operands m = Dr, Ds, Bt
-            const float v = __uint_as_float(to_tf32(refm[((m + 1) % 3) * QT * NT + i]));
-            *reinterpret_cast<float*>(sm + OFF_BF + m * SZ_BF + opoff(qt, n, KF)) = v;
-            *reinterpret_cast<float*>(sm + OFF_BB + m * SZ_BB + opoff(n, qt, KB)) = v;
-        }
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                     "r"(2 * TM_GROUP)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
+    // the barriers first: the producers start the first pass's copies while the compute warps
+    // set up the reference operands and the tensor memory
     if (tid == 0) {
         s_fail = 0;
         for (int i = 0; i < 22; ++i) {
@@ -270,16 +263,13 @@ __global__ void __launch_bounds__(t6_threads(GW), 1)
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    fence_async_smem();
-    fence_before();
     __syncthreads();
-    fence_after();
-    const uint32_t tmem = s_tmem;
     const int first = blockIdx.x, step = gridDim.x;
 
     if (warp == 2 * GW) {
         // ------------------------------------------------------------ element-map producer
         if (lane == 0) {
+            const uint64_t pol = t6_stream_policy();
             int issued[4] = {-1, -1, -1, -1};       // last use issued per (group, buffer)
             for (int k = 0, p = first; p < npass; ++k, p += step) {
                 const int g = k & 1, b = (k >> 1) & 1, use = k >> 2;
@@ -287,7 +277,7 @@ __global__ void __launch_bounds__(t6_threads(GW), 1)
                 if (*fail) break;
                 const int e0 = p * EB, nb = min(EB, E - e0);
                 t6_copy(sbase + OFF_MAP + (uint32_t)(2 * g + b) * MAP_BYTES, map + (size_t)e0 * Np,
-                        (uint32_t)nb * Np * 4u, bar_mapf(g, b));
+                        (uint32_t)nb * Np * 4u, bar_mapf(g, b), pol);
                 issued[2 * g + b] = use;
             }
             // every copy this warp started has landed before the CTA exits
@@ -297,6 +287,7 @@ __global__ void __launch_bounds__(t6_threads(GW), 1)
     } else if (warp == 2 * GW + 1) {
         // ------------------------------------------------------------ geometric-factor producer
         if (lane == 0) {
+            const uint64_t pol = t6_stream_policy();
             int issued[NSLOT];
             for (int s = 0; s < NSLOT; ++s) issued[s] = -1;
             int j = 0;
@@ -308,7 +299,7 @@ __global__ void __launch_bounds__(t6_threads(GW), 1)
                     if (use > 0 && !t6_wait(bar_slote(s), (uint32_t)((use - 1) & 1), fail, err)) { stop = true; break; }
                     if (*fail) { stop = true; break; }
                     t6_copy(sbase + OFF_G + (uint32_t)s * CH_BYTES, src + (size_t)c * CH_BYTES,
-                            c < NCH - 1 ? CH_BYTES : CH_LAST, bar_slotf(s));
+                            c < NCH - 1 ? CH_BYTES : CH_LAST, bar_slotf(s), pol);
                     issued[s] = use;
                 }
             }
@@ -317,6 +308,32 @@ __global__ void __launch_bounds__(t6_threads(GW), 1)
         }
     } else {
         // ------------------------------------------------------------ compute groups
+        // setup (barrier id 3 over the two groups): every pad entry of every operand zero, the
+        // reference operands, the tensor memory
+        constexpr int NC = 2 * GW * 32;
+        for (uint32_t i = tid; i < OFF_MAP / 16; i += NC) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
+        asm volatile("bar.sync 3, %0;" ::"n"(NC) : "memory");
+        for (int i = tid; i < QT * NT; i += NC) {
+            const int qt = i / NT, n = i - qt * NT;
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                // reference blocks in refm: Bt, Dr, Ds as [QT][NT]; operands m = Dr, Ds, Bt
+                const float v = __uint_as_float(to_tf32(refm[((m + 1) % 3) * QT * NT + i]));
+                *reinterpret_cast<float*>(sm + OFF_BF + m * SZ_BF + opoff(qt, n, KF)) = v;
+                *reinterpret_cast<float*>(sm + OFF_BB + m * SZ_BB + opoff(n, qt, KB)) = v;
+            }
+        }
+        if (warp == 0) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                         "r"(2 * TM_GROUP)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
+        fence_async_smem();
+        fence_before();
+        asm volatile("bar.sync 3, %0;" ::"n"(NC) : "memory");
+        fence_after();
+        const uint32_t tmem = s_tmem;
         // group g, warp wg of the group; q4 = the TMEM lane quarter this warp may access
         // (warp index mod 4); the group's warps of half hh take the factor chunks c = hh mod NH
         constexpr int GT = 32 * GW, TPW = 16 / GW, NH = GW / 4;
@@ -552,7 +569,7 @@ __global__ void __launch_bounds__(t6_threads(GW), 1)
     __syncthreads();
     if (warp == 0) {
         fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TM_GROUP) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(2 * TM_GROUP) : "memory");
     }
 }
 
