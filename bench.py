@@ -268,14 +268,12 @@ def run_ncu_case(a):
     st = s.solve(phiD, phi, tol=1e-8, allow_not_converged=True)
     torch.cuda.synchronize()
     if a.ncu_tcgen05 and P == 6:
-        # three launches of each tcgen05 form of the order-6 apply (four-, then eight-warp
-        # compute groups) on the same mesh
+        # three launches of the tcgen05 form of the order-6 apply on the same mesh
         N = s.query(0)["ndof"]
         xa = torch.rand(N, dtype=torch.float32, device="cuda")
         ya = torch.empty(N, dtype=torch.float32, device="cuda")
-        for form in (2, 3):
-            for _ in range(3):
-                s.apply32(0, xa, ya, tensor_cores=form)
+        for _ in range(3):
+            s.apply32(0, xa, ya, tensor_cores=2)
         torch.cuda.synchronize()
     print(json.dumps({"ncu_case": a.ncu_case, "elements": s.query(0)["nelem"], "stats": st}))
     s.close()
@@ -394,7 +392,7 @@ def main():
     ap.add_argument("--ncu-elem", type=int, default=-1, choices=[-1, 0, 1, 2],
                     help="with --ncu-case: form of the FP64 residual apply (elem_matrices; -1 the default)")
     ap.add_argument("--ncu-tcgen05", action="store_true",
-                    help="with --ncu-case: also launch each tcgen05 form of the order-6 apply three times after the solve")
+                    help="with --ncu-case: also launch the tcgen05 order-6 apply three times after the solve")
     ap.add_argument("--ncu-batch", type=int, default=0, metavar="N",
                     help="profiler driver: one batched solve of the first N random tanks; prints iterations only")
     ap.add_argument("--ncu-small", action="store_true",
@@ -588,13 +586,11 @@ def main():
             ms_m = max_over_ranks(ms_m)
             err = float(np.abs(phi_m.cpu().numpy() - phi64).max() / np.abs(phi64).max())
             if prec == "mixed_tf32":
-                kinds = {1: "warp-level mma.sync m16n8k8",
-                         2: "tcgen05.mma with TMEM accumulators, four-warp compute groups",
-                         3: "tcgen05.mma with TMEM accumulators, eight-warp compute groups"}
+                kinds = {1: "warp-level mma.sync m16n8k8", 2: "tcgen05.mma with TMEM accumulators"}
                 fine_kind = ms_solver.tc_kernel(0)
                 smooth = (f"TF32 tensor-core apply (FP32 accumulation, BF16 factors) in the Chebyshev sweeps and residuals "
                           f"of the V-cycle: {kinds.get(fine_kind, 'FP32')} on the order-{P} level (chosen at setup by "
-                          f"timing the three), warp-level MMA on the intermediate levels; FP32 apply in the inner PCG")
+                          f"timing both), warp-level MMA on the intermediate levels; FP32 apply in the inner PCG")
             else:
                 smooth = "FP32 SIMT apply throughout"
             obj = {"value": dof * a.steps * world / (ms_m / 1000.0), "unit": UNIT,
@@ -629,11 +625,11 @@ def main():
                                           "peak_source": "half the measured bf16 GEMM peak (MEASURED_PEAKS.json)"}
                 obj["apply_tf32_tensor_cores"] = tcv
                 # the order-6 operator through sem_apply32 (memset of y, kernel, Dirichlet copy) with
-                # the warp-MMA kernel and the tcgen05 kernel with four- and eight-warp groups
+                # the warp-MMA kernel the V-cycle uses and with the tcgen05 kernel
                 xa = torch.rand(N, dtype=torch.float32, device="cuda")
                 ya = torch.empty(N, dtype=torch.float32, device="cuda")
                 calls = {}
-                for form, tcv in (("warp_mma", 1), ("tcgen05_4warp_groups", 2), ("tcgen05_8warp_groups", 3)):
+                for form, tcv in (("warp_mma", 1), ("tcgen05", 2)):
                     for _ in range(3):
                         ms_solver.apply32(0, xa, ya, tensor_cores=tcv)
                     torch.cuda.synchronize()

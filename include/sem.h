@@ -289,9 +289,8 @@ sem_status sem_lambda_max(const sem_handle* h, double* lam_host);
 /* Elements per CTA pass of the prism apply chosen for a level (FP64 and FP32 kernels). */
 sem_status sem_tile_shapes(const sem_handle* h, int level, int* elems_fp64, int* elems_fp32);
 /* The operator of a level's Chebyshev sweeps under MIXED_TF32: 0 the FP32 apply (not a
- * tensor-core level), 1 the warp-level MMA kernel, 2 and 3 the tcgen05 kernel (order 6) with
- * compute groups of four and of eight warps (chosen at setup by timing the three when
- * autotune is set, else 3). */
+ * tensor-core level), 1 the warp-level MMA kernel, 2 the tcgen05 kernel (order 6; chosen at
+ * setup by timing both when autotune is set, else the tcgen05 kernel). */
 sem_status sem_tc_kernel(const sem_handle* h, int level, int* kind);
 /* The form of a level's FP64 applies (sem_options.elem_matrices): SEM_ELEM_FP64 or SEM_ELEM_DF32
  * when they multiply by precomputed element matrices, SEM_ELEM_OFF for the sum-factorised
@@ -308,12 +307,11 @@ sem_status sem_apply(sem_handle* h, int level, const double* x_dev, double* y_de
 /* The same operator in single precision, as the mixed V-cycle applies it: the FP32
  * kernel (tensor_cores = 0) or the TF32 tensor-core kernel of the MIXED_TF32
  * Chebyshev sweeps (tensor_cores = 1: warp-level MMA; prism levels of order 2..6, else
- * SEM_EINVAL; operands rounded to TF32, FP32 accumulation).  tensor_cores = 2 and 3 run
- * the same operator on tcgen05 (TMEM accumulators, operands read by descriptor; order 6
- * only, else SEM_EINVAL) with compute groups of four and of eight warps; the V-cycle
- * uses whichever of the three kernels sem_tc_kernel reports.  x_dev, y_dev: N floats,
- * distinct; y_D = x_D.  The tensor-core forms synchronise the stream and return
- * SEM_TIMEOUT if a copy or an MMA inside the kernel did not complete within 1 s. */
+ * SEM_EINVAL; operands rounded to TF32, FP32 accumulation).  tensor_cores = 2 runs the
+ * same operator on tcgen05 (TMEM accumulators, operands read by descriptor; order 6
+ * only, else SEM_EINVAL), a second kernel that the V-cycle does not use.  x_dev, y_dev:
+ * N floats, distinct; y_D = x_D.  The tensor-core forms synchronise the stream and
+ * return SEM_TIMEOUT if a copy or an MMA inside the kernel did not complete within 1 s. */
 sem_status sem_apply32(sem_handle* h, int level, const float* x_dev, float* y_dev, int tensor_cores,
                        void* stream);
 

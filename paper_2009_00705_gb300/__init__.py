@@ -359,8 +359,7 @@ def sem_fnpf_step(h: int, eta, phis, dt, g=9.81, linear=False, strategy="all", t
 
 def sem_apply32(h: int, level: int, x, y, tensor_cores: int = 0, stream=None) -> None:
     """FP32 operator apply (x, y float32 device buffers); tensor_cores 1 (or True) selects the TF32
-    warp-MMA kernel, 2 and 3 the tcgen05 kernel with four- and eight-warp compute groups (order 6
-    only)."""
+    warp-MMA kernel the V-cycle uses, 2 the tcgen05 kernel (order 6 only)."""
     _check(lib().sem_apply32(h, level, _ptr(x), _ptr(y), int(tensor_cores), _stream(stream)))
 
 

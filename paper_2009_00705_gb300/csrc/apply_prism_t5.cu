@@ -43,10 +43,7 @@ namespace sem {
 
 namespace {
 
-// threads of a CTA with compute groups of gw warps: two groups + 2 producer warps.  With eight-
-// warp groups the 18 warps put five on one SM sub-partition, whose 16,384 registers then allow 96
-// per thread: the launch bounds hold ptxas to that (the epilogue keeps its factors packed to fit)
-__host__ __device__ constexpr int t6_threads(int gw) { return (2 * gw + 2) * 32; }
+constexpr int kT6Threads = 320;                   // 8 compute warps + 2 producer warps
 constexpr unsigned long long kT6WaitNs = 1000000000ULL;
 
 constexpr int NT = 28, NZ = 7, QT = 49, QZ = 7, Np = NT * NZ;
@@ -148,23 +145,12 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// L2 policy of the streamed operands (factors, element maps: each byte read once per apply):
-// evicted first, so that the stream does not push x and y, which the gathers and the atomic
-// summation reuse, out of L2
-__device__ __forceinline__ uint64_t t6_stream_policy() {
-    uint64_t pol;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-
 // one thread: bulk-copy `bytes` (a multiple of 16) from global to shared, completing on `bar`
-__device__ void t6_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar, uint64_t pol) {
+__device__ void t6_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
-            dst),
-        "l"(src), "r"(bytes), "r"(bar), "l"(pol)
-        : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
 }
 
 __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
@@ -211,19 +197,15 @@ __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-// barrier of one compute group of GW warps (ids 1 and 2)
-template <int GW>
-__device__ __forceinline__ void group_sync(int g) {
-    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "n"(32 * GW) : "memory");
-}
+// barrier of one compute group (128 threads; ids 1 and 2)
+__device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory"); }
 // the same barrier returning whether any thread of the group passed v = true (uniform result)
-template <int GW>
 __device__ __forceinline__ bool group_sync_any(int g, bool v) {
     uint32_t r;
     asm volatile(
-        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}"
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, 128, p;\n selp.u32 %0, 1, 0, q;\n}"
         : "=r"(r)
-        : "r"((uint32_t)v), "r"(1 + g), "n"(32 * GW)
+        : "r"((uint32_t)v), "r"(1 + g)
         : "memory");
     return r != 0;
 }
@@ -231,8 +213,7 @@ __device__ __forceinline__ bool group_sync_any(int g, bool v) {
 __device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
 
-template <int GW>
-__global__ void __launch_bounds__(t6_threads(GW), 1)
+__global__ void __launch_bounds__(kT6Threads, 1)
     k_apply_prism_t6(int E, int N, int npass, const int* __restrict__ map, const __nv_bfloat16* __restrict__ G6,
                      const float* __restrict__ refm, const __grid_constant__ Vert vc, const float* __restrict__ x,
                      float* __restrict__ y, const int* __restrict__ skip, int* err) {
@@ -253,8 +234,25 @@ __global__ void __launch_bounds__(t6_threads(GW), 1)
     auto bar_mma = [&](int g) { return mb0 + 8u * (uint32_t)(20 + g); };
     volatile int* fail = &s_fail;
 
-    // the barriers first: the producers start the first pass's copies while the compute warps
-    // set up the reference operands and the tensor memory
+    // every pad entry of every operand must be zero
+    for (uint32_t i = tid; i < OFF_MAP / 16; i += kT6Threads) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+    for (int i = tid; i < QT * NT; i += kT6Threads) {
+        const int qt = i / NT, n = i - qt * NT;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            // reference blocks in refm: Bt, Dr, Ds as [QT][NT]; operands m = Dr, Ds, Bt
+            const float v = __uint_as_float(to_tf32(refm[((m + 1) % 3) * QT * NT + i]));
+            *reinterpret_cast<float*>(sm + OFF_BF + m * SZ_BF + opoff(qt, n, KF)) = v;
+            *reinterpret_cast<float*>(sm + OFF_BB + m * SZ_BB + opoff(n, qt, KB)) = v;
+        }
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(2 * TM_GROUP)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
     if (tid == 0) {
         s_fail = 0;
         for (int i = 0; i < 22; ++i) {
@@ -263,13 +261,16 @@ __global__ void __launch_bounds__(t6_threads(GW), 1)
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    fence_async_smem();
+    fence_before();
     __syncthreads();
+    fence_after();
+    const uint32_t tmem = s_tmem;
     const int first = blockIdx.x, step = gridDim.x;
 
-    if (warp == 2 * GW) {
+    if (warp == 8) {
         // ------------------------------------------------------------ element-map producer
         if (lane == 0) {
-            const uint64_t pol = t6_stream_policy();
             int issued[4] = {-1, -1, -1, -1};       // last use issued per (group, buffer)
             for (int k = 0, p = first; p < npass; ++k, p += step) {
                 const int g = k & 1, b = (k >> 1) & 1, use = k >> 2;
@@ -277,17 +278,16 @@ __global__ void __launch_bounds__(t6_threads(GW), 1)
                 if (*fail) break;
                 const int e0 = p * EB, nb = min(EB, E - e0);
                 t6_copy(sbase + OFF_MAP + (uint32_t)(2 * g + b) * MAP_BYTES, map + (size_t)e0 * Np,
-                        (uint32_t)nb * Np * 4u, bar_mapf(g, b), pol);
+                        (uint32_t)nb * Np * 4u, bar_mapf(g, b));
                 issued[2 * g + b] = use;
             }
             // every copy this warp started has landed before the CTA exits
             for (int i = 0; i < 4; ++i)
                 if (issued[i] >= 0) t6_wait(bar_mapf(i >> 1, i & 1), (uint32_t)(issued[i] & 1), fail, err, false);
         }
-    } else if (warp == 2 * GW + 1) {
+    } else if (warp == 9) {
         // ------------------------------------------------------------ geometric-factor producer
         if (lane == 0) {
-            const uint64_t pol = t6_stream_policy();
             int issued[NSLOT];
             for (int s = 0; s < NSLOT; ++s) issued[s] = -1;
             int j = 0;
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(t6_threads(GW), 1)
                     if (use > 0 && !t6_wait(bar_slote(s), (uint32_t)((use - 1) & 1), fail, err)) { stop = true; break; }
                     if (*fail) { stop = true; break; }
                     t6_copy(sbase + OFF_G + (uint32_t)s * CH_BYTES, src + (size_t)c * CH_BYTES,
-                            c < NCH - 1 ? CH_BYTES : CH_LAST, bar_slotf(s), pol);
+                            c < NCH - 1 ? CH_BYTES : CH_LAST, bar_slotf(s));
                     issued[s] = use;
                 }
             }
@@ -308,36 +308,7 @@ __global__ void __launch_bounds__(t6_threads(GW), 1)
         }
     } else {
         // ------------------------------------------------------------ compute groups
-        // setup (barrier id 3 over the two groups): every pad entry of every operand zero, the
-        // reference operands, the tensor memory
-        constexpr int NC = 2 * GW * 32;
-        for (uint32_t i = tid; i < OFF_MAP / 16; i += NC) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
-        asm volatile("bar.sync 3, %0;" ::"n"(NC) : "memory");
-        for (int i = tid; i < QT * NT; i += NC) {
-            const int qt = i / NT, n = i - qt * NT;
-#pragma unroll
-            for (int m = 0; m < 3; ++m) {
-                // reference blocks in refm: Bt, Dr, Ds as [QT][NT]; operands m = Dr, Ds, Bt
-                const float v = __uint_as_float(to_tf32(refm[((m + 1) % 3) * QT * NT + i]));
-                *reinterpret_cast<float*>(sm + OFF_BF + m * SZ_BF + opoff(qt, n, KF)) = v;
-                *reinterpret_cast<float*>(sm + OFF_BB + m * SZ_BB + opoff(n, qt, KB)) = v;
-            }
-        }
-        if (warp == 0) {
-            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                         "r"(2 * TM_GROUP)
-                         : "memory");
-            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-        }
-        fence_async_smem();
-        fence_before();
-        asm volatile("bar.sync 3, %0;" ::"n"(NC) : "memory");
-        fence_after();
-        const uint32_t tmem = s_tmem;
-        // group g, warp wg of the group; q4 = the TMEM lane quarter this warp may access
-        // (warp index mod 4); the group's warps of half hh take the factor chunks c = hh mod NH
-        constexpr int GT = 32 * GW, TPW = 16 / GW, NH = GW / 4;
-        const int g = warp / GW, wg = warp - g * GW, q4 = warp & 3, hh = wg >> 2, gt = tid - g * GT;
+        const int g = warp >> 2, q4 = warp & 3, gt = tid & 127;
         const uint32_t tg = tmem + (uint32_t)g * TM_GROUP;
         const uint32_t trow = tg + ((uint32_t)(32 * q4) << 16);
         unsigned char* U = sm + OFF_UW + (uint32_t)g * 2 * SZ_A;
@@ -355,7 +326,7 @@ __global__ void __launch_bounds__(t6_threads(GW), 1)
             const int* sMap = reinterpret_cast<const int*>(sm + OFF_MAP + (uint32_t)(2 * g + b) * MAP_BYTES);
             // pads of U and W (the last pass's X staging overwrote them): columns n = 28..31 of
             // every row and the rows of the eighth vertical point
-            for (int i = gt; i < 2 * 128 + 2 * 16 * (NT / 4); i += GT) {
+            for (int i = gt; i < 2 * 128 + 2 * 16 * (NT / 4); i += 128) {
                 uint32_t o;
                 if (i < 256) {
                     o = (i < 128 ? 0u : SZ_A) + opoff(i & 127, NT, KF);
@@ -370,10 +341,10 @@ __global__ void __launch_bounds__(t6_threads(GW), 1)
             // wt = (bh, nh): lane -> element 8 bh + lane / 4, node 4 nh + lane % 4, so the 32 lanes
             // of every operand store fall on 32 distinct banks
             if (!*fail) {
-                float xv[TPW][NZ];
+                float xv[4][NZ];
 #pragma unroll
-                for (int t = 0; t < TPW; ++t) {
-                    const int wt = wg + GW * t;
+                for (int t = 0; t < 4; ++t) {
+                    const int wt = q4 + 4 * t;
                     const int eb = (lane >> 2) + 8 * (wt / 7), n = 4 * (wt % 7) + (lane & 3);
 #pragma unroll
                     for (int kk = 0; kk < NZ; ++kk) {
@@ -386,8 +357,8 @@ __global__ void __launch_bounds__(t6_threads(GW), 1)
                     }
                 }
 #pragma unroll
-                for (int t = 0; t < TPW; ++t) {
-                    const int wt = wg + GW * t;
+                for (int t = 0; t < 4; ++t) {
+                    const int wt = q4 + 4 * t;
                     if (wt >= 14) continue;
                     const int eb = (lane >> 2) + 8 * (wt / 7), n = 4 * (wt % 7) + (lane & 3);
 #pragma unroll
@@ -406,7 +377,7 @@ __global__ void __launch_bounds__(t6_threads(GW), 1)
             }
             fence_async_smem();
             fence_before();
-            if (group_sync_any<GW>(g, *fail)) break;
+            if (group_sync_any(g, *fail)) break;
             if (gt == 0) {
                 fence_after();
 #pragma unroll
@@ -424,7 +395,7 @@ __global__ void __launch_bounds__(t6_threads(GW), 1)
             fence_after();
             // geometric factors, chunk by chunk: V over the accumulators
             const bool valid = rqz < QZ && rb < nb;
-            for (int c = hh; c < NCH; c += NH) {
+            for (int c = 0; c < NCH; ++c) {
                 const int j = k * NCH + c, s = j % NSLOT;      // the producer's chunk sequence
                 const int c0 = 8 * c;
                 uint32_t ur[8], us[8], ut[8];
@@ -433,23 +404,25 @@ __global__ void __launch_bounds__(t6_threads(GW), 1)
                 tmem_ld8(trow + TM_UT + c0, ut);
                 const bool ok = t6_wait(bar_slotf(s), (uint32_t)((j / NSLOT) & 1), fail, err);
                 const unsigned char* slot = sm + OFF_G + (uint32_t)s * CH_BYTES;
-                // the six factors of the row's eight quadrature points, kept packed (two BF16 per
-                // word) and widened where they are used
-                uint32_t gw[6][4];
+                float gf[6][8];
                 if (c < NCH - 1) {
 #pragma unroll
                     for (int f = 0; f < 6; ++f) {
                         uint4 v = make_uint4(0, 0, 0, 0);
                         if (ok && valid) v = *reinterpret_cast<const uint4*>(slot + ((f * QZ + rqz) * EB + rb) * 16);
-                        gw[f][0] = v.x; gw[f][1] = v.y; gw[f][2] = v.z; gw[f][3] = v.w;
+                        gf[f][0] = bf16_lo(v.x); gf[f][1] = bf16_hi(v.x);
+                        gf[f][2] = bf16_lo(v.y); gf[f][3] = bf16_hi(v.y);
+                        gf[f][4] = bf16_lo(v.z); gf[f][5] = bf16_hi(v.z);
+                        gf[f][6] = bf16_lo(v.w); gf[f][7] = bf16_hi(v.w);
                     }
                 } else {
 #pragma unroll
                     for (int f = 0; f < 6; ++f) {
                         uint32_t v = 0;
                         if (ok && valid) v = *reinterpret_cast<const unsigned short*>(slot + ((f * QZ + rqz) * EB + rb) * 2);
-                        gw[f][0] = v;     // quadrature columns 49..55 are padding (zero)
-                        gw[f][1] = gw[f][2] = gw[f][3] = 0u;
+                        gf[f][0] = bf16_lo(v);
+#pragma unroll
+                        for (int h = 1; h < 8; ++h) gf[f][h] = 0.f;     // quadrature columns 49..55 are padding
                     }
                 }
                 // the slot may be refilled once every lane has read it (not after a failed wait: its
@@ -458,13 +431,10 @@ __global__ void __launch_bounds__(t6_threads(GW), 1)
                 tmem_wait_ld();
 #pragma unroll
                 for (int h = 0; h < 8; ++h) {
-                    float gf[6];
-#pragma unroll
-                    for (int f = 0; f < 6; ++f) gf[f] = (h & 1) ? bf16_hi(gw[f][h >> 1]) : bf16_lo(gw[f][h >> 1]);
                     const float a = __uint_as_float(ur[h]), bb = __uint_as_float(us[h]), t = __uint_as_float(ut[h]);
-                    const float vr = gf[0] * a + gf[1] * bb + gf[2] * t;
-                    const float vs = gf[1] * a + gf[3] * bb + gf[4] * t;
-                    const float vt = gf[2] * a + gf[4] * bb + gf[5] * t;
+                    const float vr = gf[0][h] * a + gf[1][h] * bb + gf[2][h] * t;
+                    const float vs = gf[1][h] * a + gf[3][h] * bb + gf[4][h] * t;
+                    const float vt = gf[2][h] * a + gf[4][h] * bb + gf[5][h] * t;
                     ur[h] = to_tf32(vr);
                     us[h] = to_tf32(vs);
                     ut[h] = to_tf32(vt);
@@ -475,7 +445,7 @@ __global__ void __launch_bounds__(t6_threads(GW), 1)
             }
             tmem_wait_st();
             fence_before();
-            if (group_sync_any<GW>(g, *fail)) break;
+            if (group_sync_any(g, *fail)) break;
             if (gt == 0) {
                 fence_after();
 #pragma unroll
@@ -490,21 +460,7 @@ __global__ void __launch_bounds__(t6_threads(GW), 1)
             }
             if (t6_wait(bar_mma(g), 1u, fail, err) && gt == 0) pend = -1;
             fence_after();
-            if constexpr (NH == 2) {
-                // Xr (half 0) or Xt (half 1) of this row into its staging area [n][qz][b]
-                uint32_t va[16], vb[16];
-                const uint32_t col = hh == 0 ? TM_XR : TM_XT;
-                tmem_ld16(trow + col, va);
-                tmem_ld16(trow + col + 16, vb);
-                tmem_wait_ld();
-                if (rqz < QZ) {
-                    float* pr = (hh == 0 ? Xr : Xt) + rqz * 16 + rb;
-#pragma unroll
-                    for (int n = 0; n < 16; ++n) pr[n * XS] = __uint_as_float(va[n]);
-#pragma unroll
-                    for (int n = 16; n < NT; ++n) pr[n * XS] = __uint_as_float(vb[n - 16]);
-                }
-            } else {   // Xr, Xt of this row into the staging areas [n][qz][b] (row stride XS per node)
+            {   // Xr, Xt of this row into the staging areas [n][qz][b] (row stride XS per node)
                 uint32_t xa[16], xb[16], ta[16], tb[16];
                 tmem_ld16(trow + TM_XR, xa);
                 tmem_ld16(trow + TM_XR + 16, xb);
@@ -527,14 +483,14 @@ __global__ void __launch_bounds__(t6_threads(GW), 1)
                 }
             }
             fence_before();
-            group_sync<GW>(g);
+            group_sync(g);
             // transposed vertical stage and direct-stiffness summation:
             // y(k; n) = Bz(qz; k) Xr(qz; n) + Dz(qz; k) Xt(qz; n).  Warp task nt: lane -> element
             // lane % 16, node 2 nt + lane / 16
             if (!*fail) {
 #pragma unroll
-                for (int t = 0; t < TPW; ++t) {
-                    const int nt = wg + GW * t;
+                for (int t = 0; t < 4; ++t) {
+                    const int nt = q4 + 4 * t;
                     if (nt >= 14) continue;
                     const int eb = lane & 15, n = 2 * nt + (lane >> 4);
                     float xr[QZ], xt[QZ];
@@ -558,7 +514,7 @@ __global__ void __launch_bounds__(t6_threads(GW), 1)
                     }
                 }
             }
-            if (group_sync_any<GW>(g, *fail)) break;
+            if (group_sync_any(g, *fail)) break;
             // this pass's map buffer may be refilled
             if (gt == 0) mbar_arrive(bar_mape(g, b));
         }
@@ -569,7 +525,7 @@ __global__ void __launch_bounds__(t6_threads(GW), 1)
     __syncthreads();
     if (warp == 0) {
         fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(2 * TM_GROUP) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TM_GROUP) : "memory");
     }
 }
 
@@ -619,11 +575,8 @@ cudaError_t build_g16_t6(Level& L, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_apply_prism_t5(const Level& L, const float* x, float* y, const int* skip, int* err, cudaStream_t s,
-                                  int gw) {
+cudaError_t launch_apply_prism_t5(const Level& L, const float* x, float* y, const int* skip, int* err, cudaStream_t s) {
     if (L.p != 6 || L.pz != 6 || L.dim != 3 || L.G16T == nullptr) return cudaErrorInvalidValue;
-    if (gw == 0) gw = L.t6_warps;
-    if (gw != 4 && gw != 8) return cudaErrorInvalidValue;
     static bool configured[64] = {};
     static int sms[64] = {};
     int dev = 0;
@@ -631,9 +584,7 @@ cudaError_t launch_apply_prism_t5(const Level& L, const float* x, float* y, cons
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!configured[dev]) {
-        e = cudaFuncSetAttribute(k_apply_prism_t6<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_apply_prism_t6<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+        e = cudaFuncSetAttribute(k_apply_prism_t6, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
@@ -647,13 +598,9 @@ cudaError_t launch_apply_prism_t5(const Level& L, const float* x, float* y, cons
     const int npass = (L.E + EB - 1) / EB;
     const int grid = npass < sms[dev] ? npass : sms[dev];
     if (grid < 1) return cudaSuccess;
-    const __nv_bfloat16* g6 = reinterpret_cast<const __nv_bfloat16*>(L.G16T);
-    if (gw == 8)
-        k_apply_prism_t6<8><<<grid, t6_threads(8), SMEM, s>>>(L.E, (int)L.N, npass, L.map, g6, L.ref32.m, vc, x, y,
-                                                               skip, err);
-    else
-        k_apply_prism_t6<4><<<grid, t6_threads(4), SMEM, s>>>(L.E, (int)L.N, npass, L.map, g6, L.ref32.m, vc, x, y,
-                                                               skip, err);
+    k_apply_prism_t6<<<grid, kT6Threads, SMEM, s>>>(L.E, (int)L.N, npass, L.map,
+                                                   reinterpret_cast<const __nv_bfloat16*>(L.G16T), L.ref32.m, vc, x,
+                                                   y, skip, err);
     return cudaGetLastError();
 }
 

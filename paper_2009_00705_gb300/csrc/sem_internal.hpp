@@ -62,7 +62,6 @@ struct Level {
     int tile64 = 0, tile32 = 0;            // prism apply tile-shape variant (autotuned)
     int tc_kind = 1;                       // tensor-core smoothing operator (MIXED_TF32): 0 warp-level MMA,
                                            // 1 tcgen05 where compiled (order 6); autotuned at setup
-    int t6_warps = 8;                      // warps per compute group of the tcgen05 kernel (4 or 8; autotuned)
     int* csr_rowptr = nullptr;             // coarse level: assembled matrix, free rows/cols
     int* csr_col = nullptr;
     double* csr_val = nullptr;
@@ -258,16 +257,15 @@ cudaError_t launch_apply_prism_tc(const Level& L, const float* x, float* y, cons
                                   cudaStream_t s);
 bool prism_tc_supported(int p);
 // apply_prism_t5.cu: the order-6 prism apply on tcgen05 (TMEM accumulators, operands read from
-// shared memory by descriptor); same arguments and error flag as launch_apply_prism_tc; gw = warps
-// per compute group (4 or 8; 0 = the level's autotuned choice)
+// shared memory by descriptor); same arguments and error flag as launch_apply_prism_tc
 cudaError_t launch_apply_prism_t5(const Level& L, const float* x, float* y, const int* skip, int* err,
-                                  cudaStream_t s, int gw = 0);
+                                  cudaStream_t s);
 bool prism_t5_supported(int p);
 // the tensor-core apply of a level: the warp-MMA kernel (the V-cycle's), or the tcgen05 kernel
 // where it is compiled (order 6) when tcgen05 is set
 inline cudaError_t launch_apply_tensor(const Level& L, const float* x, float* y, const int* skip, int* err,
-                                       cudaStream_t s, bool tcgen05 = false, int gw = 0) {
-    return tcgen05 ? launch_apply_prism_t5(L, x, y, skip, err, s, gw) : launch_apply_prism_tc(L, x, y, skip, err, s);
+                                       cudaStream_t s, bool tcgen05 = false) {
+    return tcgen05 ? launch_apply_prism_t5(L, x, y, skip, err, s) : launch_apply_prism_tc(L, x, y, skip, err, s);
 }
 // the tensor-core apply serves isotropic prism levels of order 2..6
 inline bool level_tc(const Level& L) { return L.dim == 3 && L.pz == L.p && prism_tc_supported(L.p); }

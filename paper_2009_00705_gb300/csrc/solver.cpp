@@ -557,14 +557,8 @@ cudaError_t tune_prism(Level& L, bool fp32) {
 }
 
 // The tensor-core smoothing operator of an order-6 level: times the warp-level MMA kernel and
-// the tcgen05 kernel with compute groups of four and of eight warps on the level's own mesh and
-// keeps the fastest (cached like the tile shapes).
+// the tcgen05 kernel on the level's own mesh and keeps the faster (cached like the tile shapes).
 std::map<std::pair<int, int>, int> g_tc_cache;
-
-void set_tc_choice(Level& L, int v) {
-    L.tc_kind = v > 0 ? 1 : 0;
-    L.t6_warps = v == 1 ? 4 : 8;
-}
 
 cudaError_t tune_tc(Level& L) {
     L.tc_kind = 0;
@@ -576,7 +570,7 @@ cudaError_t tune_tc(Level& L) {
         std::lock_guard<std::mutex> lock(g_tile_mutex);
         auto it = g_tc_cache.find(key);
         if (it != g_tc_cache.end()) {
-            set_tc_choice(L, it->second);
+            L.tc_kind = it->second;
             return cudaSuccess;
         }
     }
@@ -588,12 +582,11 @@ cudaError_t tune_tc(Level& L) {
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     float best = 1e30f;
     int choice = 0;
-    for (int v = 0; v < 3 && e == cudaSuccess; ++v) {
-        set_tc_choice(L, v);
+    for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
         for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
             if (rep == 1) e = cudaEventRecord(e0, 0);
             cudaMemsetAsync(L.y32, 0, sizeof(float) * L.N, 0);
-            if (e == cudaSuccess) e = launch_apply_tensor(L, L.u32, L.y32, nullptr, err, 0, v > 0);
+            if (e == cudaSuccess) e = launch_apply_tensor(L, L.u32, L.y32, nullptr, err, 0, v == 1);
         }
         if (e == cudaSuccess) e = cudaEventRecord(e1, 0);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -604,8 +597,8 @@ cudaError_t tune_tc(Level& L) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(err);
-    set_tc_choice(L, choice);
     if (e != cudaSuccess) return e;
+    L.tc_kind = choice;
     std::lock_guard<std::mutex> lock(g_tile_mutex);
     g_tc_cache[key] = choice;
     return cudaSuccess;
@@ -1260,8 +1253,7 @@ sem_status sem_tc_kernel(const sem_handle* h, int level, int* kind) {
     CKST(check_level(h, level));
     if (!kind) { set_error("kind is NULL"); return SEM_EINVAL; }
     const Level& L = h->lv[level];
-    *kind = (h->opts.precision != SEM_PREC_MIXED_TF32 || !level_tc(L)) ? 0
-            : (L.tc_kind == 1 && L.G16T ? (L.t6_warps == 8 ? 3 : 2) : 1);
+    *kind = (h->opts.precision != SEM_PREC_MIXED_TF32 || !level_tc(L)) ? 0 : (L.tc_kind == 1 && L.G16T ? 2 : 1);
     return SEM_OK;
 }
 
@@ -1330,19 +1322,18 @@ sem_status sem_apply32(sem_handle* h, int level, const float* x, float* y, int t
     if (!x || !y || x == y) { set_error("sem_apply32: x and y must be distinct device buffers"); return SEM_EINVAL; }
     cudaStream_t s = as_stream(stream);
     const Level& L = h->lv[level];
-    if (tensor_cores < 0 || tensor_cores > 3) { set_error("sem_apply32: tensor_cores 0, 1, 2 or 3"); return SEM_EINVAL; }
+    if (tensor_cores < 0 || tensor_cores > 2) { set_error("sem_apply32: tensor_cores 0, 1 or 2"); return SEM_EINVAL; }
     if (tensor_cores) {
         if (!level_tc(L)) {
             set_error("sem_apply32: the tensor-core apply needs an isotropic prism level of order 2..6");
             return SEM_EINVAL;
         }
-        if (tensor_cores >= 2 && !prism_t5_supported(L.p)) {
+        if (tensor_cores == 2 && !prism_t5_supported(L.p)) {
             set_error("sem_apply32: the tcgen05 apply is compiled for order 6 only");
             return SEM_EINVAL;
         }
         CKS(cudaMemsetAsync(y, 0, sizeof(float) * L.N, s));
-        K(launch_apply_tensor(L, x, y, nullptr, h->sc.flags + F_TC_ERR, s, tensor_cores >= 2,
-                              tensor_cores == 3 ? 8 : 4));
+        K(launch_apply_tensor(L, x, y, nullptr, h->sc.flags + F_TC_ERR, s, tensor_cores == 2));
         CKS(cudaStreamSynchronize(s));
         sem_status ret = SEM_OK;
         CKST(check_tc_flag(h, &ret, true));

@@ -155,11 +155,11 @@ def test_tcgen05_apply_against_warp_mma_and_oracle(sem, n, nl):
         N = s.query(0)["ndof"]
         x = W.random_vector(N, seed=29).astype(np.float32)
         xd = torch.tensor(x, device="cuda")
-        ys = {k: torch.zeros(N, dtype=torch.float32, device="cuda") for k in (0, 1, 2, 3)}
+        ys = {k: torch.zeros(N, dtype=torch.float32, device="cuda") for k in (0, 1, 2)}
         for k, y in ys.items():
             s.apply32(0, xd, y, tensor_cores=k)
         torch.cuda.synchronize()
-        y32, ymma, y5, y8 = (ys[k].cpu().numpy().astype(np.float64) for k in (0, 1, 2, 3))
+        y32, ymma, y5 = (ys[k].cpu().numpy().astype(np.float64) for k in (0, 1, 2))
         _check_apply(y5, y32)
         _check_apply(ymma, y32)
         # the two tensor-core forms round alike (TF32 operands, BF16 factors): they agree more
@@ -169,9 +169,7 @@ def test_tcgen05_apply_against_warp_mma_and_oracle(sem, n, nl):
         rows = np.random.default_rng(4).choice(N, 120, replace=False)
         ref = prob.apply_rows(0, x.astype(np.float64), rows)
         assert np.abs(y5[rows] - ref).max() <= 1e-2 * np.abs(ref).max()
-        # repeated launches, and the kernel with eight-warp compute groups (the same arithmetic per
-        # element on other warps), give the same result up to the order of the atomic summation
-        assert np.abs(y8 - y5).max() <= 1e-5 * np.abs(y5).max()
+        # repeated launches give the same result up to the order of the atomic summation
         y2 = torch.zeros(N, dtype=torch.float32, device="cuda")
         s.apply32(0, xd, y2, tensor_cores=2)
         torch.cuda.synchronize()
@@ -179,9 +177,8 @@ def test_tcgen05_apply_against_warp_mma_and_oracle(sem, n, nl):
         # the tcgen05 kernel exists for order 6 only
         if n == 3:
             xc = torch.zeros(s.query(1)["ndof"], dtype=torch.float32, device="cuda")
-            for k in (2, 3):
-                with pytest.raises(sem.SemError):
-                    s.apply32(1, xc, torch.zeros_like(xc), tensor_cores=k)
+            with pytest.raises(sem.SemError):
+                s.apply32(1, xc, torch.zeros_like(xc), tensor_cores=2)
     finally:
         s.close()
 
@@ -202,7 +199,7 @@ def test_mixed_tf32_solve_with_the_tcgen05_smoother_matches_oracle(sem, autotune
                 imax=100, autotune=autotune)
     try:
         kind = s.tc_kernel(0)
-        assert kind == 3 if autotune == 0 else kind in (1, 2, 3)
+        assert kind == 2 if autotune == 0 else kind in (1, 2)
         assert s.tc_kernel(1) == 1 and s.tc_kernel(2) == 0      # order 3: warp MMA; order 1: FP32
         phi = torch.zeros(lev.N, dtype=torch.float64, device="cuda")
         st = s.solve(torch.tensor(phiD, device="cuda"), phi, tol=1e-11)
