@@ -574,14 +574,18 @@ cudaError_t tune_tc(Level& L) {
             return cudaSuccess;
         }
     }
+    // the kernels' error flag: a kernel whose bounded copy or MMA wait ran out sets it, and such
+    // a kernel is not a candidate; none completing is an error of the setup
     int* err = nullptr;
     cudaError_t e = cudaMalloc(&err, sizeof(int));
     if (e != cudaSuccess) return e;
-    cudaEvent_t e0, e1;
-    e = cudaEventCreate(&e0);
+    e = cudaMemset(err, 0, sizeof(int));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     float best = 1e30f;
     int choice = 0;
+    bool any = false;
     for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
         for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
             if (rep == 1) e = cudaEventRecord(e0, 0);
@@ -592,11 +596,19 @@ cudaError_t tune_tc(Level& L) {
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        int timed_out = 0;
+        if (e == cudaSuccess) e = cudaMemcpy(&timed_out, err, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && timed_out) {
+            e = cudaMemset(err, 0, sizeof(int));
+            continue;
+        }
         if (e == cudaSuccess && ms < best) { best = ms; choice = v; }
+        if (e == cudaSuccess) any = true;
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
     cudaFree(err);
+    if (e == cudaSuccess && !any) e = cudaErrorLaunchTimeout;
     if (e != cudaSuccess) return e;
     L.tc_kind = choice;
     std::lock_guard<std::mutex> lock(g_tile_mutex);
