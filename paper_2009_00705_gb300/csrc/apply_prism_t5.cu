@@ -25,7 +25,10 @@
 //     8-column chunk of quadrature points per slot: the factors are stored per pass
 //     of 16 elements chunk by chunk ([chunk][factor][qz][element][8 qt]), so the
 //     next pass's chunk streams in as soon as this pass's has been used, and every
-//     read of a slot is a conflict-free 16-byte load.
+//     read of a slot is a conflict-free 16-byte load.  Consecutive uses of a slot belong
+//     to different groups, so the producer publishes the use it issued to each slot and
+//     a consumer begins its parity wait only once its use is issued (the use before has
+//     then landed: a parity wait cannot tell it apart from the one two uses earlier).
 // The operands sit in shared memory in the canonical no-swizzle K-major layout
 // (8-row x 16-byte core matrices, K-adjacent ones 128 B apart, row groups K * 32 B
 // apart); the row order r = 16 qz + b makes the gather's operand stores conflict-free.
@@ -141,6 +144,35 @@ __device__ bool t6_wait(uint32_t bar, uint32_t parity, volatile int* fail, int* 
     }
 }
 
+__device__ __forceinline__ void st_release_shared(int* p, int v) {
+    asm volatile("st.release.cta.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_acquire_shared(const int* p) {
+    int v;
+    asm volatile("ld.acquire.cta.shared::cta.b32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+    return v;
+}
+
+// Wait until the producer has issued use `use` of a factor slot.  The slot's uses go to both
+// groups, so a consumer has not seen the previous use complete; a parity wait begun before that
+// use landed would take the completion of the use before it (same parity) for its own.  Once
+// use `use` is issued, the previous use was consumed, hence landed, and the parity names `use`.
+// Same bounds and failure recording as t6_wait.
+__device__ bool t6_wait_issued(const int* issued, int use, volatile int* fail, int* err) {
+    if (ld_acquire_shared(issued) >= use) return true;
+    const unsigned long long t0 = t6_ns();
+    for (;;) {
+        if (ld_acquire_shared(issued) >= use) return true;
+        if (*fail) return false;
+        if (t6_ns() - t0 > kT6WaitNs) {
+            *fail = 1;
+            atomicExch(err, 1);
+            return false;
+        }
+    }
+}
+
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
@@ -224,6 +256,7 @@ __global__ void __launch_bounds__(kT6Threads, 1)
     __shared__ __align__(8) unsigned long long mbar[22];
     __shared__ uint32_t s_tmem;
     __shared__ int s_fail;
+    __shared__ int s_issued[NSLOT];    // use of each factor slot last issued by the producer
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t sbase = smem_u32(sm);
     const uint32_t mb0 = smem_u32(&mbar[0]);
@@ -255,6 +288,7 @@ __global__ void __launch_bounds__(kT6Threads, 1)
     }
     if (tid == 0) {
         s_fail = 0;
+        for (int i = 0; i < NSLOT; ++i) s_issued[i] = -1;
         for (int i = 0; i < 22; ++i) {
             const uint32_t cnt = (i >= 14 && i < 20) ? 4u : 1u;      // slot empty: one arrival per consumer warp
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb0 + 8u * i), "r"(cnt) : "memory");
@@ -298,6 +332,7 @@ __global__ void __launch_bounds__(kT6Threads, 1)
                     const int s = j % NSLOT, use = j / NSLOT;
                     if (use > 0 && !t6_wait(bar_slote(s), (uint32_t)((use - 1) & 1), fail, err)) { stop = true; break; }
                     if (*fail) { stop = true; break; }
+                    st_release_shared(&s_issued[s], use);
                     t6_copy(sbase + OFF_G + (uint32_t)s * CH_BYTES, src + (size_t)c * CH_BYTES,
                             c < NCH - 1 ? CH_BYTES : CH_LAST, bar_slotf(s));
                     issued[s] = use;
@@ -402,7 +437,8 @@ __global__ void __launch_bounds__(kT6Threads, 1)
                 tmem_ld8(trow + TM_UR + c0, ur);
                 tmem_ld8(trow + TM_US + c0, us);
                 tmem_ld8(trow + TM_UT + c0, ut);
-                const bool ok = t6_wait(bar_slotf(s), (uint32_t)((j / NSLOT) & 1), fail, err);
+                const bool ok = t6_wait_issued(&s_issued[s], j / NSLOT, fail, err) &&
+                                t6_wait(bar_slotf(s), (uint32_t)((j / NSLOT) & 1), fail, err);
                 const unsigned char* slot = sm + OFF_G + (uint32_t)s * CH_BYTES;
                 float gf[6][8];
                 if (c < NCH - 1) {
